@@ -1,0 +1,195 @@
+/*
+ * lbm_stefan.h -- C ABI of the GB300 IREBM library.
+ *
+ * The library advances the implicit regularized enthalpy based lattice
+ * Boltzmann method (IREBM) of Luddens, Lothode and Danaila, "An implicit
+ * regularized enthalpy Lattice Boltzmann Method for the Stefan problem"
+ * (arXiv 2505.13097), on one GPU.  One call of lbm_stefan_step() runs
+ * Algorithm 3 of the paper once per step: collision (Eq. 12), pull
+ * streaming, the boundary closures of Sec. 4.2 on q, the zeroth moment, the
+ * local Newton solve of Eq. (14), the source of Eq. (13), and the next
+ * collision, fused into one kernel launch per step.
+ *
+ * Problem statement (Sec. 2, Eq. 1): dimensionless temperature theta with
+ * melting temperature 0, Stefan number Ste, equal phase properties; the
+ * liquid fraction is regularized as phi(theta) = (1 + tanh(theta/delta))/2
+ * (Sec. 4.1).  The lattice spacing is one node; tau - 1/2 = 3 dt/dx^2
+ * (end of Sec. 5) maps steps to physical time.
+ *
+ * Conventions for every entry point:
+ *  - Fields are row-major (ny rows of nx values, x fastest); D1Q3 uses ny = 1.
+ *  - Host pointers are read or written synchronously.  With on_device = 1 the
+ *    pointer is a device address (for instance a torch CUDA tensor), accessed
+ *    in order on the handle's stream.
+ *  - The library owns all its device buffers; the caller owns what it passes.
+ *  - Functions return lbm_status; nothing aborts.  lbm_stefan_last_error()
+ *    returns a message for the last failure on the calling thread.
+ *  - Kernels run asynchronously on the stream given at creation.  Errors the
+ *    device detects (Newton not converged, non-finite values) are sticky and
+ *    returned by the next call that synchronizes (lbm_stefan_sync,
+ *    lbm_stefan_get_fields, lbm_stefan_get_stats, ...).
+ */
+#ifndef LBM_STEFAN_H
+#define LBM_STEFAN_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_stefan lbm_stefan;             /* one problem, opaque */
+typedef struct lbm_stefan_batch lbm_stefan_batch; /* many problems, opaque */
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = 1,     /* invalid argument (sizes, tau <= 1/2, Ste <= 0, delta <= 0, NULL, ...) */
+    LBM_ERR_CUDA = 2,    /* a CUDA runtime call failed */
+    LBM_ERR_NEWTON = 3,  /* a node's Newton solve hit its iteration limit, or a value was not finite */
+    LBM_ERR_TIMEOUT = 4, /* reserved for bounded device waits */
+    LBM_ERR_STATE = 5    /* call out of order (e.g. step before set_ic) */
+} lbm_status;
+
+enum { LBM_D1Q3 = 1, LBM_D2Q9 = 2 };                          /* lattice (Sec. 3.2) */
+enum { LBM_FP64 = 0, LBM_FP32 = 1 };                           /* population storage */
+enum { LBM_WALL_W = 0, LBM_WALL_E = 1, LBM_WALL_S = 2, LBM_WALL_N = 3 };
+enum { LBM_ADIABATIC = 0, LBM_DIRICHLET = 1 };                 /* wall kinds (Sec. 4.2) */
+enum { LBM_BB_MIRROR = 0, LBM_BB_LINK = 1 };                   /* bounce-back forms */
+
+typedef struct {
+    int lattice;          /* LBM_D1Q3 or LBM_D2Q9 */
+    int nx, ny;           /* nodes per side, >= 2 (ny = 1 for D1Q3) */
+    double tau;           /* BGK relaxation time, > 1/2 (Eq. 8) */
+    double delta;         /* regularization width of phi, > 0 (Sec. 4.1) */
+    double ste;           /* Stefan number, > 0 (Eq. 1) */
+    int precision;        /* LBM_FP64: everything FP64; LBM_FP32: populations stored and
+                             relaxed in FP32, moments as float-float sums, Newton in FP64 */
+    double newton_tol;    /* step tolerance of the Newton solve (Algorithm 3), e.g. 1e-14 */
+    int newton_max_iter;  /* iteration limit, e.g. 60; reaching it sets LBM_ERR_NEWTON */
+    int bb_mode;          /* LBM_BB_MIRROR: q_i = q_{bar i} (Sec. 4.2.2); LBM_BB_LINK: q_i = Omega_{bar i} */
+} lbm_stefan_params;
+
+typedef struct {
+    double energy;         /* E = sum_x theta + phi(theta)/Ste after the last step (FP64) */
+    double energy_prev;    /* E before the last step */
+    double flux;           /* boundary flux of the last step: filled q minus Omega leaving */
+    double imbalance;      /* E - energy_prev - flux of the last step (energy balance) */
+    double imbalance_max;  /* largest |imbalance| since set_ic */
+    long long steps;       /* steps since set_ic */
+    long long newton_nodes;/* nodes that ran the Newton iteration in the last step */
+    int newton_max_iter;   /* largest iteration count in the last step */
+    int error;             /* sticky device error (lbm_status value, 0 if none) */
+} lbm_stefan_stats;
+
+/* ---------------------------------------------------------------- one problem */
+
+/* Create a problem.  cuda_stream is a cudaStream_t (NULL = legacy default
+ * stream).  All walls start adiabatic; the state is undefined until set_ic. */
+lbm_status lbm_stefan_create(const lbm_stefan_params* p, void* cuda_stream, lbm_stefan** out);
+
+/* Boundary condition of one wall (Sec. 4.2): kind LBM_DIRICHLET holds theta at
+ * theta_wall through the closure of Eq. (15) on q; LBM_ADIABATIC applies
+ * bounce-back.  A node on a Dirichlet wall is a Dirichlet node (corners
+ * included); its value is that of the first Dirichlet wall in W, E, S, N.
+ * Call before set_ic so that Dirichlet nodes start at theta_wall. */
+lbm_status lbm_stefan_set_bc(lbm_stefan* h, int wall, int kind, double theta_wall);
+
+/* Initial state: f_i = w_i theta0 (equilibrium), Dirichlet nodes at their wall
+ * value.  theta0 holds nx*ny doubles.  Resets the step counter and stats. */
+lbm_status lbm_stefan_set_ic(lbm_stefan* h, const double* theta0, int on_device);
+
+/* Advance nsteps >= 0 steps (Algorithm 3), asynchronously on the stream.
+ * Every step also forms the energy E and the boundary flux on the device. */
+lbm_status lbm_stefan_step(lbm_stefan* h, int nsteps);
+
+/* Advance nsteps steps and write theta(t+1), ..., theta(t+nsteps) to
+ * theta_traj (device, nsteps planes of ny*row_stride doubles, row_stride from
+ * lbm_stefan_layout).  Used to recompute a checkpoint segment for the adjoint. */
+lbm_status lbm_stefan_step_record(lbm_stefan* h, int nsteps, double* theta_traj);
+
+/* Wait for the stream; return the sticky device error, if any. */
+lbm_status lbm_stefan_sync(lbm_stefan* h);
+
+/* theta = M0(f), phi(theta) and H = theta + phi/Ste (Sec. 2), nx*ny doubles
+ * each; any of the three may be NULL.  Synchronizes. */
+lbm_status lbm_stefan_get_fields(lbm_stefan* h, double* theta, double* phi, double* H, int on_device);
+
+/* Energy, flux, Newton statistics and the sticky error.  Synchronizes. */
+lbm_status lbm_stefan_get_stats(lbm_stefan* h, lbm_stefan_stats* out);
+
+/* Device layout: bytes of one state (all populations, with padding) and the
+ * row stride, in elements, of state rows and of recorded theta planes. */
+lbm_status lbm_stefan_layout(lbm_stefan* h, size_t* state_bytes, int* row_stride);
+
+/* Copy the whole state (populations, step counter kept on the host) to or from
+ * buf, state_bytes long.  For checkpoint / resume. */
+lbm_status lbm_stefan_get_state(lbm_stefan* h, void* buf, int on_device);
+lbm_status lbm_stefan_set_state(lbm_stefan* h, const void* buf, int on_device);
+
+/* theta of the current state written to one recorded-theta plane (device,
+ * ny*row_stride doubles): the start of a recorded trajectory. */
+lbm_status lbm_stefan_theta_plane(lbm_stefan* h, double* theta_plane);
+
+/* ---------------------------------------------------------------- adjoint
+ * Discrete adjoint of the step above, for the misfit
+ *     L = 1/2 sum_x (phi(theta_T(x)) - phi_target(x))^2.
+ * Adjoint states have the layout and precision of the forward state.  The
+ * Newton root enters through the implicit function theorem on
+ * F(x) = x + phi(x)/Ste - m0 - phi(theta)/Ste (Eq. 14).  Gradients with
+ * respect to the wall temperatures and Ste accumulate on the device. */
+
+/* lambda_T = dL/dOmega(T) from theta_T (a recorded plane) and phi_target
+ * (device, nx*ny doubles); clears the wall / Ste accumulators.  If loss is
+ * not NULL it receives L (synchronizes). */
+lbm_status lbm_stefan_adjoint_seed(lbm_stefan* h, const double* theta_T, const double* phi_target,
+                                   void* adj, double* loss);
+
+/* One reverse step: adj_out = (dOmega(t+1)/dOmega(t))^T adj_in, with the
+ * recorded planes theta_t = theta(t) and theta_t1 = theta(t+1). */
+lbm_status lbm_stefan_adjoint_step(lbm_stefan* h, const double* theta_t, const double* theta_t1,
+                                   const void* adj_in, void* adj_out);
+
+/* From lambda_0: dL/dtheta0 (nx*ny doubles, zero on Dirichlet nodes),
+ * dL/dtheta_wall[4] (walls that are not Dirichlet get 0) and dL/dSte.
+ * Synchronizes. */
+lbm_status lbm_stefan_adjoint_finish(lbm_stefan* h, const void* adj0, double* g_theta0, int on_device,
+                                     double* g_wall, double* g_ste);
+
+void lbm_stefan_destroy(lbm_stefan* h);
+
+/* ---------------------------------------------------------------- batches
+ * Many independent D2Q9 problems of uneven sizes advanced by one persistent
+ * kernel launch per step; the launches of a call are captured in a CUDA
+ * graph.  Tile height and the tile-to-warp schedule come from
+ * lbm_stefan_batch_autotune (or defaults). */
+
+typedef struct {
+    int nx, ny;                 /* >= 2 each */
+    double tau, delta, ste;
+    int wall_kind[4];           /* W, E, S, N */
+    double wall_theta[4];
+} lbm_stefan_problem;
+
+lbm_status lbm_stefan_batch_create(int count, const lbm_stefan_problem* problems, int precision,
+                                   double newton_tol, int newton_max_iter, void* cuda_stream,
+                                   lbm_stefan_batch** out);
+lbm_status lbm_stefan_batch_set_ic(lbm_stefan_batch* b, int k, const double* theta0, int on_device);
+lbm_status lbm_stefan_batch_step(lbm_stefan_batch* b, int nsteps);
+lbm_status lbm_stefan_batch_get_fields(lbm_stefan_batch* b, int k, double* theta, int on_device);
+lbm_status lbm_stefan_batch_get_stats(lbm_stefan_batch* b, int k, lbm_stefan_stats* out);
+/* Time candidate tile heights and schedules for trial_steps steps each and
+ * keep the fastest; the state is saved and restored around the trials.
+ * chosen_tile_h receives the chosen height (may be NULL). */
+lbm_status lbm_stefan_batch_autotune(lbm_stefan_batch* b, int trial_steps, int* chosen_tile_h);
+/* Set the tile height (rows per warp tile) and schedule (0 = problem order,
+ * 1 = longest tiles first, round-robin over warps) explicitly. */
+lbm_status lbm_stefan_batch_set_schedule(lbm_stefan_batch* b, int tile_h, int schedule);
+void lbm_stefan_batch_destroy(lbm_stefan_batch* b);
+
+const char* lbm_stefan_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_STEFAN_H */

@@ -1,0 +1,509 @@
+/*
+ * FP64 CPU oracle of the implicit regularized enthalpy based method (IREBM).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py load this library.  It shares no
+ * code, header, table or constant with the CUDA library: lattice tables, the
+ * boundary closures, the Newton solve and the adjoint are all written here
+ * again, on purpose, in the plainest form.
+ *
+ * Source: F. Luddens, C. Lothode, I. Danaila, "An implicit regularized
+ * enthalpy Lattice Boltzmann Method for the Stefan problem" (arXiv 2505.13097).
+ * Equation numbers follow the paper's order of numbered equations:
+ *   (12) def_qi_omegai   Omega_i = (1-1/tau) f_i + f_i^eq / tau, q_i = streamed Omega_i
+ *   (13) rhs_fl_stag     f_i(t+1) = q_i + (w_i/Ste)(phi(theta) - phi(theta~))
+ *   (14) rhs_fl_2        theta~ = M0(q) + (phi(theta) - phi(theta~))/Ste
+ *   (15) Dirichlet       closure on M0(q) at a Dirichlet node
+ *   (16) Dir_on_q        single-unknown form of (15) (D1Q3, D2Q5)
+ * Algorithm 3 (IREBM step) fixes the order of the step.  Sec. 4.2.2 gives the
+ * bounce-back closure q_ix = q_{bar ix}.
+ *
+ * Storage: the oracle stores the distributions f_i (q planes of nx*ny doubles,
+ * x fastest) and recomputes theta = M0(f) at the start of every step, exactly
+ * as Algorithm 3 does.  No blocking, fusion or reordering.
+ *
+ * Readings where the paper is silent (each is listed in the design doc):
+ *  - weights: D1Q3 (2/3, 1/6, 1/6), D2Q9 (4/9, 1/9 x4, 1/36 x4), c_s^2 = 1/3.
+ *  - Newton stopping: |x_{k+1}-x_k| <= tol*max(1,|x_k|) (x_{k+1} kept), or
+ *    F(x_k) = 0, or a bracket narrower than that; at most maxit iterations.
+ *  - Newton safeguard: the root lies in [rhs-1/Ste, rhs] (0 <= phi <= 1 and
+ *    F increasing); an iterate that leaves the current bracket is replaced by
+ *    the bracket midpoint.
+ *  - Dirichlet on D2Q9: the unknown q_i share R = m0_target - sum(known q)
+ *    in proportion to w_i.  m0_target follows from Eq. (14) with
+ *    theta~ = theta_D (see orc_dirichlet_m0 for the sign of the phi term).
+ *  - A node on a Dirichlet wall is a Dirichlet node, corners included
+ *    ("Dirichlet beats Neumann"); its value is that of the first Dirichlet
+ *    wall in the order W, E, S, N.
+ *  - Bounce-back: mirror q_i = q_{bar i} (Sec. 4.2.2) where q_{bar i} is known,
+ *    else (corner diagonals, thin domains) link-wise q_i = Omega_{bar i} at the
+ *    node.  bb_mode = 1 uses the link-wise form for every unknown direction.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_MAXQ 9
+
+typedef struct {
+    int lattice;          /* 1 = D1Q3, 2 = D2Q9 */
+    int nx, ny;           /* ny = 1 for D1Q3 */
+    double tau, delta, ste;
+    double newton_tol;
+    int newton_max_iter;
+    int bb_mode;          /* 0 = mirror (Sec. 4.2.2), 1 = link-wise */
+    int wall_kind[4];     /* W, E, S, N: 0 = adiabatic, 1 = Dirichlet */
+    double wall_theta[4];
+} orc_params;
+
+typedef struct {          /* per-step diagnostics */
+    double energy_before; /* sum_x theta + phi(theta)/Ste at time t   */
+    double energy_after;  /* same at time t+1 (theta = M0(f(t+1)))    */
+    double flux;          /* sum of filled q minus Omega leaving the lattice */
+    int max_iter;         /* largest Newton iteration count            */
+    int failed;           /* number of nodes where Newton did not converge */
+} orc_diag;
+
+/* ---- lattice tables (Sec. 3.2; weights are the standard ones) ---- */
+static int lat_q(const orc_params* p) { return p->lattice == 1 ? 3 : 9; }
+
+static void lat_vec(const orc_params* p, int i, int* ex, int* ey, double* w)
+{
+    if (p->lattice == 1) {
+        static const int e1[3] = {0, 1, -1};
+        static const double w1[3] = {2.0 / 3.0, 1.0 / 6.0, 1.0 / 6.0};
+        *ex = e1[i]; *ey = 0; *w = w1[i];
+    } else {
+        static const int e2x[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+        static const int e2y[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+        static const double w2[9] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0,
+                                     1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+        *ex = e2x[i]; *ey = e2y[i]; *w = w2[i];
+    }
+}
+
+/* index of the direction opposite to i: e_{bar i} = -e_i */
+static int lat_opp(const orc_params* p, int i)
+{
+    int ex, ey, jx, jy, j, q = lat_q(p);
+    double w;
+    lat_vec(p, i, &ex, &ey, &w);
+    for (j = 0; j < q; j++) {
+        lat_vec(p, j, &jx, &jy, &w);
+        if (jx == -ex && jy == -ey) return j;
+    }
+    return -1;
+}
+
+/* ---- regularized liquid fraction, Sec. 4.1: phi_d = (1 + tanh(x/d))/2 ---- */
+double orc_phi(double x, double delta) { return 0.5 * (1.0 + tanh(x / delta)); }
+
+double orc_dphi(double x, double delta)
+{
+    double t = tanh(x / delta);
+    return 0.5 * (1.0 - t * t) / delta;
+}
+
+/*
+ * Local Newton solve of Eq. (14): find x with
+ *     F(x) = (x - m0) + (phi(x) - phi(theta))/Ste = 0,
+ * using the update of Algorithm 3 started at x = theta.  F' = 1 + phi'/Ste >= 1,
+ * so the root is unique.  The two phi terms of Algorithm 3's update are
+ * grouped as (phi(theta) - phi(x))/Ste so that they cancel before the division
+ * by Ste (same algebra, no loss of the low bits of m0 when 1/Ste is large).
+ * Stops when a Newton update moves x by at most tol*max(1,|x|) (that update
+ * is kept; the test comes before the safeguard, so a last correction that
+ * rounds just outside the bracket is not mistaken for a wild step), when F(x)
+ * is exactly 0, or when the safeguard bracket has shrunk below that size.  Returns the root; *iters = iterations used; *ok = 0 if
+ * maxit was reached first.
+ */
+double orc_newton(double m0, double theta, double ste, double delta, double tol, int maxit,
+                  int* iters, int* ok)
+{
+    double pth = orc_phi(theta, delta);
+    double lo = m0 + (pth - 1.0) / ste, hi = m0 + pth / ste;   /* F(lo) <= 0 <= F(hi): 0 <= phi <= 1 */
+    double x = theta;
+    int k;
+    *ok = 0;
+    for (k = 0; k < maxit; k++) {
+        double t = tanh(x / delta);
+        double ph = 0.5 * (1.0 + t), dph = 0.5 * (1.0 - t * t) / delta;
+        double F = (x - m0) + (ph - pth) / ste;
+        double xn;
+        if (F == 0.0) { *ok = 1; break; }
+        if (F < 0.0) { if (x > lo) lo = x; } else { if (x < hi) hi = x; }
+        /* Algorithm 3: theta^(k+1) = (m0 + phi(theta)/Ste + phi'(x) x/Ste - phi(x)/Ste) / (1 + phi'(x)/Ste) */
+        xn = (m0 + (pth - ph) / ste + dph * x / ste) / (1.0 + dph / ste);
+        if (fabs(xn - x) <= tol * fmax(1.0, fabs(x))) { x = xn; *ok = 1; k++; break; }
+        if (!(xn >= lo && xn <= hi)) {             /* safeguard: bisect the bracket */
+            xn = 0.5 * (lo + hi);
+            if (hi - lo <= tol * fmax(1.0, fabs(xn))) { x = xn; *ok = 1; k++; break; }
+        }
+        x = xn;
+    }
+    *iters = k;
+    return x;
+}
+
+/* ---- node classification for the boundary closures (Sec. 4.2) ---- */
+static int inside(const orc_params* p, int x, int y) { return x >= 0 && x < p->nx && y >= 0 && y < p->ny; }
+
+/* walls touching node (x,y): bit 0 = W, 1 = E, 2 = S, 3 = N */
+static int node_walls(const orc_params* p, int x, int y)
+{
+    int m = 0;
+    if (x == 0) m |= 1;
+    if (x == p->nx - 1) m |= 2;
+    if (p->lattice == 2) {
+        if (y == 0) m |= 4;
+        if (y == p->ny - 1) m |= 8;
+    }
+    return m;
+}
+
+/* 1 and the wall value if the node lies on a Dirichlet wall (first in W, E, S, N) */
+static int node_dirichlet(const orc_params* p, int x, int y, double* theta_d, int* wall)
+{
+    int m = node_walls(p, x, y), k;
+    for (k = 0; k < 4; k++)
+        if ((m >> k & 1) && p->wall_kind[k] == 1) {
+            *theta_d = p->wall_theta[k];
+            if (wall) *wall = k;
+            return 1;
+        }
+    return 0;
+}
+
+/*
+ * Target of M0(q) at a Dirichlet node.  Eq. (14) with theta~ = theta_D gives
+ *     M0(q) = theta_D + (phi(theta_D) - phi(theta))/Ste,
+ * theta being the node's current temperature.  Eq. (15) prints the phi
+ * difference with the opposite sign; both coincide when theta = theta_D,
+ * which holds at every step once the wall node starts at theta_D.
+ */
+static double orc_dirichlet_m0(const orc_params* p, double theta_d, double theta)
+{
+    return theta_d + (orc_phi(theta_d, p->delta) - orc_phi(theta, p->delta)) / p->ste;
+}
+
+/* ---- initial state: f_i = w_i theta0 (equilibrium); Dirichlet nodes at theta_D ---- */
+void orc_init(const orc_params* p, const double* theta0, double* f)
+{
+    int q = lat_q(p), n = p->nx * p->ny, x, y, i, ex, ey;
+    double w;
+    for (y = 0; y < p->ny; y++)
+        for (x = 0; x < p->nx; x++) {
+            double th = theta0[y * p->nx + x], td;
+            if (node_dirichlet(p, x, y, &td, NULL)) th = td;
+            for (i = 0; i < q; i++) {
+                lat_vec(p, i, &ex, &ey, &w);
+                f[i * n + y * p->nx + x] = w * th;
+            }
+        }
+}
+
+/* theta = M0(f) (Algorithm 3, line "moments") */
+void orc_theta(const orc_params* p, const double* f, double* theta)
+{
+    int q = lat_q(p), n = p->nx * p->ny, k, i;
+    for (k = 0; k < n; k++) {
+        double s = 0.0;
+        for (i = 0; i < q; i++) s += f[i * n + k];
+        theta[k] = s;
+    }
+}
+
+double orc_energy(const orc_params* p, const double* f)
+{
+    int q = lat_q(p), n = p->nx * p->ny, k, i;
+    double e = 0.0;
+    for (k = 0; k < n; k++) {
+        double th = 0.0;
+        for (i = 0; i < q; i++) th += f[i * n + k];
+        e += th + orc_phi(th, p->delta) / p->ste;
+    }
+    return e;
+}
+
+/*
+ * One IREBM time step, Algorithm 3, f -> fn.
+ * Optional outputs (may be NULL): per-node m0, theta (time t), theta~ (root),
+ * Newton iterations, and the step diagnostics.
+ */
+int orc_step(const orc_params* p, const double* f, double* fn, double* m0_out, double* theta_out,
+             double* root_out, int* iters_out, orc_diag* diag)
+{
+    const int q = lat_q(p), nx = p->nx, ny = p->ny, n = nx * ny;
+    const double omega = 1.0 / p->tau;
+    double* theta = (double*)malloc(sizeof(double) * n);
+    double* Om = (double*)malloc(sizeof(double) * q * n);
+    double flux = 0.0, e0 = 0.0, e1 = 0.0;
+    int x, y, i, failed = 0, maxit_seen = 0;
+    int ex[ORC_MAXQ], ey[ORC_MAXQ], opp[ORC_MAXQ];
+    double w[ORC_MAXQ];
+    if (!theta || !Om) { free(theta); free(Om); return -1; }
+    for (i = 0; i < q; i++) { lat_vec(p, i, &ex[i], &ey[i], &w[i]); opp[i] = lat_opp(p, i); }
+
+    /* moments: theta <- M0(f) */
+    orc_theta(p, f, theta);
+    if (diag)
+        for (x = 0; x < n; x++) e0 += theta[x] + orc_phi(theta[x], p->delta) / p->ste;
+
+    /* equilibrium and collision, Eq. (12): Omega_i = (1-1/tau) f_i + w_i theta / tau */
+    for (i = 0; i < q; i++)
+        for (x = 0; x < n; x++) Om[i * n + x] = (1.0 - omega) * f[i * n + x] + omega * w[i] * theta[x];
+
+    /* Omega leaving the lattice (for the energy balance) */
+    for (y = 0; y < ny; y++)
+        for (x = 0; x < nx; x++)
+            for (i = 0; i < q; i++)
+                if (!inside(p, x + ex[i], y + ey[i])) flux -= Om[i * n + y * nx + x];
+
+    for (y = 0; y < ny; y++)
+        for (x = 0; x < nx; x++) {
+            const int k = y * nx + x;
+            double qv[ORC_MAXQ];
+            int known[ORC_MAXQ], nunk = 0;
+            double m0, root, td, g;
+            int it, ok;
+
+            /* streaming: q_i(y) = Omega_i(y - e_i) where y - e_i is in the lattice */
+            for (i = 0; i < q; i++) {
+                int sx = x - ex[i], sy = y - ey[i];
+                known[i] = inside(p, sx, sy);
+                qv[i] = known[i] ? Om[i * n + sy * nx + sx] : 0.0;
+                if (!known[i]) nunk++;
+            }
+
+            /* boundary closures on q (Sec. 4.2) */
+            if (nunk > 0) {
+                if (node_dirichlet(p, x, y, &td, NULL)) {
+                    /* Eq. (15): M0(q) = m0_target; unknowns share the rest by weight */
+                    double rest = orc_dirichlet_m0(p, td, theta[k]), wu = 0.0;
+                    for (i = 0; i < q; i++) {
+                        if (known[i]) rest -= qv[i];
+                        else wu += w[i];
+                    }
+                    for (i = 0; i < q; i++)
+                        if (!known[i]) qv[i] = w[i] * rest / wu;
+                } else {
+                    /* bounce-back, Sec. 4.2.2 */
+                    for (i = 0; i < q; i++)
+                        if (!known[i]) {
+                            if (p->bb_mode == 0 && known[opp[i]]) qv[i] = qv[opp[i]];
+                            else qv[i] = Om[opp[i] * n + k];
+                        }
+                }
+                for (i = 0; i < q; i++)
+                    if (!known[i]) flux += qv[i];
+            }
+
+            /* Newton initialization and loop (Algorithm 3) */
+            m0 = 0.0;
+            for (i = 0; i < q; i++) m0 += qv[i];
+            root = orc_newton(m0, theta[k], p->ste, p->delta, p->newton_tol, p->newton_max_iter, &it, &ok);
+            if (!ok) failed++;
+            if (it > maxit_seen) maxit_seen = it;
+
+            /* source term and update, Eq. (13) */
+            g = (orc_phi(theta[k], p->delta) - orc_phi(root, p->delta)) / p->ste;
+            for (i = 0; i < q; i++) fn[i * n + k] = qv[i] + w[i] * g;
+
+            if (m0_out) m0_out[k] = m0;
+            if (theta_out) theta_out[k] = theta[k];
+            if (root_out) root_out[k] = root;
+            if (iters_out) iters_out[k] = it;
+        }
+
+    if (diag) {
+        double th;
+        for (x = 0; x < n; x++) {
+            th = 0.0;
+            for (i = 0; i < q; i++) th += fn[i * n + x];
+            e1 += th + orc_phi(th, p->delta) / p->ste;
+        }
+        diag->energy_before = e0;
+        diag->energy_after = e1;
+        diag->flux = flux;
+        diag->max_iter = maxit_seen;
+        diag->failed = failed;
+    }
+    free(theta);
+    free(Om);
+    return failed;
+}
+
+/* nsteps steps from theta0; final f and theta. Returns the number of Newton failures. */
+int orc_run(const orc_params* p, const double* theta0, int nsteps, double* f_out, double* theta_out)
+{
+    int q = lat_q(p), n = p->nx * p->ny, s, failed = 0;
+    double* a = (double*)malloc(sizeof(double) * q * n);
+    double* b = (double*)malloc(sizeof(double) * q * n);
+    if (!a || !b) { free(a); free(b); return -1; }
+    orc_init(p, theta0, a);
+    for (s = 0; s < nsteps; s++) {
+        double* t;
+        int r = orc_step(p, a, b, NULL, NULL, NULL, NULL, NULL);
+        if (r < 0) { failed = -1; break; }
+        failed += r;
+        t = a; a = b; b = t;
+    }
+    if (f_out) memcpy(f_out, a, sizeof(double) * q * n);
+    if (theta_out) orc_theta(p, a, theta_out);
+    free(a);
+    free(b);
+    return failed;
+}
+
+/* ------------------------------------------------------------------------
+ * Liquid-fraction misfit and its FP64 discrete adjoint.
+ *
+ * Loss: L = 1/2 sum_x (phi(theta_T(x)) - phi_target(x))^2 with theta_T = M0(f_T).
+ * The adjoint is the exact transpose of the oracle's own step (the f storage
+ * above), by reverse accumulation over a tape of theta(t) and the Newton
+ * roots.  The Newton root enters through the implicit function theorem on
+ * F(x) = x + phi(x)/Ste - m0 - phi(theta)/Ste:
+ *   d root/d m0 = 1/F',  d root/d theta = phi'(theta)/(Ste F'),
+ *   d root/d Ste = (phi(root) - phi(theta))/(Ste^2 F'),  F' = 1 + phi'(root)/Ste.
+ * ------------------------------------------------------------------------ */
+double orc_loss(const orc_params* p, const double* theta0, int nsteps, const double* phi_target)
+{
+    int n = p->nx * p->ny, k;
+    double* th = (double*)malloc(sizeof(double) * n);
+    double L = 0.0;
+    if (!th) return NAN;
+    orc_run(p, theta0, nsteps, NULL, th);
+    for (k = 0; k < n; k++) {
+        double d = orc_phi(th[k], p->delta) - phi_target[k];
+        L += 0.5 * d * d;
+    }
+    free(th);
+    return L;
+}
+
+/*
+ * Gradient of orc_loss with respect to theta0 (n values; zero at Dirichlet
+ * nodes, whose initial value is the wall's), the four wall temperatures
+ * (only Dirichlet walls receive a value) and Ste.  Returns L.
+ */
+double orc_adjoint(const orc_params* p, const double* theta0, int nsteps, const double* phi_target,
+                   double* g_theta0, double* g_wall, double* g_ste)
+{
+    const int q = lat_q(p), nx = p->nx, ny = p->ny, n = nx * ny;
+    const double omega = 1.0 / p->tau, ste = p->ste, dl = p->delta;
+    double *f = NULL, *fn = NULL, *tape_th = NULL, *tape_root = NULL, *fb = NULL, *fbn = NULL;
+    double *Ob = NULL, *thb = NULL;
+    double L = 0.0, gste = 0.0, gw[4] = {0, 0, 0, 0};
+    int ex[ORC_MAXQ], ey[ORC_MAXQ], opp[ORC_MAXQ];
+    double w[ORC_MAXQ];
+    int s, x, y, i, k;
+
+    for (i = 0; i < q; i++) { lat_vec(p, i, &ex[i], &ey[i], &w[i]); opp[i] = lat_opp(p, i); }
+    f = (double*)malloc(sizeof(double) * q * n);
+    fn = (double*)malloc(sizeof(double) * q * n);
+    tape_th = (double*)malloc(sizeof(double) * (size_t)n * (nsteps + 1));
+    tape_root = (double*)malloc(sizeof(double) * (size_t)n * (nsteps > 0 ? nsteps : 1));
+    fb = (double*)malloc(sizeof(double) * q * n);
+    fbn = (double*)malloc(sizeof(double) * q * n);
+    Ob = (double*)malloc(sizeof(double) * q * n);
+    thb = (double*)malloc(sizeof(double) * n);
+    if (!f || !fn || !tape_th || !tape_root || !fb || !fbn || !Ob || !thb) { L = NAN; goto done; }
+
+    /* forward sweep, recording theta(t) and the roots */
+    orc_init(p, theta0, f);
+    for (s = 0; s < nsteps; s++) {
+        double* t;
+        orc_step(p, f, fn, NULL, tape_th + (size_t)s * n, tape_root + (size_t)s * n, NULL, NULL);
+        t = f; f = fn; fn = t;
+    }
+    orc_theta(p, f, tape_th + (size_t)nsteps * n);
+
+    /* seed: dL/df_i(T) = (phi(theta_T) - phi*) phi'(theta_T) for every i */
+    for (k = 0; k < n; k++) {
+        double thT = tape_th[(size_t)nsteps * n + k];
+        double d = orc_phi(thT, dl) - phi_target[k];
+        L += 0.5 * d * d;
+        for (i = 0; i < q; i++) fb[i * n + k] = d * orc_dphi(thT, dl);
+    }
+
+    for (s = nsteps - 1; s >= 0; s--) {
+        const double* th = tape_th + (size_t)s * n;
+        const double* rt = tape_root + (size_t)s * n;
+        memset(Ob, 0, sizeof(double) * q * n);
+        memset(thb, 0, sizeof(double) * n);
+        for (y = 0; y < ny; y++)
+            for (x = 0; x < nx; x++) {
+                const int kk = y * nx + x;
+                double qb[ORC_MAXQ], S = 0.0, rb, Fp, m0b, td;
+                int known[ORC_MAXQ], nunk = 0;
+                for (i = 0; i < q; i++) {
+                    known[i] = inside(p, x - ex[i], y - ey[i]);
+                    if (!known[i]) nunk++;
+                }
+                /* f(t+1)_i = q_i + w_i g,  g = (phi(theta) - phi(root))/Ste */
+                for (i = 0; i < q; i++) { qb[i] = fb[i * n + kk]; S += w[i] * fb[i * n + kk]; }
+                S /= ste;
+                thb[kk] += S * orc_dphi(th[kk], dl);
+                rb = -S * orc_dphi(rt[kk], dl);
+                gste += -S * (orc_phi(th[kk], dl) - orc_phi(rt[kk], dl)) / ste;
+                /* Newton root, implicit function theorem */
+                Fp = 1.0 + orc_dphi(rt[kk], dl) / ste;
+                m0b = rb / Fp;
+                thb[kk] += rb * orc_dphi(th[kk], dl) / (ste * Fp);
+                gste += rb * (orc_phi(rt[kk], dl) - orc_phi(th[kk], dl)) / (ste * ste * Fp);
+                for (i = 0; i < q; i++) qb[i] += m0b;
+                /* boundary closures, transposed */
+                if (nunk > 0) {
+                    int wall = -1;
+                    if (node_dirichlet(p, x, y, &td, &wall)) {
+                        double wu = 0.0, A = 0.0;
+                        for (i = 0; i < q; i++)
+                            if (!known[i]) wu += w[i];
+                        for (i = 0; i < q; i++)
+                            if (!known[i]) A += qb[i] * w[i] / wu;
+                        for (i = 0; i < q; i++)
+                            if (known[i]) qb[i] -= A;
+                        gw[wall] += A * (1.0 + orc_dphi(td, dl) / ste);
+                        thb[kk] += -A * orc_dphi(th[kk], dl) / ste;
+                        gste += -A * (orc_phi(td, dl) - orc_phi(th[kk], dl)) / (ste * ste);
+                    } else {
+                        for (i = 0; i < q; i++)
+                            if (!known[i]) {
+                                if (p->bb_mode == 0 && known[opp[i]]) qb[opp[i]] += qb[i];
+                                else Ob[opp[i] * n + kk] += qb[i];
+                            }
+                    }
+                }
+                /* streaming, transposed: q_i(y) = Omega_i(y - e_i) */
+                for (i = 0; i < q; i++)
+                    if (known[i]) Ob[i * n + (y - ey[i]) * nx + (x - ex[i])] += qb[i];
+            }
+        /* collision Omega_i = (1-omega) f_i + omega w_i theta and theta = M0(f), transposed */
+        for (k = 0; k < n; k++) {
+            double tb = thb[k];
+            for (i = 0; i < q; i++) tb += omega * w[i] * Ob[i * n + k];
+            for (i = 0; i < q; i++) fbn[i * n + k] = (1.0 - omega) * Ob[i * n + k] + tb;
+        }
+        { double* t = fb; fb = fbn; fbn = t; }
+    }
+
+    /* initial state f_i = w_i theta0 (or w_i theta_D on Dirichlet nodes) */
+    for (y = 0; y < ny; y++)
+        for (x = 0; x < nx; x++) {
+            const int kk = y * nx + x;
+            double s0 = 0.0, td;
+            int wall = -1;
+            for (i = 0; i < q; i++) s0 += w[i] * fb[i * n + kk];
+            if (node_dirichlet(p, x, y, &td, &wall)) {
+                gw[wall] += s0;
+                if (g_theta0) g_theta0[kk] = 0.0;
+            } else if (g_theta0) {
+                g_theta0[kk] = s0;
+            }
+        }
+    if (g_wall) for (k = 0; k < 4; k++) g_wall[k] = gw[k];
+    if (g_ste) *g_ste = gste;
+done:
+    free(f); free(fn); free(tape_th); free(tape_root); free(fb); free(fbn); free(Ob); free(thb);
+    return L;
+}
