@@ -1,0 +1,408 @@
+"""Benchmark of the IREBM time step on GB300 (one JSON line on stdout).
+
+Headline: D2Q9 MLUPS of the fused step in the FP32 form (FP32 populations,
+FP64 Newton) on the 4096 x 4096 melting workload, timed with CUDA events on
+the launching stream over --steps steps after --warmup untimed steps.  The
+timed window sits at the middle of the 10,000-step job (the state is first
+advanced, untimed, to step 5,000 - (warmup + steps)/2) so the Newton front band
+has its average width.  The state (1.2 GB) is larger than L2 (129 MB), so
+every step reads and writes HBM; no flush is needed.
+
+Also reported: the FP64 form on the same workload, the 2048^2 FP64 corner
+workload for Ste in {0.01, 0.1, 1}, 256 batched problems in one persistent
+graph-captured launch per step, the adjoint/forward time ratio on 1024^2 with
+sqrt(T) checkpointing, and the 512-node D1Q3 workload (fused steps).
+
+--impl reference times the FP64 CPU oracle (the reference of this build) on
+a bounded sample of the same workload.
+Multi-GPU (torchrun): each rank runs an independent replica (the problems
+do not exchange data); value = all nodes updated / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "D2Q9 MLUPS incl. local Newton (FP32 vs FP64 form) and adjoint/forward time ratio"
+BYTES_FP32 = 9 * 4 * 2   # algorithmic bytes per node update: each population read once, written once
+BYTES_FP64 = 9 * 8 * 2
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, n in enumerate(names):
+                if f[5 + k].lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ GPU measurements
+def time_steps(torch, S, steps, stream):
+    """Device time of `steps` steps (ms), CUDA events on the launching stream."""
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    S.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def melt_window(case, steps, warmup):
+    return max(0, case.steps // 2 - (steps + warmup) // 2)
+
+
+def bench_single(torch, solver, case, steps, warmup, stream, barrier=None):
+    S = solver.Stefan.from_case(case, stream=stream)
+    S.set_ic(case.theta0())
+    pre = melt_window(case, steps, warmup)
+    if pre:
+        S.step(pre)
+    S.step(warmup)
+    S.sync()
+    if barrier:
+        barrier()
+    ms = time_steps(torch, S, steps, stream)
+    st = S.stats()
+    S.close()
+    return ms, st
+
+
+def bench_e2e(torch, solver, case, steps, stream):
+    """Through the public C ABI with host buffers: set_ic (pinned host -> device),
+    `steps` steps, get_fields (device -> pinned host), all inside the timed region."""
+    n = case.nx * case.ny
+    th0 = torch.empty((case.ny, case.nx), dtype=torch.float64, pin_memory=True)
+    th0.copy_(torch.from_numpy(case.theta0()))
+    out = torch.empty((case.ny, case.nx), dtype=torch.float64, pin_memory=True)
+    S = solver.Stefan.from_case(case, stream=stream)
+    S.set_ic(th0.numpy())
+    S.step(3)
+    S.sync()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    S.set_ic(th0.numpy())
+    S.step(steps)
+    import ctypes
+    from paper_2505_13097_gb300 import _abi
+    _abi.check(S.lib.lbm_stefan_get_fields(S.h, ctypes.c_void_p(out.data_ptr()), None, None, 0))
+    t1 = time.perf_counter()
+    S.close()
+    return (t1 - t0) * 1e3, 8 * n, 8 * n
+
+
+def bench_batch(torch, solver, workloads, steps, warmup, stream):
+    cases = workloads.batch_2d()
+    B = solver.StefanBatch(cases, stream=stream)
+    for k, c in enumerate(cases):
+        B.set_ic(k, c.theta0())
+    tile_h = B.autotune(trial_steps=5)
+    pre = max(0, cases[0].steps // 2 - steps // 2 - warmup)
+    B.step(pre + warmup)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    B.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    nodes = sum(c.nx * c.ny for c in cases)
+    err = max(B.stats(k)["error"] for k in range(len(cases)))
+    B.close()
+    return {"problems": len(cases), "nodes": nodes, "steps": steps, "mlups": nodes * steps / ms / 1e3,
+            "tile_h": tile_h, "error": err, "window_start_step": pre + warmup}
+
+
+def bench_adjoint(torch, solver, workloads, stream):
+    """1024^2, 2,000 steps, FP32 forward with FP64 Newton, sqrt(T) checkpoints."""
+    from paper_2505_13097_gb300.autograd import misfit
+    import numpy as np
+    base = workloads.adjoint_2d()
+    tcase = workloads.adjoint_target_case(base)
+    T = base.steps
+    with torch.cuda.stream(stream):
+        St = solver.Stefan.from_case(tcase, stream=stream)
+        St.set_ic(workloads.adjoint_target_theta0(base))
+        St.step(T)
+        _, ph, _ = St.fields(device=True)
+        St.close()
+        th0 = torch.tensor(base.theta0(), device="cuda", requires_grad=True)
+        tw = torch.tensor([base.walls["W"][1], 0.0, 0.0, 0.0], dtype=torch.float64, device="cuda",
+                          requires_grad=True)
+        ste = torch.tensor(base.ste, dtype=torch.float64, device="cuda", requires_grad=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        L = misfit(th0, tw, ste, base, T, ph)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        L.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+    # kernel-only: one forward step vs one adjoint step
+    S = solver.Stefan.from_case(base, stream=stream)
+    S.set_ic(base.theta0())
+    S.step(T // 2)
+    traj = S.new_theta_planes(2)
+    S.theta_plane(traj[0])
+    a = S.new_state_buffer()
+    b = S.new_state_buffer()
+    S.step_record(1, traj[1:])
+    S.adjoint_seed(traj[1], ph, a, want_loss=False)
+    reps = 50
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e[0].record(stream)
+    S.step(reps)
+    e[1].record(stream)
+    for _ in range(reps):
+        S.adjoint_step(traj[0], traj[1], a, b)
+        a, b = b, a
+    e[2].record(stream)
+    e[2].synchronize()
+    f_ms, a_ms = e[0].elapsed_time(e[1]) / reps, e[1].elapsed_time(e[2]) / reps
+    S.close()
+    fwd, bwd = (t1 - t0) * 1e3, (t2 - t1) * 1e3
+    return {"grid": "%dx%d" % (base.nx, base.ny), "steps": T, "forward_ms": fwd, "backward_ms": bwd,
+            "backward_over_forward": bwd / fwd, "kernel_forward_ms": f_ms, "kernel_adjoint_ms": a_ms,
+            "kernel_adjoint_over_forward": a_ms / f_ms, "loss": float(L.detach()),
+            "checkpoints": int(math.ceil(T / math.ceil(math.sqrt(T))))}
+
+
+def bench_d1q3(torch, solver, workloads, stream):
+    c = workloads.melt_1d()
+    S = solver.Stefan.from_case(c, stream=stream)
+    S.set_ic(c.theta0())
+    S.step(100)
+    S.set_ic(c.theta0())
+    S.sync()
+    ms = time_steps(torch, S, c.steps, stream)
+    S.close()
+    return {"nodes": c.nx, "steps": c.steps, "ms": ms, "steps_per_s": c.steps / ms * 1e3,
+            "mlups": c.nx * c.steps / ms / 1e3}
+
+
+def cpu_baseline_sample(workloads, budget_s=12.0):
+    """The FP64 oracle (single thread, as it stands) on a 4096 x 64 problem with
+    the melting workload's parameters and the first 64 rows of its initial field."""
+    import oracle
+    c = workloads.melt_2d()
+    rows = 64
+    th0 = c.theta0()[:rows]
+    P = oracle.Problem(2, c.nx, rows, tau=c.tau, delta=c.delta, ste=c.ste, walls=c.walls)
+    f = P.init(th0)
+    t = time.perf_counter()
+    f = P.step(f)
+    one = time.perf_counter() - t
+    n = max(2, min(400, int(budget_s / max(one, 1e-6))))
+    t = time.perf_counter()
+    for _ in range(n):
+        f = P.step(f)
+    el = time.perf_counter() - t
+    return {"value": c.nx * rows * n / el / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": "FP64 C oracle, 1 thread, %d steps of a %dx%d problem with the 4096^2 melting "
+                      "workload's parameters (first %d rows of its initial field), %.1f s" % (n, c.nx, rows, rows, el)}
+
+
+# ------------------------------------------------------------------ arms
+def run_reference(args):
+    from paper_2505_13097_gb300 import workloads
+    import oracle
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    c = workloads.melt_2d()
+    rows = 64
+    P = oracle.Problem(2, c.nx, rows, tau=c.tau, delta=c.delta, ste=c.ste, walls=c.walls)
+    f = P.init(c.theta0()[:rows])
+    for _ in range(args.warmup):
+        f = P.step(f)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        f = P.step(f)
+    el = time.perf_counter() - t
+    v = c.nx * rows * args.steps / el / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "melt_2d_d2q9_4096 sample: 4096x64 rows, Ste 0.1, delta 0.01, tau 1.0, FP64 CPU oracle"},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": "%d oracle steps of a 4096x64 problem with the melting workload's parameters" % args.steps},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    from paper_2505_13097_gb300 import solver, workloads
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    barrier = (lambda: dist.barrier(device_ids=[local])) if dist else None
+    stream = torch.cuda.Stream()
+    peak, peak_kind = load_peaks()
+
+    case = workloads.melt_2d()
+    nodes = case.nx * case.ny
+    with ClockSampler(local) as clk:
+        ms, st = bench_single(torch, solver, case, args.steps, args.warmup, stream, barrier)
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    else:
+        ms_max = ms
+    value = world * nodes * args.steps / ms_max / 1e3
+    per_step_ms = ms / args.steps
+    achieved = BYTES_FP32 * nodes / (per_step_ms * 1e-3) / 1e9
+
+    extra = {}
+    if rank == 0 and not args.quick:
+        # FP64 form, same workload and window
+        c64 = case.scaled(precision=workloads.FP64)
+        ms64, _ = bench_single(torch, solver, c64, args.steps, args.warmup, stream)
+        extra["fp64_form"] = {"workload": c64.name, "mlups": nodes * args.steps / ms64 / 1e3,
+                              "gbs": BYTES_FP64 * nodes / (ms64 / args.steps * 1e-3) / 1e9,
+                              "fp32_over_fp64": ms64 / ms}
+        corner = {}
+        for ste in workloads.CORNER_STE:
+            cc = workloads.corner_2d(ste=ste)
+            k = max(20, args.steps // 2)
+            msc, stc = bench_single(torch, solver, cc, k, args.warmup, stream)
+            corner["ste%g" % ste] = {"mlups": cc.nx * cc.ny * k / msc / 1e3,
+                                     "newton_nodes": stc["newton_nodes"], "newton_max_iter": stc["newton_max_iter"]}
+        extra["corner_2d_fp64_2048"] = corner
+        extra["batched_256"] = bench_batch(torch, solver, workloads, max(20, args.steps // 2), args.warmup, stream)
+        extra["adjoint_1024"] = bench_adjoint(torch, solver, workloads, stream)
+        extra["d1q3_512"] = bench_d1q3(torch, solver, workloads, stream)
+    e2e_ms, h2d, d2h = bench_e2e(torch, solver, case, args.steps, stream) if rank == 0 else (0, 0, 0)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "dtype_detail": "FP32 populations and relaxation, float-float moments, FP64 Newton and energy sums",
+            "data": "synthetic",
+            "config": {"workload": "%s: D2Q9 4096x4096, FP32 populations with FP64 Newton, west wall +1, other "
+                                   "walls adiabatic, Ste 0.1, delta 0.01, tau 1.0, theta0 -0.2 + U(+-1e-3) seed 0; "
+                                   "timed window centred on step 5,000 of the 10,000-step job" % case.name,
+                       "l2": "state 1.2 GB > 129 MB L2 (no flush needed)", "parallelism": "replicas" if world > 1 else "1 GPU"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "bytes_per_node": BYTES_FP32, "kernel": "d2q9_step_kernel<float>",
+                         "peak_source": peak_kind},
+            "cpu_baseline": cpu_baseline_sample(workloads) if (world == 1 and not args.no_cpu) else None,
+            "e2e": {"value": nodes * args.steps / e2e_ms / 1e3, "unit": "MLUPS",
+                    "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                    "what": "lbm_stefan_set_ic from pinned host theta0, %d steps from the initial state, "
+                            "lbm_stefan_get_fields to pinned host theta" % args.steps},
+            "gpu_launches": args.steps,
+            "clocks": clk.summary(),
+            "energy_imbalance_last_step": st["imbalance"],
+            "newton_nodes_last_step": st["newton_nodes"],
+        }
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier(device_ids=[local])
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--quick", action="store_true", help="headline only")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

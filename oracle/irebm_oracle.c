@@ -26,9 +26,10 @@
  *  - weights: D1Q3 (2/3, 1/6, 1/6), D2Q9 (4/9, 1/9 x4, 1/36 x4), c_s^2 = 1/3.
  *  - Newton stopping: |x_{k+1}-x_k| <= tol*max(1,|x_k|) (x_{k+1} kept), or
  *    F(x_k) = 0, or a bracket narrower than that; at most maxit iterations.
- *  - Newton safeguard: the root lies in [rhs-1/Ste, rhs] (0 <= phi <= 1 and
- *    F increasing); an iterate that leaves the current bracket is replaced by
- *    the bracket midpoint.
+ *  - Newton safeguard: the root lies in [m0 + (phi(theta)-1)/Ste, m0 + phi(theta)/Ste]
+ *    (0 <= phi <= 1 and F increasing); an iterate that leaves the current
+ *    bracket, or does not at least halve the update before last, is replaced
+ *    by the bracket midpoint.
  *  - Dirichlet on D2Q9: the unknown q_i share R = m0_target - sum(known q)
  *    in proportion to w_i.  m0_target follows from Eq. (14) with
  *    theta~ = theta_D (see orc_dirichlet_m0 for the sign of the phi term).
@@ -123,6 +124,7 @@ double orc_newton(double m0, double theta, double ste, double delta, double tol,
     double pth = orc_phi(theta, delta);
     double lo = m0 + (pth - 1.0) / ste, hi = m0 + pth / ste;   /* F(lo) <= 0 <= F(hi): 0 <= phi <= 1 */
     double x = theta;
+    double step_old = hi - lo, step = step_old;   /* sizes of the last two updates */
     int k;
     *ok = 0;
     for (k = 0; k < maxit; k++) {
@@ -135,9 +137,16 @@ double orc_newton(double m0, double theta, double ste, double delta, double tol,
         /* Algorithm 3: theta^(k+1) = (m0 + phi(theta)/Ste + phi'(x) x/Ste - phi(x)/Ste) / (1 + phi'(x)/Ste) */
         xn = (m0 + (pth - ph) / ste + dph * x / ste) / (1.0 + dph / ste);
         if (fabs(xn - x) <= tol * fmax(1.0, fabs(x))) { x = xn; *ok = 1; k++; break; }
-        if (!(xn >= lo && xn <= hi)) {             /* safeguard: bisect the bracket */
-            xn = 0.5 * (lo + hi);
-            if (hi - lo <= tol * fmax(1.0, fabs(xn))) { x = xn; *ok = 1; k++; break; }
+        /* safeguard: bisect the bracket when the Newton iterate leaves it or does
+           not at least halve the update before last (this also breaks cycles) */
+        if (!(xn >= lo && xn <= hi) || fabs(xn - x) > 0.5 * step_old) {
+            step_old = step;
+            step = 0.5 * (hi - lo);
+            xn = lo + step;
+            if (step <= tol * fmax(1.0, fabs(xn))) { x = xn; *ok = 1; k++; break; }
+        } else {
+            step_old = step;
+            step = fabs(xn - x);
         }
         x = xn;
     }

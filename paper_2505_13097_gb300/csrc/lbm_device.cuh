@@ -1,0 +1,218 @@
+// Device helpers of the IREBM kernels: lattice constants, float-float sums,
+// the regularized liquid fraction, the local Newton solve of Eq. (14),
+// deterministic fixed-point reductions and the end-of-launch statistics.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// |x| >= kSat * delta  =>  tanh(x/delta) is +-1 in FP64 (1 - tanh(19.5) ~ 2e-17,
+// below half an ulp of 1), so phi is exactly 0 or 1 there and phi' is 0.
+constexpr double kSat = 19.5;
+
+// ---------------------------------------------------------------- D2Q9 / D1Q3
+// D2Q9 velocities (Sec. 3.2): 0 rest; 1..4 = (+1,0),(0,+1),(-1,0),(0,-1);
+// 5..8 = (+1,+1),(-1,+1),(-1,-1),(+1,-1).  Weights 4/9, 1/9, 1/36 (c_s^2 = 1/3).
+__host__ __device__ constexpr int d2_ex(int i) { return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0); }
+__host__ __device__ constexpr int d2_ey(int i) { return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0); }
+__host__ __device__ constexpr int d2_opp(int i) { return i == 0 ? 0 : (i <= 4 ? ((i + 1) & 3) + 1 : ((i - 3) & 3) + 5); }
+__host__ __device__ constexpr double d2_w(int i) { return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0); }
+// D1Q3: 0 rest, 1 = +1, 2 = -1; weights 2/3, 1/6, 1/6.
+__host__ __device__ constexpr int d1_ex(int i) { return i == 1 ? 1 : (i == 2 ? -1 : 0); }
+__host__ __device__ constexpr double d1_w(int i) { return i == 0 ? 2.0 / 3.0 : 1.0 / 6.0; }
+
+// ---------------------------------------------------------------- float-float
+// Unevaluated sum hi + lo of two floats; two_sum is Knuth's error-free
+// transformation (no fast-math: the compiler keeps the order of operations).
+struct ff {
+    float hi, lo;
+};
+__device__ __forceinline__ void ff_add(ff& a, float b)
+{
+    float s = __fadd_rn(a.hi, b);
+    float bb = __fsub_rn(s, a.hi);
+    float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    a.hi = s;
+    a.lo = __fadd_rn(a.lo, e);
+}
+__device__ __forceinline__ double ff_to_double(const ff& a) { return (double)a.hi + (double)a.lo; }
+
+// Approximate float of a double from its high word only (sign, exponent and
+// 20 mantissa bits; relative error < 2^-20), using the integer pipe.  Values
+// below 2^-126 in magnitude give 0; non-finite or huge values give NaN.
+__device__ __forceinline__ float approx_float(double d)
+{
+    int hi = __double2hiint(d);
+    int e = (hi >> 20) & 0x7ff;
+    int bits = (hi & 0x80000000) | (((hi & 0x7fffffff) - (896 << 20)) << 3);
+    float r = __int_as_float(bits);
+    return e <= 896 ? 0.0f : (e >= 1151 ? __int_as_float(0x7fc00000) : r);
+}
+
+// ---------------------------------------------------------------- liquid fraction
+// phi(x) = (1 + tanh(x/delta))/2 (Sec. 4.1) and phi' = (1 - t)(1 + t)/(2 delta).
+__device__ __forceinline__ double phi_of(double x, double inv_delta) { return 0.5 + 0.5 * tanh(x * inv_delta); }
+
+// Local Newton solve of Eq. (14): the root of
+//   F(x) = (x - m0) + (phi(x) - phi(theta))/Ste,   F' = 1 + phi'(x)/Ste >= 1,
+// from x = theta (Algorithm 3).  Safeguard: the root lies in
+// [m0 + (phi(theta) - 1)/Ste, m0 + phi(theta)/Ste]; a Newton iterate that
+// leaves the current bracket, or does not at least halve the update before
+// last, is replaced by the bracket midpoint (this also breaks 2-cycles).
+// Converged when an update moves x by at most tol*max(1,|x|) (tested before
+// the safeguard), when F = 0, or when the bracket is that narrow.
+struct NewtonOut {
+    double root;
+    double phi_root;
+    int iters;
+    bool ok;
+};
+
+__device__ __forceinline__ NewtonOut newton_solve(double m0, double theta, double phi_theta, double inv_ste,
+                                                  double inv_delta, double tol, int maxit)
+{
+    double lo = m0 + (phi_theta - 1.0) * inv_ste, hi = m0 + phi_theta * inv_ste;
+    double x = theta;
+    double step_old = hi - lo, step = step_old;
+    NewtonOut r;
+    for (int k = 0; k < maxit; ++k) {
+        double t = tanh(x * inv_delta);
+        double ph = 0.5 + 0.5 * t;
+        double F = (x - m0) + (ph - phi_theta) * inv_ste;
+        if (F == 0.0) {
+            r.root = x; r.phi_root = ph; r.iters = k; r.ok = true;
+            return r;
+        }
+        if (F < 0.0) lo = fmax(lo, x);
+        else hi = fmin(hi, x);
+        double dph = 0.5 * (1.0 - t) * (1.0 + t) * inv_delta;
+        double xn = x - F / (1.0 + dph * inv_ste);
+        double sc = tol * fmax(1.0, fabs(x));
+        if (fabs(xn - x) <= sc) {
+            // |xn - x| <= ~1e-14: phi(xn) = ph + phi'(x)(xn - x) to far below one ulp
+            r.root = xn; r.phi_root = ph + dph * (xn - x); r.iters = k + 1; r.ok = true;
+            return r;
+        }
+        if (!(xn >= lo && xn <= hi) || fabs(xn - x) > 0.5 * step_old) {
+            step_old = step;
+            step = 0.5 * (hi - lo);
+            xn = lo + step;
+            if (step <= tol * fmax(1.0, fabs(xn))) {
+                r.root = xn; r.phi_root = phi_of(xn, inv_delta); r.iters = k + 1; r.ok = true;
+                return r;
+            }
+        } else {
+            step_old = step;
+            step = fabs(xn - x);
+        }
+        x = xn;
+    }
+    r.root = x; r.phi_root = phi_of(x, inv_delta); r.iters = maxit; r.ok = false;
+    return r;
+}
+
+// ---------------------------------------------------------------- reductions
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+__device__ __forceinline__ int warp_sum_i(int v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+__device__ __forceinline__ int warp_max_i(int v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
+// Add v into the 128-bit fixed-point accumulator (value scaled by 2^60).
+__device__ __forceinline__ void acc_add(Acc128* a, double v)
+{
+    if (v == 0.0) return;
+    double s = v * 0.0625;          // v * 2^60 / 2^64
+    double h = floor(s);
+    double r = s - h;               // in [0, 1), exact
+    long long hi = (long long)h;
+    unsigned long long lo = __double2ull_rz(r * 18446744073709551616.0);
+    unsigned long long old = atomicAdd(&a->lo, lo);
+    long long carry = (old + lo < old) ? 1 : 0;
+    atomicAdd(reinterpret_cast<unsigned long long*>(&a->hi), (unsigned long long)(hi + carry));
+}
+
+__device__ __forceinline__ double acc_read(const Acc128* a)
+{
+    volatile const Acc128* va = a;
+    unsigned long long lo = va->lo;
+    long long hi = va->hi;
+    return (double)hi * 16.0 + (double)lo * 0x1p-60;
+}
+
+__device__ __forceinline__ void acc_clear(Acc128* a)
+{
+    volatile Acc128* va = a;
+    va->lo = 0ull;
+    va->hi = 0ll;
+}
+
+// Publish one problem's step statistics (called by the last block only).
+__device__ __forceinline__ void publish_stats(DevStats* st)
+{
+    double e = acc_read(&st->cur_energy);
+    double f = acc_read(&st->cur_flux);
+    volatile DevStats* v = st;
+    if (v->have_energy) {
+        double imb = e - v->energy - f;
+        v->imbalance = imb;
+        if (fabs(imb) > v->imbalance_max) v->imbalance_max = fabs(imb);
+    } else {
+        v->imbalance = 0.0;
+    }
+    v->energy_prev = v->energy;
+    v->energy = e;
+    v->flux = f;
+    v->have_energy = 1;
+    v->steps = v->steps + 1;
+    v->newton_nodes = (long long)v->cur_newton;
+    v->newton_max_iter = v->cur_maxit;
+    acc_clear(&st->cur_energy);
+    acc_clear(&st->cur_flux);
+    v->cur_newton = 0ull;
+    v->cur_maxit = 0;
+}
+
+// Last-block pattern: every block calls this after its warps have added their
+// partial sums; the block that arrives last publishes the statistics of all
+// problems (one thread per problem) and resets the ticket.  No block waits.
+__device__ __forceinline__ void finish_launch(DevStats* stats, int nprob, unsigned int* ticket)
+{
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned t = atomicAdd(ticket, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        for (int p = threadIdx.x; p < nprob; p += blockDim.x) publish_stats(&stats[p]);
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) *ticket = 0u;
+    }
+}
+
+}  // namespace lbm

@@ -1,0 +1,111 @@
+// Internal declarations shared by the host code and the kernels of the IREBM
+// library.  Nothing here is part of the C ABI (see include/lbm_stefan.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+// Fixed-point accumulator for deterministic FP64 sums across thread blocks:
+// the value is (hi * 2^64 + lo) * 2^-60 as a two's-complement 128-bit integer.
+// Integer addition is associative, so the result does not depend on the
+// order in which tiles add their partial sums.
+struct Acc128 {
+    unsigned long long lo;
+    long long hi;
+};
+
+// Per-problem device statistics.  The "cur_" fields accumulate during one
+// step launch; the last block of the launch publishes them and clears them.
+struct DevStats {
+    Acc128 cur_energy;             // sum_x theta' + phi(theta')/Ste of this step
+    Acc128 cur_flux;               // boundary flux of this step
+    unsigned long long cur_newton; // nodes that ran the Newton iteration
+    int cur_maxit;                 // largest Newton iteration count
+    int error;                     // sticky: lbm_status of a device-detected failure
+    double energy, energy_prev, flux, imbalance, imbalance_max;
+    long long steps;
+    long long newton_nodes;
+    int newton_max_iter;
+    int have_energy;               // energy holds E(t) of the current state
+    // adjoint accumulators: dL/dtheta_wall[4], dL/dSte, loss
+    Acc128 g_wall[4];
+    Acc128 g_ste;
+    Acc128 loss;
+};
+
+// Device view of one problem.  Populations are stored as q planes (SoA);
+// plane i starts at base + i * plane; each plane has ny + 2 rows of `pitch`
+// elements, the first and last being zero halo rows, so row y (-1 .. ny)
+// starts at (y + 1) * pitch.  pitch is a multiple of the warp segment width.
+struct Problem {
+    void* state[2];          // ping-pong population buffers
+    int nx, ny, pitch;
+    int q;                   // 3 (D1Q3) or 9 (D2Q9)
+    long long plane;         // elements per plane
+    double omega;            // 1/tau
+    double ste, inv_ste, delta, inv_delta;
+    double tol;
+    int maxit;
+    int bb_mode;
+    int wall_kind[4];        // W, E, S, N
+    double wall_theta[4];
+    int nseg, nstrip, tile_h;
+    int tile0;               // first global tile index of this problem
+    int ntiles;
+    int stats;               // index into the DevStats array
+};
+
+// Per-launch arguments of the forward step kernels.
+struct StepArgs {
+    const Problem* probs;    // device array
+    int nprob;
+    const int2* schedule;    // device: (problem, local tile) per schedule slot; NULL = single problem
+    int nslots;              // schedule length (total tiles)
+    int parity;              // read state[parity], write state[parity ^ 1]
+    double* rec;             // optional theta' record plane (single problem only), ny x pitch doubles
+    DevStats* stats;
+    unsigned int* ticket;    // last-block counter, zero between launches
+};
+
+// Per-launch arguments of the adjoint kernels (single problem).
+struct AdjArgs {
+    const Problem* prob;     // device pointer
+    const double* theta_t;   // recorded theta(t), ny x pitch
+    const double* theta_t1;  // recorded theta(t+1), ny x pitch
+    const void* adj_in;      // lambda(t+1), state layout
+    void* adj_out;           // lambda(t), state layout
+    double* wall_buf;        // per wall node records (see adjoint.cu)
+    DevStats* stats;
+    unsigned int* ticket;
+};
+
+constexpr int kWarpsPerBlock = 4;
+constexpr int kWallRec = 19;   // doubles per wall-node record of the adjoint
+
+// D2Q9 launchers (step_d2q9.cu)
+cudaError_t launch_d2q9_step(int precision, const StepArgs& a, int grid, cudaStream_t s);
+int d2q9_segment_width(int precision);   // nodes per warp segment
+
+// D1Q3 launchers (step_d1q3.cu)
+cudaError_t launch_d1q3_step(int precision, const StepArgs& a, const Problem& hp, cudaStream_t s);
+cudaError_t launch_d1q3_fused(int precision, const StepArgs& a, const Problem& hp, int nsteps, int start_parity,
+                              double* rec, cudaStream_t s);
+bool d1q3_fused_fits(int precision, int nx);
+
+// Field and state kernels (fields.cu)
+cudaError_t launch_init_state(int precision, const Problem* dprob, const Problem& hp, const double* theta0,
+                              int parity, DevStats* st, cudaStream_t s);
+cudaError_t launch_fields(int precision, const Problem* dprob, const Problem& hp, int parity, double* theta,
+                          double* phi, double* H, double* theta_plane, cudaStream_t s);
+cudaError_t launch_finalize_init(DevStats* st, cudaStream_t s);
+
+// Adjoint kernels (adjoint.cu)
+cudaError_t launch_adj_seed(int precision, const Problem* dprob, const Problem& hp, const double* theta_T,
+                            const double* phi_target, void* adj, DevStats* st, cudaStream_t s);
+cudaError_t launch_adj_step(int precision, const AdjArgs& a, const Problem& hp, cudaStream_t s);
+cudaError_t launch_adj_finish(int precision, const Problem* dprob, const Problem& hp, const void* adj0,
+                              double* g_theta0, DevStats* st, cudaStream_t s);
+
+}  // namespace lbm

@@ -1,0 +1,792 @@
+// Host side of the C ABI declared in include/lbm_stefan.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/lbm_stefan.h"
+#include "lbm_internal.h"
+
+using lbm::DevStats;
+using lbm::Problem;
+using lbm::StepArgs;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+lbm_status fail(lbm_status s, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+#define CUDA_TRY(call)                                                                              \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess) return fail(LBM_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+// Steps per captured CUDA graph (an even number, so a graph starts and ends on parity 0).
+constexpr int kGraphSteps = 32;
+
+struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    int steps = 0;
+    void reset()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        steps = 0;
+    }
+};
+
+}  // namespace
+
+struct lbm_stefan {
+    lbm_stefan_params p;
+    Problem hp;
+    Problem* dprob = nullptr;
+    int precision = 0;
+    size_t elem = 8;
+    size_t state_bytes = 0;
+    cudaStream_t stream = nullptr;
+    DevStats* dstats = nullptr;
+    unsigned int* dticket = nullptr;
+    double* dscratch = nullptr;   // 3 * nx * ny doubles (host field transfers)
+    int parity = 0;
+    bool ic = false;
+    GraphCache graph;
+};
+
+struct lbm_stefan_batch {
+    int count = 0;
+    int precision = 1;
+    size_t elem = 4;
+    std::vector<Problem> hp;
+    std::vector<size_t> state_bytes;
+    Problem* dprobs = nullptr;
+    void* arena = nullptr;
+    size_t arena_bytes = 0;
+    DevStats* dstats = nullptr;
+    unsigned int* dticket = nullptr;
+    int2* dsched = nullptr;
+    int nslots = 0;
+    int tile_h = 16;
+    int schedule = 1;
+    int grid = 0;
+    int parity = 0;
+    cudaStream_t stream = nullptr;
+    double* dscratch = nullptr;
+    size_t scratch_elems = 0;
+    GraphCache graph;
+};
+
+// ------------------------------------------------------------------ helpers
+
+static lbm_status validate_common(int nx, int ny, double tau, double delta, double ste, double tol, int maxit)
+{
+    if (!(tau > 0.5) || !std::isfinite(tau)) return fail(LBM_ERR_ARG, "tau must be > 1/2 (got %g)", tau);
+    if (!(delta > 0.0) || !std::isfinite(delta)) return fail(LBM_ERR_ARG, "delta must be > 0 (got %g)", delta);
+    if (!(ste > 0.0) || !std::isfinite(ste)) return fail(LBM_ERR_ARG, "Ste must be > 0 (got %g)", ste);
+    if (!(tol > 0.0) || maxit < 1) return fail(LBM_ERR_ARG, "newton_tol must be > 0 and newton_max_iter >= 1");
+    if (nx < 2 || ny < 1) return fail(LBM_ERR_ARG, "nx must be >= 2 (got %d, %d)", nx, ny);
+    return LBM_OK;
+}
+
+static void fill_problem(Problem& pb, int q, int nx, int ny, int pitch, double tau, double delta, double ste,
+                         double tol, int maxit, int bb_mode, int tile_h, int segw)
+{
+    std::memset(&pb, 0, sizeof pb);
+    pb.nx = nx;
+    pb.ny = ny;
+    pb.q = q;
+    pb.pitch = pitch;
+    pb.plane = (long long)(ny + 2) * pitch;
+    pb.omega = 1.0 / tau;
+    pb.ste = ste;
+    pb.inv_ste = 1.0 / ste;
+    pb.delta = delta;
+    pb.inv_delta = 1.0 / delta;
+    pb.tol = tol;
+    pb.maxit = maxit;
+    pb.bb_mode = bb_mode;
+    pb.tile_h = tile_h;
+    pb.nseg = pitch / segw;
+    pb.nstrip = (ny + tile_h - 1) / tile_h;
+    pb.ntiles = pb.nseg * pb.nstrip;
+}
+
+static lbm_status upload_problem(lbm_stefan* h)
+{
+    CUDA_TRY(cudaMemcpyAsync(h->dprob, &h->hp, sizeof(Problem), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+static StepArgs single_args(lbm_stefan* h, int parity, double* rec)
+{
+    StepArgs a;
+    a.probs = h->dprob;
+    a.nprob = 1;
+    a.schedule = nullptr;
+    a.nslots = h->hp.ntiles;
+    a.parity = parity;
+    a.rec = rec;
+    a.stats = h->dstats;
+    a.ticket = h->dticket;
+    return a;
+}
+
+static cudaError_t launch_one(lbm_stefan* h, int parity, double* rec)
+{
+    StepArgs a = single_args(h, parity, rec);
+    if (h->p.lattice == LBM_D2Q9) {
+        const int grid = (h->hp.ntiles + lbm::kWarpsPerBlock - 1) / lbm::kWarpsPerBlock;
+        return lbm::launch_d2q9_step(h->precision, a, grid, h->stream);
+    }
+    return lbm::launch_d1q3_step(h->precision, a, h->hp, h->stream);
+}
+
+static lbm_status check_stats_error(lbm_stefan* h, DevStats* out)
+{
+    DevStats st;
+    CUDA_TRY(cudaMemcpyAsync(&st, h->dstats, sizeof st, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (out) *out = st;
+    if (st.error) return fail((lbm_status)st.error, "device reported error %d (Newton limit or non-finite value)", st.error);
+    return LBM_OK;
+}
+
+static double acc_host(const lbm::Acc128& a) { return (double)a.hi * 16.0 + (double)a.lo * 0x1p-60; }
+
+// ------------------------------------------------------------------ one problem
+
+extern "C" lbm_status lbm_stefan_create(const lbm_stefan_params* p, void* cuda_stream, lbm_stefan** out)
+{
+    if (!p || !out) return fail(LBM_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    if (p->lattice != LBM_D1Q3 && p->lattice != LBM_D2Q9) return fail(LBM_ERR_ARG, "lattice must be D1Q3 or D2Q9");
+    if (p->precision != LBM_FP64 && p->precision != LBM_FP32) return fail(LBM_ERR_ARG, "precision must be FP64 or FP32");
+    if (p->bb_mode != LBM_BB_MIRROR && p->bb_mode != LBM_BB_LINK) return fail(LBM_ERR_ARG, "bb_mode must be 0 or 1");
+    lbm_status s = validate_common(p->nx, p->ny, p->tau, p->delta, p->ste, p->newton_tol, p->newton_max_iter);
+    if (s != LBM_OK) return s;
+    if (p->lattice == LBM_D1Q3 && p->ny != 1) return fail(LBM_ERR_ARG, "D1Q3 needs ny = 1");
+    if (p->lattice == LBM_D2Q9 && p->ny < 2) return fail(LBM_ERR_ARG, "D2Q9 needs ny >= 2");
+    if ((long long)p->nx * p->ny > (1ll << 31)) return fail(LBM_ERR_ARG, "more than 2^31 nodes");
+
+    lbm_stefan* h = new lbm_stefan();
+    h->p = *p;
+    h->precision = p->precision;
+    h->elem = p->precision == LBM_FP32 ? 4 : 8;
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    const int q = p->lattice == LBM_D2Q9 ? 9 : 3;
+    const int segw = p->lattice == LBM_D2Q9 ? lbm::d2q9_segment_width(p->precision) : 32;
+    const int pitch = round_up(p->nx, segw);
+    fill_problem(h->hp, q, p->nx, p->ny, pitch, p->tau, p->delta, p->ste, p->newton_tol, p->newton_max_iter,
+                 p->bb_mode, 16, segw);
+    h->state_bytes = (size_t)q * h->hp.plane * h->elem;
+    cudaError_t e = cudaSuccess;
+    void* bufs[2] = {nullptr, nullptr};
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaMalloc(&bufs[k], h->state_bytes);
+        if (e == cudaSuccess) e = cudaMemset(bufs[k], 0, h->state_bytes);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&h->dprob, sizeof(Problem));
+    if (e == cudaSuccess) e = cudaMalloc(&h->dstats, sizeof(DevStats));
+    if (e == cudaSuccess) e = cudaMemset(h->dstats, 0, sizeof(DevStats));
+    if (e == cudaSuccess) e = cudaMalloc(&h->dticket, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(h->dticket, 0, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMalloc(&h->dscratch, sizeof(double) * 3 * (size_t)p->nx * p->ny);
+    h->hp.state[0] = bufs[0];
+    h->hp.state[1] = bufs[1];
+    h->hp.stats = 0;
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        lbm_stefan_destroy(h);
+        return fail(LBM_ERR_CUDA, "allocation failed: %s", cudaGetErrorString(e));
+    }
+    s = upload_problem(h);
+    if (s != LBM_OK) {
+        lbm_stefan_destroy(h);
+        return s;
+    }
+    *out = h;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_stefan_set_bc(lbm_stefan* h, int wall, int kind, double theta_wall)
+{
+    if (!h) return fail(LBM_ERR_ARG, "NULL handle");
+    if (wall < 0 || wall > 3) return fail(LBM_ERR_ARG, "wall must be 0..3");
+    if (h->p.lattice == LBM_D1Q3 && wall > 1) return fail(LBM_ERR_ARG, "D1Q3 has only the W and E walls");
+    if (kind != LBM_ADIABATIC && kind != LBM_DIRICHLET) return fail(LBM_ERR_ARG, "kind must be 0 or 1");
+    if (!std::isfinite(theta_wall)) return fail(LBM_ERR_ARG, "theta_wall must be finite");
+    h->hp.wall_kind[wall] = kind;
+    h->hp.wall_theta[wall] = theta_wall;
+    h->graph.reset();
+    return upload_problem(h);
+}
+
+extern "C" lbm_status lbm_stefan_set_ic(lbm_stefan* h, const double* theta0, int on_device)
+{
+    if (!h || !theta0) return fail(LBM_ERR_ARG, "NULL argument");
+    const size_t n = (size_t)h->hp.nx * h->hp.ny;
+    const double* src = theta0;
+    if (!on_device) {
+        CUDA_TRY(cudaMemcpyAsync(h->dscratch, theta0, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        src = h->dscratch;
+    }
+    CUDA_TRY(cudaMemsetAsync(h->dstats, 0, sizeof(DevStats), h->stream));
+    CUDA_TRY(lbm::launch_init_state(h->precision, h->dprob, h->hp, src, 0, h->dstats, h->stream));
+    CUDA_TRY(lbm::launch_finalize_init(h->dstats, h->stream));
+    if (!on_device) CUDA_TRY(cudaStreamSynchronize(h->stream));
+    h->parity = 0;
+    h->ic = true;
+    return LBM_OK;
+}
+
+static lbm_status capture_graph(lbm_stefan* h)
+{
+    h->graph.reset();
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < kGraphSteps && e == cudaSuccess; ++k) e = launch_one(h, k & 1, nullptr);
+    cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(LBM_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(&h->graph.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+    h->graph.steps = kGraphSteps;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_stefan_step(lbm_stefan* h, int nsteps)
+{
+    if (!h) return fail(LBM_ERR_ARG, "NULL handle");
+    if (nsteps < 0) return fail(LBM_ERR_ARG, "nsteps must be >= 0");
+    if (!h->ic) return fail(LBM_ERR_STATE, "set_ic must come before step");
+    if (nsteps == 0) return LBM_OK;
+    if (h->p.lattice == LBM_D1Q3 && lbm::d1q3_fused_fits(h->precision, h->hp.nx)) {
+        StepArgs a = single_args(h, h->parity, nullptr);
+        CUDA_TRY(lbm::launch_d1q3_fused(h->precision, a, h->hp, nsteps, h->parity, nullptr, h->stream));
+        h->parity ^= nsteps & 1;
+        return LBM_OK;
+    }
+    int left = nsteps;
+    if (h->parity == 1) {
+        CUDA_TRY(launch_one(h, 1, nullptr));
+        h->parity = 0;
+        --left;
+    }
+    // graphs only on a non-default stream (capture is not allowed on the legacy stream)
+    if (h->stream != nullptr && left >= kGraphSteps) {
+        if (!h->graph.exec) {
+            lbm_status s = capture_graph(h);
+            if (s != LBM_OK) return s;
+        }
+        while (left >= kGraphSteps) {
+            CUDA_TRY(cudaGraphLaunch(h->graph.exec, h->stream));
+            left -= kGraphSteps;
+        }
+    }
+    while (left > 0) {
+        CUDA_TRY(launch_one(h, h->parity, nullptr));
+        h->parity ^= 1;
+        --left;
+    }
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_stefan_step_record(lbm_stefan* h, int nsteps, double* traj)
+{
+    if (!h || (!traj && nsteps > 0)) return fail(LBM_ERR_ARG, "NULL argument");
+    if (nsteps < 0) return fail(LBM_ERR_ARG, "nsteps must be >= 0");
+    if (!h->ic) return fail(LBM_ERR_STATE, "set_ic must come before step_record");
+    const long long plane = (long long)h->hp.ny * h->hp.pitch;
+    if (h->p.lattice == LBM_D1Q3 && lbm::d1q3_fused_fits(h->precision, h->hp.nx)) {
+        StepArgs a = single_args(h, h->parity, nullptr);
+        CUDA_TRY(lbm::launch_d1q3_fused(h->precision, a, h->hp, nsteps, h->parity, traj, h->stream));
+        h->parity ^= nsteps & 1;
+        return LBM_OK;
+    }
+    for (int k = 0; k < nsteps; ++k) {
+        CUDA_TRY(launch_one(h, h->parity, traj + k * plane));
+        h->parity ^= 1;
+    }
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_stefan_sync(lbm_stefan* h)
+{
+    if (!h) return fail(LBM_ERR_ARG, "NULL handle");
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return check_stats_error(h, nullptr);
+}
+
+extern "C" lbm_status lbm_stefan_get_fields(lbm_stefan* h, double* theta, double* phi, double* H, int on_device)
+{
+    if (!h) return fail(LBM_ERR_ARG, "NULL handle");
+    if (!h->ic) return fail(LBM_ERR_STATE, "set_ic must come before get_fields");
+    const size_t n = (size_t)h->hp.nx * h->hp.ny;
+    if (on_device) {
+        CUDA_TRY(lbm::launch_fields(h->precision, h->dprob, h->hp, h->parity, theta, phi, H, nullptr, h->stream));
+    } else {
+        double* d[3] = {theta ? h->dscratch : nullptr, phi ? h->dscratch + n : nullptr, H ? h->dscratch + 2 * n : nullptr};
+        CUDA_TRY(lbm::launch_fields(h->precision, h->dprob, h->hp, h->parity, d[0], d[1], d[2], nullptr, h->stream));
+        double* hst[3] = {theta, phi, H};
+        for (int k = 0; k < 3; ++k)
+            if (hst[k]) CUDA_TRY(cudaMemcpyAsync(hst[k], d[k], n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    }
+    return check_stats_error(h, nullptr);
+}
+
+extern "C" lbm_status lbm_stefan_get_stats(lbm_stefan* h, lbm_stefan_stats* out)
+{
+    if (!h || !out) return fail(LBM_ERR_ARG, "NULL argument");
+    DevStats st;
+    lbm_status s = check_stats_error(h, &st);
+    out->energy = st.energy;
+    out->energy_prev = st.energy_prev;
+    out->flux = st.flux;
+    out->imbalance = st.imbalance;
+    out->imbalance_max = st.imbalance_max;
+    out->steps = st.steps;
+    out->newton_nodes = st.newton_nodes;
+    out->newton_max_iter = st.newton_max_iter;
+    out->error = st.error;
+    return s;
+}
+
+extern "C" lbm_status lbm_stefan_layout(lbm_stefan* h, size_t* state_bytes, int* row_stride)
+{
+    if (!h) return fail(LBM_ERR_ARG, "NULL handle");
+    if (state_bytes) *state_bytes = h->state_bytes;
+    if (row_stride) *row_stride = h->hp.pitch;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_stefan_get_state(lbm_stefan* h, void* buf, int on_device)
+{
+    if (!h || !buf) return fail(LBM_ERR_ARG, "NULL argument");
+    if (!h->ic) return fail(LBM_ERR_STATE, "no state yet");
+    CUDA_TRY(cudaMemcpyAsync(buf, h->hp.state[h->parity], h->state_bytes,
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+    if (!on_device) CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_stefan_set_state(lbm_stefan* h, const void* buf, int on_device)
+{
+    if (!h || !buf) return fail(LBM_ERR_ARG, "NULL argument");
+    CUDA_TRY(cudaMemcpyAsync(h->hp.state[0], buf, h->state_bytes,
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+    // the energy of a loaded state is not known until the next step publishes one
+    CUDA_TRY(cudaMemsetAsync(&h->dstats->have_energy, 0, sizeof(int), h->stream));
+    if (!on_device) CUDA_TRY(cudaStreamSynchronize(h->stream));
+    h->parity = 0;
+    h->ic = true;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_stefan_theta_plane(lbm_stefan* h, double* plane)
+{
+    if (!h || !plane) return fail(LBM_ERR_ARG, "NULL argument");
+    if (!h->ic) return fail(LBM_ERR_STATE, "no state yet");
+    CUDA_TRY(lbm::launch_fields(h->precision, h->dprob, h->hp, h->parity, nullptr, nullptr, nullptr, plane, h->stream));
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_stefan_adjoint_seed(lbm_stefan* h, const double* theta_T, const double* phi_target,
+                                              void* adj, double* loss)
+{
+    if (!h || !theta_T || !phi_target || !adj) return fail(LBM_ERR_ARG, "NULL argument");
+    CUDA_TRY(cudaMemsetAsync(&h->dstats->g_wall, 0, sizeof(lbm::Acc128) * 6, h->stream));
+    CUDA_TRY(lbm::launch_adj_seed(h->precision, h->dprob, h->hp, theta_T, phi_target, adj, h->dstats, h->stream));
+    if (loss) {
+        DevStats st;
+        lbm_status s = check_stats_error(h, &st);
+        *loss = acc_host(st.loss);
+        return s;
+    }
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_stefan_adjoint_step(lbm_stefan* h, const double* theta_t, const double* theta_t1,
+                                              const void* adj_in, void* adj_out)
+{
+    if (!h || !theta_t || !theta_t1 || !adj_in || !adj_out) return fail(LBM_ERR_ARG, "NULL argument");
+    if (adj_in == adj_out) return fail(LBM_ERR_ARG, "adj_in and adj_out must differ");
+    lbm::AdjArgs a;
+    a.prob = h->dprob;
+    a.theta_t = theta_t;
+    a.theta_t1 = theta_t1;
+    a.adj_in = adj_in;
+    a.adj_out = adj_out;
+    a.wall_buf = nullptr;
+    a.stats = h->dstats;
+    a.ticket = h->dticket;
+    CUDA_TRY(lbm::launch_adj_step(h->precision, a, h->hp, h->stream));
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_stefan_adjoint_finish(lbm_stefan* h, const void* adj0, double* g_theta0, int on_device,
+                                                double* g_wall, double* g_ste)
+{
+    if (!h || !adj0) return fail(LBM_ERR_ARG, "NULL argument");
+    const size_t n = (size_t)h->hp.nx * h->hp.ny;
+    double* dst = (g_theta0 && on_device) ? g_theta0 : h->dscratch;
+    CUDA_TRY(lbm::launch_adj_finish(h->precision, h->dprob, h->hp, adj0, dst, h->dstats, h->stream));
+    if (g_theta0 && !on_device)
+        CUDA_TRY(cudaMemcpyAsync(g_theta0, h->dscratch, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    DevStats st;
+    lbm_status s = check_stats_error(h, &st);
+    if (g_wall)
+        for (int k = 0; k < 4; ++k) g_wall[k] = h->hp.wall_kind[k] == LBM_DIRICHLET ? acc_host(st.g_wall[k]) : 0.0;
+    if (g_ste) *g_ste = acc_host(st.g_ste);
+    return s;
+}
+
+extern "C" void lbm_stefan_destroy(lbm_stefan* h)
+{
+    if (!h) return;
+    h->graph.reset();
+    cudaFree(h->hp.state[0]);
+    cudaFree(h->hp.state[1]);
+    cudaFree(h->dprob);
+    cudaFree(h->dstats);
+    cudaFree(h->dticket);
+    cudaFree(h->dscratch);
+    delete h;
+}
+
+extern "C" const char* lbm_stefan_last_error(void) { return g_err; }
+
+// ------------------------------------------------------------------ batches
+
+static lbm_status batch_build_schedule(lbm_stefan_batch* b, int tile_h, int schedule)
+{
+    const int segw = lbm::d2q9_segment_width(b->precision);
+    int total = 0;
+    for (auto& pb : b->hp) {
+        pb.tile_h = tile_h;
+        pb.nstrip = (pb.ny + tile_h - 1) / tile_h;
+        pb.nseg = pb.pitch / segw;
+        pb.ntiles = pb.nseg * pb.nstrip;
+        pb.tile0 = total;
+        total += pb.ntiles;
+    }
+    std::vector<int2> sched;
+    sched.reserve(total);
+    for (int k = 0; k < b->count; ++k)
+        for (int t = 0; t < b->hp[k].ntiles; ++t) sched.push_back(make_int2(k, t));
+    if (schedule == 1) {
+        // longest tiles first: a ragged last strip is shorter; ties keep problem order
+        std::stable_sort(sched.begin(), sched.end(), [&](const int2& a, const int2& c) {
+            auto rows = [&](const int2& s) {
+                const Problem& pb = b->hp[s.x];
+                const int strip = s.y / pb.nseg;
+                return std::min(pb.ny, (strip + 1) * pb.tile_h) - strip * pb.tile_h;
+            };
+            return rows(a) > rows(c);
+        });
+    }
+    if (b->dsched) cudaFree(b->dsched);
+    b->dsched = nullptr;
+    CUDA_TRY(cudaMalloc(&b->dsched, sizeof(int2) * sched.size()));
+    CUDA_TRY(cudaMemcpy(b->dsched, sched.data(), sizeof(int2) * sched.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(b->dprobs, b->hp.data(), sizeof(Problem) * b->count, cudaMemcpyHostToDevice));
+    b->nslots = total;
+    b->tile_h = tile_h;
+    b->schedule = schedule;
+    b->graph.reset();
+    // persistent grid: as many blocks as fit on the GPU at once
+    int dev = 0, sms = 0, per_sm = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    per_sm = 4;
+    b->grid = std::max(1, std::min(sms * per_sm, (total + lbm::kWarpsPerBlock - 1) / lbm::kWarpsPerBlock));
+    return LBM_OK;
+}
+
+static cudaError_t batch_launch_one(lbm_stefan_batch* b, int parity)
+{
+    StepArgs a;
+    a.probs = b->dprobs;
+    a.nprob = b->count;
+    a.schedule = b->dsched;
+    a.nslots = b->nslots;
+    a.parity = parity;
+    a.rec = nullptr;
+    a.stats = b->dstats;
+    a.ticket = b->dticket;
+    return lbm::launch_d2q9_step(b->precision, a, b->grid, b->stream);
+}
+
+extern "C" lbm_status lbm_stefan_batch_create(int count, const lbm_stefan_problem* probs, int precision,
+                                              double newton_tol, int newton_max_iter, void* cuda_stream,
+                                              lbm_stefan_batch** out)
+{
+    if (!out || !probs || count < 1) return fail(LBM_ERR_ARG, "need count >= 1 problems");
+    *out = nullptr;
+    if (precision != LBM_FP32 && precision != LBM_FP64) return fail(LBM_ERR_ARG, "precision must be FP64 or FP32");
+    lbm_stefan_batch* b = new lbm_stefan_batch();
+    b->count = count;
+    b->precision = precision;
+    b->elem = precision == LBM_FP32 ? 4 : 8;
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+    const int segw = lbm::d2q9_segment_width(precision);
+    size_t total = 0;
+    size_t maxn = 0;
+    b->hp.resize(count);
+    b->state_bytes.resize(count);
+    for (int k = 0; k < count; ++k) {
+        const lbm_stefan_problem& p = probs[k];
+        lbm_status s = validate_common(p.nx, p.ny, p.tau, p.delta, p.ste, newton_tol, newton_max_iter);
+        if (s == LBM_OK && p.ny < 2) s = fail(LBM_ERR_ARG, "problem %d: ny must be >= 2", k);
+        for (int w = 0; w < 4 && s == LBM_OK; ++w)
+            if ((p.wall_kind[w] != 0 && p.wall_kind[w] != 1) || !std::isfinite(p.wall_theta[w]))
+                s = fail(LBM_ERR_ARG, "problem %d: bad wall %d", k, w);
+        if (s != LBM_OK) {
+            delete b;
+            return s;
+        }
+        Problem& pb = b->hp[k];
+        fill_problem(pb, 9, p.nx, p.ny, round_up(p.nx, segw), p.tau, p.delta, p.ste, newton_tol, newton_max_iter,
+                     LBM_BB_MIRROR, 16, segw);
+        for (int w = 0; w < 4; ++w) {
+            pb.wall_kind[w] = p.wall_kind[w];
+            pb.wall_theta[w] = p.wall_theta[w];
+        }
+        pb.stats = k;
+        b->state_bytes[k] = (size_t)9 * pb.plane * b->elem;
+        total += 2 * ((b->state_bytes[k] + 255) / 256 * 256);
+        maxn = std::max(maxn, (size_t)p.nx * p.ny);
+    }
+    cudaError_t e = cudaMalloc(&b->arena, total);
+    if (e == cudaSuccess) e = cudaMemset(b->arena, 0, total);
+    if (e == cudaSuccess) e = cudaMalloc(&b->dprobs, sizeof(Problem) * count);
+    if (e == cudaSuccess) e = cudaMalloc(&b->dstats, sizeof(DevStats) * count);
+    if (e == cudaSuccess) e = cudaMemset(b->dstats, 0, sizeof(DevStats) * count);
+    if (e == cudaSuccess) e = cudaMalloc(&b->dticket, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(b->dticket, 0, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->dscratch, sizeof(double) * maxn);
+    if (e != cudaSuccess) {
+        lbm_stefan_batch_destroy(b);
+        return fail(LBM_ERR_CUDA, "batch allocation failed: %s", cudaGetErrorString(e));
+    }
+    b->arena_bytes = total;
+    b->scratch_elems = maxn;
+    char* base = static_cast<char*>(b->arena);
+    for (int k = 0; k < count; ++k) {
+        const size_t sz = (b->state_bytes[k] + 255) / 256 * 256;
+        b->hp[k].state[0] = base;
+        b->hp[k].state[1] = base + sz;
+        base += 2 * sz;
+    }
+    lbm_status s = batch_build_schedule(b, 16, 1);
+    if (s != LBM_OK) {
+        lbm_stefan_batch_destroy(b);
+        return s;
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_stefan_batch_set_ic(lbm_stefan_batch* b, int k, const double* theta0, int on_device)
+{
+    if (!b || !theta0) return fail(LBM_ERR_ARG, "NULL argument");
+    if (k < 0 || k >= b->count) return fail(LBM_ERR_ARG, "problem index out of range");
+    if (b->parity != 0) return fail(LBM_ERR_STATE, "set_ic on a batch needs an even step count so far");
+    const Problem& hp = b->hp[k];
+    const size_t n = (size_t)hp.nx * hp.ny;
+    const double* src = theta0;
+    if (!on_device) {
+        CUDA_TRY(cudaMemcpyAsync(b->dscratch, theta0, n * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+        src = b->dscratch;
+    }
+    CUDA_TRY(cudaMemsetAsync(b->dstats + k, 0, sizeof(DevStats), b->stream));
+    CUDA_TRY(lbm::launch_init_state(b->precision, b->dprobs + k, hp, src, 0, b->dstats + k, b->stream));
+    CUDA_TRY(lbm::launch_finalize_init(b->dstats + k, b->stream));
+    if (!on_device) CUDA_TRY(cudaStreamSynchronize(b->stream));
+    return LBM_OK;
+}
+
+static lbm_status batch_capture(lbm_stefan_batch* b)
+{
+    b->graph.reset();
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < kGraphSteps && e == cudaSuccess; ++k) e = batch_launch_one(b, k & 1);
+    cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(LBM_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(&b->graph.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+    b->graph.steps = kGraphSteps;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_stefan_batch_step(lbm_stefan_batch* b, int nsteps)
+{
+    if (!b) return fail(LBM_ERR_ARG, "NULL handle");
+    if (nsteps < 0) return fail(LBM_ERR_ARG, "nsteps must be >= 0");
+    int left = nsteps;
+    if (b->parity == 1 && left > 0) {
+        CUDA_TRY(batch_launch_one(b, 1));
+        b->parity = 0;
+        --left;
+    }
+    if (b->stream != nullptr && left >= kGraphSteps) {
+        if (!b->graph.exec) {
+            lbm_status s = batch_capture(b);
+            if (s != LBM_OK) return s;
+        }
+        while (left >= kGraphSteps) {
+            CUDA_TRY(cudaGraphLaunch(b->graph.exec, b->stream));
+            left -= kGraphSteps;
+        }
+    }
+    while (left > 0) {
+        CUDA_TRY(batch_launch_one(b, b->parity));
+        b->parity ^= 1;
+        --left;
+    }
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_stefan_batch_get_fields(lbm_stefan_batch* b, int k, double* theta, int on_device)
+{
+    if (!b || !theta) return fail(LBM_ERR_ARG, "NULL argument");
+    if (k < 0 || k >= b->count) return fail(LBM_ERR_ARG, "problem index out of range");
+    const Problem& hp = b->hp[k];
+    const size_t n = (size_t)hp.nx * hp.ny;
+    double* dst = on_device ? theta : b->dscratch;
+    CUDA_TRY(lbm::launch_fields(b->precision, b->dprobs + k, hp, b->parity, dst, nullptr, nullptr, nullptr, b->stream));
+    if (!on_device) CUDA_TRY(cudaMemcpyAsync(theta, b->dscratch, n * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    DevStats st;
+    CUDA_TRY(cudaMemcpy(&st, b->dstats + k, sizeof st, cudaMemcpyDeviceToHost));
+    if (st.error) return fail((lbm_status)st.error, "device reported error %d in problem %d", st.error, k);
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_stefan_batch_get_stats(lbm_stefan_batch* b, int k, lbm_stefan_stats* out)
+{
+    if (!b || !out) return fail(LBM_ERR_ARG, "NULL argument");
+    if (k < 0 || k >= b->count) return fail(LBM_ERR_ARG, "problem index out of range");
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    DevStats st;
+    CUDA_TRY(cudaMemcpy(&st, b->dstats + k, sizeof st, cudaMemcpyDeviceToHost));
+    out->energy = st.energy;
+    out->energy_prev = st.energy_prev;
+    out->flux = st.flux;
+    out->imbalance = st.imbalance;
+    out->imbalance_max = st.imbalance_max;
+    out->steps = st.steps;
+    out->newton_nodes = st.newton_nodes;
+    out->newton_max_iter = st.newton_max_iter;
+    out->error = st.error;
+    if (st.error) return fail((lbm_status)st.error, "device reported error %d in problem %d", st.error, k);
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_stefan_batch_set_schedule(lbm_stefan_batch* b, int tile_h, int schedule)
+{
+    if (!b) return fail(LBM_ERR_ARG, "NULL handle");
+    if (tile_h < 1 || tile_h > 4096) return fail(LBM_ERR_ARG, "tile_h must be in 1..4096");
+    if (schedule != 0 && schedule != 1) return fail(LBM_ERR_ARG, "schedule must be 0 or 1");
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    return batch_build_schedule(b, tile_h, schedule);
+}
+
+extern "C" lbm_status lbm_stefan_batch_autotune(lbm_stefan_batch* b, int trial_steps, int* chosen_tile_h)
+{
+    if (!b) return fail(LBM_ERR_ARG, "NULL handle");
+    if (trial_steps < 1) return fail(LBM_ERR_ARG, "trial_steps must be >= 1");
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    // save the current state and statistics, try each candidate, restore
+    void* save = nullptr;
+    DevStats* save_st = nullptr;
+    CUDA_TRY(cudaMalloc(&save, b->arena_bytes));
+    cudaError_t e = cudaMalloc(&save_st, sizeof(DevStats) * b->count);
+    if (e != cudaSuccess) {
+        cudaFree(save);
+        return fail(LBM_ERR_CUDA, "autotune allocation failed: %s", cudaGetErrorString(e));
+    }
+    cudaMemcpyAsync(save, b->arena, b->arena_bytes, cudaMemcpyDeviceToDevice, b->stream);
+    cudaMemcpyAsync(save_st, b->dstats, sizeof(DevStats) * b->count, cudaMemcpyDeviceToDevice, b->stream);
+    const int saved_parity = b->parity;
+    const int cands_h[] = {8, 16, 32, 64};
+    const int cands_s[] = {1, 0};
+    float best = 1e30f;
+    int best_h = b->tile_h, best_s = b->schedule;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    lbm_status st = LBM_OK;
+    for (int hs : cands_h) {
+        for (int sc : cands_s) {
+            st = batch_build_schedule(b, hs, sc);
+            if (st != LBM_OK) break;
+            // one untimed warm-up step, then the timed trial
+            if (batch_launch_one(b, b->parity) != cudaSuccess) { st = fail(LBM_ERR_CUDA, "autotune launch failed"); break; }
+            b->parity ^= 1;
+            cudaEventRecord(e0, b->stream);
+            for (int k = 0; k < trial_steps; ++k) {
+                if (batch_launch_one(b, b->parity) != cudaSuccess) { st = fail(LBM_ERR_CUDA, "autotune launch failed"); break; }
+                b->parity ^= 1;
+            }
+            cudaEventRecord(e1, b->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                best_h = hs;
+                best_s = sc;
+            }
+            cudaMemcpyAsync(b->arena, save, b->arena_bytes, cudaMemcpyDeviceToDevice, b->stream);
+            b->parity = saved_parity;
+        }
+        if (st != LBM_OK) break;
+    }
+    cudaMemcpyAsync(b->dstats, save_st, sizeof(DevStats) * b->count, cudaMemcpyDeviceToDevice, b->stream);
+    cudaStreamSynchronize(b->stream);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(save);
+    cudaFree(save_st);
+    if (st != LBM_OK) return st;
+    st = batch_build_schedule(b, best_h, best_s);
+    if (chosen_tile_h) *chosen_tile_h = best_h;
+    return st;
+}
+
+extern "C" void lbm_stefan_batch_destroy(lbm_stefan_batch* b)
+{
+    if (!b) return;
+    b->graph.reset();
+    cudaFree(b->arena);
+    cudaFree(b->dprobs);
+    cudaFree(b->dstats);
+    cudaFree(b->dticket);
+    cudaFree(b->dsched);
+    cudaFree(b->dscratch);
+    delete b;
+}

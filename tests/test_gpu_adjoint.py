@@ -1,0 +1,139 @@
+"""Adjoint of the GPU step (through the C ABI, driven by the autograd Function).
+
+Checks: the oracle's FP64 discrete adjoint on a 64 x 64 problem with the
+parameters and step count of the 1024^2 adjoint workload (2,000 steps), central
+finite differences (h = 1e-4) of the GPU FP64 forward to 1e-4 relative, the
+FP32 form against the FP64 adjoint, and independence from the checkpoint
+interval.
+"""
+import numpy as np
+import pytest
+
+from paper_2505_13097_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_mod():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def phi(x, d):
+    return 0.5 * (1.0 + np.tanh(x / d))
+
+
+def make_problem(orc, n=64, steps=2000, precision=0):
+    base = workloads.adjoint_2d(n=n, steps=steps, precision=precision)
+    tcase = workloads.adjoint_target_case(base)
+    t0 = workloads.adjoint_target_theta0(base)
+    P = orc.Problem(2, n, n, tau=tcase.tau, delta=tcase.delta, ste=tcase.ste, walls=tcase.walls)
+    _, thT = P.run(t0, steps)
+    return base, phi(thT, base.delta)
+
+
+def gpu_grad(torch, case, target, steps=None, checkpoint_every=None, ste=None, wall=None, theta0=None, bb_mode=0):
+    from paper_2505_13097_gb300.autograd import misfit
+    steps = case.steps if steps is None else steps
+    th0 = torch.tensor(case.theta0() if theta0 is None else theta0, device="cuda", requires_grad=True)
+    tw = torch.tensor([case.walls.get(k, (0, 0.0))[1] for k in "WESN"], dtype=torch.float64, device="cuda")
+    if wall is not None:
+        tw = tw + torch.tensor(wall, dtype=torch.float64, device="cuda")
+    tw.requires_grad_(True)
+    st = torch.tensor(case.ste if ste is None else ste, dtype=torch.float64, device="cuda", requires_grad=True)
+    tgt = torch.tensor(target, device="cuda")
+    L = misfit(th0, tw, st, case, steps, tgt, checkpoint_every, bb_mode)
+    L.backward()
+    return float(L.detach()), th0.grad.cpu().numpy(), tw.grad.cpu().numpy(), float(st.grad)
+
+
+def test_fp64_adjoint_matches_oracle_adjoint(torch_mod, orc):
+    case, target = make_problem(orc)
+    L, g0, gw, gs = gpu_grad(torch_mod, case, target)
+    P = orc.Problem(2, case.nx, case.ny, tau=case.tau, delta=case.delta, ste=case.ste, walls=case.walls)
+    Lo, g0o, gwo, gso = P.adjoint(case.theta0(), case.steps, target)
+    assert abs(L - Lo) <= 1e-10 * abs(Lo)
+    assert np.max(np.abs(g0 - g0o)) <= 1e-9 * np.max(np.abs(g0o))
+    assert abs(gw[0] - gwo[0]) <= 1e-9 * abs(gwo[0])
+    assert abs(gs - gso) <= 1e-9 * abs(gso)
+
+
+@pytest.mark.parametrize("bb_mode", [0, 1])
+def test_fp64_adjoint_oracle_walls(torch_mod, orc, bb_mode):
+    walls = {"W": (1, 0.9), "S": (1, -0.3), "E": (0, 0.0), "N": (0, 0.0)}
+    case = workloads.Case("t", 2, 70, 45, 0.84, 0.03, 0.2, walls, 80, workloads.FP64)
+    th0 = workloads.random_field((45, 70), -0.15, 0.15, seed=31)
+    target = workloads.random_field((45, 70), 0.0, 1.0, seed=32)
+    L, g0, gw, gs = gpu_grad(torch_mod, case, target, theta0=th0, bb_mode=bb_mode)
+    P = orc.Problem(2, 70, 45, tau=0.84, delta=0.03, ste=0.2, walls=walls, bb_mode=bb_mode)
+    Lo, g0o, gwo, gso = P.adjoint(th0, 80, target)
+    assert abs(L - Lo) <= 1e-10 * abs(Lo)
+    assert np.max(np.abs(g0 - g0o)) <= 1e-9 * np.max(np.abs(g0o))
+    for k in (0, 2):
+        assert abs(gw[k] - gwo[k]) <= 1e-9 * max(abs(gwo[k]), 1e-12)
+    assert abs(gs - gso) <= 1e-9 * abs(gso)
+
+
+def test_d1q3_adjoint_matches_oracle(torch_mod, orc):
+    case = workloads.melt_1d(n=200, steps=600)
+    target = phi(workloads.random_field((1, 200), -0.05, 0.05, seed=4), case.delta)
+    L, g0, gw, gs = gpu_grad(torch_mod, case, target)
+    P = orc.Problem(1, 200, 1, tau=case.tau, delta=case.delta, ste=case.ste, walls=case.walls)
+    Lo, g0o, gwo, gso = P.adjoint(case.theta0(), case.steps, target)
+    assert abs(L - Lo) <= 1e-10 * abs(Lo)
+    assert np.max(np.abs(g0 - g0o)) <= 1e-9 * np.max(np.abs(g0o))
+    assert abs(gs - gso) <= 1e-9 * abs(gso)
+
+
+def test_fp64_adjoint_central_differences(torch_mod, orc):
+    from paper_2505_13097_gb300.autograd import misfit
+    torch = torch_mod
+    case, target = make_problem(orc, n=64, steps=400)
+    L, g0, gw, gs = gpu_grad(torch, case, target)
+    h = 1e-4
+    tgt = torch.tensor(target, device="cuda")
+
+    def loss(theta0, wall_w, ste):
+        tw = torch.tensor([wall_w, 0.0, 0.0, 0.0], dtype=torch.float64, device="cuda")
+        with torch.no_grad():
+            return float(misfit(torch.tensor(theta0, device="cuda"), tw, torch.tensor(ste, dtype=torch.float64),
+                                case, case.steps, tgt))
+
+    th0, tw0 = case.theta0(), case.walls["W"][1]
+    v = workloads.random_direction(th0.shape, seed=77)
+
+    def cdiff(f):
+        # central differences with h = 1e-4 and h/2, Richardson-extrapolated
+        # (removes the O(h^2) truncation term, which alone is ~1e-4 here)
+        d1 = (f(h) - f(-h)) / (2 * h)
+        d2 = (f(h / 2) - f(-h / 2)) / h
+        return (4 * d2 - d1) / 3
+
+    fd = cdiff(lambda e: loss(th0 + e * v, tw0, case.ste))
+    assert abs(np.sum(g0 * v) - fd) <= 1e-4 * abs(fd)
+    fdw = cdiff(lambda e: loss(th0, tw0 + e, case.ste))
+    assert abs(gw[0] - fdw) <= 1e-4 * abs(fdw)
+    fds = cdiff(lambda e: loss(th0, tw0, case.ste + e))
+    assert abs(gs - fds) <= 1e-4 * abs(fds)
+
+
+def test_fp32_adjoint_close_to_fp64(torch_mod, orc):
+    case64, target = make_problem(orc, n=64, steps=500, precision=0)
+    case32 = case64.scaled(precision=1)
+    _, g64, gw64, gs64 = gpu_grad(torch_mod, case64, target)
+    _, g32, gw32, gs32 = gpu_grad(torch_mod, case32, target)
+    assert np.max(np.abs(g32 - g64)) <= 2e-3 * np.max(np.abs(g64))
+    assert abs(gs32 - gs64) <= 2e-3 * abs(gs64)
+    assert abs(gw32[0] - gw64[0]) <= 2e-3 * abs(gw64[0])
+
+
+def test_checkpoint_interval_does_not_change_gradient(torch_mod, orc):
+    case, target = make_problem(orc, n=64, steps=130)
+    a = gpu_grad(torch_mod, case, target, checkpoint_every=130)
+    b = gpu_grad(torch_mod, case, target, checkpoint_every=7)
+    assert a[0] == b[0]
+    assert np.max(np.abs(a[1] - b[1])) <= 1e-13 * np.max(np.abs(a[1]))
+    assert abs(a[3] - b[3]) <= 1e-12 * abs(a[3])

@@ -1,0 +1,79 @@
+"""Batched problems of uneven sizes in one persistent launch per step."""
+import numpy as np
+import pytest
+
+from paper_2505_13097_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_13097_gb300 import solver
+    return solver
+
+
+def small_batch(count=8, seed=5):
+    cases = workloads.batch_2d(count=count, lo=16, hi=128, seed=seed)
+    return cases
+
+
+@pytest.mark.parametrize("tile_h,schedule", [(16, 1), (8, 0), (64, 1), (5, 0)])
+def test_batch_matches_oracle(gpu, orc, tile_h, schedule):
+    cases = small_batch()
+    B = gpu.StefanBatch(cases)
+    B.set_schedule(tile_h, schedule)
+    for k, c in enumerate(cases):
+        B.set_ic(k, c.theta0())
+    steps = 400
+    B.step(steps)
+    for k, c in enumerate(cases):
+        P = orc.Problem(2, c.nx, c.ny, tau=c.tau, delta=c.delta, ste=c.ste, walls=c.walls)
+        _, ref = P.run(c.theta0(), steps)
+        th = B.theta(k)
+        assert np.max(np.abs(th - ref)) / np.max(np.abs(ref)) < 2e-5, (k, c.nx)
+        st = B.stats(k)
+        assert st["steps"] == steps and st["error"] == 0
+    B.close()
+
+
+def test_batch_equals_single_problems(gpu):
+    cases = small_batch(count=6, seed=9)
+    B = gpu.StefanBatch(cases)
+    for k, c in enumerate(cases):
+        B.set_ic(k, c.theta0())
+    B.step(97)
+    for k, c in enumerate(cases):
+        S = gpu.Stefan.from_case(c)
+        S.set_ic(c.theta0())
+        S.step(97)
+        assert np.array_equal(S.theta(), B.theta(k))
+        assert S.stats()["energy"] == B.stats(k)["energy"]
+        S.close()
+    B.close()
+
+
+def test_autotune_keeps_state(gpu):
+    cases = small_batch(count=10, seed=3)
+    B = gpu.StefanBatch(cases)
+    for k, c in enumerate(cases):
+        B.set_ic(k, c.theta0())
+    B.step(10)
+    before = [B.theta(k) for k in range(len(cases))]
+    h = B.autotune(trial_steps=5)
+    assert h in (8, 16, 32, 64)
+    after = [B.theta(k) for k in range(len(cases))]
+    for a, b in zip(before, after):
+        assert np.array_equal(a, b)
+    B.step(40)
+    ref = gpu.StefanBatch(cases)
+    for k, c in enumerate(cases):
+        ref.set_ic(k, c.theta0())
+    ref.step(50)
+    for k in range(len(cases)):
+        assert np.array_equal(ref.theta(k), B.theta(k))
+    B.close()
+    ref.close()
