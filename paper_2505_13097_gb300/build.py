@@ -39,13 +39,15 @@ def _stale(objs, extra_deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
+def build(force: bool = False, verbose: bool = False, extra_flags=(), out: str = None) -> str:
+    """Compile csrc/*.cu and link the shared library (default: lib/liblbm_stefan.so)."""
+    target = out or LIB
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(os.path.dirname(HERE), "include", "lbm_stefan.h"))
-    if not force and not _stale(None, headers):
+    if not force and out is None and not _stale(None, headers):
         return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
-    objdir = os.path.join(OUT_DIR, "obj")
+    os.makedirs(os.path.dirname(target), exist_ok=True)
+    objdir = os.path.join(os.path.dirname(target), "obj_" + os.path.basename(target).replace(".", "_"))
     os.makedirs(objdir, exist_ok=True)
     cc = nvcc()
 
@@ -62,13 +64,13 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     srcs = sources()
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = target + ".tmp%d" % os.getpid()
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, target)
+    return target
 
 
 if __name__ == "__main__":

@@ -38,6 +38,23 @@ __global__ void init_state_kernel(const Problem* dprob, const double* __restrict
     if ((threadIdx.x & 31) == 0) acc_add(&st->cur_energy, e);
 }
 
+__global__ void wall_constants_kernel(Problem* probs, int nprob)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nprob) return;
+    Problem& pb = probs[p];
+    for (int k = 0; k < 4; ++k) {
+        pb.wall_tanh[k] = tanh(pb.wall_theta[k] * pb.inv_delta);
+        pb.wall_phi[k] = 0.5 + 0.5 * pb.wall_tanh[k];
+    }
+}
+
+cudaError_t launch_wall_constants(Problem* dprobs, int nprob, cudaStream_t s)
+{
+    wall_constants_kernel<<<(nprob + 127) / 128, 128, 0, s>>>(dprobs, nprob);
+    return cudaGetLastError();
+}
+
 __global__ void finalize_init_kernel(DevStats* st)
 {
     st->energy = acc_read(&st->cur_energy);

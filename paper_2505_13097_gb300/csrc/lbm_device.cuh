@@ -118,6 +118,90 @@ __device__ __forceinline__ NewtonOut newton_solve(double m0, double theta, doubl
     return r;
 }
 
+// Mixed-precision form of the same solve (same root, same stopping rule).
+//  1. FP32 Newton (tanhf) locates the root to FP32 accuracy, x0 (it stops at
+//     FP32 precision or once its updates stop halving).
+//  2. FP64 Newton from x0: one FP64 tanh gives t = tanh(x0/delta), F, F' and
+//     the update d.  Newton's error e after the update is about
+//     |F''| d^2 / (2 F') (F'' = phi2/Ste with phi2 = -t(1-t^2)/delta^2), and
+//     theta' = m0 + (phi(theta) - phi(root))/Ste inherits it as (F' - 1) e;
+//     when |F''| d^2 is below 0.1 tol max(1,|x|) and |d| <= 3e-5 delta,
+//     x0 + d is accepted and phi(x0 + d) comes from the cubic Taylor
+//     expansion (third derivative phi3 = (1-t^2)(3t^2-1)/delta^3; the quartic
+//     remainder is below (d/delta)^4 / 12 < 1e-19).  Otherwise the FP64
+//     iteration goes on.  Iterations of both precisions count against maxit.
+//  3. Anything unexpected (no FP32 convergence, an FP64 update larger than
+//     1e-3 delta) falls back to newton_solve from theta.
+__device__ __forceinline__ NewtonOut newton_mixed(double m0, double theta, double phi_theta, double inv_ste,
+                                                  double inv_delta, double tol, int maxit)
+{
+    const float mf = (float)m0, pf = (float)phi_theta, isf = (float)inv_ste, idf = (float)inv_delta;
+    float lo = mf + (pf - 1.0f) * isf, hi = mf + pf * isf;
+    float x = (float)theta;
+    const float xfloor = (float)(1.0 / inv_delta);
+    float step_prev = hi - lo;
+    int k = 0;
+    // FP32 stage: plain Newton inside the bracket; it stops at FP32 precision or
+    // when the update no longer halves (the FP32 rounding floor of F is reached).
+    // Only an iterate that leaves the bracket is replaced by the midpoint.
+    for (; k < 16; ++k) {
+        const float t = tanhf(x * idf);
+        const float F = (x - mf) + (0.5f * t + 0.5f - pf) * isf;
+        if (F == 0.0f) break;
+        if (F < 0.0f) lo = fmaxf(lo, x);
+        else hi = fminf(hi, x);
+        const float dph = 0.5f * (1.0f - t) * (1.0f + t) * idf;
+        float xn = x - F / (1.0f + dph * isf);
+        if (!(xn >= lo && xn <= hi)) {
+            xn = 0.5f * (lo + hi);
+        } else {
+            const float st = fabsf(xn - x);
+            if (st <= 1e-7f * fmaxf(fabsf(x), xfloor) || (k >= 2 && st >= 0.5f * step_prev)) {
+                x = xn;
+                ++k;
+                break;
+            }
+            step_prev = st;
+        }
+        x = xn;
+    }
+    const bool conv32 = isfinite(x);
+    const double delta = 1.0 / inv_delta;
+    if (conv32) {
+        double xd = (double)x;
+        for (int j = 0; j < 3; ++j) {
+            const double t = tanh(xd * inv_delta);
+            const double s = (1.0 - t) * (1.0 + t);
+            const double ph = 0.5 + 0.5 * t;
+            const double F = (xd - m0) + (ph - phi_theta) * inv_ste;
+            const double dph = 0.5 * s * inv_delta;
+            const double Fp = 1.0 + dph * inv_ste;
+            const double d = -F / Fp;
+            const double ad = fabs(d);
+            if (ad > 1e-3 * delta) break;   // FP32 start not close enough: full FP64 solve
+            const double x1 = xd + d;
+            const double sc = tol * fmax(1.0, fabs(xd));
+            const double p2 = -t * s * inv_delta * inv_delta;                          // phi''
+            const double p3 = s * (3.0 * t * t - 1.0) * inv_delta * inv_delta * inv_delta;  // phi'''
+            // theta' = m0 + (phi(theta) - phi(x))/Ste carries a root error e as (F' - 1) e,
+            // so the test bounds F' e ~ |F''| d^2 / 2, not e alone
+            if (ad <= sc || (ad <= 3e-5 * delta && fabs(p2) * inv_ste * d * d <= 0.1 * sc)) {
+                NewtonOut r;
+                r.root = x1;
+                r.phi_root = ph + d * (dph + d * (0.5 * p2 + d * p3 * (1.0 / 6.0)));
+                r.iters = k + j + 1;
+                r.ok = r.iters <= maxit;
+                return r;
+            }
+            xd = x1;
+        }
+    }
+    NewtonOut r = newton_solve(m0, theta, phi_theta, inv_ste, inv_delta, tol, maxit);
+    r.iters += k;
+    r.ok = r.ok && r.iters <= maxit;
+    return r;
+}
+
 // ---------------------------------------------------------------- reductions
 __device__ __forceinline__ double warp_sum(double v)
 {
@@ -138,18 +222,44 @@ __device__ __forceinline__ int warp_max_i(int v)
     return v;
 }
 
-// Add v into the 128-bit fixed-point accumulator (value scaled by 2^60).
+// 128-bit fixed-point value (scaled by 2^60) as a register pair; adding two of
+// them is exact, so sums in this form do not depend on the order of terms.
+struct Fx {
+    long long hi;
+    unsigned long long lo;
+};
+
+__device__ __forceinline__ Fx to_fixed(double v)
+{
+    Fx f;
+    const double s = v * 0.0625;   // v * 2^60 / 2^64
+    const double h = floor(s);
+    const double r = s - h;        // in [0, 1), exact
+    f.hi = (long long)h;
+    f.lo = __double2ull_rz(r * 18446744073709551616.0);
+    return f;
+}
+
+__device__ __forceinline__ void fx_add(Fx& a, const Fx& b)
+{
+    const unsigned long long lo = a.lo + b.lo;
+    a.hi += b.hi + (lo < a.lo ? 1 : 0);
+    a.lo = lo;
+}
+
+__device__ __forceinline__ void acc_add_fx(Acc128* a, const Fx& v)
+{
+    if (v.hi == 0 && v.lo == 0) return;
+    const unsigned long long old = atomicAdd(&a->lo, v.lo);
+    const long long carry = (old + v.lo < old) ? 1 : 0;
+    atomicAdd(reinterpret_cast<unsigned long long*>(&a->hi), (unsigned long long)(v.hi + carry));
+}
+
+// Add v into the 128-bit fixed-point accumulator.
 __device__ __forceinline__ void acc_add(Acc128* a, double v)
 {
     if (v == 0.0) return;
-    double s = v * 0.0625;          // v * 2^60 / 2^64
-    double h = floor(s);
-    double r = s - h;               // in [0, 1), exact
-    long long hi = (long long)h;
-    unsigned long long lo = __double2ull_rz(r * 18446744073709551616.0);
-    unsigned long long old = atomicAdd(&a->lo, lo);
-    long long carry = (old + lo < old) ? 1 : 0;
-    atomicAdd(reinterpret_cast<unsigned long long*>(&a->hi), (unsigned long long)(hi + carry));
+    acc_add_fx(a, to_fixed(v));
 }
 
 __device__ __forceinline__ double acc_read(const Acc128* a)

@@ -47,14 +47,28 @@ struct Problem {
     double omega;            // 1/tau
     double ste, inv_ste, delta, inv_delta;
     double tol;
+    double sat;              // saturation threshold K*delta of the exact-source shortcut
     int maxit;
     int bb_mode;
     int wall_kind[4];        // W, E, S, N
     double wall_theta[4];
+    double wall_tanh[4];     // tanh(theta_wall / delta), set on the device (wall_constants)
+    double wall_phi[4];      // phi(theta_wall)
     int nseg, nstrip, tile_h;
     int tile0;               // first global tile index of this problem
     int ntiles;
     int stats;               // index into the DevStats array
+};
+
+// A node whose local Newton solve is deferred to the job kernel: the step
+// kernel stores its q_i (not yet relaxed) and these inputs.
+struct NewtonJob {
+    int prob;                // problem index
+    int node;                // y * nx + x
+    double m0;               // M0(q) after the wall closures
+    double theta;            // theta(t) = M0(f) at the node
+    // FP32 form: m0 and theta are stored as float-float pairs (hi, lo) in the
+    // bytes of m0 and theta, so the step kernel needs no FP64 conversion
 };
 
 // Per-launch arguments of the forward step kernels.
@@ -67,6 +81,20 @@ struct StepArgs {
     double* rec;             // optional theta' record plane (single problem only), ny x pitch doubles
     DevStats* stats;
     unsigned int* ticket;    // last-block counter, zero between launches
+    NewtonJob* jobs;         // deferred Newton nodes (D2Q9), capacity = total nodes
+    unsigned int* job_count; // number of jobs; reset by the job kernel
+};
+
+// Per-launch arguments of the Newton job kernel (runs after every D2Q9 step).
+struct JobArgs {
+    const Problem* probs;
+    int nprob;
+    int parity;              // the step read state[parity] and wrote state[parity ^ 1]
+    double* rec;             // theta' record plane of the step (single problem), may be NULL
+    DevStats* stats;
+    unsigned int* ticket;
+    const NewtonJob* jobs;
+    unsigned int* job_count;
 };
 
 // Per-launch arguments of the adjoint kernels (single problem).
@@ -87,6 +115,8 @@ constexpr int kWallRec = 19;   // doubles per wall-node record of the adjoint
 // D2Q9 launchers (step_d2q9.cu)
 cudaError_t launch_d2q9_step(int precision, const StepArgs& a, int grid, cudaStream_t s);
 int d2q9_segment_width(int precision);   // nodes per warp segment
+int d2q9_blocks_per_sm(int precision);   // resident step blocks per SM (persistent grid)
+cudaError_t launch_newton_jobs(int precision, const JobArgs& a, cudaStream_t s);
 
 // D1Q3 launchers (step_d1q3.cu)
 cudaError_t launch_d1q3_step(int precision, const StepArgs& a, const Problem& hp, cudaStream_t s);
@@ -100,6 +130,8 @@ cudaError_t launch_init_state(int precision, const Problem* dprob, const Problem
 cudaError_t launch_fields(int precision, const Problem* dprob, const Problem& hp, int parity, double* theta,
                           double* phi, double* H, double* theta_plane, cudaStream_t s);
 cudaError_t launch_finalize_init(DevStats* st, cudaStream_t s);
+// tanh(theta_wall/delta) and phi(theta_wall) of every wall, for nprob problems
+cudaError_t launch_wall_constants(Problem* dprobs, int nprob, cudaStream_t s);
 
 // Adjoint kernels (adjoint.cu)
 cudaError_t launch_adj_seed(int precision, const Problem* dprob, const Problem& hp, const double* theta_T,

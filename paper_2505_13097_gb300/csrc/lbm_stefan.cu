@@ -61,6 +61,8 @@ struct lbm_stefan {
     DevStats* dstats = nullptr;
     unsigned int* dticket = nullptr;
     double* dscratch = nullptr;   // 3 * nx * ny doubles (host field transfers)
+    lbm::NewtonJob* djobs = nullptr;    // deferred Newton nodes of one step (capacity nx * ny)
+    unsigned int* djob_count = nullptr;
     int parity = 0;
     bool ic = false;
     GraphCache graph;
@@ -86,6 +88,8 @@ struct lbm_stefan_batch {
     cudaStream_t stream = nullptr;
     double* dscratch = nullptr;
     size_t scratch_elems = 0;
+    lbm::NewtonJob* djobs = nullptr;
+    unsigned int* djob_count = nullptr;
     GraphCache graph;
 };
 
@@ -101,8 +105,19 @@ static lbm_status validate_common(int nx, int ny, double tau, double delta, doub
     return LBM_OK;
 }
 
+// Threshold of the exact-source shortcut: theta and m0 beyond K*delta on the same
+// side give theta' = m0.  FP64: K = 19.5, where tanh rounds to +-1 and the
+// shortcut is exact.  FP32 populations: K with 2 exp(-2K)/Ste = 1e-10 (the
+// neglected source), about 100x below the rounding of the stored populations.
+static double saturation_threshold(int precision, double delta, double ste)
+{
+    double k = 19.5;
+    if (precision == LBM_FP32) k = std::min(19.5, std::max(10.0, 0.5 * std::log(2.0 / (ste * 1e-10))));
+    return k * delta;
+}
+
 static void fill_problem(Problem& pb, int q, int nx, int ny, int pitch, double tau, double delta, double ste,
-                         double tol, int maxit, int bb_mode, int tile_h, int segw)
+                         double tol, int maxit, int bb_mode, int tile_h, int segw, int precision)
 {
     std::memset(&pb, 0, sizeof pb);
     pb.nx = nx;
@@ -116,6 +131,7 @@ static void fill_problem(Problem& pb, int q, int nx, int ny, int pitch, double t
     pb.delta = delta;
     pb.inv_delta = 1.0 / delta;
     pb.tol = tol;
+    pb.sat = saturation_threshold(precision, delta, ste);
     pb.maxit = maxit;
     pb.bb_mode = bb_mode;
     pb.tile_h = tile_h;
@@ -127,6 +143,7 @@ static void fill_problem(Problem& pb, int q, int nx, int ny, int pitch, double t
 static lbm_status upload_problem(lbm_stefan* h)
 {
     CUDA_TRY(cudaMemcpyAsync(h->dprob, &h->hp, sizeof(Problem), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(lbm::launch_wall_constants(h->dprob, 1, h->stream));
     CUDA_TRY(cudaStreamSynchronize(h->stream));
     return LBM_OK;
 }
@@ -142,15 +159,38 @@ static StepArgs single_args(lbm_stefan* h, int parity, double* rec)
     a.rec = rec;
     a.stats = h->dstats;
     a.ticket = h->dticket;
+    a.jobs = h->djobs;
+    a.job_count = h->djob_count;
     return a;
 }
 
+static lbm::JobArgs job_args(const Problem* probs, int nprob, int parity, double* rec, DevStats* st,
+                             unsigned int* ticket, lbm::NewtonJob* jobs, unsigned int* count)
+{
+    lbm::JobArgs j;
+    j.probs = probs;
+    j.nprob = nprob;
+    j.parity = parity;
+    j.rec = rec;
+    j.stats = st;
+    j.ticket = ticket;
+    j.jobs = jobs;
+    j.job_count = count;
+    return j;
+}
+
+// One D2Q9 step is two launches: the fused stream/collide kernel, which defers
+// the nodes that need the Newton iteration, and the job kernel that solves them.
 static cudaError_t launch_one(lbm_stefan* h, int parity, double* rec)
 {
     StepArgs a = single_args(h, parity, rec);
     if (h->p.lattice == LBM_D2Q9) {
         const int grid = (h->hp.ntiles + lbm::kWarpsPerBlock - 1) / lbm::kWarpsPerBlock;
-        return lbm::launch_d2q9_step(h->precision, a, grid, h->stream);
+        cudaError_t e = lbm::launch_d2q9_step(h->precision, a, grid, h->stream);
+        if (e != cudaSuccess) return e;
+        return lbm::launch_newton_jobs(h->precision,
+                                       job_args(h->dprob, 1, parity, rec, h->dstats, h->dticket, h->djobs, h->djob_count),
+                                       h->stream);
     }
     return lbm::launch_d1q3_step(h->precision, a, h->hp, h->stream);
 }
@@ -191,7 +231,7 @@ extern "C" lbm_status lbm_stefan_create(const lbm_stefan_params* p, void* cuda_s
     const int segw = p->lattice == LBM_D2Q9 ? lbm::d2q9_segment_width(p->precision) : 32;
     const int pitch = round_up(p->nx, segw);
     fill_problem(h->hp, q, p->nx, p->ny, pitch, p->tau, p->delta, p->ste, p->newton_tol, p->newton_max_iter,
-                 p->bb_mode, 16, segw);
+                 p->bb_mode, 16, segw, p->precision);
     h->state_bytes = (size_t)q * h->hp.plane * h->elem;
     cudaError_t e = cudaSuccess;
     void* bufs[2] = {nullptr, nullptr};
@@ -205,6 +245,9 @@ extern "C" lbm_status lbm_stefan_create(const lbm_stefan_params* p, void* cuda_s
     if (e == cudaSuccess) e = cudaMalloc(&h->dticket, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMemset(h->dticket, 0, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMalloc(&h->dscratch, sizeof(double) * 3 * (size_t)p->nx * p->ny);
+    if (e == cudaSuccess && q == 9) e = cudaMalloc(&h->djobs, sizeof(lbm::NewtonJob) * (size_t)p->nx * p->ny);
+    if (e == cudaSuccess) e = cudaMalloc(&h->djob_count, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(h->djob_count, 0, sizeof(unsigned int));
     h->hp.state[0] = bufs[0];
     h->hp.state[1] = bufs[1];
     h->hp.stats = 0;
@@ -468,6 +511,8 @@ extern "C" void lbm_stefan_destroy(lbm_stefan* h)
     cudaFree(h->dstats);
     cudaFree(h->dticket);
     cudaFree(h->dscratch);
+    cudaFree(h->djobs);
+    cudaFree(h->djob_count);
     delete h;
 }
 
@@ -507,6 +552,8 @@ static lbm_status batch_build_schedule(lbm_stefan_batch* b, int tile_h, int sche
     CUDA_TRY(cudaMalloc(&b->dsched, sizeof(int2) * sched.size()));
     CUDA_TRY(cudaMemcpy(b->dsched, sched.data(), sizeof(int2) * sched.size(), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(b->dprobs, b->hp.data(), sizeof(Problem) * b->count, cudaMemcpyHostToDevice));
+    CUDA_TRY(lbm::launch_wall_constants(b->dprobs, b->count, nullptr));
+    CUDA_TRY(cudaDeviceSynchronize());
     b->nslots = total;
     b->tile_h = tile_h;
     b->schedule = schedule;
@@ -515,7 +562,7 @@ static lbm_status batch_build_schedule(lbm_stefan_batch* b, int tile_h, int sche
     int dev = 0, sms = 0, per_sm = 0;
     CUDA_TRY(cudaGetDevice(&dev));
     CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    per_sm = 4;
+    per_sm = lbm::d2q9_blocks_per_sm(b->precision);
     b->grid = std::max(1, std::min(sms * per_sm, (total + lbm::kWarpsPerBlock - 1) / lbm::kWarpsPerBlock));
     return LBM_OK;
 }
@@ -531,7 +578,14 @@ static cudaError_t batch_launch_one(lbm_stefan_batch* b, int parity)
     a.rec = nullptr;
     a.stats = b->dstats;
     a.ticket = b->dticket;
-    return lbm::launch_d2q9_step(b->precision, a, b->grid, b->stream);
+    a.jobs = b->djobs;
+    a.job_count = b->djob_count;
+    cudaError_t e = lbm::launch_d2q9_step(b->precision, a, b->grid, b->stream);
+    if (e != cudaSuccess) return e;
+    return lbm::launch_newton_jobs(b->precision,
+                                   job_args(b->dprobs, b->count, parity, nullptr, b->dstats, b->dticket, b->djobs,
+                                            b->djob_count),
+                                   b->stream);
 }
 
 extern "C" lbm_status lbm_stefan_batch_create(int count, const lbm_stefan_problem* probs, int precision,
@@ -549,6 +603,7 @@ extern "C" lbm_status lbm_stefan_batch_create(int count, const lbm_stefan_proble
     const int segw = lbm::d2q9_segment_width(precision);
     size_t total = 0;
     size_t maxn = 0;
+    size_t total_nodes = 0;
     b->hp.resize(count);
     b->state_bytes.resize(count);
     for (int k = 0; k < count; ++k) {
@@ -564,7 +619,7 @@ extern "C" lbm_status lbm_stefan_batch_create(int count, const lbm_stefan_proble
         }
         Problem& pb = b->hp[k];
         fill_problem(pb, 9, p.nx, p.ny, round_up(p.nx, segw), p.tau, p.delta, p.ste, newton_tol, newton_max_iter,
-                     LBM_BB_MIRROR, 16, segw);
+                     LBM_BB_MIRROR, 16, segw, precision);
         for (int w = 0; w < 4; ++w) {
             pb.wall_kind[w] = p.wall_kind[w];
             pb.wall_theta[w] = p.wall_theta[w];
@@ -573,6 +628,7 @@ extern "C" lbm_status lbm_stefan_batch_create(int count, const lbm_stefan_proble
         b->state_bytes[k] = (size_t)9 * pb.plane * b->elem;
         total += 2 * ((b->state_bytes[k] + 255) / 256 * 256);
         maxn = std::max(maxn, (size_t)p.nx * p.ny);
+        total_nodes += (size_t)p.nx * p.ny;
     }
     cudaError_t e = cudaMalloc(&b->arena, total);
     if (e == cudaSuccess) e = cudaMemset(b->arena, 0, total);
@@ -582,6 +638,9 @@ extern "C" lbm_status lbm_stefan_batch_create(int count, const lbm_stefan_proble
     if (e == cudaSuccess) e = cudaMalloc(&b->dticket, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMemset(b->dticket, 0, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMalloc(&b->dscratch, sizeof(double) * maxn);
+    if (e == cudaSuccess) e = cudaMalloc(&b->djobs, sizeof(lbm::NewtonJob) * total_nodes);
+    if (e == cudaSuccess) e = cudaMalloc(&b->djob_count, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(b->djob_count, 0, sizeof(unsigned int));
     if (e != cudaSuccess) {
         lbm_stefan_batch_destroy(b);
         return fail(LBM_ERR_CUDA, "batch allocation failed: %s", cudaGetErrorString(e));
@@ -788,5 +847,7 @@ extern "C" void lbm_stefan_batch_destroy(lbm_stefan_batch* b)
     cudaFree(b->dticket);
     cudaFree(b->dsched);
     cudaFree(b->dscratch);
+    cudaFree(b->djobs);
+    cudaFree(b->djob_count);
     delete b;
 }

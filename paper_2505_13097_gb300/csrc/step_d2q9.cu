@@ -96,10 +96,12 @@ __device__ __noinline__ double wall_closure(P* q, const P* u, int x, int y, cons
     int walls = (x == 0 ? 1 : 0) | (x == pb.nx - 1 ? 2 : 0) | (y == 0 ? 4 : 0) | (y == pb.ny - 1 ? 8 : 0);
     dir = false;
     theta_d = 0.0;
+    int wk = -1;
     for (int k = 0; k < 4; ++k)
         if (((walls >> k) & 1) && pb.wall_kind[k] == 1) {
             dir = true;
             theta_d = pb.wall_theta[k];
+            wk = k;
             break;
         }
     double out = 0.0, in = 0.0;
@@ -112,7 +114,21 @@ __device__ __noinline__ double wall_closure(P* q, const P* u, int x, int y, cons
         double th = 0.0;
 #pragma unroll
         for (int i = 0; i < 9; ++i) th += (double)u[i];
-        double m0t = theta_d + (phi_of(theta_d, pb.inv_delta) - phi_of(th, pb.inv_delta)) * pb.inv_ste;
+        // phi(theta) - phi(theta_D): the wall node stays within rounding of theta_D, so the
+        // tanh addition theorem with tanh(d/delta) = z - z^3/3 + 2z^5/15 (|z| <= 1e-4,
+        // remainder < 1e-29) replaces a full tanh; the general case falls back to tanh
+        const double z = (th - theta_d) * pb.inv_delta;
+        double dphi;
+        if (fabs(z) <= 1e-4) {
+            const double z2 = z * z;
+            const double tz = z * (1.0 - z2 * (1.0 / 3.0 - z2 * (2.0 / 15.0)));
+            const double td = pb.wall_tanh[wk];
+            // tanh(a + b) - tanh(a) = tz (1 - td^2) / (1 + td tz)
+            dphi = 0.5 * tz * (1.0 - td) * (1.0 + td) / (1.0 + td * tz);
+        } else {
+            dphi = phi_of(th, pb.inv_delta) - pb.wall_phi[wk];
+        }
+        const double m0t = theta_d - dphi * pb.inv_ste;
         double known = 0.0, wu = 0.0;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
@@ -192,13 +208,93 @@ struct TileSums {
     int liquid = 0, newton = 0, maxit = 0;
 };
 
-// One warp tile: segment `seg` of problem pb, rows [ya, yb).
+// ---------------------------------------------------------------- row ring
+// Each warp streams its rows through a ring of kStages row slots in shared
+// memory with cp.async (16-byte copies that bypass L1), so several rows are in
+// flight per warp without holding registers.  A slot holds one row of all nine
+// planes (32*N values each) plus the one element left and right of the
+// segment for the planes that are shifted along x.  Row y is computed from the
+// slots of rows y-1, y and y+1; the load of row y+kStages-1 is then issued into
+// the slot of row y-1.  Waits are cp.async.wait_group (no spinning).
+#ifndef LBM_RING_STAGES
+#define LBM_RING_STAGES 5
+#endif
+#ifndef LBM_STEP_MIN_BLOCKS
+#define LBM_STEP_MIN_BLOCKS 2
+#endif
+constexpr int kStages = LBM_RING_STAGES;
+
 template <typename P>
+struct Ring {
+    static constexpr int N = Vw<P>::N;
+    static constexpr int ROW = 32 * N;                  // values per plane row
+    static constexpr int HALO = 9 * ROW;                // offset of the halo values
+    static constexpr int SLOT = (9 * ROW + 18 + 3) / 4 * 4;   // values per slot, 16-byte multiple
+    static constexpr int WARP_BYTES = kStages * SLOT * (int)sizeof(P);
+};
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+template <int BYTES>
+__device__ __forceinline__ void cp_async_small(void* smem, const void* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int K>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory"); }
+
+// Issue the copies of row r (-1 .. ny) of all planes into `slot`.
+template <typename P>
+__device__ __forceinline__ void ring_load(P* slot, const P* src, long long pl, long long pitch, int r, int segx,
+                                          int lane, bool has_left, bool has_right)
+{
+    using R = Ring<P>;
+    const P* row = src + (long long)(r + 1) * pitch + segx;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) cp_async16(slot + i * R::ROW + lane * R::N, row + i * pl + lane * R::N);
+    if (lane == 0 && has_left) {
+        // planes shifted along +x (1, 5, 8) pull the element left of the segment
+        cp_async_small<sizeof(P)>(slot + R::HALO + 2 * 1, row + 1 * pl - 1);
+        cp_async_small<sizeof(P)>(slot + R::HALO + 2 * 5, row + 5 * pl - 1);
+        cp_async_small<sizeof(P)>(slot + R::HALO + 2 * 8, row + 8 * pl - 1);
+    }
+    if (lane == 31 && has_right) {
+        // planes shifted along -x (3, 6, 7) pull the element right of the segment
+        cp_async_small<sizeof(P)>(slot + R::HALO + 2 * 3 + 1, row + 3 * pl + R::ROW);
+        cp_async_small<sizeof(P)>(slot + R::HALO + 2 * 6 + 1, row + 6 * pl + R::ROW);
+        cp_async_small<sizeof(P)>(slot + R::HALO + 2 * 7 + 1, row + 7 * pl + R::ROW);
+    }
+}
+
+template <typename P>
+__device__ __forceinline__ void lds(const P* p, P (&v)[Vw<P>::N]);
+template <>
+__device__ __forceinline__ void lds<float>(const float* p, float (&v)[4])
+{
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+template <>
+__device__ __forceinline__ void lds<double>(const double* p, double (&v)[2])
+{
+    const double2 t = *reinterpret_cast<const double2*>(p);
+    v[0] = t.x; v[1] = t.y;
+}
+
+// One warp tile: segment `seg` of problem pb, rows [ya, yb).
+template <typename P, bool REC>
 __device__ __forceinline__ void d2q9_tile(const Problem& pb, const P* __restrict__ src, P* __restrict__ dst,
                                           double* __restrict__ rec, int seg, int ya, int yb, Acc<P>& acc,
-                                          TileSums& ts, DevStats* st)
+                                          TileSums& ts, DevStats* st, P* ring, int pi, NewtonJob* jobs,
+                                          unsigned int* job_count)
 {
-    constexpr int N = Vw<P>::N;
+    using R = Ring<P>;
+    constexpr int N = R::N;
     const int lane = threadIdx.x & 31;
     const int segx = seg * 32 * N;
     const int x0 = segx + lane * N;
@@ -208,59 +304,78 @@ __device__ __forceinline__ void d2q9_tile(const Problem& pb, const P* __restrict
     const bool has_right = segx + 32 * N < pb.nx;
     const P omc = (P)(1.0 - pb.omega);
     const P wP[3] = {(P)d2_w(0), (P)d2_w(1), (P)d2_w(5)};
-    const double thr = kSat * pb.delta;
-    const float thr_f = (float)thr;
+    const float thr_f = (float)pb.sat;
 
-    auto rp = [&](int i, int r) -> const P* { return src + i * pl + (long long)(r + 1) * pitch + x0; };
-    auto hl = [&](int i, int r) -> P {
-        return (lane == 0 && has_left) ? __ldg(src + i * pl + (long long)(r + 1) * pitch + segx - 1) : (P)0;
-    };
-    auto hr = [&](int i, int r) -> P {
-        return (lane == 31 && has_right) ? __ldg(src + i * pl + (long long)(r + 1) * pitch + segx + 32 * N) : (P)0;
-    };
-
-    P up2[N], up5[N], up6[N], cu4[N], cu7[N], cu8[N];
-    {
-        P t[N];
-        ldv<P>(rp(2, ya - 1), up2);
-        ldv<P>(rp(5, ya - 1), t);
-        from_left<P, N>(t, hl(5, ya - 1), lane, up5);
-        ldv<P>(rp(6, ya - 1), t);
-        from_right<P, N>(t, hr(6, ya - 1), lane, up6);
-        ldv<P>(rp(4, ya), cu4);
-        ldv<P>(rp(7, ya), cu7);
-        ldv<P>(rp(8, ya), cu8);
+    // prologue: rows ya-1 .. ya+kStages-2 (one per slot), one commit group per row.
+    // Iteration y then needs rows <= y+1 and leaves rows y+2 .. y+kStages-2 in
+    // flight (wait_group kStages-3); it refills the slot of row y-1 with row y+kStages-1.
+#pragma unroll
+    for (int s = 0; s < kStages; ++s) {
+        const int r = ya - 1 + s;
+        if (r <= yb) ring_load<P>(ring + ((r + 1) % kStages) * R::SLOT, src, pl, pitch, r, segx, lane, has_left, has_right);
+        cp_async_commit();
     }
 
     for (int y = ya; y < yb; ++y) {
-        P r0[N], r1[N], r3[N], c2[N], c5[N], c6[N], n4[N], n7[N], n8[N];
-        ldv<P>(rp(0, y), r0);
-        ldv<P>(rp(1, y), r1);
-        ldv<P>(rp(3, y), r3);
-        ldv<P>(rp(2, y), c2);
-        ldv<P>(rp(5, y), c5);
-        ldv<P>(rp(6, y), c6);
-        ldv<P>(rp(4, y + 1), n4);
-        ldv<P>(rp(7, y + 1), n7);
-        ldv<P>(rp(8, y + 1), n8);
-        const P h1 = hl(1, y), h3 = hr(3, y), h5 = hl(5, y), h6 = hr(6, y), h7 = hr(7, y + 1), h8 = hl(8, y + 1);
+        cp_async_wait<kStages - 3>();   // rows <= y+1 have landed (for this lane)
+        __syncwarp();                   // ... and for every lane of the warp
+        const P* sm1 = ring + ((y) % kStages) * R::SLOT;        // row y-1  (slot index (r+1) % S)
+        const P* s0 = ring + ((y + 1) % kStages) * R::SLOT;     // row y
+        const P* sp1 = ring + ((y + 2) % kStages) * R::SLOT;    // row y+1
 
-        P q1[N], q3[N], q7[N], q8[N];
-        from_left<P, N>(r1, h1, lane, q1);
-        from_right<P, N>(r3, h3, lane, q3);
-        from_right<P, N>(n7, h7, lane, q7);
-        from_left<P, N>(n8, h8, lane, q8);
+        P u0[N], u1[N], u2[N], u3[N], u4[N], u5[N], u6[N], u7[N], u8[N];
+        lds<P>(s0 + 0 * R::ROW + lane * N, u0);
+        lds<P>(s0 + 1 * R::ROW + lane * N, u1);
+        lds<P>(s0 + 2 * R::ROW + lane * N, u2);
+        lds<P>(s0 + 3 * R::ROW + lane * N, u3);
+        lds<P>(s0 + 4 * R::ROW + lane * N, u4);
+        lds<P>(s0 + 5 * R::ROW + lane * N, u5);
+        lds<P>(s0 + 6 * R::ROW + lane * N, u6);
+        lds<P>(s0 + 7 * R::ROW + lane * N, u7);
+        lds<P>(s0 + 8 * R::ROW + lane * N, u8);
+
+        P qf[9][N];
+        {
+            P t[N], s[N];
+#pragma unroll
+            for (int k = 0; k < N; ++k) qf[0][k] = u0[k];
+            from_left<P, N>(u1, s0[R::HALO + 2 * 1], lane, s);
+#pragma unroll
+            for (int k = 0; k < N; ++k) qf[1][k] = s[k];
+            from_right<P, N>(u3, s0[R::HALO + 2 * 3 + 1], lane, s);
+#pragma unroll
+            for (int k = 0; k < N; ++k) qf[3][k] = s[k];
+            lds<P>(sm1 + 2 * R::ROW + lane * N, t);
+#pragma unroll
+            for (int k = 0; k < N; ++k) qf[2][k] = t[k];
+            lds<P>(sm1 + 5 * R::ROW + lane * N, t);
+            from_left<P, N>(t, sm1[R::HALO + 2 * 5], lane, s);
+#pragma unroll
+            for (int k = 0; k < N; ++k) qf[5][k] = s[k];
+            lds<P>(sm1 + 6 * R::ROW + lane * N, t);
+            from_right<P, N>(t, sm1[R::HALO + 2 * 6 + 1], lane, s);
+#pragma unroll
+            for (int k = 0; k < N; ++k) qf[6][k] = s[k];
+            lds<P>(sp1 + 4 * R::ROW + lane * N, t);
+#pragma unroll
+            for (int k = 0; k < N; ++k) qf[4][k] = t[k];
+            lds<P>(sp1 + 7 * R::ROW + lane * N, t);
+            from_right<P, N>(t, sp1[R::HALO + 2 * 7 + 1], lane, s);
+#pragma unroll
+            for (int k = 0; k < N; ++k) qf[7][k] = s[k];
+            lds<P>(sp1 + 8 * R::ROW + lane * N, t);
+            from_left<P, N>(t, sp1[R::HALO + 2 * 8], lane, s);
+#pragma unroll
+            for (int k = 0; k < N; ++k) qf[8][k] = s[k];
+        }
 
         P c[N];          // per node: theta' - (1-omega) m0, rounded to P
-        P qf[9][N];      // pulled (and wall-filled) populations
-        double thn[N];   // theta' for the record plane
+        double thn[REC ? N : 1];
         bool newton_k[N];
         typename M0T<P>::T m0[N];
         bool any_wall = false;
 #pragma unroll
         for (int k = 0; k < N; ++k) {
-            qf[0][k] = r0[k]; qf[1][k] = q1[k]; qf[2][k] = up2[k]; qf[3][k] = q3[k]; qf[4][k] = n4[k];
-            qf[5][k] = up5[k]; qf[6][k] = up6[k]; qf[7][k] = q7[k]; qf[8][k] = q8[k];
             const int x = x0 + k;
             any_wall |= (x < pb.nx) && (x == 0 || x == pb.nx - 1 || y == 0 || y == pb.ny - 1);
         }
@@ -276,8 +391,8 @@ __device__ __forceinline__ void d2q9_tile(const Problem& pb, const P* __restrict
                     P qq[9], uu[9];
 #pragma unroll
                     for (int i = 0; i < 9; ++i) qq[i] = qf[i][k];
-                    uu[0] = r0[k]; uu[1] = r1[k]; uu[2] = c2[k]; uu[3] = r3[k]; uu[4] = cu4[k];
-                    uu[5] = c5[k]; uu[6] = c6[k]; uu[7] = cu7[k]; uu[8] = cu8[k];
+                    uu[0] = u0[k]; uu[1] = u1[k]; uu[2] = u2[k]; uu[3] = u3[k]; uu[4] = u4[k];
+                    uu[5] = u5[k]; uu[6] = u6[k]; uu[7] = u7[k]; uu[8] = u8[k];
                     ts.flux += wall_closure<P>(qq, uu, x, y, pb, dir_k[k], thd_k[k]);
 #pragma unroll
                     for (int i = 0; i < 9; ++i) qf[i][k] = qq[i];
@@ -294,7 +409,7 @@ __device__ __forceinline__ void d2q9_tile(const Problem& pb, const P* __restrict
             // small weights first
 #pragma unroll
             for (int i = 8; i >= 0; --i) m0_add(m0[k], qf[i][k]);
-            P u[9] = {r0[k], r1[k], c2[k], r3[k], cu4[k], c5[k], c6[k], cu7[k], cu8[k]};
+            const P u[9] = {u0[k], u1[k], u2[k], u3[k], u4[k], u5[k], u6[k], u7[k], u8[k]};
             const float tf = approx_sum<P>(u);
             const float mf = m0_f(m0[k]);
             const float marg = 1e-5f * (1.0f + fabsf(tf));
@@ -304,61 +419,85 @@ __device__ __forceinline__ void d2q9_tile(const Problem& pb, const P* __restrict
             any_newton |= newton_k[k];
             if (!valid) {
                 c[k] = (P)0;
-                thn[k] = 0.0;
+                if constexpr (REC) thn[k] = 0.0;
 #pragma unroll
                 for (int i = 0; i < 9; ++i) qf[i][k] = (P)0;
             } else if (dir_k[k]) {
                 const double md = m0_d(m0[k]);
                 const double td = thd_k[k];
                 c[k] = (P)(td - (1.0 - pb.omega) * md);
-                thn[k] = td;
+                if constexpr (REC) thn[k] = td;
                 acc.add_d(td);
-                ts.phi_sum += phi_of(td, pb.inv_delta);
+                // phi(theta_D) of this node's Dirichlet wall (first in W, E, S, N)
+                {
+                    const int x = x0 + k;
+                    const int walls = (x == 0 ? 1 : 0) | (x == pb.nx - 1 ? 2 : 0) | (y == 0 ? 4 : 0) | (y == pb.ny - 1 ? 8 : 0);
+                    int wk = 0;
+                    while (wk < 4 && !(((walls >> wk) & 1) && pb.wall_kind[wk] == 1)) ++wk;
+                    ts.phi_sum += pb.wall_phi[wk < 4 ? wk : 0];
+                }
             } else if (!newton_k[k]) {
                 // saturated: theta' = m0, no source; c = omega * m0
                 if constexpr (sizeof(P) == 4) {
                     const ff& mm = m0[k];
                     c[k] = (P)__fmaf_rn((float)pb.omega, mm.hi, (float)pb.omega * mm.lo);
                     acc.add_ff(mm);
-                    thn[k] = rec ? ff_to_double(mm) : 0.0;
+                    if constexpr (REC) thn[k] = ff_to_double(mm);
                 } else {
                     const double md = m0_d(m0[k]);
                     c[k] = (P)(pb.omega * md);
                     acc.add_d(md);
-                    thn[k] = md;
+                    if constexpr (REC) thn[k] = md;
                 }
                 ts.liquid += sat_liq ? 1 : 0;
             }
         }
         if (__any_sync(kFull, any_newton)) {
+            // The local Newton solve of these nodes is deferred to the job kernel,
+            // which spreads the FP64 work of the front band over the whole GPU:
+            // append (m0, theta) to the job list and store q_i unrelaxed.
+            int cnt = 0;
+#pragma unroll
+            for (int k = 0; k < N; ++k) cnt += newton_k[k] ? 1 : 0;
+            int incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const int total = __shfl_sync(kFull, incl, 31);
+            unsigned base = 0;
+            if (lane == 0) base = atomicAdd(job_count, (unsigned)total);
+            base = __shfl_sync(kFull, base, 0);
+            unsigned slot = base + (unsigned)(incl - cnt);
 #pragma unroll
             for (int k = 0; k < N; ++k) {
                 if (!newton_k[k]) continue;
-                double th = 0.0;
+                const P u[9] = {u0[k], u1[k], u2[k], u3[k], u4[k], u5[k], u6[k], u7[k], u8[k]};
+                NewtonJob jb;
+                jb.prob = pi;
+                jb.node = y * pb.nx + x0 + k;
                 if constexpr (sizeof(P) == 4) {
                     ff t;
                     m0_init(t);
-                    const P u[9] = {r0[k], r1[k], c2[k], r3[k], cu4[k], c5[k], c6[k], cu7[k], cu8[k]};
 #pragma unroll
                     for (int i = 8; i >= 0; --i) ff_add(t, u[i]);
-                    th = ff_to_double(t);
+                    const ff& mm = m0[k];
+                    float* pm = reinterpret_cast<float*>(&jb.m0);
+                    float* pt = reinterpret_cast<float*>(&jb.theta);
+                    pm[0] = mm.hi; pm[1] = mm.lo;
+                    pt[0] = t.hi; pt[1] = t.lo;
                 } else {
-                    const P u[9] = {r0[k], r1[k], c2[k], r3[k], cu4[k], c5[k], c6[k], cu7[k], cu8[k]};
+                    double th = 0.0;
 #pragma unroll
                     for (int i = 8; i >= 0; --i) th += u[i];
+                    jb.m0 = m0_d(m0[k]);
+                    jb.theta = th;
                 }
-                const double md = m0_d(m0[k]);
-                const double pth = phi_of(th, pb.inv_delta);
-                NewtonOut nr = newton_solve(md, th, pth, pb.inv_ste, pb.inv_delta, pb.tol, pb.maxit);
-                if (!nr.ok || !isfinite(nr.root)) atomicOr(&st->error, 3);
-                // theta' = M0(f~) = m0 + (phi(theta) - phi(theta'))/Ste  (Eq. 13 summed over i)
-                const double tn = md + (pth - nr.phi_root) * pb.inv_ste;
-                c[k] = (P)(tn - (1.0 - pb.omega) * md);
-                thn[k] = tn;
-                acc.add_d(tn);
-                ts.phi_sum += nr.phi_root;
-                ts.newton += 1;
-                ts.maxit = max(ts.maxit, nr.iters);
+                jobs[slot] = jb;
+                ++slot;
+                c[k] = (P)0;
+                if constexpr (REC) thn[k] = 0.0;
             }
         }
 
@@ -369,33 +508,39 @@ __device__ __forceinline__ void d2q9_tile(const Problem& pb, const P* __restrict
             const P wi = i == 0 ? wP[0] : (i <= 4 ? wP[1] : wP[2]);
             P o[N];
 #pragma unroll
-            for (int k = 0; k < N; ++k) o[k] = fma(omc, qf[i][k], wi * c[k]);
+            for (int k = 0; k < N; ++k) o[k] = newton_k[k] ? qf[i][k] : fma(omc, qf[i][k], wi * c[k]);
             stv<P>(drow + i * pl, o);
         }
-        if (rec) {
+        if constexpr (REC) {
             double* rr = rec + (long long)y * pitch + x0;
 #pragma unroll
             for (int k = 0; k < N; k += 2) *reinterpret_cast<double2*>(rr + k) = make_double2(thn[k], thn[k + 1]);
         }
 
-        // roll the register window
-#pragma unroll
-        for (int k = 0; k < N; ++k) { up2[k] = c2[k]; cu4[k] = n4[k]; cu7[k] = n7[k]; cu8[k] = n8[k]; }
-        from_left<P, N>(c5, h5, lane, up5);
-        from_right<P, N>(c6, h6, lane, up6);
+        // the slot of row y-1 is free once every lane has read it
+        __syncwarp();
+        const int rn = y + kStages - 1;
+        if (rn <= yb) ring_load<P>(ring + ((rn + 1) % kStages) * R::SLOT, src, pl, pitch, rn, segx, lane, has_left, has_right);
+        cp_async_commit();
     }
+    cp_async_wait<0>();
+    __syncwarp();
 }
 
-template <typename P>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) d2q9_step_kernel(StepArgs a)
+template <typename P, bool REC>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, LBM_STEP_MIN_BLOCKS) d2q9_step_kernel(StepArgs a)
 {
+    extern __shared__ __align__(16) unsigned char smem[];
+    using R = Ring<P>;
+    const int wib = threadIdx.x >> 5;
+    P* ring = reinterpret_cast<P*>(smem + wib * R::WARP_BYTES);
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const int lane = threadIdx.x & 31;
     for (int slot = warp; slot < a.nslots; slot += nwarps) {
         int pi, t;
         if (a.schedule) {
-            int2 s = a.schedule[slot];
+            const int2 s = a.schedule[slot];
             pi = s.x;
             t = s.y;
         } else {
@@ -412,12 +557,12 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) d2q9_step_kernel(StepArgs
         P* dst = static_cast<P*>(pb.state[a.parity ^ 1]);
         Acc<P> acc;
         TileSums ts;
-        d2q9_tile<P>(pb, src, dst, a.rec, seg, ya, yb, acc, ts, st);
+        d2q9_tile<P, REC>(pb, src, dst, a.rec, seg, ya, yb, acc, ts, st, ring, pi, a.jobs, a.job_count);
         // tile partial sums: fixed lane order, then one fixed-point atomic per quantity
-        double e = warp_sum(acc.get() + ((double)ts.liquid + ts.phi_sum) * pb.inv_ste);
-        double f = warp_sum(ts.flux);
-        int nn = warp_sum_i(ts.newton);
-        int mi = warp_max_i(ts.maxit);
+        const double e = warp_sum(acc.get() + ((double)ts.liquid + ts.phi_sum) * pb.inv_ste);
+        const double f = warp_sum(ts.flux);
+        const int nn = warp_sum_i(ts.newton);
+        const int mi = warp_max_i(ts.maxit);
         if (lane == 0) {
             acc_add(&st->cur_energy, e);
             acc_add(&st->cur_flux, f);
@@ -425,7 +570,119 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) d2q9_step_kernel(StepArgs
             if (mi) atomicMax(&st->cur_maxit, mi);
         }
     }
-    finish_launch(a.stats, a.nprob, a.ticket);
+    // statistics are published by the job kernel that follows every step
+}
+
+// ---------------------------------------------------------------- Newton jobs
+// Local Newton solves deferred by the step kernel (Eq. 14, mixed-precision
+// form), one job per lane, consecutive jobs per warp.  For each job:
+//   theta' = m0 + (phi(theta) - phi(root))/Ste,  c = theta' - (1-omega) m0,
+//   Omega~_i = (1-omega) q_i + w_i c   (q_i was stored by the step kernel).
+// Energy contributions theta' + phi(theta')/Ste are summed per problem as
+// exact 128-bit fixed-point integers (independent of the job order).  The last
+// warp to finish publishes the step statistics and clears the job list.
+template <typename P, bool REC>
+__global__ void __launch_bounds__(128) newton_jobs_kernel(JobArgs a)
+{
+    const unsigned count = *reinterpret_cast<volatile unsigned*>(a.job_count);
+    const int lane = threadIdx.x & 31;
+    const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned nw = (gridDim.x * blockDim.x) >> 5;
+    for (unsigned base = gw * 32; base < count; base += nw * 32) {
+        const unsigned j = base + lane;
+        int sidx = -1, it = 0;
+        Fx e{0, 0ull};
+        if (j < count) {
+            const NewtonJob jb = a.jobs[j];
+            const Problem& pb = a.probs[jb.prob];
+            sidx = pb.stats;
+            double m0, th;
+            if constexpr (sizeof(P) == 4) {
+                const float* pm = reinterpret_cast<const float*>(&jb.m0);
+                const float* pt = reinterpret_cast<const float*>(&jb.theta);
+                m0 = (double)pm[0] + (double)pm[1];
+                th = (double)pt[0] + (double)pt[1];
+            } else {
+                m0 = jb.m0;
+                th = jb.theta;
+            }
+            const double pth = phi_of(th, pb.inv_delta);
+            const NewtonOut nr = newton_mixed(m0, th, pth, pb.inv_ste, pb.inv_delta, pb.tol, pb.maxit);
+            if (!nr.ok || !isfinite(nr.root)) atomicOr(&a.stats[sidx].error, 3);
+            const double tn = m0 + (pth - nr.phi_root) * pb.inv_ste;
+            const P c = (P)(tn - (1.0 - pb.omega) * m0);
+            const P omc = (P)(1.0 - pb.omega);
+            const int x = jb.node % pb.nx, y = jb.node / pb.nx;
+            P* d = static_cast<P*>(pb.state[a.parity ^ 1]) + (long long)(y + 1) * pb.pitch + x;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const P wi = (P)d2_w(i);
+                d[i * pb.plane] = fma(omc, d[i * pb.plane], wi * c);
+            }
+            if (REC) a.rec[(long long)y * pb.pitch + x] = tn;
+            e = to_fixed(tn + nr.phi_root * pb.inv_ste);
+            it = nr.iters;
+        }
+        // lanes of the same problem: the lowest lane sums them exactly and adds once
+        const unsigned grp = __match_any_sync(kFull, sidx);
+        const int leader = __ffs(grp) - 1;
+        Fx sum{0, 0ull};
+        int n = 0, mx = 0;
+        for (int l = 0; l < 32; ++l) {
+            Fx v;
+            v.hi = __shfl_sync(kFull, e.hi, l);
+            v.lo = __shfl_sync(kFull, e.lo, l);
+            const int vi = __shfl_sync(kFull, it, l);
+            if ((grp >> l) & 1) {
+                fx_add(sum, v);
+                ++n;
+                mx = max(mx, vi);
+            }
+        }
+        if (lane == leader && sidx >= 0) {
+            DevStats* st = &a.stats[sidx];
+            acc_add_fx(&st->cur_energy, sum);
+            atomicAdd(&st->cur_newton, (unsigned long long)n);
+            atomicMax(&st->cur_maxit, mx);
+        }
+    }
+    // last warp: publish every problem's step statistics, clear the job list
+    unsigned t = 0;
+    if (lane == 0) {
+        __threadfence();
+        t = atomicAdd(a.ticket, 1u);
+    }
+    t = __shfl_sync(kFull, t, 0);
+    if (t == nw - 1) {
+        __threadfence();
+        for (int p = lane; p < a.nprob; p += 32) publish_stats(&a.stats[p]);
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) {
+            *a.job_count = 0u;
+            *a.ticket = 0u;
+        }
+    }
+}
+
+template <typename P>
+constexpr int step_smem_bytes()
+{
+    return kWarpsPerBlock * Ring<P>::WARP_BYTES;
+}
+
+template <typename P, bool REC>
+static cudaError_t launch_t(const StepArgs& a, int grid, cudaStream_t s)
+{
+    constexpr int sm = step_smem_bytes<P>();
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(d2q9_step_kernel<P, REC>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    d2q9_step_kernel<P, REC><<<grid, kWarpsPerBlock * 32, sm, s>>>(a);
+    return cudaGetLastError();
 }
 
 int d2q9_segment_width(int precision) { return precision == 1 ? 32 * 4 : 32 * 2; }
@@ -433,9 +690,41 @@ int d2q9_segment_width(int precision) { return precision == 1 ? 32 * 4 : 32 * 2;
 cudaError_t launch_d2q9_step(int precision, const StepArgs& a, int grid, cudaStream_t s)
 {
     if (grid <= 0) return cudaErrorInvalidValue;
-    if (precision == 1) d2q9_step_kernel<float><<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
-    else d2q9_step_kernel<double><<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
+    if (precision == 1) return a.rec ? launch_t<float, true>(a, grid, s) : launch_t<float, false>(a, grid, s);
+    return a.rec ? launch_t<double, true>(a, grid, s) : launch_t<double, false>(a, grid, s);
+}
+
+cudaError_t launch_newton_jobs(int precision, const JobArgs& a, cudaStream_t s)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = sms * 8;
+    if (precision == 1) {
+        if (a.rec) newton_jobs_kernel<float, true><<<grid, 128, 0, s>>>(a);
+        else newton_jobs_kernel<float, false><<<grid, 128, 0, s>>>(a);
+    } else {
+        if (a.rec) newton_jobs_kernel<double, true><<<grid, 128, 0, s>>>(a);
+        else newton_jobs_kernel<double, false><<<grid, 128, 0, s>>>(a);
+    }
     return cudaGetLastError();
+}
+
+int d2q9_blocks_per_sm(int precision)
+{
+    int n = 0;
+    if (precision == 1) {
+        cudaFuncSetAttribute(d2q9_step_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             step_smem_bytes<float>());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, d2q9_step_kernel<float, false>, kWarpsPerBlock * 32,
+                                                      step_smem_bytes<float>());
+    } else {
+        cudaFuncSetAttribute(d2q9_step_kernel<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             step_smem_bytes<double>());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, d2q9_step_kernel<double, false>, kWarpsPerBlock * 32,
+                                                      step_smem_bytes<double>());
+    }
+    return n > 0 ? n : 1;
 }
 
 }  // namespace lbm

@@ -164,7 +164,8 @@ def test_link_bounce_back_conserves_energy_gpu(gpu):
     S.step(500)
     st = S.stats()
     assert abs(st["energy"] - e0) < 1e-11 * abs(e0)
-    assert st["imbalance_max"] < 1e-10
+    # per step, each node's theta' + phi/Ste carries a few ulps of (|theta| + 1/Ste)
+    assert st["imbalance_max"] < 8 * 200 * 120 * 2.2e-16 * (1 + 1 / c.ste)
     S.close()
 
 
