@@ -44,9 +44,14 @@ __global__ void wall_constants_kernel(Problem* probs, int nprob)
     if (p >= nprob) return;
     Problem& pb = probs[p];
     for (int k = 0; k < 4; ++k) {
-        pb.wall_tanh[k] = tanh(pb.wall_theta[k] * pb.inv_delta);
-        pb.wall_phi[k] = 0.5 + 0.5 * pb.wall_tanh[k];
+        const double t = tanh(pb.wall_theta[k] * pb.inv_delta);
+        pb.wall_tanh[k] = t;
+        pb.wall_phi[k] = 0.5 + 0.5 * t;
+        pb.wall_th_hi[k] = (float)pb.wall_theta[k];
+        pb.wall_th_lo[k] = (float)(pb.wall_theta[k] - (double)pb.wall_th_hi[k]);
+        pb.wall_slope[k] = (float)(0.5 * (1.0 - t) * (1.0 + t) * pb.inv_delta * pb.inv_ste);
     }
+    pb.wall_dth_max = (float)(1e-4 * pb.delta);
 }
 
 cudaError_t launch_wall_constants(Problem* dprobs, int nprob, cudaStream_t s)

@@ -54,6 +54,10 @@ struct Problem {
     double wall_theta[4];
     double wall_tanh[4];     // tanh(theta_wall / delta), set on the device (wall_constants)
     double wall_phi[4];      // phi(theta_wall)
+    float wall_th_hi[4];     // theta_wall as a float-float pair
+    float wall_th_lo[4];
+    float wall_slope[4];     // phi'(theta_wall)/Ste = (1 - tanh^2)/(2 delta Ste)
+    float wall_dth_max;      // 1e-4 delta: range of the linear phi difference at a Dirichlet node
     int nseg, nstrip, tile_h;
     int tile0;               // first global tile index of this problem
     int ntiles;

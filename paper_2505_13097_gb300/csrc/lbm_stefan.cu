@@ -9,6 +9,10 @@
 #include "../../include/lbm_stefan.h"
 #include "lbm_internal.h"
 
+#ifndef LBM_PLANE_PAD
+#define LBM_PLANE_PAD 0
+#endif
+
 using lbm::DevStats;
 using lbm::Problem;
 using lbm::StepArgs;
@@ -124,7 +128,9 @@ static void fill_problem(Problem& pb, int q, int nx, int ny, int pitch, double t
     pb.ny = ny;
     pb.q = q;
     pb.pitch = pitch;
-    pb.plane = (long long)(ny + 2) * pitch;
+    // planes one stride apart (+ LBM_PLANE_PAD elements) so that the nine
+    // streams of a step do not fall on the same memory partitions
+    pb.plane = (long long)(ny + 2) * pitch + LBM_PLANE_PAD;
     pb.omega = 1.0 / tau;
     pb.ste = ste;
     pb.inv_ste = 1.0 / ste;
@@ -185,6 +191,7 @@ static cudaError_t launch_one(lbm_stefan* h, int parity, double* rec)
 {
     StepArgs a = single_args(h, parity, rec);
     if (h->p.lattice == LBM_D2Q9) {
+        // one tile per warp; the hardware scheduler balances the short tiles
         const int grid = (h->hp.ntiles + lbm::kWarpsPerBlock - 1) / lbm::kWarpsPerBlock;
         cudaError_t e = lbm::launch_d2q9_step(h->precision, a, grid, h->stream);
         if (e != cudaSuccess) return e;

@@ -83,75 +83,139 @@ __device__ __forceinline__ void from_right(const P (&v)[N], P h, int lane, P (&s
 // Boundary closures of Sec. 4.2 at one wall node (x, y).  q holds the pulled
 // values (entries of unknown directions are overwritten), u the node's own
 // Omega.  Returns the boundary flux contribution (filled q minus Omega that
-// leaves the lattice); dir/theta_d report a Dirichlet node.
-template <typename P>
-__device__ __noinline__ double wall_closure(P* q, const P* u, int x, int y, const Problem& pb, bool& dir, double& theta_d)
+// leaves the lattice) as a float-float pair; wall reports the node's Dirichlet
+// wall (first in W, E, S, N) or -1.
+struct WallInfo {
+    unsigned unk;   // bit i: q_i not defined by streaming
+    int wall;       // Dirichlet wall index, -1 for bounce-back
+};
+
+__device__ __forceinline__ WallInfo wall_info(int x, int y, const Problem& pb)
 {
-    unsigned unk = 0;
+    WallInfo w;
+    w.unk = 0;
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
-        int sx = x - d2_ex(i), sy = y - d2_ey(i);
-        if (sx < 0 || sx >= pb.nx || sy < 0 || sy >= pb.ny) unk |= 1u << i;
+        const int sx = x - d2_ex(i), sy = y - d2_ey(i);
+        if (sx < 0 || sx >= pb.nx || sy < 0 || sy >= pb.ny) w.unk |= 1u << i;
     }
-    int walls = (x == 0 ? 1 : 0) | (x == pb.nx - 1 ? 2 : 0) | (y == 0 ? 4 : 0) | (y == pb.ny - 1 ? 8 : 0);
-    dir = false;
-    theta_d = 0.0;
-    int wk = -1;
+    const int walls = (x == 0 ? 1 : 0) | (x == pb.nx - 1 ? 2 : 0) | (y == 0 ? 4 : 0) | (y == pb.ny - 1 ? 8 : 0);
+    w.wall = -1;
     for (int k = 0; k < 4; ++k)
         if (((walls >> k) & 1) && pb.wall_kind[k] == 1) {
-            dir = true;
-            theta_d = pb.wall_theta[k];
-            wk = k;
+            w.wall = k;
             break;
         }
+    return w;
+}
+
+// FP64 form: the closure in FP64.
+__device__ __noinline__ double wall_closure_d(double* q, const double* u, int x, int y, const Problem& pb, int& wall)
+{
+    const WallInfo wi = wall_info(x, y, pb);
+    wall = wi.wall;
     double out = 0.0, in = 0.0;
 #pragma unroll
     for (int j = 1; j < 9; ++j)
-        if ((unk >> d2_opp(j)) & 1) out += (double)u[j];
-    if (dir) {
+        if ((wi.unk >> d2_opp(j)) & 1) out += u[j];
+    if (wi.wall >= 0) {
         // Eq. (14) with theta' = theta_D fixes M0(q) = theta_D + (phi(theta_D) - phi(theta))/Ste;
-        // the unknown q share what the known ones leave, in proportion to w_i.
+        // the unknown q share what the known ones leave, in proportion to w_i
         double th = 0.0;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) th += (double)u[i];
-        // phi(theta) - phi(theta_D): the wall node stays within rounding of theta_D, so the
-        // tanh addition theorem with tanh(d/delta) = z - z^3/3 + 2z^5/15 (|z| <= 1e-4,
-        // remainder < 1e-29) replaces a full tanh; the general case falls back to tanh
+        for (int i = 0; i < 9; ++i) th += u[i];
+        const double theta_d = pb.wall_theta[wi.wall];
+        // the wall node stays within rounding of theta_D: tanh addition theorem with
+        // tanh(z) = z - z^3/3 + 2z^5/15 for |z| <= 1e-4 (remainder < 1e-29), else tanh
         const double z = (th - theta_d) * pb.inv_delta;
         double dphi;
         if (fabs(z) <= 1e-4) {
             const double z2 = z * z;
             const double tz = z * (1.0 - z2 * (1.0 / 3.0 - z2 * (2.0 / 15.0)));
-            const double td = pb.wall_tanh[wk];
-            // tanh(a + b) - tanh(a) = tz (1 - td^2) / (1 + td tz)
-            dphi = 0.5 * tz * (1.0 - td) * (1.0 + td) / (1.0 + td * tz);
+            const double td = pb.wall_tanh[wi.wall];
+            dphi = 0.5 * tz * (1.0 - td) * (1.0 + td) / (1.0 + td * tz);   // phi(theta) - phi(theta_D)
         } else {
-            dphi = phi_of(th, pb.inv_delta) - pb.wall_phi[wk];
+            dphi = phi_of(th, pb.inv_delta) - pb.wall_phi[wi.wall];
         }
         const double m0t = theta_d - dphi * pb.inv_ste;
         double known = 0.0, wu = 0.0;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            if ((unk >> i) & 1) wu += d2_w(i);
-            else known += (double)q[i];
+            if ((wi.unk >> i) & 1) wu += d2_w(i);
+            else known += q[i];
         }
-        double r = (m0t - known) / wu;
+        const double r = (m0t - known) / wu;
 #pragma unroll
         for (int i = 1; i < 9; ++i)
-            if ((unk >> i) & 1) {
-                q[i] = (P)(d2_w(i) * r);
-                in += (double)q[i];
+            if ((wi.unk >> i) & 1) {
+                q[i] = d2_w(i) * r;
+                in += q[i];
             }
     } else {
 #pragma unroll
         for (int i = 1; i < 9; ++i)
-            if ((unk >> i) & 1) {
-                int o = d2_opp(i);
-                q[i] = (pb.bb_mode == 0 && !((unk >> o) & 1)) ? q[o] : u[o];
-                in += (double)q[i];
+            if ((wi.unk >> i) & 1) {
+                const int o = d2_opp(i);
+                q[i] = (pb.bb_mode == 0 && !((wi.unk >> o) & 1)) ? q[o] : u[o];
+                in += q[i];
             }
     }
     return in - out;
+}
+
+// FP32 form: the same closure with float-float sums and no FP64 instruction on
+// the common path.  phi(theta) - phi(theta_D) = phi'(theta_D)(theta - theta_D)
+// + O((theta - theta_D)^2/delta^2): the node stays within rounding of theta_D,
+// so the second-order term is below 1e-8 of FP32 resolution whenever
+// |theta - theta_D| <= 1e-4 delta; otherwise the FP64 expression is used.
+__device__ __noinline__ ff wall_closure_f(float* q, const float* u, int x, int y, const Problem& pb, int& wall)
+{
+    const WallInfo wi = wall_info(x, y, pb);
+    wall = wi.wall;
+    ff out{0.f, 0.f}, in{0.f, 0.f};
+#pragma unroll
+    for (int j = 1; j < 9; ++j)
+        if ((wi.unk >> d2_opp(j)) & 1) ff_add(out, u[j]);
+    if (wi.wall >= 0) {
+        const int k = wi.wall;
+        ff th{0.f, 0.f}, known{0.f, 0.f};
+        float wu = 0.f;
+#pragma unroll
+        for (int i = 8; i >= 0; --i) {
+            ff_add(th, u[i]);
+            if ((wi.unk >> i) & 1) wu += (float)d2_w(i);
+            else ff_add(known, q[i]);
+        }
+        // m0t = theta_D - (phi(theta) - phi(theta_D))/Ste
+        const float dth = (th.hi - pb.wall_th_hi[k]) + (th.lo - pb.wall_th_lo[k]);
+        ff m0t{pb.wall_th_hi[k], pb.wall_th_lo[k]};
+        if (fabsf(dth) <= pb.wall_dth_max) {
+            ff_add(m0t, -pb.wall_slope[k] * dth);
+        } else {
+            const double dphi = phi_of(ff_to_double(th), pb.inv_delta) - pb.wall_phi[k];
+            ff_add(m0t, (float)(-dphi * pb.inv_ste));
+        }
+        // R = m0t - sum(known), shared by the unknown q in proportion to w_i
+        const float r = ((m0t.hi - known.hi) + (m0t.lo - known.lo)) / wu;
+#pragma unroll
+        for (int i = 1; i < 9; ++i)
+            if ((wi.unk >> i) & 1) {
+                q[i] = (float)d2_w(i) * r;
+                ff_add(in, q[i]);
+            }
+    } else {
+#pragma unroll
+        for (int i = 1; i < 9; ++i)
+            if ((wi.unk >> i) & 1) {
+                const int o = d2_opp(i);
+                q[i] = (pb.bb_mode == 0 && !((wi.unk >> o) & 1)) ? q[o] : u[o];
+                ff_add(in, q[i]);
+            }
+    }
+    ff f{in.hi, in.lo};
+    ff_add(f, -out.hi);
+    f.lo -= out.lo;
+    return f;
 }
 
 template <typename P>
@@ -204,7 +268,9 @@ __device__ __forceinline__ float approx_sum<double>(const double* u)
 }
 
 struct TileSums {
-    double flux = 0.0, phi_sum = 0.0;
+    double flux = 0.0, phi_sum = 0.0;   // FP64 form
+    ff flux_f{0.f, 0.f};                // FP32 form
+    int dir_count[4] = {0, 0, 0, 0};   // Dirichlet nodes per wall (adds phi(theta_D)/Ste each)
     int liquid = 0, newton = 0, maxit = 0;
 };
 
@@ -302,7 +368,14 @@ __device__ __forceinline__ void d2q9_tile(const Problem& pb, const P* __restrict
     const long long pitch = pb.pitch;
     const bool has_left = segx > 0;
     const bool has_right = segx + 32 * N < pb.nx;
+    // problem constants, converted once per tile (the compiler cannot hoist loads
+    // of *pb above the stores of the loop, and a conversion from FP64 costs an
+    // FP64-pipe instruction on this GPU)
     const P omc = (P)(1.0 - pb.omega);
+    const float om_f = (float)pb.omega;
+    const double omc_d = 1.0 - pb.omega;
+    const double inv_delta = pb.inv_delta;
+    const int nx = pb.nx, ny = pb.ny;
     const P wP[3] = {(P)d2_w(0), (P)d2_w(1), (P)d2_w(5)};
     const float thr_f = (float)pb.sat;
 
@@ -377,23 +450,30 @@ __device__ __forceinline__ void d2q9_tile(const Problem& pb, const P* __restrict
 #pragma unroll
         for (int k = 0; k < N; ++k) {
             const int x = x0 + k;
-            any_wall |= (x < pb.nx) && (x == 0 || x == pb.nx - 1 || y == 0 || y == pb.ny - 1);
+            any_wall |= (x < nx) && (x == 0 || x == nx - 1 || y == 0 || y == ny - 1);
         }
         bool dir_k[N];
-        double thd_k[N];
+        int wall_k[N];
 #pragma unroll
-        for (int k = 0; k < N; ++k) { dir_k[k] = false; thd_k[k] = 0.0; }
+        for (int k = 0; k < N; ++k) { dir_k[k] = false; wall_k[k] = -1; }
         if (__any_sync(kFull, any_wall)) {
 #pragma unroll
             for (int k = 0; k < N; ++k) {
                 const int x = x0 + k;
-                if (x < pb.nx && (x == 0 || x == pb.nx - 1 || y == 0 || y == pb.ny - 1)) {
+                if (x < nx && (x == 0 || x == nx - 1 || y == 0 || y == ny - 1)) {
                     P qq[9], uu[9];
 #pragma unroll
                     for (int i = 0; i < 9; ++i) qq[i] = qf[i][k];
                     uu[0] = u0[k]; uu[1] = u1[k]; uu[2] = u2[k]; uu[3] = u3[k]; uu[4] = u4[k];
                     uu[5] = u5[k]; uu[6] = u6[k]; uu[7] = u7[k]; uu[8] = u8[k];
-                    ts.flux += wall_closure<P>(qq, uu, x, y, pb, dir_k[k], thd_k[k]);
+                    if constexpr (sizeof(P) == 4) {
+                        const ff fl = wall_closure_f(qq, uu, x, y, pb, wall_k[k]);
+                        ff_add(ts.flux_f, fl.hi);
+                        ts.flux_f.lo += fl.lo;
+                    } else {
+                        ts.flux += wall_closure_d(qq, uu, x, y, pb, wall_k[k]);
+                    }
+                    dir_k[k] = wall_k[k] >= 0;
 #pragma unroll
                     for (int i = 0; i < 9; ++i) qf[i][k] = qq[i];
                 }
@@ -404,7 +484,7 @@ __device__ __forceinline__ void d2q9_tile(const Problem& pb, const P* __restrict
 #pragma unroll
         for (int k = 0; k < N; ++k) {
             const int x = x0 + k;
-            const bool valid = x < pb.nx;
+            const bool valid = x < nx;
             m0_init(m0[k]);
             // small weights first
 #pragma unroll
@@ -423,24 +503,24 @@ __device__ __forceinline__ void d2q9_tile(const Problem& pb, const P* __restrict
 #pragma unroll
                 for (int i = 0; i < 9; ++i) qf[i][k] = (P)0;
             } else if (dir_k[k]) {
-                const double md = m0_d(m0[k]);
-                const double td = thd_k[k];
-                c[k] = (P)(td - (1.0 - pb.omega) * md);
-                if constexpr (REC) thn[k] = td;
-                acc.add_d(td);
-                // phi(theta_D) of this node's Dirichlet wall (first in W, E, S, N)
-                {
-                    const int x = x0 + k;
-                    const int walls = (x == 0 ? 1 : 0) | (x == pb.nx - 1 ? 2 : 0) | (y == 0 ? 4 : 0) | (y == pb.ny - 1 ? 8 : 0);
-                    int wk = 0;
-                    while (wk < 4 && !(((walls >> wk) & 1) && pb.wall_kind[wk] == 1)) ++wk;
-                    ts.phi_sum += pb.wall_phi[wk < 4 ? wk : 0];
+                // theta' = theta_D; c = theta_D - (1-omega) m0
+                const int wk = wall_k[k];
+                ts.dir_count[wk] += 1;
+                if constexpr (sizeof(P) == 4) {
+                    const ff& mm = m0[k];
+                    const float oc = (float)omc;
+                    c[k] = (P)((pb.wall_th_hi[wk] - oc * mm.hi) + (pb.wall_th_lo[wk] - oc * mm.lo));
+                    acc.add_ff(ff{pb.wall_th_hi[wk], pb.wall_th_lo[wk]});
+                } else {
+                    c[k] = (P)(pb.wall_theta[wk] - omc_d * m0_d(m0[k]));
+                    acc.add_d(pb.wall_theta[wk]);
                 }
+                if constexpr (REC) thn[k] = pb.wall_theta[wk];
             } else if (!newton_k[k]) {
                 // saturated: theta' = m0, no source; c = omega * m0
                 if constexpr (sizeof(P) == 4) {
                     const ff& mm = m0[k];
-                    c[k] = (P)__fmaf_rn((float)pb.omega, mm.hi, (float)pb.omega * mm.lo);
+                    c[k] = (P)__fmaf_rn(om_f, mm.hi, om_f * mm.lo);
                     acc.add_ff(mm);
                     if constexpr (REC) thn[k] = ff_to_double(mm);
                 } else {
@@ -476,7 +556,7 @@ __device__ __forceinline__ void d2q9_tile(const Problem& pb, const P* __restrict
                 const P u[9] = {u0[k], u1[k], u2[k], u3[k], u4[k], u5[k], u6[k], u7[k], u8[k]};
                 NewtonJob jb;
                 jb.prob = pi;
-                jb.node = y * pb.nx + x0 + k;
+                jb.node = y * nx + x0 + k;
                 if constexpr (sizeof(P) == 4) {
                     ff t;
                     m0_init(t);
@@ -559,8 +639,12 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, LBM_STEP_MIN_BLOCKS) d2q9
         TileSums ts;
         d2q9_tile<P, REC>(pb, src, dst, a.rec, seg, ya, yb, acc, ts, st, ring, pi, a.jobs, a.job_count);
         // tile partial sums: fixed lane order, then one fixed-point atomic per quantity
-        const double e = warp_sum(acc.get() + ((double)ts.liquid + ts.phi_sum) * pb.inv_ste);
-        const double f = warp_sum(ts.flux);
+        double dsum = 0.0;
+#pragma unroll
+        for (int w = 0; w < 4; ++w)
+            if (ts.dir_count[w]) dsum += ts.dir_count[w] * pb.wall_phi[w];
+        const double e = warp_sum(acc.get() + ((double)ts.liquid + ts.phi_sum + dsum) * pb.inv_ste);
+        const double f = warp_sum(sizeof(P) == 4 ? ff_to_double(ts.flux_f) : ts.flux);
         const int nn = warp_sum_i(ts.newton);
         const int mi = warp_max_i(ts.maxit);
         if (lane == 0) {
