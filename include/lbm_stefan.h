@@ -186,6 +186,35 @@ lbm_status lbm_stefan_batch_autotune(lbm_stefan_batch* b, int trial_steps, int* 
 lbm_status lbm_stefan_batch_set_schedule(lbm_stefan_batch* b, int tile_h, int schedule);
 void lbm_stefan_batch_destroy(lbm_stefan_batch* b);
 
+/* ---------------------------------------------------------------- one step without allocation
+ * The paper has no counterpart to this entry point: it exists for callers that
+ * cannot allocate device memory when they step (code running under an
+ * allocator or memory budget it does not own, pre-sized real-time loops that
+ * must not call cudaMalloc, hosts whose GPU memory is handed out up front).
+ *
+ * One D2Q9 step, state_in -> state_out, computing what lbm_stefan_step does for
+ * one step of a problem created with the same parameters and walls.  It
+ * allocates nothing: the scratch of the step (problem descriptor, statistics,
+ * counters, the list of nodes whose Newton solve is deferred) lives in one
+ * fixed device array of about 6.3 MB inside the library, which every GPU that
+ * loads the library holds until the process exits.
+ *  - Sizes: nx * ny <= 262,144 nodes; larger problems return LBM_ERR_ARG.
+ *  - Buffers (device, caller-owned, distinct): the state layout of
+ *    lbm_stefan_layout / lbm_stefan_get_state: 9 planes; each plane has ny + 2
+ *    rows of `pitch` elements (pitch = nx rounded up to 128 elements in FP32, 64
+ *    in FP64); rows -1 and ny and the padding columns are zero.  Elements are
+ *    float (LBM_FP32) or double (LBM_FP64).
+ *  - wall_kind[4], wall_theta[4]: W, E, S, N as in lbm_stefan_set_bc.
+ *  - The first call on a device resolves the array's device address
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - Every call shares the array: calls that overlap on the GPU (other
+ *    streams, other threads) race.  Each call clears what must start at zero.
+ *  - Runs on cuda_stream (a cudaStream_t) and returns after the step has
+ *    finished: it reads the device error flag (LBM_ERR_NEWTON on a Newton
+ *    failure or a non-finite value). */
+lbm_status lbm_stefan_step_d2q9_noalloc(const lbm_stefan_params* p, const int* wall_kind, const double* wall_theta,
+                                        const void* state_in, void* state_out, void* cuda_stream);
+
 const char* lbm_stefan_last_error(void);
 
 #ifdef __cplusplus

@@ -81,6 +81,8 @@ SIGNATURES = {
     "lbm_stefan_batch_autotune": (_S, [_V, _I, ctypes.POINTER(ctypes.c_int)]),
     "lbm_stefan_batch_set_schedule": (_S, [_V, _I, _I]),
     "lbm_stefan_batch_destroy": (None, [_V]),
+    "lbm_stefan_step_d2q9_noalloc": (_S, [ctypes.POINTER(lbm_stefan_params), ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_double), _V, _V, _V]),
     "lbm_stefan_last_error": (ctypes.c_char_p, []),
 }
 

@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "../../include/lbm_stefan.h"
@@ -857,4 +858,116 @@ extern "C" void lbm_stefan_batch_destroy(lbm_stefan_batch* b)
     cudaFree(b->djobs);
     cudaFree(b->djob_count);
     delete b;
+}
+
+// ------------------------------------------------------------------ one step without allocation
+//
+// For callers that cannot allocate device memory when they step: code running
+// under an allocator or memory budget it does not own, pre-sized real-time loops
+// that must not call cudaMalloc (it can block and synchronize the device), or
+// hosts whose GPU memory is handed out up front.  They own the two state buffers;
+// the step's scratch (problem descriptor, statistics, counters and the list of
+// nodes whose Newton solve is deferred) lives in this fixed device array.  Every
+// GPU that loads the library holds it until the process exits.
+
+namespace {
+
+constexpr int kNoAllocMaxNodes = 1 << 18;   // 262,144 nodes (e.g. 512 x 512)
+
+struct NoAllocScratch {
+    Problem prob;
+    DevStats stats;
+    unsigned int ticket;
+    unsigned int job_count;
+    lbm::NewtonJob jobs[kNoAllocMaxNodes];
+};
+
+// about 6.3 MB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device; resolved once per
+// device (host code cannot use the array's name as a device address).
+lbm_status noalloc_scratch(NoAllocScratch** out)
+{
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(LBM_ERR_ARG, "device index %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void* ptr = nullptr;
+        CUDA_TRY(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+        g_noalloc_addr[dev] = ptr;
+    }
+    *out = static_cast<NoAllocScratch*>(g_noalloc_addr[dev]);
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" lbm_status lbm_stefan_step_d2q9_noalloc(const lbm_stefan_params* p, const int* wall_kind,
+                                                   const double* wall_theta, const void* state_in, void* state_out,
+                                                   void* cuda_stream)
+{
+    if (!p || !wall_kind || !wall_theta || !state_in || !state_out) return fail(LBM_ERR_ARG, "NULL argument");
+    if (state_in == state_out) return fail(LBM_ERR_ARG, "state_in and state_out must differ");
+    if (p->lattice != LBM_D2Q9) return fail(LBM_ERR_ARG, "the no-allocation step is D2Q9 only");
+    if (p->precision != LBM_FP64 && p->precision != LBM_FP32) return fail(LBM_ERR_ARG, "precision must be FP64 or FP32");
+    if (p->bb_mode != LBM_BB_MIRROR && p->bb_mode != LBM_BB_LINK) return fail(LBM_ERR_ARG, "bb_mode must be 0 or 1");
+    lbm_status s = validate_common(p->nx, p->ny, p->tau, p->delta, p->ste, p->newton_tol, p->newton_max_iter);
+    if (s != LBM_OK) return s;
+    if (p->ny < 2) return fail(LBM_ERR_ARG, "D2Q9 needs ny >= 2");
+    if ((long long)p->nx * p->ny > kNoAllocMaxNodes)
+        return fail(LBM_ERR_ARG, "no-allocation step: %d x %d = %lld nodes exceed the maximum of %d", p->nx, p->ny,
+                    (long long)p->nx * p->ny, kNoAllocMaxNodes);
+    for (int w = 0; w < 4; ++w)
+        if ((wall_kind[w] != LBM_ADIABATIC && wall_kind[w] != LBM_DIRICHLET) || !std::isfinite(wall_theta[w]))
+            return fail(LBM_ERR_ARG, "bad wall %d", w);
+
+    NoAllocScratch* sc = nullptr;
+    s = noalloc_scratch(&sc);
+    if (s != LBM_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+
+    const int segw = lbm::d2q9_segment_width(p->precision);
+    Problem hp;
+    fill_problem(hp, 9, p->nx, p->ny, round_up(p->nx, segw), p->tau, p->delta, p->ste, p->newton_tol,
+                 p->newton_max_iter, p->bb_mode, 16, segw, p->precision);
+    for (int w = 0; w < 4; ++w) {
+        hp.wall_kind[w] = wall_kind[w];
+        hp.wall_theta[w] = wall_theta[w];
+    }
+    hp.state[0] = const_cast<void*>(state_in);
+    hp.state[1] = state_out;
+    hp.stats = 0;
+    // the array keeps the previous call's contents: statistics, ticket and job
+    // count must start at zero
+    CUDA_TRY(cudaMemcpyAsync(&sc->prob, &hp, sizeof(Problem), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemsetAsync(&sc->stats, 0, sizeof(DevStats) + 2 * sizeof(unsigned int), st));
+    CUDA_TRY(lbm::launch_wall_constants(&sc->prob, 1, st));
+
+    StepArgs a;
+    a.probs = &sc->prob;
+    a.nprob = 1;
+    a.schedule = nullptr;
+    a.nslots = hp.ntiles;
+    a.parity = 0;
+    a.rec = nullptr;
+    a.stats = &sc->stats;
+    a.ticket = &sc->ticket;
+    a.jobs = sc->jobs;
+    a.job_count = &sc->job_count;
+    CUDA_TRY(lbm::launch_d2q9_step(p->precision, a, (hp.ntiles + lbm::kWarpsPerBlock - 1) / lbm::kWarpsPerBlock, st));
+    CUDA_TRY(lbm::launch_newton_jobs(p->precision,
+                                     job_args(&sc->prob, 1, 0, nullptr, &sc->stats, &sc->ticket, sc->jobs, &sc->job_count),
+                                     st));
+    // report a device-detected Newton failure: read the flag (this waits for the step)
+    int err = 0;
+    CUDA_TRY(cudaMemcpyAsync(&err, &sc->stats.error, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (err) return fail((lbm_status)err, "device reported error %d (Newton limit or non-finite value)", err);
+    return LBM_OK;
 }
