@@ -255,6 +255,37 @@ __device__ __forceinline__ void acc_add_fx(Acc128* a, const Fx& v)
     atomicAdd(reinterpret_cast<unsigned long long*>(&a->hi), (unsigned long long)(v.hi + carry));
 }
 
+// Exact fixed-point value of a float with integer operations only (no FP64
+// instruction): v = m * 2^(e-150), scaled by 2^60.  Bits below 2^-60 are dropped.
+__device__ __forceinline__ Fx float_to_fixed(float v)
+{
+    Fx f{0, 0ull};
+    const unsigned bits = __float_as_uint(v);
+    const int e = (bits >> 23) & 0xff;
+    unsigned long long m = bits & 0x7fffffu;
+    if (e == 0 && m == 0) return f;
+    if (e != 0) m |= 0x800000u;
+    const int sh = (e == 0 ? 1 : e) - 90;   // m * 2^(e - 150 + 60)
+    unsigned long long lo = 0, hi = 0;
+    if (sh >= 0) {
+        if (sh < 64) {
+            lo = m << sh;
+            hi = sh > 40 ? (m >> (64 - sh)) : 0ull;
+        } else {
+            hi = m << (sh - 64);
+        }
+    } else if (sh > -64) {
+        lo = m >> (-sh);
+    }
+    if (bits >> 31) {   // two's complement of the 128-bit value
+        lo = ~lo + 1ull;
+        hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+    }
+    f.lo = lo;
+    f.hi = (long long)hi;
+    return f;
+}
+
 // Add v into the 128-bit fixed-point accumulator.
 __device__ __forceinline__ void acc_add(Acc128* a, double v)
 {
@@ -278,11 +309,18 @@ __device__ __forceinline__ void acc_clear(Acc128* a)
 }
 
 // Publish one problem's step statistics (called by the last block only).
-__device__ __forceinline__ void publish_stats(DevStats* st)
+// E = fixed-point sum + (liquid nodes + sum_w Dirichlet nodes of wall w * phi(theta_w)) / Ste.
+__device__ __forceinline__ void publish_stats(DevStats* st, const Problem* pb)
 {
     double e = acc_read(&st->cur_energy);
-    double f = acc_read(&st->cur_flux);
+    const double f = acc_read(&st->cur_flux);
     volatile DevStats* v = st;
+    if (pb) {
+        double c = (double)v->cur_liquid;
+        for (int w = 0; w < 4; ++w)
+            if (v->cur_dir[w]) c += (double)v->cur_dir[w] * pb->wall_phi[w];
+        e += c * pb->inv_ste;
+    }
     if (v->have_energy) {
         double imb = e - v->energy - f;
         v->imbalance = imb;
@@ -300,6 +338,8 @@ __device__ __forceinline__ void publish_stats(DevStats* st)
     acc_clear(&st->cur_energy);
     acc_clear(&st->cur_flux);
     v->cur_newton = 0ull;
+    v->cur_liquid = 0ull;
+    for (int w = 0; w < 4; ++w) v->cur_dir[w] = 0ull;
     v->cur_maxit = 0;
 }
 
@@ -318,7 +358,7 @@ __device__ __forceinline__ void finish_launch(DevStats* stats, int nprob, unsign
     __syncthreads();
     if (last) {
         __threadfence();
-        for (int p = threadIdx.x; p < nprob; p += blockDim.x) publish_stats(&stats[p]);
+        for (int p = threadIdx.x; p < nprob; p += blockDim.x) publish_stats(&stats[p], nullptr);
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) *ticket = 0u;

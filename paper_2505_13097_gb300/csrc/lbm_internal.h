@@ -22,6 +22,8 @@ struct DevStats {
     Acc128 cur_energy;             // sum_x theta' + phi(theta')/Ste of this step
     Acc128 cur_flux;               // boundary flux of this step
     unsigned long long cur_newton; // nodes that ran the Newton iteration
+    unsigned long long cur_liquid; // saturated liquid nodes (each adds 1/Ste to the energy)
+    unsigned long long cur_dir[4]; // Dirichlet nodes per wall (each adds phi(theta_wall)/Ste)
     int cur_maxit;                 // largest Newton iteration count
     int error;                     // sticky: lbm_status of a device-detected failure
     double energy, energy_prev, flux, imbalance, imbalance_max;

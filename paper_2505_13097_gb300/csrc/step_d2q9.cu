@@ -61,6 +61,22 @@ __device__ __forceinline__ void stv<double>(double* p, const double (&v)[2])
     *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
 }
 
+// stores of one thread's N consecutive values (128-, 64- or 32/64-bit)
+__device__ __forceinline__ void stv_n(float* p, const float (&v)[4]) { *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]); }
+__device__ __forceinline__ void stv_n(float* p, const float (&v)[2]) { *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]); }
+__device__ __forceinline__ void stv_n(double* p, const double (&v)[2]) { *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]); }
+__device__ __forceinline__ void stv_n(double* p, const double (&v)[1]) { *p = v[0]; }
+template <int N>
+__device__ __forceinline__ void st_rec(double* p, const double (&v)[N])
+{
+    if constexpr (N == 1) {
+        *p = v[0];
+    } else {
+#pragma unroll
+        for (int k = 0; k < N; k += 2) *reinterpret_cast<double2*>(p + k) = make_double2(v[k], v[k + 1]);
+    }
+}
+
 // value at x-1 (pull along e_x = +1); h = element left of the segment
 template <typename P, int N>
 __device__ __forceinline__ void from_left(const P (&v)[N], P h, int lane, P (&s)[N])
@@ -286,7 +302,7 @@ struct TileSums {
 #define LBM_RING_STAGES 5
 #endif
 #ifndef LBM_STEP_MIN_BLOCKS
-#define LBM_STEP_MIN_BLOCKS 2
+#define LBM_STEP_MIN_BLOCKS 4
 #endif
 constexpr int kStages = LBM_RING_STAGES;
 
@@ -350,6 +366,175 @@ __device__ __forceinline__ void lds<double>(const double* p, double (&v)[2])
 {
     const double2 t = *reinterpret_cast<const double2*>(p);
     v[0] = t.x; v[1] = t.y;
+}
+
+// Everything of one row after the pulls: wall closures, moments, the exact
+// saturated branch, deferral of Newton nodes to the job list, relaxation and
+// stores (Omega~_i = (1-omega) q_i + w_i c with c = theta' - (1-omega) m0).
+template <typename P, int N, bool REC>
+__device__ __forceinline__ void row_update(const Problem& pb, int y, int x0, int lane, P (&qf)[9][N], const P (&u0)[N],
+                                           const P (&u1)[N], const P (&u2)[N], const P (&u3)[N], const P (&u4)[N],
+                                           const P (&u5)[N], const P (&u6)[N], const P (&u7)[N], const P (&u8)[N],
+                                           P* __restrict__ dst, double* __restrict__ rec, Acc<P>& acc, TileSums& ts,
+                                           DevStats* st, int pi, NewtonJob* jobs, unsigned int* job_count, const P omc,
+                                           const float om_f, const double omc_d, const P (&wP)[3], const float thr_f,
+                                           const int nx, const int ny)
+{
+    const long long pl = pb.plane;
+    const long long pitch = pb.pitch;
+    P c[N];          // per node: theta' - (1-omega) m0, rounded to P
+    double thn[REC ? N : 1];
+    bool newton_k[N];
+    typename M0T<P>::T m0[N];
+    bool any_wall = false;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        const int x = x0 + k;
+        any_wall |= (x < nx) && (x == 0 || x == nx - 1 || y == 0 || y == ny - 1);
+    }
+    bool dir_k[N];
+    int wall_k[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) { dir_k[k] = false; wall_k[k] = -1; }
+    if (__any_sync(kFull, any_wall)) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            const int x = x0 + k;
+            if (x < nx && (x == 0 || x == nx - 1 || y == 0 || y == ny - 1)) {
+                P qq[9], uu[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) qq[i] = qf[i][k];
+                uu[0] = u0[k]; uu[1] = u1[k]; uu[2] = u2[k]; uu[3] = u3[k]; uu[4] = u4[k];
+                uu[5] = u5[k]; uu[6] = u6[k]; uu[7] = u7[k]; uu[8] = u8[k];
+                if constexpr (sizeof(P) == 4) {
+                    const ff fl = wall_closure_f(qq, uu, x, y, pb, wall_k[k]);
+                    ff_add(ts.flux_f, fl.hi);
+                    ts.flux_f.lo += fl.lo;
+                } else {
+                    ts.flux += wall_closure_d(qq, uu, x, y, pb, wall_k[k]);
+                }
+                dir_k[k] = wall_k[k] >= 0;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) qf[i][k] = qq[i];
+            }
+        }
+    }
+
+    bool any_newton = false;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        const int x = x0 + k;
+        const bool valid = x < nx;
+        m0_init(m0[k]);
+        // small weights first
+#pragma unroll
+        for (int i = 8; i >= 0; --i) m0_add(m0[k], qf[i][k]);
+        const P u[9] = {u0[k], u1[k], u2[k], u3[k], u4[k], u5[k], u6[k], u7[k], u8[k]};
+        const float tf = approx_sum<P>(u);
+        const float mf = m0_f(m0[k]);
+        const float marg = 1e-5f * (1.0f + fabsf(tf));
+        const bool sat_liq = tf >= thr_f + marg && mf >= thr_f + marg;
+        const bool sat_sol = tf <= -thr_f - marg && mf <= -thr_f - marg;
+        newton_k[k] = valid && !dir_k[k] && !(sat_liq || sat_sol);
+        any_newton |= newton_k[k];
+        if (!valid) {
+            c[k] = (P)0;
+            if constexpr (REC) thn[k] = 0.0;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) qf[i][k] = (P)0;
+        } else if (dir_k[k]) {
+            // theta' = theta_D; c = theta_D - (1-omega) m0
+            const int wk = wall_k[k];
+            ts.dir_count[wk] += 1;
+            if constexpr (sizeof(P) == 4) {
+                const ff& mm = m0[k];
+                const float oc = (float)omc;
+                c[k] = (P)((pb.wall_th_hi[wk] - oc * mm.hi) + (pb.wall_th_lo[wk] - oc * mm.lo));
+                acc.add_ff(ff{pb.wall_th_hi[wk], pb.wall_th_lo[wk]});
+            } else {
+                c[k] = (P)(pb.wall_theta[wk] - omc_d * m0_d(m0[k]));
+                acc.add_d(pb.wall_theta[wk]);
+            }
+            if constexpr (REC) thn[k] = pb.wall_theta[wk];
+        } else if (!newton_k[k]) {
+            // saturated: theta' = m0, no source; c = omega * m0
+            if constexpr (sizeof(P) == 4) {
+                const ff& mm = m0[k];
+                c[k] = (P)__fmaf_rn(om_f, mm.hi, om_f * mm.lo);
+                acc.add_ff(mm);
+                if constexpr (REC) thn[k] = ff_to_double(mm);
+            } else {
+                const double md = m0_d(m0[k]);
+                c[k] = (P)(pb.omega * md);
+                acc.add_d(md);
+                if constexpr (REC) thn[k] = md;
+            }
+            ts.liquid += sat_liq ? 1 : 0;
+        }
+    }
+    if (__any_sync(kFull, any_newton)) {
+        // The local Newton solve of these nodes is deferred to the job kernel,
+        // which spreads the FP64 work of the front band over the whole GPU:
+        // append (m0, theta) to the job list and store q_i unrelaxed.
+        int cnt = 0;
+#pragma unroll
+        for (int k = 0; k < N; ++k) cnt += newton_k[k] ? 1 : 0;
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int total = __shfl_sync(kFull, incl, 31);
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(job_count, (unsigned)total);
+        base = __shfl_sync(kFull, base, 0);
+        unsigned slot = base + (unsigned)(incl - cnt);
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            if (!newton_k[k]) continue;
+            const P u[9] = {u0[k], u1[k], u2[k], u3[k], u4[k], u5[k], u6[k], u7[k], u8[k]};
+            NewtonJob jb;
+            jb.prob = pi;
+            jb.node = y * nx + x0 + k;
+            if constexpr (sizeof(P) == 4) {
+                ff t;
+                m0_init(t);
+#pragma unroll
+                for (int i = 8; i >= 0; --i) ff_add(t, u[i]);
+                const ff& mm = m0[k];
+                float* pm = reinterpret_cast<float*>(&jb.m0);
+                float* pt = reinterpret_cast<float*>(&jb.theta);
+                pm[0] = mm.hi; pm[1] = mm.lo;
+                pt[0] = t.hi; pt[1] = t.lo;
+            } else {
+                double th = 0.0;
+#pragma unroll
+                for (int i = 8; i >= 0; --i) th += u[i];
+                jb.m0 = m0_d(m0[k]);
+                jb.theta = th;
+            }
+            jobs[slot] = jb;
+            ++slot;
+            c[k] = (P)0;
+            if constexpr (REC) thn[k] = 0.0;
+        }
+    }
+
+    // Omega~_i = (1-omega) q_i + w_i c
+    P* drow = dst + (long long)(y + 1) * pitch + x0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const P wi = i == 0 ? wP[0] : (i <= 4 ? wP[1] : wP[2]);
+        P o[N];
+#pragma unroll
+        for (int k = 0; k < N; ++k) o[k] = newton_k[k] ? qf[i][k] : fma(omc, qf[i][k], wi * c[k]);
+        stv_n(drow + i * pl, o);
+    }
+    if constexpr (REC) {
+        st_rec<N>(rec + (long long)y * pitch + x0, thn);
+    }
+
 }
 
 // One warp tile: segment `seg` of problem pb, rows [ya, yb).
@@ -442,170 +627,153 @@ __device__ __forceinline__ void d2q9_tile(const Problem& pb, const P* __restrict
             for (int k = 0; k < N; ++k) qf[8][k] = s[k];
         }
 
-        P c[N];          // per node: theta' - (1-omega) m0, rounded to P
-        double thn[REC ? N : 1];
-        bool newton_k[N];
-        typename M0T<P>::T m0[N];
-        bool any_wall = false;
-#pragma unroll
-        for (int k = 0; k < N; ++k) {
-            const int x = x0 + k;
-            any_wall |= (x < nx) && (x == 0 || x == nx - 1 || y == 0 || y == ny - 1);
-        }
-        bool dir_k[N];
-        int wall_k[N];
-#pragma unroll
-        for (int k = 0; k < N; ++k) { dir_k[k] = false; wall_k[k] = -1; }
-        if (__any_sync(kFull, any_wall)) {
-#pragma unroll
-            for (int k = 0; k < N; ++k) {
-                const int x = x0 + k;
-                if (x < nx && (x == 0 || x == nx - 1 || y == 0 || y == ny - 1)) {
-                    P qq[9], uu[9];
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) qq[i] = qf[i][k];
-                    uu[0] = u0[k]; uu[1] = u1[k]; uu[2] = u2[k]; uu[3] = u3[k]; uu[4] = u4[k];
-                    uu[5] = u5[k]; uu[6] = u6[k]; uu[7] = u7[k]; uu[8] = u8[k];
-                    if constexpr (sizeof(P) == 4) {
-                        const ff fl = wall_closure_f(qq, uu, x, y, pb, wall_k[k]);
-                        ff_add(ts.flux_f, fl.hi);
-                        ts.flux_f.lo += fl.lo;
-                    } else {
-                        ts.flux += wall_closure_d(qq, uu, x, y, pb, wall_k[k]);
-                    }
-                    dir_k[k] = wall_k[k] >= 0;
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) qf[i][k] = qq[i];
-                }
-            }
-        }
-
-        bool any_newton = false;
-#pragma unroll
-        for (int k = 0; k < N; ++k) {
-            const int x = x0 + k;
-            const bool valid = x < nx;
-            m0_init(m0[k]);
-            // small weights first
-#pragma unroll
-            for (int i = 8; i >= 0; --i) m0_add(m0[k], qf[i][k]);
-            const P u[9] = {u0[k], u1[k], u2[k], u3[k], u4[k], u5[k], u6[k], u7[k], u8[k]};
-            const float tf = approx_sum<P>(u);
-            const float mf = m0_f(m0[k]);
-            const float marg = 1e-5f * (1.0f + fabsf(tf));
-            const bool sat_liq = tf >= thr_f + marg && mf >= thr_f + marg;
-            const bool sat_sol = tf <= -thr_f - marg && mf <= -thr_f - marg;
-            newton_k[k] = valid && !dir_k[k] && !(sat_liq || sat_sol);
-            any_newton |= newton_k[k];
-            if (!valid) {
-                c[k] = (P)0;
-                if constexpr (REC) thn[k] = 0.0;
-#pragma unroll
-                for (int i = 0; i < 9; ++i) qf[i][k] = (P)0;
-            } else if (dir_k[k]) {
-                // theta' = theta_D; c = theta_D - (1-omega) m0
-                const int wk = wall_k[k];
-                ts.dir_count[wk] += 1;
-                if constexpr (sizeof(P) == 4) {
-                    const ff& mm = m0[k];
-                    const float oc = (float)omc;
-                    c[k] = (P)((pb.wall_th_hi[wk] - oc * mm.hi) + (pb.wall_th_lo[wk] - oc * mm.lo));
-                    acc.add_ff(ff{pb.wall_th_hi[wk], pb.wall_th_lo[wk]});
-                } else {
-                    c[k] = (P)(pb.wall_theta[wk] - omc_d * m0_d(m0[k]));
-                    acc.add_d(pb.wall_theta[wk]);
-                }
-                if constexpr (REC) thn[k] = pb.wall_theta[wk];
-            } else if (!newton_k[k]) {
-                // saturated: theta' = m0, no source; c = omega * m0
-                if constexpr (sizeof(P) == 4) {
-                    const ff& mm = m0[k];
-                    c[k] = (P)__fmaf_rn(om_f, mm.hi, om_f * mm.lo);
-                    acc.add_ff(mm);
-                    if constexpr (REC) thn[k] = ff_to_double(mm);
-                } else {
-                    const double md = m0_d(m0[k]);
-                    c[k] = (P)(pb.omega * md);
-                    acc.add_d(md);
-                    if constexpr (REC) thn[k] = md;
-                }
-                ts.liquid += sat_liq ? 1 : 0;
-            }
-        }
-        if (__any_sync(kFull, any_newton)) {
-            // The local Newton solve of these nodes is deferred to the job kernel,
-            // which spreads the FP64 work of the front band over the whole GPU:
-            // append (m0, theta) to the job list and store q_i unrelaxed.
-            int cnt = 0;
-#pragma unroll
-            for (int k = 0; k < N; ++k) cnt += newton_k[k] ? 1 : 0;
-            int incl = cnt;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int v = __shfl_up_sync(kFull, incl, o);
-                if (lane >= o) incl += v;
-            }
-            const int total = __shfl_sync(kFull, incl, 31);
-            unsigned base = 0;
-            if (lane == 0) base = atomicAdd(job_count, (unsigned)total);
-            base = __shfl_sync(kFull, base, 0);
-            unsigned slot = base + (unsigned)(incl - cnt);
-#pragma unroll
-            for (int k = 0; k < N; ++k) {
-                if (!newton_k[k]) continue;
-                const P u[9] = {u0[k], u1[k], u2[k], u3[k], u4[k], u5[k], u6[k], u7[k], u8[k]};
-                NewtonJob jb;
-                jb.prob = pi;
-                jb.node = y * nx + x0 + k;
-                if constexpr (sizeof(P) == 4) {
-                    ff t;
-                    m0_init(t);
-#pragma unroll
-                    for (int i = 8; i >= 0; --i) ff_add(t, u[i]);
-                    const ff& mm = m0[k];
-                    float* pm = reinterpret_cast<float*>(&jb.m0);
-                    float* pt = reinterpret_cast<float*>(&jb.theta);
-                    pm[0] = mm.hi; pm[1] = mm.lo;
-                    pt[0] = t.hi; pt[1] = t.lo;
-                } else {
-                    double th = 0.0;
-#pragma unroll
-                    for (int i = 8; i >= 0; --i) th += u[i];
-                    jb.m0 = m0_d(m0[k]);
-                    jb.theta = th;
-                }
-                jobs[slot] = jb;
-                ++slot;
-                c[k] = (P)0;
-                if constexpr (REC) thn[k] = 0.0;
-            }
-        }
-
-        // Omega~_i = (1-omega) q_i + w_i c
-        P* drow = dst + (long long)(y + 1) * pitch + x0;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const P wi = i == 0 ? wP[0] : (i <= 4 ? wP[1] : wP[2]);
-            P o[N];
-#pragma unroll
-            for (int k = 0; k < N; ++k) o[k] = newton_k[k] ? qf[i][k] : fma(omc, qf[i][k], wi * c[k]);
-            stv<P>(drow + i * pl, o);
-        }
-        if constexpr (REC) {
-            double* rr = rec + (long long)y * pitch + x0;
-#pragma unroll
-            for (int k = 0; k < N; k += 2) *reinterpret_cast<double2*>(rr + k) = make_double2(thn[k], thn[k + 1]);
-        }
-
-        // the slot of row y-1 is free once every lane has read it
+        // every lane has its values of row y-1 in registers: refill that slot with
+        // row y+kStages-1 now, so the load overlaps this row's arithmetic
         __syncwarp();
-        const int rn = y + kStages - 1;
-        if (rn <= yb) ring_load<P>(ring + ((rn + 1) % kStages) * R::SLOT, src, pl, pitch, rn, segx, lane, has_left, has_right);
-        cp_async_commit();
+        {
+            const int rn = y + kStages - 1;
+            if (rn <= yb) ring_load<P>(ring + ((rn + 1) % kStages) * R::SLOT, src, pl, pitch, rn, segx, lane, has_left, has_right);
+            cp_async_commit();
+        }
+        row_update<P, N, REC>(pb, y, x0, lane, qf, u0, u1, u2, u3, u4, u5, u6, u7, u8, dst, rec, acc, ts, st, pi,
+                              jobs, job_count, omc, om_f, omc_d, wP, thr_f, nx, ny);
+
     }
     cp_async_wait<0>();
     __syncwarp();
 }
+
+// ---------------------------------------------------------------- direct tile
+// Same update with rows loaded straight from global memory into registers:
+// 2 floats (FP32 form) or 1 double per thread, so a warp covers 256 bytes of
+// each plane row and the kernel needs few registers and no shared memory; many
+// resident warps keep enough rows in flight.  Planes pulled along +y come from
+// the previous row (kept shifted in registers), planes pulled along -y from the
+// next row (loaded one row ahead and kept for the moments of the next row).
+#ifndef LBM_DIRECT_PREFETCH
+#define LBM_DIRECT_PREFETCH 1
+#endif
+
+template <typename P> struct Vd;
+template <> struct Vd<float> { static constexpr int N = 2; };
+template <> struct Vd<double> { static constexpr int N = 1; };
+
+__device__ __forceinline__ void ldg_n(const float* p, float (&v)[2])
+{
+    const float2 t = __ldg(reinterpret_cast<const float2*>(p));
+    v[0] = t.x; v[1] = t.y;
+}
+__device__ __forceinline__ void ldg_n(const double* p, double (&v)[1]) { v[0] = __ldg(p); }
+
+template <typename P, bool REC>
+__device__ __forceinline__ void d2q9_tile_direct(const Problem& pb, const P* __restrict__ src, P* __restrict__ dst,
+                                                 double* __restrict__ rec, int seg, int ya, int yb, Acc<P>& acc,
+                                                 TileSums& ts, DevStats* st, int pi, NewtonJob* jobs,
+                                                 unsigned int* job_count)
+{
+    constexpr int N = Vd<P>::N;
+    const int lane = threadIdx.x & 31;
+    const int segx = seg * 32 * N;
+    const int x0 = segx + lane * N;
+    const long long pl = pb.plane;
+    const long long pitch = pb.pitch;
+    const bool has_left = segx > 0;
+    const bool has_right = segx + 32 * N < pb.nx;
+    const P omc = (P)(1.0 - pb.omega);
+    const float om_f = (float)pb.omega;
+    const double omc_d = 1.0 - pb.omega;
+    const int nx = pb.nx, ny = pb.ny;
+    const P wP[3] = {(P)d2_w(0), (P)d2_w(1), (P)d2_w(5)};
+    const float thr_f = (float)pb.sat;
+
+    auto rp = [&](int i, int r) -> const P* { return src + i * pl + (long long)(r + 1) * pitch + x0; };
+    auto hl = [&](int i, int r) -> P {
+        return (lane == 0 && has_left) ? __ldg(src + i * pl + (long long)(r + 1) * pitch + segx - 1) : (P)0;
+    };
+    auto hr = [&](int i, int r) -> P {
+        return (lane == 31 && has_right) ? __ldg(src + i * pl + (long long)(r + 1) * pitch + segx + 32 * N) : (P)0;
+    };
+
+    P up2[N], up5[N], up6[N], cu4[N], cu7[N], cu8[N];
+    {
+        P t[N];
+        ldg_n(rp(2, ya - 1), up2);
+        ldg_n(rp(5, ya - 1), t);
+        from_left<P, N>(t, hl(5, ya - 1), lane, up5);
+        ldg_n(rp(6, ya - 1), t);
+        from_right<P, N>(t, hr(6, ya - 1), lane, up6);
+        ldg_n(rp(4, ya), cu4);
+        ldg_n(rp(7, ya), cu7);
+        ldg_n(rp(8, ya), cu8);
+    }
+    // loads of one row: planes 0,1,3,2,5,6 at row y, planes 4,7,8 at row y+1, and
+    // the elements beyond the segment for the planes shifted along x
+    struct RowLoads {
+        P r0[N], r1[N], r3[N], c2[N], c5[N], c6[N], n4[N], n7[N], n8[N];
+        P h1, h3, h5, h6, h7, h8;
+    };
+    auto issue = [&](RowLoads& L, int y) {
+        ldg_n(rp(0, y), L.r0);
+        ldg_n(rp(1, y), L.r1);
+        ldg_n(rp(3, y), L.r3);
+        ldg_n(rp(2, y), L.c2);
+        ldg_n(rp(5, y), L.c5);
+        ldg_n(rp(6, y), L.c6);
+        ldg_n(rp(4, y + 1), L.n4);
+        ldg_n(rp(7, y + 1), L.n7);
+        ldg_n(rp(8, y + 1), L.n8);
+        L.h1 = hl(1, y);
+        L.h3 = hr(3, y);
+        L.h5 = hl(5, y);
+        L.h6 = hr(6, y);
+        L.h7 = hr(7, y + 1);
+        L.h8 = hl(8, y + 1);
+    };
+    RowLoads cur;
+    issue(cur, ya);
+    for (int y = ya; y < yb; ++y) {
+        // next row's loads first, so they are in flight during this row's arithmetic
+        RowLoads nxt;
+        if (LBM_DIRECT_PREFETCH && y + 1 < yb) issue(nxt, y + 1);
+        P qf[9][N];
+        {
+            P s[N];
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                qf[0][k] = cur.r0[k]; qf[2][k] = up2[k]; qf[4][k] = cur.n4[k]; qf[5][k] = up5[k]; qf[6][k] = up6[k];
+            }
+            from_left<P, N>(cur.r1, cur.h1, lane, s);
+#pragma unroll
+            for (int k = 0; k < N; ++k) qf[1][k] = s[k];
+            from_right<P, N>(cur.r3, cur.h3, lane, s);
+#pragma unroll
+            for (int k = 0; k < N; ++k) qf[3][k] = s[k];
+            from_right<P, N>(cur.n7, cur.h7, lane, s);
+#pragma unroll
+            for (int k = 0; k < N; ++k) qf[7][k] = s[k];
+            from_left<P, N>(cur.n8, cur.h8, lane, s);
+#pragma unroll
+            for (int k = 0; k < N; ++k) qf[8][k] = s[k];
+        }
+        row_update<P, N, REC>(pb, y, x0, lane, qf, cur.r0, cur.r1, cur.c2, cur.r3, cu4, cur.c5, cur.c6, cu7, cu8, dst,
+                              rec, acc, ts, st, pi, jobs, job_count, omc, om_f, omc_d, wP, thr_f, nx, ny);
+        // roll the register window
+#pragma unroll
+        for (int k = 0; k < N; ++k) { up2[k] = cur.c2[k]; cu4[k] = cur.n4[k]; cu7[k] = cur.n7[k]; cu8[k] = cur.n8[k]; }
+        from_left<P, N>(cur.c5, cur.h5, lane, up5);
+        from_right<P, N>(cur.c6, cur.h6, lane, up6);
+        if (LBM_DIRECT_PREFETCH) {
+            cur = nxt;
+        } else if (y + 1 < yb) {
+            issue(cur, y + 1);
+        }
+    }
+}
+
+#ifndef LBM_STEP_DIRECT
+#define LBM_STEP_DIRECT 1
+#endif
+
 
 template <typename P, bool REC>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, LBM_STEP_MIN_BLOCKS) d2q9_step_kernel(StepArgs a)
@@ -637,21 +805,44 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, LBM_STEP_MIN_BLOCKS) d2q9
         P* dst = static_cast<P*>(pb.state[a.parity ^ 1]);
         Acc<P> acc;
         TileSums ts;
+#if LBM_STEP_DIRECT
+        d2q9_tile_direct<P, REC>(pb, src, dst, a.rec, seg, ya, yb, acc, ts, st, pi, a.jobs, a.job_count);
+#else
         d2q9_tile<P, REC>(pb, src, dst, a.rec, seg, ya, yb, acc, ts, st, ring, pi, a.jobs, a.job_count);
-        // tile partial sums: fixed lane order, then one fixed-point atomic per quantity
-        double dsum = 0.0;
+#endif
+        // tile partial sums in a fixed lane order, then exact fixed-point atomics;
+        // node counts go to integer counters (the publisher adds their phi/Ste terms)
+        Fx e, f;
+        if constexpr (sizeof(P) == 4) {
+            ff se = acc.s, sf = ts.flux_f;
 #pragma unroll
-        for (int w = 0; w < 4; ++w)
-            if (ts.dir_count[w]) dsum += ts.dir_count[w] * pb.wall_phi[w];
-        const double e = warp_sum(acc.get() + ((double)ts.liquid + ts.phi_sum + dsum) * pb.inv_ste);
-        const double f = warp_sum(sizeof(P) == 4 ? ff_to_double(ts.flux_f) : ts.flux);
-        const int nn = warp_sum_i(ts.newton);
-        const int mi = warp_max_i(ts.maxit);
+            for (int o = 16; o > 0; o >>= 1) {
+                const float eh = __shfl_xor_sync(kFull, se.hi, o), el = __shfl_xor_sync(kFull, se.lo, o);
+                const float fh = __shfl_xor_sync(kFull, sf.hi, o), fl = __shfl_xor_sync(kFull, sf.lo, o);
+                ff_add(se, eh);
+                se.lo += el;
+                ff_add(sf, fh);
+                sf.lo += fl;
+            }
+            e = float_to_fixed(se.hi);
+            fx_add(e, float_to_fixed(se.lo));
+            f = float_to_fixed(sf.hi);
+            fx_add(f, float_to_fixed(sf.lo));
+        } else {
+            e = to_fixed(warp_sum(acc.get()));
+            f = to_fixed(warp_sum(ts.flux));
+        }
+        const int nl = warp_sum_i(ts.liquid);
+        int nd[4];
+#pragma unroll
+        for (int w = 0; w < 4; ++w) nd[w] = warp_sum_i(ts.dir_count[w]);
         if (lane == 0) {
-            acc_add(&st->cur_energy, e);
-            acc_add(&st->cur_flux, f);
-            if (nn) atomicAdd(&st->cur_newton, (unsigned long long)nn);
-            if (mi) atomicMax(&st->cur_maxit, mi);
+            acc_add_fx(&st->cur_energy, e);
+            acc_add_fx(&st->cur_flux, f);
+            if (nl) atomicAdd(&st->cur_liquid, (unsigned long long)nl);
+#pragma unroll
+            for (int w = 0; w < 4; ++w)
+                if (nd[w]) atomicAdd(&st->cur_dir[w], (unsigned long long)nd[w]);
         }
     }
     // statistics are published by the job kernel that follows every step
@@ -730,19 +921,20 @@ __global__ void __launch_bounds__(128) newton_jobs_kernel(JobArgs a)
             atomicMax(&st->cur_maxit, mx);
         }
     }
-    // last warp: publish every problem's step statistics, clear the job list
-    unsigned t = 0;
-    if (lane == 0) {
+    // last block: publish every problem's step statistics, clear the job list
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
         __threadfence();
-        t = atomicAdd(a.ticket, 1u);
+        last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
     }
-    t = __shfl_sync(kFull, t, 0);
-    if (t == nw - 1) {
+    __syncthreads();
+    if (last) {
         __threadfence();
-        for (int p = lane; p < a.nprob; p += 32) publish_stats(&a.stats[p]);
+        for (int p = threadIdx.x; p < a.nprob; p += blockDim.x) publish_stats(&a.stats[a.probs[p].stats], &a.probs[p]);
         __threadfence();
-        __syncwarp();
-        if (lane == 0) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
             *a.job_count = 0u;
             *a.ticket = 0u;
         }
@@ -752,7 +944,7 @@ __global__ void __launch_bounds__(128) newton_jobs_kernel(JobArgs a)
 template <typename P>
 constexpr int step_smem_bytes()
 {
-    return kWarpsPerBlock * Ring<P>::WARP_BYTES;
+    return LBM_STEP_DIRECT ? 0 : kWarpsPerBlock * Ring<P>::WARP_BYTES;
 }
 
 template <typename P, bool REC>
@@ -769,7 +961,11 @@ static cudaError_t launch_t(const StepArgs& a, int grid, cudaStream_t s)
     return cudaGetLastError();
 }
 
-int d2q9_segment_width(int precision) { return precision == 1 ? 32 * 4 : 32 * 2; }
+int d2q9_segment_width(int precision)
+{
+    if (LBM_STEP_DIRECT) return precision == 1 ? 32 * Vd<float>::N : 32 * Vd<double>::N;
+    return precision == 1 ? 32 * 4 : 32 * 2;
+}
 
 cudaError_t launch_d2q9_step(int precision, const StepArgs& a, int grid, cudaStream_t s)
 {
@@ -783,7 +979,7 @@ cudaError_t launch_newton_jobs(int precision, const JobArgs& a, cudaStream_t s)
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = sms * 8;
+    const int grid = sms * 4;
     if (precision == 1) {
         if (a.rec) newton_jobs_kernel<float, true><<<grid, 128, 0, s>>>(a);
         else newton_jobs_kernel<float, false><<<grid, 128, 0, s>>>(a);
