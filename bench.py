@@ -368,14 +368,15 @@ def run_gpu(args):
                        "l2": "state 1.2 GB > 129 MB L2 (no flush needed)", "parallelism": "replicas" if world > 1 else "1 GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
-                         "bytes_per_node": BYTES_FP32, "kernel": "d2q9_step_kernel<float>",
+                         "bytes_per_node": BYTES_FP32,
+                         "kernel": "d2q9_step_kernel<float> + newton_jobs_kernel<float> (one step)",
                          "peak_source": peak_kind},
             "cpu_baseline": cpu_baseline_sample(workloads) if (world == 1 and not args.no_cpu) else None,
             "e2e": {"value": nodes * args.steps / e2e_ms / 1e3, "unit": "MLUPS",
                     "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                     "what": "lbm_stefan_set_ic from pinned host theta0, %d steps from the initial state, "
                             "lbm_stefan_get_fields to pinned host theta" % args.steps},
-            "gpu_launches": args.steps,
+            "gpu_launches": 2 * args.steps,   # per step: the fused step kernel and the Newton job kernel
             "clocks": clk.summary(),
             "energy_imbalance_last_step": st["imbalance"],
             "newton_nodes_last_step": st["newton_nodes"],

@@ -371,7 +371,7 @@ __device__ __forceinline__ void lds<double>(const double* p, double (&v)[2])
 // Everything of one row after the pulls: wall closures, moments, the exact
 // saturated branch, deferral of Newton nodes to the job list, relaxation and
 // stores (Omega~_i = (1-omega) q_i + w_i c with c = theta' - (1-omega) m0).
-template <typename P, int N, bool REC>
+template <typename P, int N, bool REC, bool EDGE>
 __device__ __forceinline__ void row_update(const Problem& pb, int y, int x0, int lane, P (&qf)[9][N], const P (&u0)[N],
                                            const P (&u1)[N], const P (&u2)[N], const P (&u3)[N], const P (&u4)[N],
                                            const P (&u5)[N], const P (&u6)[N], const P (&u7)[N], const P (&u8)[N],
@@ -387,16 +387,19 @@ __device__ __forceinline__ void row_update(const Problem& pb, int y, int x0, int
     bool newton_k[N];
     typename M0T<P>::T m0[N];
     bool any_wall = false;
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-        const int x = x0 + k;
-        any_wall |= (x < nx) && (x == 0 || x == nx - 1 || y == 0 || y == ny - 1);
-    }
     bool dir_k[N];
     int wall_k[N];
 #pragma unroll
     for (int k = 0; k < N; ++k) { dir_k[k] = false; wall_k[k] = -1; }
-    if (__any_sync(kFull, any_wall)) {
+    if constexpr (EDGE) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            const int x = x0 + k;
+            any_wall |= (x < nx) && (x == 0 || x == nx - 1 || y == 0 || y == ny - 1);
+        }
+    }
+    // EDGE = false: the caller knows the warp's row has no wall node and no node beyond nx
+    if (EDGE && __any_sync(kFull, any_wall)) {
 #pragma unroll
         for (int k = 0; k < N; ++k) {
             const int x = x0 + k;
@@ -424,7 +427,7 @@ __device__ __forceinline__ void row_update(const Problem& pb, int y, int x0, int
 #pragma unroll
     for (int k = 0; k < N; ++k) {
         const int x = x0 + k;
-        const bool valid = x < nx;
+        const bool valid = !EDGE || x < nx;
         m0_init(m0[k]);
         // small weights first
 #pragma unroll
@@ -635,8 +638,8 @@ __device__ __forceinline__ void d2q9_tile(const Problem& pb, const P* __restrict
             if (rn <= yb) ring_load<P>(ring + ((rn + 1) % kStages) * R::SLOT, src, pl, pitch, rn, segx, lane, has_left, has_right);
             cp_async_commit();
         }
-        row_update<P, N, REC>(pb, y, x0, lane, qf, u0, u1, u2, u3, u4, u5, u6, u7, u8, dst, rec, acc, ts, st, pi,
-                              jobs, job_count, omc, om_f, omc_d, wP, thr_f, nx, ny);
+        row_update<P, N, REC, true>(pb, y, x0, lane, qf, u0, u1, u2, u3, u4, u5, u6, u7, u8, dst, rec, acc, ts, st, pi,
+                                    jobs, job_count, omc, om_f, omc_d, wP, thr_f, nx, ny);
 
     }
     cp_async_wait<0>();
@@ -679,6 +682,7 @@ __device__ __forceinline__ void d2q9_tile_direct(const Problem& pb, const P* __r
     const long long pitch = pb.pitch;
     const bool has_left = segx > 0;
     const bool has_right = segx + 32 * N < pb.nx;
+    const bool seg_interior = has_left && has_right;   // no wall column, every node inside
     const P omc = (P)(1.0 - pb.omega);
     const float om_f = (float)pb.omega;
     const double omc_d = 1.0 - pb.omega;
@@ -755,8 +759,14 @@ __device__ __forceinline__ void d2q9_tile_direct(const Problem& pb, const P* __r
 #pragma unroll
             for (int k = 0; k < N; ++k) qf[8][k] = s[k];
         }
-        row_update<P, N, REC>(pb, y, x0, lane, qf, cur.r0, cur.r1, cur.c2, cur.r3, cu4, cur.c5, cur.c6, cu7, cu8, dst,
-                              rec, acc, ts, st, pi, jobs, job_count, omc, om_f, omc_d, wP, thr_f, nx, ny);
+        if (seg_interior && y > 0 && y < ny - 1)
+            row_update<P, N, REC, false>(pb, y, x0, lane, qf, cur.r0, cur.r1, cur.c2, cur.r3, cu4, cur.c5, cur.c6, cu7,
+                                         cu8, dst, rec, acc, ts, st, pi, jobs, job_count, omc, om_f, omc_d, wP, thr_f,
+                                         nx, ny);
+        else
+            row_update<P, N, REC, true>(pb, y, x0, lane, qf, cur.r0, cur.r1, cur.c2, cur.r3, cu4, cur.c5, cur.c6, cu7,
+                                        cu8, dst, rec, acc, ts, st, pi, jobs, job_count, omc, om_f, omc_d, wP, thr_f,
+                                        nx, ny);
         // roll the register window
 #pragma unroll
         for (int k = 0; k < N; ++k) { up2[k] = cur.c2[k]; cu4[k] = cur.n4[k]; cu7[k] = cur.n7[k]; cu8[k] = cur.n8[k]; }
