@@ -149,6 +149,16 @@ lbm_status lbm_stefan_adjoint_seed(lbm_stefan* h, const double* theta_T, const d
 lbm_status lbm_stefan_adjoint_step(lbm_stefan* h, const double* theta_t, const double* theta_t1,
                                    const void* adj_in, void* adj_out);
 
+/* nsteps reverse steps over one recorded segment: theta_traj holds nsteps+1
+ * planes theta(t0), ..., theta(t0+nsteps) (device, ny*row_stride doubles each,
+ * as written by lbm_stefan_theta_plane and lbm_stefan_step_record); adj holds
+ * lambda(t0+nsteps) on entry.  The two state-sized device buffers adj and
+ * adj_other alternate; *result_index is 0 if lambda(t0) ends in adj, 1 if in
+ * adj_other.  Asynchronous on the handle's stream; LBM_ERR_ARG for NULL
+ * pointers, nsteps < 0 or adj == adj_other. */
+lbm_status lbm_stefan_adjoint_run(lbm_stefan* h, int nsteps, const double* theta_traj, void* adj,
+                                  void* adj_other, int* result_index);
+
 /* From lambda_0: dL/dtheta0 (nx*ny doubles, zero on Dirichlet nodes),
  * dL/dtheta_wall[4] (walls that are not Dirichlet get 0) and dL/dSte.
  * Synchronizes. */

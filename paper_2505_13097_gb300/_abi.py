@@ -70,6 +70,7 @@ SIGNATURES = {
     "lbm_stefan_theta_plane": (_S, [_V, _V]),
     "lbm_stefan_adjoint_seed": (_S, [_V, _V, _V, _V, _D]),
     "lbm_stefan_adjoint_step": (_S, [_V, _V, _V, _V, _V]),
+    "lbm_stefan_adjoint_run": (_S, [_V, _I, _V, _V, _V, ctypes.POINTER(ctypes.c_int)]),
     "lbm_stefan_adjoint_finish": (_S, [_V, _V, _V, _I, _D, _D]),
     "lbm_stefan_destroy": (None, [_V]),
     "lbm_stefan_batch_create": (_S, [_I, ctypes.POINTER(lbm_stefan_problem), _I, ctypes.c_double, _I, _V,

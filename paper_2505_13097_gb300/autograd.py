@@ -62,15 +62,14 @@ class StefanMisfit(torch.autograd.Function):
         other = S.new_state_buffer()
         starts = [c[0] for c in ctx.checkpoints]
         ends = starts[1:] + [ctx.steps]
+        planes = S.new_theta_planes(max(e - s for s, e in zip(starts, ends)) + 1)
         for (start, buf), end in reversed(list(zip(ctx.checkpoints, ends))):
             n = end - start
-            traj = S.new_theta_planes(n + 1)
+            traj = planes[:n + 1]
             S.set_state(buf)
             S.theta_plane(traj[0])
             S.step_record(n, traj[1:])
-            for s in range(n - 1, -1, -1):
-                S.adjoint_step(traj[s], traj[s + 1], adj, other)
-                adj, other = other, adj
+            adj, other = S.adjoint_run(traj, adj, other)
         g0 = torch.empty((S.ny, S.nx), dtype=torch.float64, device="cuda")
         gw, gs = S.adjoint_finish(adj, g0)
         S.close()

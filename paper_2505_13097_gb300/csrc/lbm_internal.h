@@ -103,20 +103,31 @@ struct JobArgs {
     unsigned int* job_count;
 };
 
+// Constants of the interior-node adjoint terms, converted once on the host.
+struct AdjConst {
+    float omc_f, om_f, inv_delta_f, inv_ste_f, inv_ste2_f, thr_f;
+    double omc, om, inv_delta, inv_ste, thr;
+};
+
 // Per-launch arguments of the adjoint kernels (single problem).
 struct AdjArgs {
-    const Problem* prob;     // device pointer
+    Problem pb;              // by value: read from the kernel parameter bank
+    AdjConst c;
     const double* theta_t;   // recorded theta(t), ny x pitch
     const double* theta_t1;  // recorded theta(t+1), ny x pitch
     const void* adj_in;      // lambda(t+1), state layout
     void* adj_out;           // lambda(t), state layout
-    double* wall_buf;        // per wall node records (see adjoint.cu)
     DevStats* stats;
-    unsigned int* ticket;
+    int tile_h;              // rows per warp tile of the D2Q9 adjoint
+    int ntiles;              // nseg * ceil(ny / tile_h)
+    // plane i of adj_in / adj_out (D2Q9): kernel parameters, so that the
+    // addresses come from the parameter bank instead of per-thread registers
+    const void* in_plane[9];
+    void* out_plane[9];
 };
 
 constexpr int kWarpsPerBlock = 4;
-constexpr int kWallRec = 19;   // doubles per wall-node record of the adjoint
+constexpr int kAdjTileH = 32;  // default rows per warp tile of the D2Q9 adjoint
 
 // D2Q9 launchers (step_d2q9.cu)
 cudaError_t launch_d2q9_step(int precision, const StepArgs& a, int grid, cudaStream_t s);

@@ -70,6 +70,7 @@ struct lbm_stefan {
     unsigned int* djob_count = nullptr;
     int parity = 0;
     bool ic = false;
+    int adj_tile_h = lbm::kAdjTileH;   // rows per warp tile of the D2Q9 adjoint
     GraphCache graph;
 };
 
@@ -119,6 +120,24 @@ static double saturation_threshold(int precision, double delta, double ste)
     double k = 19.5;
     if (precision == LBM_FP32) k = std::min(19.5, std::max(10.0, 0.5 * std::log(2.0 / (ste * 1e-10))));
     return k * delta;
+}
+
+// Rows per warp tile of the D2Q9 adjoint: the tallest of 32, 16, 8, 4 that
+// still gives four warp tiles per resident warp slot (16 per SM).  Each tile
+// also evaluates the row below and above it, so tall tiles waste less.
+#ifndef LBM_ADJ_TILE_H
+#define LBM_ADJ_TILE_H 0
+#endif
+static int adjoint_tile_h(const Problem& hp)
+{
+    if (LBM_ADJ_TILE_H > 0) return LBM_ADJ_TILE_H;
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        sms = 152;
+    const long long want = 4LL * 16 * sms;
+    int th = lbm::kAdjTileH;
+    while (th > 4 && (long long)hp.nseg * ((hp.ny + th - 1) / th) < want) th /= 2;
+    return th;
 }
 
 static void fill_problem(Problem& pb, int q, int nx, int ny, int pitch, double tau, double delta, double ste,
@@ -255,6 +274,7 @@ extern "C" lbm_status lbm_stefan_create(const lbm_stefan_params* p, void* cuda_s
     if (e == cudaSuccess) e = cudaMalloc(&h->dscratch, sizeof(double) * 3 * (size_t)p->nx * p->ny);
     if (e == cudaSuccess && q == 9) e = cudaMalloc(&h->djobs, sizeof(lbm::NewtonJob) * (size_t)p->nx * p->ny);
     if (e == cudaSuccess) e = cudaMalloc(&h->djob_count, sizeof(unsigned int));
+    if (e == cudaSuccess && q == 9) h->adj_tile_h = adjoint_tile_h(h->hp);
     if (e == cudaSuccess) e = cudaMemset(h->djob_count, 0, sizeof(unsigned int));
     h->hp.state[0] = bufs[0];
     h->hp.state[1] = bufs[1];
@@ -474,21 +494,65 @@ extern "C" lbm_status lbm_stefan_adjoint_seed(lbm_stefan* h, const double* theta
     return LBM_OK;
 }
 
+static lbm::AdjArgs adj_args(lbm_stefan* h, const double* theta_t, const double* theta_t1, const void* adj_in,
+                             void* adj_out)
+{
+    lbm::AdjArgs a;
+    a.pb = h->hp;
+    a.theta_t = theta_t;
+    a.theta_t1 = theta_t1;
+    a.adj_in = adj_in;
+    a.adj_out = adj_out;
+    a.stats = h->dstats;
+    lbm::AdjConst& c = a.c;
+    c.omc = 1.0 - h->hp.omega;
+    c.om = h->hp.omega;
+    c.inv_delta = h->hp.inv_delta;
+    c.inv_ste = h->hp.inv_ste;
+    c.thr = h->hp.sat;
+    c.omc_f = (float)c.omc;
+    c.om_f = (float)c.om;
+    c.inv_delta_f = (float)c.inv_delta;
+    c.inv_ste_f = (float)c.inv_ste;
+    c.inv_ste2_f = (float)(c.inv_ste * c.inv_ste);
+    c.thr_f = (float)c.thr;
+    a.tile_h = h->adj_tile_h;
+    a.ntiles = h->hp.nseg * ((h->hp.ny + a.tile_h - 1) / a.tile_h);
+    const size_t pb = (size_t)h->hp.plane * h->elem;
+    for (int i = 0; i < 9; ++i) {
+        a.in_plane[i] = i < h->hp.q ? static_cast<const char*>(adj_in) + i * pb : nullptr;
+        a.out_plane[i] = i < h->hp.q ? static_cast<char*>(adj_out) + i * pb : nullptr;
+    }
+    return a;
+}
+
 extern "C" lbm_status lbm_stefan_adjoint_step(lbm_stefan* h, const double* theta_t, const double* theta_t1,
                                               const void* adj_in, void* adj_out)
 {
     if (!h || !theta_t || !theta_t1 || !adj_in || !adj_out) return fail(LBM_ERR_ARG, "NULL argument");
     if (adj_in == adj_out) return fail(LBM_ERR_ARG, "adj_in and adj_out must differ");
-    lbm::AdjArgs a;
-    a.prob = h->dprob;
-    a.theta_t = theta_t;
-    a.theta_t1 = theta_t1;
-    a.adj_in = adj_in;
-    a.adj_out = adj_out;
-    a.wall_buf = nullptr;
-    a.stats = h->dstats;
-    a.ticket = h->dticket;
-    CUDA_TRY(lbm::launch_adj_step(h->precision, a, h->hp, h->stream));
+    CUDA_TRY(lbm::launch_adj_step(h->precision, adj_args(h, theta_t, theta_t1, adj_in, adj_out), h->hp, h->stream));
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_stefan_adjoint_run(lbm_stefan* h, int nsteps, const double* theta_traj, void* adj,
+                                             void* adj_other, int* result_index)
+{
+    if (!h || !adj || !adj_other || !result_index || (!theta_traj && nsteps > 0))
+        return fail(LBM_ERR_ARG, "NULL argument");
+    if (nsteps < 0) return fail(LBM_ERR_ARG, "nsteps must be >= 0");
+    if (adj == adj_other) return fail(LBM_ERR_ARG, "adj and adj_other must differ");
+    const long long plane = (long long)h->hp.ny * h->hp.pitch;
+    void* buf[2] = {adj, adj_other};
+    int cur = 0;
+    for (int s = nsteps - 1; s >= 0; --s) {
+        CUDA_TRY(lbm::launch_adj_step(h->precision,
+                                      adj_args(h, theta_traj + s * plane, theta_traj + (s + 1) * plane, buf[cur],
+                                               buf[cur ^ 1]),
+                                      h->hp, h->stream));
+        cur ^= 1;
+    }
+    *result_index = cur;
     return LBM_OK;
 }
 

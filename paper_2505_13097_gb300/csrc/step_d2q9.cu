@@ -77,25 +77,6 @@ __device__ __forceinline__ void st_rec(double* p, const double (&v)[N])
     }
 }
 
-// value at x-1 (pull along e_x = +1); h = element left of the segment
-template <typename P, int N>
-__device__ __forceinline__ void from_left(const P (&v)[N], P h, int lane, P (&s)[N])
-{
-    P up = __shfl_up_sync(kFull, v[N - 1], 1);
-    s[0] = lane == 0 ? h : up;
-#pragma unroll
-    for (int k = 1; k < N; ++k) s[k] = v[k - 1];
-}
-// value at x+1 (pull along e_x = -1); h = element right of the segment
-template <typename P, int N>
-__device__ __forceinline__ void from_right(const P (&v)[N], P h, int lane, P (&s)[N])
-{
-    P dn = __shfl_down_sync(kFull, v[0], 1);
-    s[N - 1] = lane == 31 ? h : dn;
-#pragma unroll
-    for (int k = 0; k < N - 1; ++k) s[k] = v[k + 1];
-}
-
 // Boundary closures of Sec. 4.2 at one wall node (x, y).  q holds the pulled
 // values (entries of unknown directions are overwritten), u the node's own
 // Omega.  Returns the boundary flux contribution (filled q minus Omega that

@@ -128,7 +128,7 @@ class Stefan:
         check(self.lib.lbm_stefan_set_state(self.h, ptr, dev))
 
     def new_theta_planes(self, n):
-        return torch.zeros((n, self.ny, self.row_stride), dtype=torch.float64, device="cuda")
+        return torch.empty((n, self.ny, self.row_stride), dtype=torch.float64, device="cuda")
 
     def theta_plane(self, plane):
         check(self.lib.lbm_stefan_theta_plane(self.h, ctypes.c_void_p(plane.data_ptr())))
@@ -147,6 +147,15 @@ class Stefan:
                                                ctypes.c_void_p(theta_t1.data_ptr()),
                                                ctypes.c_void_p(adj_in.data_ptr()),
                                                ctypes.c_void_p(adj_out.data_ptr())))
+
+    def adjoint_run(self, traj, adj, adj_other):
+        """len(traj)-1 reverse steps over the recorded planes traj (theta(t0) ..
+        theta(t0+n), one contiguous tensor); returns (result, spare) buffers."""
+        idx = ctypes.c_int()
+        check(self.lib.lbm_stefan_adjoint_run(self.h, int(traj.shape[0]) - 1, ctypes.c_void_p(traj.data_ptr()),
+                                              ctypes.c_void_p(adj.data_ptr()), ctypes.c_void_p(adj_other.data_ptr()),
+                                              ctypes.byref(idx)))
+        return (adj, adj_other) if idx.value == 0 else (adj_other, adj)
 
     def adjoint_finish(self, adj0, g_theta0):
         gw = (ctypes.c_double * 4)()

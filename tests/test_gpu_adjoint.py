@@ -157,3 +157,87 @@ def test_checkpoint_interval_does_not_change_gradient(torch_mod, orc):
     assert a[0] == b[0]
     assert np.max(np.abs(a[1] - b[1])) <= 1e-13 * np.max(np.abs(a[1]))
     assert abs(a[3] - b[3]) <= 1e-12 * abs(a[3])
+
+
+# Shapes for the marching D2Q9 adjoint: several segments (64 columns in the
+# FP32 form, 32 in the FP64 form) with a ragged last one, an east wall in the
+# column right of a segment (nx = 64k + 1), several row tiles with a ragged
+# last one, and rows fewer than a tile.
+ADJ_SHAPES = [(193, 75), (129, 40), (97, 33), (66, 2), (33, 3)]
+ADJ_WALLS = [
+    {"W": (1, 0.9), "E": (1, -0.4), "S": (0, 0.0), "N": (1, 0.2)},
+    {"W": (0, 0.0), "E": (1, 0.6), "S": (1, -0.3), "N": (0, 0.0)},
+]
+
+
+def _adj_case(nx, ny, walls, precision, steps):
+    case = workloads.Case("t", 2, nx, ny, 0.8, 0.03, 0.25, walls, steps, precision)
+    # mushy and saturated regions both present
+    th0 = workloads.random_field((ny, nx), -0.4, 0.4, seed=nx * 1000 + ny)
+    target = workloads.random_field((ny, nx), 0.0, 1.0, seed=nx + 7 * ny)
+    return case, th0, target
+
+
+@pytest.mark.parametrize("shape", ADJ_SHAPES)
+@pytest.mark.parametrize("wi", [0, 1])
+@pytest.mark.parametrize("bb_mode", [0, 1])
+def test_fp64_adjoint_oracle_shapes(torch_mod, orc, shape, wi, bb_mode):
+    nx, ny = shape
+    case, th0, target = _adj_case(nx, ny, ADJ_WALLS[wi], workloads.FP64, 25)
+    L, g0, gw, gs = gpu_grad(torch_mod, case, target, theta0=th0, bb_mode=bb_mode)
+    P = orc.Problem(2, nx, ny, tau=case.tau, delta=case.delta, ste=case.ste, walls=case.walls, bb_mode=bb_mode)
+    Lo, g0o, gwo, gso = P.adjoint(th0, case.steps, target)
+    assert abs(L - Lo) <= 1e-10 * abs(Lo)
+    assert np.max(np.abs(g0 - g0o)) <= 1e-9 * np.max(np.abs(g0o))
+    for k in range(4):
+        if case.walls[k_name(k)][0] == 1:
+            assert abs(gw[k] - gwo[k]) <= 1e-9 * max(abs(gwo[k]), 1e-12)
+        else:
+            assert gw[k] == 0.0
+    assert abs(gs - gso) <= 1e-9 * abs(gso)
+
+
+@pytest.mark.parametrize("shape", ADJ_SHAPES)
+@pytest.mark.parametrize("bb_mode", [0, 1])
+def test_fp32_adjoint_oracle_shapes(torch_mod, orc, shape, bb_mode):
+    """FP32 form (FP32 populations and adjoint, interior terms in FP32) against
+    the FP64 oracle adjoint: within 2e-3 of the largest gradient entry."""
+    nx, ny = shape
+    case, th0, target = _adj_case(nx, ny, ADJ_WALLS[0], workloads.FP32, 25)
+    L, g0, gw, gs = gpu_grad(torch_mod, case, target, theta0=th0, bb_mode=bb_mode)
+    P = orc.Problem(2, nx, ny, tau=case.tau, delta=case.delta, ste=case.ste, walls=case.walls, bb_mode=bb_mode)
+    Lo, g0o, gwo, gso = P.adjoint(th0, case.steps, target)
+    assert abs(L - Lo) <= 1e-4 * abs(Lo)
+    assert np.max(np.abs(g0 - g0o)) <= 2e-3 * np.max(np.abs(g0o))
+    for k in range(4):
+        if case.walls[k_name(k)][0] == 1:
+            assert abs(gw[k] - gwo[k]) <= 2e-3 * max(abs(gwo[k]), 1e-12)
+    assert abs(gs - gso) <= 2e-3 * abs(gso)
+
+
+def k_name(k):
+    return "WESN"[k]
+
+
+def test_adjoint_run_matches_single_steps(torch_mod, orc):
+    """lbm_stefan_adjoint_run over a recorded segment equals the same reverse
+    steps issued one at a time (bit for bit)."""
+    from paper_2505_13097_gb300 import solver
+    torch = torch_mod
+    case, th0, target = _adj_case(129, 40, ADJ_WALLS[1], workloads.FP32, 9)
+    S = solver.Stefan.from_case(case)
+    S.set_ic(th0)
+    traj = S.new_theta_planes(case.steps + 1)
+    S.theta_plane(traj[0])
+    S.step_record(case.steps, traj[1:])
+    a = S.new_state_buffer()
+    S.adjoint_seed(traj[-1], torch.tensor(target, device="cuda"), a, want_loss=False)
+    b = a.clone()
+    x, y = S.new_state_buffer(), S.new_state_buffer()
+    res, _ = S.adjoint_run(traj, a, x)
+    for s in range(case.steps - 1, -1, -1):
+        S.adjoint_step(traj[s], traj[s + 1], b, y)
+        b, y = y, b
+    torch.cuda.synchronize()
+    assert torch.equal(res, b)
+    S.close()
