@@ -2,6 +2,7 @@
 // library.  Nothing here is part of the C ABI (see include/lbm_stefan.h).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -91,6 +92,17 @@ struct StepArgs {
     unsigned int* job_count; // number of jobs; reset by the job kernel
 };
 
+// TMA descriptors of the single-problem FP32 D2Q9 step: state[0], state[1]
+// as 3-D tensors (column over `pitch`, row y + 1 over ny + 2 rows, plane 0..8);
+// a load copies (kTmaW + 2 kTmaHalo) columns x 1 row x 9 planes.
+constexpr int kTmaW = 128;               // columns per block (one node per consumer thread)
+constexpr int kTmaHalo = 4;              // extra loaded columns on each side (16 bytes)
+struct TmaMaps {
+    CUtensorMap load[2];
+    int nsegs;                           // pitch / kTmaW column strips
+    int nparts;                          // row ranges per strip; grid = nsegs * nparts
+};
+
 // Per-launch arguments of the Newton job kernel (runs after every D2Q9 step).
 struct JobArgs {
     const Problem* probs;
@@ -133,6 +145,8 @@ constexpr int kAdjTileH = 32;  // default rows per warp tile of the D2Q9 adjoint
 cudaError_t launch_d2q9_step(int precision, const StepArgs& a, int grid, cudaStream_t s);
 int d2q9_segment_width(int precision);   // nodes per warp segment
 int d2q9_blocks_per_sm(int precision);   // resident step blocks per SM (persistent grid)
+cudaError_t launch_d2q9_tma(const StepArgs& a, const TmaMaps& m, cudaStream_t s);
+int d2q9_tma_blocks_per_sm();
 cudaError_t launch_newton_jobs(int precision, const JobArgs& a, cudaStream_t s);
 
 // D1Q3 launchers (step_d1q3.cu)

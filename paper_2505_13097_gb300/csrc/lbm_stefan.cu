@@ -10,6 +10,8 @@
 #include "../../include/lbm_stefan.h"
 #include "lbm_internal.h"
 
+#include <cudaTypedefs.h>
+
 #ifndef LBM_PLANE_PAD
 #define LBM_PLANE_PAD 0
 #endif
@@ -71,6 +73,8 @@ struct lbm_stefan {
     int parity = 0;
     bool ic = false;
     int adj_tile_h = lbm::kAdjTileH;   // rows per warp tile of the D2Q9 adjoint
+    bool use_tma = false;              // FP32 D2Q9: the TMA row-pipeline step kernel
+    lbm::TmaMaps tma;
     GraphCache graph;
 };
 
@@ -211,9 +215,14 @@ static cudaError_t launch_one(lbm_stefan* h, int parity, double* rec)
 {
     StepArgs a = single_args(h, parity, rec);
     if (h->p.lattice == LBM_D2Q9) {
-        // one tile per warp; the hardware scheduler balances the short tiles
-        const int grid = (h->hp.ntiles + lbm::kWarpsPerBlock - 1) / lbm::kWarpsPerBlock;
-        cudaError_t e = lbm::launch_d2q9_step(h->precision, a, grid, h->stream);
+        cudaError_t e;
+        if (h->use_tma) {
+            e = lbm::launch_d2q9_tma(a, h->tma, h->stream);
+        } else {
+            // one tile per warp; the hardware scheduler balances the short tiles
+            const int grid = (h->hp.ntiles + lbm::kWarpsPerBlock - 1) / lbm::kWarpsPerBlock;
+            e = lbm::launch_d2q9_step(h->precision, a, grid, h->stream);
+        }
         if (e != cudaSuccess) return e;
         return lbm::launch_newton_jobs(h->precision,
                                        job_args(h->dprob, 1, parity, rec, h->dstats, h->dticket, h->djobs, h->djob_count),
@@ -236,6 +245,69 @@ static double acc_host(const lbm::Acc128& a) { return (double)a.hi * 16.0 + (dou
 
 // ------------------------------------------------------------------ one problem
 
+// ------------------------------------------------------------------ TMA descriptors
+#ifndef LBM_USE_TMA
+#define LBM_USE_TMA 1
+#endif
+#ifndef LBM_TMA_ROWS
+#define LBM_TMA_ROWS 16   // rows per block of the TMA step kernel
+#endif
+
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }();
+    return fn;
+}
+
+// The nine planes of one FP32 state buffer as a tensor (column, row incl. the
+// two ghost rows, plane); box_x columns x 1 row x 9 planes per copy.
+static bool encode_state_map(CUtensorMap* m, void* base, const Problem& hp, int box_x)
+{
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)hp.pitch, (cuuint64_t)hp.ny + 2, 9};
+    const cuuint64_t strides[2] = {(cuuint64_t)hp.pitch * 4, (cuuint64_t)hp.plane * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)box_x, 1, 9};
+    const cuuint32_t elem[3] = {1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, elem, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Row stride of a single problem's state: whole kernel segments; FP32 D2Q9
+// rows hold whole 128-column strips of the TMA step kernel.
+static int state_pitch(int lattice, int precision, int nx)
+{
+    if (lattice != LBM_D2Q9) return round_up(nx, 32);
+    const int segw = lbm::d2q9_segment_width(precision);
+    return round_up(nx, precision == LBM_FP32 ? std::max(segw, lbm::kTmaW) : segw);
+}
+
+// Descriptors and grid of the TMA step kernel; false leaves the warp-tile kernel in use.
+static bool setup_tma(lbm_stefan* h)
+{
+    const Problem& hp = h->hp;
+    if (hp.pitch % lbm::kTmaW != 0 || (hp.plane * 4) % 16 != 0) return false;
+    for (int k = 0; k < 2; ++k)
+        if (!encode_state_map(&h->tma.load[k], hp.state[k], hp, lbm::kTmaW + 2 * lbm::kTmaHalo)) return false;
+    h->tma.nsegs = hp.pitch / lbm::kTmaW;
+    // short row ranges: many blocks in flight hide the latency of each block's
+    // row chain (measured: 16 rows beat 8, 32, 64 and one range per SM slot)
+    h->tma.nparts = std::max(1, (hp.ny + LBM_TMA_ROWS - 1) / LBM_TMA_ROWS);
+    const int per_sm = lbm::d2q9_tma_blocks_per_sm();   // also selects the shared-memory carveout
+#ifdef LBM_TMA_VERBOSE
+    fprintf(stderr, "tma: blocks/SM %d nsegs %d nparts %d\n", per_sm, h->tma.nsegs, h->tma.nparts);
+#endif
+    return per_sm > 0;
+}
+
 extern "C" lbm_status lbm_stefan_create(const lbm_stefan_params* p, void* cuda_stream, lbm_stefan** out)
 {
     if (!p || !out) return fail(LBM_ERR_ARG, "NULL argument");
@@ -256,7 +328,8 @@ extern "C" lbm_status lbm_stefan_create(const lbm_stefan_params* p, void* cuda_s
     h->stream = static_cast<cudaStream_t>(cuda_stream);
     const int q = p->lattice == LBM_D2Q9 ? 9 : 3;
     const int segw = p->lattice == LBM_D2Q9 ? lbm::d2q9_segment_width(p->precision) : 32;
-    const int pitch = round_up(p->nx, segw);
+    const bool tma = LBM_USE_TMA && p->lattice == LBM_D2Q9 && p->precision == LBM_FP32;
+    const int pitch = state_pitch(p->lattice, p->precision, p->nx);
     fill_problem(h->hp, q, p->nx, p->ny, pitch, p->tau, p->delta, p->ste, p->newton_tol, p->newton_max_iter,
                  p->bb_mode, 16, segw, p->precision);
     h->state_bytes = (size_t)q * h->hp.plane * h->elem;
@@ -279,6 +352,7 @@ extern "C" lbm_status lbm_stefan_create(const lbm_stefan_params* p, void* cuda_s
     h->hp.state[0] = bufs[0];
     h->hp.state[1] = bufs[1];
     h->hp.stats = 0;
+    if (e == cudaSuccess && tma) h->use_tma = setup_tma(h);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         lbm_stefan_destroy(h);
@@ -998,7 +1072,7 @@ extern "C" lbm_status lbm_stefan_step_d2q9_noalloc(const lbm_stefan_params* p, c
 
     const int segw = lbm::d2q9_segment_width(p->precision);
     Problem hp;
-    fill_problem(hp, 9, p->nx, p->ny, round_up(p->nx, segw), p->tau, p->delta, p->ste, p->newton_tol,
+    fill_problem(hp, 9, p->nx, p->ny, state_pitch(LBM_D2Q9, p->precision, p->nx), p->tau, p->delta, p->ste, p->newton_tol,
                  p->newton_max_iter, p->bb_mode, 16, segw, p->precision);
     for (int w = 0; w < 4; ++w) {
         hp.wall_kind[w] = wall_kind[w];

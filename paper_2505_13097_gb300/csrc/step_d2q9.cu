@@ -66,6 +66,7 @@ __device__ __forceinline__ void stv_n(float* p, const float (&v)[4]) { *reinterp
 __device__ __forceinline__ void stv_n(float* p, const float (&v)[2]) { *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]); }
 __device__ __forceinline__ void stv_n(double* p, const double (&v)[2]) { *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]); }
 __device__ __forceinline__ void stv_n(double* p, const double (&v)[1]) { *p = v[0]; }
+__device__ __forceinline__ void stv_n(float* p, const float (&v)[1]) { *p = v[0]; }
 template <int N>
 __device__ __forceinline__ void st_rec(double* p, const double (&v)[N])
 {
@@ -352,16 +353,24 @@ __device__ __forceinline__ void lds<double>(const double* p, double (&v)[2])
 // Everything of one row after the pulls: wall closures, moments, the exact
 // saturated branch, deferral of Newton nodes to the job list, relaxation and
 // stores (Omega~_i = (1-omega) q_i + w_i c with c = theta' - (1-omega) m0).
-template <typename P, int N, bool REC, bool EDGE>
+// Row outputs: straight to the plane rows in global memory, or to a row buffer
+// in shared memory that a TMA bulk store writes out.
+template <typename P, int N>
+struct GlobalRowOut {
+    P* row;          // dst + (y + 1) * pitch + x0
+    long long pl;
+    __device__ __forceinline__ void store(int i, const P (&o)[N]) const { stv_n(row + i * pl, o); }
+};
+
+template <typename P, int N, bool REC, bool EDGE, typename Out>
 __device__ __forceinline__ void row_update(const Problem& pb, int y, int x0, int lane, P (&qf)[9][N], const P (&u0)[N],
                                            const P (&u1)[N], const P (&u2)[N], const P (&u3)[N], const P (&u4)[N],
                                            const P (&u5)[N], const P (&u6)[N], const P (&u7)[N], const P (&u8)[N],
-                                           P* __restrict__ dst, double* __restrict__ rec, Acc<P>& acc, TileSums& ts,
+                                           const Out& out, double* __restrict__ rec, Acc<P>& acc, TileSums& ts,
                                            DevStats* st, int pi, NewtonJob* jobs, unsigned int* job_count, const P omc,
                                            const float om_f, const double omc_d, const P (&wP)[3], const float thr_f,
                                            const int nx, const int ny)
 {
-    const long long pl = pb.plane;
     const long long pitch = pb.pitch;
     P c[N];          // per node: theta' - (1-omega) m0, rounded to P
     double thn[REC ? N : 1];
@@ -405,17 +414,28 @@ __device__ __forceinline__ void row_update(const Problem& pb, int y, int x0, int
     }
 
     bool any_newton = false;
+    float row_m0 = 0.f;   // FP32 form: sum of theta' = m0 over this lane's saturated nodes
 #pragma unroll
     for (int k = 0; k < N; ++k) {
         const int x = x0 + k;
         const bool valid = !EDGE || x < nx;
-        m0_init(m0[k]);
-        // small weights first
-#pragma unroll
-        for (int i = 8; i >= 0; --i) m0_add(m0[k], qf[i][k]);
         const P u[9] = {u0[k], u1[k], u2[k], u3[k], u4[k], u5[k], u6[k], u7[k], u8[k]};
         const float tf = approx_sum<P>(u);
-        const float mf = m0_f(m0[k]);
+        float mf;
+        if constexpr (sizeof(P) == 4) {
+            // FP32 form: a plain FP32 sum (small weights first) decides saturation and
+            // gives theta' = m0 there, to the rounding of the stored populations; the
+            // float-float sum is formed only where it is needed (Newton and
+            // Dirichlet nodes)
+            mf = 0.f;
+#pragma unroll
+            for (int i = 8; i >= 0; --i) mf += qf[i][k];
+        } else {
+            m0_init(m0[k]);
+#pragma unroll
+            for (int i = 8; i >= 0; --i) m0_add(m0[k], qf[i][k]);
+            mf = m0_f(m0[k]);
+        }
         const float marg = 1e-5f * (1.0f + fabsf(tf));
         const bool sat_liq = tf >= thr_f + marg && mf >= thr_f + marg;
         const bool sat_sol = tf <= -thr_f - marg && mf <= -thr_f - marg;
@@ -431,7 +451,10 @@ __device__ __forceinline__ void row_update(const Problem& pb, int y, int x0, int
             const int wk = wall_k[k];
             ts.dir_count[wk] += 1;
             if constexpr (sizeof(P) == 4) {
-                const ff& mm = m0[k];
+                ff mm;
+                m0_init(mm);
+#pragma unroll
+                for (int i = 8; i >= 0; --i) ff_add(mm, qf[i][k]);
                 const float oc = (float)omc;
                 c[k] = (P)((pb.wall_th_hi[wk] - oc * mm.hi) + (pb.wall_th_lo[wk] - oc * mm.lo));
                 acc.add_ff(ff{pb.wall_th_hi[wk], pb.wall_th_lo[wk]});
@@ -443,10 +466,9 @@ __device__ __forceinline__ void row_update(const Problem& pb, int y, int x0, int
         } else if (!newton_k[k]) {
             // saturated: theta' = m0, no source; c = omega * m0
             if constexpr (sizeof(P) == 4) {
-                const ff& mm = m0[k];
-                c[k] = (P)__fmaf_rn(om_f, mm.hi, om_f * mm.lo);
-                acc.add_ff(mm);
-                if constexpr (REC) thn[k] = ff_to_double(mm);
+                c[k] = (P)(om_f * mf);
+                row_m0 += mf;
+                if constexpr (REC) thn[k] = (double)mf;
             } else {
                 const double md = m0_d(m0[k]);
                 c[k] = (P)(pb.omega * md);
@@ -456,6 +478,7 @@ __device__ __forceinline__ void row_update(const Problem& pb, int y, int x0, int
             ts.liquid += sat_liq ? 1 : 0;
         }
     }
+    if constexpr (sizeof(P) == 4) acc.add_ff(ff{row_m0, 0.f});
     if (__any_sync(kFull, any_newton)) {
         // The local Newton solve of these nodes is deferred to the job kernel,
         // which spreads the FP64 work of the front band over the whole GPU:
@@ -482,11 +505,14 @@ __device__ __forceinline__ void row_update(const Problem& pb, int y, int x0, int
             jb.prob = pi;
             jb.node = y * nx + x0 + k;
             if constexpr (sizeof(P) == 4) {
-                ff t;
+                ff t, mm;
                 m0_init(t);
+                m0_init(mm);
 #pragma unroll
-                for (int i = 8; i >= 0; --i) ff_add(t, u[i]);
-                const ff& mm = m0[k];
+                for (int i = 8; i >= 0; --i) {
+                    ff_add(t, u[i]);
+                    ff_add(mm, qf[i][k]);
+                }
                 float* pm = reinterpret_cast<float*>(&jb.m0);
                 float* pt = reinterpret_cast<float*>(&jb.theta);
                 pm[0] = mm.hi; pm[1] = mm.lo;
@@ -506,14 +532,13 @@ __device__ __forceinline__ void row_update(const Problem& pb, int y, int x0, int
     }
 
     // Omega~_i = (1-omega) q_i + w_i c
-    P* drow = dst + (long long)(y + 1) * pitch + x0;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const P wi = i == 0 ? wP[0] : (i <= 4 ? wP[1] : wP[2]);
         P o[N];
 #pragma unroll
         for (int k = 0; k < N; ++k) o[k] = newton_k[k] ? qf[i][k] : fma(omc, qf[i][k], wi * c[k]);
-        stv_n(drow + i * pl, o);
+        out.store(i, o);
     }
     if constexpr (REC) {
         st_rec<N>(rec + (long long)y * pitch + x0, thn);
@@ -619,7 +644,8 @@ __device__ __forceinline__ void d2q9_tile(const Problem& pb, const P* __restrict
             if (rn <= yb) ring_load<P>(ring + ((rn + 1) % kStages) * R::SLOT, src, pl, pitch, rn, segx, lane, has_left, has_right);
             cp_async_commit();
         }
-        row_update<P, N, REC, true>(pb, y, x0, lane, qf, u0, u1, u2, u3, u4, u5, u6, u7, u8, dst, rec, acc, ts, st, pi,
+        row_update<P, N, REC, true>(pb, y, x0, lane, qf, u0, u1, u2, u3, u4, u5, u6, u7, u8,
+                                    GlobalRowOut<P, N>{dst + (long long)(y + 1) * pitch + x0, pl}, rec, acc, ts, st, pi,
                                     jobs, job_count, omc, om_f, omc_d, wP, thr_f, nx, ny);
 
     }
@@ -742,12 +768,12 @@ __device__ __forceinline__ void d2q9_tile_direct(const Problem& pb, const P* __r
         }
         if (seg_interior && y > 0 && y < ny - 1)
             row_update<P, N, REC, false>(pb, y, x0, lane, qf, cur.r0, cur.r1, cur.c2, cur.r3, cu4, cur.c5, cur.c6, cu7,
-                                         cu8, dst, rec, acc, ts, st, pi, jobs, job_count, omc, om_f, omc_d, wP, thr_f,
-                                         nx, ny);
+                                         cu8, GlobalRowOut<P, N>{dst + (long long)(y + 1) * pitch + x0, pl}, rec, acc,
+                                         ts, st, pi, jobs, job_count, omc, om_f, omc_d, wP, thr_f, nx, ny);
         else
             row_update<P, N, REC, true>(pb, y, x0, lane, qf, cur.r0, cur.r1, cur.c2, cur.r3, cu4, cur.c5, cur.c6, cu7,
-                                        cu8, dst, rec, acc, ts, st, pi, jobs, job_count, omc, om_f, omc_d, wP, thr_f,
-                                        nx, ny);
+                                        cu8, GlobalRowOut<P, N>{dst + (long long)(y + 1) * pitch + x0, pl}, rec, acc,
+                                        ts, st, pi, jobs, job_count, omc, om_f, omc_d, wP, thr_f, nx, ny);
         // roll the register window
 #pragma unroll
         for (int k = 0; k < N; ++k) { up2[k] = cur.c2[k]; cu4[k] = cur.n4[k]; cu7[k] = cur.n7[k]; cu8[k] = cur.n8[k]; }
@@ -764,6 +790,46 @@ __device__ __forceinline__ void d2q9_tile_direct(const Problem& pb, const P* __r
 #ifndef LBM_STEP_DIRECT
 #define LBM_STEP_DIRECT 1
 #endif
+
+// A warp's partial sums in a fixed lane order, then exact fixed-point atomics;
+// node counts go to integer counters (the publisher adds their phi/Ste terms).
+template <typename P>
+__device__ __forceinline__ void flush_tile_sums(const Acc<P>& acc, const TileSums& ts, DevStats* st, int lane)
+{
+    Fx e, f;
+    if constexpr (sizeof(P) == 4) {
+        ff se = acc.s, sf = ts.flux_f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float eh = __shfl_xor_sync(kFull, se.hi, o), el = __shfl_xor_sync(kFull, se.lo, o);
+            const float fh = __shfl_xor_sync(kFull, sf.hi, o), fl = __shfl_xor_sync(kFull, sf.lo, o);
+            ff_add(se, eh);
+            se.lo += el;
+            ff_add(sf, fh);
+            sf.lo += fl;
+        }
+        e = float_to_fixed(se.hi);
+        fx_add(e, float_to_fixed(se.lo));
+        f = float_to_fixed(sf.hi);
+        fx_add(f, float_to_fixed(sf.lo));
+    } else {
+        e = to_fixed(warp_sum(acc.get()));
+        f = to_fixed(warp_sum(ts.flux));
+    }
+    const int nl = warp_sum_i(ts.liquid);
+    int nd[4];
+#pragma unroll
+    for (int w = 0; w < 4; ++w) nd[w] = warp_sum_i(ts.dir_count[w]);
+    if (lane == 0) {
+        acc_add_fx(&st->cur_energy, e);
+        acc_add_fx(&st->cur_flux, f);
+        if (nl) atomicAdd(&st->cur_liquid, (unsigned long long)nl);
+#pragma unroll
+        for (int w = 0; w < 4; ++w)
+            if (nd[w]) atomicAdd(&st->cur_dir[w], (unsigned long long)nd[w]);
+    }
+}
+
 
 
 template <typename P, bool REC>
@@ -801,42 +867,186 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, LBM_STEP_MIN_BLOCKS) d2q9
 #else
         d2q9_tile<P, REC>(pb, src, dst, a.rec, seg, ya, yb, acc, ts, st, ring, pi, a.jobs, a.job_count);
 #endif
-        // tile partial sums in a fixed lane order, then exact fixed-point atomics;
-        // node counts go to integer counters (the publisher adds their phi/Ste terms)
-        Fx e, f;
-        if constexpr (sizeof(P) == 4) {
-            ff se = acc.s, sf = ts.flux_f;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float eh = __shfl_xor_sync(kFull, se.hi, o), el = __shfl_xor_sync(kFull, se.lo, o);
-                const float fh = __shfl_xor_sync(kFull, sf.hi, o), fl = __shfl_xor_sync(kFull, sf.lo, o);
-                ff_add(se, eh);
-                se.lo += el;
-                ff_add(sf, fh);
-                sf.lo += fl;
-            }
-            e = float_to_fixed(se.hi);
-            fx_add(e, float_to_fixed(se.lo));
-            f = float_to_fixed(sf.hi);
-            fx_add(f, float_to_fixed(sf.lo));
-        } else {
-            e = to_fixed(warp_sum(acc.get()));
-            f = to_fixed(warp_sum(ts.flux));
-        }
-        const int nl = warp_sum_i(ts.liquid);
-        int nd[4];
-#pragma unroll
-        for (int w = 0; w < 4; ++w) nd[w] = warp_sum_i(ts.dir_count[w]);
-        if (lane == 0) {
-            acc_add_fx(&st->cur_energy, e);
-            acc_add_fx(&st->cur_flux, f);
-            if (nl) atomicAdd(&st->cur_liquid, (unsigned long long)nl);
-#pragma unroll
-            for (int w = 0; w < 4; ++w)
-                if (nd[w]) atomicAdd(&st->cur_dir[w], (unsigned long long)nd[w]);
-        }
+        flush_tile_sums<P>(acc, ts, st, lane);
     }
     // statistics are published by the job kernel that follows every step
+}
+
+// ---------------------------------------------------------------- TMA row pipeline
+// Single-problem FP32 step, warp-specialized.  A block owns a strip of
+// kTmaW = 128 columns and a contiguous range of rows [ya, yb).  A producer
+// warp streams rows of all nine planes into a ring of shared-memory slots
+// with TMA tensor loads (136 columns: four more on each side for the pulls
+// along x; outside the tensor the hardware fills zeros); a load completes on
+// the slot's `full` mbarrier.  Four consumer warps (32 columns each, one node
+// per lane) take the pulled values of row y from the slots of rows y-1, y and
+// y+1 (shared-memory loads at +-1 column, no shuffles), run the row update
+// above, store their outputs straight to global memory, and release the slot
+// of row y-1 on its `empty` mbarrier, which the producer waits on before it
+// reuses the slot.  The consumers are not synchronized with one another, and
+// the ring keeps up to kTmaStages rows in flight per block without holding
+// registers.  Every mbarrier wait is bounded: on a timeout the kernel records
+// LBM_ERR_TIMEOUT, stops, and the producer waits (bounded) for its own copies
+// in flight before it exits.
+#ifndef LBM_TMA_STAGES
+#define LBM_TMA_STAGES 8
+#endif
+constexpr int kTmaStages = LBM_TMA_STAGES;
+constexpr int kTmaBox = kTmaW + 2 * kTmaHalo;                  // 136 loaded columns
+constexpr int kTmaSlot = (9 * kTmaBox * 4 + 127) / 128 * 32;   // floats per slot (128-byte multiple)
+constexpr int kTmaConsumers = kTmaW / 32;                       // consumer warps
+constexpr int kTmaThreads = kTmaW + 32;                         // + the producer warp
+constexpr unsigned kTmaRowBytes = 9u * kTmaBox * 4u;             // bytes one row load delivers
+constexpr int kTmaWaitLimit = 1 << 24;
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* b, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* b)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(b)) : "memory");
+}
+// test_wait: returns at once (try_wait may suspend the thread for a while)
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* b, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok)
+                 : "r"(smem_addr(b)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* b, unsigned parity)
+{
+    for (int i = 0; i < kTmaWaitLimit; ++i)
+        if (mbar_try_wait(b, parity)) return true;
+    return false;
+}
+// rows of all nine planes, box origin (x, row, plane 0)
+__device__ __forceinline__ void tma_load_rows(const CUtensorMap* m, float* dst, unsigned long long* bar, int x, int row)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n"
+        ::"r"(smem_addr(dst)), "l"(m), "r"(x), "r"(row), "r"(0), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+
+template <bool REC>
+__global__ void __launch_bounds__(kTmaThreads) d2q9_tma_kernel(const StepArgs a, const __grid_constant__ TmaMaps m)
+{
+    __shared__ __align__(128) float ring[kTmaStages * kTmaSlot];
+    __shared__ __align__(8) unsigned long long full[kTmaStages];
+    __shared__ __align__(8) unsigned long long empty[kTmaStages];
+
+    const Problem& pb = a.probs[0];
+    DevStats* st = &a.stats[pb.stats];
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int lane = tid & 31;
+    const int nx = pb.nx, ny = pb.ny;
+    const int seg = blockIdx.x % m.nsegs;
+    const int part = blockIdx.x / m.nsegs;
+    const int ya = (int)((long long)ny * part / m.nparts);
+    const int yb = (int)((long long)ny * (part + 1) / m.nparts);
+    const int segx = seg * kTmaW;
+
+    if (tid == 0) {
+        for (int k = 0; k < kTmaStages; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], kTmaConsumers);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+    // row r (ya-1 <= r <= yb) is the k-th load, k = r - ya + 1: slot k % S, use k / S
+
+    if (warp == kTmaConsumers) {
+        // ---- producer
+        if (lane == 0) {
+            const CUtensorMap* lmap = &m.load[a.parity];
+            int last = -1;   // last k issued
+            bool ok = true;
+            for (int r = ya - 1; r <= yb; ++r) {
+                const int k = r - (ya - 1);
+                const int sl = k % kTmaStages;
+                if (k >= kTmaStages && !mbar_wait_bounded(&empty[sl], (unsigned)((k / kTmaStages - 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+                mbar_expect_tx(&full[sl], kTmaRowBytes);
+                tma_load_rows(lmap, ring + sl * kTmaSlot, &full[sl], segx - kTmaHalo, r + 1);
+                last = k;
+            }
+            if (!ok) {
+                atomicExch(&st->error, 4);   // LBM_ERR_TIMEOUT
+                // the copies still in flight land before the block may exit
+                for (int k = max(0, last - kTmaStages + 1); k <= last; ++k)
+                    (void)mbar_wait_bounded(&full[k % kTmaStages], (unsigned)((k / kTmaStages) & 1));
+            }
+        }
+        return;
+    }
+
+    // ---- consumers
+    const int x = segx + tid;
+    const float omc = (float)(1.0 - pb.omega);
+    const float om_f = (float)pb.omega;
+    const double omc_d = 1.0 - pb.omega;
+    const float wP[3] = {(float)d2_w(0), (float)d2_w(1), (float)d2_w(5)};
+    const float thr_f = (float)pb.sat;
+    const int wx0 = segx + warp * 32;   // first column of this warp
+    const bool warp_interior_x = wx0 > 0 && wx0 + 31 < nx - 1;
+    float* dst = static_cast<float*>(pb.state[a.parity ^ 1]);
+    const long long pl = pb.plane;
+    const long long pitch = pb.pitch;
+    Acc<float> acc;
+    TileSums ts;
+    auto wait_row = [&](int r) -> bool {
+        const int k = r - (ya - 1);
+        return mbar_wait_bounded(&full[k % kTmaStages], (unsigned)((k / kTmaStages) & 1));
+    };
+    bool ok = wait_row(ya - 1) && wait_row(ya);
+    for (int y = ya; ok && y < yb; ++y) {
+        ok = wait_row(y + 1);
+        if (!ok) break;
+        const int km = y - 1 - (ya - 1);
+        const float* sm1 = ring + (km % kTmaStages) * kTmaSlot + kTmaHalo + tid;
+        const float* s0 = ring + ((km + 1) % kTmaStages) * kTmaSlot + kTmaHalo + tid;
+        const float* sp1 = ring + ((km + 2) % kTmaStages) * kTmaSlot + kTmaHalo + tid;
+        float u0[1], u1[1], u2[1], u3[1], u4[1], u5[1], u6[1], u7[1], u8[1];
+        u0[0] = s0[0 * kTmaBox]; u1[0] = s0[1 * kTmaBox]; u2[0] = s0[2 * kTmaBox];
+        u3[0] = s0[3 * kTmaBox]; u4[0] = s0[4 * kTmaBox]; u5[0] = s0[5 * kTmaBox];
+        u6[0] = s0[6 * kTmaBox]; u7[0] = s0[7 * kTmaBox]; u8[0] = s0[8 * kTmaBox];
+        float qf[9][1];
+        qf[0][0] = u0[0];
+        qf[1][0] = s0[1 * kTmaBox - 1];    // Omega_1(x - 1, y)
+        qf[3][0] = s0[3 * kTmaBox + 1];    // Omega_3(x + 1, y)
+        qf[2][0] = sm1[2 * kTmaBox];       // Omega_2(x, y - 1)
+        qf[5][0] = sm1[5 * kTmaBox - 1];   // Omega_5(x - 1, y - 1)
+        qf[6][0] = sm1[6 * kTmaBox + 1];   // Omega_6(x + 1, y - 1)
+        qf[4][0] = sp1[4 * kTmaBox];       // Omega_4(x, y + 1)
+        qf[7][0] = sp1[7 * kTmaBox + 1];   // Omega_7(x + 1, y + 1)
+        qf[8][0] = sp1[8 * kTmaBox - 1];   // Omega_8(x - 1, y + 1)
+        // every lane has read the slot of row y - 1: release it to the producer
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[km % kTmaStages]);
+        const GlobalRowOut<float, 1> out{dst + (long long)(y + 1) * pitch + x, pl};
+        if (warp_interior_x && y > 0 && y < ny - 1)
+            row_update<float, 1, REC, false>(pb, y, x, lane, qf, u0, u1, u2, u3, u4, u5, u6, u7, u8, out, a.rec, acc,
+                                             ts, st, 0, a.jobs, a.job_count, omc, om_f, omc_d, wP, thr_f, nx, ny);
+        else
+            row_update<float, 1, REC, true>(pb, y, x, lane, qf, u0, u1, u2, u3, u4, u5, u6, u7, u8, out, a.rec, acc,
+                                            ts, st, 0, a.jobs, a.job_count, omc, om_f, omc_d, wP, thr_f, nx, ny);
+    }
+    if (!ok && lane == 0) atomicExch(&st->error, 4);   // LBM_ERR_TIMEOUT
+    flush_tile_sums<float>(acc, ts, st, lane);
 }
 
 // ---------------------------------------------------------------- Newton jobs
@@ -963,6 +1173,25 @@ cudaError_t launch_d2q9_step(int precision, const StepArgs& a, int grid, cudaStr
     if (grid <= 0) return cudaErrorInvalidValue;
     if (precision == 1) return a.rec ? launch_t<float, true>(a, grid, s) : launch_t<float, false>(a, grid, s);
     return a.rec ? launch_t<double, true>(a, grid, s) : launch_t<double, false>(a, grid, s);
+}
+
+cudaError_t launch_d2q9_tma(const StepArgs& a, const TmaMaps& m, cudaStream_t s)
+{
+    const int grid = m.nsegs * m.nparts;
+    if (grid <= 0) return cudaErrorInvalidValue;
+    if (a.rec) d2q9_tma_kernel<true><<<grid, kTmaThreads, 0, s>>>(a, m);
+    else d2q9_tma_kernel<false><<<grid, kTmaThreads, 0, s>>>(a, m);
+    return cudaGetLastError();
+}
+
+int d2q9_tma_blocks_per_sm()
+{
+    // all of the unified L1 / shared memory as shared memory: five blocks per SM
+    cudaFuncSetAttribute(d2q9_tma_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(d2q9_tma_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, d2q9_tma_kernel<false>, kTmaThreads, 0);
+    return n > 0 ? n : 1;
 }
 
 cudaError_t launch_newton_jobs(int precision, const JobArgs& a, cudaStream_t s)

@@ -51,7 +51,11 @@ def test_batch_equals_single_problems(gpu):
         S.set_ic(c.theta0())
         S.step(97)
         assert np.array_equal(S.theta(), B.theta(k))
-        assert S.stats()["energy"] == B.stats(k)["energy"]
+        # the single FP32 problem runs the TMA row-pipeline kernel, which groups
+        # the float-float partial energy sums differently from the batch kernel:
+        # equal up to the rounding of those partial sums
+        e1, e2 = S.stats()["energy"], B.stats(k)["energy"]
+        assert abs(e1 - e2) <= 1e-9 * abs(e2)
         S.close()
     B.close()
 
