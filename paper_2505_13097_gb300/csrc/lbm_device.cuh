@@ -122,23 +122,27 @@ __device__ __forceinline__ NewtonOut newton_solve(double m0, double theta, doubl
 //  1. FP32 Newton (tanhf) locates the root to FP32 accuracy, x0 (it stops at
 //     FP32 precision or once its updates stop halving).
 //  2. FP64 Newton from x0: one FP64 tanh gives t = tanh(x0/delta), F, F' and
-//     the update d.  Newton's error e after the update is about
-//     |F''| d^2 / (2 F') (F'' = phi2/Ste with phi2 = -t(1-t^2)/delta^2), and
-//     theta' = m0 + (phi(theta) - phi(root))/Ste inherits it as (F' - 1) e;
-//     when |F''| d^2 is below 0.1 tol max(1,|x|) and |d| <= 3e-5 delta,
-//     x0 + d is accepted and phi(x0 + d) comes from the cubic Taylor
-//     expansion (third derivative phi3 = (1-t^2)(3t^2-1)/delta^3; the quartic
-//     remainder is below (d/delta)^4 / 12 < 1e-19).  Otherwise the FP64
-//     iteration goes on.  Iterations of both precisions count against maxit.
+//     the update d = -F/F' (1/F' from an FP32 reciprocal and one FP64 Newton
+//     step: relative error ~1e-14, i.e. ~1e-14 of d).  Newton's error e after
+//     the update is about |F''| d^2 / (2 F') (F'' = phi2/Ste with
+//     phi2 = -t(1-t^2)/delta^2), and theta' = m0 + (phi(theta) - phi(root))/Ste
+//     inherits it as (F' - 1) e; when |F''| d^2 is below 0.1 tol max(1,|x|) and
+//     |d| <= 3e-5 delta, x0 + d is accepted and phi(x0 + d) comes from the
+//     cubic Taylor expansion (third derivative phi3 = (1-t^2)(3t^2-1)/delta^3;
+//     the quartic remainder is below (d/delta)^4 / 12 < 1e-19).  Otherwise the
+//     FP64 iteration goes on.  Iterations of both precisions count against maxit.
 //  3. Anything unexpected (no FP32 convergence, an FP64 update larger than
 //     1e-3 delta) falls back to newton_solve from theta.
-__device__ __forceinline__ NewtonOut newton_mixed(double m0, double theta, double phi_theta, double inv_ste,
-                                                  double inv_delta, double tol, int maxit)
+// The FP32 and derived constants come converted in the Problem: on this GPU
+// every FP64 instruction, conversions included, shares the narrow FP64 pipe.
+__device__ __forceinline__ NewtonOut newton_mixed(double m0, double theta, double phi_theta, const Problem& pb)
 {
-    const float mf = (float)m0, pf = (float)phi_theta, isf = (float)inv_ste, idf = (float)inv_delta;
+    const double inv_ste = pb.inv_ste, inv_delta = pb.inv_delta, tol = pb.tol;
+    const int maxit = pb.maxit;
+    const float mf = (float)m0, pf = (float)phi_theta, isf = pb.inv_ste_f, idf = pb.inv_delta_f;
     float lo = mf + (pf - 1.0f) * isf, hi = mf + pf * isf;
     float x = (float)theta;
-    const float xfloor = (float)(1.0 / inv_delta);
+    const float xfloor = pb.delta_f;
     float step_prev = hi - lo;
     int k = 0;
     // FP32 stage: plain Newton inside the bracket; it stops at FP32 precision or
@@ -166,7 +170,7 @@ __device__ __forceinline__ NewtonOut newton_mixed(double m0, double theta, doubl
         x = xn;
     }
     const bool conv32 = isfinite(x);
-    const double delta = 1.0 / inv_delta;
+    const double delta = pb.delta;
     if (conv32) {
         double xd = (double)x;
         for (int j = 0; j < 3; ++j) {
@@ -176,13 +180,15 @@ __device__ __forceinline__ NewtonOut newton_mixed(double m0, double theta, doubl
             const double F = (xd - m0) + (ph - phi_theta) * inv_ste;
             const double dph = 0.5 * s * inv_delta;
             const double Fp = 1.0 + dph * inv_ste;
-            const double d = -F / Fp;
+            const double r0 = (double)(1.0f / (float)Fp);
+            const double rinv = fma(r0, fma(-Fp, r0, 1.0), r0);
+            const double d = -F * rinv;
             const double ad = fabs(d);
             if (ad > 1e-3 * delta) break;   // FP32 start not close enough: full FP64 solve
             const double x1 = xd + d;
             const double sc = tol * fmax(1.0, fabs(xd));
-            const double p2 = -t * s * inv_delta * inv_delta;                          // phi''
-            const double p3 = s * (3.0 * t * t - 1.0) * inv_delta * inv_delta * inv_delta;  // phi'''
+            const double p2 = -t * s * pb.inv_delta2;                   // second derivative of phi
+            const double p3 = s * (3.0 * t * t - 1.0) * pb.inv_delta3;  // third derivative of phi
             // theta' = m0 + (phi(theta) - phi(x))/Ste carries a root error e as (F' - 1) e,
             // so the test bounds F' e ~ |F''| d^2 / 2, not e alone
             if (ad <= sc || (ad <= 3e-5 * delta && fabs(p2) * inv_ste * d * d <= 0.1 * sc)) {

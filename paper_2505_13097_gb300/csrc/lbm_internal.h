@@ -51,6 +51,10 @@ struct Problem {
     double ste, inv_ste, delta, inv_delta;
     double tol;
     double sat;              // saturation threshold K*delta of the exact-source shortcut
+    // constants of the mixed-precision Newton solve, converted on the host so
+    // that a solve spends no FP64 instruction on them
+    double inv_delta2, inv_delta3;
+    float inv_ste_f, inv_delta_f, delta_f;
     int maxit;
     int bb_mode;
     int wall_kind[4];        // W, E, S, N

@@ -161,6 +161,11 @@ static void fill_problem(Problem& pb, int q, int nx, int ny, int pitch, double t
     pb.delta = delta;
     pb.inv_delta = 1.0 / delta;
     pb.tol = tol;
+    pb.inv_delta2 = pb.inv_delta * pb.inv_delta;
+    pb.inv_delta3 = pb.inv_delta2 * pb.inv_delta;
+    pb.inv_ste_f = (float)pb.inv_ste;
+    pb.inv_delta_f = (float)pb.inv_delta;
+    pb.delta_f = (float)delta;
     pb.sat = saturation_threshold(precision, delta, ste);
     pb.maxit = maxit;
     pb.bb_mode = bb_mode;

@@ -63,7 +63,7 @@ __device__ __forceinline__ NodeOut d1q3_node(const Problem& pb, int x, const P (
             phn = m0 > 0.0 ? 1.0 : 0.0;
         } else {
             const double pth = phi_of(th, pb.inv_delta);
-            NewtonOut nr = newton_mixed(m0, th, pth, pb.inv_ste, pb.inv_delta, pb.tol, pb.maxit);
+            NewtonOut nr = newton_mixed(m0, th, pth, pb);
             r.fail = !nr.ok || !isfinite(nr.root);
             tn = m0 + (pth - nr.phi_root) * pb.inv_ste;
             phn = nr.phi_root;

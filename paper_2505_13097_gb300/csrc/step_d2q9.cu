@@ -1083,7 +1083,7 @@ __global__ void __launch_bounds__(128) newton_jobs_kernel(JobArgs a)
                 th = jb.theta;
             }
             const double pth = phi_of(th, pb.inv_delta);
-            const NewtonOut nr = newton_mixed(m0, th, pth, pb.inv_ste, pb.inv_delta, pb.tol, pb.maxit);
+            const NewtonOut nr = newton_mixed(m0, th, pth, pb);
             if (!nr.ok || !isfinite(nr.root)) atomicOr(&a.stats[sidx].error, 3);
             const double tn = m0 + (pth - nr.phi_root) * pb.inv_ste;
             const P c = (P)(tn - (1.0 - pb.omega) * m0);
@@ -1199,7 +1199,7 @@ cudaError_t launch_newton_jobs(int precision, const JobArgs& a, cudaStream_t s)
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = sms * 4;
+    const int grid = sms * 8;   // 8 x 128 threads per SM: about one pass over ~150k nodes
     if (precision == 1) {
         if (a.rec) newton_jobs_kernel<float, true><<<grid, 128, 0, s>>>(a);
         else newton_jobs_kernel<float, false><<<grid, 128, 0, s>>>(a);
