@@ -102,6 +102,14 @@ lbm_status lbm_stefan_set_ic(lbm_stefan* h, const double* theta0, int on_device)
  * Every step also forms the energy E and the boundary flux on the device. */
 lbm_status lbm_stefan_step(lbm_stefan* h, int nsteps);
 
+/* D2Q9 only: advance nsteps >= 1 steps launched one by one (no graph) with a
+ * CUDA event before, between and after the two kernels of each step, wait for
+ * them, and return the mean device time per step of each kernel in ms:
+ * ms_kernels[0] the stream/collide kernel (the TMA kernel in the FP32 form),
+ * ms_kernels[1] the Newton job kernel.  Same result as lbm_stefan_step; for
+ * measuring each kernel against its roofline.  Synchronizes. */
+lbm_status lbm_stefan_step_timed(lbm_stefan* h, int nsteps, double* ms_kernels);
+
 /* Advance nsteps steps and write theta(t+1), ..., theta(t+nsteps) to
  * theta_traj (device, nsteps planes of ny*row_stride doubles, row_stride from
  * lbm_stefan_layout).  Used to recompute a checkpoint segment for the adjoint. */

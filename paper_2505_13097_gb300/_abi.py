@@ -60,6 +60,7 @@ SIGNATURES = {
     "lbm_stefan_set_bc": (_S, [_V, _I, _I, ctypes.c_double]),
     "lbm_stefan_set_ic": (_S, [_V, _V, _I]),
     "lbm_stefan_step": (_S, [_V, _I]),
+    "lbm_stefan_step_timed": (_S, [_V, _I, _D]),
     "lbm_stefan_step_record": (_S, [_V, _I, _V]),
     "lbm_stefan_sync": (_S, [_V]),
     "lbm_stefan_get_fields": (_S, [_V, _V, _V, _V, _I]),

@@ -459,6 +459,51 @@ extern "C" lbm_status lbm_stefan_step(lbm_stefan* h, int nsteps)
     return LBM_OK;
 }
 
+extern "C" lbm_status lbm_stefan_step_timed(lbm_stefan* h, int nsteps, double* ms_kernels)
+{
+    if (!h || !ms_kernels) return fail(LBM_ERR_ARG, "NULL argument");
+    if (h->p.lattice != LBM_D2Q9) return fail(LBM_ERR_ARG, "kernel timing covers the D2Q9 step");
+    if (nsteps < 1) return fail(LBM_ERR_ARG, "nsteps must be >= 1");
+    if (!h->ic) return fail(LBM_ERR_STATE, "set_ic must come before step_timed");
+    std::vector<cudaEvent_t> ev(2 * (size_t)nsteps + 1, nullptr);
+    lbm_status st = LBM_OK;
+    cudaError_t e = cudaSuccess;
+    for (size_t k = 0; k < ev.size() && e == cudaSuccess; ++k) e = cudaEventCreate(&ev[k]);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], h->stream);
+    for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
+        StepArgs a = single_args(h, h->parity, nullptr);
+        if (h->use_tma) {
+            e = lbm::launch_d2q9_tma(a, h->tma, h->stream);
+        } else {
+            const int grid = (h->hp.ntiles + lbm::kWarpsPerBlock - 1) / lbm::kWarpsPerBlock;
+            e = lbm::launch_d2q9_step(h->precision, a, grid, h->stream);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(ev[2 * k + 1], h->stream);
+        if (e == cudaSuccess)
+            e = lbm::launch_newton_jobs(h->precision,
+                                        job_args(h->dprob, 1, h->parity, nullptr, h->dstats, h->dticket, h->djobs,
+                                                 h->djob_count),
+                                        h->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[2 * k + 2], h->stream);
+        h->parity ^= 1;
+    }
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev.back());
+    double t0 = 0.0, t1 = 0.0;
+    for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
+        float a = 0.f, b = 0.f;
+        e = cudaEventElapsedTime(&a, ev[2 * k], ev[2 * k + 1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[2 * k + 1], ev[2 * k + 2]);
+        t0 += a;
+        t1 += b;
+    }
+    for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
+    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "CUDA error: %s", cudaGetErrorString(e));
+    ms_kernels[0] = t0 / nsteps;
+    ms_kernels[1] = t1 / nsteps;
+    return st;
+}
+
 extern "C" lbm_status lbm_stefan_step_record(lbm_stefan* h, int nsteps, double* traj)
 {
     if (!h || (!traj && nsteps > 0)) return fail(LBM_ERR_ARG, "NULL argument");

@@ -84,6 +84,13 @@ class Stefan:
     def step(self, n=1):
         check(self.lib.lbm_stefan_step(self.h, int(n)))
 
+    def step_timed(self, nsteps):
+        """Advance nsteps D2Q9 steps launch by launch; returns the mean device
+        time per step (ms) of the stream/collide kernel and of the job kernel."""
+        out = (ctypes.c_double * 2)()
+        check(self.lib.lbm_stefan_step_timed(self.h, int(nsteps), ctypes.cast(out, ctypes.POINTER(ctypes.c_double))))
+        return out[0], out[1]
+
     def step_record(self, n, traj):
         """traj: CUDA float64 tensor holding at least n planes of ny x row_stride."""
         if not _is_cuda_tensor(traj) or traj.dtype != torch.float64:

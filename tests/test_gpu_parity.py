@@ -182,6 +182,26 @@ def test_deterministic(gpu):
     assert outs[0][1] == outs[1][1]
 
 
+@pytest.mark.parametrize("precision", [workloads.FP32, workloads.FP64])
+def test_step_timed_matches_step(gpu, precision):
+    """lbm_stefan_step_timed (launch by launch, events between the kernels)
+    advances the state exactly like lbm_stefan_step and reports positive times."""
+    c = workloads.melt_2d(n=300, steps=40, precision=precision)
+    outs = []
+    for timed in (False, True):
+        S = gpu.Stefan.from_case(c)
+        S.set_ic(c.theta0())
+        if timed:
+            k0, k1 = S.step_timed(c.steps)
+            assert k0 > 0.0 and k1 > 0.0
+        else:
+            S.step(c.steps)
+        outs.append((S.theta(), S.stats()["energy"], S.stats()["steps"]))
+        S.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert outs[0][1] == outs[1][1] and outs[0][2] == outs[1][2] == c.steps
+
+
 def test_checkpoint_resume_is_exact(gpu):
     c = workloads.melt_2d(n=200, steps=0)
     S = gpu.Stefan.from_case(c)
