@@ -323,7 +323,7 @@ def run_gpu(args):
     stream = torch.cuda.Stream()
     peak, peak_kind = load_peaks()
 
-    case = workloads.melt_2d()
+    case = workloads.melt_2d() if args.n is None else workloads.melt_2d(n=args.n)
     nodes = case.nx * case.ny
     with ClockSampler(local) as clk:
         ms, st = bench_single(torch, solver, case, args.steps, args.warmup, stream, barrier, args.window_step)
@@ -367,10 +367,11 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "dtype_detail": "FP32 populations and relaxation, FP32 m0 at saturated nodes, float-float moments at Newton and Dirichlet nodes, FP64 Newton and energy sums",
             "data": "synthetic",
-            "config": {"workload": "%s: D2Q9 4096x4096, FP32 populations with FP64 Newton, west wall +1, other "
+            "config": {"workload": "%s: D2Q9 %dx%d, FP32 populations with FP64 Newton, west wall +1, other "
                                    "walls adiabatic, Ste 0.1, delta 0.01, tau 1.0, theta0 -0.2 + U(+-1e-3) seed 0; "
                                    "timed window centred on step %d of the 10,000-step job"
-                                   % (case.name, args.window_step if args.window_step is not None else case.steps // 2),
+                                   % (case.name, case.nx, case.ny,
+                                      args.window_step if args.window_step is not None else case.steps // 2),
                        "l2": "state 1.2 GB > 129 MB L2 (no flush needed)", "parallelism": "replicas" if world > 1 else "1 GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
@@ -408,6 +409,8 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--quick", action="store_true", help="headline only")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
+    ap.add_argument("--n", type=int, default=None,
+                    help="side of the melting workload (default 4096, the benchmark); a profiling aid")
     ap.add_argument("--window-step", type=int, default=None,
                     help="centre the timed window on this step (default: mid-run, step 5,000); a profiling aid")
     args = ap.parse_args()
