@@ -374,7 +374,13 @@ def run_gpu(args):
                                       args.window_step if args.window_step is not None else case.steps // 2),
                        "l2": "state 1.2 GB > 129 MB L2 (no flush needed)", "parallelism": "replicas" if world > 1 else "1 GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         # dram__bytes_read.sum + dram__bytes_write.sum of one launch of this kernel in an
+                         # ncu capture of the 2048^2 workload (282.4 MB for 4.19 M nodes), scaled by the
+                         # node count of the launch (traffic grows with the nodes streamed)
+                         "traffic": 282437376 / (2048 * 2048) * nodes,
+                         "traffic_note": "ncu capture of d2q9_tma_kernel on the 2048^2 melting workload, scaled to "
+                                         "this launch's node count",
                          "bytes_per_node": BYTES_FP32, "units_per_launch": nodes,
                          "kernel": "d2q9_tma_kernel<false>", "kernel_ms": k_step_ms,
                          "job_kernel": "newton_jobs_kernel<float,false>", "job_kernel_ms": k_job_ms,
