@@ -121,16 +121,20 @@ __device__ __forceinline__ NewtonOut newton_solve(double m0, double theta, doubl
 // Mixed-precision form of the same solve (same root, same stopping rule).
 //  1. FP32 Newton (tanhf) locates the root to FP32 accuracy, x0 (it stops at
 //     FP32 precision or once its updates stop halving).
-//  2. FP64 Newton from x0: one FP64 tanh gives t = tanh(x0/delta), F, F' and
-//     the update d = -F/F' (1/F' from an FP32 reciprocal and one FP64 Newton
-//     step: relative error ~1e-14, i.e. ~1e-14 of d).  Newton's error e after
-//     the update is about |F''| d^2 / (2 F') (F'' = phi2/Ste with
-//     phi2 = -t(1-t^2)/delta^2), and theta' = m0 + (phi(theta) - phi(root))/Ste
-//     inherits it as (F' - 1) e; when |F''| d^2 is below 0.1 tol max(1,|x|) and
-//     |d| <= 3e-5 delta, x0 + d is accepted and phi(x0 + d) comes from the
-//     cubic Taylor expansion (third derivative phi3 = (1-t^2)(3t^2-1)/delta^3;
-//     the quartic remainder is below (d/delta)^4 / 12 < 1e-19).  Otherwise the
-//     FP64 iteration goes on.  Iterations of both precisions count against maxit.
+//  2. FP64 step from x0: one FP64 tanh gives t = tanh(x0/delta), F, F', F''
+//     and F''' (F^(k) = phi^(k)/Ste, phi2 = -t(1-t^2)/delta^2,
+//     phi3 = (1-t^2)(3t^2-1)/delta^3), the Newton update dn = -F/F' (1/F' from
+//     an FP32 reciprocal and one FP64 Newton step: relative error ~1e-14) and
+//     Halley's update d = dn / (1 + dn F''/(2F')).  Halley's error e is about
+//     |F''^2/(4F'^2) - F'''/(6F')| |dn|^3, and theta' = m0 + (phi(theta) -
+//     phi(root))/Ste inherits it as (F' - 1) e; when F' e is below
+//     0.1 tol max(1,|x|) and |d| <= 3e-5 delta, x0 + d is accepted and
+//     phi(x0 + d) comes from the cubic Taylor expansion (the quartic remainder
+//     is below (d/delta)^4 / 12 < 1e-19).  From the FP32 start (|dn| ~ 1e-8)
+//     one FP64 evaluation suffices; a plain Newton step would leave F' e ~
+//     |F''| dn^2 / 2, above the tolerance in the middle of the band, and need a
+//     second one.  Otherwise the FP64 iteration goes on.  Iterations of both
+//     precisions count against maxit.
 //  3. Anything unexpected (no FP32 convergence, an FP64 update larger than
 //     1e-3 delta) falls back to newton_solve from theta.
 // The FP32 and derived constants come converted in the Problem: on this GPU
@@ -182,16 +186,22 @@ __device__ __forceinline__ NewtonOut newton_mixed(double m0, double theta, doubl
             const double Fp = 1.0 + dph * inv_ste;
             const double r0 = (double)(1.0f / (float)Fp);
             const double rinv = fma(r0, fma(-Fp, r0, 1.0), r0);
-            const double d = -F * rinv;
-            const double ad = fabs(d);
-            if (ad > 1e-3 * delta) break;   // FP32 start not close enough: full FP64 solve
-            const double x1 = xd + d;
-            const double sc = tol * fmax(1.0, fabs(xd));
+            const double dn = -F * rinv;   // Newton update
+            const double adn = fabs(dn);
+            if (adn > 1e-3 * delta) break;   // FP32 start not close enough: full FP64 solve
             const double p2 = -t * s * pb.inv_delta2;                   // second derivative of phi
             const double p3 = s * (3.0 * t * t - 1.0) * pb.inv_delta3;  // third derivative of phi
-            // theta' = m0 + (phi(theta) - phi(x))/Ste carries a root error e as (F' - 1) e,
-            // so the test bounds F' e ~ |F''| d^2 / 2, not e alone
-            if (ad <= sc || (ad <= 3e-5 * delta && fabs(p2) * inv_ste * d * d <= 0.1 * sc)) {
+            // Halley update d = dn / (1 + dn F''/(2F')), 1/(1 + eps) to second order (accepted only
+            // for |eps| <= 1e-4: the neglected eps^3 |dn| is below 1e-12 |dn|)
+            const double eps = 0.5 * dn * p2 * inv_ste * rinv;
+            const double d = dn * (1.0 - eps + eps * eps);
+            const double ad = fabs(d);
+            const double x1 = xd + d;
+            const double sc = tol * fmax(1.0, fabs(xd));
+            // theta' = m0 + (phi(theta) - phi(x))/Ste carries a root error e as (F' - 1) e;
+            // after the Halley step F' e ~ |F''^2/(4F') - F'''/6| |dn|^3
+            const double g = (0.25 * p2 * p2 * inv_ste * rinv + fabs(p3) * (1.0 / 6.0)) * inv_ste;
+            if (ad <= sc || (ad <= 3e-5 * delta && fabs(eps) <= 1e-4 && g * adn * adn * adn <= 0.1 * sc)) {
                 NewtonOut r;
                 r.root = x1;
                 r.phi_root = ph + d * (dph + d * (0.5 * p2 + d * p3 * (1.0 / 6.0)));

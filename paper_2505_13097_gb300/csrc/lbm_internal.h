@@ -102,9 +102,14 @@ struct StepArgs {
 constexpr int kTmaW = 128;               // columns per block (one node per consumer thread)
 constexpr int kTmaHalo = 4;              // extra loaded columns on each side (16 bytes)
 struct TmaMaps {
-    CUtensorMap load[2];
-    int nsegs;                           // pitch / kTmaW column strips
+    CUtensorMap load[2];                 // single problem
+    int nsegs;                           // pitch / kTmaW column strips (single problem)
     int nparts;                          // row ranges per strip; grid = nsegs * nparts
+    // batches: block b takes tile tiles[b] = (problem, strip, first row, end row)
+    // with the descriptors gmaps[2 * problem + parity] (device memory)
+    const int4* tiles;
+    const CUtensorMap* gmaps;
+    int ntiles;
 };
 
 // Per-launch arguments of the Newton job kernel (runs after every D2Q9 step).

@@ -100,6 +100,10 @@ struct lbm_stefan_batch {
     size_t scratch_elems = 0;
     lbm::NewtonJob* djobs = nullptr;
     unsigned int* djob_count = nullptr;
+    bool use_tma = false;              // FP32: the TMA row-pipeline kernel over a tile table
+    lbm::TmaMaps tma;
+    CUtensorMap* dmaps = nullptr;      // 2 descriptors per problem
+    int4* dtiles = nullptr;
     GraphCache graph;
 };
 
@@ -716,6 +720,57 @@ extern "C" const char* lbm_stefan_last_error(void) { return g_err; }
 
 // ------------------------------------------------------------------ batches
 
+// Descriptors of every problem's two state buffers for the TMA kernel; false
+// leaves the batch on the warp-tile kernel.
+static bool batch_setup_tma(lbm_stefan_batch* b)
+{
+    std::vector<CUtensorMap> maps(2 * (size_t)b->count);
+    for (int k = 0; k < b->count; ++k) {
+        const Problem& hp = b->hp[k];
+        if (hp.pitch % lbm::kTmaW != 0) return false;
+        for (int p = 0; p < 2; ++p)
+            if (!encode_state_map(&maps[2 * k + p], hp.state[p], hp, lbm::kTmaW + 2 * lbm::kTmaHalo)) return false;
+    }
+    if (cudaMalloc(&b->dmaps, sizeof(CUtensorMap) * maps.size()) != cudaSuccess ||
+        cudaMemcpy(b->dmaps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return lbm::d2q9_tma_blocks_per_sm() > 0;   // also selects the shared-memory carveout
+}
+
+// TMA tiles: every problem's 128-column strips cut into row ranges of about
+// `rows` rows; schedule 1 puts the largest problems first.
+static lbm_status batch_build_tma_tiles(lbm_stefan_batch* b, int rows, int schedule)
+{
+    std::vector<int> order(b->count);
+    for (int k = 0; k < b->count; ++k) order[k] = k;
+    if (schedule == 1)
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+            return (long long)b->hp[x].nx * b->hp[x].ny > (long long)b->hp[y].nx * b->hp[y].ny;
+        });
+    std::vector<int4> tiles;
+    for (int k : order) {
+        const Problem& pb = b->hp[k];
+        const int nsegs = pb.pitch / lbm::kTmaW;
+        const int nparts = std::max(1, (pb.ny + rows - 1) / rows);
+        for (int part = 0; part < nparts; ++part)
+            for (int seg = 0; seg < nsegs; ++seg)
+                tiles.push_back(make_int4(k, seg, (int)((long long)pb.ny * part / nparts),
+                                          (int)((long long)pb.ny * (part + 1) / nparts)));
+    }
+    if (b->dtiles) cudaFree(b->dtiles);
+    b->dtiles = nullptr;
+    CUDA_TRY(cudaMalloc(&b->dtiles, sizeof(int4) * tiles.size()));
+    CUDA_TRY(cudaMemcpy(b->dtiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice));
+    b->tma.tiles = b->dtiles;
+    b->tma.gmaps = b->dmaps;
+    b->tma.ntiles = (int)tiles.size();
+    b->tma.nsegs = 1;
+    b->tma.nparts = 1;
+    return LBM_OK;
+}
+
 static lbm_status batch_build_schedule(lbm_stefan_batch* b, int tile_h, int schedule)
 {
     const int segw = lbm::d2q9_segment_width(b->precision);
@@ -754,6 +809,10 @@ static lbm_status batch_build_schedule(lbm_stefan_batch* b, int tile_h, int sche
     b->tile_h = tile_h;
     b->schedule = schedule;
     b->graph.reset();
+    if (b->use_tma) {
+        lbm_status s = batch_build_tma_tiles(b, tile_h, schedule);
+        if (s != LBM_OK) return s;
+    }
     // persistent grid: as many blocks as fit on the GPU at once
     int dev = 0, sms = 0, per_sm = 0;
     CUDA_TRY(cudaGetDevice(&dev));
@@ -776,7 +835,8 @@ static cudaError_t batch_launch_one(lbm_stefan_batch* b, int parity)
     a.ticket = b->dticket;
     a.jobs = b->djobs;
     a.job_count = b->djob_count;
-    cudaError_t e = lbm::launch_d2q9_step(b->precision, a, b->grid, b->stream);
+    cudaError_t e = b->use_tma ? lbm::launch_d2q9_tma(a, b->tma, b->stream)
+                               : lbm::launch_d2q9_step(b->precision, a, b->grid, b->stream);
     if (e != cudaSuccess) return e;
     return lbm::launch_newton_jobs(b->precision,
                                    job_args(b->dprobs, b->count, parity, nullptr, b->dstats, b->dticket, b->djobs,
@@ -814,8 +874,8 @@ extern "C" lbm_status lbm_stefan_batch_create(int count, const lbm_stefan_proble
             return s;
         }
         Problem& pb = b->hp[k];
-        fill_problem(pb, 9, p.nx, p.ny, round_up(p.nx, segw), p.tau, p.delta, p.ste, newton_tol, newton_max_iter,
-                     LBM_BB_MIRROR, 16, segw, precision);
+        fill_problem(pb, 9, p.nx, p.ny, state_pitch(LBM_D2Q9, precision, p.nx), p.tau, p.delta, p.ste, newton_tol,
+                     newton_max_iter, LBM_BB_MIRROR, 16, segw, precision);
         for (int w = 0; w < 4; ++w) {
             pb.wall_kind[w] = p.wall_kind[w];
             pb.wall_theta[w] = p.wall_theta[w];
@@ -850,6 +910,7 @@ extern "C" lbm_status lbm_stefan_batch_create(int count, const lbm_stefan_proble
         b->hp[k].state[1] = base + sz;
         base += 2 * sz;
     }
+    if (LBM_USE_TMA && precision == LBM_FP32) b->use_tma = batch_setup_tma(b);
     lbm_status s = batch_build_schedule(b, 16, 1);
     if (s != LBM_OK) {
         lbm_stefan_batch_destroy(b);
@@ -1045,6 +1106,8 @@ extern "C" void lbm_stefan_batch_destroy(lbm_stefan_batch* b)
     cudaFree(b->dscratch);
     cudaFree(b->djobs);
     cudaFree(b->djob_count);
+    cudaFree(b->dmaps);
+    cudaFree(b->dtiles);
     delete b;
 }
 

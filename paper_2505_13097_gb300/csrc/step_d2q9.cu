@@ -947,16 +947,30 @@ __global__ void __launch_bounds__(kTmaThreads) d2q9_tma_kernel(const StepArgs a,
     __shared__ __align__(8) unsigned long long full[kTmaStages];
     __shared__ __align__(8) unsigned long long empty[kTmaStages];
 
-    const Problem& pb = a.probs[0];
+    int pi, seg, ya, yb;
+    const CUtensorMap* lmap;
+    if (m.tiles) {
+        const int4 t = m.tiles[blockIdx.x];
+        pi = t.x;
+        seg = t.y;
+        ya = t.z;
+        yb = t.w;
+        lmap = &m.gmaps[2 * pi + a.parity];
+    } else {
+        pi = 0;
+        seg = blockIdx.x % m.nsegs;
+        const int part = blockIdx.x / m.nsegs;
+        const int nyp = a.probs[0].ny;
+        ya = (int)((long long)nyp * part / m.nparts);
+        yb = (int)((long long)nyp * (part + 1) / m.nparts);
+        lmap = &m.load[a.parity];
+    }
+    const Problem& pb = a.probs[pi];
     DevStats* st = &a.stats[pb.stats];
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
     const int lane = tid & 31;
     const int nx = pb.nx, ny = pb.ny;
-    const int seg = blockIdx.x % m.nsegs;
-    const int part = blockIdx.x / m.nsegs;
-    const int ya = (int)((long long)ny * part / m.nparts);
-    const int yb = (int)((long long)ny * (part + 1) / m.nparts);
     const int segx = seg * kTmaW;
 
     if (tid == 0) {
@@ -972,7 +986,6 @@ __global__ void __launch_bounds__(kTmaThreads) d2q9_tma_kernel(const StepArgs a,
     if (warp == kTmaConsumers) {
         // ---- producer
         if (lane == 0) {
-            const CUtensorMap* lmap = &m.load[a.parity];
             int last = -1;   // last k issued
             bool ok = true;
             for (int r = ya - 1; r <= yb; ++r) {
@@ -1042,10 +1055,10 @@ __global__ void __launch_bounds__(kTmaThreads) d2q9_tma_kernel(const StepArgs a,
         const GlobalRowOut<float, 1> out{dst + (long long)(y + 1) * pitch + x, pl};
         if (warp_interior_x && y > 0 && y < ny - 1)
             row_update<float, 1, REC, false>(pb, y, x, lane, qf, u0, u1, u2, u3, u4, u5, u6, u7, u8, out, a.rec, acc,
-                                             ts, st, 0, a.jobs, a.job_count, omc, om_f, omc_d, wP, thr_f, nx, ny);
+                                             ts, st, pi, a.jobs, a.job_count, omc, om_f, omc_d, wP, thr_f, nx, ny);
         else
             row_update<float, 1, REC, true>(pb, y, x, lane, qf, u0, u1, u2, u3, u4, u5, u6, u7, u8, out, a.rec, acc,
-                                            ts, st, 0, a.jobs, a.job_count, omc, om_f, omc_d, wP, thr_f, nx, ny);
+                                            ts, st, pi, a.jobs, a.job_count, omc, om_f, omc_d, wP, thr_f, nx, ny);
     }
     if (!ok && lane == 0) atomicExch(&st->error, 4);   // LBM_ERR_TIMEOUT
     flush_tile_sums<float>(acc, ts, st, lane);
@@ -1179,7 +1192,7 @@ cudaError_t launch_d2q9_step(int precision, const StepArgs& a, int grid, cudaStr
 
 cudaError_t launch_d2q9_tma(const StepArgs& a, const TmaMaps& m, cudaStream_t s)
 {
-    const int grid = m.nsegs * m.nparts;
+    const int grid = m.tiles ? m.ntiles : m.nsegs * m.nparts;
     if (grid <= 0) return cudaErrorInvalidValue;
     if (a.rec) d2q9_tma_kernel<true><<<grid, kTmaThreads, 0, s>>>(a, m);
     else d2q9_tma_kernel<false><<<grid, kTmaThreads, 0, s>>>(a, m);
