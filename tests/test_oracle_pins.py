@@ -388,3 +388,47 @@ def test_oracle_adjoint_d1q3(orc):
     v = workloads.random_direction((1, n), seed=5)
     fd = (P.loss(th0 + h * v, steps, target) - P.loss(th0 - h * v, steps, target)) / (2 * h)
     assert abs(np.sum(g0 * v) - fd) < 1e-6 * max(1e-3, abs(fd))
+
+
+# ---------------------------------------------------------------- interface position (reading c9)
+def test_front_first_zero_linear_profiles():
+    from oracle.front import first_zero
+    # zero between nodes: theta_i = 0.7 - 0.3 i vanishes at i = 7/3
+    line = 0.7 - 0.3 * np.arange(10)
+    assert abs(first_zero(line) - 7.0 / 3.0) < 1e-15
+    # zero on a node, and a cold wall (freezing from the wall)
+    assert first_zero(1.0 - 0.25 * np.arange(9)) == 4.0
+    assert abs(first_zero(-0.5 + 0.2 * np.arange(9)) - 2.5) < 1e-15
+    # degenerate lines
+    assert first_zero(np.array([0.0, 1.0, -1.0])) == 0.0
+    assert first_zero(np.ones(7)) == 6.0
+
+
+def test_front_integrated_sharp_step_equals_midpoint():
+    from oracle.front import first_zero, integrated
+    for k in (1, 3, 8):
+        line = np.where(np.arange(12) < k, 1.0, -1.0)
+        assert abs(integrated(line, 1e-6) - (k - 0.5)) < 1e-12
+        assert abs(first_zero(line) - (k - 0.5)) < 1e-15
+
+
+def test_front_integrated_smooth_profile():
+    # a sigmoid spread over a few nodes and centred between nodes: the sum of
+    # phi over a long line minus the wall half cell is the centre (Poisson
+    # summation: the error is exponentially small in the width)
+    from oracle.front import integrated
+    x0, delta = 20.3, 0.01
+    line = 0.005 * (x0 - np.arange(60))   # theta/delta = (x0 - i)/2
+    assert abs(integrated(line, delta) - x0) < 1e-6
+
+
+def test_front_walls_and_means():
+    from oracle.front import front_position
+    rng = np.random.Generator(np.random.PCG64(3))
+    th = rng.uniform(-1, 1, size=(5, 7))
+    fz_w, it_w, lw, _ = front_position(th, 0.05, 0)
+    # E wall = W wall of the mirrored field; S wall = W wall of the transpose
+    assert front_position(th[:, ::-1], 0.05, 1)[0] == fz_w
+    assert front_position(th.T, 0.05, 2)[0] == fz_w
+    assert front_position(th.T[::-1, :], 0.05, 3)[0] == fz_w
+    assert abs(fz_w - lw.mean()) < 1e-15 and len(lw) == 5
