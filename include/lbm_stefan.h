@@ -122,6 +122,20 @@ lbm_status lbm_stefan_sync(lbm_stefan* h);
  * each; any of the three may be NULL.  Synchronizes. */
 lbm_status lbm_stefan_get_fields(lbm_stefan* h, double* theta, double* phi, double* H, int on_device);
 
+/* Interface position of the current state (the paper plots it, Sec. 6.1, but
+ * does not define how it is read off the lattice).  Along every lattice line
+ * that starts at `wall` (0 W, 1 E, 2 S, 3 N: rows for W/E, columns for S/N;
+ * D1Q3 has W and E), node 0 on the wall, in node units (multiply by dx):
+ *  - first zero: the first sign change of theta from the wall node's sign,
+ *    linearly interpolated between its two nodes; 0 if theta is 0 on the
+ *    wall node, n - 1 if the sign never changes;
+ *  - integrated: the wall side's phase fraction phi (hot wall) or 1 - phi
+ *    (cold wall) summed along the line, minus the wall node's half cell.
+ * first_zero / integrated receive the means over the lines; line_* (host,
+ * ny or nx doubles, may be NULL) the values per line.  Synchronizes. */
+lbm_status lbm_stefan_front_position(lbm_stefan* h, int wall, double* first_zero, double* integrated,
+                                     double* line_first_zero, double* line_integrated);
+
 /* Energy, flux, Newton statistics and the sticky error.  Synchronizes. */
 lbm_status lbm_stefan_get_stats(lbm_stefan* h, lbm_stefan_stats* out);
 

@@ -65,6 +65,7 @@ SIGNATURES = {
     "lbm_stefan_sync": (_S, [_V]),
     "lbm_stefan_get_fields": (_S, [_V, _V, _V, _V, _I]),
     "lbm_stefan_get_stats": (_S, [_V, ctypes.POINTER(lbm_stefan_stats)]),
+    "lbm_stefan_front_position": (_S, [_V, _I, _D, _D, _D, _D]),
     "lbm_stefan_layout": (_S, [_V, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_int)]),
     "lbm_stefan_get_state": (_S, [_V, _V, _I]),
     "lbm_stefan_set_state": (_S, [_V, _V, _I]),

@@ -87,6 +87,79 @@ __global__ void fields_kernel(const Problem* dprob, int parity, double* theta, d
     }
 }
 
+// Interface position along the lattice lines that start at `wall` (0 W, 1 E,
+// 2 S, 3 N; node 0 on the wall), one warp per line: the first sign change of
+// theta = M0(f) from the wall node's sign, linearly interpolated (node units;
+// 0 if theta is 0 on the wall node, n - 1 if the sign never changes), and the
+// wall side's phase fraction summed along the line minus the wall half cell.
+// out[line] and out[nlines + line].
+template <typename P>
+__global__ void front_kernel(const Problem* dprob, int parity, int wall, double* out)
+{
+    const Problem& pb = *dprob;
+    const P* s = static_cast<const P*>(pb.state[parity]);
+    const bool rows = wall <= 1;
+    const int nlines = rows ? pb.ny : pb.nx;
+    const int n = rows ? pb.nx : pb.ny;
+    const int lane = threadIdx.x & 31;
+    const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int line = w0; line < nlines; line += nw) {
+        auto theta_at = [&](int i) -> double {
+            int x, y;
+            if (wall == 0) { x = i; y = line; }
+            else if (wall == 1) { x = pb.nx - 1 - i; y = line; }
+            else if (wall == 2) { x = line; y = i; }
+            else { x = line; y = pb.ny - 1 - i; }
+            double th = 0.0;
+            for (int k = pb.q - 1; k >= 0; --k) th += (double)s[k * pb.plane + (long long)(y + 1) * pb.pitch + x];
+            return th;
+        };
+        const double t0 = __shfl_sync(kFull, lane == 0 ? theta_at(0) : 0.0, 0);
+        const bool hot = t0 > 0.0;
+        double fz = t0 == 0.0 ? 0.0 : -1.0;   // -1: not found yet
+        double prev_last = t0;                // theta of the node before this chunk
+        double sum = 0.0;
+        for (int c = 0; c < n; c += 32) {
+            const int i = c + lane;
+            const double th = i < n ? theta_at(i) : 0.0;
+            if (i < n) {
+                const double ph = 0.5 + 0.5 * tanh(th * pb.inv_delta);
+                sum += hot ? ph : 1.0 - ph;
+            }
+            if (fz < 0.0) {
+                const bool cross = i >= 1 && i < n && (hot ? th <= 0.0 : th >= 0.0);
+                const unsigned m = __ballot_sync(kFull, cross);
+                double before = __shfl_up_sync(kFull, th, 1);
+                if (lane == 0) before = prev_last;
+                if (m) {
+                    const int first = __ffs(m) - 1;
+                    const double a = __shfl_sync(kFull, before, first);
+                    const double b = __shfl_sync(kFull, th, first);
+                    fz = (double)(c + first - 1) + a / (a - b);
+                }
+            }
+            prev_last = __shfl_sync(kFull, th, 31);
+        }
+        if (fz < 0.0) fz = (double)(n - 1);
+        sum = warp_sum(sum);
+        if (lane == 0) {
+            out[line] = fz;
+            out[nlines + line] = sum - 0.5;
+        }
+    }
+}
+
+cudaError_t launch_front(int precision, const Problem* dprob, const Problem& hp, int parity, int wall, double* out,
+                         cudaStream_t s)
+{
+    const int nlines = wall <= 1 ? hp.ny : hp.nx;
+    const int blocks = (nlines + 3) / 4;
+    if (precision == 1) front_kernel<float><<<blocks, 128, 0, s>>>(dprob, parity, wall, out);
+    else front_kernel<double><<<blocks, 128, 0, s>>>(dprob, parity, wall, out);
+    return cudaGetLastError();
+}
+
 static int grid_for(long long n) { return (int)((n + 255) / 256 < 152 * 16 ? (n + 255) / 256 : 152 * 16); }
 
 cudaError_t launch_init_state(int precision, const Problem* dprob, const Problem& hp, const double* theta0,

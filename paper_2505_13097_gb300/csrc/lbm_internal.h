@@ -167,6 +167,8 @@ bool d1q3_fused_fits(int precision, int nx);
 // Field and state kernels (fields.cu)
 cudaError_t launch_init_state(int precision, const Problem* dprob, const Problem& hp, const double* theta0,
                               int parity, DevStats* st, cudaStream_t s);
+cudaError_t launch_front(int precision, const Problem* dprob, const Problem& hp, int parity, int wall, double* out,
+                         cudaStream_t s);
 cudaError_t launch_fields(int precision, const Problem* dprob, const Problem& hp, int parity, double* theta,
                           double* phi, double* H, double* theta_plane, cudaStream_t s);
 cudaError_t launch_finalize_init(DevStats* st, cudaStream_t s);

@@ -551,6 +551,30 @@ extern "C" lbm_status lbm_stefan_get_fields(lbm_stefan* h, double* theta, double
     return check_stats_error(h, nullptr);
 }
 
+extern "C" lbm_status lbm_stefan_front_position(lbm_stefan* h, int wall, double* first_zero, double* integrated,
+                                                double* line_first_zero, double* line_integrated)
+{
+    if (!h) return fail(LBM_ERR_ARG, "NULL handle");
+    if (wall < 0 || wall > 3) return fail(LBM_ERR_ARG, "wall must be 0..3");
+    if (h->p.lattice == LBM_D1Q3 && wall > 1) return fail(LBM_ERR_ARG, "D1Q3 has only the W and E walls");
+    if (!h->ic) return fail(LBM_ERR_STATE, "set_ic must come before front_position");
+    const int nlines = wall <= 1 ? h->hp.ny : h->hp.nx;
+    CUDA_TRY(lbm::launch_front(h->precision, h->dprob, h->hp, h->parity, wall, h->dscratch, h->stream));
+    std::vector<double> out(2 * (size_t)nlines);
+    CUDA_TRY(cudaMemcpyAsync(out.data(), h->dscratch, sizeof(double) * out.size(), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < nlines; ++k) {
+        a += out[k];
+        b += out[nlines + k];
+    }
+    if (first_zero) *first_zero = a / nlines;
+    if (integrated) *integrated = b / nlines;
+    if (line_first_zero) std::memcpy(line_first_zero, out.data(), sizeof(double) * nlines);
+    if (line_integrated) std::memcpy(line_integrated, out.data() + nlines, sizeof(double) * nlines);
+    return LBM_OK;
+}
+
 extern "C" lbm_status lbm_stefan_get_stats(lbm_stefan* h, lbm_stefan_stats* out)
 {
     if (!h || !out) return fail(LBM_ERR_ARG, "NULL argument");

@@ -84,6 +84,18 @@ class Stefan:
     def step(self, n=1):
         check(self.lib.lbm_stefan_step(self.h, int(n)))
 
+    def front_position(self, wall="W"):
+        """Interface position from `wall` in node units: (mean first zero, mean
+        integrated phase fraction, per-line first zeros, per-line integrated)."""
+        w = _abi.WALLS[wall] if isinstance(wall, str) else int(wall)
+        n = self.ny if w <= 1 else self.nx
+        a, b = ctypes.c_double(), ctypes.c_double()
+        la, lb = np.empty(n), np.empty(n)
+        dp = ctypes.POINTER(ctypes.c_double)
+        check(self.lib.lbm_stefan_front_position(self.h, w, ctypes.byref(a), ctypes.byref(b),
+                                                 la.ctypes.data_as(dp), lb.ctypes.data_as(dp)))
+        return a.value, b.value, la, lb
+
     def step_timed(self, nsteps):
         """Advance nsteps D2Q9 steps launch by launch; returns the mean device
         time per step (ms) of the stream/collide kernel and of the job kernel."""

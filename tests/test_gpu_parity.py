@@ -332,3 +332,29 @@ def test_full_size_melt_2d_properties(gpu):
     fronts = np.argmax(th < 0.0, axis=1)
     assert fronts.max() - fronts.min() <= 1
     assert abs(st["imbalance"]) < 1e-3 * max(1.0, abs(st["flux"])) + 1e-2
+
+
+@pytest.mark.parametrize("lattice,precision,wall", [(2, workloads.FP32, "W"), (2, workloads.FP64, "W"),
+                                                    (2, workloads.FP64, "S"), (1, workloads.FP64, "W")])
+def test_front_position_matches_oracle_definition(gpu, lattice, precision, wall):
+    """lbm_stefan_front_position against the oracle's definition applied to
+    the GPU's own theta field (same field, so the check is the reduction)."""
+    from oracle.front import front_position
+    if lattice == 2:
+        c = workloads.melt_2d(n=300, steps=300, precision=precision)
+        if wall == "S":
+            c = c.scaled(walls={"S": (1, 1.0), "W": (0, 0.0), "E": (0, 0.0), "N": (0, 0.0)})
+    else:
+        c = workloads.melt_1d(n=512, steps=2000)
+    S = gpu.Stefan.from_case(c)
+    S.set_ic(c.theta0())
+    S.step(c.steps)
+    th = S.theta()
+    fz, it, lfz, lit = S.front_position(wall)
+    S.close()
+    w = "WESN".index(wall)
+    ofz, oit, olfz, olit = front_position(th.reshape(c.ny, c.nx), c.delta, w)
+    assert np.max(np.abs(lfz - olfz)) <= 1e-12 * max(1.0, np.max(np.abs(olfz)))
+    assert np.max(np.abs(lit - olit)) <= 1e-10
+    assert abs(fz - ofz) <= 1e-12 * max(1.0, abs(ofz)) and abs(it - oit) <= 1e-10
+    assert 1.0 < ofz < 100.0   # a front has formed near the hot wall
