@@ -6,7 +6,8 @@ no code with the CUDA library in ``paper_2505_13097_gb300``; both only take
 their inputs from the seeded generators in ``paper_2505_13097_gb300.workloads``.
 
 ``irebm_oracle.c`` holds the method (Algorithm 3 of the paper, the boundary
-closures of Sec. 4.2 and the discrete adjoint); this module only marshals
+closures of Sec. 4.2, the discrete adjoint, and the explicit enthalpy based
+method of Algorithm 2 for comparison); this module only marshals
 numpy arrays into it.  ``neumann`` holds the closed-form solution of Sec. 2.
 """
 from __future__ import annotations
@@ -84,6 +85,18 @@ def lib():
             l.orc_loss.argtypes = [_P, _D, ctypes.c_int, _D]
             l.orc_adjoint.restype = ctypes.c_double
             l.orc_adjoint.argtypes = [_P, _D, ctypes.c_int, _D, _D, _D, _D]
+            l.orc_eebm_theta.restype = ctypes.c_double
+            l.orc_eebm_theta.argtypes = [ctypes.c_double, ctypes.c_double]
+            l.orc_eebm_enthalpy.restype = ctypes.c_double
+            l.orc_eebm_enthalpy.argtypes = [ctypes.c_double, ctypes.c_double]
+            l.orc_eebm_init.restype = None
+            l.orc_eebm_init.argtypes = [_P, _D, _D]
+            l.orc_eebm_fields.restype = None
+            l.orc_eebm_fields.argtypes = [_P, _D, _D, _D]
+            l.orc_eebm_step.restype = ctypes.c_int
+            l.orc_eebm_step.argtypes = [_P, _D, _D, ctypes.POINTER(Diag)]
+            l.orc_eebm_run.restype = ctypes.c_int
+            l.orc_eebm_run.argtypes = [_P, _D, ctypes.c_int, _D, _D]
             _lib = l
     return _lib
 
@@ -179,6 +192,46 @@ class Problem:
         if not np.isfinite(L):
             raise MemoryError("oracle adjoint")
         return L, g0, gw, float(gs[0])
+
+
+    # ---- explicit enthalpy based method (EEBM, Algorithm 2): f carries H = M0(f)
+    def eebm_init(self, theta0):
+        f = np.empty((self.q, self.ny, self.nx))
+        lib().orc_eebm_init(ctypes.byref(self.p), _dp(_f64(theta0).reshape(self.shape)), _dp(f))
+        return f
+
+    def eebm_fields(self, f):
+        """(theta, H) of an EEBM state: H = M0(f), theta = Theta(H)."""
+        th, H = np.empty(self.shape), np.empty(self.shape)
+        lib().orc_eebm_fields(ctypes.byref(self.p), _dp(_f64(f)), _dp(th), _dp(H))
+        return th, H
+
+    def eebm_step(self, f, detail=False):
+        f = _f64(f)
+        fn = np.empty_like(f)
+        d = Diag()
+        if lib().orc_eebm_step(ctypes.byref(self.p), _dp(f), _dp(fn), ctypes.byref(d)) < 0:
+            raise MemoryError("oracle step")
+        if not detail:
+            return fn
+        return fn, dict(energy_before=d.energy_before, energy_after=d.energy_after, flux=d.flux)
+
+    def eebm_run(self, theta0, nsteps):
+        """``nsteps`` EEBM steps from the equilibrium state of ``theta0``: (f, theta)."""
+        f = np.empty((self.q, self.ny, self.nx))
+        th = np.empty(self.shape)
+        if lib().orc_eebm_run(ctypes.byref(self.p), _dp(_f64(theta0).reshape(self.shape)), int(nsteps),
+                              _dp(f), _dp(th)) < 0:
+            raise MemoryError("oracle run")
+        return f, th
+
+
+def eebm_theta(H, ste):
+    return lib().orc_eebm_theta(float(H), float(ste))
+
+
+def eebm_enthalpy(theta, ste):
+    return lib().orc_eebm_enthalpy(float(theta), float(ste))
 
 
 def phi(x, delta):

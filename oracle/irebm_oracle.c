@@ -516,3 +516,154 @@ done:
     free(f); free(fn); free(tape_th); free(tape_root); free(fb); free(fbn); free(Ob); free(thb);
     return L;
 }
+
+/* ======================================================================
+ * Explicit enthalpy based method (EEBM), Algorithm 2 and Sec. 3.4 of the
+ * paper: the distributions carry the enthalpy, H = M0(f); the temperature
+ * follows explicitly from H through Theta (no source term, no Newton):
+ *     Theta(H) = H if H < 0,  0 if 0 <= H <= 1/Ste,  H - 1/Ste if H > 1/Ste;
+ * equilibrium f_i^eq = w_i theta (i != 0), f_0^eq = H - (1 - w_0) theta, so
+ * that M0(f^eq) = H; collision Omega_i = f_i - (f_i - f_i^eq)/tau; streaming
+ * f~_i(y) = Omega_i(y - e_i).
+ * Boundary closures (the paper leaves EEBM's to standard techniques): the
+ * same as IREBM's on the streamed distributions, with the Dirichlet target
+ * M0(f~) = H(theta_D) = theta_D + [theta_D > 0]/Ste (the enthalpy of the wall
+ * value; a wall at exactly 0 is taken solid), and bounce-back unchanged.
+ * ====================================================================== */
+double orc_eebm_theta(double H, double ste)
+{
+    if (H < 0.0) return H;
+    if (H > 1.0 / ste) return H - 1.0 / ste;
+    return 0.0;
+}
+
+double orc_eebm_enthalpy(double theta, double ste) { return theta + (theta > 0.0 ? 1.0 / ste : 0.0); }
+
+/* equilibrium state of theta0 (Dirichlet nodes at their wall value) */
+void orc_eebm_init(const orc_params* p, const double* theta0, double* f)
+{
+    int q = lat_q(p), n = p->nx * p->ny, x, y, i, ex, ey;
+    double w, w0;
+    lat_vec(p, 0, &ex, &ey, &w0);
+    for (y = 0; y < p->ny; y++)
+        for (x = 0; x < p->nx; x++) {
+            double th = theta0[y * p->nx + x], td, H;
+            if (node_dirichlet(p, x, y, &td, NULL)) th = td;
+            H = orc_eebm_enthalpy(th, p->ste);
+            for (i = 0; i < q; i++) {
+                lat_vec(p, i, &ex, &ey, &w);
+                f[i * n + y * p->nx + x] = i == 0 ? H - (1.0 - w0) * th : w * th;
+            }
+        }
+}
+
+/* theta = Theta(M0(f)) */
+void orc_eebm_fields(const orc_params* p, const double* f, double* theta, double* H)
+{
+    int q = lat_q(p), n = p->nx * p->ny, k, i;
+    for (k = 0; k < n; k++) {
+        double s = 0.0;
+        for (i = 0; i < q; i++) s += f[i * n + k];
+        if (H) H[k] = s;
+        if (theta) theta[k] = orc_eebm_theta(s, p->ste);
+    }
+}
+
+/* One EEBM step, Algorithm 2, f -> fn; diag (may be NULL): sum of H before
+ * and after, and the boundary flux of H (filled distributions minus the
+ * post-collision ones that leave the lattice). */
+int orc_eebm_step(const orc_params* p, const double* f, double* fn, orc_diag* diag)
+{
+    const int q = lat_q(p), nx = p->nx, ny = p->ny, n = nx * ny;
+    const double omega = 1.0 / p->tau;
+    double* Om = (double*)malloc(sizeof(double) * q * n);
+    double flux = 0.0, e0 = 0.0, e1 = 0.0;
+    int x, y, i, k;
+    int ex[ORC_MAXQ], ey[ORC_MAXQ], opp[ORC_MAXQ];
+    double w[ORC_MAXQ];
+    if (!Om) return -1;
+    for (i = 0; i < q; i++) { lat_vec(p, i, &ex[i], &ey[i], &w[i]); opp[i] = lat_opp(p, i); }
+
+    /* moments, equilibrium and collision */
+    for (k = 0; k < n; k++) {
+        double H = 0.0, th;
+        for (i = 0; i < q; i++) H += f[i * n + k];
+        e0 += H;
+        th = orc_eebm_theta(H, p->ste);
+        for (i = 0; i < q; i++) {
+            const double feq = i == 0 ? H - (1.0 - w[0]) * th : w[i] * th;
+            Om[i * n + k] = f[i * n + k] - (f[i * n + k] - feq) / p->tau;
+        }
+    }
+    (void)omega;
+    for (y = 0; y < ny; y++)
+        for (x = 0; x < nx; x++)
+            for (i = 0; i < q; i++)
+                if (!inside(p, x + ex[i], y + ey[i])) flux -= Om[i * n + y * nx + x];
+
+    /* streaming and the closures of the unknown streamed distributions */
+    for (y = 0; y < ny; y++)
+        for (x = 0; x < nx; x++) {
+            double qv[ORC_MAXQ], td;
+            int known[ORC_MAXQ], nunk = 0;
+            k = y * nx + x;
+            for (i = 0; i < q; i++) {
+                int sx = x - ex[i], sy = y - ey[i];
+                known[i] = inside(p, sx, sy);
+                qv[i] = known[i] ? Om[i * n + sy * nx + sx] : 0.0;
+                if (!known[i]) nunk++;
+            }
+            if (nunk > 0) {
+                if (node_dirichlet(p, x, y, &td, NULL)) {
+                    double rest = orc_eebm_enthalpy(td, p->ste), wu = 0.0;
+                    for (i = 0; i < q; i++) {
+                        if (known[i]) rest -= qv[i];
+                        else wu += w[i];
+                    }
+                    for (i = 0; i < q; i++)
+                        if (!known[i]) qv[i] = w[i] * rest / wu;
+                } else {
+                    for (i = 0; i < q; i++)
+                        if (!known[i]) {
+                            if (p->bb_mode == 0 && known[opp[i]]) qv[i] = qv[opp[i]];
+                            else qv[i] = Om[opp[i] * n + k];
+                        }
+                }
+                for (i = 0; i < q; i++)
+                    if (!known[i]) flux += qv[i];
+            }
+            for (i = 0; i < q; i++) fn[i * n + k] = qv[i];
+        }
+    if (diag) {
+        for (k = 0; k < n; k++)
+            for (i = 0; i < q; i++) e1 += fn[i * n + k];
+        diag->energy_before = e0;
+        diag->energy_after = e1;
+        diag->flux = flux;
+        diag->max_iter = 0;
+        diag->failed = 0;
+    }
+    free(Om);
+    return 0;
+}
+
+/* nsteps EEBM steps from the equilibrium state of theta0: final f and theta */
+int orc_eebm_run(const orc_params* p, const double* theta0, int nsteps, double* f_out, double* theta_out)
+{
+    const int q = lat_q(p), n = p->nx * p->ny;
+    double* a = (double*)malloc(sizeof(double) * q * n);
+    double* b = (double*)malloc(sizeof(double) * q * n);
+    int s;
+    if (!a || !b) { free(a); free(b); return -1; }
+    orc_eebm_init(p, theta0, a);
+    for (s = 0; s < nsteps; s++) {
+        double* t;
+        if (orc_eebm_step(p, a, b, NULL) < 0) { free(a); free(b); return -1; }
+        t = a; a = b; b = t;
+    }
+    if (f_out) memcpy(f_out, a, sizeof(double) * q * n);
+    if (theta_out) orc_eebm_fields(p, a, theta_out, NULL);
+    free(a);
+    free(b);
+    return 0;
+}

@@ -432,3 +432,75 @@ def test_front_walls_and_means():
     assert front_position(th.T, 0.05, 2)[0] == fz_w
     assert front_position(th.T[::-1, :], 0.05, 3)[0] == fz_w
     assert abs(fz_w - lw.mean()) < 1e-15 and len(lw) == 5
+
+
+# ---------------------------------------------------------------- EEBM (Algorithm 2), the comparison method
+def test_eebm_theta_enthalpy_maps():
+    from oracle import eebm_enthalpy, eebm_theta
+    ste = 0.25
+    for th in (-3.0, -1e-9, 1e-9, 0.7, 5.0):
+        H = eebm_enthalpy(th, ste)
+        assert abs(eebm_theta(H, ste) - th) <= 4 * np.spacing(H)
+    for H in (0.0, 1.0, 2.0, 4.0):          # the melting plateau [0, 1/Ste]
+        assert eebm_theta(H, ste) == 0.0
+    assert eebm_theta(4.5, ste) == 0.5 and eebm_theta(-0.5, ste) == -0.5
+
+
+def test_eebm_uniform_state_is_a_fixed_point(orc):
+    P = orc.Problem(2, 9, 7, tau=0.8, ste=0.3)
+    for th in (-0.4, 0.6):
+        f0 = P.eebm_init(np.full((7, 9), th))
+        f = f0
+        for _ in range(5):
+            f = P.eebm_step(f)
+        # H = sum f is re-rounded every step: fixed to the last bits
+        assert np.max(np.abs(f - f0)) <= 1e-15
+
+
+@pytest.mark.parametrize("lattice", [1, 2])
+def test_eebm_conserves_enthalpy_in_a_closed_box(orc, lattice):
+    # link-wise bounce-back on every wall: streaming permutes, collision keeps M0
+    ny = 1 if lattice == 1 else 11
+    P = orc.Problem(lattice, 13, ny, tau=0.7, ste=0.2, bb_mode=1)
+    th0 = np.random.Generator(np.random.PCG64(5)).uniform(-1, 1, size=(ny, 13))
+    f = P.eebm_init(th0)
+    e0 = P.eebm_fields(f)[1].sum()
+    for _ in range(200):
+        f = P.eebm_step(f)
+    assert abs(P.eebm_fields(f)[1].sum() - e0) <= 1e-12 * np.abs(P.eebm_fields(f)[1]).sum()
+
+
+def test_eebm_energy_balance_with_a_dirichlet_wall(orc):
+    P = orc.Problem(2, 12, 9, tau=0.9, ste=0.1, walls={"W": (1, 1.0), "S": (1, -0.5)})
+    f = P.eebm_init(np.full((9, 12), -0.2))
+    for _ in range(30):
+        fn, d = P.eebm_step(f, detail=True)
+        assert abs(d["energy_after"] - d["energy_before"] - d["flux"]) <= 1e-12 * (1 + abs(d["energy_before"]))
+        f = fn
+
+
+def test_eebm_equals_irebm_in_the_solid(orc):
+    # a field that stays below the melting point: EEBM's equilibrium is the
+    # plain one (H = theta) and IREBM's source vanishes (phi = 0 to e^-600),
+    # so both reduce to the same heat-equation LBM through different code
+    walls = {"W": (1, -0.3), "N": (1, -0.9)}
+    P = orc.Problem(2, 14, 10, tau=0.85, delta=0.001, ste=0.5, walls=walls)
+    th0 = np.random.Generator(np.random.PCG64(8)).uniform(-1.0, -0.5, size=(10, 14))
+    _, te = P.eebm_run(th0, 60)
+    _, ti = P.run(th0, 60)
+    assert np.max(np.abs(te - ti)) <= 1e-14
+
+
+def test_eebm_front_follows_the_neumann_solution(orc):
+    # sharp interface: the first zero lies within one node of 2 lambda sqrt(t) (Eq. 2)
+    import math
+    from oracle import neumann
+    from oracle.front import front_position
+    n, steps, tau, ste = 512, 20000, 1.0, 0.1
+    P = orc.Problem(1, n, 1, tau=tau, ste=ste, walls={"W": (1, 1.0)})
+    _, th = P.eebm_run(np.full((1, n), -0.5), steps)
+    dx = 1.0 / (n - 1)
+    t = steps * (tau - 0.5) * dx * dx / 3.0
+    x_exact = 2.0 * neumann.stefan_lambda(ste, -0.5) * math.sqrt(t) / dx
+    fz = front_position(th, 0.01, 0)[0]
+    assert abs(fz - x_exact) <= 1.0
