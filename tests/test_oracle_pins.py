@@ -440,7 +440,7 @@ def test_eebm_theta_enthalpy_maps():
     ste = 0.25
     for th in (-3.0, -1e-9, 1e-9, 0.7, 5.0):
         H = eebm_enthalpy(th, ste)
-        assert abs(eebm_theta(H, ste) - th) <= 4 * np.spacing(H)
+        assert abs(eebm_theta(H, ste) - th) <= 4 * abs(np.spacing(H))
     for H in (0.0, 1.0, 2.0, 4.0):          # the melting plateau [0, 1/Ste]
         assert eebm_theta(H, ste) == 0.0
     assert eebm_theta(4.5, ste) == 0.5 and eebm_theta(-0.5, ste) == -0.5
