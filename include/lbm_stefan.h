@@ -55,6 +55,7 @@ enum { LBM_FP64 = 0, LBM_FP32 = 1 };                           /* population sto
 enum { LBM_WALL_W = 0, LBM_WALL_E = 1, LBM_WALL_S = 2, LBM_WALL_N = 3 };
 enum { LBM_ADIABATIC = 0, LBM_DIRICHLET = 1 };                 /* wall kinds (Sec. 4.2) */
 enum { LBM_BB_MIRROR = 0, LBM_BB_LINK = 1 };                   /* bounce-back forms */
+enum { LBM_IREBM = 0, LBM_EEBM = 1 };                          /* step method (Algorithms 3 and 2) */
 
 typedef struct {
     int lattice;          /* LBM_D1Q3 or LBM_D2Q9 */
@@ -93,6 +94,19 @@ lbm_status lbm_stefan_create(const lbm_stefan_params* p, void* cuda_stream, lbm_
  * included); its value is that of the first Dirichlet wall in W, E, S, N.
  * Call before set_ic so that Dirichlet nodes start at theta_wall. */
 lbm_status lbm_stefan_set_bc(lbm_stefan* h, int wall, int kind, double theta_wall);
+
+/* Step method.  LBM_IREBM (default): Algorithm 3.  LBM_EEBM: the explicit
+ * enthalpy based method of Algorithm 2 (Sec. 3.4), the paper's comparison
+ * scheme, D2Q9 only: the populations carry the enthalpy H = M0(f),
+ * theta = Theta(H) (H below 0, 0 on [0, 1/Ste], H - 1/Ste above), the
+ * equilibrium is w_i theta (i != 0) and H - (1 - w_0) theta (i = 0), no Newton;
+ * the closures act on the streamed populations as for IREBM, a Dirichlet node
+ * holding M0 at the enthalpy of its wall value (theta_D + [theta_D > 0]/Ste);
+ * delta is not used.  For EEBM, get_fields returns theta = Theta(H), phi = the
+ * liquid fraction min(max(Ste H, 0), 1) and H; the energy statistics are the
+ * sum of H; the adjoint calls return LBM_ERR_STATE.  Discards the state: call
+ * lbm_stefan_set_ic afterwards.  LBM_ERR_ARG for an unknown method or D1Q3. */
+lbm_status lbm_stefan_set_method(lbm_stefan* h, int method);
 
 /* Initial state: f_i = w_i theta0 (equilibrium), Dirichlet nodes at their wall
  * value.  theta0 holds nx*ny doubles.  Resets the step counter and stats. */

@@ -17,6 +17,7 @@ LBM_D1Q3, LBM_D2Q9 = 1, 2
 LBM_FP64, LBM_FP32 = 0, 1
 LBM_ADIABATIC, LBM_DIRICHLET = 0, 1
 LBM_BB_MIRROR, LBM_BB_LINK = 0, 1
+LBM_IREBM, LBM_EEBM = 0, 1
 WALLS = {"W": 0, "E": 1, "S": 2, "N": 3}
 
 
@@ -58,6 +59,7 @@ _S = ctypes.c_int   # lbm_status
 SIGNATURES = {
     "lbm_stefan_create": (_S, [ctypes.POINTER(lbm_stefan_params), _V, ctypes.POINTER(_V)]),
     "lbm_stefan_set_bc": (_S, [_V, _I, _I, ctypes.c_double]),
+    "lbm_stefan_set_method": (_S, [_V, _I]),
     "lbm_stefan_set_ic": (_S, [_V, _V, _I]),
     "lbm_stefan_step": (_S, [_V, _I]),
     "lbm_stefan_step_timed": (_S, [_V, _I, _D]),

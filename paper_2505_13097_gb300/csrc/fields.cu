@@ -31,6 +31,16 @@ __global__ void init_state_kernel(const Problem* dprob, const double* __restrict
         const int x = (int)(k % pb.nx), y = (int)(k / pb.nx);
         double th = theta0[k], td;
         if (dirichlet_value(pb, x, y, td)) th = td;
+        if (pb.method == 1) {
+            // EEBM: equilibrium of H = theta + [theta > 0]/Ste (Algorithm 2): w_i theta,
+            // and H - (1 - w_0) theta for i = 0
+            const double H = th + (th > 0.0 ? pb.inv_ste : 0.0);
+            for (int i = 0; i < pb.q; ++i)
+                s[i * pb.plane + (long long)(y + 1) * pb.pitch + x] =
+                    (P)(i == 0 ? H - (1.0 - lat_w(pb.q, 0)) * th : lat_w(pb.q, i) * th);
+            e += H;
+            continue;
+        }
         for (int i = 0; i < pb.q; ++i) s[i * pb.plane + (long long)(y + 1) * pb.pitch + x] = (P)(lat_w(pb.q, i) * th);
         e += th + phi_of(th, pb.inv_delta) * pb.inv_ste;
     }
@@ -52,6 +62,11 @@ __global__ void wall_constants_kernel(Problem* probs, int nprob)
         pb.wall_slope[k] = (float)(0.5 * (1.0 - t) * (1.0 + t) * pb.inv_delta * pb.inv_ste);
     }
     pb.wall_dth_max = (float)(1e-4 * pb.delta);
+    for (int k = 0; k < 4; ++k) {
+        pb.wall_H[k] = pb.wall_theta[k] + (pb.wall_theta[k] > 0.0 ? pb.inv_ste : 0.0);
+        pb.wall_H_hi[k] = (float)pb.wall_H[k];
+        pb.wall_H_lo[k] = (float)(pb.wall_H[k] - (double)pb.wall_H_hi[k]);
+    }
 }
 
 cudaError_t launch_wall_constants(Problem* dprobs, int nprob, cudaStream_t s)
@@ -79,6 +94,16 @@ __global__ void fields_kernel(const Problem* dprob, int parity, double* theta, d
         const int x = (int)(k % pb.nx), y = (int)(k / pb.nx);
         double th = 0.0;
         for (int i = pb.q - 1; i >= 0; --i) th += (double)s[i * pb.plane + (long long)(y + 1) * pb.pitch + x];
+        if (pb.method == 1) {
+            // EEBM: M0 is the enthalpy; theta = Theta(H), liquid fraction min(max(Ste H, 0), 1)
+            const double h = th;
+            th = eebm_theta(h, pb.inv_ste);
+            if (theta) theta[k] = th;
+            if (phi) phi[k] = fmin(fmax(h * pb.ste, 0.0), 1.0);
+            if (H) H[k] = h;
+            if (theta_plane) theta_plane[(long long)y * pb.pitch + x] = th;
+            continue;
+        }
         const double ph = phi_of(th, pb.inv_delta);
         if (theta) theta[k] = th;
         if (phi) phi[k] = ph;
@@ -113,7 +138,7 @@ __global__ void front_kernel(const Problem* dprob, int parity, int wall, double*
             else { x = line; y = pb.ny - 1 - i; }
             double th = 0.0;
             for (int k = pb.q - 1; k >= 0; --k) th += (double)s[k * pb.plane + (long long)(y + 1) * pb.pitch + x];
-            return th;
+            return pb.method == 1 ? eebm_theta(th, pb.inv_ste) : th;
         };
         const double t0 = __shfl_sync(kFull, lane == 0 ? theta_at(0) : 0.0, 0);
         const bool hot = t0 > 0.0;

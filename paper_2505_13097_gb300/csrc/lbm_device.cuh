@@ -57,6 +57,17 @@ __device__ __forceinline__ float approx_float(double d)
 }
 
 // ---------------------------------------------------------------- liquid fraction
+// EEBM (Algorithm 2): temperature of an enthalpy, Theta(H) = H below 0, 0 on
+// the melting plateau [0, 1/Ste], H - 1/Ste above it.
+__device__ __forceinline__ double eebm_theta(double H, double inv_ste)
+{
+    return H < 0.0 ? H : (H > inv_ste ? H - inv_ste : 0.0);
+}
+__device__ __forceinline__ float eebm_theta(float H, float inv_ste)
+{
+    return H < 0.0f ? H : (H > inv_ste ? H - inv_ste : 0.0f);
+}
+
 // phi(x) = (1 + tanh(x/delta))/2 (Sec. 4.1) and phi' = (1 - t)(1 + t)/(2 delta).
 __device__ __forceinline__ double phi_of(double x, double inv_delta) { return 0.5 + 0.5 * tanh(x * inv_delta); }
 

@@ -65,6 +65,9 @@ struct Problem {
     float wall_th_lo[4];
     float wall_slope[4];     // phi'(theta_wall)/Ste = (1 - tanh^2)/(2 delta Ste)
     float wall_dth_max;      // 1e-4 delta: range of the linear phi difference at a Dirichlet node
+    int method;              // 0 IREBM (Algorithm 3), 1 EEBM (Algorithm 2; D2Q9)
+    double wall_H[4];        // EEBM: enthalpy of theta_wall, theta_wall + [theta_wall > 0]/Ste
+    float wall_H_hi[4], wall_H_lo[4];
     int nseg, nstrip, tile_h;
     int tile0;               // first global tile index of this problem
     int ntiles;

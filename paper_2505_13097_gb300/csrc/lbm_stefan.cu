@@ -389,6 +389,17 @@ extern "C" lbm_status lbm_stefan_set_bc(lbm_stefan* h, int wall, int kind, doubl
     return upload_problem(h);
 }
 
+extern "C" lbm_status lbm_stefan_set_method(lbm_stefan* h, int method)
+{
+    if (!h) return fail(LBM_ERR_ARG, "NULL handle");
+    if (method != LBM_IREBM && method != LBM_EEBM) return fail(LBM_ERR_ARG, "method must be 0 (IREBM) or 1 (EEBM)");
+    if (method == LBM_EEBM && h->p.lattice != LBM_D2Q9) return fail(LBM_ERR_ARG, "EEBM is implemented for D2Q9");
+    h->hp.method = method;
+    h->ic = false;   // the state of one method is not a state of the other
+    h->graph.reset();
+    return upload_problem(h);
+}
+
 extern "C" lbm_status lbm_stefan_set_ic(lbm_stefan* h, const double* theta0, int on_device)
 {
     if (!h || !theta0) return fail(LBM_ERR_ARG, "NULL argument");
@@ -634,6 +645,7 @@ extern "C" lbm_status lbm_stefan_theta_plane(lbm_stefan* h, double* plane)
 extern "C" lbm_status lbm_stefan_adjoint_seed(lbm_stefan* h, const double* theta_T, const double* phi_target,
                                               void* adj, double* loss)
 {
+    if (h && h->hp.method != LBM_IREBM) return fail(LBM_ERR_STATE, "the adjoint is that of the IREBM step");
     if (!h || !theta_T || !phi_target || !adj) return fail(LBM_ERR_ARG, "NULL argument");
     CUDA_TRY(cudaMemsetAsync(&h->dstats->g_wall, 0, sizeof(lbm::Acc128) * 6, h->stream));
     CUDA_TRY(lbm::launch_adj_seed(h->precision, h->dprob, h->hp, theta_T, phi_target, adj, h->dstats, h->stream));
@@ -681,6 +693,7 @@ static lbm::AdjArgs adj_args(lbm_stefan* h, const double* theta_t, const double*
 extern "C" lbm_status lbm_stefan_adjoint_step(lbm_stefan* h, const double* theta_t, const double* theta_t1,
                                               const void* adj_in, void* adj_out)
 {
+    if (h && h->hp.method != LBM_IREBM) return fail(LBM_ERR_STATE, "the adjoint is that of the IREBM step");
     if (!h || !theta_t || !theta_t1 || !adj_in || !adj_out) return fail(LBM_ERR_ARG, "NULL argument");
     if (adj_in == adj_out) return fail(LBM_ERR_ARG, "adj_in and adj_out must differ");
     CUDA_TRY(lbm::launch_adj_step(h->precision, adj_args(h, theta_t, theta_t1, adj_in, adj_out), h->hp, h->stream));
@@ -690,6 +703,7 @@ extern "C" lbm_status lbm_stefan_adjoint_step(lbm_stefan* h, const double* theta
 extern "C" lbm_status lbm_stefan_adjoint_run(lbm_stefan* h, int nsteps, const double* theta_traj, void* adj,
                                              void* adj_other, int* result_index)
 {
+    if (h && h->hp.method != LBM_IREBM) return fail(LBM_ERR_STATE, "the adjoint is that of the IREBM step");
     if (!h || !adj || !adj_other || !result_index || (!theta_traj && nsteps > 0))
         return fail(LBM_ERR_ARG, "NULL argument");
     if (nsteps < 0) return fail(LBM_ERR_ARG, "nsteps must be >= 0");

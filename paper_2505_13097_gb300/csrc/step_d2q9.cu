@@ -135,7 +135,8 @@ __device__ __noinline__ double wall_closure_d(double* q, const double* u, int x,
         } else {
             dphi = phi_of(th, pb.inv_delta) - pb.wall_phi[wi.wall];
         }
-        const double m0t = theta_d - dphi * pb.inv_ste;
+        // EEBM: the enthalpy of the wall value (Algorithm 2 keeps H = M0)
+        const double m0t = pb.method == 1 ? pb.wall_H[wi.wall] : theta_d - dphi * pb.inv_ste;
         double known = 0.0, wu = 0.0;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
@@ -184,10 +185,12 @@ __device__ __noinline__ ff wall_closure_f(float* q, const float* u, int x, int y
             if ((wi.unk >> i) & 1) wu += (float)d2_w(i);
             else ff_add(known, q[i]);
         }
-        // m0t = theta_D - (phi(theta) - phi(theta_D))/Ste
+        // m0t = theta_D - (phi(theta) - phi(theta_D))/Ste (EEBM: the wall value's enthalpy)
         const float dth = (th.hi - pb.wall_th_hi[k]) + (th.lo - pb.wall_th_lo[k]);
         ff m0t{pb.wall_th_hi[k], pb.wall_th_lo[k]};
-        if (fabsf(dth) <= pb.wall_dth_max) {
+        if (pb.method == 1) {
+            m0t = ff{pb.wall_H_hi[k], pb.wall_H_lo[k]};
+        } else if (fabsf(dth) <= pb.wall_dth_max) {
             ff_add(m0t, -pb.wall_slope[k] * dth);
         } else {
             const double dphi = phi_of(ff_to_double(th), pb.inv_delta) - pb.wall_phi[k];
@@ -546,6 +549,86 @@ __device__ __forceinline__ void row_update(const Problem& pb, int y, int x0, int
 
 }
 
+// EEBM row update (Algorithm 2 in the stored-Omega form): after the pulls and
+// the closures (Dirichlet target M0(q) = H(theta_D)), H = M0(q) is the
+// enthalpy, theta = Theta(H), and the collision relaxes toward the modified
+// equilibrium, Omega~_i = (1-omega) q_i + omega w_i theta for i != 0 and
+// Omega~_0 = (1-omega) q_0 + omega (H - (1-w_0) theta).  No Newton node; the
+// energy is the sum of H.
+template <typename P, int N, bool REC, bool EDGE, typename Out>
+__device__ __forceinline__ void row_update_eebm(const Problem& pb, int y, int x0, P (&qf)[9][N], const P (&u0)[N],
+                                                const P (&u1)[N], const P (&u2)[N], const P (&u3)[N],
+                                                const P (&u4)[N], const P (&u5)[N], const P (&u6)[N],
+                                                const P (&u7)[N], const P (&u8)[N], const Out& out,
+                                                double* __restrict__ rec, Acc<P>& acc, TileSums& ts, const P omc,
+                                                const P (&wP)[3], const int nx, const int ny)
+{
+    const long long pitch = pb.pitch;
+    if constexpr (EDGE) {
+        bool any_wall = false;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            const int x = x0 + k;
+            any_wall |= (x < nx) && (x == 0 || x == nx - 1 || y == 0 || y == ny - 1);
+        }
+        if (__any_sync(kFull, any_wall)) {
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                const int x = x0 + k;
+                if (x < nx && (x == 0 || x == nx - 1 || y == 0 || y == ny - 1)) {
+                    P qq[9], uu[9];
+                    int wall;
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) qq[i] = qf[i][k];
+                    uu[0] = u0[k]; uu[1] = u1[k]; uu[2] = u2[k]; uu[3] = u3[k]; uu[4] = u4[k];
+                    uu[5] = u5[k]; uu[6] = u6[k]; uu[7] = u7[k]; uu[8] = u8[k];
+                    if constexpr (sizeof(P) == 4) {
+                        const ff fl = wall_closure_f(qq, uu, x, y, pb, wall);
+                        ff_add(ts.flux_f, fl.hi);
+                        ts.flux_f.lo += fl.lo;
+                    } else {
+                        ts.flux += wall_closure_d(qq, uu, x, y, pb, wall);
+                    }
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) qf[i][k] = qq[i];
+                }
+            }
+        }
+    }
+    const P om = (P)1 - omc;
+    const P inv_ste = (P)pb.inv_ste;
+    P hs = 0;
+    double thn[REC ? N : 1];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        const bool valid = !EDGE || x0 + k < nx;
+        P H = 0;
+#pragma unroll
+        for (int i = 8; i >= 0; --i) H += qf[i][k];
+        if (!valid) {
+            H = 0;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) qf[i][k] = (P)0;
+        }
+        const P th = eebm_theta(H, inv_ste);
+        hs += H;
+        if constexpr (REC) thn[k] = (double)th;
+        qf[0][k] = fma(omc, qf[0][k], om * (H - ((P)1 - wP[0]) * th));
+#pragma unroll
+        for (int i = 1; i < 9; ++i) qf[i][k] = fma(omc, qf[i][k], om * (i <= 4 ? wP[1] : wP[2]) * th);
+    }
+    if constexpr (sizeof(P) == 4) acc.add_ff(ff{hs, 0.f});
+    else acc.add_d(hs);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        P o[N];
+#pragma unroll
+        for (int k = 0; k < N; ++k) o[k] = qf[i][k];
+        out.store(i, o);
+    }
+    if constexpr (REC) st_rec<N>(rec + (long long)y * pitch + x0, thn);
+}
+
 // One warp tile: segment `seg` of problem pb, rows [ya, yb).
 template <typename P, bool REC>
 __device__ __forceinline__ void d2q9_tile(const Problem& pb, const P* __restrict__ src, P* __restrict__ dst,
@@ -644,9 +727,14 @@ __device__ __forceinline__ void d2q9_tile(const Problem& pb, const P* __restrict
             if (rn <= yb) ring_load<P>(ring + ((rn + 1) % kStages) * R::SLOT, src, pl, pitch, rn, segx, lane, has_left, has_right);
             cp_async_commit();
         }
-        row_update<P, N, REC, true>(pb, y, x0, lane, qf, u0, u1, u2, u3, u4, u5, u6, u7, u8,
-                                    GlobalRowOut<P, N>{dst + (long long)(y + 1) * pitch + x0, pl}, rec, acc, ts, st, pi,
-                                    jobs, job_count, omc, om_f, omc_d, wP, thr_f, nx, ny);
+        if (pb.method == 1)
+            row_update_eebm<P, N, REC, true>(pb, y, x0, qf, u0, u1, u2, u3, u4, u5, u6, u7, u8,
+                                             GlobalRowOut<P, N>{dst + (long long)(y + 1) * pitch + x0, pl}, rec, acc,
+                                             ts, omc, wP, nx, ny);
+        else
+            row_update<P, N, REC, true>(pb, y, x0, lane, qf, u0, u1, u2, u3, u4, u5, u6, u7, u8,
+                                        GlobalRowOut<P, N>{dst + (long long)(y + 1) * pitch + x0, pl}, rec, acc, ts, st,
+                                        pi, jobs, job_count, omc, om_f, omc_d, wP, thr_f, nx, ny);
 
     }
     cp_async_wait<0>();
@@ -766,7 +854,11 @@ __device__ __forceinline__ void d2q9_tile_direct(const Problem& pb, const P* __r
 #pragma unroll
             for (int k = 0; k < N; ++k) qf[8][k] = s[k];
         }
-        if (seg_interior && y > 0 && y < ny - 1)
+        if (pb.method == 1)
+            row_update_eebm<P, N, REC, true>(pb, y, x0, qf, cur.r0, cur.r1, cur.c2, cur.r3, cu4, cur.c5, cur.c6, cu7,
+                                             cu8, GlobalRowOut<P, N>{dst + (long long)(y + 1) * pitch + x0, pl}, rec,
+                                             acc, ts, omc, wP, nx, ny);
+        else if (seg_interior && y > 0 && y < ny - 1)
             row_update<P, N, REC, false>(pb, y, x0, lane, qf, cur.r0, cur.r1, cur.c2, cur.r3, cu4, cur.c5, cur.c6, cu7,
                                          cu8, GlobalRowOut<P, N>{dst + (long long)(y + 1) * pitch + x0, pl}, rec, acc,
                                          ts, st, pi, jobs, job_count, omc, om_f, omc_d, wP, thr_f, nx, ny);
@@ -941,7 +1033,7 @@ __device__ __forceinline__ void tma_load_rows(const CUtensorMap* m, float* dst, 
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
 
 template <bool REC>
-__global__ void __launch_bounds__(kTmaThreads) d2q9_tma_kernel(const StepArgs a, const __grid_constant__ TmaMaps m)
+__global__ void __launch_bounds__(kTmaThreads, 5) d2q9_tma_kernel(const StepArgs a, const __grid_constant__ TmaMaps m)
 {
     __shared__ __align__(128) float ring[kTmaStages * kTmaSlot];
     __shared__ __align__(8) unsigned long long full[kTmaStages];
@@ -1053,7 +1145,10 @@ __global__ void __launch_bounds__(kTmaThreads) d2q9_tma_kernel(const StepArgs a,
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[km % kTmaStages]);
         const GlobalRowOut<float, 1> out{dst + (long long)(y + 1) * pitch + x, pl};
-        if (warp_interior_x && y > 0 && y < ny - 1)
+        if (pb.method == 1)
+            row_update_eebm<float, 1, REC, true>(pb, y, x, qf, u0, u1, u2, u3, u4, u5, u6, u7, u8, out, a.rec, acc, ts,
+                                                 omc, wP, nx, ny);
+        else if (warp_interior_x && y > 0 && y < ny - 1)
             row_update<float, 1, REC, false>(pb, y, x, lane, qf, u0, u1, u2, u3, u4, u5, u6, u7, u8, out, a.rec, acc,
                                              ts, st, pi, a.jobs, a.job_count, omc, om_f, omc_d, wP, thr_f, nx, ny);
         else

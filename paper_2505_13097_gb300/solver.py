@@ -74,6 +74,11 @@ class Stefan:
         w = _abi.WALLS[wall] if isinstance(wall, str) else int(wall)
         check(self.lib.lbm_stefan_set_bc(self.h, w, int(kind), float(theta_wall)))
 
+    def set_method(self, method):
+        """"IREBM" (Algorithm 3, default) or "EEBM" (Algorithm 2, D2Q9); set_ic follows."""
+        m = {"IREBM": _abi.LBM_IREBM, "EEBM": _abi.LBM_EEBM}.get(method, method)
+        check(self.lib.lbm_stefan_set_method(self.h, int(m)))
+
     def set_ic(self, theta0):
         if not _is_cuda_tensor(theta0):
             theta0 = np.asarray(theta0, dtype=np.float64).reshape(self.ny, self.nx)
