@@ -141,6 +141,20 @@ def bench_single(torch, solver, case, steps, warmup, stream, barrier=None, centr
     return ms, st
 
 
+def bench_eebm(torch, solver, case, steps, warmup, stream, nodes, irebm_ms):
+    """EEBM (Algorithm 2) on the melting workload, FP32 populations, same window."""
+    S = solver.Stefan.from_case(case, stream=stream)
+    S.set_method("EEBM")
+    S.set_ic(case.theta0())
+    S.step(melt_window(case, steps, warmup) + warmup)
+    S.sync()
+    ms = time_steps(torch, S, steps, stream)
+    k = S.step_timed(min(steps, 50))
+    S.close()
+    return {"mlups": nodes * steps / ms / 1e3, "ms_per_step": ms / steps, "kernel_ms": k[0],
+            "kernel_gbs": BYTES_FP32 * nodes / (k[0] * 1e-3) / 1e9, "irebm_over_eebm": irebm_ms / ms}
+
+
 def bench_e2e(torch, solver, case, steps, stream):
     """Through the public C ABI with host buffers: set_ic (pinned host -> device),
     `steps` steps, get_fields (device -> pinned host), all inside the timed region."""
@@ -355,6 +369,8 @@ def run_gpu(args):
             corner["ste%g" % ste] = {"mlups": cc.nx * cc.ny * k / msc / 1e3,
                                      "newton_nodes": stc["newton_nodes"], "newton_max_iter": stc["newton_max_iter"]}
         extra["corner_2d_fp64_2048"] = corner
+        # the paper's comparison scheme on the same workload and window (Sec. 6 compares run times)
+        extra["eebm_form"] = bench_eebm(torch, solver, case, args.steps, args.warmup, stream, nodes, ms)
         extra["batched_256"] = bench_batch(torch, solver, workloads, max(20, args.steps // 2), args.warmup, stream)
         extra["adjoint_1024"] = bench_adjoint(torch, solver, workloads, stream)
         extra["d1q3_512"] = bench_d1q3(torch, solver, workloads, stream)
