@@ -112,14 +112,14 @@ def _f64(a):
 class Problem:
     """One Stefan problem: lattice, sizes, tau, delta, Ste, Newton settings, walls.
 
-    ``lattice`` is 1 (D1Q3, ``ny`` = 1) or 2 (D2Q9).  ``walls`` maps "W", "E",
+    ``lattice`` is 1 (D1Q3, ``ny`` = 1), 2 (D2Q9) or 3 (D2Q5).  ``walls`` maps "W", "E",
     "S", "N" to ``(kind, theta)`` with kind 0 = adiabatic, 1 = Dirichlet.
     """
 
     def __init__(self, lattice, nx, ny=1, tau=1.0, delta=0.01, ste=0.1, walls=None,
                  newton_tol=1e-14, newton_max_iter=60, bb_mode=0):
         self.lattice, self.nx, self.ny = int(lattice), int(nx), int(ny)
-        self.q = 3 if self.lattice == 1 else 9
+        self.q = {1: 3, 2: 9, 3: 5}[self.lattice]
         p = Params()
         p.lattice, p.nx, p.ny = self.lattice, self.nx, self.ny
         p.tau, p.delta, p.ste = float(tau), float(delta), float(ste)

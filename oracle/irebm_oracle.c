@@ -23,7 +23,8 @@
  * as Algorithm 3 does.  No blocking, fusion or reordering.
  *
  * Readings where the paper is silent (each is listed in the design doc):
- *  - weights: D1Q3 (2/3, 1/6, 1/6), D2Q9 (4/9, 1/9 x4, 1/36 x4), c_s^2 = 1/3.
+ *  - weights: D1Q3 (2/3, 1/6, 1/6), D2Q5 (1/3, 1/6 x4), D2Q9 (4/9, 1/9 x4,
+ *    1/36 x4), c_s^2 = 1/3 on all three.
  *  - Newton stopping: |x_{k+1}-x_k| <= tol*max(1,|x_k|) (x_{k+1} kept), or
  *    F(x_k) = 0, or a bracket narrower than that; at most maxit iterations.
  *  - Newton safeguard: the root lies in [m0 + (phi(theta)-1)/Ste, m0 + phi(theta)/Ste]
@@ -44,10 +45,10 @@
 #include <stdlib.h>
 #include <string.h>
 
-#define ORC_MAXQ 9
+#define ORC_MAXQ 9   /* D2Q9; D2Q5 and D1Q3 use the first 5 / 3 entries */
 
 typedef struct {
-    int lattice;          /* 1 = D1Q3, 2 = D2Q9 */
+    int lattice;          /* 1 = D1Q3, 2 = D2Q9, 3 = D2Q5 */
     int nx, ny;           /* ny = 1 for D1Q3 */
     double tau, delta, ste;
     double newton_tol;
@@ -66,7 +67,7 @@ typedef struct {          /* per-step diagnostics */
 } orc_diag;
 
 /* ---- lattice tables (Sec. 3.2; weights are the standard ones) ---- */
-static int lat_q(const orc_params* p) { return p->lattice == 1 ? 3 : 9; }
+static int lat_q(const orc_params* p) { return p->lattice == 1 ? 3 : (p->lattice == 3 ? 5 : 9); }
 
 static void lat_vec(const orc_params* p, int i, int* ex, int* ey, double* w)
 {
@@ -74,6 +75,12 @@ static void lat_vec(const orc_params* p, int i, int* ex, int* ey, double* w)
         static const int e1[3] = {0, 1, -1};
         static const double w1[3] = {2.0 / 3.0, 1.0 / 6.0, 1.0 / 6.0};
         *ex = e1[i]; *ey = 0; *w = w1[i];
+    } else if (p->lattice == 3) {
+        /* D2Q5: rest, +x, +y, -x, -y; weights 1/3 and 1/6 (c_s^2 = 1/3) */
+        static const int e5x[5] = {0, 1, 0, -1, 0};
+        static const int e5y[5] = {0, 0, 1, 0, -1};
+        static const double w5[5] = {1.0 / 3.0, 1.0 / 6.0, 1.0 / 6.0, 1.0 / 6.0, 1.0 / 6.0};
+        *ex = e5x[i]; *ey = e5y[i]; *w = w5[i];
     } else {
         static const int e2x[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
         static const int e2y[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
@@ -163,7 +170,7 @@ static int node_walls(const orc_params* p, int x, int y)
     int m = 0;
     if (x == 0) m |= 1;
     if (x == p->nx - 1) m |= 2;
-    if (p->lattice == 2) {
+    if (p->lattice != 1) {
         if (y == 0) m |= 4;
         if (y == p->ny - 1) m |= 8;
     }

@@ -504,3 +504,69 @@ def test_eebm_front_follows_the_neumann_solution(orc):
     x_exact = 2.0 * neumann.stefan_lambda(ste, -0.5) * math.sqrt(t) / dx
     fz = front_position(th, 0.01, 0)[0]
     assert abs(fz - x_exact) <= 1.0
+
+
+# ---------------------------------------------------------------- D2Q5 lattice (Sec. 3.2, Sec. 4.2)
+@pytest.mark.parametrize("tau,walls,bb_mode", [
+    (1.0, {"W": (1, 1.0), "E": (1, -0.5)}, 0),
+    (0.7, {}, 0),
+    (0.7, {}, 1),
+])
+def test_d2q5_planar_field_is_d1q3(orc, tau, walls, bb_mode):
+    # a field uniform in y with adiabatic S/N walls: the y-moving D2Q5 populations
+    # pull identical rows, so together with the rest population they act as
+    # D1Q3's rest population (1/3 + 2/6 = 2/3) and every row equals the D1Q3 run.
+    # At tau = 1 the history term (1 - 1/tau) q_i drops out, so Dirichlet walls
+    # can be included: their corners share the unknown remainder between +x and
+    # +y (two unknowns), which changes how it is split but not theta~ = theta_D
+    nx, ny, steps = 40, 5, 120
+    th0 = np.tile(workloads.random_field((1, nx), -0.3, 0.3, seed=41), (ny, 1))
+    P5 = orc.Problem(3, nx, ny, tau=tau, delta=0.02, ste=0.3, walls=walls, bb_mode=bb_mode)
+    P1 = orc.Problem(1, nx, 1, tau=tau, delta=0.02, ste=0.3, walls=walls, bb_mode=bb_mode)
+    _, t5 = P5.run(th0, steps)
+    _, t1 = P1.run(th0[:1], steps)
+    assert np.max(np.abs(t5 - t1)) <= 1e-13
+
+
+def test_d2q5_conserves_energy_in_a_closed_box(orc):
+    P = orc.Problem(3, 17, 13, tau=0.8, delta=0.05, ste=0.2, bb_mode=1)
+    f = P.init(workloads.random_field((13, 17), -0.5, 0.5, seed=42))
+    e0 = P.energy(f)
+    for _ in range(100):
+        f = P.step(f)
+    assert abs(P.energy(f) - e0) <= 1e-12 * abs(e0)
+
+
+def test_d2q5_dirichlet_single_unknown_holds_the_wall(orc):
+    # Eq. (16): on a wall node (not a corner) one q is unknown and fixes M0(q);
+    # the node then stays at theta_D
+    P = orc.Problem(3, 12, 9, tau=0.9, delta=0.05, ste=0.2, walls={"W": (1, 0.7)})
+    _, th = P.run(workloads.random_field((9, 12), -0.5, 0.5, seed=43), 30)
+    assert np.max(np.abs(th[:, 0] - 0.7)) <= 1e-14
+
+
+@pytest.mark.parametrize("bb_mode", [0, 1])
+def test_d2q5_planar_in_y_is_d1q3(orc, bb_mode):
+    # the same reduction with the field uniform in x: the columns follow D1Q3
+    # along y (catches a swapped or mis-signed y velocity)
+    nx, ny, steps = 4, 36, 90
+    col = workloads.random_field((1, ny), -0.3, 0.3, seed=44)[0]
+    th0 = np.tile(col[:, None], (1, nx))
+    P5 = orc.Problem(3, nx, ny, tau=0.65, delta=0.02, ste=0.3, bb_mode=bb_mode)
+    P1 = orc.Problem(1, ny, 1, tau=0.65, delta=0.02, ste=0.3, bb_mode=bb_mode)
+    _, t5 = P5.run(th0, steps)
+    _, t1 = P1.run(col[None, :], steps)
+    assert np.max(np.abs(t5 - t1[0][:, None])) <= 1e-13
+
+
+def test_d2q5_linear_steady_state(orc):
+    # Dirichlet W = 2, E = 1 far above the melting point (phi = 1 to rounding):
+    # plain diffusion, whose steady state is the straight line between the walls.
+    # tau = 1 (no history term): with tau != 1 the corners, Dirichlet nodes with
+    # two unknowns that share the remainder, feed a small offset into the +y
+    # populations that the (1 - 1/tau) q_i term carries inwards
+    nx, ny = 21, 6
+    P = orc.Problem(3, nx, ny, tau=1.0, delta=0.01, ste=0.5, walls={"W": (1, 2.0), "E": (1, 1.0)})
+    _, th = P.run(np.full((ny, nx), 1.5), 6000)
+    exact = 2.0 - np.arange(nx) / (nx - 1)
+    assert np.max(np.abs(th - exact[None, :])) <= 1e-10
