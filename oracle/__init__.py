@@ -114,12 +114,16 @@ class Problem:
 
     ``lattice`` is 1 (D1Q3, ``ny`` = 1), 2 (D2Q9) or 3 (D2Q5).  ``walls`` maps "W", "E",
     "S", "N" to ``(kind, theta)`` with kind 0 = adiabatic, 1 = Dirichlet.
+    ``bb_mode`` closes the adiabatic walls: 0 mirror bounce-back, 1 link-wise
+    bounce-back (Sec. 4.2.2), 2 the D2Q5 Neumann closure of Eq. (17).
     """
 
     def __init__(self, lattice, nx, ny=1, tau=1.0, delta=0.01, ste=0.1, walls=None,
                  newton_tol=1e-14, newton_max_iter=60, bb_mode=0):
         self.lattice, self.nx, self.ny = int(lattice), int(nx), int(ny)
         self.q = {1: 3, 2: 9, 3: 5}[self.lattice]
+        if int(bb_mode) == 2 and (self.lattice != 3 or self.nx < 3 or self.ny < 3):
+            raise ValueError("the Neumann closure of Eq. (17) is the D2Q5 one, nx and ny >= 3")
         p = Params()
         p.lattice, p.nx, p.ny = self.lattice, self.nx, self.ny
         p.tau, p.delta, p.ste = float(tau), float(delta), float(ste)
@@ -129,6 +133,10 @@ class Problem:
             p.wall_kind[k] = int(kind)
             p.wall_theta[k] = float(th)
         self.p = p
+
+    def _no_eq17(self, what):
+        if self.p.bb_mode == 2:
+            raise NotImplementedError(what + " is written for the bounce-back closures")
 
     @property
     def shape(self):
@@ -179,11 +187,13 @@ class Problem:
         return f, th
 
     def loss(self, theta0, nsteps, phi_target):
+        self._no_eq17("the adjoint")
         return lib().orc_loss(ctypes.byref(self.p), _dp(_f64(theta0).reshape(self.shape)), int(nsteps),
                               _dp(_f64(phi_target).reshape(self.shape)))
 
     def adjoint(self, theta0, nsteps, phi_target):
         """Loss and its gradient: (L, dL/dtheta0, dL/dtheta_wall[4], dL/dSte)."""
+        self._no_eq17("the adjoint")
         g0 = np.empty(self.shape)
         gw = np.zeros(4)
         gs = np.zeros(1)
@@ -196,6 +206,7 @@ class Problem:
 
     # ---- explicit enthalpy based method (EEBM, Algorithm 2): f carries H = M0(f)
     def eebm_init(self, theta0):
+        self._no_eq17("EEBM")
         f = np.empty((self.q, self.ny, self.nx))
         lib().orc_eebm_init(ctypes.byref(self.p), _dp(_f64(theta0).reshape(self.shape)), _dp(f))
         return f
@@ -207,6 +218,7 @@ class Problem:
         return th, H
 
     def eebm_step(self, f, detail=False):
+        self._no_eq17("EEBM")
         f = _f64(f)
         fn = np.empty_like(f)
         d = Diag()
@@ -218,6 +230,7 @@ class Problem:
 
     def eebm_run(self, theta0, nsteps):
         """``nsteps`` EEBM steps from the equilibrium state of ``theta0``: (f, theta)."""
+        self._no_eq17("EEBM")
         f = np.empty((self.q, self.ny, self.nx))
         th = np.empty(self.shape)
         if lib().orc_eebm_run(ctypes.byref(self.p), _dp(_f64(theta0).reshape(self.shape)), int(nsteps),

@@ -15,6 +15,7 @@
  *   (14) rhs_fl_2        theta~ = M0(q) + (phi(theta) - phi(theta~))/Ste
  *   (15) Dirichlet       closure on M0(q) at a Dirichlet node
  *   (16) Dir_on_q        single-unknown form of (15) (D1Q3, D2Q5)
+ *   (17) Neu_on_q        Neumann closure through the inner neighbour's M0(q) (D2Q5)
  * Algorithm 3 (IREBM step) fixes the order of the step.  Sec. 4.2.2 gives the
  * bounce-back closure q_ix = q_{bar ix}.
  *
@@ -40,6 +41,10 @@
  *  - Bounce-back: mirror q_i = q_{bar i} (Sec. 4.2.2) where q_{bar i} is known,
  *    else (corner diagonals, thin domains) link-wise q_i = Omega_{bar i} at the
  *    node.  bb_mode = 1 uses the link-wise form for every unknown direction.
+ *  - bb_mode = 2 (D2Q5, nx and ny >= 3): the Neumann closure of Eq. (17),
+ *    M0(q) at a wall node = M0(q) at the node one step inwards; at a corner of
+ *    two adiabatic walls that is the diagonal interior node, and the two
+ *    unknowns share the remainder by weight (equally).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -241,6 +246,20 @@ double orc_energy(const orc_params* p, const double* f)
     return e;
 }
 
+/* M0 of the streamed populations at node (x, y): sum_i Omega_i(x - e_i) over
+ * the lattice (every x - e_i inside for an interior node) */
+static double orc_pulled_m0(const orc_params* p, const double* Om, int x, int y)
+{
+    const int n = p->nx * p->ny;
+    double s = 0.0, w;
+    int i, ex, ey;
+    for (i = 0; i < lat_q(p); i++) {
+        lat_vec(p, i, &ex, &ey, &w);
+        if (inside(p, x - ex, y - ey)) s += Om[i * n + (y - ey) * p->nx + (x - ex)];
+    }
+    return s;
+}
+
 /*
  * One IREBM time step, Algorithm 3, f -> fn.
  * Optional outputs (may be NULL): per-node m0, theta (time t), theta~ (root),
@@ -296,6 +315,19 @@ int orc_step(const orc_params* p, const double* f, double* fn, double* m0_out, d
                 if (node_dirichlet(p, x, y, &td, NULL)) {
                     /* Eq. (15): M0(q) = m0_target; unknowns share the rest by weight */
                     double rest = orc_dirichlet_m0(p, td, theta[k]), wu = 0.0;
+                    for (i = 0; i < q; i++) {
+                        if (known[i]) rest -= qv[i];
+                        else wu += w[i];
+                    }
+                    for (i = 0; i < q; i++)
+                        if (!known[i]) qv[i] = w[i] * rest / wu;
+                } else if (p->bb_mode == 2) {
+                    /* Eq. (17): M0(q) of the node equals M0(q) of the interior node
+                     * one lattice step inwards (the diagonal one at a corner); the
+                     * unknowns share the rest by weight, as at a Dirichlet node */
+                    const int sx = x + (x == 0 ? 1 : (x == nx - 1 ? -1 : 0));
+                    const int sy = y + (y == 0 ? 1 : (y == ny - 1 ? -1 : 0));
+                    double rest = orc_pulled_m0(p, Om, sx, sy), wu = 0.0;
                     for (i = 0; i < q; i++) {
                         if (known[i]) rest -= qv[i];
                         else wu += w[i];

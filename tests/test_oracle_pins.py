@@ -570,3 +570,74 @@ def test_d2q5_linear_steady_state(orc):
     _, th = P.run(np.full((ny, nx), 1.5), 6000)
     exact = 2.0 - np.arange(nx) / (nx - 1)
     assert np.max(np.abs(th - exact[None, :])) <= 1e-10
+
+
+# ---------------------------------------------------------------- D2Q5 Neumann closure, Eq. (17)
+def _eq17_partner(nx, ny, x, y):
+    return (x + (1 if x == 0 else (-1 if x == nx - 1 else 0)),
+            y + (1 if y == 0 else (-1 if y == ny - 1 else 0)))
+
+
+def test_eq17_wall_m0_equals_inner_neighbour(orc):
+    # Eq. (17) makes M0(q) of a wall node equal M0(q) of the node one step
+    # inwards (the diagonal interior node at a corner of two adiabatic walls);
+    # checked on one step from an arbitrary (non-equilibrium) state
+    nx, ny = 9, 7
+    P = orc.Problem(3, nx, ny, tau=0.8, delta=0.05, ste=0.3, bb_mode=2)
+    rng = np.random.default_rng(45)
+    f = rng.uniform(-0.2, 0.2, size=(5, ny, nx))
+    _, d = P.step(f, detail=True)
+    m0 = d["m0"]
+    for y in range(ny):
+        for x in range(nx):
+            if 0 < x < nx - 1 and 0 < y < ny - 1:
+                continue
+            sx, sy = _eq17_partner(nx, ny, x, y)
+            assert abs(m0[y, x] - m0[sy, sx]) <= 1e-15, (x, y)
+    # an interior node keeps its streamed M0
+    Om = f * (1 - 1 / 0.8) + (1 / 0.8) * np.array([1 / 3, 1 / 6, 1 / 6, 1 / 6, 1 / 6])[:, None, None] * f.sum(0)
+    x, y = 4, 3
+    ref = Om[0, y, x] + Om[1, y, x - 1] + Om[2, y - 1, x] + Om[3, y, x + 1] + Om[4, y + 1, x]
+    assert abs(m0[y, x] - ref) <= 1e-15
+
+
+def test_eq17_keeps_walls_equal_to_inner_neighbours(orc):
+    # the Neumann condition theta(x_L) = theta(x_L + e_ix) of Eq. (17) holds at
+    # every step once it holds at the start: M0(q) and theta agree, so does the
+    # Newton root of Eq. (14)
+    nx, ny = 14, 11
+    th0 = workloads.random_field((ny, nx), -0.4, 0.4, seed=46)
+    th0[0, :], th0[-1, :] = th0[1, :], th0[-2, :]
+    th0[:, 0], th0[:, -1] = th0[:, 1], th0[:, -2]
+    P = orc.Problem(3, nx, ny, tau=0.75, delta=0.05, ste=0.2, bb_mode=2)
+    _, th = P.run(th0, 60)
+    assert np.max(np.abs(th[0, :] - th[1, :])) <= 1e-12
+    assert np.max(np.abs(th[-1, :] - th[-2, :])) <= 1e-12
+    assert np.max(np.abs(th[:, 0] - th[:, 1])) <= 1e-12
+    assert np.max(np.abs(th[:, -1] - th[:, -2])) <= 1e-12
+    # the fronts move: not a trivially frozen field
+    assert np.max(np.abs(th - th0)) > 1e-2
+
+
+def test_eq17_with_dirichlet_walls(orc):
+    # the paper's 2D setting: Dirichlet on two walls, Eq. (17) on the other two;
+    # the Dirichlet nodes (corners included) stay at theta_D, the adiabatic
+    # wall nodes away from the Dirichlet corners follow their inner neighbours
+    nx, ny = 12, 10
+    th0 = np.full((ny, nx), 0.3)
+    P = orc.Problem(3, nx, ny, tau=0.9, delta=0.05, ste=0.2, bb_mode=2,
+                    walls={"W": (1, -0.5), "S": (1, -0.5)})
+    _, th = P.run(th0, 80)
+    assert np.max(np.abs(th[:, 0] + 0.5)) <= 1e-14 and np.max(np.abs(th[0, :] + 0.5)) <= 1e-14
+    assert np.max(np.abs(th[-1, 1:] - th[-2, 1:])) <= 1e-12
+    assert np.max(np.abs(th[1:, -1] - th[1:, -2])) <= 1e-12
+
+
+def test_eq17_argument_checks(orc):
+    with pytest.raises(ValueError):
+        orc.Problem(2, 8, 8, bb_mode=2)
+    with pytest.raises(ValueError):
+        orc.Problem(3, 2, 8, bb_mode=2)
+    P = orc.Problem(3, 8, 8, bb_mode=2)
+    with pytest.raises(NotImplementedError):
+        P.adjoint(np.zeros((8, 8)), 2, np.zeros((8, 8)))
