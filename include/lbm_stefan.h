@@ -50,16 +50,16 @@ typedef enum {
     LBM_ERR_STATE = 5    /* call out of order (e.g. step before set_ic) */
 } lbm_status;
 
-enum { LBM_D1Q3 = 1, LBM_D2Q9 = 2 };                          /* lattice (Sec. 3.2) */
+enum { LBM_D1Q3 = 1, LBM_D2Q9 = 2, LBM_D2Q5 = 3 };             /* lattice (Sec. 3.2) */
 enum { LBM_FP64 = 0, LBM_FP32 = 1 };                           /* population storage */
 enum { LBM_WALL_W = 0, LBM_WALL_E = 1, LBM_WALL_S = 2, LBM_WALL_N = 3 };
 enum { LBM_ADIABATIC = 0, LBM_DIRICHLET = 1 };                 /* wall kinds (Sec. 4.2) */
-enum { LBM_BB_MIRROR = 0, LBM_BB_LINK = 1 };                   /* bounce-back forms */
+enum { LBM_BB_MIRROR = 0, LBM_BB_LINK = 1, LBM_NEU_EQ17 = 2 }; /* adiabatic-wall closures */
 enum { LBM_IREBM = 0, LBM_EEBM = 1 };                          /* step method (Algorithms 3 and 2) */
 
 typedef struct {
-    int lattice;          /* LBM_D1Q3 or LBM_D2Q9 */
-    int nx, ny;           /* nodes per side, >= 2 (ny = 1 for D1Q3) */
+    int lattice;          /* LBM_D1Q3, LBM_D2Q9 or LBM_D2Q5 */
+    int nx, ny;           /* nodes per side, >= 2 (ny = 1 for D1Q3; nx, ny >= 3 for D2Q5) */
     double tau;           /* BGK relaxation time, > 1/2 (Eq. 8) */
     double delta;         /* regularization width of phi, > 0 (Sec. 4.1) */
     double ste;           /* Stefan number, > 0 (Eq. 1) */
@@ -67,7 +67,12 @@ typedef struct {
                              relaxed in FP32, moments as float-float sums, Newton in FP64 */
     double newton_tol;    /* step tolerance of the Newton solve (Algorithm 3), e.g. 1e-14 */
     int newton_max_iter;  /* iteration limit, e.g. 60; reaching it sets LBM_ERR_NEWTON */
-    int bb_mode;          /* LBM_BB_MIRROR: q_i = q_{bar i} (Sec. 4.2.2); LBM_BB_LINK: q_i = Omega_{bar i} */
+    int bb_mode;          /* closure of the adiabatic walls: LBM_BB_MIRROR: q_i = q_{bar i}
+                             (Sec. 4.2.2); LBM_BB_LINK: q_i = Omega_{bar i} at the node;
+                             LBM_NEU_EQ17 (D2Q5 only): Eq. (17), M0(q) of a wall node equals
+                             M0(q) of the node one step inwards (at a corner of two adiabatic
+                             walls the diagonal interior node, the two unknowns sharing the
+                             rest equally) */
 } lbm_stefan_params;
 
 typedef struct {
@@ -105,7 +110,8 @@ lbm_status lbm_stefan_set_bc(lbm_stefan* h, int wall, int kind, double theta_wal
  * delta is not used.  For EEBM, get_fields returns theta = Theta(H), phi = the
  * liquid fraction min(max(Ste H, 0), 1) and H; the energy statistics are the
  * sum of H; the adjoint calls return LBM_ERR_STATE.  Discards the state: call
- * lbm_stefan_set_ic afterwards.  LBM_ERR_ARG for an unknown method or D1Q3. */
+ * lbm_stefan_set_ic afterwards.  LBM_ERR_ARG for an unknown method or a
+ * lattice other than D2Q9. */
 lbm_status lbm_stefan_set_method(lbm_stefan* h, int method);
 
 /* Initial state: f_i = w_i theta0 (equilibrium), Dirichlet nodes at their wall
@@ -116,7 +122,7 @@ lbm_status lbm_stefan_set_ic(lbm_stefan* h, const double* theta0, int on_device)
  * Every step also forms the energy E and the boundary flux on the device. */
 lbm_status lbm_stefan_step(lbm_stefan* h, int nsteps);
 
-/* D2Q9 only: advance nsteps >= 1 steps launched one by one (no graph) with a
+/* D2Q9 and D2Q5: advance nsteps >= 1 steps launched one by one (no graph) with a
  * CUDA event before, between and after the two kernels of each step, wait for
  * them, and return the mean device time per step of each kernel in ms:
  * ms_kernels[0] the stream/collide kernel (the TMA kernel in the FP32 form),
@@ -172,7 +178,8 @@ lbm_status lbm_stefan_theta_plane(lbm_stefan* h, double* theta_plane);
  * Adjoint states have the layout and precision of the forward state.  The
  * Newton root enters through the implicit function theorem on
  * F(x) = x + phi(x)/Ste - m0 - phi(theta)/Ste (Eq. 14).  Gradients with
- * respect to the wall temperatures and Ste accumulate on the device. */
+ * respect to the wall temperatures and Ste accumulate on the device.  D1Q3
+ * and D2Q9 with the bounce-back closures; LBM_ERR_ARG for D2Q5. */
 
 /* lambda_T = dL/dOmega(T) from theta_T (a recorded plane) and phi_target
  * (device, nx*ny doubles); clears the wall / Ste accumulators.  If loss is

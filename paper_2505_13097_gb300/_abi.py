@@ -13,10 +13,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "lib", "liblbm_stefan.so")
 
 LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_NEWTON, LBM_ERR_TIMEOUT, LBM_ERR_STATE = range(6)
-LBM_D1Q3, LBM_D2Q9 = 1, 2
+LBM_D1Q3, LBM_D2Q9, LBM_D2Q5 = 1, 2, 3
 LBM_FP64, LBM_FP32 = 0, 1
 LBM_ADIABATIC, LBM_DIRICHLET = 0, 1
-LBM_BB_MIRROR, LBM_BB_LINK = 0, 1
+LBM_BB_MIRROR, LBM_BB_LINK, LBM_NEU_EQ17 = 0, 1, 2
 LBM_IREBM, LBM_EEBM = 0, 1
 WALLS = {"W": 0, "E": 1, "S": 2, "N": 3}
 

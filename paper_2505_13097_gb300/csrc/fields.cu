@@ -9,7 +9,7 @@ namespace lbm {
 __device__ __forceinline__ bool dirichlet_value(const Problem& pb, int x, int y, double& td)
 {
     const int walls = (x == 0 ? 1 : 0) | (x == pb.nx - 1 ? 2 : 0) |
-                      (pb.q == 9 ? ((y == 0 ? 4 : 0) | (y == pb.ny - 1 ? 8 : 0)) : 0);
+                      (pb.q != 3 ? ((y == 0 ? 4 : 0) | (y == pb.ny - 1 ? 8 : 0)) : 0);
     for (int k = 0; k < 4; ++k)
         if (((walls >> k) & 1) && pb.wall_kind[k] == 1) {
             td = pb.wall_theta[k];
@@ -17,8 +17,6 @@ __device__ __forceinline__ bool dirichlet_value(const Problem& pb, int x, int y,
         }
     return false;
 }
-
-__device__ __forceinline__ double lat_w(int q, int i) { return q == 9 ? d2_w(i) : d1_w(i); }
 
 template <typename P>
 __global__ void init_state_kernel(const Problem* dprob, const double* __restrict__ theta0, int parity, DevStats* st)

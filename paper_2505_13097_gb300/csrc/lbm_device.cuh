@@ -17,7 +17,7 @@ constexpr unsigned kFull = 0xffffffffu;
 // below half an ulp of 1), so phi is exactly 0 or 1 there and phi' is 0.
 constexpr double kSat = 19.5;
 
-// ---------------------------------------------------------------- D2Q9 / D1Q3
+// ---------------------------------------------------------------- D2Q9 / D1Q3 / D2Q5
 // D2Q9 velocities (Sec. 3.2): 0 rest; 1..4 = (+1,0),(0,+1),(-1,0),(0,-1);
 // 5..8 = (+1,+1),(-1,+1),(-1,-1),(+1,-1).  Weights 4/9, 1/9, 1/36 (c_s^2 = 1/3).
 __host__ __device__ constexpr int d2_ex(int i) { return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0); }
@@ -27,6 +27,10 @@ __host__ __device__ constexpr double d2_w(int i) { return i == 0 ? 4.0 / 9.0 : (
 // D1Q3: 0 rest, 1 = +1, 2 = -1; weights 2/3, 1/6, 1/6.
 __host__ __device__ constexpr int d1_ex(int i) { return i == 1 ? 1 : (i == 2 ? -1 : 0); }
 __host__ __device__ constexpr double d1_w(int i) { return i == 0 ? 2.0 / 3.0 : 1.0 / 6.0; }
+// D2Q5: 0 rest, 1..4 = (+1,0),(0,+1),(-1,0),(0,-1) as in D2Q9; weights 1/3, 1/6 (c_s^2 = 1/3).
+__host__ __device__ constexpr double d5_w(int i) { return i == 0 ? 1.0 / 3.0 : 1.0 / 6.0; }
+// weight i of the lattice with q velocities (3, 5 or 9)
+__host__ __device__ constexpr double lat_w(int q, int i) { return q == 9 ? d2_w(i) : (q == 5 ? d5_w(i) : d1_w(i)); }
 
 // ---------------------------------------------------------------- float-float
 // Unevaluated sum hi + lo of two floats; two_sum is Knuth's error-free

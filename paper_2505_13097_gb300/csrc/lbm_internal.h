@@ -45,7 +45,7 @@ struct DevStats {
 struct Problem {
     void* state[2];          // ping-pong population buffers
     int nx, ny, pitch;
-    int q;                   // 3 (D1Q3) or 9 (D2Q9)
+    int q;                   // 3 (D1Q3), 5 (D2Q5) or 9 (D2Q9)
     long long plane;         // elements per plane
     double omega;            // 1/tau
     double ste, inv_ste, delta, inv_delta;
@@ -159,7 +159,11 @@ int d2q9_segment_width(int precision);   // nodes per warp segment
 int d2q9_blocks_per_sm(int precision);   // resident step blocks per SM (persistent grid)
 cudaError_t launch_d2q9_tma(const StepArgs& a, const TmaMaps& m, cudaStream_t s);
 int d2q9_tma_blocks_per_sm();
-cudaError_t launch_newton_jobs(int precision, const JobArgs& a, cudaStream_t s);
+cudaError_t launch_newton_jobs(int precision, int q, const JobArgs& a, cudaStream_t s);   // q = 9 or 5
+
+// D2Q5 launchers (step_d2q5.cu): one tile per warp over a.nslots tiles
+cudaError_t launch_d2q5_step(int precision, const StepArgs& a, cudaStream_t s);
+int d2q5_segment_width(int precision);   // nodes per warp segment
 
 // D1Q3 launchers (step_d1q3.cu)
 cudaError_t launch_d1q3_step(int precision, const StepArgs& a, const Problem& hp, cudaStream_t s);

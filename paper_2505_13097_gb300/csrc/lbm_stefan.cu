@@ -218,11 +218,19 @@ static lbm::JobArgs job_args(const Problem* probs, int nprob, int parity, double
     return j;
 }
 
-// One D2Q9 step is two launches: the fused stream/collide kernel, which defers
-// the nodes that need the Newton iteration, and the job kernel that solves them.
+// One D2Q9 or D2Q5 step is two launches: the fused stream/collide kernel, which
+// defers the nodes that need the Newton iteration, and the job kernel that
+// solves them.
 static cudaError_t launch_one(lbm_stefan* h, int parity, double* rec)
 {
     StepArgs a = single_args(h, parity, rec);
+    if (h->p.lattice == LBM_D2Q5) {
+        const cudaError_t e = lbm::launch_d2q5_step(h->precision, a, h->stream);
+        if (e != cudaSuccess) return e;
+        return lbm::launch_newton_jobs(h->precision, 5,
+                                       job_args(h->dprob, 1, parity, rec, h->dstats, h->dticket, h->djobs, h->djob_count),
+                                       h->stream);
+    }
     if (h->p.lattice == LBM_D2Q9) {
         cudaError_t e;
         if (h->use_tma) {
@@ -233,7 +241,7 @@ static cudaError_t launch_one(lbm_stefan* h, int parity, double* rec)
             e = lbm::launch_d2q9_step(h->precision, a, grid, h->stream);
         }
         if (e != cudaSuccess) return e;
-        return lbm::launch_newton_jobs(h->precision,
+        return lbm::launch_newton_jobs(h->precision, h->hp.q,
                                        job_args(h->dprob, 1, parity, rec, h->dstats, h->dticket, h->djobs, h->djob_count),
                                        h->stream);
     }
@@ -294,7 +302,8 @@ static bool encode_state_map(CUtensorMap* m, void* base, const Problem& hp, int 
 // rows hold whole 128-column strips of the TMA step kernel.
 static int state_pitch(int lattice, int precision, int nx)
 {
-    if (lattice != LBM_D2Q9) return round_up(nx, 32);
+    if (lattice == LBM_D1Q3) return round_up(nx, 32);
+    if (lattice == LBM_D2Q5) return round_up(nx, lbm::d2q5_segment_width(precision));
     const int segw = lbm::d2q9_segment_width(precision);
     return round_up(nx, precision == LBM_FP32 ? std::max(segw, lbm::kTmaW) : segw);
 }
@@ -321,13 +330,18 @@ extern "C" lbm_status lbm_stefan_create(const lbm_stefan_params* p, void* cuda_s
 {
     if (!p || !out) return fail(LBM_ERR_ARG, "NULL argument");
     *out = nullptr;
-    if (p->lattice != LBM_D1Q3 && p->lattice != LBM_D2Q9) return fail(LBM_ERR_ARG, "lattice must be D1Q3 or D2Q9");
+    if (p->lattice != LBM_D1Q3 && p->lattice != LBM_D2Q9 && p->lattice != LBM_D2Q5)
+        return fail(LBM_ERR_ARG, "lattice must be D1Q3, D2Q9 or D2Q5");
     if (p->precision != LBM_FP64 && p->precision != LBM_FP32) return fail(LBM_ERR_ARG, "precision must be FP64 or FP32");
-    if (p->bb_mode != LBM_BB_MIRROR && p->bb_mode != LBM_BB_LINK) return fail(LBM_ERR_ARG, "bb_mode must be 0 or 1");
+    if (p->bb_mode != LBM_BB_MIRROR && p->bb_mode != LBM_BB_LINK && p->bb_mode != LBM_NEU_EQ17)
+        return fail(LBM_ERR_ARG, "bb_mode must be 0, 1 or 2");
+    if (p->bb_mode == LBM_NEU_EQ17 && p->lattice != LBM_D2Q5)
+        return fail(LBM_ERR_ARG, "the Neumann closure of Eq. (17) is the D2Q5 one");
     lbm_status s = validate_common(p->nx, p->ny, p->tau, p->delta, p->ste, p->newton_tol, p->newton_max_iter);
     if (s != LBM_OK) return s;
     if (p->lattice == LBM_D1Q3 && p->ny != 1) return fail(LBM_ERR_ARG, "D1Q3 needs ny = 1");
     if (p->lattice == LBM_D2Q9 && p->ny < 2) return fail(LBM_ERR_ARG, "D2Q9 needs ny >= 2");
+    if (p->lattice == LBM_D2Q5 && (p->nx < 3 || p->ny < 3)) return fail(LBM_ERR_ARG, "D2Q5 needs nx, ny >= 3");
     if ((long long)p->nx * p->ny > (1ll << 31)) return fail(LBM_ERR_ARG, "more than 2^31 nodes");
 
     lbm_stefan* h = new lbm_stefan();
@@ -335,8 +349,10 @@ extern "C" lbm_status lbm_stefan_create(const lbm_stefan_params* p, void* cuda_s
     h->precision = p->precision;
     h->elem = p->precision == LBM_FP32 ? 4 : 8;
     h->stream = static_cast<cudaStream_t>(cuda_stream);
-    const int q = p->lattice == LBM_D2Q9 ? 9 : 3;
-    const int segw = p->lattice == LBM_D2Q9 ? lbm::d2q9_segment_width(p->precision) : 32;
+    const int q = p->lattice == LBM_D2Q9 ? 9 : (p->lattice == LBM_D2Q5 ? 5 : 3);
+    const int segw = p->lattice == LBM_D2Q9   ? lbm::d2q9_segment_width(p->precision)
+                     : p->lattice == LBM_D2Q5 ? lbm::d2q5_segment_width(p->precision)
+                                              : 32;
     const bool tma = LBM_USE_TMA && p->lattice == LBM_D2Q9 && p->precision == LBM_FP32;
     const int pitch = state_pitch(p->lattice, p->precision, p->nx);
     fill_problem(h->hp, q, p->nx, p->ny, pitch, p->tau, p->delta, p->ste, p->newton_tol, p->newton_max_iter,
@@ -354,7 +370,7 @@ extern "C" lbm_status lbm_stefan_create(const lbm_stefan_params* p, void* cuda_s
     if (e == cudaSuccess) e = cudaMalloc(&h->dticket, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMemset(h->dticket, 0, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMalloc(&h->dscratch, sizeof(double) * 3 * (size_t)p->nx * p->ny);
-    if (e == cudaSuccess && q == 9) e = cudaMalloc(&h->djobs, sizeof(lbm::NewtonJob) * (size_t)p->nx * p->ny);
+    if (e == cudaSuccess && q != 3) e = cudaMalloc(&h->djobs, sizeof(lbm::NewtonJob) * (size_t)p->nx * p->ny);
     if (e == cudaSuccess) e = cudaMalloc(&h->djob_count, sizeof(unsigned int));
     if (e == cudaSuccess && q == 9) h->adj_tile_h = adjoint_tile_h(h->hp);
     if (e == cudaSuccess) e = cudaMemset(h->djob_count, 0, sizeof(unsigned int));
@@ -477,7 +493,7 @@ extern "C" lbm_status lbm_stefan_step(lbm_stefan* h, int nsteps)
 extern "C" lbm_status lbm_stefan_step_timed(lbm_stefan* h, int nsteps, double* ms_kernels)
 {
     if (!h || !ms_kernels) return fail(LBM_ERR_ARG, "NULL argument");
-    if (h->p.lattice != LBM_D2Q9) return fail(LBM_ERR_ARG, "kernel timing covers the D2Q9 step");
+    if (h->p.lattice == LBM_D1Q3) return fail(LBM_ERR_ARG, "kernel timing covers the D2Q9 and D2Q5 steps");
     if (nsteps < 1) return fail(LBM_ERR_ARG, "nsteps must be >= 1");
     if (!h->ic) return fail(LBM_ERR_STATE, "set_ic must come before step_timed");
     std::vector<cudaEvent_t> ev(2 * (size_t)nsteps + 1, nullptr);
@@ -487,7 +503,9 @@ extern "C" lbm_status lbm_stefan_step_timed(lbm_stefan* h, int nsteps, double* m
     if (e == cudaSuccess) e = cudaEventRecord(ev[0], h->stream);
     for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
         StepArgs a = single_args(h, h->parity, nullptr);
-        if (h->use_tma) {
+        if (h->p.lattice == LBM_D2Q5) {
+            e = lbm::launch_d2q5_step(h->precision, a, h->stream);
+        } else if (h->use_tma) {
             e = lbm::launch_d2q9_tma(a, h->tma, h->stream);
         } else {
             const int grid = (h->hp.ntiles + lbm::kWarpsPerBlock - 1) / lbm::kWarpsPerBlock;
@@ -495,7 +513,7 @@ extern "C" lbm_status lbm_stefan_step_timed(lbm_stefan* h, int nsteps, double* m
         }
         if (e == cudaSuccess) e = cudaEventRecord(ev[2 * k + 1], h->stream);
         if (e == cudaSuccess)
-            e = lbm::launch_newton_jobs(h->precision,
+            e = lbm::launch_newton_jobs(h->precision, h->hp.q,
                                         job_args(h->dprob, 1, h->parity, nullptr, h->dstats, h->dticket, h->djobs,
                                                  h->djob_count),
                                         h->stream);
@@ -645,6 +663,7 @@ extern "C" lbm_status lbm_stefan_theta_plane(lbm_stefan* h, double* plane)
 extern "C" lbm_status lbm_stefan_adjoint_seed(lbm_stefan* h, const double* theta_T, const double* phi_target,
                                               void* adj, double* loss)
 {
+    if (h && h->p.lattice == LBM_D2Q5) return fail(LBM_ERR_ARG, "the adjoint covers D1Q3 and D2Q9");
     if (h && h->hp.method != LBM_IREBM) return fail(LBM_ERR_STATE, "the adjoint is that of the IREBM step");
     if (!h || !theta_T || !phi_target || !adj) return fail(LBM_ERR_ARG, "NULL argument");
     CUDA_TRY(cudaMemsetAsync(&h->dstats->g_wall, 0, sizeof(lbm::Acc128) * 6, h->stream));
@@ -693,6 +712,7 @@ static lbm::AdjArgs adj_args(lbm_stefan* h, const double* theta_t, const double*
 extern "C" lbm_status lbm_stefan_adjoint_step(lbm_stefan* h, const double* theta_t, const double* theta_t1,
                                               const void* adj_in, void* adj_out)
 {
+    if (h && h->p.lattice == LBM_D2Q5) return fail(LBM_ERR_ARG, "the adjoint covers D1Q3 and D2Q9");
     if (h && h->hp.method != LBM_IREBM) return fail(LBM_ERR_STATE, "the adjoint is that of the IREBM step");
     if (!h || !theta_t || !theta_t1 || !adj_in || !adj_out) return fail(LBM_ERR_ARG, "NULL argument");
     if (adj_in == adj_out) return fail(LBM_ERR_ARG, "adj_in and adj_out must differ");
@@ -703,6 +723,7 @@ extern "C" lbm_status lbm_stefan_adjoint_step(lbm_stefan* h, const double* theta
 extern "C" lbm_status lbm_stefan_adjoint_run(lbm_stefan* h, int nsteps, const double* theta_traj, void* adj,
                                              void* adj_other, int* result_index)
 {
+    if (h && h->p.lattice == LBM_D2Q5) return fail(LBM_ERR_ARG, "the adjoint covers D1Q3 and D2Q9");
     if (h && h->hp.method != LBM_IREBM) return fail(LBM_ERR_STATE, "the adjoint is that of the IREBM step");
     if (!h || !adj || !adj_other || !result_index || (!theta_traj && nsteps > 0))
         return fail(LBM_ERR_ARG, "NULL argument");
@@ -725,6 +746,7 @@ extern "C" lbm_status lbm_stefan_adjoint_run(lbm_stefan* h, int nsteps, const do
 extern "C" lbm_status lbm_stefan_adjoint_finish(lbm_stefan* h, const void* adj0, double* g_theta0, int on_device,
                                                 double* g_wall, double* g_ste)
 {
+    if (h && h->p.lattice == LBM_D2Q5) return fail(LBM_ERR_ARG, "the adjoint covers D1Q3 and D2Q9");
     if (!h || !adj0) return fail(LBM_ERR_ARG, "NULL argument");
     const size_t n = (size_t)h->hp.nx * h->hp.ny;
     double* dst = (g_theta0 && on_device) ? g_theta0 : h->dscratch;
@@ -876,7 +898,7 @@ static cudaError_t batch_launch_one(lbm_stefan_batch* b, int parity)
     cudaError_t e = b->use_tma ? lbm::launch_d2q9_tma(a, b->tma, b->stream)
                                : lbm::launch_d2q9_step(b->precision, a, b->grid, b->stream);
     if (e != cudaSuccess) return e;
-    return lbm::launch_newton_jobs(b->precision,
+    return lbm::launch_newton_jobs(b->precision, 9,
                                    job_args(b->dprobs, b->count, parity, nullptr, b->dstats, b->dticket, b->djobs,
                                             b->djob_count),
                                    b->stream);
@@ -1250,7 +1272,7 @@ extern "C" lbm_status lbm_stefan_step_d2q9_noalloc(const lbm_stefan_params* p, c
     a.jobs = sc->jobs;
     a.job_count = &sc->job_count;
     CUDA_TRY(lbm::launch_d2q9_step(p->precision, a, (hp.ntiles + lbm::kWarpsPerBlock - 1) / lbm::kWarpsPerBlock, st));
-    CUDA_TRY(lbm::launch_newton_jobs(p->precision,
+    CUDA_TRY(lbm::launch_newton_jobs(p->precision, 9,
                                      job_args(&sc->prob, 1, 0, nullptr, &sc->stats, &sc->ticket, sc->jobs, &sc->job_count),
                                      st));
     // report a device-detected Newton failure: read the flag (this waits for the step)

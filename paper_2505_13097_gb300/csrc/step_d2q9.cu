@@ -26,7 +26,7 @@
 // take the exact saturated branch (phi = 0 or 1 on both sides of Eq. 14, so
 // theta' = m0 and the source vanishes) without any FP64 work.
 // FP64 form: everything in FP64 (the saturation test uses the integer pipe).
-#include "lbm_device.cuh"
+#include "step_common.cuh"
 
 namespace lbm {
 
@@ -61,22 +61,6 @@ __device__ __forceinline__ void stv<double>(double* p, const double (&v)[2])
     *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
 }
 
-// stores of one thread's N consecutive values (128-, 64- or 32/64-bit)
-__device__ __forceinline__ void stv_n(float* p, const float (&v)[4]) { *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]); }
-__device__ __forceinline__ void stv_n(float* p, const float (&v)[2]) { *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]); }
-__device__ __forceinline__ void stv_n(double* p, const double (&v)[2]) { *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]); }
-__device__ __forceinline__ void stv_n(double* p, const double (&v)[1]) { *p = v[0]; }
-__device__ __forceinline__ void stv_n(float* p, const float (&v)[1]) { *p = v[0]; }
-template <int N>
-__device__ __forceinline__ void st_rec(double* p, const double (&v)[N])
-{
-    if constexpr (N == 1) {
-        *p = v[0];
-    } else {
-#pragma unroll
-        for (int k = 0; k < N; k += 2) *reinterpret_cast<double2*>(p + k) = make_double2(v[k], v[k + 1]);
-    }
-}
 
 // Boundary closures of Sec. 4.2 at one wall node (x, y).  q holds the pulled
 // values (entries of unknown directions are overwritten), u the node's own
@@ -122,21 +106,7 @@ __device__ __noinline__ double wall_closure_d(double* q, const double* u, int x,
         double th = 0.0;
 #pragma unroll
         for (int i = 0; i < 9; ++i) th += u[i];
-        const double theta_d = pb.wall_theta[wi.wall];
-        // the wall node stays within rounding of theta_D: tanh addition theorem with
-        // tanh(z) = z - z^3/3 + 2z^5/15 for |z| <= 1e-4 (remainder < 1e-29), else tanh
-        const double z = (th - theta_d) * pb.inv_delta;
-        double dphi;
-        if (fabs(z) <= 1e-4) {
-            const double z2 = z * z;
-            const double tz = z * (1.0 - z2 * (1.0 / 3.0 - z2 * (2.0 / 15.0)));
-            const double td = pb.wall_tanh[wi.wall];
-            dphi = 0.5 * tz * (1.0 - td) * (1.0 + td) / (1.0 + td * tz);   // phi(theta) - phi(theta_D)
-        } else {
-            dphi = phi_of(th, pb.inv_delta) - pb.wall_phi[wi.wall];
-        }
-        // EEBM: the enthalpy of the wall value (Algorithm 2 keeps H = M0)
-        const double m0t = pb.method == 1 ? pb.wall_H[wi.wall] : theta_d - dphi * pb.inv_ste;
+        const double m0t = dir_m0_target_d(th, wi.wall, pb);
         double known = 0.0, wu = 0.0;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
@@ -163,10 +133,7 @@ __device__ __noinline__ double wall_closure_d(double* q, const double* u, int x,
 }
 
 // FP32 form: the same closure with float-float sums and no FP64 instruction on
-// the common path.  phi(theta) - phi(theta_D) = phi'(theta_D)(theta - theta_D)
-// + O((theta - theta_D)^2/delta^2): the node stays within rounding of theta_D,
-// so the second-order term is below 1e-8 of FP32 resolution whenever
-// |theta - theta_D| <= 1e-4 delta; otherwise the FP64 expression is used.
+// the common path (dir_m0_target_f).
 __device__ __noinline__ ff wall_closure_f(float* q, const float* u, int x, int y, const Problem& pb, int& wall)
 {
     const WallInfo wi = wall_info(x, y, pb);
@@ -185,17 +152,7 @@ __device__ __noinline__ ff wall_closure_f(float* q, const float* u, int x, int y
             if ((wi.unk >> i) & 1) wu += (float)d2_w(i);
             else ff_add(known, q[i]);
         }
-        // m0t = theta_D - (phi(theta) - phi(theta_D))/Ste (EEBM: the wall value's enthalpy)
-        const float dth = (th.hi - pb.wall_th_hi[k]) + (th.lo - pb.wall_th_lo[k]);
-        ff m0t{pb.wall_th_hi[k], pb.wall_th_lo[k]};
-        if (pb.method == 1) {
-            m0t = ff{pb.wall_H_hi[k], pb.wall_H_lo[k]};
-        } else if (fabsf(dth) <= pb.wall_dth_max) {
-            ff_add(m0t, -pb.wall_slope[k] * dth);
-        } else {
-            const double dphi = phi_of(ff_to_double(th), pb.inv_delta) - pb.wall_phi[k];
-            ff_add(m0t, (float)(-dphi * pb.inv_ste));
-        }
+        const ff m0t = dir_m0_target_f(th, k, pb);
         // R = m0t - sum(known), shared by the unknown q in proportion to w_i
         const float r = ((m0t.hi - known.hi) + (m0t.lo - known.lo)) / wu;
 #pragma unroll
@@ -219,35 +176,6 @@ __device__ __noinline__ ff wall_closure_f(float* q, const float* u, int x, int y
     return f;
 }
 
-template <typename P>
-struct Acc;   // per-lane accumulator of sum theta' (float-float or double)
-template <>
-struct Acc<float> {
-    ff s{0.f, 0.f};
-    __device__ void add_ff(const ff& v) { ff_add(s, v.hi); s.lo = __fadd_rn(s.lo, v.lo); }
-    __device__ void add_d(double v) { float h = (float)v; ff_add(s, h); s.lo = __fadd_rn(s.lo, (float)(v - (double)h)); }
-    __device__ double get() const { return ff_to_double(s); }
-};
-template <>
-struct Acc<double> {
-    double s = 0.0;
-    __device__ void add_d(double v) { s += v; }
-    __device__ double get() const { return s; }
-};
-
-// m0 accumulator type per precision
-template <typename P> struct M0T;
-template <> struct M0T<float> { using T = ff; };
-template <> struct M0T<double> { using T = double; };
-
-__device__ __forceinline__ void m0_init(ff& a) { a.hi = 0.f; a.lo = 0.f; }
-__device__ __forceinline__ void m0_init(double& a) { a = 0.0; }
-__device__ __forceinline__ void m0_add(ff& a, float v) { ff_add(a, v); }
-__device__ __forceinline__ void m0_add(double& a, double v) { a += v; }
-__device__ __forceinline__ double m0_d(const ff& a) { return ff_to_double(a); }
-__device__ __forceinline__ double m0_d(const double& a) { return a; }
-__device__ __forceinline__ float m0_f(const ff& a) { return a.hi; }
-__device__ __forceinline__ float m0_f(const double& a) { return approx_float(a); }
 
 template <typename P>
 __device__ __forceinline__ float approx_sum(const P* u);
@@ -268,12 +196,6 @@ __device__ __forceinline__ float approx_sum<double>(const double* u)
     return s;
 }
 
-struct TileSums {
-    double flux = 0.0, phi_sum = 0.0;   // FP64 form
-    ff flux_f{0.f, 0.f};                // FP32 form
-    int dir_count[4] = {0, 0, 0, 0};   // Dirichlet nodes per wall (adds phi(theta_D)/Ste each)
-    int liquid = 0, newton = 0, maxit = 0;
-};
 
 // ---------------------------------------------------------------- row ring
 // Each warp streams its rows through a ring of kStages row slots in shared
@@ -883,44 +805,6 @@ __device__ __forceinline__ void d2q9_tile_direct(const Problem& pb, const P* __r
 #define LBM_STEP_DIRECT 1
 #endif
 
-// A warp's partial sums in a fixed lane order, then exact fixed-point atomics;
-// node counts go to integer counters (the publisher adds their phi/Ste terms).
-template <typename P>
-__device__ __forceinline__ void flush_tile_sums(const Acc<P>& acc, const TileSums& ts, DevStats* st, int lane)
-{
-    Fx e, f;
-    if constexpr (sizeof(P) == 4) {
-        ff se = acc.s, sf = ts.flux_f;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float eh = __shfl_xor_sync(kFull, se.hi, o), el = __shfl_xor_sync(kFull, se.lo, o);
-            const float fh = __shfl_xor_sync(kFull, sf.hi, o), fl = __shfl_xor_sync(kFull, sf.lo, o);
-            ff_add(se, eh);
-            se.lo += el;
-            ff_add(sf, fh);
-            sf.lo += fl;
-        }
-        e = float_to_fixed(se.hi);
-        fx_add(e, float_to_fixed(se.lo));
-        f = float_to_fixed(sf.hi);
-        fx_add(f, float_to_fixed(sf.lo));
-    } else {
-        e = to_fixed(warp_sum(acc.get()));
-        f = to_fixed(warp_sum(ts.flux));
-    }
-    const int nl = warp_sum_i(ts.liquid);
-    int nd[4];
-#pragma unroll
-    for (int w = 0; w < 4; ++w) nd[w] = warp_sum_i(ts.dir_count[w]);
-    if (lane == 0) {
-        acc_add_fx(&st->cur_energy, e);
-        acc_add_fx(&st->cur_flux, f);
-        if (nl) atomicAdd(&st->cur_liquid, (unsigned long long)nl);
-#pragma unroll
-        for (int w = 0; w < 4; ++w)
-            if (nd[w]) atomicAdd(&st->cur_dir[w], (unsigned long long)nd[w]);
-    }
-}
 
 
 
@@ -1161,13 +1045,14 @@ __global__ void __launch_bounds__(kTmaThreads, 5) d2q9_tma_kernel(const StepArgs
 
 // ---------------------------------------------------------------- Newton jobs
 // Local Newton solves deferred by the step kernel (Eq. 14, mixed-precision
-// form), one job per lane, consecutive jobs per warp.  For each job:
+// form), one job per lane, consecutive jobs per warp; Q = 9 (D2Q9) or 5 (D2Q5)
+// planes.  For each job:
 //   theta' = m0 + (phi(theta) - phi(root))/Ste,  c = theta' - (1-omega) m0,
 //   Omega~_i = (1-omega) q_i + w_i c   (q_i was stored by the step kernel).
 // Energy contributions theta' + phi(theta')/Ste are summed per problem as
 // exact 128-bit fixed-point integers (independent of the job order).  The last
 // warp to finish publishes the step statistics and clears the job list.
-template <typename P, bool REC>
+template <typename P, bool REC, int Q>
 __global__ void __launch_bounds__(128) newton_jobs_kernel(JobArgs a)
 {
     const unsigned count = *reinterpret_cast<volatile unsigned*>(a.job_count);
@@ -1201,8 +1086,8 @@ __global__ void __launch_bounds__(128) newton_jobs_kernel(JobArgs a)
             const int x = jb.node % pb.nx, y = jb.node / pb.nx;
             P* d = static_cast<P*>(pb.state[a.parity ^ 1]) + (long long)(y + 1) * pb.pitch + x;
 #pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                const P wi = (P)d2_w(i);
+            for (int i = 0; i < Q; ++i) {
+                const P wi = (P)lat_w(Q, i);
                 d[i * pb.plane] = fma(omc, d[i * pb.plane], wi * c);
             }
             if (REC) a.rec[(long long)y * pb.pitch + x] = tn;
@@ -1304,19 +1189,27 @@ int d2q9_tma_blocks_per_sm()
     return n > 0 ? n : 1;
 }
 
-cudaError_t launch_newton_jobs(int precision, const JobArgs& a, cudaStream_t s)
+template <int Q>
+static void launch_jobs_q(int precision, const JobArgs& a, int grid, cudaStream_t s)
+{
+    if (precision == 1) {
+        if (a.rec) newton_jobs_kernel<float, true, Q><<<grid, 128, 0, s>>>(a);
+        else newton_jobs_kernel<float, false, Q><<<grid, 128, 0, s>>>(a);
+    } else {
+        if (a.rec) newton_jobs_kernel<double, true, Q><<<grid, 128, 0, s>>>(a);
+        else newton_jobs_kernel<double, false, Q><<<grid, 128, 0, s>>>(a);
+    }
+}
+
+cudaError_t launch_newton_jobs(int precision, int q, const JobArgs& a, cudaStream_t s)
 {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = sms * 8;   // 8 x 128 threads per SM: about one pass over ~150k nodes
-    if (precision == 1) {
-        if (a.rec) newton_jobs_kernel<float, true><<<grid, 128, 0, s>>>(a);
-        else newton_jobs_kernel<float, false><<<grid, 128, 0, s>>>(a);
-    } else {
-        if (a.rec) newton_jobs_kernel<double, true><<<grid, 128, 0, s>>>(a);
-        else newton_jobs_kernel<double, false><<<grid, 128, 0, s>>>(a);
-    }
+    if (q == 9) launch_jobs_q<9>(precision, a, grid, s);
+    else if (q == 5) launch_jobs_q<5>(precision, a, grid, s);
+    else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

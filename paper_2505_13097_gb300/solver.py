@@ -66,6 +66,7 @@ class Stefan:
 
     @classmethod
     def from_case(cls, case, stream=None, **kw):
+        kw.setdefault("bb_mode", case.bb_mode)
         return cls(case.lattice, case.nx, case.ny, case.tau, case.delta, case.ste, case.precision,
                    case.walls, stream=stream, **kw)
 
@@ -102,7 +103,7 @@ class Stefan:
         return a.value, b.value, la, lb
 
     def step_timed(self, nsteps):
-        """Advance nsteps D2Q9 steps launch by launch; returns the mean device
+        """Advance nsteps D2Q9 or D2Q5 steps launch by launch; returns the mean device
         time per step (ms) of the stream/collide kernel and of the job kernel."""
         out = (ctypes.c_double * 2)()
         check(self.lib.lbm_stefan_step_timed(self.h, int(nsteps), ctypes.cast(out, ctypes.POINTER(ctypes.c_double))))

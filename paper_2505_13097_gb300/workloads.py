@@ -20,7 +20,14 @@ benchmark configurations:
                      5,000 steps, FP32 populations;
 * ``adjoint_2d``     D2Q9 1024 x 1024, 2,000 steps, FP32 forward; the target
                      liquid fraction comes from a run with Ste and the wall
-                     temperature raised 5 % and theta0 + 1e-3 N(0,1) (seed 1).
+                     temperature raised 5 % and theta0 + 1e-3 N(0,1) (seed 1);
+* ``cavity_2d``      the paper's 2D case (Sec. 6.2) on D2Q5: the lower-left
+                     quarter of a square cavity of liquid at theta = 1
+                     (T_i = 10 C over T_f = 0 C) frozen from the west and south
+                     walls at theta = -2 (T = -20 C), the north and east walls
+                     symmetry lines closed by Eq. (17); Ste = c (T_i - T_f)/h_sl
+                     = 1.762 * 10 / 338, tau 0.84 and delta 0.01 (the timing
+                     table's values), FP32 populations; 4096 x 4096 by default.
 
 tau = 1.0 wherever the configuration does not fix it (the design doc lists this
 reading).  Walls are given as {"W": (kind, theta), ...} with kind 0 =
@@ -41,7 +48,7 @@ FP64, FP32 = 0, 1
 @dataclasses.dataclass
 class Case:
     name: str
-    lattice: int                  # 1 = D1Q3, 2 = D2Q9
+    lattice: int                  # 1 = D1Q3, 2 = D2Q9, 3 = D2Q5
     nx: int
     ny: int
     tau: float
@@ -53,6 +60,7 @@ class Case:
     theta_init: float = 0.0
     noise: float = 0.0
     seed: int = 0
+    bb_mode: int = 0              # adiabatic walls: 0 mirror, 1 link-wise bounce-back, 2 Eq. (17)
 
     def theta0(self) -> np.ndarray:
         """Initial temperature field, shape (ny, nx), float64."""
@@ -126,6 +134,15 @@ def adjoint_target_case(base: Case, rel=0.05) -> Case:
 def adjoint_target_theta0(base: Case, amp=1e-3, seed=1) -> np.ndarray:
     rng = np.random.Generator(np.random.PCG64(seed))
     return base.theta0() + amp * rng.standard_normal(size=(base.ny, base.nx))
+
+
+CAVITY_STE = 1.762 * 10.0 / 338.0
+
+
+def cavity_2d(n=4096, steps=5000, precision=FP32) -> Case:
+    return Case("cavity_2d_d2q5_%d" % n, 3, n, n, 0.84, 0.01, CAVITY_STE,
+                {"W": (DIRICHLET, -2.0), "S": (DIRICHLET, -2.0), "E": (ADIABATIC, 0.0), "N": (ADIABATIC, 0.0)},
+                steps, precision, theta_init=1.0, bb_mode=2)
 
 
 def random_field(shape, lo, hi, seed) -> np.ndarray:

@@ -56,9 +56,10 @@ def _params(**kw):
 
 
 @pytest.mark.parametrize("bad", [dict(tau=0.5), dict(tau=float("nan")), dict(ste=0.0), dict(delta=-1.0),
-                                 dict(nx=1), dict(lattice=3), dict(precision=2), dict(bb_mode=5),
+                                 dict(nx=1), dict(lattice=4), dict(precision=2), dict(bb_mode=5),
                                  dict(lattice=1, ny=2), dict(lattice=2, ny=1), dict(newton_max_iter=0),
-                                 dict(newton_tol=0.0)])
+                                 dict(newton_tol=0.0), dict(lattice=3, nx=2), dict(lattice=3, ny=2),
+                                 dict(lattice=2, bb_mode=2), dict(lattice=3, bb_mode=3)])
 def test_create_rejects_bad_arguments(lib, bad):
     from paper_2505_13097_gb300 import _abi
     h = ctypes.c_void_p()
