@@ -35,6 +35,8 @@ sys.path.insert(0, ROOT)
 METRIC = "D2Q9 MLUPS incl. local Newton (FP32 vs FP64 form) and adjoint/forward time ratio"
 BYTES_FP32 = 9 * 4 * 2   # algorithmic bytes per node update: each population read once, written once
 BYTES_FP64 = 9 * 8 * 2
+BYTES_D2Q5_FP32 = 5 * 4 * 2   # D2Q5: five populations
+BYTES_D2Q5_FP64 = 5 * 8 * 2
 
 
 def log(*a):
@@ -136,7 +138,7 @@ def bench_single(torch, solver, case, steps, warmup, stream, barrier=None, centr
     ms = time_steps(torch, S, steps, stream)
     st = S.stats()
     # per-kernel device times (CUDA events between the two launches of a step)
-    st["kernel_ms"] = S.step_timed(min(steps, 50)) if case.lattice == 2 else None
+    st["kernel_ms"] = S.step_timed(min(steps, 50)) if case.lattice in (2, 3) else None
     S.close()
     return ms, st
 
@@ -153,6 +155,25 @@ def bench_eebm(torch, solver, case, steps, warmup, stream, nodes, irebm_ms):
     S.close()
     return {"mlups": nodes * steps / ms / 1e3, "ms_per_step": ms / steps, "kernel_ms": k[0],
             "kernel_gbs": BYTES_FP32 * nodes / (k[0] * 1e-3) / 1e9, "irebm_over_eebm": irebm_ms / ms}
+
+
+def bench_d2q5(torch, solver, workloads, steps, warmup, stream, peak):
+    """The paper's 2D cavity (Sec. 6.2) on its D2Q5 lattice with the Eq. (17)
+    closure, 4096^2, FP32 and FP64 populations, window centred on step 2,500."""
+    out = {}
+    for prec, tag, bpn in ((workloads.FP32, "fp32", BYTES_D2Q5_FP32), (workloads.FP64, "fp64", BYTES_D2Q5_FP64)):
+        c = workloads.cavity_2d(precision=prec)
+        n = c.nx * c.ny
+        ms, st = bench_single(torch, solver, c, steps, warmup, stream)
+        k_step, k_job = st["kernel_ms"]
+        gbs = bpn * n / (k_step * 1e-3) / 1e9
+        out[tag] = {"workload": c.name, "mlups": n * steps / ms / 1e3, "ms_per_step": ms / steps,
+                    "kernel": "d2q5_step_kernel<%s,false>" % ("float" if prec == workloads.FP32 else "double"),
+                    "kernel_ms": k_step, "job_kernel_ms": k_job, "bytes_per_node": bpn,
+                    "kernel_gbs": gbs, "kernel_frac": gbs / peak,
+                    "whole_step_gbs": bpn * n / (ms / steps * 1e-3) / 1e9,
+                    "newton_nodes_last_step": st["newton_nodes"]}
+    return out
 
 
 def bench_e2e(torch, solver, case, steps, stream):
@@ -374,6 +395,7 @@ def run_gpu(args):
         extra["batched_256"] = bench_batch(torch, solver, workloads, max(20, args.steps // 2), args.warmup, stream)
         extra["adjoint_1024"] = bench_adjoint(torch, solver, workloads, stream)
         extra["d1q3_512"] = bench_d1q3(torch, solver, workloads, stream)
+        extra["d2q5_cavity_4096"] = bench_d2q5(torch, solver, workloads, args.steps, args.warmup, stream, peak)
     e2e_ms, h2d, d2h = bench_e2e(torch, solver, case, args.steps, stream) if rank == 0 else (0, 0, 0)
 
     if rank == 0:

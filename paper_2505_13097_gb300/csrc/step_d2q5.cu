@@ -447,8 +447,12 @@ __device__ __forceinline__ void d2q5_tile(const Problem& pb, const P* __restrict
     }
 }
 
+// Four resident 128-thread blocks per SM (at most 128 registers, a few values
+// spilled to L1): measured on the 4096^2 cavity, 0.159 ms per FP32 launch
+// against 0.198 ms uncapped (168 registers, three blocks) and 0.177 ms with two
+// floats per lane
 #ifndef LBM_D2Q5_MIN_BLOCKS
-#define LBM_D2Q5_MIN_BLOCKS 1   // minimum resident 128-thread blocks per SM (register cap)
+#define LBM_D2Q5_MIN_BLOCKS 4
 #endif
 
 template <typename P, bool REC>
