@@ -157,14 +157,15 @@ def bench_eebm(torch, solver, case, steps, warmup, stream, nodes, irebm_ms):
             "kernel_gbs": BYTES_FP32 * nodes / (k[0] * 1e-3) / 1e9, "irebm_over_eebm": irebm_ms / ms}
 
 
-def bench_d2q5(torch, solver, workloads, steps, warmup, stream, peak):
+def bench_d2q5(torch, solver, workloads, steps, warmup, stream, peak, n=4096, fp64=True, centre=None):
     """The paper's 2D cavity (Sec. 6.2) on its D2Q5 lattice with the Eq. (17)
-    closure, 4096^2, FP32 and FP64 populations, window centred on step 2,500."""
+    closure, n^2, FP32 and FP64 populations, window centred on step 2,500."""
     out = {}
-    for prec, tag, bpn in ((workloads.FP32, "fp32", BYTES_D2Q5_FP32), (workloads.FP64, "fp64", BYTES_D2Q5_FP64)):
-        c = workloads.cavity_2d(precision=prec)
+    legs = [(workloads.FP32, "fp32", BYTES_D2Q5_FP32)] + ([(workloads.FP64, "fp64", BYTES_D2Q5_FP64)] if fp64 else [])
+    for prec, tag, bpn in legs:
+        c = workloads.cavity_2d(n=n, precision=prec)
         n = c.nx * c.ny
-        ms, st = bench_single(torch, solver, c, steps, warmup, stream)
+        ms, st = bench_single(torch, solver, c, steps, warmup, stream, centre=centre)
         k_step, k_job = st["kernel_ms"]
         gbs = bpn * n / (k_step * 1e-3) / 1e9
         out[tag] = {"workload": c.name, "mlups": n * steps / ms / 1e3, "ms_per_step": ms / steps,
@@ -357,6 +358,13 @@ def run_gpu(args):
     barrier = (lambda: dist.barrier(device_ids=[local])) if dist else None
     stream = torch.cuda.Stream()
     peak, peak_kind = load_peaks()
+    if args.only_d2q5:
+        # profiling aid: the D2Q5 cavity leg alone, FP32
+        if rank == 0:
+            print(json.dumps({"d2q5_cavity": bench_d2q5(torch, solver, workloads, args.steps, args.warmup, stream, peak,
+                                                       n=args.n or 4096, fp64=False, centre=args.window_step)}),
+                  flush=True)
+        return 0
 
     case = workloads.melt_2d() if args.n is None else workloads.melt_2d(n=args.n)
     nodes = case.nx * case.ny
@@ -457,6 +465,8 @@ def main():
                     help="side of the melting workload (default 4096, the benchmark); a profiling aid")
     ap.add_argument("--window-step", type=int, default=None,
                     help="centre the timed window on this step (default: mid-run, step 5,000); a profiling aid")
+    ap.add_argument("--only-d2q5", action="store_true",
+                    help="time the D2Q5 cavity leg alone, FP32, side --n (default 4096); a profiling aid")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
