@@ -97,6 +97,17 @@ def lib():
             l.orc_eebm_step.argtypes = [_P, _D, _D, ctypes.POINTER(Diag)]
             l.orc_eebm_run.restype = ctypes.c_int
             l.orc_eebm_run.argtypes = [_P, _D, ctypes.c_int, _D, _D]
+            l.orc_ilfbm_lever.restype = ctypes.c_double
+            l.orc_ilfbm_lever.argtypes = [ctypes.c_double, ctypes.c_double]
+            l.orc_ilfbm_init.restype = None
+            l.orc_ilfbm_init.argtypes = [_P, _D, _D, _D]
+            l.orc_ilfbm_energy.restype = ctypes.c_double
+            l.orc_ilfbm_energy.argtypes = [_P, _D, _D]
+            l.orc_ilfbm_step.restype = ctypes.c_int
+            l.orc_ilfbm_step.argtypes = [_P, _D, _D, _D, _D, ctypes.c_double, ctypes.c_int, _I,
+                                         ctypes.POINTER(Diag)]
+            l.orc_ilfbm_run.restype = ctypes.c_int
+            l.orc_ilfbm_run.argtypes = [_P, _D, ctypes.c_int, ctypes.c_double, ctypes.c_int, _D, _D, _D, _I]
             _lib = l
     return _lib
 
@@ -237,6 +248,50 @@ class Problem:
                               _dp(f), _dp(th)) < 0:
             raise MemoryError("oracle run")
         return f, th
+
+    # ---- implicit liquid fraction based method (ILFBM, Algorithm 1): state (f, l)
+    def ilfbm_init(self, theta0):
+        self._no_eq17("ILFBM")
+        f = np.empty((self.q, self.ny, self.nx))
+        ell = np.empty(self.shape)
+        lib().orc_ilfbm_init(ctypes.byref(self.p), _dp(_f64(theta0).reshape(self.shape)), _dp(f), _dp(ell))
+        return f, ell
+
+    def ilfbm_energy(self, f, ell):
+        """sum theta + l/Ste, theta = M0(f)."""
+        return lib().orc_ilfbm_energy(ctypes.byref(self.p), _dp(_f64(f)), _dp(_f64(ell)))
+
+    def ilfbm_step(self, f, ell, tol=1e-12, maxit=200):
+        """One step of Algorithm 1: (f~, l~, inner iterations, converged, diagnostics)."""
+        self._no_eq17("ILFBM")
+        f, ell = _f64(f), _f64(ell)
+        fn, ln = np.empty_like(f), np.empty_like(ell)
+        it = ctypes.c_int()
+        d = Diag()
+        r = lib().orc_ilfbm_step(ctypes.byref(self.p), _dp(f), _dp(ell), _dp(fn), _dp(ln), float(tol), int(maxit),
+                                 ctypes.byref(it), ctypes.byref(d))
+        if r < 0:
+            raise MemoryError("oracle step")
+        return fn, ln, it.value, r == 0, dict(energy_before=d.energy_before, energy_after=d.energy_after,
+                                              flux=d.flux)
+
+    def ilfbm_run(self, theta0, nsteps, tol=1e-12, maxit=200):
+        """``nsteps`` ILFBM steps from (w_i theta0, [theta0 > 0]): (f, l, theta,
+        steps whose inner loop did not converge, largest inner iteration count)."""
+        self._no_eq17("ILFBM")
+        f = np.empty((self.q, self.ny, self.nx))
+        ell, th = np.empty(self.shape), np.empty(self.shape)
+        mx = ctypes.c_int()
+        r = lib().orc_ilfbm_run(ctypes.byref(self.p), _dp(_f64(theta0).reshape(self.shape)), int(nsteps), float(tol),
+                                int(maxit), _dp(f), _dp(ell), _dp(th), ctypes.byref(mx))
+        if r < 0:
+            raise MemoryError("oracle run")
+        return f, ell, th, r, mx.value
+
+
+def ilfbm_lever(H, ste):
+    """Lever rule of Algorithm 1: l(H) = 0 below 0, Ste H on [0, 1/Ste], 1 above."""
+    return lib().orc_ilfbm_lever(float(H), float(ste))
 
 
 def eebm_theta(H, ste):

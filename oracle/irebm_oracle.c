@@ -706,3 +706,192 @@ int orc_eebm_run(const orc_params* p, const double* theta0, int nsteps, double* 
     free(b);
     return 0;
 }
+
+/* ======================================================================
+ * Implicit liquid fraction based method (ILFBM), Algorithm 1 (Sec. 3.3),
+ * the paper's second comparison scheme.  The distributions carry the
+ * temperature, theta = M0(f), f_i^eq = w_i theta; a separate field l (the
+ * liquid fraction) enters through the source g_i = (w_i/Ste)(l - l~), and l~
+ * is found by an inner loop of collision, streaming and the lever rule
+ *     l(H) = 0 if H < 0,  Ste H if 0 <= H <= 1/Ste,  1 if H > 1/Ste.
+ * One step from (f, l):
+ *     theta = M0(f); l^(0) = l; for k = 1, 2, ...:
+ *         Omega_i = f_i - (f_i - w_i theta)/tau + (w_i/Ste)(l - l^(k-1))
+ *         f^(k)_i(y) = Omega_i(y - e_i), closures on the unknown ones
+ *         H^(k) = M0(f^(k)) + l^(k-1)/Ste,   l^(k) = l(H^(k))
+ *     until max_y |l^(k) - l^(k-1)| <= tol (or k = maxit: not converged);
+ *     f~ = f^(k), l~ = l^(k).
+ * Readings (the algorithm names the loop's test but not its form):
+ *  - the printed first line of Algorithm 1 ("H <- phi(theta)") is not used:
+ *    H is formed in the loop;
+ *  - convergence: the largest change of l over the lattice is at most tol
+ *    (f^(k) depends on l^(k-1) only through the source, so it settles with l);
+ *  - closures on the streamed f: Dirichlet makes M0(f~) = theta_D, the
+ *    unknowns sharing the rest by weight; bounce-back as for IREBM; a
+ *    Dirichlet node's liquid fraction is that of its wall value, [theta_D > 0];
+ *  - initial l = [theta0 > 0] (the phase of the initial temperature).
+ * ====================================================================== */
+double orc_ilfbm_lever(double H, double ste)
+{
+    if (H < 0.0) return 0.0;
+    if (H > 1.0 / ste) return 1.0;
+    return ste * H;
+}
+
+void orc_ilfbm_init(const orc_params* p, const double* theta0, double* f, double* ell)
+{
+    int q = lat_q(p), n = p->nx * p->ny, x, y, i, ex, ey;
+    double w;
+    for (y = 0; y < p->ny; y++)
+        for (x = 0; x < p->nx; x++) {
+            double th = theta0[y * p->nx + x], td;
+            if (node_dirichlet(p, x, y, &td, NULL)) th = td;
+            for (i = 0; i < q; i++) {
+                lat_vec(p, i, &ex, &ey, &w);
+                f[i * n + y * p->nx + x] = w * th;
+            }
+            ell[y * p->nx + x] = th > 0.0 ? 1.0 : 0.0;
+        }
+}
+
+/* sum_x theta + l/Ste with theta = M0(f) */
+double orc_ilfbm_energy(const orc_params* p, const double* f, const double* ell)
+{
+    int q = lat_q(p), n = p->nx * p->ny, k, i;
+    double e = 0.0;
+    for (k = 0; k < n; k++) {
+        double th = 0.0;
+        for (i = 0; i < q; i++) th += f[i * n + k];
+        e += th + ell[k] / p->ste;
+    }
+    return e;
+}
+
+/* One ILFBM step (f, ell) -> (fn, elln).  Returns 0 when the inner loop
+ * converged, 1 when it reached maxit, -1 on allocation failure; *iters gets
+ * the number of inner iterations; diag (may be NULL): energies before and
+ * after and the boundary flux of the last inner iteration. */
+int orc_ilfbm_step(const orc_params* p, const double* f, const double* ell, double* fn, double* elln, double tol,
+                   int maxit, int* iters, orc_diag* diag)
+{
+    const int q = lat_q(p), nx = p->nx, ny = p->ny, n = nx * ny;
+    double* theta = (double*)malloc(sizeof(double) * n);
+    double* Om = (double*)malloc(sizeof(double) * q * n);
+    double* lprev = (double*)malloc(sizeof(double) * n);
+    double flux = 0.0;
+    int x, y, i, k, it = 0, converged = 0;
+    int ex[ORC_MAXQ], ey[ORC_MAXQ], opp[ORC_MAXQ];
+    double w[ORC_MAXQ];
+    if (!theta || !Om || !lprev) { free(theta); free(Om); free(lprev); return -1; }
+    for (i = 0; i < q; i++) { lat_vec(p, i, &ex[i], &ey[i], &w[i]); opp[i] = lat_opp(p, i); }
+
+    /* moments: theta = M0(f); inner loop initialization l^(0) = l */
+    orc_theta(p, f, theta);
+    memcpy(lprev, ell, sizeof(double) * n);
+    while (!converged && it < maxit) {
+        double change = 0.0;
+        it++;
+        /* collision with the source of the current liquid-fraction iterate */
+        for (i = 0; i < q; i++)
+            for (k = 0; k < n; k++)
+                Om[i * n + k] = f[i * n + k] - (f[i * n + k] - w[i] * theta[k]) / p->tau +
+                                w[i] / p->ste * (ell[k] - lprev[k]);
+        /* streaming and closures */
+        flux = 0.0;
+        for (y = 0; y < ny; y++)
+            for (x = 0; x < nx; x++)
+                for (i = 0; i < q; i++)
+                    if (!inside(p, x + ex[i], y + ey[i])) flux -= Om[i * n + y * nx + x];
+        for (y = 0; y < ny; y++)
+            for (x = 0; x < nx; x++) {
+                double qv[ORC_MAXQ], td;
+                int known[ORC_MAXQ], nunk = 0;
+                k = y * nx + x;
+                for (i = 0; i < q; i++) {
+                    int sx = x - ex[i], sy = y - ey[i];
+                    known[i] = inside(p, sx, sy);
+                    qv[i] = known[i] ? Om[i * n + sy * nx + sx] : 0.0;
+                    if (!known[i]) nunk++;
+                }
+                if (nunk > 0) {
+                    if (node_dirichlet(p, x, y, &td, NULL)) {
+                        double rest = td, wu = 0.0;
+                        for (i = 0; i < q; i++) {
+                            if (known[i]) rest -= qv[i];
+                            else wu += w[i];
+                        }
+                        for (i = 0; i < q; i++)
+                            if (!known[i]) qv[i] = w[i] * rest / wu;
+                    } else {
+                        for (i = 0; i < q; i++)
+                            if (!known[i]) {
+                                if (p->bb_mode == 0 && known[opp[i]]) qv[i] = qv[opp[i]];
+                                else qv[i] = Om[opp[i] * n + k];
+                            }
+                    }
+                    for (i = 0; i < q; i++)
+                        if (!known[i]) flux += qv[i];
+                }
+                for (i = 0; i < q; i++) fn[i * n + k] = qv[i];
+            }
+        /* enthalpy and lever rule; Dirichlet nodes keep the phase of their wall value */
+        for (y = 0; y < ny; y++)
+            for (x = 0; x < nx; x++) {
+                double m0 = 0.0, td, lk;
+                k = y * nx + x;
+                for (i = 0; i < q; i++) m0 += fn[i * n + k];
+                if (node_dirichlet(p, x, y, &td, NULL)) lk = td > 0.0 ? 1.0 : 0.0;
+                else lk = orc_ilfbm_lever(m0 + lprev[k] / p->ste, p->ste);
+                if (fabs(lk - lprev[k]) > change) change = fabs(lk - lprev[k]);
+                elln[k] = lk;
+            }
+        converged = change <= tol;
+        memcpy(lprev, elln, sizeof(double) * n);
+    }
+    if (iters) *iters = it;
+    if (diag) {
+        diag->energy_before = orc_ilfbm_energy(p, f, ell);
+        diag->energy_after = orc_ilfbm_energy(p, fn, elln);
+        diag->flux = flux;
+        diag->max_iter = it;
+        diag->failed = !converged;
+    }
+    free(theta);
+    free(Om);
+    free(lprev);
+    return converged ? 0 : 1;
+}
+
+/* nsteps ILFBM steps from (w_i theta0, [theta0 > 0]): final f, l and theta;
+ * the number of steps whose inner loop did not converge, -1 on allocation
+ * failure; *max_iters the largest inner iteration count */
+int orc_ilfbm_run(const orc_params* p, const double* theta0, int nsteps, double tol, int maxit, double* f_out,
+                  double* ell_out, double* theta_out, int* max_iters)
+{
+    const int q = lat_q(p), n = p->nx * p->ny;
+    double* a = (double*)malloc(sizeof(double) * q * n);
+    double* b = (double*)malloc(sizeof(double) * q * n);
+    double* la = (double*)malloc(sizeof(double) * n);
+    double* lb = (double*)malloc(sizeof(double) * n);
+    int s, failed = 0, mx = 0;
+    if (!a || !b || !la || !lb) { free(a); free(b); free(la); free(lb); return -1; }
+    orc_ilfbm_init(p, theta0, a, la);
+    for (s = 0; s < nsteps; s++) {
+        double* t;
+        int it = 0, r = orc_ilfbm_step(p, a, la, b, lb, tol, maxit, &it, NULL);
+        if (r < 0) { failed = -1; break; }
+        failed += r;
+        if (it > mx) mx = it;
+        t = a; a = b; b = t;
+        t = la; la = lb; lb = t;
+    }
+    if (f_out) memcpy(f_out, a, sizeof(double) * q * n);
+    if (ell_out) memcpy(ell_out, la, sizeof(double) * n);
+    if (theta_out) orc_theta(p, a, theta_out);
+    if (max_iters) *max_iters = mx;
+    free(a);
+    free(b);
+    free(la);
+    free(lb);
+    return failed;
+}

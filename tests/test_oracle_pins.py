@@ -641,3 +641,120 @@ def test_eq17_argument_checks(orc):
     P = orc.Problem(3, 8, 8, bb_mode=2)
     with pytest.raises(NotImplementedError):
         P.adjoint(np.zeros((8, 8)), 2, np.zeros((8, 8)))
+
+
+# ---------------------------------------------------------------- ILFBM (Algorithm 1)
+def test_ilfbm_lever_rule():
+    from oracle import ilfbm_lever
+    ste = 0.25
+    assert ilfbm_lever(-1e-9, ste) == 0.0 and ilfbm_lever(0.0, ste) == 0.0
+    assert ilfbm_lever(2.0, ste) == 0.5 and ilfbm_lever(4.0, ste) == 1.0 and ilfbm_lever(4.5, ste) == 1.0
+
+
+@pytest.mark.parametrize("lattice,shape", [(1, (1, 40)), (2, (9, 11)), (3, (8, 12))])
+def test_ilfbm_single_phase_is_eebm(orc, lattice, shape):
+    # a lattice that stays solid: l = 0 throughout, the source vanishes, and
+    # Algorithm 1 is the plain BGK step, as is Algorithm 2 below the melting point
+    ny, nx = shape
+    th0 = workloads.random_field(shape, -2.0, -1.0, seed=51)
+    walls = {"W": (1, -1.5), "E": (0, 0.0)}
+    P = orc.Problem(lattice, nx, ny, tau=0.7, delta=0.01, ste=0.3, walls=walls)
+    _, ell, th, failed, mx = P.ilfbm_run(th0, 80)
+    _, th_e = P.eebm_run(th0, 80)
+    assert failed == 0 and mx == 1 and np.all(ell == 0.0)
+    # the two equilibria round differently (w_0 theta against H - (1 - w_0) theta)
+    assert np.max(np.abs(th - th_e)) <= 1e-13
+
+
+@pytest.mark.parametrize("lattice,shape", [(1, (1, 60)), (2, (10, 14))])
+def test_ilfbm_conserves_energy_in_a_closed_box(orc, lattice, shape):
+    # link-wise bounce-back: every inner iteration keeps sum theta + l^(k-1)/Ste,
+    # so a converged step conserves sum theta + l/Ste to the loop's tolerance
+    ny, nx = shape
+    P = orc.Problem(lattice, nx, ny, tau=0.8, delta=0.01, ste=0.5, bb_mode=1)
+    f, ell = P.ilfbm_init(workloads.random_field(shape, -0.6, 0.6, seed=52))
+    e0 = P.ilfbm_energy(f, ell)
+    for _ in range(60):
+        f, ell, it, ok, d = P.ilfbm_step(f, ell, tol=1e-13)
+        assert ok
+        assert abs(d["energy_after"] - d["energy_before"]) <= nx * ny * 1e-13 / 0.5 + 1e-12 * abs(e0)
+    assert abs(P.ilfbm_energy(f, ell) - e0) <= 60 * nx * ny * 1e-13 / 0.5 + 1e-11 * abs(e0)
+
+
+def test_ilfbm_converged_step_is_a_lever_rule_fixed_point(orc):
+    # at convergence l~ = l(theta~ + l~/Ste) (Algorithm 1's last two lines with
+    # l^(k) = l^(k-1)); a node strictly between the phases then sits at the
+    # melting point, theta~ = 0 (isothermal phase change)
+    from oracle import ilfbm_lever
+    ste, tol = 0.3, 1e-13
+    P = orc.Problem(1, 80, 1, tau=0.62, delta=0.01, ste=ste, walls={"W": (1, 1.0), "E": (1, -0.5)})
+    f, ell = P.ilfbm_init(np.full((1, 80), -0.5))
+    mushy = 0
+    for _ in range(400):
+        f, ell, it, ok, _ = P.ilfbm_step(f, ell, tol=tol)
+        assert ok
+    th = f.sum(axis=0)[0]
+    for x in range(1, 79):
+        assert abs(ell[0, x] - ilfbm_lever(th[x] + ell[0, x] / ste, ste)) <= 2 * tol
+        if 0.0 < ell[0, x] < 1.0:
+            mushy += 1
+            assert abs(th[x]) <= 2 * tol / ste
+    assert mushy >= 1
+
+
+def test_ilfbm_inner_loop_fails_on_the_d2q5_cavity(orc):
+    # Sec. 6.2: the paper reports that ILFBM's inner iterations did not converge
+    # in its 2D case; the oracle's loop does not converge either in some steps
+    # of the D2Q5 cavity (200 iterations), while the D1Q3 bar converges
+    c = workloads.cavity_2d(n=32, steps=150, precision=workloads.FP64)
+    P = orc.Problem(3, c.nx, c.ny, tau=c.tau, delta=c.delta, ste=c.ste, walls=c.walls)
+    *_, failed, mx = P.ilfbm_run(c.theta0(), c.steps, maxit=200)
+    assert failed > 0 and mx == 200
+    P1 = orc.Problem(1, 64, 1, tau=0.62, delta=0.01, ste=0.2857, walls={"W": (1, 1.0), "E": (1, -0.5)})
+    *_, failed1, mx1 = P1.ilfbm_run(np.full((1, 64), -0.5), 1500, maxit=200)
+    assert failed1 == 0 and mx1 < 200
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("method", ["eebm", "ilfbm"])
+def test_paper_1d_case_printed_error_comparison_schemes(orc, method):
+    """Sec. 6.1, the final-time solution figure: maximum temperature error
+    4.06e-3 (EEBM) and 4.50e-3 (ILFBM) on the same bar as the IREBM case
+    (N = 801, 160 s), tau = 0.62 (the timing table's value).  Without
+    regularization the front jumps from node to node and the error
+    oscillates as it does (the paper's interface-error figure shows the same
+    for these two schemes), so the time at which it is read matters: the
+    printed value must lie within the band the maximum error sweeps over the
+    last cell crossing of the front before 160 s, 7,200 steps at the final
+    front speed lambda / sqrt(t)."""
+    g = json.load(open(os.path.join(GOLDEN, "paper_1d_case.json")))
+    ste, th0, n, tau = g["ste"], g["theta0"], g["N"], g["tau"]
+    lam = neumann.stefan_lambda(ste, th0)
+    t0 = (g["x_f0"] / (2 * lam)) ** 2
+    dx = 1.0 / (n - 1)
+    dt = (tau - 0.5) * dx * dx / 3.0
+    steps = int(round((g["t_final"] - t0) / dt))
+    window = int(round(dx / (lam / np.sqrt(g["t_final"])) / dt))
+    x = np.arange(n) * dx
+    P = orc.Problem(1, n, 1, tau=tau, delta=g["delta"], ste=ste, walls={"W": (1, 1.0), "E": (1, th0)})
+    init = neumann.profile(x, t0, ste, th0, lam)[None, :]
+    errs = []
+    if method == "eebm":
+        f, _ = P.eebm_run(init, steps - window)
+    else:
+        f, ell, _, failed, _ = P.ilfbm_run(init, steps - window, tol=1e-12, maxit=200)
+        assert failed == 0
+    for k in range(1, window + 1):
+        if method == "eebm":
+            f = P.eebm_step(f)
+        else:
+            f, ell, _, ok, _ = P.ilfbm_step(f, ell, tol=1e-12, maxit=200)
+            assert ok
+        if k % 100 == 0 or k == window:
+            th = f.sum(axis=0)[0] if method == "ilfbm" else P.eebm_fields(f)[0][0]
+            exact = neumann.profile(x, t0 + (steps - window + k) * dt, ste, th0, lam)
+            errs.append(np.max(np.abs(th - exact)))
+    ref = g["max_error_" + method]
+    assert min(errs) <= ref <= max(errs), (min(errs), max(errs))
+    # and the band is that of a staircase front, not of a wrong scheme
+    assert max(errs) < 3 * ref and min(errs) > ref / 3
