@@ -164,15 +164,15 @@ def bench_d2q5(torch, solver, workloads, steps, warmup, stream, peak, n=4096, fp
     legs = [(workloads.FP32, "fp32", BYTES_D2Q5_FP32)] + ([(workloads.FP64, "fp64", BYTES_D2Q5_FP64)] if fp64 else [])
     for prec, tag, bpn in legs:
         c = workloads.cavity_2d(n=n, precision=prec)
-        n = c.nx * c.ny
+        nodes = c.nx * c.ny
         ms, st = bench_single(torch, solver, c, steps, warmup, stream, centre=centre)
         k_step, k_job = st["kernel_ms"]
-        gbs = bpn * n / (k_step * 1e-3) / 1e9
-        out[tag] = {"workload": c.name, "mlups": n * steps / ms / 1e3, "ms_per_step": ms / steps,
+        gbs = bpn * nodes / (k_step * 1e-3) / 1e9
+        out[tag] = {"workload": c.name, "mlups": nodes * steps / ms / 1e3, "ms_per_step": ms / steps,
                     "kernel": "d2q5_step_kernel<%s,false>" % ("float" if prec == workloads.FP32 else "double"),
                     "kernel_ms": k_step, "job_kernel_ms": k_job, "bytes_per_node": bpn,
                     "kernel_gbs": gbs, "kernel_frac": gbs / peak,
-                    "whole_step_gbs": bpn * n / (ms / steps * 1e-3) / 1e9,
+                    "whole_step_gbs": bpn * nodes / (ms / steps * 1e-3) / 1e9,
                     "newton_nodes_last_step": st["newton_nodes"]}
     return out
 
