@@ -55,7 +55,7 @@ enum { LBM_FP64 = 0, LBM_FP32 = 1 };                           /* population sto
 enum { LBM_WALL_W = 0, LBM_WALL_E = 1, LBM_WALL_S = 2, LBM_WALL_N = 3 };
 enum { LBM_ADIABATIC = 0, LBM_DIRICHLET = 1 };                 /* wall kinds (Sec. 4.2) */
 enum { LBM_BB_MIRROR = 0, LBM_BB_LINK = 1, LBM_NEU_EQ17 = 2 }; /* adiabatic-wall closures */
-enum { LBM_IREBM = 0, LBM_EEBM = 1 };                          /* step method (Algorithms 3 and 2) */
+enum { LBM_IREBM = 0, LBM_EEBM = 1, LBM_ILFBM = 2 };           /* step method (Algorithms 3, 2, 1) */
 
 typedef struct {
     int lattice;          /* LBM_D1Q3, LBM_D2Q9 or LBM_D2Q5 */
@@ -87,7 +87,10 @@ typedef struct {
     int error;             /* sticky device error (lbm_status value, 0 if none) */
 } lbm_stefan_stats;
 
-/* ---------------------------------------------------------------- one problem */
+/* ---------------------------------------------------------------- one problem
+ * State buffers (lbm_stefan_layout): q planes of populations (ny + 2 rows of
+ * row_stride elements each, the first and last rows zero halo rows); D1Q3
+ * adds a fourth plane, the liquid fraction of LBM_ILFBM. */
 
 /* Create a problem.  cuda_stream is a cudaStream_t (NULL = legacy default
  * stream).  All walls start adiabatic; the state is undefined until set_ic. */
@@ -111,7 +114,20 @@ lbm_status lbm_stefan_set_bc(lbm_stefan* h, int wall, int kind, double theta_wal
  * liquid fraction min(max(Ste H, 0), 1) and H; the energy statistics are the
  * sum of H; the adjoint calls return LBM_ERR_STATE.  Discards the state: call
  * lbm_stefan_set_ic afterwards.  LBM_ERR_ARG for an unknown method or a
- * lattice other than D2Q9. */
+ * lattice other than D2Q9.
+ * LBM_ILFBM: the implicit liquid fraction based method of Algorithm 1
+ * (Sec. 3.3), the paper's other comparison scheme, D1Q3 in FP64 up to 2,844
+ * nodes: theta = M0(f), f_i^eq = w_i theta, and a liquid-fraction field l
+ * (the fourth plane of the D1Q3 state, zero for the other methods) updated
+ * by an inner loop of collision with the source (w_i/Ste)(l - l^(k-1)),
+ * streaming, H^(k) = M0(f^(k)) + l^(k-1)/Ste and the lever rule l(H) = 0,
+ * Ste H, 1 (H < 0, in [0, 1/Ste], above), until max |l^(k) - l^(k-1)| <=
+ * newton_tol; newton_max_iter bounds the loop (reaching it sets
+ * LBM_ERR_NEWTON).  Dirichlet nodes hold theta_D with l = [theta_D > 0];
+ * set_ic puts l = [theta0 > 0].  get_fields returns theta, phi = l and
+ * H = theta + l/Ste; the energy statistics are the sum of H and
+ * newton_max_iter the last step's inner iteration count; step_record,
+ * step_timed and the adjoint calls return LBM_ERR_STATE / LBM_ERR_ARG. */
 lbm_status lbm_stefan_set_method(lbm_stefan* h, int method);
 
 /* Initial state: f_i = w_i theta0 (equilibrium), Dirichlet nodes at their wall

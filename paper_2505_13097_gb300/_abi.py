@@ -17,7 +17,7 @@ LBM_D1Q3, LBM_D2Q9, LBM_D2Q5 = 1, 2, 3
 LBM_FP64, LBM_FP32 = 0, 1
 LBM_ADIABATIC, LBM_DIRICHLET = 0, 1
 LBM_BB_MIRROR, LBM_BB_LINK, LBM_NEU_EQ17 = 0, 1, 2
-LBM_IREBM, LBM_EEBM = 0, 1
+LBM_IREBM, LBM_EEBM, LBM_ILFBM = 0, 1, 2
 WALLS = {"W": 0, "E": 1, "S": 2, "N": 3}
 
 

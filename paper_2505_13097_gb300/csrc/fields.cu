@@ -1,7 +1,9 @@
 // State initialization and field extraction.
 //  * init: f_i = w_i theta0 (equilibrium, so Omega_i = w_i theta0), with nodes on
-//    a Dirichlet wall set to the wall value; accumulates E(0).
-//  * fields: theta = M0(f) = sum_i Omega_i, phi(theta), H = theta + phi/Ste (Sec. 2).
+//    a Dirichlet wall set to the wall value; accumulates E(0).  EEBM: the
+//    equilibrium of H(theta0); ILFBM: also l = [theta0 > 0] in plane q.
+//  * fields: theta = M0(f) = sum_i Omega_i, phi(theta), H = theta + phi/Ste (Sec. 2);
+//    EEBM: theta = Theta(H); ILFBM: phi = l.
 #include "lbm_device.cuh"
 
 namespace lbm {
@@ -40,6 +42,13 @@ __global__ void init_state_kernel(const Problem* dprob, const double* __restrict
             continue;
         }
         for (int i = 0; i < pb.q; ++i) s[i * pb.plane + (long long)(y + 1) * pb.pitch + x] = (P)(lat_w(pb.q, i) * th);
+        if (pb.method == 2) {
+            // ILFBM (Algorithm 1): the liquid fraction of the initial phase, plane q
+            const double l = th > 0.0 ? 1.0 : 0.0;
+            s[pb.q * pb.plane + (long long)(y + 1) * pb.pitch + x] = (P)l;
+            e += th + l * pb.inv_ste;
+            continue;
+        }
         e += th + phi_of(th, pb.inv_delta) * pb.inv_ste;
     }
     e = warp_sum(e);
@@ -102,7 +111,9 @@ __global__ void fields_kernel(const Problem* dprob, int parity, double* theta, d
             if (theta_plane) theta_plane[(long long)y * pb.pitch + x] = th;
             continue;
         }
-        const double ph = phi_of(th, pb.inv_delta);
+        // ILFBM: the liquid fraction is a field of its own (plane q)
+        const double ph = pb.method == 2 ? (double)s[pb.q * pb.plane + (long long)(y + 1) * pb.pitch + x]
+                                         : phi_of(th, pb.inv_delta);
         if (theta) theta[k] = th;
         if (phi) phi[k] = ph;
         if (H) H[k] = th + ph * pb.inv_ste;

@@ -357,7 +357,8 @@ extern "C" lbm_status lbm_stefan_create(const lbm_stefan_params* p, void* cuda_s
     const int pitch = state_pitch(p->lattice, p->precision, p->nx);
     fill_problem(h->hp, q, p->nx, p->ny, pitch, p->tau, p->delta, p->ste, p->newton_tol, p->newton_max_iter,
                  p->bb_mode, 16, segw, p->precision);
-    h->state_bytes = (size_t)q * h->hp.plane * h->elem;
+    // D1Q3: a fourth plane holds the liquid fraction of ILFBM (Algorithm 1), zero otherwise
+    h->state_bytes = (size_t)(q == 3 ? 4 : q) * h->hp.plane * h->elem;
     cudaError_t e = cudaSuccess;
     void* bufs[2] = {nullptr, nullptr};
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
@@ -408,8 +409,11 @@ extern "C" lbm_status lbm_stefan_set_bc(lbm_stefan* h, int wall, int kind, doubl
 extern "C" lbm_status lbm_stefan_set_method(lbm_stefan* h, int method)
 {
     if (!h) return fail(LBM_ERR_ARG, "NULL handle");
-    if (method != LBM_IREBM && method != LBM_EEBM) return fail(LBM_ERR_ARG, "method must be 0 (IREBM) or 1 (EEBM)");
+    if (method != LBM_IREBM && method != LBM_EEBM && method != LBM_ILFBM)
+        return fail(LBM_ERR_ARG, "method must be 0 (IREBM), 1 (EEBM) or 2 (ILFBM)");
     if (method == LBM_EEBM && h->p.lattice != LBM_D2Q9) return fail(LBM_ERR_ARG, "EEBM is implemented for D2Q9");
+    if (method == LBM_ILFBM && (h->p.lattice != LBM_D1Q3 || h->precision != LBM_FP64 || !lbm::ilfbm_d1q3_fits(h->hp.nx)))
+        return fail(LBM_ERR_ARG, "ILFBM is implemented for D1Q3 in FP64 up to 2,844 nodes");
     h->hp.method = method;
     h->ic = false;   // the state of one method is not a state of the other
     h->graph.reset();
@@ -459,6 +463,14 @@ extern "C" lbm_status lbm_stefan_step(lbm_stefan* h, int nsteps)
     if (nsteps < 0) return fail(LBM_ERR_ARG, "nsteps must be >= 0");
     if (!h->ic) return fail(LBM_ERR_STATE, "set_ic must come before step");
     if (nsteps == 0) return LBM_OK;
+    if (h->hp.method == LBM_ILFBM) {
+        // all steps in one launch (one block over the lattice, whose barriers
+        // separate the inner iterations)
+        StepArgs a = single_args(h, h->parity, nullptr);
+        CUDA_TRY(lbm::launch_ilfbm_d1q3(a, h->hp, nsteps, h->stream));
+        h->parity ^= nsteps & 1;
+        return LBM_OK;
+    }
     if (h->p.lattice == LBM_D1Q3 && lbm::d1q3_fused_fits(h->precision, h->hp.nx)) {
         StepArgs a = single_args(h, h->parity, nullptr);
         CUDA_TRY(lbm::launch_d1q3_fused(h->precision, a, h->hp, nsteps, h->parity, nullptr, h->stream));
@@ -542,6 +554,7 @@ extern "C" lbm_status lbm_stefan_step_record(lbm_stefan* h, int nsteps, double* 
     if (!h || (!traj && nsteps > 0)) return fail(LBM_ERR_ARG, "NULL argument");
     if (nsteps < 0) return fail(LBM_ERR_ARG, "nsteps must be >= 0");
     if (!h->ic) return fail(LBM_ERR_STATE, "set_ic must come before step_record");
+    if (h->hp.method == LBM_ILFBM) return fail(LBM_ERR_STATE, "step_record records the IREBM and EEBM steps");
     const long long plane = (long long)h->hp.ny * h->hp.pitch;
     if (h->p.lattice == LBM_D1Q3 && lbm::d1q3_fused_fits(h->precision, h->hp.nx)) {
         StepArgs a = single_args(h, h->parity, nullptr);

@@ -1,0 +1,147 @@
+"""ILFBM (Algorithm 1, the implicit liquid fraction based method) on the GPU,
+D1Q3 in FP64, against the oracle's ILFBM (``oracle.Problem.ilfbm_run``).
+
+Parity: theta to 1e-12 relative (FP64), the liquid fraction to 1e-10
+absolute (the lever rule's slope Ste maps theta's rounding into l).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import neumann
+from paper_2505_13097_gb300 import _abi, workloads
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_1d_case.json")
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_13097_gb300 import solver
+    return solver
+
+
+def make(gpu, n, tau, ste, walls, bb_mode=0, tol=1e-12, maxit=200):
+    S = gpu.Stefan(_abi.LBM_D1Q3, n, 1, tau, 0.01, ste, _abi.LBM_FP64, walls, newton_tol=tol, newton_max_iter=maxit,
+                   bb_mode=bb_mode)
+    S.set_method("ILFBM")
+    return S
+
+
+@pytest.mark.parametrize("n", [2, 5, 64, 513, 801, 2844])
+@pytest.mark.parametrize("wi", [0, 1, 2])
+@pytest.mark.parametrize("bb_mode", [0, 1])
+def test_ilfbm_parity(gpu, orc, n, wi, bb_mode):
+    walls = [{"W": (1, 1.0), "E": (1, -0.5)}, {"W": (1, 0.8), "E": (0, 0.0)}, {}][wi]
+    tau, ste, steps = 0.62, 0.2857, 300
+    th0 = workloads.random_field((1, n), -0.6, 0.4, seed=n + 7 * wi)
+    S = make(gpu, n, tau, ste, walls, bb_mode)
+    S.set_ic(th0)
+    S.step(steps)
+    th, l, H = S.fields()
+    st = S.stats()
+    S.close()
+    P = orc.Problem(1, n, 1, tau=tau, delta=0.01, ste=ste, walls=walls, bb_mode=bb_mode)
+    _, lo, tho, failed, mx = P.ilfbm_run(th0, steps, tol=1e-12, maxit=200)
+    assert failed == 0 and st["error"] == 0
+    assert np.max(np.abs(th - tho)) <= 1e-12 * np.max(np.abs(tho))
+    assert np.max(np.abs(l - lo)) <= 1e-10
+    assert np.max(np.abs(H - (th + l / ste))) <= 1e-12 * np.max(np.abs(H))
+    assert 1 <= st["newton_max_iter"] <= mx
+
+
+def test_ilfbm_closed_bar_conserves_energy(gpu):
+    # link-wise bounce-back at both ends: sum theta + l/Ste is kept by every inner
+    # iteration, so by every converged step to the loop's tolerance
+    n, ste = 400, 0.5
+    S = make(gpu, n, 0.8, ste, {}, bb_mode=1, tol=1e-13)
+    S.set_ic(workloads.random_field((1, n), -0.6, 0.6, seed=3))
+    e0 = S.stats()["energy"]
+    S.step(500)
+    st = S.stats()
+    assert st["error"] == 0
+    assert abs(st["energy"] - e0) <= 500 * n * 1e-13 / ste + 1e-11 * abs(e0)
+    assert st["imbalance_max"] <= n * 1e-13 / ste + 1e-11 * abs(e0)
+
+
+def test_ilfbm_iteration_limit_reports_error(gpu):
+    # one inner iteration cannot settle a moving front: the loop stops at its
+    # limit and the step reports LBM_ERR_NEWTON (the state stays usable)
+    S = make(gpu, 128, 0.62, 0.2857, {"W": (1, 1.0), "E": (1, -0.5)}, maxit=1)
+    S.set_ic(np.full((1, 128), -0.5))
+    S.step(50)
+    with pytest.raises(_abi.LBMError) as e:
+        S.sync()
+    assert e.value.status == _abi.LBM_ERR_NEWTON
+    S.close()
+
+
+def test_ilfbm_paper_1d_case(gpu, orc):
+    """Sec. 6.1 bar (N = 801, Ste = 0.2857, tau = 0.62) on the GPU: the printed
+    final-time maximum error of ILFBM, 4.50e-3, lies within the band that the
+    error sweeps over the last cell crossing of the front (the sharp front
+    jumps from node to node), and the first 20,000 steps equal the oracle's."""
+    g = json.load(open(GOLDEN))
+    ste, th_c, n, tau = g["ste"], g["theta0"], g["N"], g["tau"]
+    lam = neumann.stefan_lambda(ste, th_c)
+    t0 = (g["x_f0"] / (2 * lam)) ** 2
+    dx = 1.0 / (n - 1)
+    dt = (tau - 0.5) * dx * dx / 3.0
+    steps = int(round((g["t_final"] - t0) / dt))
+    window = int(round(dx / (lam / np.sqrt(g["t_final"])) / dt))
+    x = np.arange(n) * dx
+    init = neumann.profile(x, t0, ste, th_c, lam)[None, :]
+    walls = {"W": (_abi.LBM_DIRICHLET, 1.0), "E": (_abi.LBM_DIRICHLET, th_c)}
+    S = make(gpu, n, tau, ste, walls)
+    S.set_ic(init)
+    S.step(20000)
+    th_20k = S.theta()
+    S.step(steps - window - 20000)
+    errs = []
+    done = steps - window
+    while done < steps:
+        k = min(100, steps - done)
+        S.step(k)
+        done += k
+        errs.append(np.max(np.abs(S.theta()[0] - neumann.profile(x, t0 + done * dt, ste, th_c, lam))))
+    st = S.stats()
+    S.close()
+    assert st["error"] == 0
+    assert min(errs) <= g["max_error_ilfbm"] <= max(errs), (min(errs), max(errs))
+    P = orc.Problem(1, n, 1, tau=tau, delta=g["delta"], ste=ste, walls={"W": (1, 1.0), "E": (1, th_c)})
+    _, _, tho, failed, _ = P.ilfbm_run(init, 20000, tol=1e-12, maxit=200)
+    assert failed == 0
+    assert np.max(np.abs(th_20k - tho)) <= 1e-12
+
+
+def test_ilfbm_argument_errors(gpu):
+    cases = [
+        (_abi.LBM_D2Q9, 32, 32, _abi.LBM_FP64),
+        (_abi.LBM_D1Q3, 64, 1, _abi.LBM_FP32),
+        (_abi.LBM_D1Q3, 2845, 1, _abi.LBM_FP64),
+    ]
+    for lat, nx, ny, prec in cases:
+        S = gpu.Stefan(lat, nx, ny, 0.8, 0.01, 0.1, prec, {})
+        with pytest.raises(_abi.LBMError) as e:
+            S.set_method("ILFBM")
+        assert e.value.status == _abi.LBM_ERR_ARG
+        S.close()
+    import torch
+    S = make(gpu, 64, 0.8, 0.1, {"W": (1, 1.0)})
+    S.set_ic(np.full((1, 64), -0.2))
+    traj = torch.empty(2 * S.row_stride, dtype=torch.float64, device="cuda")
+    with pytest.raises(_abi.LBMError) as e:
+        S.step_record(2, traj)
+    assert e.value.status == _abi.LBM_ERR_STATE
+    planes = S.new_theta_planes(2)
+    a, b = S.new_state_buffer(), S.new_state_buffer()
+    with pytest.raises(_abi.LBMError) as e:
+        S.adjoint_step(planes[0], planes[1], a, b)
+    assert e.value.status == _abi.LBM_ERR_STATE
+    S.close()
