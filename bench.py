@@ -291,6 +291,31 @@ def bench_d1q3(torch, solver, workloads, stream):
             "mlups": c.nx * c.steps / ms / 1e3}
 
 
+def bench_bar_1d(torch, solver, workloads, stream, steps=20000):
+    """The paper's 1D bar (N = 801, tau 0.62, delta 0.01) with IREBM and with
+    ILFBM (Algorithm 1), `steps` steps each, and the time of the full 160 s run
+    (204,800 steps) at that rate: the GPU counterpart of the paper's 1D timing
+    table (one M1 core: IREBM 5.586 s, ILFBM 22.01 s at N = 801)."""
+    c = workloads.bar_1d()
+    out = {"workload": c.name, "steps_timed": steps}
+    for method in ("IREBM", "ILFBM"):
+        # ILFBM: the inner loop's tolerance on l and its iteration limit
+        kw = dict(newton_tol=1e-12, newton_max_iter=200) if method == "ILFBM" else {}
+        S = solver.Stefan.from_case(c, stream=stream, **kw)
+        S.set_method(method)
+        S.set_ic(c.theta0())
+        S.step(200)
+        S.sync()
+        ms = time_steps(torch, S, steps, stream)
+        st = S.stats()
+        S.sync()
+        S.close()
+        out[method.lower()] = {"steps_per_s": steps / ms * 1e3, "full_run_s": c.steps * ms / steps / 1e3,
+                               "iterations_last_step": st["newton_max_iter"]}
+    out["ilfbm_over_irebm"] = out["ilfbm"]["full_run_s"] / out["irebm"]["full_run_s"]
+    return out
+
+
 def cpu_baseline_sample(workloads, budget_s=12.0):
     """The FP64 oracle (single thread, as it stands) on a 4096 x 64 problem with
     the melting workload's parameters and the first 64 rows of its initial field."""
@@ -403,6 +428,7 @@ def run_gpu(args):
         extra["batched_256"] = bench_batch(torch, solver, workloads, max(20, args.steps // 2), args.warmup, stream)
         extra["adjoint_1024"] = bench_adjoint(torch, solver, workloads, stream)
         extra["d1q3_512"] = bench_d1q3(torch, solver, workloads, stream)
+        extra["bar_1d_801_irebm_ilfbm"] = bench_bar_1d(torch, solver, workloads, stream)
         extra["d2q5_cavity_4096"] = bench_d2q5(torch, solver, workloads, args.steps, args.warmup, stream, peak)
     e2e_ms, h2d, d2h = bench_e2e(torch, solver, case, args.steps, stream) if rank == 0 else (0, 0, 0)
 

@@ -21,6 +21,10 @@ benchmark configurations:
 * ``adjoint_2d``     D2Q9 1024 x 1024, 2,000 steps, FP32 forward; the target
                      liquid fraction comes from a run with Ste and the wall
                      temperature raised 5 % and theta0 + 1e-3 N(0,1) (seed 1);
+* ``bar_1d``         the paper's 1D bar (Sec. 6.1) for timing: D1Q3, 801 nodes,
+                     Ste = 100/350, solid at theta = -0.5 with the hot end at +1
+                     and the cold end held at -0.5, tau 0.62, delta 0.01 (the
+                     timing table's values), 204,800 steps (160 s), FP64;
 * ``cavity_2d``      the paper's 2D case (Sec. 6.2) on D2Q5: the lower-left
                      quarter of a square cavity of liquid at theta = 1
                      (T_i = 10 C over T_f = 0 C) frozen from the west and south
@@ -134,6 +138,11 @@ def adjoint_target_case(base: Case, rel=0.05) -> Case:
 def adjoint_target_theta0(base: Case, amp=1e-3, seed=1) -> np.ndarray:
     rng = np.random.Generator(np.random.PCG64(seed))
     return base.theta0() + amp * rng.standard_normal(size=(base.ny, base.nx))
+
+
+def bar_1d(n=801, steps=204800) -> Case:
+    return Case("bar_1d_d1q3_%d" % n, 1, n, 1, 0.62, 0.01, 100.0 / 350.0,
+                {"W": (DIRICHLET, 1.0), "E": (DIRICHLET, -0.5)}, steps, FP64, theta_init=-0.5)
 
 
 CAVITY_STE = 1.762 * 10.0 / 338.0
