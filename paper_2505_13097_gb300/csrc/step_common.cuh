@@ -143,4 +143,52 @@ __device__ __forceinline__ ff dir_m0_target_f(const ff& th, int k, const Problem
     return m0t;
 }
 
+// ---------------------------------------------------------------- mbarriers and TMA
+// Shared by the warp-specialized TMA step kernels (D2Q9 and D2Q5): a producer
+// lane issues tiled tensor loads of whole rows into a ring of shared-memory
+// slots, each completing on the slot's `full` mbarrier; consumers release a
+// slot on its `empty` mbarrier.  Every wait is bounded.
+constexpr int kTmaWaitLimit = 1 << 20;   // try_wait calls before a wait gives up
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* b, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* b)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(b)) : "memory");
+}
+// try_wait: the thread sleeps in hardware until the phase completes or a short
+// time limit passes, instead of spinning on issue slots the other warps need
+// (measured 3 % faster than a test_wait spin)
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* b, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok)
+                 : "r"(smem_addr(b)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* b, unsigned parity)
+{
+    for (int i = 0; i < kTmaWaitLimit; ++i)
+        if (mbar_try_wait(b, parity)) return true;
+    return false;
+}
+// one row of every plane of the tensor map, box origin (x, row, plane 0)
+__device__ __forceinline__ void tma_load_rows(const CUtensorMap* m, float* dst, unsigned long long* bar, int x, int row)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n"
+        ::"r"(smem_addr(dst)), "l"(m), "r"(x), "r"(row), "r"(0), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+
 }  // namespace lbm
