@@ -217,7 +217,6 @@ class Problem:
 
     # ---- explicit enthalpy based method (EEBM, Algorithm 2): f carries H = M0(f)
     def eebm_init(self, theta0):
-        self._no_eq17("EEBM")
         f = np.empty((self.q, self.ny, self.nx))
         lib().orc_eebm_init(ctypes.byref(self.p), _dp(_f64(theta0).reshape(self.shape)), _dp(f))
         return f
@@ -229,7 +228,6 @@ class Problem:
         return th, H
 
     def eebm_step(self, f, detail=False):
-        self._no_eq17("EEBM")
         f = _f64(f)
         fn = np.empty_like(f)
         d = Diag()
@@ -241,7 +239,6 @@ class Problem:
 
     def eebm_run(self, theta0, nsteps):
         """``nsteps`` EEBM steps from the equilibrium state of ``theta0``: (f, theta)."""
-        self._no_eq17("EEBM")
         f = np.empty((self.q, self.ny, self.nx))
         th = np.empty(self.shape)
         if lib().orc_eebm_run(ctypes.byref(self.p), _dp(_f64(theta0).reshape(self.shape)), int(nsteps),

@@ -567,7 +567,8 @@ done:
  * Boundary closures (the paper leaves EEBM's to standard techniques): the
  * same as IREBM's on the streamed distributions, with the Dirichlet target
  * M0(f~) = H(theta_D) = theta_D + [theta_D > 0]/Ste (the enthalpy of the wall
- * value; a wall at exactly 0 is taken solid), and bounce-back unchanged.
+ * value; a wall at exactly 0 is taken solid), bounce-back unchanged, and on
+ * D2Q5 the Neumann closure of Eq. (17) on H (bb_mode 2).
  * ====================================================================== */
 double orc_eebm_theta(double H, double ste)
 {
@@ -653,8 +654,17 @@ int orc_eebm_step(const orc_params* p, const double* f, double* fn, orc_diag* di
                 if (!known[i]) nunk++;
             }
             if (nunk > 0) {
-                if (node_dirichlet(p, x, y, &td, NULL)) {
-                    double rest = orc_eebm_enthalpy(td, p->ste), wu = 0.0;
+                if (node_dirichlet(p, x, y, &td, NULL) || p->bb_mode == 2) {
+                    /* Dirichlet: M0 = H(theta_D); Eq. (17): M0 = M0 of the streamed
+                     * distributions one node inwards (the diagonal one at a corner) */
+                    double rest, wu = 0.0;
+                    if (node_dirichlet(p, x, y, &td, NULL)) {
+                        rest = orc_eebm_enthalpy(td, p->ste);
+                    } else {
+                        const int sx = x + (x == 0 ? 1 : (x == nx - 1 ? -1 : 0));
+                        const int sy = y + (y == 0 ? 1 : (y == ny - 1 ? -1 : 0));
+                        rest = orc_pulled_m0(p, Om, sx, sy);
+                    }
                     for (i = 0; i < q; i++) {
                         if (known[i]) rest -= qv[i];
                         else wu += w[i];

@@ -417,7 +417,7 @@ extern "C" lbm_status lbm_stefan_set_method(lbm_stefan* h, int method)
     if (!h) return fail(LBM_ERR_ARG, "NULL handle");
     if (method != LBM_IREBM && method != LBM_EEBM && method != LBM_ILFBM)
         return fail(LBM_ERR_ARG, "method must be 0 (IREBM), 1 (EEBM) or 2 (ILFBM)");
-    if (method == LBM_EEBM && h->p.lattice != LBM_D2Q9) return fail(LBM_ERR_ARG, "EEBM is implemented for D2Q9");
+    // EEBM: D1Q3, D2Q9 and D2Q5 (every closure); the no-allocation step and batches stay IREBM
     if (method == LBM_ILFBM && (h->p.lattice != LBM_D1Q3 || h->precision != LBM_FP64 || !lbm::ilfbm_d1q3_fits(h->hp.nx)))
         return fail(LBM_ERR_ARG, "ILFBM is implemented for D1Q3 in FP64 up to 2,844 nodes");
     h->hp.method = method;

@@ -7,6 +7,7 @@
 //    steps.  A 512-node lattice is far too small to fill the GPU, so the
 //    per-step cost is launch latency unless the steps are fused.
 // Moments are summed in FP64 for both storage precisions (three terms).
+// EEBM (Algorithm 2) runs in the same kernels (method 1 of the problem).
 #include "lbm_device.cuh"
 
 namespace lbm {
@@ -43,7 +44,9 @@ __device__ __forceinline__ NodeOut d1q3_node(const Problem& pb, int x, const P (
             dir = true;
             thd = pb.wall_theta[side];
             // Eq. (16): the single unknown closes M0(q), with M0(q) from Eq. (14) at theta' = theta_D
-            const double m0t = thd + (phi_of(thd, pb.inv_delta) - phi_of(th, pb.inv_delta)) * pb.inv_ste;
+            // (EEBM: the wall value's enthalpy, Algorithm 2 keeps H = M0)
+            const double m0t = pb.method == 1 ? pb.wall_H[side]
+                                              : thd + (phi_of(thd, pb.inv_delta) - phi_of(th, pb.inv_delta)) * pb.inv_ste;
             q[iu] = (double)(P)(m0t - q[0] - q[io]);
         } else {
             // bounce-back q_iu = q_io (Sec. 4.2.2), or link-wise q_iu = Omega_io at the node
@@ -52,6 +55,17 @@ __device__ __forceinline__ NodeOut d1q3_node(const Problem& pb, int x, const P (
         r.flux = q[iu] - out;
     }
     const double m0 = q[2] + q[1] + q[0];
+    if (pb.method == 1) {
+        // EEBM (Algorithm 2): H = M0(q), theta = Theta(H), relaxation toward
+        // w_i theta (i != 0) and H - (1 - w_0) theta (i = 0); the energy is H
+        const double H = m0, t = eebm_theta(H, pb.inv_ste), om = pb.omega, omc = 1.0 - pb.omega;
+        o[0] = (P)(omc * q[0] + om * (H - (1.0 - d1_w(0)) * t));
+        o[1] = (P)(omc * q[1] + om * d1_w(1) * t);
+        o[2] = (P)(omc * q[2] + om * d1_w(2) * t);
+        r.theta_new = t;
+        r.energy = H;
+        return r;
+    }
     double tn, phn;
     if (dir) {
         tn = thd;

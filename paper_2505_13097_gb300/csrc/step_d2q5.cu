@@ -369,6 +369,75 @@ __device__ __forceinline__ void row5_update(const Problem& pb, const P* __restri
     if constexpr (REC) st_rec<N>(rec + (long long)y * pb.pitch + x0, thn);
 }
 
+// EEBM row update (Algorithm 2 in the stored-Omega form, as for D2Q9): after
+// the pulls and the closures (Dirichlet target M0(q) = H(theta_D); Eq. 17 and
+// bounce-back unchanged), H = M0(q), theta = Theta(H), and
+// Omega~_i = (1-omega) q_i + omega w_i theta (i != 0),
+// Omega~_0 = (1-omega) q_0 + omega (H - (1-w_0) theta).  No Newton node; the
+// energy is the sum of H.
+template <typename P, int N, bool REC, bool EDGE>
+__device__ __forceinline__ void row5_update_eebm(const Problem& pb, const P* __restrict__ src, P* __restrict__ drow,
+                                                 int y, int x0, P (&qf)[5][N], const P (&u)[5][N],
+                                                 double* __restrict__ rec, Acc<P>& acc, TileSums& ts, const P omc,
+                                                 const P w0, const P w1)
+{
+    const int nx = pb.nx, ny = pb.ny;
+    const long long pl = pb.plane;
+    if constexpr (EDGE) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            const int x = x0 + k;
+            if (x < nx && (x == 0 || x == nx - 1 || y == 0 || y == ny - 1)) {
+                P qq[5], uu[5];
+                int wall;
+#pragma unroll
+                for (int i = 0; i < 5; ++i) { qq[i] = qf[i][k]; uu[i] = u[i][k]; }
+                if constexpr (sizeof(P) == 4) {
+                    const ff fl = wall5_closure_f(qq, uu, x, y, pb, src, wall);
+                    ff_add(ts.flux_f, fl.hi);
+                    ts.flux_f.lo += fl.lo;
+                } else {
+                    ts.flux += wall5_closure_d(qq, uu, x, y, pb, src, wall);
+                }
+#pragma unroll
+                for (int i = 0; i < 5; ++i) qf[i][k] = qq[i];
+            }
+        }
+    }
+    const P om = (P)1 - omc;
+    const P inv_ste = (P)pb.inv_ste;
+    P hs = 0;
+    double thn[REC ? N : 1];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        const bool valid = !EDGE || x0 + k < nx;
+        P H = 0;
+#pragma unroll
+        for (int i = 4; i >= 0; --i) H += qf[i][k];
+        if (!valid) {
+            H = 0;
+#pragma unroll
+            for (int i = 0; i < 5; ++i) qf[i][k] = (P)0;
+        }
+        const P th = eebm_theta(H, inv_ste);
+        hs += H;
+        if constexpr (REC) thn[k] = (double)th;
+        qf[0][k] = fma(omc, qf[0][k], om * (H - ((P)1 - w0) * th));
+#pragma unroll
+        for (int i = 1; i < 5; ++i) qf[i][k] = fma(omc, qf[i][k], om * w1 * th);
+    }
+    if constexpr (sizeof(P) == 4) acc.add_ff(ff{hs, 0.f});
+    else acc.add_d(hs);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        P o[N];
+#pragma unroll
+        for (int k = 0; k < N; ++k) o[k] = qf[i][k];
+        stv_n(drow + i * pl, o);
+    }
+    if constexpr (REC) st_rec<N>(rec + (long long)y * pb.pitch + x0, thn);
+}
+
 // ---------------------------------------------------------------- warp tile
 template <typename P, bool REC>
 __device__ __forceinline__ void d2q5_tile(const Problem& pb, const P* __restrict__ src, P* __restrict__ dst,
@@ -434,7 +503,9 @@ __device__ __forceinline__ void d2q5_tile(const Problem& pb, const P* __restrict
         from_left<P, N>(cur.r1, cur.h1, lane, qf[1]);
         from_right<P, N>(cur.r3, cur.h3, lane, qf[3]);
         P* drow = dst + (long long)(y + 1) * pitch + x0;
-        if (seg_interior && y > 0 && y < ny - 1)
+        if (pb.method == 1)
+            row5_update_eebm<P, N, REC, true>(pb, src, drow, y, x0, qf, u, rec, acc, ts, omc, w0, w1);
+        else if (seg_interior && y > 0 && y < ny - 1)
             row5_update<P, N, REC, false>(pb, src, drow, y, x0, lane, qf, u, rec, acc, ts, pi, jobs, job_count, omc,
                                           om_f, omc_d, w0, w1, thr_f);
         else
@@ -603,7 +674,9 @@ __global__ void __launch_bounds__(k5Threads, 5) d2q5_tma_kernel(const StepArgs a
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[km % k5Stages]);
         float* drow = dst + (long long)(y + 1) * pitch + x;
-        if (warp_interior_x && y > 0 && y < ny - 1)
+        if (pb.method == 1)
+            row5_update_eebm<float, 1, REC, true>(pb, src, drow, y, x, qf, u, a.rec, acc, ts, omc, w0, w1);
+        else if (warp_interior_x && y > 0 && y < ny - 1)
             row5_update<float, 1, REC, false>(pb, src, drow, y, x, lane, qf, u, a.rec, acc, ts, 0, a.jobs, a.job_count,
                                               omc, om_f, omc_d, w0, w1, thr_f);
         else

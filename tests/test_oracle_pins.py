@@ -633,6 +633,32 @@ def test_eq17_with_dirichlet_walls(orc):
     assert np.max(np.abs(th[1:, -1] - th[1:, -2])) <= 1e-12
 
 
+def test_eq17_eebm_wall_enthalpy_equals_inner_neighbour(orc):
+    # EEBM with the Eq. (17) closure: H = M0 of the closed streamed distributions,
+    # so every adiabatic wall node's H after a step equals its partner's
+    nx, ny = 8, 7
+    P = orc.Problem(3, nx, ny, tau=0.9, delta=0.01, ste=0.4, bb_mode=2)
+    f = np.random.default_rng(47).uniform(-0.3, 0.5, size=(5, ny, nx))
+    H = P.eebm_fields(P.eebm_step(f))[1]
+    for y in range(ny):
+        for x in range(nx):
+            if 0 < x < nx - 1 and 0 < y < ny - 1:
+                continue
+            sx, sy = _eq17_partner(nx, ny, x, y)
+            assert abs(H[y, x] - H[sy, sx]) <= 1e-15, (x, y)
+
+
+@pytest.mark.parametrize("tau,walls", [(1.0, {"W": (1, 1.0), "E": (1, -0.5)}), (0.7, {})])
+def test_d2q5_eebm_planar_field_is_d1q3_eebm(orc, tau, walls):
+    # Algorithm 2 on D2Q5 with a y-uniform field: rest + (0, +-1) populations carry
+    # H - theta/3, as D1Q3's rest population does, so every row is the D1Q3 run
+    nx, ny, steps = 30, 4, 100
+    th0 = np.tile(workloads.random_field((1, nx), -0.4, 0.4, seed=48), (ny, 1))
+    _, t5 = orc.Problem(3, nx, ny, tau=tau, delta=0.01, ste=0.3, walls=walls).eebm_run(th0, steps)
+    _, t1 = orc.Problem(1, nx, 1, tau=tau, delta=0.01, ste=0.3, walls=walls).eebm_run(th0[:1], steps)
+    assert np.max(np.abs(t5 - t1)) <= 1e-13
+
+
 def test_eq17_argument_checks(orc):
     with pytest.raises(ValueError):
         orc.Problem(2, 8, 8, bb_mode=2)
