@@ -105,16 +105,16 @@ lbm_status lbm_stefan_set_bc(lbm_stefan* h, int wall, int kind, double theta_wal
 
 /* Step method.  LBM_IREBM (default): Algorithm 3.  LBM_EEBM: the explicit
  * enthalpy based method of Algorithm 2 (Sec. 3.4), the paper's comparison
- * scheme, D2Q9 only: the populations carry the enthalpy H = M0(f),
+ * scheme, on D1Q3, D2Q9 and D2Q5: the populations carry the enthalpy H = M0(f),
  * theta = Theta(H) (H below 0, 0 on [0, 1/Ste], H - 1/Ste above), the
  * equilibrium is w_i theta (i != 0) and H - (1 - w_0) theta (i = 0), no Newton;
- * the closures act on the streamed populations as for IREBM, a Dirichlet node
- * holding M0 at the enthalpy of its wall value (theta_D + [theta_D > 0]/Ste);
+ * the closures act on the streamed populations as for IREBM (Eq. 17 included),
+ * a Dirichlet node holding M0 at the enthalpy of its wall value
+ * (theta_D + [theta_D > 0]/Ste);
  * delta is not used.  For EEBM, get_fields returns theta = Theta(H), phi = the
  * liquid fraction min(max(Ste H, 0), 1) and H; the energy statistics are the
  * sum of H; the adjoint calls return LBM_ERR_STATE.  Discards the state: call
- * lbm_stefan_set_ic afterwards.  LBM_ERR_ARG for an unknown method or a
- * lattice other than D2Q9.
+ * lbm_stefan_set_ic afterwards.  LBM_ERR_ARG for an unknown method.
  * LBM_ILFBM: the implicit liquid fraction based method of Algorithm 1
  * (Sec. 3.3), the paper's other comparison scheme, D1Q3 in FP64 up to 2,844
  * nodes: theta = M0(f), f_i^eq = w_i theta, and a liquid-fraction field l
@@ -127,7 +127,8 @@ lbm_status lbm_stefan_set_bc(lbm_stefan* h, int wall, int kind, double theta_wal
  * set_ic puts l = [theta0 > 0].  get_fields returns theta, phi = l and
  * H = theta + l/Ste; the energy statistics are the sum of H and
  * newton_max_iter the last step's inner iteration count; step_record,
- * step_timed and the adjoint calls return LBM_ERR_STATE / LBM_ERR_ARG. */
+ * step_timed and the adjoint calls return LBM_ERR_STATE / LBM_ERR_ARG;
+ * LBM_ERR_ARG for ILFBM on another lattice, in FP32 or beyond 2,844 nodes. */
 lbm_status lbm_stefan_set_method(lbm_stefan* h, int method);
 
 /* Initial state: f_i = w_i theta0 (equilibrium), Dirichlet nodes at their wall

@@ -76,7 +76,7 @@ class Stefan:
         check(self.lib.lbm_stefan_set_bc(self.h, w, int(kind), float(theta_wall)))
 
     def set_method(self, method):
-        """"IREBM" (Algorithm 3, default), "EEBM" (Algorithm 2, D2Q9) or "ILFBM"
+        """"IREBM" (Algorithm 3, default), "EEBM" (Algorithm 2) or "ILFBM"
         (Algorithm 1, D1Q3 FP64); set_ic follows."""
         m = {"IREBM": _abi.LBM_IREBM, "EEBM": _abi.LBM_EEBM, "ILFBM": _abi.LBM_ILFBM}.get(method, method)
         check(self.lib.lbm_stefan_set_method(self.h, int(m)))
