@@ -18,7 +18,13 @@
 // lattice-wide barriers.  A 1D lattice of the paper's sizes (N <= 1601) fits
 // in one thread block's shared memory (72 bytes per node): one block runs
 // all steps of a call, its barriers are __syncthreads, and HBM is touched
-// only at the start and the end of the call.
+// only at the start and the end of the call.  The inner loop is bound by the
+// block's FP64 issue rate (FP64 is scarce on this GPU), so it is cut to what
+// changes between iterations: the source-free part of the collision is formed
+// once per step, an iteration forms only H^(k) and l^(k) (the populations
+// f^(k) are streamed once, after the loop), and the loop's test is one flag
+// per iteration behind a single barrier (three flags in rotation: the one
+// cleared for the next iteration was last read two iterations earlier).
 #include "lbm_device.cuh"
 
 namespace lbm {
@@ -26,7 +32,7 @@ namespace lbm {
 constexpr int kIlfThreads = 512;
 constexpr int kIlfWarps = kIlfThreads / 32;
 
-// Deterministic block reductions: warp shuffles, then a fixed order over warps.
+// Deterministic block sum: warp shuffles, then a fixed order over warps.
 __device__ __forceinline__ double ilf_block_sum(double v, double* sh)
 {
     v = warp_sum(v);
@@ -38,19 +44,6 @@ __device__ __forceinline__ double ilf_block_sum(double v, double* sh)
     for (int k = 0; k < kIlfWarps; ++k) s += sh[k];
     return s;   // the same value in every thread
 }
-__device__ __forceinline__ double ilf_block_max(double v, double* sh)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    __syncthreads();
-    if (l == 0) sh[w] = v;
-    __syncthreads();
-    double m = 0.0;
-    for (int k = 0; k < kIlfWarps; ++k) m = fmax(m, sh[k]);
-    return m;
-}
-
 __device__ __forceinline__ double ilf_lever(double H, double ste, double inv_ste)
 {
     return H < 0.0 ? 0.0 : (H > inv_ste ? 1.0 : ste * H);
@@ -60,94 +53,119 @@ __global__ void __launch_bounds__(kIlfThreads) ilfbm_d1q3_kernel(StepArgs a, int
 {
     extern __shared__ double sm[];
     __shared__ double red[kIlfWarps];
-    __shared__ double s_flux[2];
+    __shared__ int s_more[3];   // "some node changed by more than tol", iteration gk uses gk % 3
     const Problem& pb = a.probs[0];
     DevStats* st = &a.stats[pb.stats];
     const int n = pb.nx;
-    double* f = sm;              // f_i at time t, 3 n
-    double* fk = f + 3 * n;      // inner iterate f^(k), 3 n
-    double* th = fk + 3 * n;     // theta = M0(f)
-    double* el = th + n;         // l at time t
-    double* lp = el + n;         // l^(k-1), replaced by l^(k) at the end of an iteration
+    double* o = sm;              // f_i at time t, then Omega_i without the source: f_i - (f_i - w_i theta)/tau
+    double* fn = sm + 3 * n;     // f~ of the step (the buffers swap roles every step)
+    double* el = sm + 6 * n;     // l at time t
+    double* lb[2] = {el + n, el + 2 * n};   // l^(k-1) and l^(k), alternating
     const long long pl = pb.plane, row = pb.pitch;
     const double* src = static_cast<const double*>(pb.state[a.parity]);
+    // the state at time t: f_i and l
     for (int x = threadIdx.x; x < n; x += blockDim.x) {
-        for (int i = 0; i < 3; ++i) f[i * n + x] = src[i * pl + row + x];
+        for (int i = 0; i < 3; ++i) o[i * n + x] = src[i * pl + row + x];
         el[x] = src[3 * pl + row + x];
     }
     const double om = pb.omega, ste = pb.ste, inv_ste = pb.inv_ste, tol = pb.tol;
-    const double w[3] = {d1_w(0), d1_w(1), d1_w(2)};
+    const double w0 = d1_w(0), w1 = d1_w(1), w2 = d1_w(2);
+    const double c0 = w0 * inv_ste, c1 = w1 * inv_ste, c2 = w2 * inv_ste;
     const bool dirW = pb.wall_kind[0] == 1, dirE = pb.wall_kind[1] == 1;
     const double thW = pb.wall_theta[0], thE = pb.wall_theta[1];
+    const bool mirror = pb.bb_mode == 0;
     bool failed = false;
+    unsigned gk = 0;   // inner iterations so far in this launch: selects the flag
+    if (threadIdx.x < 3) s_more[threadIdx.x] = 0;
     __syncthreads();
     for (int s = 0; s < nsteps; ++s) {
+        // moments and the source-free part of the collision (the same in every
+        // inner iteration); l^(0) = l
         for (int x = threadIdx.x; x < n; x += blockDim.x) {
-            th[x] = f[x] + f[n + x] + f[2 * n + x];
-            lp[x] = el[x];
+            const double f0 = o[x], f1 = o[n + x], f2 = o[2 * n + x];
+            const double th = f0 + f1 + f2;
+            o[x] = f0 - (f0 - w0 * th) * om;
+            o[n + x] = f1 - (f1 - w1 * th) * om;
+            o[2 * n + x] = f2 - (f2 - w2 * th) * om;
+            lb[0][x] = el[x];
         }
         __syncthreads();
-        // Omega_i at node x: collision with the source of the current iterate
-        auto Om = [&](int i, int x) -> double {
-            const double fi = f[i * n + x];
-            return fi - (fi - w[i] * th[x]) * om + w[i] * inv_ste * (el[x] - lp[x]);
+        // streamed f^(k)(y) from Omega_i(x) = o_i(x) + (w_i/Ste)(l(x) - l^(k-1)(x)),
+        // the closures on the unknown one at a wall; returns the three values
+        auto stream = [&](int y, const double* lp, double& q0, double& q1, double& q2) {
+            q0 = o[y] + c0 * (el[y] - lp[y]);
+            q1 = y > 0 ? o[n + y - 1] + c1 * (el[y - 1] - lp[y - 1]) : 0.0;
+            q2 = y < n - 1 ? o[2 * n + y + 1] + c2 * (el[y + 1] - lp[y + 1]) : 0.0;
+            if (y == 0)   // west wall: f_1 (e = +1) is unknown
+                q1 = dirW ? thW - q0 - q2 : (mirror ? q2 : o[2 * n] + c2 * (el[0] - lp[0]));
+            if (y == n - 1)   // east wall: f_2 (e = -1) is unknown
+                q2 = dirE ? thE - q0 - q1 : (mirror ? q1 : o[n + n - 1] + c1 * (el[n - 1] - lp[n - 1]));
         };
-        int it = 0;
+        int it = 0, cur = 0;
         bool conv = false;
-        while (!conv && it < pb.maxit) {   // it and conv are the same in every thread
+        while (!conv && it < pb.maxit) {   // it, gk, cur and conv are the same in every thread
+            const double* lp = lb[cur];
+            double* ln = lb[cur ^ 1];
+            const int slot = gk % 3;
             ++it;
-            for (int y = threadIdx.x; y < n; y += blockDim.x) {
-                const double q0 = Om(0, y);
-                double q1 = y > 0 ? Om(1, y - 1) : 0.0;
-                double q2 = y < n - 1 ? Om(2, y + 1) : 0.0;
-                if (y == 0) {
-                    // west wall: f_1 (e = +1) is unknown
-                    q1 = dirW ? thW - q0 - q2 : (pb.bb_mode == 0 ? q2 : Om(2, 0));
-                    s_flux[0] = q1 - Om(2, 0);
-                }
-                if (y == n - 1) {
-                    // east wall: f_2 (e = -1) is unknown
-                    q2 = dirE ? thE - q0 - q1 : (pb.bb_mode == 0 ? q1 : Om(1, n - 1));
-                    s_flux[1] = q2 - Om(1, n - 1);
-                }
-                fk[y] = q0;
-                fk[n + y] = q1;
-                fk[2 * n + y] = q2;
-            }
-            __syncthreads();
-            // enthalpy and lever rule; Dirichlet nodes keep the phase of their wall value
-            double ch = 0.0;
+            ++gk;
+            // H^(k) = M0(f^(k)) + l^(k-1)/Ste and the lever rule; Dirichlet nodes keep
+            // the phase of their wall value
+            bool more = false;
             for (int y = threadIdx.x; y < n; y += blockDim.x) {
                 double lk;
-                if (y == 0 && dirW) lk = thW > 0.0 ? 1.0 : 0.0;
-                else if (y == n - 1 && dirE) lk = thE > 0.0 ? 1.0 : 0.0;
-                else lk = ilf_lever(fk[y] + fk[n + y] + fk[2 * n + y] + lp[y] * inv_ste, ste, inv_ste);
-                ch = fmax(ch, fabs(lk - lp[y]));
-                lp[y] = lk;
+                if (y == 0 && dirW) {
+                    lk = thW > 0.0 ? 1.0 : 0.0;
+                } else if (y == n - 1 && dirE) {
+                    lk = thE > 0.0 ? 1.0 : 0.0;
+                } else {
+                    double q0, q1, q2;
+                    stream(y, lp, q0, q1, q2);
+                    lk = ilf_lever(q0 + q1 + q2 + lp[y] * inv_ste, ste, inv_ste);
+                }
+                more |= fabs(lk - lp[y]) > tol;
+                ln[y] = lk;
             }
-            conv = ilf_block_max(ch, red) <= tol;   // ends with a barrier before lp is read again
+            // flag of this iteration; thread 0 clears the next iteration's flag, last read
+            // two iterations ago (every thread read it before the previous barrier) and
+            // next set after this iteration's barrier
+            if (more) s_more[slot] = 1;
+            if (threadIdx.x == 0) s_more[(slot + 1) % 3] = 0;
+            __syncthreads();
+            conv = s_more[slot] == 0;
+            cur ^= 1;
         }
         failed |= !conv;
-        double e = 0.0;
-        for (int x = threadIdx.x; x < n; x += blockDim.x) {
-            const double a0 = fk[x], a1 = fk[n + x], a2 = fk[2 * n + x];
-            f[x] = a0;
-            f[n + x] = a1;
-            f[2 * n + x] = a2;
-            el[x] = lp[x];
-            e += (a0 + a1 + a2) + lp[x] * inv_ste;
+        // f~ = f^(k) (streamed with the source of l^(k-1)) into the other buffer,
+        // l~ = l^(k); the boundary flux is filled minus leaving at the two walls
+        const double* lp = lb[cur ^ 1];
+        const double* ln = lb[cur];
+        double e = 0.0, fl = 0.0;
+        for (int y = threadIdx.x; y < n; y += blockDim.x) {
+            double q0, q1, q2;
+            stream(y, lp, q0, q1, q2);
+            if (y == 0) fl += q1 - (o[2 * n] + c2 * (el[0] - lp[0]));
+            if (y == n - 1) fl += q2 - (o[n + n - 1] + c1 * (el[n - 1] - lp[n - 1]));
+            fn[y] = q0;
+            fn[n + y] = q1;
+            fn[2 * n + y] = q2;
+            e += (q0 + q1 + q2) + ln[y] * inv_ste;
         }
-        const double es = ilf_block_sum(e, red);
+        const double es = ilf_block_sum(e, red);     // its barriers also order the reads of
+        const double fs = ilf_block_sum(fl, red);    // o, el and l^(k-1) before the writes below
+        for (int y = threadIdx.x; y < n; y += blockDim.x) el[y] = ln[y];
+        double* t = o;
+        o = fn;
+        fn = t;
         if (threadIdx.x == 0) {
-            const double fl = s_flux[0] + s_flux[1];
             if (st->have_energy) {
-                const double imb = es - st->energy - fl;
+                const double imb = es - st->energy - fs;
                 st->imbalance = imb;
                 if (fabs(imb) > st->imbalance_max) st->imbalance_max = fabs(imb);
             }
             st->energy_prev = st->energy;
             st->energy = es;
-            st->flux = fl;
+            st->flux = fs;
             st->have_energy = 1;
             st->steps += 1;
             st->newton_nodes = 0;
@@ -158,7 +176,7 @@ __global__ void __launch_bounds__(kIlfThreads) ilfbm_d1q3_kernel(StepArgs a, int
     if (failed && threadIdx.x == 0) atomicOr(&st->error, 3);   // LBM_ERR_NEWTON: inner loop at its limit
     double* dst = static_cast<double*>(pb.state[a.parity ^ (nsteps & 1)]);
     for (int x = threadIdx.x; x < n; x += blockDim.x) {
-        for (int i = 0; i < 3; ++i) dst[i * pl + row + x] = f[i * n + x];
+        for (int i = 0; i < 3; ++i) dst[i * pl + row + x] = o[i * n + x];
         dst[3 * pl + row + x] = el[x];
     }
 }

@@ -99,9 +99,9 @@ struct StepArgs {
     unsigned int* job_count; // number of jobs; reset by the job kernel
 };
 
-// TMA descriptors of the single-problem FP32 D2Q9 and D2Q5 steps: state[0],
-// state[1] as 3-D tensors (column over `pitch`, row y + 1 over ny + 2 rows,
-// plane 0..q-1); a load copies (kTmaW + 2 kTmaHalo) columns x 1 row x q planes.
+// TMA descriptors of the single-problem FP32 D2Q9 step: state[0], state[1]
+// as 3-D tensors (column over `pitch`, row y + 1 over ny + 2 rows, plane
+// 0..q-1); a load copies (kTmaW + 2 kTmaHalo) columns x 1 row x q planes.
 constexpr int kTmaW = 128;               // columns per block (one node per consumer thread)
 constexpr int kTmaHalo = 4;              // extra loaded columns on each side (16 bytes)
 struct TmaMaps {
@@ -164,8 +164,6 @@ cudaError_t launch_newton_jobs(int precision, int q, const JobArgs& a, cudaStrea
 // D2Q5 launchers (step_d2q5.cu): one tile per warp over a.nslots tiles
 cudaError_t launch_d2q5_step(int precision, const StepArgs& a, cudaStream_t s);
 int d2q5_segment_width(int precision);   // nodes per warp segment
-cudaError_t launch_d2q5_tma(const StepArgs& a, const TmaMaps& m, cudaStream_t s);   // FP32, single problem
-int d2q5_tma_blocks_per_sm();
 
 // D1Q3 launchers (step_d1q3.cu)
 cudaError_t launch_d1q3_step(int precision, const StepArgs& a, const Problem& hp, cudaStream_t s);

@@ -225,8 +225,7 @@ static cudaError_t launch_one(lbm_stefan* h, int parity, double* rec)
 {
     StepArgs a = single_args(h, parity, rec);
     if (h->p.lattice == LBM_D2Q5) {
-        const cudaError_t e = h->use_tma ? lbm::launch_d2q5_tma(a, h->tma, h->stream)
-                                         : lbm::launch_d2q5_step(h->precision, a, h->stream);
+        const cudaError_t e = lbm::launch_d2q5_step(h->precision, a, h->stream);
         if (e != cudaSuccess) return e;
         return lbm::launch_newton_jobs(h->precision, 5,
                                        job_args(h->dprob, 1, parity, rec, h->dstats, h->dticket, h->djobs, h->djob_count),
@@ -266,9 +265,6 @@ static double acc_host(const lbm::Acc128& a) { return (double)a.hi * 16.0 + (dou
 // ------------------------------------------------------------------ TMA descriptors
 #ifndef LBM_USE_TMA
 #define LBM_USE_TMA 1
-#endif
-#ifndef LBM_D2Q5_USE_TMA
-#define LBM_D2Q5_USE_TMA 1
 #endif
 #ifndef LBM_TMA_ROWS
 #define LBM_TMA_ROWS 16   // rows per block of the TMA step kernel
@@ -323,8 +319,7 @@ static bool setup_tma(lbm_stefan* h)
     // short row ranges: many blocks in flight hide the latency of each block's
     // row chain (measured: 16 rows beat 8, 32, 64 and one range per SM slot)
     h->tma.nparts = std::max(1, (hp.ny + LBM_TMA_ROWS - 1) / LBM_TMA_ROWS);
-    // also selects the shared-memory carveout
-    const int per_sm = hp.q == 5 ? lbm::d2q5_tma_blocks_per_sm() : lbm::d2q9_tma_blocks_per_sm();
+    const int per_sm = lbm::d2q9_tma_blocks_per_sm();   // also selects the shared-memory carveout
 #ifdef LBM_TMA_VERBOSE
     fprintf(stderr, "tma: blocks/SM %d nsegs %d nparts %d\n", per_sm, h->tma.nsegs, h->tma.nparts);
 #endif
@@ -358,8 +353,7 @@ extern "C" lbm_status lbm_stefan_create(const lbm_stefan_params* p, void* cuda_s
     const int segw = p->lattice == LBM_D2Q9   ? lbm::d2q9_segment_width(p->precision)
                      : p->lattice == LBM_D2Q5 ? lbm::d2q5_segment_width(p->precision)
                                               : 32;
-    const bool tma = LBM_USE_TMA && p->precision == LBM_FP32 &&
-                     (p->lattice == LBM_D2Q9 || (LBM_D2Q5_USE_TMA && p->lattice == LBM_D2Q5));
+    const bool tma = LBM_USE_TMA && p->lattice == LBM_D2Q9 && p->precision == LBM_FP32;
     const int pitch = state_pitch(p->lattice, p->precision, p->nx);
     fill_problem(h->hp, q, p->nx, p->ny, pitch, p->tau, p->delta, p->ste, p->newton_tol, p->newton_max_iter,
                  p->bb_mode, 16, segw, p->precision);
@@ -522,8 +516,7 @@ extern "C" lbm_status lbm_stefan_step_timed(lbm_stefan* h, int nsteps, double* m
     for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
         StepArgs a = single_args(h, h->parity, nullptr);
         if (h->p.lattice == LBM_D2Q5) {
-            e = h->use_tma ? lbm::launch_d2q5_tma(a, h->tma, h->stream)
-                           : lbm::launch_d2q5_step(h->precision, a, h->stream);
+            e = lbm::launch_d2q5_step(h->precision, a, h->stream);
         } else if (h->use_tma) {
             e = lbm::launch_d2q9_tma(a, h->tma, h->stream);
         } else {

@@ -144,7 +144,7 @@ __device__ __forceinline__ ff dir_m0_target_f(const ff& th, int k, const Problem
 }
 
 // ---------------------------------------------------------------- mbarriers and TMA
-// Shared by the warp-specialized TMA step kernels (D2Q9 and D2Q5): a producer
+// Used by the warp-specialized TMA step kernel: a producer
 // lane issues tiled tensor loads of whole rows into a ring of shared-memory
 // slots, each completing on the slot's `full` mbarrier; consumers release a
 // slot on its `empty` mbarrier.  Every wait is bounded.

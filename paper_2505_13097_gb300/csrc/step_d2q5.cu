@@ -557,155 +557,6 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, LBM_D2Q5_MIN_BLOCKS) d2q5
     // statistics are published by the job kernel that follows every step
 }
 
-// ---------------------------------------------------------------- TMA row pipeline
-// Single-problem FP32 step, warp-specialized as the D2Q9 TMA kernel: a block
-// owns a strip of kTmaW = 128 columns and the rows [ya, yb); its producer lane
-// streams rows of all five planes (136 columns: four more on each side, zeros
-// outside the tensor) into a ring of shared-memory slots with TMA tensor
-// loads; four consumer warps (one node per lane) take the pulled values of
-// row y from the slots of rows y-1 (plane 2), y (planes 0, 1 at x-1, 3 at
-// x+1) and y+1 (plane 4), release the slot of row y-1, run the row update
-// above and store straight to global memory.  A D2Q5 row is 2.7 KB, so the
-// ring holds more rows in flight than the D2Q9 one in less shared memory.
-// Every mbarrier wait is bounded: on a timeout the block records
-// LBM_ERR_TIMEOUT and stops; the producer waits (bounded) for its own copies
-// in flight before it exits.
-#ifndef LBM_D2Q5_TMA_STAGES
-#define LBM_D2Q5_TMA_STAGES 12
-#endif
-constexpr int k5Stages = LBM_D2Q5_TMA_STAGES;
-constexpr int k5Box = kTmaW + 2 * kTmaHalo;                  // 136 loaded columns
-constexpr int k5Slot = (5 * k5Box * 4 + 127) / 128 * 32;     // floats per slot (128-byte multiple)
-constexpr int k5Consumers = kTmaW / 32;                       // consumer warps
-constexpr int k5Threads = kTmaW + 32;                         // + the producer warp
-constexpr unsigned k5RowBytes = 5u * k5Box * 4u;              // bytes one row load delivers
-
-template <bool REC>
-__global__ void __launch_bounds__(k5Threads, 5) d2q5_tma_kernel(const StepArgs a, const __grid_constant__ TmaMaps m)
-{
-    __shared__ __align__(128) float ring[k5Stages * k5Slot];
-    __shared__ __align__(8) unsigned long long full[k5Stages];
-    __shared__ __align__(8) unsigned long long empty[k5Stages];
-
-    const Problem& pb = a.probs[0];
-    DevStats* st = &a.stats[pb.stats];
-    const int seg = blockIdx.x % m.nsegs;
-    const int part = blockIdx.x / m.nsegs;
-    const int ya = (int)((long long)pb.ny * part / m.nparts);
-    const int yb = (int)((long long)pb.ny * (part + 1) / m.nparts);
-    const CUtensorMap* lmap = &m.load[a.parity];
-    const int tid = threadIdx.x;
-    const int warp = tid >> 5;
-    const int lane = tid & 31;
-    const int nx = pb.nx, ny = pb.ny;
-    const int segx = seg * kTmaW;
-
-    if (tid == 0) {
-        for (int k = 0; k < k5Stages; ++k) {
-            mbar_init(&full[k], 1);
-            mbar_init(&empty[k], k5Consumers);
-        }
-        fence_mbar_init();
-    }
-    __syncthreads();
-    // row r (ya-1 <= r <= yb) is the k-th load, k = r - ya + 1: slot k % S, use k / S
-
-    if (warp == k5Consumers) {
-        // ---- producer
-        if (lane == 0) {
-            int last = -1;   // last k issued
-            bool ok = true;
-            for (int r = ya - 1; r <= yb; ++r) {
-                const int k = r - (ya - 1);
-                const int sl = k % k5Stages;
-                if (k >= k5Stages && !mbar_wait_bounded(&empty[sl], (unsigned)((k / k5Stages - 1) & 1))) {
-                    ok = false;
-                    break;
-                }
-                mbar_expect_tx(&full[sl], k5RowBytes);
-                tma_load_rows(lmap, ring + sl * k5Slot, &full[sl], segx - kTmaHalo, r + 1);
-                last = k;
-            }
-            if (!ok) {
-                atomicExch(&st->error, 4);   // LBM_ERR_TIMEOUT
-                // the copies still in flight land before the block may exit
-                for (int k = max(0, last - k5Stages + 1); k <= last; ++k)
-                    (void)mbar_wait_bounded(&full[k % k5Stages], (unsigned)((k / k5Stages) & 1));
-            }
-        }
-        return;
-    }
-
-    // ---- consumers
-    const int x = segx + tid;
-    const float omc = (float)(1.0 - pb.omega);
-    const float om_f = (float)pb.omega;
-    const double omc_d = 1.0 - pb.omega;
-    const float w0 = (float)d5_w(0), w1 = (float)d5_w(1);
-    const float thr_f = (float)pb.sat;
-    const int wx0 = segx + warp * 32;   // first column of this warp
-    const bool warp_interior_x = wx0 > 0 && wx0 + 31 < nx - 1;
-    const float* src = static_cast<const float*>(pb.state[a.parity]);   // Eq. (17) partners
-    float* dst = static_cast<float*>(pb.state[a.parity ^ 1]);
-    const long long pitch = pb.pitch;
-    Acc<float> acc;
-    TileSums ts;
-    auto wait_row = [&](int r) -> bool {
-        const int k = r - (ya - 1);
-        return mbar_wait_bounded(&full[k % k5Stages], (unsigned)((k / k5Stages) & 1));
-    };
-    bool ok = wait_row(ya - 1) && wait_row(ya);
-    for (int y = ya; ok && y < yb; ++y) {
-        ok = wait_row(y + 1);
-        if (!ok) break;
-        const int km = y - 1 - (ya - 1);
-        const float* sm1 = ring + (km % k5Stages) * k5Slot + kTmaHalo + tid;
-        const float* s0 = ring + ((km + 1) % k5Stages) * k5Slot + kTmaHalo + tid;
-        const float* sp1 = ring + ((km + 2) % k5Stages) * k5Slot + kTmaHalo + tid;
-        float u[5][1], qf[5][1];
-#pragma unroll
-        for (int i = 0; i < 5; ++i) u[i][0] = s0[i * k5Box];
-        qf[0][0] = u[0][0];
-        qf[1][0] = s0[1 * k5Box - 1];    // Omega_1(x - 1, y)
-        qf[3][0] = s0[3 * k5Box + 1];    // Omega_3(x + 1, y)
-        qf[2][0] = sm1[2 * k5Box];       // Omega_2(x, y - 1)
-        qf[4][0] = sp1[4 * k5Box];       // Omega_4(x, y + 1)
-        // every lane has read the slot of row y - 1: release it to the producer
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[km % k5Stages]);
-        float* drow = dst + (long long)(y + 1) * pitch + x;
-        if (pb.method == 1)
-            row5_update_eebm<float, 1, REC, true>(pb, src, drow, y, x, qf, u, a.rec, acc, ts, omc, w0, w1);
-        else if (warp_interior_x && y > 0 && y < ny - 1)
-            row5_update<float, 1, REC, false>(pb, src, drow, y, x, lane, qf, u, a.rec, acc, ts, 0, a.jobs, a.job_count,
-                                              omc, om_f, omc_d, w0, w1, thr_f);
-        else
-            row5_update<float, 1, REC, true>(pb, src, drow, y, x, lane, qf, u, a.rec, acc, ts, 0, a.jobs, a.job_count,
-                                             omc, om_f, omc_d, w0, w1, thr_f);
-    }
-    if (!ok && lane == 0) atomicExch(&st->error, 4);   // LBM_ERR_TIMEOUT
-    flush_tile_sums<float>(acc, ts, st, lane);
-}
-
-cudaError_t launch_d2q5_tma(const StepArgs& a, const TmaMaps& m, cudaStream_t s)
-{
-    const int grid = m.nsegs * m.nparts;
-    if (grid <= 0) return cudaErrorInvalidValue;
-    if (a.rec) d2q5_tma_kernel<true><<<grid, k5Threads, 0, s>>>(a, m);
-    else d2q5_tma_kernel<false><<<grid, k5Threads, 0, s>>>(a, m);
-    return cudaGetLastError();
-}
-
-int d2q5_tma_blocks_per_sm()
-{
-    // all of the unified L1 / shared memory as shared memory
-    cudaFuncSetAttribute(d2q5_tma_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    cudaFuncSetAttribute(d2q5_tma_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, d2q5_tma_kernel<false>, k5Threads, 0);
-    return n > 0 ? n : 1;
-}
-
 int d2q5_segment_width(int precision) { return precision == 1 ? 32 * V5<float>::N : 32 * V5<double>::N; }
 
 cudaError_t launch_d2q5_step(int precision, const StepArgs& a, cudaStream_t s)

@@ -2,7 +2,10 @@
 D1Q3 in FP64, against the oracle's ILFBM (``oracle.Problem.ilfbm_run``).
 
 Parity: theta to 1e-12 relative (FP64), the liquid fraction to 1e-10
-absolute (the lever rule's slope Ste maps theta's rounding into l).
+absolute (the lever rule's slope Ste maps theta's rounding into l), or ten
+times the problem's own rounding floor where that is larger (random fields
+with many mushy nodes: measured up to 6.5e-12 for the oracle against itself
+started one ulp away, 2,844 nodes, 300 steps).
 """
 import json
 import os
@@ -49,9 +52,16 @@ def test_ilfbm_parity(gpu, orc, n, wi, bb_mode):
     S.close()
     P = orc.Problem(1, n, 1, tau=tau, delta=0.01, ste=ste, walls=walls, bb_mode=bb_mode)
     _, lo, tho, failed, mx = P.ilfbm_run(th0, steps, tol=1e-12, maxit=200)
+    # the problem's own FP64 rounding floor (as for IREBM): the oracle against the
+    # oracle started one ulp away at random nodes; mushy nodes amplify rounding
+    rng = np.random.Generator(np.random.PCG64(12345))
+    pert = th0 + np.spacing(th0) * rng.choice([-1, 0, 1], size=th0.shape)
+    _, lp_, thp, _, _ = P.ilfbm_run(pert, steps, tol=1e-12, maxit=200)
+    tol_t = max(1e-12, 10 * np.max(np.abs(thp - tho)) / np.max(np.abs(tho)))
+    tol_l = max(1e-10, 10 * np.max(np.abs(lp_ - lo)))
     assert failed == 0 and st["error"] == 0
-    assert np.max(np.abs(th - tho)) <= 1e-12 * np.max(np.abs(tho))
-    assert np.max(np.abs(l - lo)) <= 1e-10
+    assert np.max(np.abs(th - tho)) <= tol_t * np.max(np.abs(tho))
+    assert np.max(np.abs(l - lo)) <= tol_l
     assert np.max(np.abs(H - (th + l / ste))) <= 1e-12 * np.max(np.abs(H))
     assert 1 <= st["newton_max_iter"] <= mx
 
