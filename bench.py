@@ -174,6 +174,19 @@ def bench_d2q5(torch, solver, workloads, steps, warmup, stream, peak, n=4096, fp
                     "kernel_gbs": gbs, "kernel_frac": gbs / peak,
                     "whole_step_gbs": bpn * nodes / (ms / steps * 1e-3) / 1e9,
                     "newton_nodes_last_step": st["newton_nodes"]}
+        if prec == workloads.FP32 and fp64:
+            # the paper's comparison scheme on the same lattice, workload and window
+            # (its 2D timing table compares EEBM and IREBM on D2Q5)
+            S = solver.Stefan.from_case(c, stream=stream)
+            S.set_method("EEBM")
+            S.set_ic(c.theta0())
+            S.step(melt_window(c, steps, warmup, centre) + warmup)
+            S.sync()
+            mse = time_steps(torch, S, steps, stream)
+            ke = S.step_timed(min(steps, 50))
+            S.close()
+            out["eebm_fp32"] = {"mlups": nodes * steps / mse / 1e3, "ms_per_step": mse / steps, "kernel_ms": ke[0],
+                                "kernel_gbs": bpn * nodes / (ke[0] * 1e-3) / 1e9, "irebm_over_eebm": ms / mse}
     return out
 
 
@@ -292,13 +305,14 @@ def bench_d1q3(torch, solver, workloads, stream):
 
 
 def bench_bar_1d(torch, solver, workloads, stream, steps=20000):
-    """The paper's 1D bar (N = 801, tau 0.62, delta 0.01) with IREBM and with
-    ILFBM (Algorithm 1), `steps` steps each, and the time of the full 160 s run
-    (204,800 steps) at that rate: the GPU counterpart of the paper's 1D timing
-    table (one M1 core: IREBM 5.586 s, ILFBM 22.01 s at N = 801)."""
+    """The paper's 1D bar (N = 801, tau 0.62, delta 0.01) with IREBM, EEBM
+    (Algorithm 2) and ILFBM (Algorithm 1), `steps` steps each, and the time of
+    the full 160 s run (204,800 steps) at that rate: the GPU counterpart of the
+    paper's 1D timing table (one M1 core at N = 801: EEBM 1.538 s, IREBM
+    5.586 s, ILFBM 22.01 s)."""
     c = workloads.bar_1d()
     out = {"workload": c.name, "steps_timed": steps}
-    for method in ("IREBM", "ILFBM"):
+    for method in ("IREBM", "EEBM", "ILFBM"):
         # ILFBM: the inner loop's tolerance on l and its iteration limit
         kw = dict(newton_tol=1e-12, newton_max_iter=200) if method == "ILFBM" else {}
         S = solver.Stefan.from_case(c, stream=stream, **kw)
@@ -313,6 +327,7 @@ def bench_bar_1d(torch, solver, workloads, stream, steps=20000):
         out[method.lower()] = {"steps_per_s": steps / ms * 1e3, "full_run_s": c.steps * ms / steps / 1e3,
                                "iterations_last_step": st["newton_max_iter"]}
     out["ilfbm_over_irebm"] = out["ilfbm"]["full_run_s"] / out["irebm"]["full_run_s"]
+    out["irebm_over_eebm"] = out["irebm"]["full_run_s"] / out["eebm"]["full_run_s"]
     return out
 
 
@@ -428,7 +443,7 @@ def run_gpu(args):
         extra["batched_256"] = bench_batch(torch, solver, workloads, max(20, args.steps // 2), args.warmup, stream)
         extra["adjoint_1024"] = bench_adjoint(torch, solver, workloads, stream)
         extra["d1q3_512"] = bench_d1q3(torch, solver, workloads, stream)
-        extra["bar_1d_801_irebm_ilfbm"] = bench_bar_1d(torch, solver, workloads, stream)
+        extra["bar_1d_801_three_schemes"] = bench_bar_1d(torch, solver, workloads, stream)
         extra["d2q5_cavity_4096"] = bench_d2q5(torch, solver, workloads, args.steps, args.warmup, stream, peak)
     e2e_ms, h2d, d2h = bench_e2e(torch, solver, case, args.steps, stream) if rank == 0 else (0, 0, 0)
 
