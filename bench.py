@@ -106,6 +106,22 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# ------------------------------------------------------------------ replicas
+def max_over_ranks(torch, dist, value, device):
+    """The largest `value` over the ranks of the process group (the job ends with
+    its slowest replica); `value` itself without a process group."""
+    if dist is None:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(world, nodes, steps, ms_max):
+    """Whole-job throughput: every replica's node updates over the slowest replica's time."""
+    return world * nodes * steps / ms_max / 1e3
+
+
 # ------------------------------------------------------------------ GPU measurements
 def time_steps(torch, S, steps, stream):
     """Device time of `steps` steps (ms), CUDA events on the launching stream."""
@@ -410,13 +426,8 @@ def run_gpu(args):
     nodes = case.nx * case.ny
     with ClockSampler(local) as clk:
         ms, st = bench_single(torch, solver, case, args.steps, args.warmup, stream, barrier, args.window_step)
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    else:
-        ms_max = ms
-    value = world * nodes * args.steps / ms_max / 1e3
+    ms_max = max_over_ranks(torch, dist, ms, "cuda")
+    value = job_mlups(world, nodes, args.steps, ms_max)
     per_step_ms = ms / args.steps
     k_step_ms, k_job_ms = st["kernel_ms"]
     # the dominant kernel: the TMA stream/collide kernel moves 72 algorithmic bytes per node
