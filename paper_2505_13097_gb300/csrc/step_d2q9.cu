@@ -874,8 +874,12 @@ constexpr int kTmaConsumers = kTmaW / 32;                       // consumer warp
 constexpr int kTmaThreads = kTmaW + 32;                         // + the producer warp
 constexpr unsigned kTmaRowBytes = 9u * kTmaBox * 4u;             // bytes one row load delivers
 
+#ifndef LBM_TMA_MIN_BLOCKS
+#define LBM_TMA_MIN_BLOCKS 5   // resident blocks per SM the register budget is fitted to
+#endif
+
 template <bool REC>
-__global__ void __launch_bounds__(kTmaThreads, 5) d2q9_tma_kernel(const StepArgs a, const __grid_constant__ TmaMaps m)
+__global__ void __launch_bounds__(kTmaThreads, LBM_TMA_MIN_BLOCKS) d2q9_tma_kernel(const StepArgs a, const __grid_constant__ TmaMaps m)
 {
     __shared__ __align__(128) float ring[kTmaStages * kTmaSlot];
     __shared__ __align__(8) unsigned long long full[kTmaStages];

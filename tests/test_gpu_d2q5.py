@@ -224,7 +224,7 @@ def test_d2q5_argument_errors(gpu):
         assert e.value.status == _abi.LBM_ERR_ARG
     S = make()
     with pytest.raises(_abi.LBMError) as e:
-        S.set_method("EEBM")
+        S.set_method("ILFBM")
     assert e.value.status == _abi.LBM_ERR_ARG
     S.set_ic(np.zeros((32, 32)))
     planes = S.new_theta_planes(2)

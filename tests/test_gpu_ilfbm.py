@@ -4,8 +4,9 @@ D1Q3 in FP64, against the oracle's ILFBM (``oracle.Problem.ilfbm_run``).
 Parity: theta to 1e-12 relative (FP64), the liquid fraction to 1e-10
 absolute (the lever rule's slope Ste maps theta's rounding into l), or ten
 times the problem's own rounding floor where that is larger (random fields
-with many mushy nodes: measured up to 6.5e-12 for the oracle against itself
-started one ulp away, 2,844 nodes, 300 steps).
+with many mushy nodes: up to 1e-11 for the oracle against itself started one
+ulp away, 801 nodes, 300 steps).  The smooth single-front paper case keeps
+the plain 1e-12.
 """
 import json
 import os
@@ -53,12 +54,18 @@ def test_ilfbm_parity(gpu, orc, n, wi, bb_mode):
     P = orc.Problem(1, n, 1, tau=tau, delta=0.01, ste=ste, walls=walls, bb_mode=bb_mode)
     _, lo, tho, failed, mx = P.ilfbm_run(th0, steps, tol=1e-12, maxit=200)
     # the problem's own FP64 rounding floor (as for IREBM): the oracle against the
-    # oracle started one ulp away at random nodes; mushy nodes amplify rounding
-    rng = np.random.Generator(np.random.PCG64(12345))
-    pert = th0 + np.spacing(th0) * rng.choice([-1, 0, 1], size=th0.shape)
-    _, lp_, thp, _, _ = P.ilfbm_run(pert, steps, tol=1e-12, maxit=200)
-    tol_t = max(1e-12, 10 * np.max(np.abs(thp - tho)) / np.max(np.abs(tho)))
-    tol_l = max(1e-10, 10 * np.max(np.abs(lp_ - lo)))
+    # oracle started one ulp away at random nodes, the largest of three such
+    # starts (random fields put many nodes in the mushy band, which amplifies
+    # rounding; the floor varies by 6x between starts)
+    fl_t = fl_l = 0.0
+    for seed in (12345, 1, 2):
+        rng = np.random.Generator(np.random.PCG64(seed))
+        pert = th0 + np.spacing(th0) * rng.choice([-1, 0, 1], size=th0.shape)
+        _, lp_, thp, _, _ = P.ilfbm_run(pert, steps, tol=1e-12, maxit=200)
+        fl_t = max(fl_t, np.max(np.abs(thp - tho)))
+        fl_l = max(fl_l, np.max(np.abs(lp_ - lo)))
+    tol_t = max(1e-12, 10 * fl_t / np.max(np.abs(tho)))
+    tol_l = max(1e-10, 10 * fl_l)
     assert failed == 0 and st["error"] == 0
     assert np.max(np.abs(th - tho)) <= tol_t * np.max(np.abs(tho))
     assert np.max(np.abs(l - lo)) <= tol_l
