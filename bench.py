@@ -414,6 +414,11 @@ def run_gpu(args):
     barrier = (lambda: dist.barrier(device_ids=[local])) if dist else None
     stream = torch.cuda.Stream()
     peak, peak_kind = load_peaks()
+    if args.only_bar:
+        # profiling aid: the 1D bar with the three schemes, --steps steps each
+        if rank == 0:
+            print(json.dumps({"bar_1d": bench_bar_1d(torch, solver, workloads, stream, steps=args.steps)}), flush=True)
+        return 0
     if args.only_d2q5:
         # profiling aid: the D2Q5 cavity leg alone, FP32
         if rank == 0:
@@ -517,6 +522,8 @@ def main():
                     help="side of the melting workload (default 4096, the benchmark); a profiling aid")
     ap.add_argument("--window-step", type=int, default=None,
                     help="centre the timed window on this step (default: mid-run, step 5,000); a profiling aid")
+    ap.add_argument("--only-bar", action="store_true",
+                    help="time the 1D bar (IREBM, EEBM, ILFBM) alone, --steps steps each; a profiling aid")
     ap.add_argument("--only-d2q5", action="store_true",
                     help="time the D2Q5 cavity leg alone, FP32, side --n (default 4096); a profiling aid")
     args = ap.parse_args()
