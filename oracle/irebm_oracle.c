@@ -23,7 +23,7 @@
  * x fastest) and recomputes theta = M0(f) at the start of every step, exactly
  * as Algorithm 3 does.  No blocking, fusion or reordering.
  *
- * Readings where the paper is silent (each is listed in the design doc):
+ * Readings where the paper is silent:
  *  - weights: D1Q3 (2/3, 1/6, 1/6), D2Q5 (1/3, 1/6 x4), D2Q9 (4/9, 1/9 x4,
  *    1/36 x4), c_s^2 = 1/3 on all three.
  *  - Newton stopping: |x_{k+1}-x_k| <= tol*max(1,|x_k|) (x_{k+1} kept), or

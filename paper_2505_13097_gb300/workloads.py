@@ -33,8 +33,8 @@ benchmark configurations:
                      = 1.762 * 10 / 338, tau 0.84 and delta 0.01 (the timing
                      table's values), FP32 populations; 4096 x 4096 by default.
 
-tau = 1.0 wherever the configuration does not fix it (the design doc lists this
-reading).  Walls are given as {"W": (kind, theta), ...} with kind 0 =
+tau = 1.0 wherever the configuration does not fix it (a reading: the paper
+gives tau only for its own cases).  Walls are given as {"W": (kind, theta), ...} with kind 0 =
 adiabatic, 1 = Dirichlet.
 """
 from __future__ import annotations
