@@ -32,18 +32,6 @@ namespace lbm {
 constexpr int kIlfThreads = 512;
 constexpr int kIlfWarps = kIlfThreads / 32;
 
-// Deterministic block sum: warp shuffles, then a fixed order over warps.
-__device__ __forceinline__ double ilf_block_sum(double v, double* sh)
-{
-    v = warp_sum(v);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    __syncthreads();
-    if (l == 0) sh[w] = v;
-    __syncthreads();
-    double s = 0.0;
-    for (int k = 0; k < kIlfWarps; ++k) s += sh[k];
-    return s;   // the same value in every thread
-}
 __device__ __forceinline__ double ilf_lever(double H, double ste, double inv_ste)
 {
     return H < 0.0 ? 0.0 : (H > inv_ste ? 1.0 : ste * H);
@@ -52,7 +40,7 @@ __device__ __forceinline__ double ilf_lever(double H, double ste, double inv_ste
 __global__ void __launch_bounds__(kIlfThreads) ilfbm_d1q3_kernel(StepArgs a, int nsteps)
 {
     extern __shared__ double sm[];
-    __shared__ double red[kIlfWarps];
+    __shared__ double red_e[2][kIlfWarps], red_f[2][kIlfWarps];   // per-step partial sums, step parity
     __shared__ int s_more[3];   // "some node changed by more than tol", iteration gk uses gk % 3
     const Problem& pb = a.probs[0];
     DevStats* st = &a.stats[pb.stats];
@@ -76,6 +64,18 @@ __global__ void __launch_bounds__(kIlfThreads) ilfbm_d1q3_kernel(StepArgs a, int
     const bool mirror = pb.bb_mode == 0;
     bool failed = false;
     unsigned gk = 0;   // inner iterations so far in this launch: selects the flag
+    // thread 0: the statistics carried across the steps of this launch
+    double E = 0.0, E_prev = 0.0, imb = 0.0, imb_max = 0.0, flux = 0.0;
+    int have = 0, last_it = 0;
+    if (threadIdx.x == 0) {
+        E = st->energy;
+        E_prev = st->energy_prev;
+        imb = st->imbalance;
+        imb_max = st->imbalance_max;
+        flux = st->flux;
+        have = st->have_energy;
+        last_it = st->newton_max_iter;
+    }
     if (threadIdx.x < 3) s_more[threadIdx.x] = 0;
     __syncthreads();
     for (int s = 0; s < nsteps; ++s) {
@@ -151,27 +151,48 @@ __global__ void __launch_bounds__(kIlfThreads) ilfbm_d1q3_kernel(StepArgs a, int
             fn[2 * n + y] = q2;
             e += (q0 + q1 + q2) + ln[y] * inv_ste;
         }
-        const double es = ilf_block_sum(e, red);     // its barriers also order the reads of
-        const double fs = ilf_block_sum(fl, red);    // o, el and l^(k-1) before the writes below
+        e = warp_sum(e);
+        fl = warp_sum(fl);
+        const int h = s & 1;
+        if ((threadIdx.x & 31) == 0) {
+            red_e[h][threadIdx.x >> 5] = e;
+            red_f[h][threadIdx.x >> 5] = fl;
+        }
+        __syncthreads();   // every read of o, el and l^(k-1) of this step is done
         for (int y = threadIdx.x; y < n; y += blockDim.x) el[y] = ln[y];
         double* t = o;
         o = fn;
         fn = t;
         if (threadIdx.x == 0) {
-            if (st->have_energy) {
-                const double imb = es - st->energy - fs;
-                st->imbalance = imb;
-                if (fabs(imb) > st->imbalance_max) st->imbalance_max = fabs(imb);
+            // the warps' sums in a fixed order; a half of red_* is written again two
+            // steps later, after the next step's barriers, which thread 0 reaches
+            // only after this
+            double es = 0.0, fs = 0.0;
+            for (int k = 0; k < kIlfWarps; ++k) {
+                es += red_e[h][k];
+                fs += red_f[h][k];
             }
-            st->energy_prev = st->energy;
-            st->energy = es;
-            st->flux = fs;
-            st->have_energy = 1;
-            st->steps += 1;
-            st->newton_nodes = 0;
-            st->newton_max_iter = it;   // inner iterations of this step
+            if (have) {
+                imb = es - E - fs;
+                if (fabs(imb) > imb_max) imb_max = fabs(imb);
+            }
+            E_prev = E;
+            E = es;
+            flux = fs;
+            have = 1;
+            last_it = it;
         }
-        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        st->energy = E;
+        st->energy_prev = E_prev;
+        st->imbalance = imb;
+        st->imbalance_max = imb_max;
+        st->flux = flux;
+        st->have_energy = have;
+        st->steps += nsteps;
+        st->newton_nodes = 0;
+        st->newton_max_iter = last_it;   // inner iterations of the last step
     }
     if (failed && threadIdx.x == 0) atomicOr(&st->error, 3);   // LBM_ERR_NEWTON: inner loop at its limit
     double* dst = static_cast<double*>(pb.state[a.parity ^ (nsteps & 1)]);

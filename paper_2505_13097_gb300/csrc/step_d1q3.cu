@@ -133,21 +133,15 @@ __global__ void __launch_bounds__(128) d1q3_step_kernel(StepArgs a)
 }
 
 constexpr int kFusedThreads = 512;
+constexpr int kFusedWarps = kFusedThreads / 32;
 
-// Deterministic block sum (fixed shuffle tree, then fixed order over warps).
-__device__ __forceinline__ double block_sum(double v, double* sh)
-{
-    v = warp_sum(v);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    __syncthreads();
-    if (l == 0) sh[w] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0)
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += sh[k];
-    return s;   // valid in thread 0
-}
-
+// One block keeps the lattice in shared memory and runs `nsteps` steps.  A
+// step ends at a single barrier: the warps' partial sums go to a per-step
+// parity half of a small array, and thread 0 sums them in a fixed warp order
+// (deterministic) after the barrier while the others start the next step; a
+// warp writes that half again only two steps later, after the next barrier,
+// which thread 0 reaches only when it has read it.  Thread 0 keeps the
+// statistics in registers and writes them once at the end.
 template <typename P>
 __global__ void __launch_bounds__(kFusedThreads) d1q3_fused_kernel(StepArgs a, int nsteps, double* rec)
 {
@@ -156,11 +150,27 @@ __global__ void __launch_bounds__(kFusedThreads) d1q3_fused_kernel(StepArgs a, i
     DevStats* st = &a.stats[pb.stats];
     const int n = pb.nx;
     P* buf[2] = {reinterpret_cast<P*>(smem_raw), reinterpret_cast<P*>(smem_raw) + 3 * n};
-    __shared__ double red[128];   // [0,16) energy, [32,48) flux, [64,80) Newton nodes, [96,112) max iterations
+    __shared__ double red_e[2][kFusedWarps], red_f[2][kFusedWarps];
+    __shared__ int red_n[2][kFusedWarps], red_m[2][kFusedWarps];
     const long long pl = pb.plane, row = pb.pitch;
     const P* src = static_cast<const P*>(pb.state[a.parity]);
     for (int x = threadIdx.x; x < n; x += blockDim.x)
         for (int i = 0; i < 3; ++i) buf[0][i * n + x] = src[i * pl + row + x];
+    // thread 0: the statistics carried across the steps of this launch
+    double E = 0.0, imb = 0.0, imb_max = 0.0, flux = 0.0, E_prev = 0.0;
+    int have = 0, last_n = 0, last_m = 0;
+    if (threadIdx.x == 0) {
+        E = st->energy;
+        E_prev = st->energy_prev;
+        imb = st->imbalance;
+        imb_max = st->imbalance_max;
+        flux = st->flux;
+        have = st->have_energy;
+        last_n = (int)st->newton_nodes;
+        last_m = st->newton_max_iter;
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    bool fail = false;
     __syncthreads();
     int cur = 0;
     for (int s = 0; s < nsteps; ++s) {
@@ -168,7 +178,6 @@ __global__ void __launch_bounds__(kFusedThreads) d1q3_fused_kernel(StepArgs a, i
         P* out = buf[cur ^ 1];
         double e = 0.0, f = 0.0;
         int nn = 0, mi = 0;
-        bool fail = false;
         for (int x = threadIdx.x; x < n; x += blockDim.x) {
             P u[3] = {in[x], in[n + x], in[2 * n + x]}, o[3];
             const P ql = x > 0 ? in[n + x - 1] : (P)0;
@@ -184,39 +193,51 @@ __global__ void __launch_bounds__(kFusedThreads) d1q3_fused_kernel(StepArgs a, i
             mi = max(mi, r.iters);
             fail |= r.fail;
         }
-        if (fail) atomicOr(&st->error, 3);
+        e = warp_sum(e);
+        f = warp_sum(f);
         nn = warp_sum_i(nn);
         mi = warp_max_i(mi);
-        const double es = block_sum(e, red);
-        const double fs = block_sum(f, red + 32);
-        __syncthreads();
-        if ((threadIdx.x & 31) == 0) {
-            red[64 + (threadIdx.x >> 5)] = (double)nn;
-            red[96 + (threadIdx.x >> 5)] = (double)mi;
+        const int h = s & 1;
+        if (l == 0) {
+            red_e[h][w] = e;
+            red_f[h][w] = f;
+            red_n[h][w] = nn;
+            red_m[h][w] = mi;
         }
-        __syncthreads();
+        __syncthreads();   // the step's writes of `out` and of the partial sums are complete
         if (threadIdx.x == 0) {
-            long long nsum = 0;
-            int mmax = 0;
-            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-                nsum += (long long)red[64 + k];
-                mmax = max(mmax, (int)red[96 + k]);
+            double es = 0.0, fs = 0.0;
+            int nsum = 0, mmax = 0;
+            for (int k = 0; k < kFusedWarps; ++k) {
+                es += red_e[h][k];
+                fs += red_f[h][k];
+                nsum += red_n[h][k];
+                mmax = max(mmax, red_m[h][k]);
             }
-            if (st->have_energy) {
-                const double imb = es - st->energy - fs;
-                st->imbalance = imb;
-                if (fabs(imb) > st->imbalance_max) st->imbalance_max = fabs(imb);
+            if (have) {
+                imb = es - E - fs;
+                if (fabs(imb) > imb_max) imb_max = fabs(imb);
             }
-            st->energy_prev = st->energy;
-            st->energy = es;
-            st->flux = fs;
-            st->have_energy = 1;
-            st->steps += 1;
-            st->newton_nodes = nsum;
-            st->newton_max_iter = mmax;
+            E_prev = E;
+            E = es;
+            flux = fs;
+            have = 1;
+            last_n = nsum;
+            last_m = mmax;
         }
-        __syncthreads();
         cur ^= 1;
+    }
+    if (fail) atomicOr(&st->error, 3);
+    if (threadIdx.x == 0) {
+        st->energy = E;
+        st->energy_prev = E_prev;
+        st->imbalance = imb;
+        st->imbalance_max = imb_max;
+        st->flux = flux;
+        st->have_energy = have;
+        st->steps += nsteps;
+        st->newton_nodes = last_n;
+        st->newton_max_iter = last_m;
     }
     P* dst = static_cast<P*>(pb.state[a.parity ^ (nsteps & 1)]);
     for (int x = threadIdx.x; x < n; x += blockDim.x)
