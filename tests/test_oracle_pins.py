@@ -730,12 +730,17 @@ def test_ilfbm_converged_step_is_a_lever_rule_fixed_point(orc):
 
 def test_ilfbm_inner_loop_fails_on_the_d2q5_cavity(orc):
     # Sec. 6.2: the paper reports that ILFBM's inner iterations did not converge
-    # in its 2D case; the oracle's loop does not converge either in some steps
-    # of the D2Q5 cavity (200 iterations), while the D1Q3 bar converges
+    # in its 2D case.  A mushy node's iterate subtracts the weighted mean of its
+    # neighbours' previous iterates; the checkerboard mode's factor is
+    # 1 - sum_i w_i (-1)^(e_ix + e_iy): 4/3 on D2Q5 (the loop fails in some steps
+    # of the D2Q5 cavity), 8/9 on D2Q9 and 2/3 on D1Q3 (the loops converge)
     c = workloads.cavity_2d(n=32, steps=150, precision=workloads.FP64)
     P = orc.Problem(3, c.nx, c.ny, tau=c.tau, delta=c.delta, ste=c.ste, walls=c.walls)
     *_, failed, mx = P.ilfbm_run(c.theta0(), c.steps, maxit=200)
     assert failed > 0 and mx == 200
+    P9 = orc.Problem(2, c.nx, c.ny, tau=c.tau, delta=c.delta, ste=c.ste, walls=c.walls)
+    *_, failed9, mx9 = P9.ilfbm_run(c.theta0(), c.steps, maxit=200)
+    assert failed9 == 0 and mx9 < 200
     P1 = orc.Problem(1, 64, 1, tau=0.62, delta=0.01, ste=0.2857, walls={"W": (1, 1.0), "E": (1, -0.5)})
     *_, failed1, mx1 = P1.ilfbm_run(np.full((1, 64), -0.5), 1500, maxit=200)
     assert failed1 == 0 and mx1 < 200
