@@ -116,9 +116,12 @@ lbm_status lbm_stefan_set_bc(lbm_stefan* h, int wall, int kind, double theta_wal
  * sum of H; the adjoint calls return LBM_ERR_STATE.  Discards the state: call
  * lbm_stefan_set_ic afterwards.  LBM_ERR_ARG for an unknown method.
  * LBM_ILFBM: the implicit liquid fraction based method of Algorithm 1
- * (Sec. 3.3), the paper's other comparison scheme, D1Q3 in FP64 up to 2,844
- * nodes: theta = M0(f), f_i^eq = w_i theta, and a liquid-fraction field l
- * (the fourth plane of the D1Q3 state, zero for the other methods) updated
+ * (Sec. 3.3), the paper's other comparison scheme, in FP64 on D1Q3 (up to
+ * 2,844 nodes, one block) and on D2Q9 / D2Q5 (one launch per inner
+ * iteration; the state buffers grow by one plane, so lbm_stefan_layout's
+ * state_bytes changes): theta = M0(f), f_i^eq = w_i theta, and a
+ * liquid-fraction field l (the plane after the q populations: the fourth
+ * plane of the D1Q3 state, zero for the other methods) updated
  * by an inner loop of collision with the source (w_i/Ste)(l - l^(k-1)),
  * streaming, H^(k) = M0(f^(k)) + l^(k-1)/Ste and the lever rule l(H) = 0,
  * Ste H, 1 (H < 0, in [0, 1/Ste], above), until max |l^(k) - l^(k-1)| <=
@@ -128,7 +131,8 @@ lbm_status lbm_stefan_set_bc(lbm_stefan* h, int wall, int kind, double theta_wal
  * H = theta + l/Ste; the energy statistics are the sum of H and
  * newton_max_iter the last step's inner iteration count; step_record,
  * step_timed and the adjoint calls return LBM_ERR_STATE / LBM_ERR_ARG;
- * LBM_ERR_ARG for ILFBM on another lattice, in FP32 or beyond 2,844 nodes. */
+ * LBM_ERR_ARG for ILFBM in FP32, with the Eq. (17) closure, or on D1Q3
+ * beyond 2,844 nodes. */
 lbm_status lbm_stefan_set_method(lbm_stefan* h, int method);
 
 /* Initial state: f_i = w_i theta0 (equilibrium), Dirichlet nodes at their wall

@@ -1,5 +1,6 @@
 // ILFBM step (Algorithm 1, the implicit liquid fraction based method of
-// Sec. 3.3), the paper's second comparison scheme, on D1Q3 in FP64.
+// Sec. 3.3), the paper's second comparison scheme, in FP64: D1Q3 in one
+// block (below), D2Q9 and D2Q5 with one launch per inner iteration (at the end).
 //
 // State: f_i (planes 0..2, theta = M0(f)) and the liquid fraction l (plane 3
 // of the same buffer).  One step:
@@ -200,6 +201,270 @@ __global__ void __launch_bounds__(kIlfThreads) ilfbm_d1q3_kernel(StepArgs a, int
         for (int i = 0; i < 3; ++i) dst[i * pl + row + x] = o[i * n + x];
         dst[3 * pl + row + x] = el[x];
     }
+}
+
+// ---------------------------------------------------------------- 2D lattices
+// ILFBM on D2Q9 and D2Q5 (Q = 9 or 5; the D2Q5 velocities are D2Q9's first
+// five), FP64.  The inner loop needs a lattice-wide barrier per iteration, so
+// an iteration is one launch; a step is
+//   ilf2_collide   Omega0_i = f_i - (f_i - w_i theta)/tau in place, l^(0) = l
+//   ilf2_s0        S0(y) = sum_i Omega0_i(y - e_i) at the interior nodes
+//   ilf2_iter x maxit
+//                  l^(k)(y) = l(H^(k)(y)), H^(k) = S0(y) + sum_i (w_i/Ste)
+//                  (l - l^(k-1))(y - e_i) + l^(k-1)(y)/Ste at interior nodes, the
+//                  closed streamed populations at wall nodes; a "changed" flag
+//                  per iteration (three in rotation: launch k reads k-1's,
+//                  sets its own and clears k+1's, last read by launch k-1); the
+//                  first launch that finds the previous iteration unchanged
+//                  records it and every later launch returns at once
+//   ilf2_final     f~_i(y) = Omega_i(y - e_i) with the source of l^(K-1) and
+//                  the closures, l~ = l^(K); energy sum theta~ + l~/Ste, flux,
+//                  iteration count, the iteration-limit error; publishes
+// Scratch (nx*ny doubles each, in the handle's field scratch): S0, l^(k) x 2.
+struct Ilf2Args {
+    const Problem* prob;
+    int parity;              // state[parity] holds f, then Omega0; f~ goes to state[parity ^ 1]
+    double* s0;
+    double* lb[2];           // l^(k-1) / l^(k) of iteration k: lb[(k-1) & 1] / lb[k & 1]
+    unsigned int* flags;     // [0] done, [1] converged iteration, [2..4] changed per iteration mod 3
+    DevStats* stats;
+    unsigned int* ticket;
+};
+
+template <int Q>
+__device__ __forceinline__ bool ilf2_known(const Problem& pb, int x, int y, int i)
+{
+    const int sx = x - d2_ex(i), sy = y - d2_ey(i);
+    return sx >= 0 && sx < pb.nx && sy >= 0 && sy < pb.ny;
+}
+
+__device__ __forceinline__ int ilf2_dirichlet(const Problem& pb, int x, int y)
+{
+    const int walls = (x == 0 ? 1 : 0) | (x == pb.nx - 1 ? 2 : 0) | (y == 0 ? 4 : 0) | (y == pb.ny - 1 ? 8 : 0);
+    for (int k = 0; k < 4; ++k)
+        if (((walls >> k) & 1) && pb.wall_kind[k] == 1) return k;
+    return -1;
+}
+
+// Omega_i at node (x, y) with the source of the iterate lp: Omega0_i + (w_i/Ste)(l - lp)
+template <int Q>
+__device__ __forceinline__ double ilf2_omega(const Problem& pb, const double* st, const double* lp, int i, int x, int y)
+{
+    const long long nd = (long long)y * pb.nx + x;
+    const double* lq = st + Q * pb.plane;
+    return st[i * pb.plane + (long long)(y + 1) * pb.pitch + x] +
+           lat_w(Q, i) * pb.inv_ste * (lq[(long long)(y + 1) * pb.pitch + x] - lp[nd]);
+}
+
+// the streamed populations of node (x, y) with the source of lp, closed at a wall
+// (Dirichlet: the unknowns share theta_D - sum(known) by weight; bounce-back:
+// mirror where the opposite is known, else link-wise); returns the flux term
+// (filled minus leaving) when `flux` is set
+template <int Q>
+__device__ __forceinline__ double ilf2_streamed(const Problem& pb, const double* st, const double* lp, int x, int y,
+                                                double (&q)[Q], bool flux)
+{
+    unsigned unk = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        if (ilf2_known<Q>(pb, x, y, i)) q[i] = ilf2_omega<Q>(pb, st, lp, i, x - d2_ex(i), y - d2_ey(i));
+        else { q[i] = 0.0; unk |= 1u << i; }
+    }
+    if (!unk) return 0.0;
+    const int wk = ilf2_dirichlet(pb, x, y);
+    double in = 0.0, out = 0.0;
+    if (wk >= 0) {
+        double rest = pb.wall_theta[wk], wu = 0.0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if ((unk >> i) & 1) wu += lat_w(Q, i);
+            else rest -= q[i];
+        }
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+            if ((unk >> i) & 1) q[i] = lat_w(Q, i) * rest / wu;
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+            if ((unk >> i) & 1) {
+                const int o = d2_opp(i);
+                q[i] = (pb.bb_mode == 0 && !((unk >> o) & 1)) ? q[o] : ilf2_omega<Q>(pb, st, lp, o, x, y);
+            }
+    }
+    if (flux) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+            if ((unk >> i) & 1) {
+                in += q[i];
+                out += ilf2_omega<Q>(pb, st, lp, d2_opp(i), x, y);   // Omega leaving through the wall
+            }
+    }
+    return in - out;
+}
+
+template <int Q>
+__global__ void __launch_bounds__(256) ilf2_collide(Ilf2Args a)
+{
+    const Problem& pb = *a.prob;
+    double* st = static_cast<double*>(pb.state[a.parity]);
+    const long long n = (long long)pb.nx * pb.ny;
+    if (blockIdx.x == 0 && threadIdx.x < 5) a.flags[threadIdx.x] = 0u;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(k % pb.nx), y = (int)(k / pb.nx);
+        const long long at = (long long)(y + 1) * pb.pitch + x;
+        double f[Q], th = 0.0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            f[i] = st[i * pb.plane + at];
+            th += f[i];
+        }
+#pragma unroll
+        for (int i = 0; i < Q; ++i) st[i * pb.plane + at] = f[i] - (f[i] - lat_w(Q, i) * th) * pb.omega;
+        a.lb[0][k] = st[Q * pb.plane + at];
+    }
+}
+
+template <int Q>
+__global__ void __launch_bounds__(256) ilf2_s0(Ilf2Args a)
+{
+    const Problem& pb = *a.prob;
+    const double* st = static_cast<const double*>(pb.state[a.parity]);
+    const long long n = (long long)pb.nx * pb.ny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(k % pb.nx), y = (int)(k / pb.nx);
+        if (x == 0 || x == pb.nx - 1 || y == 0 || y == pb.ny - 1) continue;
+        double s = 0.0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+            s += st[i * pb.plane + (long long)(y - d2_ey(i) + 1) * pb.pitch + x - d2_ex(i)];
+        a.s0[k] = s;
+    }
+}
+
+template <int Q>
+__global__ void __launch_bounds__(256) ilf2_iter(Ilf2Args a, int k)
+{
+    volatile unsigned int* fl = a.flags;
+    if (fl[0]) return;   // converged in an earlier iteration
+    if (k > 1 && fl[2 + (k - 1) % 3] == 0u) {
+        // iteration k - 1 changed nothing: it is the last one
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            fl[1] = (unsigned)(k - 1);
+            fl[0] = 1u;
+        }
+        return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) fl[2 + (k + 1) % 3] = 0u;
+    const Problem& pb = *a.prob;
+    const double* st = static_cast<const double*>(pb.state[a.parity]);
+    const double* lq = st + Q * pb.plane;
+    const double* lp = a.lb[(k - 1) & 1];
+    double* ln = a.lb[k & 1];
+    const long long n = (long long)pb.nx * pb.ny;
+    bool more = false;
+    for (long long nd = blockIdx.x * (long long)blockDim.x + threadIdx.x; nd < n; nd += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(nd % pb.nx), y = (int)(nd / pb.nx);
+        const int wk = ilf2_dirichlet(pb, x, y);
+        double lk;
+        if (wk >= 0) {
+            lk = pb.wall_theta[wk] > 0.0 ? 1.0 : 0.0;
+        } else {
+            double H;
+            if (x > 0 && x < pb.nx - 1 && y > 0 && y < pb.ny - 1) {
+                H = a.s0[nd];
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    const int sx = x - d2_ex(i), sy = y - d2_ey(i);
+                    const long long sn = (long long)sy * pb.nx + sx;
+                    H += lat_w(Q, i) * pb.inv_ste * (lq[(long long)(sy + 1) * pb.pitch + sx] - lp[sn]);
+                }
+            } else {
+                double q[Q];
+                (void)ilf2_streamed<Q>(pb, st, lp, x, y, q, false);
+                H = 0.0;
+#pragma unroll
+                for (int i = 0; i < Q; ++i) H += q[i];
+            }
+            H += lp[nd] * pb.inv_ste;
+            lk = ilf_lever(H, pb.ste, pb.inv_ste);
+        }
+        more |= fabs(lk - lp[nd]) > pb.tol;
+        ln[nd] = lk;
+    }
+    if (__any_sync(kFull, more) && (threadIdx.x & 31) == 0) fl[2 + k % 3] = 1u;
+}
+
+template <int Q>
+__global__ void __launch_bounds__(256) ilf2_final(Ilf2Args a, int maxit)
+{
+    const Problem& pb = *a.prob;
+    const volatile unsigned int* fl = a.flags;
+    const bool done = fl[0] != 0u;
+    const int K = done ? (int)fl[1] : maxit;
+    const bool conv = done || fl[2 + maxit % 3] == 0u;
+    const double* st = static_cast<const double*>(pb.state[a.parity]);
+    double* dst = static_cast<double*>(pb.state[a.parity ^ 1]);
+    const double* lp = a.lb[(K - 1) & 1];
+    const double* ln = a.lb[K & 1];
+    DevStats* sts = &a.stats[pb.stats];
+    const long long n = (long long)pb.nx * pb.ny;
+    double e = 0.0, fx = 0.0;
+    for (long long nd = blockIdx.x * (long long)blockDim.x + threadIdx.x; nd < n; nd += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(nd % pb.nx), y = (int)(nd / pb.nx);
+        double q[Q];
+        fx += ilf2_streamed<Q>(pb, st, lp, x, y, q, true);
+        const long long at = (long long)(y + 1) * pb.pitch + x;
+        double th = 0.0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            dst[i * pb.plane + at] = q[i];
+            th += q[i];
+        }
+        dst[Q * pb.plane + at] = ln[nd];
+        e += th + ln[nd] * pb.inv_ste;
+    }
+    e = warp_sum(e);
+    fx = warp_sum(fx);
+    if ((threadIdx.x & 31) == 0) {
+        acc_add(&sts->cur_energy, e);
+        acc_add(&sts->cur_flux, fx);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        atomicMax(&sts->cur_maxit, K);
+        if (!conv) atomicOr(&sts->error, 3);   // LBM_ERR_NEWTON: the inner loop reached its limit
+    }
+    finish_launch(a.stats, 1, a.ticket);
+}
+
+template <int Q>
+static cudaError_t ilf2_step(const Ilf2Args& a, int maxit, int grid, cudaStream_t s)
+{
+    ilf2_collide<Q><<<grid, 256, 0, s>>>(a);
+    ilf2_s0<Q><<<grid, 256, 0, s>>>(a);
+    for (int k = 1; k <= maxit; ++k) ilf2_iter<Q><<<grid, 256, 0, s>>>(a, k);
+    ilf2_final<Q><<<grid, 256, 0, s>>>(a, maxit);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ilfbm_2d(const Problem& hp, const Problem* dprob, int parity, double* scratch,
+                            unsigned int* flags, DevStats* stats, unsigned int* ticket, cudaStream_t s)
+{
+    Ilf2Args a;
+    a.prob = dprob;
+    a.parity = parity;
+    const long long n = (long long)hp.nx * hp.ny;
+    a.s0 = scratch;
+    a.lb[0] = scratch + n;
+    a.lb[1] = scratch + 2 * n;
+    a.flags = flags;
+    a.stats = stats;
+    a.ticket = ticket;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long want = (n + 255) / 256;
+    const int grid = (int)(want < (long long)sms * 8 ? want : (long long)sms * 8);
+    return hp.q == 9 ? ilf2_step<9>(a, hp.maxit, grid, s) : ilf2_step<5>(a, hp.maxit, grid, s);
 }
 
 static size_t ilfbm_smem(int nx) { return (size_t)9 * nx * sizeof(double); }

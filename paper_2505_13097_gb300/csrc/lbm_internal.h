@@ -65,7 +65,7 @@ struct Problem {
     float wall_th_lo[4];
     float wall_slope[4];     // phi'(theta_wall)/Ste = (1 - tanh^2)/(2 delta Ste)
     float wall_dth_max;      // 1e-4 delta: range of the linear phi difference at a Dirichlet node
-    int method;              // 0 IREBM (Algorithm 3), 1 EEBM (Algorithm 2; D2Q9), 2 ILFBM (Algorithm 1; D1Q3)
+    int method;              // 0 IREBM (Algorithm 3), 1 EEBM (Algorithm 2), 2 ILFBM (Algorithm 1; FP64)
     double wall_H[4];        // EEBM: enthalpy of theta_wall, theta_wall + [theta_wall > 0]/Ste
     float wall_H_hi[4], wall_H_lo[4];
     int nseg, nstrip, tile_h;
@@ -174,6 +174,10 @@ bool d1q3_fused_fits(int precision, int nx);
 // ILFBM (Algorithm 1) on D1Q3, FP64, one block over the whole lattice (ilfbm.cu)
 cudaError_t launch_ilfbm_d1q3(const StepArgs& a, const Problem& hp, int nsteps, cudaStream_t s);
 bool ilfbm_d1q3_fits(int nx);
+// one ILFBM step on D2Q9 / D2Q5 (hp.q), FP64: scratch holds 3 nx*ny doubles,
+// flags 5 unsigned ints; publishes the step statistics
+cudaError_t launch_ilfbm_2d(const Problem& hp, const Problem* dprob, int parity, double* scratch,
+                            unsigned int* flags, DevStats* stats, unsigned int* ticket, cudaStream_t s);
 
 // Field and state kernels (fields.cu)
 cudaError_t launch_init_state(int precision, const Problem* dprob, const Problem& hp, const double* theta0,

@@ -73,6 +73,7 @@ struct lbm_stefan {
     int parity = 0;
     bool ic = false;
     int adj_tile_h = lbm::kAdjTileH;   // rows per warp tile of the D2Q9 adjoint
+    unsigned int* dilf = nullptr;      // 2D ILFBM: inner-loop flags (done, iteration, changed x 3)
     bool use_tma = false;              // FP32 D2Q9: the TMA row-pipeline step kernel
     lbm::TmaMaps tma;
     GraphCache graph;
@@ -412,8 +413,36 @@ extern "C" lbm_status lbm_stefan_set_method(lbm_stefan* h, int method)
     if (method != LBM_IREBM && method != LBM_EEBM && method != LBM_ILFBM)
         return fail(LBM_ERR_ARG, "method must be 0 (IREBM), 1 (EEBM) or 2 (ILFBM)");
     // EEBM: D1Q3, D2Q9 and D2Q5 (every closure); the no-allocation step and batches stay IREBM
-    if (method == LBM_ILFBM && (h->p.lattice != LBM_D1Q3 || h->precision != LBM_FP64 || !lbm::ilfbm_d1q3_fits(h->hp.nx)))
-        return fail(LBM_ERR_ARG, "ILFBM is implemented for D1Q3 in FP64 up to 2,844 nodes");
+    if (method == LBM_ILFBM) {
+        if (h->precision != LBM_FP64) return fail(LBM_ERR_ARG, "ILFBM is implemented in FP64");
+        if (h->p.bb_mode == LBM_NEU_EQ17) return fail(LBM_ERR_ARG, "ILFBM uses the bounce-back closures");
+        if (h->p.lattice == LBM_D1Q3 && !lbm::ilfbm_d1q3_fits(h->hp.nx))
+            return fail(LBM_ERR_ARG, "ILFBM on D1Q3 holds the lattice in one block: at most 2,844 nodes");
+        if (h->p.lattice != LBM_D1Q3) {
+            // the liquid fraction needs a plane of its own after the q populations
+            const size_t need = (size_t)(h->hp.q + 1) * h->hp.plane * h->elem;
+            if (h->state_bytes < need) {
+                void* nb[2] = {nullptr, nullptr};
+                cudaError_t e = cudaSuccess;
+                for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+                    e = cudaMalloc(&nb[k], need);
+                    if (e == cudaSuccess) e = cudaMemset(nb[k], 0, need);
+                }
+                if (e != cudaSuccess) {
+                    cudaFree(nb[0]);
+                    cudaFree(nb[1]);
+                    return fail(LBM_ERR_CUDA, "allocation failed: %s", cudaGetErrorString(e));
+                }
+                CUDA_TRY(cudaStreamSynchronize(h->stream));   // no step still reads the old buffers
+                cudaFree(h->hp.state[0]);
+                cudaFree(h->hp.state[1]);
+                h->hp.state[0] = nb[0];
+                h->hp.state[1] = nb[1];
+                h->state_bytes = need;
+            }
+            if (!h->dilf) CUDA_TRY(cudaMalloc(&h->dilf, 8 * sizeof(unsigned int)));
+        }
+    }
     h->hp.method = method;
     h->ic = false;   // the state of one method is not a state of the other
     h->graph.reset();
@@ -463,12 +492,23 @@ extern "C" lbm_status lbm_stefan_step(lbm_stefan* h, int nsteps)
     if (nsteps < 0) return fail(LBM_ERR_ARG, "nsteps must be >= 0");
     if (!h->ic) return fail(LBM_ERR_STATE, "set_ic must come before step");
     if (nsteps == 0) return LBM_OK;
-    if (h->hp.method == LBM_ILFBM) {
+    if (h->hp.method == LBM_ILFBM && h->p.lattice == LBM_D1Q3) {
         // all steps in one launch (one block over the lattice, whose barriers
         // separate the inner iterations)
         StepArgs a = single_args(h, h->parity, nullptr);
         CUDA_TRY(lbm::launch_ilfbm_d1q3(a, h->hp, nsteps, h->stream));
         h->parity ^= nsteps & 1;
+        return LBM_OK;
+    }
+    if (h->hp.method == LBM_ILFBM) {
+        // 2D: one launch per inner iteration (newton_max_iter of them, those
+        // after convergence return at once), framed by the collision and the
+        // final streaming
+        for (int k = 0; k < nsteps; ++k) {
+            CUDA_TRY(lbm::launch_ilfbm_2d(h->hp, h->dprob, h->parity, h->dscratch, h->dilf, h->dstats, h->dticket,
+                                          h->stream));
+            h->parity ^= 1;
+        }
         return LBM_OK;
     }
     if (h->p.lattice == LBM_D1Q3 && lbm::d1q3_fused_fits(h->precision, h->hp.nx)) {
@@ -506,6 +546,7 @@ extern "C" lbm_status lbm_stefan_step_timed(lbm_stefan* h, int nsteps, double* m
 {
     if (!h || !ms_kernels) return fail(LBM_ERR_ARG, "NULL argument");
     if (h->p.lattice == LBM_D1Q3) return fail(LBM_ERR_ARG, "kernel timing covers the D2Q9 and D2Q5 steps");
+    if (h->hp.method == LBM_ILFBM) return fail(LBM_ERR_STATE, "kernel timing covers the IREBM and EEBM steps");
     if (nsteps < 1) return fail(LBM_ERR_ARG, "nsteps must be >= 1");
     if (!h->ic) return fail(LBM_ERR_STATE, "set_ic must come before step_timed");
     std::vector<cudaEvent_t> ev(2 * (size_t)nsteps + 1, nullptr);
@@ -786,6 +827,7 @@ extern "C" void lbm_stefan_destroy(lbm_stefan* h)
     cudaFree(h->dscratch);
     cudaFree(h->djobs);
     cudaFree(h->djob_count);
+    cudaFree(h->dilf);
     delete h;
 }
 

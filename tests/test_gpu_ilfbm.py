@@ -1,5 +1,6 @@
-"""ILFBM (Algorithm 1, the implicit liquid fraction based method) on the GPU,
-D1Q3 in FP64, against the oracle's ILFBM (``oracle.Problem.ilfbm_run``).
+"""ILFBM (Algorithm 1, the implicit liquid fraction based method) on the GPU
+in FP64, D1Q3 and D2Q9 (and D2Q5, whose inner loop does not converge),
+against the oracle's ILFBM (``oracle.Problem.ilfbm_run``).
 
 Parity: theta to 1e-12 relative (FP64), the liquid fraction to 1e-10
 absolute (the lever rule's slope Ste maps theta's rounding into l), or ten
@@ -139,7 +140,6 @@ def test_ilfbm_paper_1d_case(gpu, orc):
 
 def test_ilfbm_argument_errors(gpu):
     cases = [
-        (_abi.LBM_D2Q9, 32, 32, _abi.LBM_FP64),
         (_abi.LBM_D1Q3, 64, 1, _abi.LBM_FP32),
         (_abi.LBM_D1Q3, 2845, 1, _abi.LBM_FP64),
     ]
@@ -160,5 +160,100 @@ def test_ilfbm_argument_errors(gpu):
     a, b = S.new_state_buffer(), S.new_state_buffer()
     with pytest.raises(_abi.LBMError) as e:
         S.adjoint_step(planes[0], planes[1], a, b)
+    assert e.value.status == _abi.LBM_ERR_STATE
+    S.close()
+
+
+# ---------------------------------------------------------------- 2D lattices
+ILF2_CASES = [
+    (40, 30, {"W": (1, 1.0), "E": (0, 0.0)}, 0),
+    (67, 45, {"W": (1, -1.0), "S": (1, -1.0)}, 1),
+    (130, 5, {"W": (1, 0.7), "E": (1, -0.4), "S": (1, 0.2), "N": (1, -0.9)}, 0),
+    (3, 3, {}, 1),
+]
+
+
+@pytest.mark.parametrize("case", range(len(ILF2_CASES)))
+@pytest.mark.parametrize("init", ["uniform", "random"])
+def test_ilfbm_d2q9_parity(gpu, orc, case, init):
+    nx, ny, walls, bb_mode = ILF2_CASES[case]
+    tau, ste, steps, maxit = 0.8, 0.3, 60, 400
+    th0 = (np.full((ny, nx), -0.3) if init == "uniform"
+           else workloads.random_field((ny, nx), -0.5, 0.3, seed=nx * 3 + ny))
+    S = gpu.Stefan(_abi.LBM_D2Q9, nx, ny, tau, 0.01, ste, _abi.LBM_FP64, walls, newton_tol=1e-12,
+                   newton_max_iter=maxit, bb_mode=bb_mode)
+    S.set_method("ILFBM")
+    S.set_ic(th0)
+    S.step(steps)
+    th, l, H = S.fields()
+    st = S.stats()
+    S.close()
+    P = orc.Problem(2, nx, ny, tau=tau, delta=0.01, ste=ste, walls=walls, bb_mode=bb_mode)
+    _, lo, tho, failed, mx = P.ilfbm_run(th0, steps, tol=1e-12, maxit=maxit)
+    fl_t = fl_l = 0.0
+    for seed in (12345, 1, 2):
+        rng = np.random.Generator(np.random.PCG64(seed))
+        pert = th0 + np.spacing(th0) * rng.choice([-1, 0, 1], size=th0.shape)
+        _, lp_, thp, _, _ = P.ilfbm_run(pert, steps, tol=1e-12, maxit=maxit)
+        fl_t = max(fl_t, np.max(np.abs(thp - tho)))
+        fl_l = max(fl_l, np.max(np.abs(lp_ - lo)))
+    assert failed == 0 and st["error"] == 0
+    assert np.max(np.abs(th - tho)) <= max(1e-12 * np.max(np.abs(tho)), 10 * fl_t)
+    assert np.max(np.abs(l - lo)) <= max(1e-10, 10 * fl_l)
+    assert 1 <= st["newton_max_iter"] <= mx
+
+
+def test_ilfbm_d2q9_closed_box_conserves_energy(gpu):
+    nx, ny, ste = 50, 40, 0.5
+    S = gpu.Stefan(_abi.LBM_D2Q9, nx, ny, 0.8, 0.01, ste, _abi.LBM_FP64, {}, newton_tol=1e-13, newton_max_iter=400,
+                   bb_mode=1)
+    S.set_method("ILFBM")
+    S.set_ic(workloads.random_field((ny, nx), -0.6, 0.6, seed=4))
+    e0 = S.stats()["energy"]
+    S.step(40)
+    st = S.stats()
+    assert st["error"] == 0
+    assert abs(st["energy"] - e0) <= 40 * nx * ny * 1e-13 / ste + 1e-11 * abs(e0)
+
+
+def test_ilfbm_d2q5_inner_loop_fails_as_in_the_oracle(gpu, orc):
+    # the D2Q5 cavity: the inner loop reaches its limit in the oracle (the
+    # checkerboard factor of the iteration is 4/3) and the GPU reports it
+    c = workloads.cavity_2d(n=32, steps=20, precision=workloads.FP64)
+    P = orc.Problem(3, c.nx, c.ny, tau=c.tau, delta=c.delta, ste=c.ste, walls=c.walls)
+    *_, failed, _ = P.ilfbm_run(c.theta0(), c.steps, maxit=100)
+    assert failed > 0
+    S = gpu.Stefan(_abi.LBM_D2Q5, c.nx, c.ny, c.tau, c.delta, c.ste, _abi.LBM_FP64, c.walls, newton_max_iter=100)
+    S.set_method("ILFBM")
+    S.set_ic(c.theta0())
+    S.step(c.steps)
+    with pytest.raises(_abi.LBMError) as e:
+        S.sync()
+    assert e.value.status == _abi.LBM_ERR_NEWTON
+    S.close()
+
+
+def test_ilfbm_2d_argument_errors(gpu):
+    S = gpu.Stefan(_abi.LBM_D2Q9, 32, 32, 0.8, 0.01, 0.1, _abi.LBM_FP32, {})
+    with pytest.raises(_abi.LBMError) as e:
+        S.set_method("ILFBM")
+    assert e.value.status == _abi.LBM_ERR_ARG
+    S.close()
+    S = gpu.Stefan(_abi.LBM_D2Q5, 32, 32, 0.8, 0.01, 0.1, _abi.LBM_FP64, {}, bb_mode=2)
+    with pytest.raises(_abi.LBMError) as e:
+        S.set_method("ILFBM")
+    assert e.value.status == _abi.LBM_ERR_ARG
+    S.close()
+    # the state grows by the liquid-fraction plane
+    S = gpu.Stefan(_abi.LBM_D2Q9, 32, 32, 0.8, 0.01, 0.1, _abi.LBM_FP64, {})
+    b0 = S.state_bytes
+    S.set_method("ILFBM")
+    import ctypes
+    sb, rs = ctypes.c_size_t(), ctypes.c_int()
+    _abi.check(S.lib.lbm_stefan_layout(S.h, ctypes.byref(sb), ctypes.byref(rs)))
+    assert sb.value == b0 // 9 * 10
+    S.set_ic(np.full((32, 32), -0.2))
+    with pytest.raises(_abi.LBMError) as e:
+        S.step_timed(2)
     assert e.value.status == _abi.LBM_ERR_STATE
     S.close()
