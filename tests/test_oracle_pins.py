@@ -789,3 +789,58 @@ def test_paper_1d_case_printed_error_comparison_schemes(orc, method):
     assert min(errs) <= ref <= max(errs), (min(errs), max(errs))
     # and the band is that of a staircase front, not of a wrong scheme
     assert max(errs) < 3 * ref and min(errs) > ref / 3
+
+
+# ---------------------------------------------------------------- tau = 1 closed forms of the comparison schemes
+def _shift(a, ex, ey):
+    """a(y - e) on the interior: value at (x - ex, y - ey)."""
+    return np.roll(np.roll(a, ey, axis=0), ex, axis=1)
+
+
+_VEL = {1: [(0, 0), (1, 0), (-1, 0)], 3: [(0, 0), (1, 0), (0, 1), (-1, 0), (0, -1)],
+        2: [(0, 0), (1, 0), (0, 1), (-1, 0), (0, -1), (1, 1), (-1, 1), (-1, -1), (1, -1)]}
+_W = {1: [2 / 3, 1 / 6, 1 / 6], 3: [1 / 3] + [1 / 6] * 4, 2: [4 / 9] + [1 / 9] * 4 + [1 / 36] * 4}
+
+
+@pytest.mark.parametrize("lattice,shape", [(1, (1, 30)), (3, (9, 11)), (2, (9, 11))])
+def test_eebm_tau1_is_explicit_enthalpy_update(orc, lattice, shape):
+    # Algorithm 2 at tau = 1 from an equilibrium state: H(t+1, y) = H(y) +
+    # sum_{i != 0} w_i (Theta(H)(y - e_i) - Theta(H)(y)), the explicit enthalpy
+    # scheme on the lattice's stencil (interior nodes: walls act one node deep)
+    from oracle import eebm_theta
+    ny, nx = shape
+    ste = 0.4
+    P = orc.Problem(lattice, nx, ny, tau=1.0, delta=0.01, ste=ste)
+    th0 = workloads.random_field(shape, -0.6, 0.6, seed=61)
+    f0 = P.eebm_init(th0)
+    H0 = P.eebm_fields(f0)[1]
+    T0 = np.vectorize(lambda h: eebm_theta(h, ste))(H0)
+    H1 = P.eebm_fields(P.eebm_step(f0))[1]
+    ref = H0.copy()
+    for (ex, ey), w in zip(_VEL[lattice][1:], _W[lattice][1:]):
+        ref += w * (_shift(T0, ex, ey) - T0)
+    sl = (slice(1, -1) if ny > 1 else slice(None), slice(1, -1))
+    assert np.max(np.abs(H1[sl] - ref[sl])) <= 1e-14
+
+
+@pytest.mark.parametrize("lattice,shape", [(1, (1, 40)), (2, (10, 12))])
+def test_ilfbm_tau1_source_streams_from_the_upstream_node(orc, lattice, shape):
+    # Algorithm 1 at tau = 1: Omega_i = w_i theta + (w_i/Ste)(l - l^(k-1)), so a
+    # converged step gives theta~(y) = sum_i w_i [theta + (l - l~)/Ste](y - e_i)
+    # to the loop's tolerance (the source is added at the node it streams from)
+    ny, nx = shape
+    ste, tol = 0.3, 1e-13
+    P = orc.Problem(lattice, nx, ny, tau=1.0, delta=0.01, ste=ste)
+    f, ell = P.ilfbm_init(workloads.random_field(shape, -0.4, 0.4, seed=62))
+    for _ in range(5):
+        f, ell, _, ok, _ = P.ilfbm_step(f, ell, tol=tol)
+        assert ok
+    th = f.sum(axis=0)
+    fn, ln, it, ok, _ = P.ilfbm_step(f, ell, tol=tol)
+    assert ok and it > 1
+    thn = fn.sum(axis=0)
+    ref = np.zeros_like(th)
+    for (ex, ey), w in zip(_VEL[lattice], _W[lattice]):
+        ref += w * _shift(th + (ell - ln) / ste, ex, ey)
+    sl = (slice(1, -1) if ny > 1 else slice(None), slice(1, -1))
+    assert np.max(np.abs(thn[sl] - ref[sl])) <= 2 * tol / ste + 1e-14
