@@ -220,12 +220,14 @@ __global__ void __launch_bounds__(kIlfThreads) ilfbm_d1q3_kernel(StepArgs a, int
 //   ilf2_final     f~_i(y) = Omega_i(y - e_i) with the source of l^(K-1) and
 //                  the closures, l~ = l^(K); energy sum theta~ + l~/Ste, flux,
 //                  iteration count, the iteration-limit error; publishes
-// Scratch (nx*ny doubles each, in the handle's field scratch): S0, l^(k) x 2.
+// Scratch (nx*ny doubles each): S0, l^(k) x 2, l - l^(k) x 2 (the interior
+// stencil reads the differences, so an iteration spends one FMA per velocity).
 struct Ilf2Args {
     const Problem* prob;
     int parity;              // state[parity] holds f, then Omega0; f~ goes to state[parity ^ 1]
     double* s0;
     double* lb[2];           // l^(k-1) / l^(k) of iteration k: lb[(k-1) & 1] / lb[k & 1]
+    double* dl[2];           // l - l^(k-1) / l - l^(k), written beside lb: the stencil's input
     unsigned int* flags;     // [0] done, [1] converged iteration, [2..4] changed per iteration mod 3
     DevStats* stats;
     unsigned int* ticket;
@@ -321,6 +323,7 @@ __global__ void __launch_bounds__(256) ilf2_collide(Ilf2Args a)
 #pragma unroll
         for (int i = 0; i < Q; ++i) st[i * pb.plane + at] = f[i] - (f[i] - lat_w(Q, i) * th) * pb.omega;
         a.lb[0][k] = st[Q * pb.plane + at];
+        a.dl[0][k] = 0.0;   // l - l^(0)
     }
 }
 
@@ -359,7 +362,9 @@ __global__ void __launch_bounds__(256) ilf2_iter(Ilf2Args a, int k)
     const double* st = static_cast<const double*>(pb.state[a.parity]);
     const double* lq = st + Q * pb.plane;
     const double* lp = a.lb[(k - 1) & 1];
+    const double* dp = a.dl[(k - 1) & 1];
     double* ln = a.lb[k & 1];
+    double* dn = a.dl[k & 1];
     const long long n = (long long)pb.nx * pb.ny;
     bool more = false;
     for (long long nd = blockIdx.x * (long long)blockDim.x + threadIdx.x; nd < n; nd += (long long)gridDim.x * blockDim.x) {
@@ -374,9 +379,8 @@ __global__ void __launch_bounds__(256) ilf2_iter(Ilf2Args a, int k)
                 H = a.s0[nd];
 #pragma unroll
                 for (int i = 0; i < Q; ++i) {
-                    const int sx = x - d2_ex(i), sy = y - d2_ey(i);
-                    const long long sn = (long long)sy * pb.nx + sx;
-                    H += lat_w(Q, i) * pb.inv_ste * (lq[(long long)(sy + 1) * pb.pitch + sx] - lp[sn]);
+                    const long long sn = (long long)(y - d2_ey(i)) * pb.nx + x - d2_ex(i);
+                    H += lat_w(Q, i) * pb.inv_ste * dp[sn];
                 }
             } else {
                 double q[Q];
@@ -390,6 +394,7 @@ __global__ void __launch_bounds__(256) ilf2_iter(Ilf2Args a, int k)
         }
         more |= fabs(lk - lp[nd]) > pb.tol;
         ln[nd] = lk;
+        dn[nd] = lq[(long long)(y + 1) * pb.pitch + x] - lk;
     }
     if (__any_sync(kFull, more) && (threadIdx.x & 31) == 0) fl[2 + k % 3] = 1u;
 }
@@ -456,6 +461,8 @@ cudaError_t launch_ilfbm_2d(const Problem& hp, const Problem* dprob, int parity,
     a.s0 = scratch;
     a.lb[0] = scratch + n;
     a.lb[1] = scratch + 2 * n;
+    a.dl[0] = scratch + 3 * n;
+    a.dl[1] = scratch + 4 * n;
     a.flags = flags;
     a.stats = stats;
     a.ticket = ticket;

@@ -174,7 +174,7 @@ bool d1q3_fused_fits(int precision, int nx);
 // ILFBM (Algorithm 1) on D1Q3, FP64, one block over the whole lattice (ilfbm.cu)
 cudaError_t launch_ilfbm_d1q3(const StepArgs& a, const Problem& hp, int nsteps, cudaStream_t s);
 bool ilfbm_d1q3_fits(int nx);
-// one ILFBM step on D2Q9 / D2Q5 (hp.q), FP64: scratch holds 3 nx*ny doubles,
+// one ILFBM step on D2Q9 / D2Q5 (hp.q), FP64: scratch holds 5 nx*ny doubles,
 // flags 5 unsigned ints; publishes the step statistics
 cudaError_t launch_ilfbm_2d(const Problem& hp, const Problem* dprob, int parity, double* scratch,
                             unsigned int* flags, DevStats* stats, unsigned int* ticket, cudaStream_t s);

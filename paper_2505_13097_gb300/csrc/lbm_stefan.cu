@@ -74,6 +74,7 @@ struct lbm_stefan {
     bool ic = false;
     int adj_tile_h = lbm::kAdjTileH;   // rows per warp tile of the D2Q9 adjoint
     unsigned int* dilf = nullptr;      // 2D ILFBM: inner-loop flags (done, iteration, changed x 3)
+    double* dilf_scratch = nullptr;    // 2D ILFBM: S0, two l iterates, two l differences (5 nx*ny)
     bool use_tma = false;              // FP32 D2Q9: the TMA row-pipeline step kernel
     lbm::TmaMaps tma;
     GraphCache graph;
@@ -441,6 +442,8 @@ extern "C" lbm_status lbm_stefan_set_method(lbm_stefan* h, int method)
                 h->state_bytes = need;
             }
             if (!h->dilf) CUDA_TRY(cudaMalloc(&h->dilf, 8 * sizeof(unsigned int)));
+            if (!h->dilf_scratch)
+                CUDA_TRY(cudaMalloc(&h->dilf_scratch, 5 * sizeof(double) * (size_t)h->hp.nx * h->hp.ny));
         }
     }
     h->hp.method = method;
@@ -505,8 +508,8 @@ extern "C" lbm_status lbm_stefan_step(lbm_stefan* h, int nsteps)
         // after convergence return at once), framed by the collision and the
         // final streaming
         for (int k = 0; k < nsteps; ++k) {
-            CUDA_TRY(lbm::launch_ilfbm_2d(h->hp, h->dprob, h->parity, h->dscratch, h->dilf, h->dstats, h->dticket,
-                                          h->stream));
+            CUDA_TRY(lbm::launch_ilfbm_2d(h->hp, h->dprob, h->parity, h->dilf_scratch, h->dilf, h->dstats,
+                                          h->dticket, h->stream));
             h->parity ^= 1;
         }
         return LBM_OK;
@@ -828,6 +831,7 @@ extern "C" void lbm_stefan_destroy(lbm_stefan* h)
     cudaFree(h->djobs);
     cudaFree(h->djob_count);
     cudaFree(h->dilf);
+    cudaFree(h->dilf_scratch);
     delete h;
 }
 
