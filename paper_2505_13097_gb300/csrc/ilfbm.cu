@@ -222,6 +222,8 @@ __global__ void __launch_bounds__(kIlfThreads) ilfbm_d1q3_kernel(StepArgs a, int
 //                  iteration count, the iteration-limit error; publishes
 // Scratch (nx*ny doubles each): S0, l^(k) x 2, l - l^(k) x 2 (the interior
 // stencil reads the differences, so an iteration spends one FMA per velocity).
+// Node indices stay below 2^31 (the library's size limit), so the column and
+// row come from a 32-bit division.
 struct Ilf2Args {
     const Problem* prob;
     int parity;              // state[parity] holds f, then Omega0; f~ goes to state[parity ^ 1]
@@ -312,7 +314,7 @@ __global__ void __launch_bounds__(256) ilf2_collide(Ilf2Args a)
     const long long n = (long long)pb.nx * pb.ny;
     if (blockIdx.x == 0 && threadIdx.x < 5) a.flags[threadIdx.x] = 0u;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(k % pb.nx), y = (int)(k / pb.nx);
+        const int x = (int)((unsigned)k % (unsigned)pb.nx), y = (int)((unsigned)k / (unsigned)pb.nx);
         const long long at = (long long)(y + 1) * pb.pitch + x;
         double f[Q], th = 0.0;
 #pragma unroll
@@ -334,7 +336,7 @@ __global__ void __launch_bounds__(256) ilf2_s0(Ilf2Args a)
     const double* st = static_cast<const double*>(pb.state[a.parity]);
     const long long n = (long long)pb.nx * pb.ny;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(k % pb.nx), y = (int)(k / pb.nx);
+        const int x = (int)((unsigned)k % (unsigned)pb.nx), y = (int)((unsigned)k / (unsigned)pb.nx);
         if (x == 0 || x == pb.nx - 1 || y == 0 || y == pb.ny - 1) continue;
         double s = 0.0;
 #pragma unroll
@@ -368,7 +370,7 @@ __global__ void __launch_bounds__(256) ilf2_iter(Ilf2Args a, int k)
     const long long n = (long long)pb.nx * pb.ny;
     bool more = false;
     for (long long nd = blockIdx.x * (long long)blockDim.x + threadIdx.x; nd < n; nd += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(nd % pb.nx), y = (int)(nd / pb.nx);
+        const int x = (int)((unsigned)nd % (unsigned)pb.nx), y = (int)((unsigned)nd / (unsigned)pb.nx);
         const int wk = ilf2_dirichlet(pb, x, y);
         double lk;
         if (wk >= 0) {
@@ -415,7 +417,7 @@ __global__ void __launch_bounds__(256) ilf2_final(Ilf2Args a, int maxit)
     const long long n = (long long)pb.nx * pb.ny;
     double e = 0.0, fx = 0.0;
     for (long long nd = blockIdx.x * (long long)blockDim.x + threadIdx.x; nd < n; nd += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(nd % pb.nx), y = (int)(nd / pb.nx);
+        const int x = (int)((unsigned)nd % (unsigned)pb.nx), y = (int)((unsigned)nd / (unsigned)pb.nx);
         double q[Q];
         fx += ilf2_streamed<Q>(pb, st, lp, x, y, q, true);
         const long long at = (long long)(y + 1) * pb.pitch + x;
