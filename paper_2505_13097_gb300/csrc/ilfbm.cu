@@ -225,7 +225,8 @@ __global__ void __launch_bounds__(kIlfThreads) ilfbm_d1q3_kernel(StepArgs a, int
 // Node indices stay below 2^31 (the library's size limit), so the column and
 // row come from a 32-bit division.
 struct Ilf2Args {
-    const Problem* prob;
+    Problem pb;              // by value: the kernels read it from the parameter bank,
+                             // so no store of theirs can alias it
     int parity;              // state[parity] holds f, then Omega0; f~ goes to state[parity ^ 1]
     double* s0;
     double* lb[2];           // l^(k-1) / l^(k) of iteration k: lb[(k-1) & 1] / lb[k & 1]
@@ -309,7 +310,7 @@ __device__ __forceinline__ double ilf2_streamed(const Problem& pb, const double*
 template <int Q>
 __global__ void __launch_bounds__(256) ilf2_collide(Ilf2Args a)
 {
-    const Problem& pb = *a.prob;
+    const Problem& pb = a.pb;
     double* st = static_cast<double*>(pb.state[a.parity]);
     const long long n = (long long)pb.nx * pb.ny;
     if (blockIdx.x == 0 && threadIdx.x < 5) a.flags[threadIdx.x] = 0u;
@@ -332,7 +333,7 @@ __global__ void __launch_bounds__(256) ilf2_collide(Ilf2Args a)
 template <int Q>
 __global__ void __launch_bounds__(256) ilf2_s0(Ilf2Args a)
 {
-    const Problem& pb = *a.prob;
+    const Problem& pb = a.pb;
     const double* st = static_cast<const double*>(pb.state[a.parity]);
     const long long n = (long long)pb.nx * pb.ny;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
@@ -360,7 +361,7 @@ __global__ void __launch_bounds__(256) ilf2_iter(Ilf2Args a, int k)
         return;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) fl[2 + (k + 1) % 3] = 0u;
-    const Problem& pb = *a.prob;
+    const Problem& pb = a.pb;
     const double* st = static_cast<const double*>(pb.state[a.parity]);
     const double* lq = st + Q * pb.plane;
     const double* lp = a.lb[(k - 1) & 1];
@@ -404,7 +405,7 @@ __global__ void __launch_bounds__(256) ilf2_iter(Ilf2Args a, int k)
 template <int Q>
 __global__ void __launch_bounds__(256) ilf2_final(Ilf2Args a, int maxit)
 {
-    const Problem& pb = *a.prob;
+    const Problem& pb = a.pb;
     const volatile unsigned int* fl = a.flags;
     const bool done = fl[0] != 0u;
     const int K = done ? (int)fl[1] : maxit;
@@ -453,11 +454,11 @@ static cudaError_t ilf2_step(const Ilf2Args& a, int maxit, int grid, cudaStream_
     return cudaGetLastError();
 }
 
-cudaError_t launch_ilfbm_2d(const Problem& hp, const Problem* dprob, int parity, double* scratch,
+cudaError_t launch_ilfbm_2d(const Problem& hp, int parity, double* scratch,
                             unsigned int* flags, DevStats* stats, unsigned int* ticket, cudaStream_t s)
 {
     Ilf2Args a;
-    a.prob = dprob;
+    a.pb = hp;
     a.parity = parity;
     const long long n = (long long)hp.nx * hp.ny;
     a.s0 = scratch;

@@ -175,8 +175,8 @@ bool d1q3_fused_fits(int precision, int nx);
 cudaError_t launch_ilfbm_d1q3(const StepArgs& a, const Problem& hp, int nsteps, cudaStream_t s);
 bool ilfbm_d1q3_fits(int nx);
 // one ILFBM step on D2Q9 / D2Q5 (hp.q), FP64: scratch holds 5 nx*ny doubles,
-// flags 5 unsigned ints; publishes the step statistics
-cudaError_t launch_ilfbm_2d(const Problem& hp, const Problem* dprob, int parity, double* scratch,
+// flags 5 unsigned ints; publishes the step statistics (hp: the host copy, passed by value)
+cudaError_t launch_ilfbm_2d(const Problem& hp, int parity, double* scratch,
                             unsigned int* flags, DevStats* stats, unsigned int* ticket, cudaStream_t s);
 
 // Field and state kernels (fields.cu)

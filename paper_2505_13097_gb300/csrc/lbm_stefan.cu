@@ -508,8 +508,8 @@ extern "C" lbm_status lbm_stefan_step(lbm_stefan* h, int nsteps)
         // after convergence return at once), framed by the collision and the
         // final streaming
         for (int k = 0; k < nsteps; ++k) {
-            CUDA_TRY(lbm::launch_ilfbm_2d(h->hp, h->dprob, h->parity, h->dilf_scratch, h->dilf, h->dstats,
-                                          h->dticket, h->stream));
+            CUDA_TRY(lbm::launch_ilfbm_2d(h->hp, h->parity, h->dilf_scratch, h->dilf, h->dstats, h->dticket,
+                                          h->stream));
             h->parity ^= 1;
         }
         return LBM_OK;
