@@ -18,7 +18,8 @@ LBM_FP64, LBM_FP32 = 0, 1
 LBM_ADIABATIC, LBM_DIRICHLET = 0, 1
 LBM_BB_MIRROR, LBM_BB_LINK, LBM_NEU_EQ17 = 0, 1, 2
 LBM_IREBM, LBM_EEBM, LBM_ILFBM = 0, 1, 2
-WALLS = {"W": 0, "E": 1, "S": 2, "N": 3}
+LBM_WALL_W, LBM_WALL_E, LBM_WALL_S, LBM_WALL_N = 0, 1, 2, 3
+WALLS = {"W": LBM_WALL_W, "E": LBM_WALL_E, "S": LBM_WALL_S, "N": LBM_WALL_N}
 
 
 class lbm_stefan_params(ctypes.Structure):

@@ -78,3 +78,22 @@ def test_null_handles_are_rejected(lib):
     assert lib.lbm_stefan_batch_create(0, None, 1, 1e-14, 60, None, None) == _abi.LBM_ERR_ARG
     lib.lbm_stefan_destroy(None)
     lib.lbm_stefan_batch_destroy(None)
+
+
+def test_binding_constants_match_the_header():
+    # every enum constant of include/*.h has the same value in the Python binding
+    import sys
+    sys.path.insert(0, ROOT)
+    from paper_2505_13097_gb300 import _abi
+    consts = {}
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for body in re.findall(r"enum\s*\{([^}]*)\}", src):
+            for m in re.finditer(r"(LBM_[A-Z0-9_]+)\s*=\s*(\d+)", body):
+                consts[m.group(1)] = int(m.group(2))
+        for body in re.findall(r"typedef\s+enum\s*\{([^}]*)\}", src):
+            for m in re.finditer(r"(LBM_[A-Z0-9_]+)\s*=\s*(\d+)", body):
+                consts[m.group(1)] = int(m.group(2))
+    assert {"LBM_D2Q5", "LBM_NEU_EQ17", "LBM_ILFBM", "LBM_ERR_NEWTON"} <= set(consts)
+    for name, v in consts.items():
+        assert getattr(_abi, name) == v, name
