@@ -328,22 +328,28 @@ def bench_bar_1d(torch, solver, workloads, stream, steps=20000):
     5.586 s, ILFBM 22.01 s)."""
     c = workloads.bar_1d()
     out = {"workload": c.name, "steps_timed": steps}
+    from paper_2505_13097_gb300 import _abi
     for method in ("IREBM", "EEBM", "ILFBM"):
         # ILFBM: the inner loop's tolerance on l and its iteration limit
         kw = dict(newton_tol=1e-12, newton_max_iter=200) if method == "ILFBM" else {}
         S = solver.Stefan.from_case(c, stream=stream, **kw)
-        S.set_method(method)
-        S.set_ic(c.theta0())
-        S.step(200)
-        S.sync()
-        ms = time_steps(torch, S, steps, stream)
-        st = S.stats()
-        S.sync()
-        S.close()
-        out[method.lower()] = {"steps_per_s": steps / ms * 1e3, "full_run_s": c.steps * ms / steps / 1e3,
-                               "iterations_last_step": st["newton_max_iter"]}
-    out["ilfbm_over_irebm"] = out["ilfbm"]["full_run_s"] / out["irebm"]["full_run_s"]
-    out["irebm_over_eebm"] = out["irebm"]["full_run_s"] / out["eebm"]["full_run_s"]
+        try:
+            S.set_method(method)
+            S.set_ic(c.theta0())
+            S.step(200)
+            S.sync()
+            ms = time_steps(torch, S, steps, stream)
+            st = S.stats()
+            S.sync()
+            out[method.lower()] = {"steps_per_s": steps / ms * 1e3, "full_run_s": c.steps * ms / steps / 1e3,
+                                   "iterations_last_step": st["newton_max_iter"]}
+        except _abi.LBMError as e:   # reported, not fatal
+            out[method.lower()] = {"error": str(e)}
+        finally:
+            S.close()
+    if all("full_run_s" in out[m] for m in ("irebm", "eebm", "ilfbm")):
+        out["ilfbm_over_irebm"] = out["ilfbm"]["full_run_s"] / out["irebm"]["full_run_s"]
+        out["irebm_over_eebm"] = out["irebm"]["full_run_s"] / out["eebm"]["full_run_s"]
     return out
 
 
