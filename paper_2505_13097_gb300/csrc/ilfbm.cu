@@ -2,8 +2,8 @@
 // Sec. 3.3), the paper's second comparison scheme, in FP64: D1Q3 in one
 // block (below), D2Q9 and D2Q5 with one launch per inner iteration (at the end).
 //
-// State: f_i (planes 0..2, theta = M0(f)) and the liquid fraction l (plane 3
-// of the same buffer).  One step:
+// State: f_i (planes 0..q-1, theta = M0(f)) and the liquid fraction l (plane
+// q of the same buffer).  One step:
 //   theta = M0(f); l^(0) = l; for k = 1, 2, ...:
 //     Omega_i = f_i - (f_i - w_i theta)/tau + (w_i/Ste)(l - l^(k-1))
 //     f^(k)_i(y) = Omega_i(y - e_i), closures on the unknown one at a wall
@@ -16,7 +16,7 @@
 //
 // Every inner iteration streams the whole lattice, and the loop's test is a
 // maximum over the lattice, so the iterations of a step are separated by
-// lattice-wide barriers.  A 1D lattice of the paper's sizes (N <= 1601) fits
+// lattice-wide barriers.  D1Q3: a lattice of the paper's sizes (N <= 1601) fits
 // in one thread block's shared memory (72 bytes per node): one block runs
 // all steps of a call, its barriers are __syncthreads, and HBM is touched
 // only at the start and the end of the call.  The inner loop is bound by the
