@@ -524,7 +524,7 @@ def run_gpu(args):
                          # kernel, loads and stores unchanged) after the last DRAM counters were taken
                          "traffic": None,
                          "traffic_note": "last ncu capture of d2q9_tma_kernel (2048^2 melting workload, before the "
-                                         "refactor of its helpers): 282.4 MB per launch, 93.5 % of its algorithmic "
+                                         "refactor of its helpers): 282.4 MB per launch, 93.5 %% of its algorithmic "
                                          "bytes; scaled to this launch's node count: %.3g bytes"
                                          % (282437376 / (2048 * 2048) * nodes),
                          "bytes_per_node": BYTES_FP32, "units_per_launch": nodes,
