@@ -520,13 +520,12 @@ def run_gpu(args):
                          # dram__bytes_read.sum + dram__bytes_write.sum of one launch of this kernel in an
                          # ncu capture of the 2048^2 workload (282.4 MB for 4.19 M nodes), scaled by the
                          # node count of the launch (traffic grows with the nodes streamed)
-                         # null: the kernel's source was refactored (closure helpers shared with the D2Q5
-                         # kernel, loads and stores unchanged) after the last DRAM counters were taken
-                         "traffic": None,
-                         "traffic_note": "last ncu capture of d2q9_tma_kernel (2048^2 melting workload, before the "
-                                         "refactor of its helpers): 282.4 MB per launch, 93.5 %% of its algorithmic "
-                                         "bytes; scaled to this launch's node count: %.3g bytes"
-                                         % (282437376 / (2048 * 2048) * nodes),
+                         # dram__bytes_read.sum + dram__bytes_write.sum of one launch of this kernel in an
+                         # ncu capture of the 2048^2 workload (164.6 + 118.5 MB for 4.19 M nodes), scaled by
+                         # the node count of the launch (traffic grows with the nodes streamed)
+                         "traffic": 283079936 / (2048 * 2048) * nodes,
+                         "traffic_note": "ncu capture of d2q9_tma_kernel on the 2048^2 melting workload (93.7 percent "
+                                         "of its algorithmic bytes), scaled to this launch's node count",
                          "bytes_per_node": BYTES_FP32, "units_per_launch": nodes,
                          "kernel": "d2q9_tma_kernel<false>", "kernel_ms": k_step_ms,
                          "job_kernel": "newton_jobs_kernel<float,false>", "job_kernel_ms": k_job_ms,
