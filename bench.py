@@ -9,9 +9,12 @@ has its average width.  The state (1.2 GB) is larger than L2 (129 MB), so
 every step reads and writes HBM; no flush is needed.
 
 Also reported: the FP64 form on the same workload, the 2048^2 FP64 corner
-workload for Ste in {0.01, 0.1, 1}, 256 batched problems in one persistent
-graph-captured launch per step, the adjoint/forward time ratio on 1024^2 with
-sqrt(T) checkpointing, and the 512-node D1Q3 workload (fused steps).
+workload for Ste in {0.01, 0.1, 1}, EEBM (Algorithm 2) on the same window, 256
+batched problems in one persistent graph-captured launch per step, the
+adjoint/forward time ratio on 1024^2 with sqrt(T) checkpointing, the 512-node
+D1Q3 workload (fused steps), the paper's 2D cavity on D2Q5 (4096^2, Eq. 17
+closure; IREBM FP32 and FP64, EEBM), the paper's 1D bar (N = 801) and its 2D
+cavity on D2Q9 (N = 801, FP64) with the three schemes (IREBM, EEBM, ILFBM).
 
 --impl reference times the FP64 CPU oracle (the reference of this build) on
 a bounded sample of the same workload.
