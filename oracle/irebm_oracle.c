@@ -16,12 +16,17 @@
  *   (15) Dirichlet       closure on M0(q) at a Dirichlet node
  *   (16) Dir_on_q        single-unknown form of (15) (D1Q3, D2Q5)
  *   (17) Neu_on_q        Neumann closure through the inner neighbour's M0(q) (D2Q5)
- * Algorithm 3 (IREBM step) fixes the order of the step.  Sec. 4.2.2 gives the
- * bounce-back closure q_ix = q_{bar ix}.
+ * One step, as the paper states the method (Sec. 4, Algorithm 3), written here
+ * from the equations: theta = M0(f); the collision of Eq. (12); pull
+ * streaming of Omega into q; the closures of Sec. 4.2 on the q that streaming
+ * leaves undefined (Eqs. 15-17, and the bounce-back q_ix = q_{bar ix} of
+ * Sec. 4.2.2); the local nonlinear equation (14) for theta~, solved by
+ * Newton's method from theta; the source and update of Eq. (13).  Each of
+ * these is one pass over the lattice, in that order.
  *
  * Storage: the oracle stores the distributions f_i (q planes of nx*ny doubles,
- * x fastest) and recomputes theta = M0(f) at the start of every step, exactly
- * as Algorithm 3 does.  No blocking, fusion or reordering.
+ * x fastest) and recomputes theta = M0(f) at the start of every step.  No
+ * blocking, fusion or reordering of those passes.
  *
  * Readings where the paper is silent:
  *  - weights: D1Q3 (2/3, 1/6, 1/6), D2Q5 (1/3, 1/6 x4), D2Q9 (4/9, 1/9 x4,
