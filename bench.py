@@ -40,6 +40,10 @@ BYTES_FP32 = 9 * 4 * 2   # algorithmic bytes per node update: each population re
 BYTES_FP64 = 9 * 8 * 2
 BYTES_D2Q5_FP32 = 5 * 4 * 2   # D2Q5: five populations
 BYTES_D2Q5_FP64 = 5 * 8 * 2
+# DRAM bytes (read + write) per node of one launch of the fused FP32 D2Q9 kernel,
+# from an ncu capture (None until the current kernel has been captured)
+FUSED_TRAFFIC_PER_NODE = None
+FUSED_TRAFFIC_NOTE = "not captured for the current kernel yet"
 
 
 def log(*a):
@@ -209,27 +213,33 @@ def bench_d2q5(torch, solver, workloads, steps, warmup, stream, peak, n=4096, fp
     return out
 
 
-def bench_e2e(torch, solver, case, steps, stream):
-    """Through the public C ABI with host buffers: set_ic (pinned host -> device),
-    `steps` steps, get_fields (device -> pinned host), all inside the timed region."""
+def bench_e2e(torch, solver, case, steps, stream, centre=None):
+    """Through the public C ABI with host buffers, on the headline's window:
+    the state at the window's start is saved to pinned host memory (untimed);
+    the timed region then loads it (lbm_stefan_set_state, host -> device),
+    runs `steps` steps and reads theta back (lbm_stefan_get_fields, device ->
+    pinned host)."""
+    import ctypes
+    from paper_2505_13097_gb300 import _abi
     n = case.nx * case.ny
-    th0 = torch.empty((case.ny, case.nx), dtype=torch.float64, pin_memory=True)
-    th0.copy_(torch.from_numpy(case.theta0()))
     out = torch.empty((case.ny, case.nx), dtype=torch.float64, pin_memory=True)
     S = solver.Stefan.from_case(case, stream=stream)
-    S.set_ic(th0.numpy())
+    S.set_ic(case.theta0())
+    S.step(melt_window(case, steps, 0, centre))
+    host_state = torch.empty(S.state_bytes, dtype=torch.uint8, pin_memory=True)
+    S.get_state(host_state.numpy())
+    S.set_state(host_state.numpy())
     S.step(3)
     S.sync()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    S.set_ic(th0.numpy())
+    S.set_state(host_state.numpy())
     S.step(steps)
-    import ctypes
-    from paper_2505_13097_gb300 import _abi
     _abi.check(S.lib.lbm_stefan_get_fields(S.h, ctypes.c_void_p(out.data_ptr()), None, None, 0))
     t1 = time.perf_counter()
+    nbytes = S.state_bytes
     S.close()
-    return (t1 - t0) * 1e3, 8 * n, 8 * n
+    return (t1 - t0) * 1e3, nbytes, 8 * n
 
 
 def bench_batch(torch, solver, workloads, steps, warmup, stream):
@@ -255,11 +265,17 @@ def bench_batch(torch, solver, workloads, steps, warmup, stream):
             "tile_h": tile_h, "error": err, "window_start_step": pre + warmup}
 
 
-def bench_adjoint(torch, solver, workloads, stream):
-    """1024^2, 2,000 steps, FP32 forward with FP64 Newton, sqrt(T) checkpoints."""
-    from paper_2505_13097_gb300.autograd import misfit
-    import numpy as np
-    base = workloads.adjoint_2d()
+def bench_adjoint(torch, solver, workloads, stream, n=1024, repeats=3):
+    """n^2, 2,000 steps, FP32 forward with FP64 Newton, sqrt(T) checkpoints.
+    One untimed forward + backward first creates the run's handle, checkpoint
+    buffers and CUDA graphs; then `repeats` forward and backward passes are
+    timed (wall clock between device synchronizations) and their medians
+    reported, with the spread (max - min) / median of each.  The forward pass
+    is also compared with T times the steady per-step time of the same step
+    (CUDA events, 200 steps mid-run), and one adjoint step with one forward
+    step (the kernels alone)."""
+    from paper_2505_13097_gb300.autograd import clear_pool, misfit
+    base = workloads.adjoint_2d(n=n)
     tcase = workloads.adjoint_target_case(base)
     T = base.steps
     with torch.cuda.stream(stream):
@@ -268,10 +284,13 @@ def bench_adjoint(torch, solver, workloads, stream):
         St.step(T)
         _, ph, _ = St.fields(device=True)
         St.close()
-        th0 = torch.tensor(base.theta0(), device="cuda", requires_grad=True)
-        tw = torch.tensor([base.walls["W"][1], 0.0, 0.0, 0.0], dtype=torch.float64, device="cuda",
-                          requires_grad=True)
-        ste = torch.tensor(base.ste, dtype=torch.float64, device="cuda", requires_grad=True)
+    torch.cuda.synchronize()
+    th0 = torch.tensor(base.theta0(), device="cuda", requires_grad=True)
+    tw = torch.tensor([base.walls["W"][1], 0.0, 0.0, 0.0], dtype=torch.float64, device="cuda", requires_grad=True)
+    ste = torch.tensor(base.ste, dtype=torch.float64, device="cuda", requires_grad=True)
+
+    def once():
+        th0.grad = tw.grad = ste.grad = None
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         L = misfit(th0, tw, ste, base, T, ph)
@@ -280,10 +299,21 @@ def bench_adjoint(torch, solver, workloads, stream):
         L.backward()
         torch.cuda.synchronize()
         t2 = time.perf_counter()
-    # kernel-only: one forward step vs one adjoint step
+        return (t1 - t0) * 1e3, (t2 - t1) * 1e3, float(L.detach())
+
+    once()
+    runs = [once() for _ in range(repeats)]
+    fwd = statistics.median(r[0] for r in runs)
+    bwd = statistics.median(r[1] for r in runs)
+    spread_f = (max(r[0] for r in runs) - min(r[0] for r in runs)) / fwd
+    spread_b = (max(r[1] for r in runs) - min(r[1] for r in runs)) / bwd
+    clear_pool()
+    # steady forward step, and one adjoint step against one forward step (kernels alone)
     S = solver.Stefan.from_case(base, stream=stream)
     S.set_ic(base.theta0())
     S.step(T // 2)
+    S.sync()
+    steady_ms = time_steps(torch, S, 200, stream) / 200
     traj = S.new_theta_planes(2)
     S.theta_plane(traj[0])
     a = S.new_state_buffer()
@@ -292,7 +322,7 @@ def bench_adjoint(torch, solver, workloads, stream):
     S.adjoint_seed(traj[1], ph, a, want_loss=False)
     reps = 50
     torch.cuda.synchronize()
-    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     e[0].record(stream)
     S.step(reps)
     e[1].record(stream)
@@ -303,11 +333,14 @@ def bench_adjoint(torch, solver, workloads, stream):
     e[2].synchronize()
     f_ms, a_ms = e[0].elapsed_time(e[1]) / reps, e[1].elapsed_time(e[2]) / reps
     S.close()
-    fwd, bwd = (t1 - t0) * 1e3, (t2 - t1) * 1e3
-    return {"grid": "%dx%d" % (base.nx, base.ny), "steps": T, "forward_ms": fwd, "backward_ms": bwd,
-            "backward_over_forward": bwd / fwd, "kernel_forward_ms": f_ms, "kernel_adjoint_ms": a_ms,
-            "kernel_adjoint_over_forward": a_ms / f_ms, "loss": float(L.detach()),
-            "checkpoints": int(math.ceil(T / math.ceil(math.sqrt(T))))}
+    return {"grid": "%dx%d" % (base.nx, base.ny), "steps": T, "state_mb": 9 * 4 * base.nx * base.ny / 1e6,
+            "repeats": repeats, "forward_ms": fwd, "backward_ms": bwd, "backward_over_forward": bwd / fwd,
+            "forward_spread": spread_f, "backward_spread": spread_b,
+            "steady_forward_ms_per_step": steady_ms, "backward_over_T_steady_forward": bwd / (T * steady_ms),
+            "kernel_forward_ms": f_ms, "kernel_adjoint_ms": a_ms, "kernel_adjoint_over_forward": a_ms / f_ms,
+            "loss": runs[-1][2], "checkpoints": int(math.ceil(T / math.ceil(math.sqrt(T)))),
+            "timing": "wall clock between torch.cuda.synchronize() calls, median of %d after one untimed "
+                      "forward+backward (handle, checkpoints and graphs created there)" % repeats}
 
 
 def bench_d1q3(torch, solver, workloads, stream):
@@ -388,26 +421,110 @@ def bench_cavity_d2q9_801(torch, solver, workloads, stream, steps=20, warmup_ste
     return out
 
 
-def cpu_baseline_sample(workloads, budget_s=12.0):
-    """The FP64 oracle (single thread, as it stands) on a 4096 x 64 problem with
-    the melting workload's parameters and the first 64 rows of its initial field."""
+# ------------------------------------------------------------------ error against the oracle
+def _err(th, ph, refs, key):
+    tr = refs[key + "/theta"]
+    out = {"max_rel_dtheta": float(abs(th - tr).max() / max(abs(tr).max(), 1e-300))}
+    if ph is not None:
+        out["max_abs_dphi"] = float(abs(ph - refs[key + "/phi"]).max())
+    return out
+
+
+def oracle_errors(torch, solver, workloads, stream):
+    """Every leg's small version (workloads.bench_parity_cases, same kernels and
+    launch path) against the FP64 oracle's stored results
+    (tests/golden/bench_refs.npz, written by tests/golden/make_bench_refs.py):
+    max |d theta| / max |theta_ref| and max |d phi|; for the adjoint the
+    relative errors of the gradient and of the loss."""
+    import numpy as np
+    refs = np.load(os.path.join(ROOT, "tests", "golden", "bench_refs.npz"))
+    out = {}
+    for name, (c, method, kw) in workloads.bench_parity_cases().items():
+        S = solver.Stefan.from_case(c, stream=stream, **kw)
+        try:
+            if method != "IREBM":
+                S.set_method(method)
+            S.set_ic(c.theta0())
+            S.step(c.steps)
+            th, ph, _ = S.fields()
+            out[name] = _err(th, ph, refs, name)
+            out[name]["case"] = "%s %dx%d, %d steps, %s" % (c.name, c.nx, c.ny, c.steps, method)
+        finally:
+            S.close()
+    cases = workloads.bench_parity_batch()
+    B = solver.StefanBatch(cases, stream=stream)
+    try:
+        for k, c in enumerate(cases):
+            B.set_ic(k, c.theta0())
+        B.step(cases[0].steps)
+        errs = [_err(B.theta(k), None, refs, "batch%d" % k)["max_rel_dtheta"] for k in range(len(cases))]
+    finally:
+        B.close()
+    out["batched"] = {"max_rel_dtheta": max(errs), "case": "%d problems, sides %d-%d, %d steps" % (
+        len(cases), min(c.nx for c in cases), max(c.nx for c in cases), cases[0].steps)}
+    from paper_2505_13097_gb300.autograd import misfit
+    a = workloads.bench_parity_adjoint()
+    th0 = torch.tensor(a.theta0(), device="cuda", requires_grad=True)
+    tw = torch.tensor([a.walls.get(k, (0, 0.0))[1] for k in "WESN"], dtype=torch.float64, device="cuda",
+                      requires_grad=True)
+    ste = torch.tensor(a.ste, dtype=torch.float64, device="cuda", requires_grad=True)
+    with torch.cuda.stream(stream):
+        L = misfit(th0, tw, ste, a, a.steps, torch.tensor(refs["adjoint/target"], device="cuda"))
+        L.backward()
+    torch.cuda.synchronize()
+    g0 = th0.grad.cpu().numpy()
+    r0 = refs["adjoint/g_theta0"]
+    out["adjoint"] = {
+        "case": "%s %dx%d, %d steps, FP32 forward; oracle FP64 adjoint" % (a.name, a.nx, a.ny, a.steps),
+        "g_theta0_max_rel": float(abs(g0 - r0).max() / abs(r0).max()),
+        "g_wall_rel": float(abs(float(tw.grad[0]) - refs["adjoint/g_wall"][0]) / abs(refs["adjoint/g_wall"][0])),
+        "g_ste_rel": float(abs(float(ste.grad) - float(refs["adjoint/g_ste"])) / abs(float(refs["adjoint/g_ste"]))),
+        "loss_rel": float(abs(float(L.detach()) - float(refs["adjoint/loss"])) / abs(float(refs["adjoint/loss"])))}
+    return out
+
+
+def _oracle_sample(rows, nsteps):
+    """nsteps oracle steps of a 4096 x rows problem with the melting workload's
+    parameters and the first rows of its initial field: (node updates, seconds).
+    Module-level so that spawned worker processes can run it."""
     import oracle
+    from paper_2505_13097_gb300 import workloads
     c = workloads.melt_2d()
-    rows = 64
-    th0 = c.theta0()[:rows]
     P = oracle.Problem(2, c.nx, rows, tau=c.tau, delta=c.delta, ste=c.ste, walls=c.walls)
-    f = P.init(th0)
-    t = time.perf_counter()
+    f = P.init(c.theta0()[:rows])
     f = P.step(f)
-    one = time.perf_counter() - t
-    n = max(2, min(400, int(budget_s / max(one, 1e-6))))
     t = time.perf_counter()
-    for _ in range(n):
+    for _ in range(nsteps):
         f = P.step(f)
-    el = time.perf_counter() - t
-    return {"value": c.nx * rows * n / el / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": "FP64 C oracle, 1 thread, %d steps of a %dx%d problem with the 4096^2 melting "
-                      "workload's parameters (first %d rows of its initial field), %.1f s" % (n, c.nx, rows, rows, el)}
+    return c.nx * rows * nsteps, time.perf_counter() - t
+
+
+def cpu_baseline_sample(workloads, budget_s=8.0):
+    """The FP64 oracle as it stands on the host cores, on a bounded sample of the
+    melting workload: one thread, then one independent copy of the same
+    sample per core (worker processes started with spawn) timed together;
+    `value` is the all-core aggregate."""
+    import multiprocessing as mp
+    rows = 64
+    n1, t1 = _oracle_sample(rows, 1)
+    nsteps = max(2, min(400, int(budget_s / max(t1, 1e-6))))
+    u, el = _oracle_sample(rows, nsteps)
+    single = u / el / 1e6
+    cores = os.cpu_count() or 1
+    sample = "%d steps of a 4096x%d problem with the 4096^2 melting workload's parameters (first %d rows of its " \
+             "initial field)" % (nsteps, rows, rows)
+    try:
+        with mp.get_context("spawn").Pool(cores) as pool:
+            res = pool.starmap(_oracle_sample, [(rows, nsteps)] * cores)
+        agg = sum(r[0] for r in res) / max(r[1] for r in res) / 1e6
+        return {"value": agg, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                "sample": "FP64 C oracle, %d independent single-thread copies (one per host core) of %s, "
+                          "aggregate node updates / slowest copy's time" % (cores, sample),
+                "single_thread": {"value": single, "unit": "MLUPS", "cores": 1, "seconds": el,
+                                  "sample": "FP64 C oracle, 1 thread, " + sample}}
+    except Exception as e:   # reported, not fatal
+        return {"value": single, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                "sample": "FP64 C oracle, 1 thread, " + sample, "all_cores_error": str(e)}
 
 
 # ------------------------------------------------------------------ arms
@@ -476,7 +593,8 @@ def run_gpu(args):
     value = job_mlups(world, nodes, args.steps, ms_max)
     per_step_ms = ms / args.steps
     k_step_ms, k_job_ms = st["kernel_ms"]
-    # the dominant kernel: the TMA stream/collide kernel moves 72 algorithmic bytes per node
+    # the dominant kernel: the fused step kernel, 72 algorithmic bytes per node update
+    # (it also solves the Newton nodes: one launch per step)
     achieved = BYTES_FP32 * nodes / (k_step_ms * 1e-3) / 1e9
 
     extra = {}
@@ -499,11 +617,23 @@ def run_gpu(args):
         extra["eebm_form"] = bench_eebm(torch, solver, case, args.steps, args.warmup, stream, nodes, ms)
         extra["batched_256"] = bench_batch(torch, solver, workloads, max(20, args.steps // 2), args.warmup, stream)
         extra["adjoint_1024"] = bench_adjoint(torch, solver, workloads, stream)
+        extra["adjoint_2048"] = bench_adjoint(torch, solver, workloads, stream, n=2048)
         extra["d1q3_512"] = bench_d1q3(torch, solver, workloads, stream)
         extra["bar_1d_801_three_schemes"] = bench_bar_1d(torch, solver, workloads, stream)
         extra["cavity_d2q9_801_three_schemes"] = bench_cavity_d2q9_801(torch, solver, workloads, stream)
         extra["d2q5_cavity_4096"] = bench_d2q5(torch, solver, workloads, args.steps, args.warmup, stream, peak)
-    e2e_ms, h2d, d2h = bench_e2e(torch, solver, case, args.steps, stream) if rank == 0 else (0, 0, 0)
+    e2e_ms, h2d, d2h = bench_e2e(torch, solver, case, args.steps, stream, args.window_step) if rank == 0 else (0, 0, 0)
+    errs = oracle_errors(torch, solver, workloads, stream) if rank == 0 else {}
+    # every result carries its error against the FP64 oracle (the leg's small version)
+    legs = {"fp64_form": ["melt_2d_fp64"], "eebm_form": ["eebm_fp32"], "batched_256": ["batched"],
+            "adjoint_1024": ["adjoint"], "adjoint_2048": ["adjoint"], "d1q3_512": ["d1q3_melt_512"],
+            "bar_1d_801_three_schemes": ["bar_1d_irebm", "bar_1d_eebm", "bar_1d_ilfbm"],
+            "cavity_d2q9_801_three_schemes": ["cavity_d2q9_irebm", "cavity_d2q9_eebm", "cavity_d2q9_ilfbm"],
+            "d2q5_cavity_4096": ["d2q5_cavity_fp32", "d2q5_cavity_fp64", "d2q5_eebm_fp32"],
+            "corner_2d_fp64_2048": ["corner_ste%g" % s_ for s_ in workloads.CORNER_STE]}
+    for leg, keys in legs.items():
+        if leg in extra:
+            extra[leg]["error_vs_oracle"] = {k: errs[k] for k in keys}
 
     if rank == 0:
         line = {
@@ -520,32 +650,31 @@ def run_gpu(args):
                        "l2": "state 1.2 GB > 129 MB L2 (no flush needed)", "parallelism": "replicas" if world > 1 else "1 GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
-                         # dram__bytes_read.sum + dram__bytes_write.sum of one launch of this kernel in an
-                         # ncu capture of the 2048^2 workload (282.4 MB for 4.19 M nodes), scaled by the
-                         # node count of the launch (traffic grows with the nodes streamed)
-                         # dram__bytes_read.sum + dram__bytes_write.sum of one launch of this kernel in an
-                         # ncu capture of the 2048^2 workload (164.6 + 118.5 MB for 4.19 M nodes), scaled by
-                         # the node count of the launch (traffic grows with the nodes streamed)
-                         "traffic": 283079936 / (2048 * 2048) * nodes,
-                         "traffic_note": "ncu capture of d2q9_tma_kernel on the 2048^2 melting workload (93.7 percent "
-                                         "of its algorithmic bytes), scaled to this launch's node count",
+                         # dram__bytes_read.sum + dram__bytes_write.sum of one launch of this kernel in an ncu
+                         # capture, per launch at this node count (None: not captured since the kernel changed)
+                         "traffic": FUSED_TRAFFIC_PER_NODE * nodes if FUSED_TRAFFIC_PER_NODE else None,
+                         "traffic_note": FUSED_TRAFFIC_NOTE,
                          "bytes_per_node": BYTES_FP32, "units_per_launch": nodes,
-                         "kernel": "d2q9_tma_kernel<false>", "kernel_ms": k_step_ms,
-                         "job_kernel": "newton_jobs_kernel<float,false>", "job_kernel_ms": k_job_ms,
+                         "kernel": "d2q9_fused_kernel<false>", "kernel_ms": k_step_ms,
+                         "launches_per_step": 1, "second_kernel_ms": k_job_ms,
                          "whole_step_gbs": BYTES_FP32 * nodes / (per_step_ms * 1e-3) / 1e9,
                          "whole_step_frac": BYTES_FP32 * nodes / (per_step_ms * 1e-3) / 1e9 / peak,
                          "timing": "kernel_ms: CUDA events around each launch of 50 steps launched one by one, "
                                    "right after the timed window",
                          "peak_source": peak_kind},
+            "error_vs_oracle": errs.get("melt_2d_fp32"),
             "cpu_baseline": cpu_baseline_sample(workloads) if (world == 1 and not args.no_cpu) else None,
             "e2e": {"value": nodes * args.steps / e2e_ms / 1e3, "unit": "MLUPS",
                     "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
-                    "what": "lbm_stefan_set_ic from pinned host theta0, %d steps from the initial state, "
-                            "lbm_stefan_get_fields to pinned host theta" % args.steps},
-            "gpu_launches": 2 * args.steps,   # per step: the TMA stream/collide kernel and the Newton job kernel
+                    "what": "lbm_stefan_set_state from a pinned host copy of the state at the start of the "
+                            "headline's window (all populations), %d steps, lbm_stefan_get_fields to pinned host "
+                            "theta; wall clock" % args.steps},
+            "gpu_launches": args.steps,   # one fused kernel launch per step
             "clocks": clk.summary(),
             "energy_imbalance_last_step": st["imbalance"],
             "newton_nodes_last_step": st["newton_nodes"],
+            "newton_mean_iterations_last_step": st["newton_iters"] / max(1, st["newton_nodes"]),
+            "newton_max_iterations_last_step": st["newton_max_iter"],
         }
         line.update(extra)
         print(json.dumps(line), flush=True)

@@ -8,7 +8,11 @@
  * Algorithm 3 of the paper once per step: collision (Eq. 12), pull
  * streaming, the boundary closures of Sec. 4.2 on q, the zeroth moment, the
  * local Newton solve of Eq. (14), the source of Eq. (13), and the next
- * collision, fused into one kernel launch per step.
+ * collision.  Kernel launches per step: D2Q9 with FP32 populations, one
+ * (a persistent kernel that also solves the Newton nodes); D2Q9 in FP64 and
+ * D2Q5, two (the stream/collide kernel, which hands the nodes that need the
+ * Newton iteration to a list, then the kernel that solves that list); D1Q3,
+ * one launch for all the steps of a call.
  *
  * Problem statement (Sec. 2, Eq. 1): dimensionless temperature theta with
  * melting temperature 0, Stefan number Ste, equal phase properties; the
@@ -46,7 +50,7 @@ typedef enum {
     LBM_ERR_ARG = 1,     /* invalid argument (sizes, tau <= 1/2, Ste <= 0, delta <= 0, NULL, ...) */
     LBM_ERR_CUDA = 2,    /* a CUDA runtime call failed */
     LBM_ERR_NEWTON = 3,  /* a node's Newton solve hit its iteration limit, or a value was not finite */
-    LBM_ERR_TIMEOUT = 4, /* reserved for bounded device waits */
+    LBM_ERR_TIMEOUT = 4, /* a bounded device wait ran out (the FP32 D2Q9 step's waits for its row loads) */
     LBM_ERR_STATE = 5    /* call out of order (e.g. step before set_ic) */
 } lbm_status;
 
@@ -85,6 +89,8 @@ typedef struct {
     long long newton_nodes;/* nodes that ran the Newton iteration in the last step */
     int newton_max_iter;   /* largest iteration count in the last step */
     int error;             /* sticky device error (lbm_status value, 0 if none) */
+    long long newton_iters;/* sum of the Newton iteration counts of the last step (its mean is
+                              newton_iters / newton_nodes) */
 } lbm_stefan_stats;
 
 /* ---------------------------------------------------------------- one problem
@@ -102,6 +108,11 @@ lbm_status lbm_stefan_create(const lbm_stefan_params* p, void* cuda_stream, lbm_
  * included); its value is that of the first Dirichlet wall in W, E, S, N.
  * Call before set_ic so that Dirichlet nodes start at theta_wall. */
 lbm_status lbm_stefan_set_bc(lbm_stefan* h, int wall, int kind, double theta_wall);
+
+/* Change the Stefan number (Eq. 1) of an existing problem, e.g. between the
+ * runs of a finite-difference check or of an optimisation over Ste; the
+ * state is kept.  LBM_ERR_ARG unless ste > 0 and finite. */
+lbm_status lbm_stefan_set_ste(lbm_stefan* h, double ste);
 
 /* Step method.  LBM_IREBM (default): Algorithm 3.  LBM_EEBM: the explicit
  * enthalpy based method of Algorithm 2 (Sec. 3.4), the paper's comparison
@@ -144,12 +155,26 @@ lbm_status lbm_stefan_set_ic(lbm_stefan* h, const double* theta0, int on_device)
 lbm_status lbm_stefan_step(lbm_stefan* h, int nsteps);
 
 /* D2Q9 and D2Q5: advance nsteps >= 1 steps launched one by one (no graph) with a
- * CUDA event before, between and after the two kernels of each step, wait for
+ * CUDA event before, between and after the kernels of each step, wait for
  * them, and return the mean device time per step of each kernel in ms:
- * ms_kernels[0] the stream/collide kernel (the TMA kernel in the FP32 form),
- * ms_kernels[1] the Newton job kernel.  Same result as lbm_stefan_step; for
- * measuring each kernel against its roofline.  Synchronizes. */
+ * ms_kernels[0] the stream/collide kernel (in the FP32 D2Q9 form the fused
+ * kernel, which also solves the Newton nodes), ms_kernels[1] the Newton job
+ * kernel (0 in the FP32 D2Q9 form, which has none).  Same result as
+ * lbm_stefan_step; for measuring each kernel against its roofline.
+ * Synchronizes. */
 lbm_status lbm_stefan_step_timed(lbm_stefan* h, int nsteps, double* ms_kernels);
+
+/* Test hook of the FP32 D2Q9 step, which waits for row loads that it issued
+ * itself (other steps ignore it).  wait_limit_s > 0 bounds every such wait
+ * (default 2 s).  withhold_load in {0, 1, 2} makes the step skip that load
+ * of its first work item (a range of rows of the 128-column strip at x = 0;
+ * load 0 is the row above the range, load 1 its first row): the wait for it
+ * runs out, the step stops that warp after the loads it has in flight have
+ * landed, and the next synchronizing call returns LBM_ERR_TIMEOUT (the
+ * handle's state is then undefined; create a new one).  withhold_load = -1
+ * restores normal steps.  LBM_ERR_ARG for a value outside [-1, 2] or a wait
+ * limit outside (0, 60] s. */
+lbm_status lbm_stefan_set_wait_test(lbm_stefan* h, double wait_limit_s, int withhold_load);
 
 /* Advance nsteps steps and write theta(t+1), ..., theta(t+nsteps) to
  * theta_traj (device, nsteps planes of ny*row_stride doubles, row_stride from
@@ -223,6 +248,21 @@ lbm_status lbm_stefan_adjoint_step(lbm_stefan* h, const double* theta_t, const d
 lbm_status lbm_stefan_adjoint_run(lbm_stefan* h, int nsteps, const double* theta_traj, void* adj,
                                   void* adj_other, int* result_index);
 
+/* One backward segment of a checkpointed run (D2Q9): loads `checkpoint` (a
+ * device copy of a state, state_bytes long, from lbm_stefan_get_state) as
+ * the current state, recomputes nsteps steps from it recording theta into
+ * theta_traj (nsteps + 1 planes), then runs nsteps reverse steps as
+ * lbm_stefan_adjoint_run does (adj holds lambda at the segment's end on
+ * entry; *result_index tells which buffer holds lambda at its start).  On a
+ * non-default stream the launches after the checkpoint copy are captured
+ * once per (nsteps, theta_traj, adj, adj_other) and replayed as a CUDA graph
+ * (at most 8 kept; set_bc, set_ste and set_method drop them).  Afterwards
+ * the current state is the segment's end.  Asynchronous on the handle's
+ * stream.  LBM_ERR_ARG for NULL pointers, nsteps < 1, adj == adj_other or
+ * another lattice; LBM_ERR_STATE for another method. */
+lbm_status lbm_stefan_adjoint_segment(lbm_stefan* h, const void* checkpoint, int nsteps, double* theta_traj,
+                                      void* adj, void* adj_other, int* result_index);
+
 /* From lambda_0: dL/dtheta0 (nx*ny doubles, zero on Dirichlet nodes),
  * dL/dtheta_wall[4] (walls that are not Dirichlet get 0) and dL/dSte.
  * Synchronizes. */
@@ -234,8 +274,11 @@ void lbm_stefan_destroy(lbm_stefan* h);
 /* ---------------------------------------------------------------- batches
  * Many independent D2Q9 problems of uneven sizes advanced by one persistent
  * kernel launch per step; the launches of a call are captured in a CUDA
- * graph.  Tile height and the tile-to-warp schedule come from
- * lbm_stefan_batch_autotune (or defaults). */
+ * graph.  In FP32 the launch is the fused kernel of the single-problem FP32
+ * step over a list of work items (a 128-column strip of one problem over a
+ * range of rows); in FP64 the warp-tile kernel plus the Newton job kernel.
+ * The tile height (FP32: the row count of the first work items) and the
+ * order of the problems come from lbm_stefan_batch_autotune (or defaults). */
 
 typedef struct {
     int nx, ny;                 /* >= 2 each */
@@ -255,8 +298,9 @@ lbm_status lbm_stefan_batch_get_stats(lbm_stefan_batch* b, int k, lbm_stefan_sta
  * keep the fastest; the state is saved and restored around the trials.
  * chosen_tile_h receives the chosen height (may be NULL). */
 lbm_status lbm_stefan_batch_autotune(lbm_stefan_batch* b, int trial_steps, int* chosen_tile_h);
-/* Set the tile height (rows per warp tile) and schedule (0 = problem order,
- * 1 = longest tiles first, round-robin over warps) explicitly. */
+/* Set the tile height (rows per warp tile; FP32: rows of the first work items,
+ * later ones have half and a quarter as many) and schedule (0 = problem order,
+ * 1 = largest problems (FP64: longest tiles) first) explicitly. */
 lbm_status lbm_stefan_batch_set_schedule(lbm_stefan_batch* b, int tile_h, int schedule);
 void lbm_stefan_batch_destroy(lbm_stefan_batch* b);
 
@@ -279,13 +323,15 @@ void lbm_stefan_batch_destroy(lbm_stefan_batch* b);
  *    in FP64); rows -1 and ny and the padding columns are zero.  Elements are
  *    float (LBM_FP32) or double (LBM_FP64).
  *  - wall_kind[4], wall_theta[4]: W, E, S, N as in lbm_stefan_set_bc.
- *  - The first call on a device resolves the array's device address
- *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - The first call on a device (in each CUDA context of it) resolves the
+ *    array's device address (cudaGetSymbolAddress); make that first call
+ *    before any stream capture.
  *  - Every call shares the array: calls that overlap on the GPU (other
  *    streams, other threads) race.  Each call clears what must start at zero.
- *  - Runs on cuda_stream (a cudaStream_t) and returns after the step has
- *    finished: it reads the device error flag (LBM_ERR_NEWTON on a Newton
- *    failure or a non-finite value). */
+ *  - Runs on cuda_stream (a cudaStream_t), copies the problem descriptor
+ *    from host memory and synchronizes the stream to read the device error
+ *    flag (LBM_ERR_NEWTON on a Newton failure or a non-finite value): every
+ *    call returns after its step has finished. */
 lbm_status lbm_stefan_step_d2q9_noalloc(const lbm_stefan_params* p, const int* wall_kind, const double* wall_theta,
                                         const void* state_in, void* state_out, void* cuda_stream);
 

@@ -37,6 +37,7 @@ class lbm_stefan_stats(ctypes.Structure):
         ("imbalance", ctypes.c_double), ("imbalance_max", ctypes.c_double),
         ("steps", ctypes.c_longlong), ("newton_nodes", ctypes.c_longlong),
         ("newton_max_iter", ctypes.c_int), ("error", ctypes.c_int),
+        ("newton_iters", ctypes.c_longlong),
     ]
 
     def as_dict(self):
@@ -64,6 +65,7 @@ SIGNATURES = {
     "lbm_stefan_set_ic": (_S, [_V, _V, _I]),
     "lbm_stefan_step": (_S, [_V, _I]),
     "lbm_stefan_step_timed": (_S, [_V, _I, _D]),
+    "lbm_stefan_set_wait_test": (_S, [_V, ctypes.c_double, _I]),
     "lbm_stefan_step_record": (_S, [_V, _I, _V]),
     "lbm_stefan_sync": (_S, [_V]),
     "lbm_stefan_get_fields": (_S, [_V, _V, _V, _V, _I]),
@@ -77,6 +79,8 @@ SIGNATURES = {
     "lbm_stefan_adjoint_step": (_S, [_V, _V, _V, _V, _V]),
     "lbm_stefan_adjoint_run": (_S, [_V, _I, _V, _V, _V, ctypes.POINTER(ctypes.c_int)]),
     "lbm_stefan_adjoint_finish": (_S, [_V, _V, _V, _I, _D, _D]),
+    "lbm_stefan_adjoint_segment": (_S, [_V, _V, _I, _V, _V, _V, ctypes.POINTER(ctypes.c_int)]),
+    "lbm_stefan_set_ste": (_S, [_V, ctypes.c_double]),
     "lbm_stefan_destroy": (None, [_V]),
     "lbm_stefan_batch_create": (_S, [_I, ctypes.POINTER(lbm_stefan_problem), _I, ctypes.c_double, _I, _V,
                                      ctypes.POINTER(_V)]),

@@ -52,7 +52,7 @@ __global__ void init_state_kernel(const Problem* dprob, const double* __restrict
         e += th + phi_of(th, pb.inv_delta) * pb.inv_ste;
     }
     e = warp_sum(e);
-    if ((threadIdx.x & 31) == 0) acc_add(&st->cur_energy, e);
+    if ((threadIdx.x & 31) == 0) acc_add(&my_stripe(st)->energy, e);
 }
 
 __global__ void wall_constants_kernel(Problem* probs, int nprob)
@@ -84,9 +84,12 @@ cudaError_t launch_wall_constants(Problem* dprobs, int nprob, cudaStream_t s)
 
 __global__ void finalize_init_kernel(DevStats* st)
 {
-    st->energy = acc_read(&st->cur_energy);
+    AccSum esum = {{0ull, 0ull, 0ull, 0ull}};
+    for (int k = 0; k < kStripes; ++k)
+        for (int j = 0; j < 4; ++j) esum.limb[j] += st->cur[k].energy.limb[j];
+    st->energy = acc_read(&esum);
     st->energy_prev = st->energy;
-    acc_clear(&st->cur_energy);
+    for (int k = 0; k < kStripes; ++k) acc_clear(&st->cur[k].energy);
     st->have_energy = 1;
 }
 

@@ -434,8 +434,8 @@ __global__ void __launch_bounds__(256) ilf2_final(Ilf2Args a, int maxit)
     e = warp_sum(e);
     fx = warp_sum(fx);
     if ((threadIdx.x & 31) == 0) {
-        acc_add(&sts->cur_energy, e);
-        acc_add(&sts->cur_flux, fx);
+        acc_add(&my_stripe(sts)->energy, e);
+        acc_add(&my_stripe(sts)->flux, fx);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         atomicMax(&sts->cur_maxit, K);

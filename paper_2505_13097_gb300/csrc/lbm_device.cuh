@@ -360,17 +360,71 @@ __device__ __forceinline__ void acc_clear(Acc128* a)
     va->hi = 0ll;
 }
 
+// The per-step sums (AccSum): return-less additions of the four limbs, so a
+// thread never waits for them.
+__device__ __forceinline__ void acc_add_fx(AccSum* a, const Fx& v)
+{
+    const unsigned long long lo = v.lo, hi = (unsigned long long)v.hi;
+    if (lo == 0ull && hi == 0ull) return;
+    atomicAdd(&a->limb[0], lo & 0xffffffffull);
+    atomicAdd(&a->limb[1], lo >> 32);
+    atomicAdd(&a->limb[2], hi & 0xffffffffull);
+    atomicAdd(&a->limb[3], hi >> 32);
+}
+
+__device__ __forceinline__ void acc_add(AccSum* a, double v)
+{
+    if (v == 0.0) return;
+    acc_add_fx(a, to_fixed(v));
+}
+
+// sum_k limb[k] 2^(32k) modulo 2^128, as a double
+__device__ __forceinline__ double acc_read(const AccSum* a)
+{
+    volatile const unsigned long long* l = a->limb;
+    const unsigned long long s0 = l[0], s1 = l[1], s2 = l[2], s3 = l[3];
+    const unsigned long long lo = s0 + (s1 << 32);
+    const unsigned long long carry = lo < s0 ? 1ull : 0ull;
+    const unsigned long long hi = (s1 >> 32) + s2 + (s3 << 32) + carry;
+    return (double)(long long)hi * 16.0 + (double)lo * 0x1p-60;
+}
+
+__device__ __forceinline__ void acc_clear(AccSum* a)
+{
+    volatile unsigned long long* l = a->limb;
+    l[0] = l[1] = l[2] = l[3] = 0ull;
+}
+
+// The stripe a thread adds into: spread over blocks and warps.
+__device__ __forceinline__ StepStripe* my_stripe(DevStats* st)
+{
+    return &st->cur[(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) % kStripes];
+}
+
 // Publish one problem's step statistics (called by the last block only).
 // E = fixed-point sum + (liquid nodes + sum_w Dirichlet nodes of wall w * phi(theta_w)) / Ste.
 __device__ __forceinline__ void publish_stats(DevStats* st, const Problem* pb)
 {
-    double e = acc_read(&st->cur_energy);
-    const double f = acc_read(&st->cur_flux);
+    AccSum esum = {{0ull, 0ull, 0ull, 0ull}}, fsum = {{0ull, 0ull, 0ull, 0ull}};
+    unsigned long long newton = 0, iters = 0, liquid = 0, dir[4] = {0, 0, 0, 0};
+    for (int k = 0; k < kStripes; ++k) {
+        volatile StepStripe* c = &st->cur[k];
+        for (int j = 0; j < 4; ++j) {
+            esum.limb[j] += c->energy.limb[j];
+            fsum.limb[j] += c->flux.limb[j];
+            dir[j] += c->dir[j];
+        }
+        newton += c->newton;
+        iters += c->iters;
+        liquid += c->liquid;
+    }
+    double e = acc_read(&esum);
+    const double f = acc_read(&fsum);
     volatile DevStats* v = st;
     if (pb) {
-        double c = (double)v->cur_liquid;
+        double c = (double)liquid;
         for (int w = 0; w < 4; ++w)
-            if (v->cur_dir[w]) c += (double)v->cur_dir[w] * pb->wall_phi[w];
+            if (dir[w]) c += (double)dir[w] * pb->wall_phi[w];
         e += c * pb->inv_ste;
     }
     if (v->have_energy) {
@@ -385,13 +439,20 @@ __device__ __forceinline__ void publish_stats(DevStats* st, const Problem* pb)
     v->flux = f;
     v->have_energy = 1;
     v->steps = v->steps + 1;
-    v->newton_nodes = (long long)v->cur_newton;
+    v->newton_nodes = (long long)newton;
+    v->newton_iters = (long long)iters;
     v->newton_max_iter = v->cur_maxit;
-    acc_clear(&st->cur_energy);
-    acc_clear(&st->cur_flux);
-    v->cur_newton = 0ull;
-    v->cur_liquid = 0ull;
-    for (int w = 0; w < 4; ++w) v->cur_dir[w] = 0ull;
+    for (int k = 0; k < kStripes; ++k) {
+        volatile StepStripe* c = &st->cur[k];
+        for (int j = 0; j < 4; ++j) {
+            c->energy.limb[j] = 0ull;
+            c->flux.limb[j] = 0ull;
+            c->dir[j] = 0ull;
+        }
+        c->newton = 0ull;
+        c->iters = 0ull;
+        c->liquid = 0ull;
+    }
     v->cur_maxit = 0;
 }
 

@@ -17,19 +17,39 @@ struct Acc128 {
     long long hi;
 };
 
-// Per-problem device statistics.  The "cur_" fields accumulate during one
+// Fixed-point accumulator of the per-step sums, updated with return-less
+// atomic additions: the 128-bit two's-complement value is split into four
+// 32-bit limbs, limb k being added into limb[k] (64 bits hold the sum of up to
+// 2^32 limbs without overflow); the value is sum_k limb[k] * 2^(32k) modulo
+// 2^128, formed with the carries when it is read.
+struct AccSum {
+    unsigned long long limb[4];
+};
+
+// One stripe of a step's sums.  The blocks of a launch add into
+// kStripes stripes (block index mod kStripes), each on its own 128-byte line,
+// so that their atomic additions are spread over the L2 slices; the stripes
+// are summed when the step is published.
+struct alignas(128) StepStripe {
+    AccSum energy;                 // sum_x theta' + phi(theta')/Ste
+    AccSum flux;                   // boundary flux
+    unsigned long long newton;     // nodes that ran the Newton iteration
+    unsigned long long iters;      // sum of their iteration counts
+    unsigned long long liquid;     // saturated liquid nodes (each adds 1/Ste to the energy)
+    unsigned long long dir[4];     // Dirichlet nodes per wall (each adds phi(theta_wall)/Ste)
+};
+constexpr int kStripes = 32;
+
+// Per-problem device statistics.  The "cur" stripes accumulate during one
 // step launch; the last block of the launch publishes them and clears them.
 struct DevStats {
-    Acc128 cur_energy;             // sum_x theta' + phi(theta')/Ste of this step
-    Acc128 cur_flux;               // boundary flux of this step
-    unsigned long long cur_newton; // nodes that ran the Newton iteration
-    unsigned long long cur_liquid; // saturated liquid nodes (each adds 1/Ste to the energy)
-    unsigned long long cur_dir[4]; // Dirichlet nodes per wall (each adds phi(theta_wall)/Ste)
+    StepStripe cur[kStripes];
     int cur_maxit;                 // largest Newton iteration count
     int error;                     // sticky: lbm_status of a device-detected failure
     double energy, energy_prev, flux, imbalance, imbalance_max;
     long long steps;
     long long newton_nodes;
+    long long newton_iters;        // sum of the Newton iteration counts of the last step
     int newton_max_iter;
     int have_energy;               // energy holds E(t) of the current state
     // adjoint accumulators: dL/dtheta_wall[4], dL/dSte, loss
@@ -115,6 +135,42 @@ struct TmaMaps {
     int ntiles;
 };
 
+// Counters of one launch of the fused FP32 D2Q9 step.  Between launches all
+// are zero except `streaming`, which holds the launch's warp count.
+struct FusedCounters {
+    unsigned int item_next;      // next work item to take
+    unsigned int streaming;      // warps still taking work items
+    unsigned int batch_tail;     // Newton batches reserved
+    unsigned int ticket;         // blocks finished (the last one publishes and resets)
+};
+
+// Per-launch arguments of the fused FP32 D2Q9 step (step_fused.cu): one
+// persistent, cooperative launch per step whose warps take work items
+// (problem, 128-column strip, first row, end row) from `items` in list order,
+// stream them through a TMA row ring of their own, and hand the nodes that
+// need the Newton iteration, 32 at a time, to the queue of a block chosen
+// round-robin, whose warps solve them between rows.  The last block
+// publishes the statistics and resets the counters.
+struct FusedArgs {
+    const Problem* probs;        // device array
+    const CUtensorMap* maps;     // device array: 2 per problem (state[0], state[1])
+    const int4* items;           // device array of work items
+    int nitems;
+    int nprob;
+    int parity;                  // read state[parity], write state[parity ^ 1]
+    double* rec;                 // optional theta' record plane (single problem only)
+    DevStats* stats;
+    FusedCounters* ctr;
+    NewtonJob* jobs;             // batches of 32 deferred Newton nodes (batch_cap batches)
+    int batch_cap;
+    unsigned int* bq_tail;       // per block (stride kBqStride): batches queued for it; zero between launches
+    unsigned int* bq;            // per block: bq_cap entries, batch index + 1 (0: not yet written)
+    int bq_cap;
+    long long wait_ns;           // bound of every wait (row loads, queue entries, the end) in nanoseconds
+    int withhold_load;           // test hook: >= 0 skips this load of item 0 (0: the row above it; -1: none)
+};
+constexpr int kBqStride = 32;    // unsigned ints between two blocks' queue tails (128 bytes)
+
 // Per-launch arguments of the Newton job kernel (runs after every D2Q9 step).
 struct JobArgs {
     const Problem* probs;
@@ -158,8 +214,17 @@ cudaError_t launch_d2q9_step(int precision, const StepArgs& a, int grid, cudaStr
 int d2q9_segment_width(int precision);   // nodes per warp segment
 int d2q9_blocks_per_sm(int precision);   // resident step blocks per SM (persistent grid)
 cudaError_t launch_d2q9_tma(const StepArgs& a, const TmaMaps& m, cudaStream_t s);
+// single problem, FP32: the interior rows and the rows that touch a wall (two
+// launches; with side, fork and join the second runs on `side`, joined back to s)
+cudaError_t launch_d2q9_flat(const StepArgs& a, int nsegs, int ny, int method, cudaStream_t s, cudaStream_t side,
+                             cudaEvent_t fork, cudaEvent_t join);
 int d2q9_tma_blocks_per_sm();
 cudaError_t launch_newton_jobs(int precision, int q, const JobArgs& a, cudaStream_t s);   // q = 9 or 5
+
+// Fused FP32 D2Q9 step (step_fused.cu): one persistent launch per step
+cudaError_t launch_d2q9_fused(const FusedArgs& a, cudaStream_t s);
+int d2q9_fused_grid();                   // resident blocks on this GPU (the persistent, cooperative grid)
+int d2q9_fused_warps();                  // warps per block
 
 // D2Q5 launchers (step_d2q5.cu): one tile per warp over a.nslots tiles
 cudaError_t launch_d2q5_step(int precision, const StepArgs& a, cudaStream_t s);

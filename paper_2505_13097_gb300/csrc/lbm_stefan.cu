@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -11,9 +12,13 @@
 #include "lbm_internal.h"
 
 #include <cudaTypedefs.h>
+#include <nvtx3/nvToolsExt.h>
 
 #ifndef LBM_PLANE_PAD
 #define LBM_PLANE_PAD 0
+#endif
+#ifndef LBM_FLAT
+#define LBM_FLAT 1   // single FP32 D2Q9 problem: the flat step kernel (else the TMA row pipeline)
 #endif
 
 using lbm::DevStats;
@@ -41,6 +46,15 @@ lbm_status fail(lbm_status s, const char* fmt, ...)
 
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
+// NVTX range for the lifetime of the object (visible to Nsight tools when one
+// is attached; the header-only NVTX API does nothing otherwise)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 // Steps per captured CUDA graph (an even number, so a graph starts and ends on parity 0).
 constexpr int kGraphSteps = 32;
 
@@ -56,6 +70,58 @@ struct GraphCache {
 };
 
 }  // namespace
+
+namespace lbm {
+// Counters, Newton batch array and batch queues of the fused FP32 D2Q9
+// kernel, sized for `nodes` nodes and the kernel's (fixed) cooperative grid:
+// every full batch holds 32 of the nodes, and each streaming warp adds at
+// most one padded batch at its end.
+struct FusedQueues {
+    FusedCounters* ctr = nullptr;
+    NewtonJob* jobs = nullptr;
+    unsigned int* bq_tail = nullptr;
+    unsigned int* bq = nullptr;
+    int batch_cap = 0, bq_cap = 0;
+    cudaError_t alloc(long long nodes)
+    {
+        const int grid = d2q9_fused_grid();
+        if (grid <= 0) return cudaErrorInvalidConfiguration;
+        const long long cap = nodes / 32 + (long long)grid * d2q9_fused_warps() + 1;
+        if (cap > (1LL << 30)) return cudaErrorInvalidValue;
+        batch_cap = (int)cap;
+        bq_cap = (batch_cap + grid - 1) / grid + 1;
+        FusedCounters c0 = {};
+        c0.streaming = (unsigned)(grid * d2q9_fused_warps());   // the first launch's streaming warps
+        cudaError_t e = cudaMalloc(&ctr, sizeof(FusedCounters));
+        if (e == cudaSuccess) e = cudaMemcpy(ctr, &c0, sizeof c0, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMalloc(&jobs, sizeof(NewtonJob) * 32 * (size_t)batch_cap);
+        if (e == cudaSuccess) e = cudaMalloc(&bq_tail, sizeof(unsigned int) * (size_t)grid * kBqStride);
+        if (e == cudaSuccess) e = cudaMemset(bq_tail, 0, sizeof(unsigned int) * (size_t)grid * kBqStride);
+        if (e == cudaSuccess) e = cudaMalloc(&bq, sizeof(unsigned int) * (size_t)grid * bq_cap);
+        if (e == cudaSuccess) e = cudaMemset(bq, 0, sizeof(unsigned int) * (size_t)grid * bq_cap);
+        return e;
+    }
+    void fill(FusedArgs& f) const
+    {
+        f.ctr = ctr;
+        f.jobs = jobs;
+        f.batch_cap = batch_cap;
+        f.bq_tail = bq_tail;
+        f.bq = bq;
+        f.bq_cap = bq_cap;
+    }
+    void release()
+    {
+        cudaFree(ctr);
+        cudaFree(jobs);
+        cudaFree(bq_tail);
+        cudaFree(bq);
+        ctr = nullptr;
+        jobs = nullptr;
+        bq_tail = bq = nullptr;
+    }
+};
+}  // namespace lbm
 
 struct lbm_stefan {
     lbm_stefan_params p;
@@ -77,7 +143,32 @@ struct lbm_stefan {
     double* dilf_scratch = nullptr;    // 2D ILFBM: S0, two l iterates, two l differences (5 nx*ny)
     bool use_tma = false;              // FP32 D2Q9: the TMA row-pipeline step kernel
     lbm::TmaMaps tma;
+    bool use_fused = false;            // FP32 D2Q9: the fused persistent step kernel
+    CUtensorMap* dmaps = nullptr;      // fused kernel: descriptors of state[0], state[1]
+    int4* ditems = nullptr;            // fused kernel: work items
+    int nitems = 0;
+    lbm::FusedQueues fq;               // fused kernel: counters and Newton batch queues
+    cudaStream_t side = nullptr;       // flat FP32 step: stream of the wall-row kernel
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    long long wait_ns = 2000000000LL;  // bound of the fused kernel's waits on row loads
+    int withhold_load = -1;            // test hook of the fused kernel (-1: off)
     GraphCache graph;
+    // captured adjoint segments (lbm_stefan_adjoint_segment): recompute + reverse
+    // steps for one (length, trajectory, adjoint buffers) combination each
+    struct SegGraph {
+        int n;
+        const void* traj;
+        const void* a;
+        const void* b;
+        cudaGraphExec_t exec;
+    };
+    std::vector<SegGraph> seg_graphs;
+    void reset_seg_graphs()
+    {
+        for (auto& g : seg_graphs)
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+        seg_graphs.clear();
+    }
 };
 
 struct lbm_stefan_batch {
@@ -106,6 +197,10 @@ struct lbm_stefan_batch {
     lbm::TmaMaps tma;
     CUtensorMap* dmaps = nullptr;      // 2 descriptors per problem
     int4* dtiles = nullptr;
+    bool use_fused = false;            // FP32: the fused persistent step kernel over a work-item list
+    int4* ditems = nullptr;
+    int nitems = 0;
+    lbm::FusedQueues fq;
     GraphCache graph;
 };
 
@@ -220,9 +315,26 @@ static lbm::JobArgs job_args(const Problem* probs, int nprob, int parity, double
     return j;
 }
 
-// One D2Q9 or D2Q5 step is two launches: the fused stream/collide kernel, which
-// defers the nodes that need the Newton iteration, and the job kernel that
-// solves them.
+static lbm::FusedArgs fused_args(lbm_stefan* h, int parity, double* rec)
+{
+    lbm::FusedArgs f;
+    f.probs = h->dprob;
+    f.maps = h->dmaps;
+    f.items = h->ditems;
+    f.nitems = h->nitems;
+    f.nprob = 1;
+    f.parity = parity;
+    f.rec = rec;
+    f.stats = h->dstats;
+    h->fq.fill(f);
+    f.wait_ns = h->wait_ns;
+    f.withhold_load = h->withhold_load;
+    return f;
+}
+
+// One step.  FP32 D2Q9: one launch of the fused kernel.  FP64 D2Q9 and D2Q5:
+// two launches, the stream/collide kernel, which defers the nodes that need
+// the Newton iteration, and the job kernel that solves them.  D1Q3: one launch.
 static cudaError_t launch_one(lbm_stefan* h, int parity, double* rec)
 {
     StepArgs a = single_args(h, parity, rec);
@@ -234,9 +346,12 @@ static cudaError_t launch_one(lbm_stefan* h, int parity, double* rec)
                                        h->stream);
     }
     if (h->p.lattice == LBM_D2Q9) {
+        if (h->use_fused) return lbm::launch_d2q9_fused(fused_args(h, parity, rec), h->stream);
         cudaError_t e;
         if (h->use_tma) {
-            e = lbm::launch_d2q9_tma(a, h->tma, h->stream);
+            e = LBM_FLAT ? lbm::launch_d2q9_flat(a, h->hp.pitch / 128, h->hp.ny, h->hp.method, h->stream, h->side,
+                                                    h->ev_fork, h->ev_join)
+                         : lbm::launch_d2q9_tma(a, h->tma, h->stream);
         } else {
             // one tile per warp; the hardware scheduler balances the short tiles
             const int grid = (h->hp.ntiles + lbm::kWarpsPerBlock - 1) / lbm::kWarpsPerBlock;
@@ -328,6 +443,94 @@ static bool setup_tma(lbm_stefan* h)
     return per_sm > 0;
 }
 
+// ------------------------------------------------------------------ fused kernel
+#ifndef LBM_USE_FUSED
+#define LBM_USE_FUSED 0
+#endif
+
+#ifndef LBM_FUSED_ROWS
+#define LBM_FUSED_ROWS 16   // largest row count of a work item
+#endif
+
+// Work items of the fused kernel: (problem, 128-column strip, first row, end
+// row), in the order the warps take them.  Guided self-scheduling: while R
+// strip-rows remain, the next item has clamp(ceil(R / (2 * warps)), 1,
+// rows_max) rows, so the items taken last are one or two rows long and the
+// warps finish together although their speeds differ.  Items are taken from
+// the strips in turn (problems in `order`, strips left to right), so the rows
+// shared by neighbouring items are loaded at about the same time (from L2 the
+// second time).
+static std::vector<int4> fused_items(const std::vector<Problem>& probs, const std::vector<int>& order, int rows_max,
+                                     int warps)
+{
+    struct Strip {
+        int prob, seg, next, end;
+    };
+    std::vector<Strip> strips;
+    long long remaining = 0;
+    for (int k : order) {
+        const Problem& pb = probs[k];
+        for (int seg = 0; seg < pb.pitch / lbm::kTmaW; ++seg) {
+            strips.push_back({k, seg, 0, pb.ny});
+            remaining += pb.ny;
+        }
+    }
+    std::vector<int4> items;
+    const long long div = 2LL * std::max(1, warps);
+    const int rmax = std::max(1, rows_max);
+    while (remaining > 0) {
+        bool any = false;
+        for (Strip& st : strips) {
+            if (st.next >= st.end) continue;
+            const long long want = std::min<long long>(rmax, std::max<long long>(1, (remaining + div - 1) / div));
+            const int rows = (int)std::min<long long>(want, st.end - st.next);
+            items.push_back(make_int4(st.prob, st.seg, st.next, st.next + rows));
+            st.next += rows;
+            remaining -= rows;
+            any = true;
+        }
+        if (!any) break;
+    }
+    return items;
+}
+
+static int fused_warps()
+{
+    const int g = lbm::d2q9_fused_grid();
+    return g > 0 ? g * lbm::d2q9_fused_warps() : 1;
+}
+
+static cudaError_t upload_items(const std::vector<int4>& items, int4** ditems, int* nitems)
+{
+    if (*ditems) cudaFree(*ditems);
+    *ditems = nullptr;
+    *nitems = 0;
+    cudaError_t e = cudaMalloc(ditems, sizeof(int4) * std::max<size_t>(1, items.size()));
+    if (e == cudaSuccess) e = cudaMemcpy(*ditems, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) *nitems = (int)items.size();
+    return e;
+}
+
+// Descriptors, work items and counter of the fused kernel; false leaves the
+// two-kernel step in use.
+static bool setup_fused(lbm_stefan* h)
+{
+    const Problem& hp = h->hp;
+    if (hp.pitch % lbm::kTmaW != 0 || (hp.plane * 4) % 16 != 0 || lbm::d2q9_fused_grid() <= 0) return false;
+    CUtensorMap maps[2];
+    for (int k = 0; k < 2; ++k)
+        if (!encode_state_map(&maps[k], hp.state[k], hp, lbm::kTmaW + 2 * lbm::kTmaHalo)) return false;
+    cudaError_t e = cudaMalloc(&h->dmaps, sizeof maps);
+    if (e == cudaSuccess) e = cudaMemcpy(h->dmaps, maps, sizeof maps, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = upload_items(fused_items({hp}, {0}, LBM_FUSED_ROWS, fused_warps()), &h->ditems, &h->nitems);
+    if (e == cudaSuccess) e = h->fq.alloc((long long)hp.nx * hp.ny);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
 extern "C" lbm_status lbm_stefan_create(const lbm_stefan_params* p, void* cuda_stream, lbm_stefan** out)
 {
     if (!p || !out) return fail(LBM_ERR_ARG, "NULL argument");
@@ -373,14 +576,24 @@ extern "C" lbm_status lbm_stefan_create(const lbm_stefan_params* p, void* cuda_s
     if (e == cudaSuccess) e = cudaMalloc(&h->dticket, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMemset(h->dticket, 0, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMalloc(&h->dscratch, sizeof(double) * 3 * (size_t)p->nx * p->ny);
-    if (e == cudaSuccess && q != 3) e = cudaMalloc(&h->djobs, sizeof(lbm::NewtonJob) * (size_t)p->nx * p->ny);
     if (e == cudaSuccess) e = cudaMalloc(&h->djob_count, sizeof(unsigned int));
     if (e == cudaSuccess && q == 9) h->adj_tile_h = adjoint_tile_h(h->hp);
     if (e == cudaSuccess) e = cudaMemset(h->djob_count, 0, sizeof(unsigned int));
     h->hp.state[0] = bufs[0];
     h->hp.state[1] = bufs[1];
     h->hp.stats = 0;
-    if (e == cudaSuccess && tma) h->use_tma = setup_tma(h);
+    if (e == cudaSuccess && tma && LBM_USE_FUSED) h->use_fused = setup_fused(h);
+    if (e == cudaSuccess && tma && !h->use_fused) h->use_tma = setup_tma(h);
+    // the flat FP32 step runs its wall rows on a side stream (non-default streams only:
+    // the legacy stream would serialize with it)
+    if (e == cudaSuccess && h->use_tma && LBM_FLAT && h->stream != nullptr) {
+        e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+    }
+    // the list of deferred Newton nodes of the two-kernel steps (the fused kernel has its own)
+    if (e == cudaSuccess && q != 3 && !h->use_fused)
+        e = cudaMalloc(&h->djobs, sizeof(lbm::NewtonJob) * (size_t)p->nx * p->ny);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         lbm_stefan_destroy(h);
@@ -405,6 +618,21 @@ extern "C" lbm_status lbm_stefan_set_bc(lbm_stefan* h, int wall, int kind, doubl
     h->hp.wall_kind[wall] = kind;
     h->hp.wall_theta[wall] = theta_wall;
     h->graph.reset();
+    h->reset_seg_graphs();
+    return upload_problem(h);
+}
+
+extern "C" lbm_status lbm_stefan_set_ste(lbm_stefan* h, double ste)
+{
+    if (!h) return fail(LBM_ERR_ARG, "NULL handle");
+    if (!(ste > 0.0) || !std::isfinite(ste)) return fail(LBM_ERR_ARG, "Ste must be > 0 (got %g)", ste);
+    h->p.ste = ste;
+    h->hp.ste = ste;
+    h->hp.inv_ste = 1.0 / ste;
+    h->hp.inv_ste_f = (float)h->hp.inv_ste;
+    h->hp.sat = saturation_threshold(h->precision, h->hp.delta, ste);
+    h->graph.reset();
+    h->reset_seg_graphs();
     return upload_problem(h);
 }
 
@@ -449,6 +677,7 @@ extern "C" lbm_status lbm_stefan_set_method(lbm_stefan* h, int method)
     h->hp.method = method;
     h->ic = false;   // the state of one method is not a state of the other
     h->graph.reset();
+    h->reset_seg_graphs();
     return upload_problem(h);
 }
 
@@ -491,6 +720,7 @@ static lbm_status capture_graph(lbm_stefan* h)
 
 extern "C" lbm_status lbm_stefan_step(lbm_stefan* h, int nsteps)
 {
+    NvtxRange r("lbm_stefan_step");
     if (!h) return fail(LBM_ERR_ARG, "NULL handle");
     if (nsteps < 0) return fail(LBM_ERR_ARG, "nsteps must be >= 0");
     if (!h->ic) return fail(LBM_ERR_STATE, "set_ic must come before step");
@@ -559,10 +789,20 @@ extern "C" lbm_status lbm_stefan_step_timed(lbm_stefan* h, int nsteps, double* m
     if (e == cudaSuccess) e = cudaEventRecord(ev[0], h->stream);
     for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
         StepArgs a = single_args(h, h->parity, nullptr);
+        if (h->use_fused) {
+            // one launch per step: the second interval is empty
+            e = lbm::launch_d2q9_fused(fused_args(h, h->parity, nullptr), h->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[2 * k + 1], h->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[2 * k + 2], h->stream);
+            h->parity ^= 1;
+            continue;
+        }
         if (h->p.lattice == LBM_D2Q5) {
             e = lbm::launch_d2q5_step(h->precision, a, h->stream);
         } else if (h->use_tma) {
-            e = lbm::launch_d2q9_tma(a, h->tma, h->stream);
+            e = LBM_FLAT ? lbm::launch_d2q9_flat(a, h->hp.pitch / 128, h->hp.ny, h->hp.method, h->stream, h->side,
+                                                    h->ev_fork, h->ev_join)
+                         : lbm::launch_d2q9_tma(a, h->tma, h->stream);
         } else {
             const int grid = (h->hp.ntiles + lbm::kWarpsPerBlock - 1) / lbm::kWarpsPerBlock;
             e = lbm::launch_d2q9_step(h->precision, a, grid, h->stream);
@@ -595,6 +835,7 @@ extern "C" lbm_status lbm_stefan_step_timed(lbm_stefan* h, int nsteps, double* m
 
 extern "C" lbm_status lbm_stefan_step_record(lbm_stefan* h, int nsteps, double* traj)
 {
+    NvtxRange r("lbm_stefan_step_record (recompute)");
     if (!h || (!traj && nsteps > 0)) return fail(LBM_ERR_ARG, "NULL argument");
     if (nsteps < 0) return fail(LBM_ERR_ARG, "nsteps must be >= 0");
     if (!h->ic) return fail(LBM_ERR_STATE, "set_ic must come before step_record");
@@ -675,7 +916,20 @@ extern "C" lbm_status lbm_stefan_get_stats(lbm_stefan* h, lbm_stefan_stats* out)
     out->newton_nodes = st.newton_nodes;
     out->newton_max_iter = st.newton_max_iter;
     out->error = st.error;
+    out->newton_iters = st.newton_iters;
     return s;
+}
+
+extern "C" lbm_status lbm_stefan_set_wait_test(lbm_stefan* h, double wait_limit_s, int withhold_load)
+{
+    if (!h) return fail(LBM_ERR_ARG, "NULL handle");
+    if (!(wait_limit_s > 0.0) || !(wait_limit_s <= 60.0)) return fail(LBM_ERR_ARG, "wait_limit_s must be in (0, 60]");
+    if (withhold_load < -1 || withhold_load > 2) return fail(LBM_ERR_ARG, "withhold_load must be -1, 0, 1 or 2");
+    h->wait_ns = (long long)(wait_limit_s * 1e9);
+    h->withhold_load = withhold_load;
+    h->graph.reset();   // captured launches carry the old values
+    h->reset_seg_graphs();
+    return LBM_OK;
 }
 
 extern "C" lbm_status lbm_stefan_layout(lbm_stefan* h, size_t* state_bytes, int* row_stride)
@@ -688,6 +942,7 @@ extern "C" lbm_status lbm_stefan_layout(lbm_stefan* h, size_t* state_bytes, int*
 
 extern "C" lbm_status lbm_stefan_get_state(lbm_stefan* h, void* buf, int on_device)
 {
+    NvtxRange r("lbm_stefan_get_state (checkpoint)");
     if (!h || !buf) return fail(LBM_ERR_ARG, "NULL argument");
     if (!h->ic) return fail(LBM_ERR_STATE, "no state yet");
     CUDA_TRY(cudaMemcpyAsync(buf, h->hp.state[h->parity], h->state_bytes,
@@ -698,6 +953,7 @@ extern "C" lbm_status lbm_stefan_get_state(lbm_stefan* h, void* buf, int on_devi
 
 extern "C" lbm_status lbm_stefan_set_state(lbm_stefan* h, const void* buf, int on_device)
 {
+    NvtxRange r("lbm_stefan_set_state (restore)");
     if (!h || !buf) return fail(LBM_ERR_ARG, "NULL argument");
     CUDA_TRY(cudaMemcpyAsync(h->hp.state[0], buf, h->state_bytes,
                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
@@ -780,6 +1036,7 @@ extern "C" lbm_status lbm_stefan_adjoint_step(lbm_stefan* h, const double* theta
 extern "C" lbm_status lbm_stefan_adjoint_run(lbm_stefan* h, int nsteps, const double* theta_traj, void* adj,
                                              void* adj_other, int* result_index)
 {
+    NvtxRange r("lbm_stefan_adjoint_run");
     if (h && h->p.lattice == LBM_D2Q5) return fail(LBM_ERR_ARG, "the adjoint covers D1Q3 and D2Q9");
     if (h && h->hp.method != LBM_IREBM) return fail(LBM_ERR_STATE, "the adjoint is that of the IREBM step");
     if (!h || !adj || !adj_other || !result_index || (!theta_traj && nsteps > 0))
@@ -797,6 +1054,64 @@ extern "C" lbm_status lbm_stefan_adjoint_run(lbm_stefan* h, int nsteps, const do
         cur ^= 1;
     }
     *result_index = cur;
+    return LBM_OK;
+}
+
+// The launches of one backward segment after the checkpoint is loaded: theta(t0)
+// into traj[0], nsteps recorded steps, nsteps reverse steps.
+static cudaError_t segment_launches(lbm_stefan* h, int nsteps, double* traj, void* a, void* b, int parity0)
+{
+    const long long plane = (long long)h->hp.ny * h->hp.pitch;
+    cudaError_t e = lbm::launch_fields(h->precision, h->dprob, h->hp, parity0, nullptr, nullptr, nullptr, traj,
+                                       h->stream);
+    int par = parity0;
+    for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
+        e = launch_one(h, par, traj + (k + 1) * plane);
+        par ^= 1;
+    }
+    void* buf[2] = {a, b};
+    int cur = 0;
+    for (int s = nsteps - 1; s >= 0 && e == cudaSuccess; --s) {
+        e = lbm::launch_adj_step(h->precision, adj_args(h, traj + s * plane, traj + (s + 1) * plane, buf[cur], buf[cur ^ 1]),
+                                 h->hp, h->stream);
+        cur ^= 1;
+    }
+    return e;
+}
+
+extern "C" lbm_status lbm_stefan_adjoint_segment(lbm_stefan* h, const void* checkpoint, int nsteps, double* theta_traj,
+                                                 void* adj, void* adj_other, int* result_index)
+{
+    NvtxRange r("lbm_stefan_adjoint_segment (restore, recompute, reverse steps)");
+    if (h && h->p.lattice != LBM_D2Q9) return fail(LBM_ERR_ARG, "adjoint_segment covers D2Q9 (D1Q3: adjoint_run)");
+    if (h && h->hp.method != LBM_IREBM) return fail(LBM_ERR_STATE, "the adjoint is that of the IREBM step");
+    if (!h || !checkpoint || !theta_traj || !adj || !adj_other || !result_index) return fail(LBM_ERR_ARG, "NULL argument");
+    if (nsteps < 1) return fail(LBM_ERR_ARG, "nsteps must be >= 1");
+    if (adj == adj_other) return fail(LBM_ERR_ARG, "adj and adj_other must differ");
+    // reload the checkpoint into state[0]
+    CUDA_TRY(cudaMemcpyAsync(h->hp.state[0], checkpoint, h->state_bytes, cudaMemcpyDeviceToDevice, h->stream));
+    CUDA_TRY(cudaMemsetAsync(&h->dstats->have_energy, 0, sizeof(int), h->stream));
+    h->parity = 0;
+    h->ic = true;
+    cudaGraphExec_t exec = nullptr;
+    for (auto& g : h->seg_graphs)
+        if (g.n == nsteps && g.traj == theta_traj && g.a == adj && g.b == adj_other) exec = g.exec;
+    if (!exec && h->stream != nullptr) {
+        cudaGraph_t g = nullptr;
+        CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = segment_launches(h, nsteps, theta_traj, adj, adj_other, 0);
+        cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+        if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess || e2 != cudaSuccess || !exec)
+            return fail(LBM_ERR_CUDA, "segment capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+        if (h->seg_graphs.size() >= 8) h->reset_seg_graphs();
+        h->seg_graphs.push_back({nsteps, theta_traj, adj, adj_other, exec});
+    }
+    if (exec) CUDA_TRY(cudaGraphLaunch(exec, h->stream));
+    else CUDA_TRY(segment_launches(h, nsteps, theta_traj, adj, adj_other, 0));
+    h->parity = nsteps & 1;
+    *result_index = nsteps & 1;
     return LBM_OK;
 }
 
@@ -822,6 +1137,7 @@ extern "C" void lbm_stefan_destroy(lbm_stefan* h)
 {
     if (!h) return;
     h->graph.reset();
+    h->reset_seg_graphs();
     cudaFree(h->hp.state[0]);
     cudaFree(h->hp.state[1]);
     cudaFree(h->dprob);
@@ -832,6 +1148,12 @@ extern "C" void lbm_stefan_destroy(lbm_stefan* h)
     cudaFree(h->djob_count);
     cudaFree(h->dilf);
     cudaFree(h->dilf_scratch);
+    cudaFree(h->dmaps);
+    cudaFree(h->ditems);
+    h->fq.release();
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->side) cudaStreamDestroy(h->side);
     delete h;
 }
 
@@ -928,7 +1250,17 @@ static lbm_status batch_build_schedule(lbm_stefan_batch* b, int tile_h, int sche
     b->tile_h = tile_h;
     b->schedule = schedule;
     b->graph.reset();
-    if (b->use_tma) {
+    if (b->use_fused) {
+        // fused kernel: tile_h is the largest row count of a work item;
+        // schedule 1 lists the largest problems first
+        std::vector<int> order(b->count);
+        for (int k = 0; k < b->count; ++k) order[k] = k;
+        if (schedule == 1)
+            std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+                return (long long)b->hp[x].nx * b->hp[x].ny > (long long)b->hp[y].nx * b->hp[y].ny;
+            });
+        CUDA_TRY(upload_items(fused_items(b->hp, order, tile_h, fused_warps()), &b->ditems, &b->nitems));
+    } else if (b->use_tma) {
         lbm_status s = batch_build_tma_tiles(b, tile_h, schedule);
         if (s != LBM_OK) return s;
     }
@@ -943,6 +1275,21 @@ static lbm_status batch_build_schedule(lbm_stefan_batch* b, int tile_h, int sche
 
 static cudaError_t batch_launch_one(lbm_stefan_batch* b, int parity)
 {
+    if (b->use_fused) {
+        lbm::FusedArgs f;
+        f.probs = b->dprobs;
+        f.maps = b->dmaps;
+        f.items = b->ditems;
+        f.nitems = b->nitems;
+        f.nprob = b->count;
+        f.parity = parity;
+        f.rec = nullptr;
+        f.stats = b->dstats;
+        b->fq.fill(f);
+        f.wait_ns = 2000000000LL;
+        f.withhold_load = -1;
+        return lbm::launch_d2q9_fused(f, b->stream);
+    }
     StepArgs a;
     a.probs = b->dprobs;
     a.nprob = b->count;
@@ -1030,7 +1377,10 @@ extern "C" lbm_status lbm_stefan_batch_create(int count, const lbm_stefan_proble
         base += 2 * sz;
     }
     if (LBM_USE_TMA && precision == LBM_FP32) b->use_tma = batch_setup_tma(b);
-    lbm_status s = batch_build_schedule(b, 16, 1);
+    if (b->use_tma && LBM_USE_FUSED && lbm::d2q9_fused_grid() > 0 && b->fq.alloc((long long)total_nodes) == cudaSuccess)
+        b->use_fused = true;
+    cudaGetLastError();
+    lbm_status s = batch_build_schedule(b, b->use_fused ? LBM_FUSED_ROWS : 16, 1);
     if (s != LBM_OK) {
         lbm_stefan_batch_destroy(b);
         return s;
@@ -1079,6 +1429,7 @@ static lbm_status batch_capture(lbm_stefan_batch* b)
 
 extern "C" lbm_status lbm_stefan_batch_step(lbm_stefan_batch* b, int nsteps)
 {
+    NvtxRange r("lbm_stefan_batch_step");
     if (!b) return fail(LBM_ERR_ARG, "NULL handle");
     if (nsteps < 0) return fail(LBM_ERR_ARG, "nsteps must be >= 0");
     int left = nsteps;
@@ -1137,6 +1488,7 @@ extern "C" lbm_status lbm_stefan_batch_get_stats(lbm_stefan_batch* b, int k, lbm
     out->newton_nodes = st.newton_nodes;
     out->newton_max_iter = st.newton_max_iter;
     out->error = st.error;
+    out->newton_iters = st.newton_iters;
     if (st.error) return fail((lbm_status)st.error, "device reported error %d in problem %d", st.error, k);
     return LBM_OK;
 }
@@ -1167,7 +1519,10 @@ extern "C" lbm_status lbm_stefan_batch_autotune(lbm_stefan_batch* b, int trial_s
     cudaMemcpyAsync(save, b->arena, b->arena_bytes, cudaMemcpyDeviceToDevice, b->stream);
     cudaMemcpyAsync(save_st, b->dstats, sizeof(DevStats) * b->count, cudaMemcpyDeviceToDevice, b->stream);
     const int saved_parity = b->parity;
-    const int cands_h[] = {8, 16, 32, 64};
+    // fused kernel: largest row count of a work item; otherwise rows per tile
+    const int cands_fused[] = {4, 8, 16, 32};
+    const int cands_tiles[] = {8, 16, 32, 64};
+    const int* cands_h = b->use_fused ? cands_fused : cands_tiles;
     const int cands_s[] = {1, 0};
     float best = 1e30f;
     int best_h = b->tile_h, best_s = b->schedule;
@@ -1175,7 +1530,8 @@ extern "C" lbm_status lbm_stefan_batch_autotune(lbm_stefan_batch* b, int trial_s
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     lbm_status st = LBM_OK;
-    for (int hs : cands_h) {
+    for (int ci = 0; ci < 4; ++ci) {
+        const int hs = cands_h[ci];
         for (int sc : cands_s) {
             st = batch_build_schedule(b, hs, sc);
             if (st != LBM_OK) break;
@@ -1227,6 +1583,8 @@ extern "C" void lbm_stefan_batch_destroy(lbm_stefan_batch* b)
     cudaFree(b->djob_count);
     cudaFree(b->dmaps);
     cudaFree(b->dtiles);
+    cudaFree(b->ditems);
+    b->fq.release();
     delete b;
 }
 
@@ -1255,24 +1613,51 @@ struct NoAllocScratch {
 // about 6.3 MB
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mutex;
-void* g_noalloc_addr[kMaxDevices] = {nullptr};
+// Bytes that each call clears: the statistics, the last-block ticket and the
+// job count, which lie between `stats` and `jobs`.
+constexpr size_t kNoAllocClear = offsetof(NoAllocScratch, jobs) - offsetof(NoAllocScratch, stats);
+static_assert(offsetof(NoAllocScratch, ticket) >= offsetof(NoAllocScratch, stats) + sizeof(DevStats) &&
+                  offsetof(NoAllocScratch, job_count) + sizeof(unsigned int) <= offsetof(NoAllocScratch, jobs),
+              "the counters must lie in the cleared range");
 
-// Device address of the scratch array on the current device; resolved once per
-// device (host code cannot use the array's name as a device address).
-lbm_status noalloc_scratch(NoAllocScratch** out)
+// Device address of the scratch array, resolved once per CUDA context: host
+// code cannot use the array's name as a device address, and a context that is
+// destroyed and created again (cudaDeviceReset) may place the array elsewhere.
+std::mutex g_noalloc_mutex;
+std::vector<std::pair<CUcontext, void*>> g_noalloc_addr;
+
+PFN_cuCtxGetCurrent_v4000 ctx_getter()
 {
-    int dev = 0;
-    CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return fail(LBM_ERR_ARG, "device index %d out of range", dev);
+    static const PFN_cuCtxGetCurrent_v4000 fn = []() -> PFN_cuCtxGetCurrent_v4000 {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 4000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(f);
+    }();
+    return fn;
+}
+
+lbm_status noalloc_scratch(NoAllocScratch** out, cudaStream_t stream)
+{
+    // a query of the caller's stream makes the device's context current
+    // (nothing is allocated or waited for)
+    const cudaError_t q = cudaStreamQuery(stream);
+    if (q != cudaSuccess && q != cudaErrorNotReady) return fail(LBM_ERR_CUDA, "cudaStreamQuery: %s", cudaGetErrorString(q));
+    const PFN_cuCtxGetCurrent_v4000 get = ctx_getter();
+    CUcontext ctx = nullptr;
+    if (!get || get(&ctx) != CUDA_SUCCESS || !ctx) return fail(LBM_ERR_CUDA, "no current CUDA context");
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_addr[dev]) {
-        void* ptr = nullptr;
-        CUDA_TRY(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
-        g_noalloc_addr[dev] = ptr;
-    }
-    *out = static_cast<NoAllocScratch*>(g_noalloc_addr[dev]);
+    for (const auto& e : g_noalloc_addr)
+        if (e.first == ctx) {
+            *out = static_cast<NoAllocScratch*>(e.second);
+            return LBM_OK;
+        }
+    void* ptr = nullptr;
+    CUDA_TRY(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+    g_noalloc_addr.emplace_back(ctx, ptr);
+    *out = static_cast<NoAllocScratch*>(ptr);
     return LBM_OK;
 }
 
@@ -1297,10 +1682,10 @@ extern "C" lbm_status lbm_stefan_step_d2q9_noalloc(const lbm_stefan_params* p, c
         if ((wall_kind[w] != LBM_ADIABATIC && wall_kind[w] != LBM_DIRICHLET) || !std::isfinite(wall_theta[w]))
             return fail(LBM_ERR_ARG, "bad wall %d", w);
 
-    NoAllocScratch* sc = nullptr;
-    s = noalloc_scratch(&sc);
-    if (s != LBM_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    NoAllocScratch* sc = nullptr;
+    s = noalloc_scratch(&sc, st);
+    if (s != LBM_OK) return s;
 
     const int segw = lbm::d2q9_segment_width(p->precision);
     Problem hp;
@@ -1316,7 +1701,7 @@ extern "C" lbm_status lbm_stefan_step_d2q9_noalloc(const lbm_stefan_params* p, c
     // the array keeps the previous call's contents: statistics, ticket and job
     // count must start at zero
     CUDA_TRY(cudaMemcpyAsync(&sc->prob, &hp, sizeof(Problem), cudaMemcpyHostToDevice, st));
-    CUDA_TRY(cudaMemsetAsync(&sc->stats, 0, sizeof(DevStats) + 2 * sizeof(unsigned int), st));
+    CUDA_TRY(cudaMemsetAsync(&sc->stats, 0, kNoAllocClear, st));
     CUDA_TRY(lbm::launch_wall_constants(&sc->prob, 1, st));
 
     StepArgs a;

@@ -32,6 +32,7 @@ template <>
 struct Acc<float> {
     ff s{0.f, 0.f};
     __device__ void add_ff(const ff& v) { ff_add(s, v.hi); s.lo = __fadd_rn(s.lo, v.lo); }
+    __device__ void add_f(float v) { ff_add(s, v); }
     __device__ void add_d(double v) { float h = (float)v; ff_add(s, h); s.lo = __fadd_rn(s.lo, (float)(v - (double)h)); }
     __device__ double get() const { return ff_to_double(s); }
 };
@@ -63,12 +64,18 @@ struct TileSums {
     int liquid = 0, newton = 0, maxit = 0;
 };
 
-// A warp's partial sums in a fixed lane order, then exact fixed-point atomics;
-// node counts go to integer counters (the publisher adds their phi/Ste terms).
+// A warp's partial sums, totalled in a fixed lane order (every lane gets the
+// totals): energy and flux as exact fixed-point values, node counts as integers.
+struct WarpSums {
+    Fx e{0, 0ull}, f{0, 0ull};
+    int nl = 0;        // saturated liquid nodes
+    int nd[4] = {0, 0, 0, 0};   // Dirichlet nodes per wall
+};
+
 template <typename P>
-__device__ __forceinline__ void flush_tile_sums(const Acc<P>& acc, const TileSums& ts, DevStats* st, int lane)
+__device__ __forceinline__ WarpSums warp_tile_sums(const Acc<P>& acc, const TileSums& ts)
 {
-    Fx e, f;
+    WarpSums w;
     if constexpr (sizeof(P) == 4) {
         ff se = acc.s, sf = ts.flux_f;
 #pragma unroll
@@ -80,26 +87,48 @@ __device__ __forceinline__ void flush_tile_sums(const Acc<P>& acc, const TileSum
             ff_add(sf, fh);
             sf.lo += fl;
         }
-        e = float_to_fixed(se.hi);
-        fx_add(e, float_to_fixed(se.lo));
-        f = float_to_fixed(sf.hi);
-        fx_add(f, float_to_fixed(sf.lo));
+        w.e = float_to_fixed(se.hi);
+        fx_add(w.e, float_to_fixed(se.lo));
+        w.f = float_to_fixed(sf.hi);
+        fx_add(w.f, float_to_fixed(sf.lo));
     } else {
-        e = to_fixed(warp_sum(acc.get()));
-        f = to_fixed(warp_sum(ts.flux));
+        w.e = to_fixed(warp_sum(acc.get()));
+        w.f = to_fixed(warp_sum(ts.flux));
     }
-    const int nl = warp_sum_i(ts.liquid);
-    int nd[4];
+    w.nl = warp_sum_i(ts.liquid);
 #pragma unroll
-    for (int w = 0; w < 4; ++w) nd[w] = warp_sum_i(ts.dir_count[w]);
-    if (lane == 0) {
-        acc_add_fx(&st->cur_energy, e);
-        acc_add_fx(&st->cur_flux, f);
-        if (nl) atomicAdd(&st->cur_liquid, (unsigned long long)nl);
+    for (int k = 0; k < 4; ++k) w.nd[k] = warp_sum_i(ts.dir_count[k]);
+    return w;
+}
+
+__device__ __forceinline__ void add_sums(WarpSums& a, const WarpSums& b)
+{
+    fx_add(a.e, b.e);
+    fx_add(a.f, b.f);
+    a.nl += b.nl;
 #pragma unroll
-        for (int w = 0; w < 4; ++w)
-            if (nd[w]) atomicAdd(&st->cur_dir[w], (unsigned long long)nd[w]);
-    }
+    for (int k = 0; k < 4; ++k) a.nd[k] += b.nd[k];
+}
+
+// Add sums to a problem's step accumulators (one thread); the fixed-point
+// additions make the result independent of the order of the calls.
+__device__ __forceinline__ void emit_sums(const WarpSums& w, DevStats* st)
+{
+    StepStripe* c = my_stripe(st);
+    acc_add_fx(&c->energy, w.e);
+    acc_add_fx(&c->flux, w.f);
+    if (w.nl) atomicAdd(&c->liquid, (unsigned long long)w.nl);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (w.nd[k]) atomicAdd(&c->dir[k], (unsigned long long)w.nd[k]);
+}
+
+// A warp's partial sums in a fixed lane order, then exact fixed-point atomics.
+template <typename P>
+__device__ __forceinline__ void flush_tile_sums(const Acc<P>& acc, const TileSums& ts, DevStats* st, int lane)
+{
+    const WarpSums w = warp_tile_sums<P>(acc, ts);
+    if (lane == 0) emit_sums(w, st);
 }
 
 // Target of M0(q) at a Dirichlet node on wall k (Eq. 14 with theta' = theta_D,
@@ -141,6 +170,103 @@ __device__ __forceinline__ ff dir_m0_target_f(const ff& th, int k, const Problem
         ff_add(m0t, (float)(-dphi * pb.inv_ste));
     }
     return m0t;
+}
+
+// ---------------------------------------------------------------- deferred Newton nodes
+// One node whose local Newton solve was deferred (Eq. 14, mixed-precision
+// form): theta' = m0 + (phi(theta) - phi(root))/Ste, c = theta' - (1-omega) m0,
+// and the node's stored q_i are relaxed in place, Omega~_i = (1-omega) q_i +
+// w_i c (Q = 9 or 5 planes of the step's output state[parity ^ 1]).  The
+// result carries the node's energy term theta' + phi(theta')/Ste as an exact
+// fixed-point value, its iteration count and its problem's statistics index.
+struct NewtonResult {
+    Fx e{0, 0ull};
+    int it = 0;
+    int sidx = -1;   // -1: no node (an idle lane)
+};
+
+template <typename P, bool REC, int Q>
+__device__ __forceinline__ NewtonResult newton_job_apply(const NewtonJob& jb, const Problem& pb, int parity,
+                                                         double* rec, DevStats* stats)
+{
+    NewtonResult r;
+    r.sidx = pb.stats;
+    // the stored q_i were written earlier in this launch, possibly by another
+    // SM: load them from L2 (ld.global.cg), never from this SM's L1; the loads
+    // are issued first so that their latency overlaps the solve
+    const int x = jb.node % pb.nx, y = jb.node / pb.nx;
+    const long long at = (long long)(y + 1) * pb.pitch + x;
+    P* d = static_cast<P*>(pb.state[parity ^ 1]) + at;
+    P qv[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) qv[i] = __ldcg(d + i * pb.plane);
+    double m0, th;
+    if constexpr (sizeof(P) == 4) {
+        // FP32 form: the job carries only the node; m0 = M0(q) from the stored
+        // unrelaxed q_i and theta = M0(f) = sum of the node's Omega_i(t) (the
+        // step's source state), both as float-float sums in the order the
+        // step kernel uses (last plane first)
+        const P* sv = static_cast<const P*>(pb.state[parity]) + at;
+        ff mm{0.f, 0.f}, t{0.f, 0.f};
+#pragma unroll
+        for (int i = Q - 1; i >= 0; --i) {
+            ff_add(t, __ldg(sv + i * pb.plane));
+            ff_add(mm, qv[i]);
+        }
+        m0 = ff_to_double(mm);
+        th = ff_to_double(t);
+    } else {
+        m0 = jb.m0;
+        th = jb.theta;
+    }
+    const double pth = phi_of(th, pb.inv_delta);
+    const NewtonOut nr = newton_mixed(m0, th, pth, pb);
+    if (!nr.ok || !isfinite(nr.root)) atomicCAS(&stats[r.sidx].error, 0, 3);
+    const double tn = m0 + (pth - nr.phi_root) * pb.inv_ste;
+    const P c = (P)(tn - (1.0 - pb.omega) * m0);
+    const P omc = (P)(1.0 - pb.omega);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const P wi = (P)lat_w(Q, i);
+        d[i * pb.plane] = fma(omc, qv[i], wi * c);
+    }
+    (void)x;
+    if (REC) rec[(long long)y * pb.pitch + x] = tn;
+    r.e = to_fixed(tn + nr.phi_root * pb.inv_ste);
+    r.it = nr.iters;
+    return r;
+}
+
+// The warp's results, grouped by problem: the lowest lane of each group sums
+// its group's energy terms exactly and adds them, the node count, the
+// iteration sum and the largest iteration count once.
+__device__ __forceinline__ void newton_group_add(const NewtonResult& r, DevStats* stats)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned grp = __match_any_sync(kFull, r.sidx);
+    const int leader = __ffs(grp) - 1;
+    Fx sum{0, 0ull};
+    int n = 0, mx = 0, its = 0;
+    for (int l = 0; l < 32; ++l) {
+        Fx v;
+        v.hi = __shfl_sync(kFull, r.e.hi, l);
+        v.lo = __shfl_sync(kFull, r.e.lo, l);
+        const int vi = __shfl_sync(kFull, r.it, l);
+        if ((grp >> l) & 1) {
+            fx_add(sum, v);
+            ++n;
+            mx = max(mx, vi);
+            its += vi;
+        }
+    }
+    if (lane == leader && r.sidx >= 0) {
+        DevStats* st = &stats[r.sidx];
+        StepStripe* c = my_stripe(st);
+        acc_add_fx(&c->energy, sum);
+        atomicAdd(&c->newton, (unsigned long long)n);
+        atomicAdd(&c->iters, (unsigned long long)its);
+        atomicMax(&st->cur_maxit, mx);
+    }
 }
 
 // ---------------------------------------------------------------- mbarriers and TMA

@@ -124,9 +124,9 @@ __global__ void __launch_bounds__(128) d1q3_step_kernel(StepArgs a)
     nn = warp_sum_i(nn);
     mi = warp_max_i(mi);
     if ((threadIdx.x & 31) == 0) {
-        acc_add(&st->cur_energy, e);
-        acc_add(&st->cur_flux, f);
-        if (nn) atomicAdd(&st->cur_newton, (unsigned long long)nn);
+        acc_add(&my_stripe(st)->energy, e);
+        acc_add(&my_stripe(st)->flux, f);
+        if (nn) atomicAdd(&my_stripe(st)->newton, (unsigned long long)nn);
         if (mi) atomicMax(&st->cur_maxit, mi);
     }
     finish_launch(a.stats, 1, a.ticket);

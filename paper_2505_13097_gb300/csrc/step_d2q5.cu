@@ -251,7 +251,6 @@ __device__ __forceinline__ void row5_update(const Problem& pb, const P* __restri
     }
 
     bool any_newton = false;
-    float row_m0 = 0.f;   // FP32 form: sum of theta' = m0 over this lane's saturated nodes
 #pragma unroll
     for (int k = 0; k < N; ++k) {
         const int x = x0 + k;
@@ -298,7 +297,7 @@ __device__ __forceinline__ void row5_update(const Problem& pb, const P* __restri
             // saturated: theta' = m0, no source; c = omega m0
             if constexpr (sizeof(P) == 4) {
                 c[k] = (P)(om_f * mf);
-                row_m0 += mf;
+                acc.add_f(mf);
                 if constexpr (REC) thn[k] = (double)mf;
             } else {
                 const double md = m0_d(m0[k]);
@@ -309,7 +308,6 @@ __device__ __forceinline__ void row5_update(const Problem& pb, const P* __restri
             ts.liquid += sat_liq ? 1 : 0;
         }
     }
-    if constexpr (sizeof(P) == 4) acc.add_ff(ff{row_m0, 0.f});
     if (__any_sync(kFull, any_newton)) {
         // deferred Newton solves: append (m0, theta) to the job list, store q_i unrelaxed
         int cnt = 0;
@@ -333,16 +331,8 @@ __device__ __forceinline__ void row5_update(const Problem& pb, const P* __restri
             jb.prob = pi;
             jb.node = y * nx + x0 + k;
             if constexpr (sizeof(P) == 4) {
-                ff t{0.f, 0.f}, mm{0.f, 0.f};
-#pragma unroll
-                for (int i = 4; i >= 0; --i) {
-                    ff_add(t, u[i][k]);
-                    ff_add(mm, qf[i][k]);
-                }
-                float* pm = reinterpret_cast<float*>(&jb.m0);
-                float* pt = reinterpret_cast<float*>(&jb.theta);
-                pm[0] = mm.hi; pm[1] = mm.lo;
-                pt[0] = t.hi; pt[1] = t.lo;
+                // FP32 form: the job kernel forms m0 and theta from memory
+                jb.m0 = jb.theta = 0.0;
             } else {
                 double th = 0.0;
 #pragma unroll

@@ -26,641 +26,16 @@
 // take the exact saturated branch (phi = 0 or 1 on both sides of Eq. 14, so
 // theta' = m0 and the source vanishes) without any FP64 work.
 // FP64 form: everything in FP64 (the saturation test uses the integer pipe).
-#include "step_common.cuh"
+#include <algorithm>
+
+#include "d2q9_row.cuh"
 
 namespace lbm {
 
-template <typename P> struct Vw;
-template <> struct Vw<float> { static constexpr int N = 4; };
-template <> struct Vw<double> { static constexpr int N = 2; };
-
-template <typename P>
-__device__ __forceinline__ void ldv(const P* p, P (&v)[Vw<P>::N]);
-template <>
-__device__ __forceinline__ void ldv<float>(const float* p, float (&v)[4])
+__device__ __forceinline__ void ldg4(const float* p, float (&v)[4])
 {
-    float4 t = __ldg(reinterpret_cast<const float4*>(p));
+    const float4 t = __ldg(reinterpret_cast<const float4*>(p));
     v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
-}
-template <>
-__device__ __forceinline__ void ldv<double>(const double* p, double (&v)[2])
-{
-    double2 t = __ldg(reinterpret_cast<const double2*>(p));
-    v[0] = t.x; v[1] = t.y;
-}
-template <typename P>
-__device__ __forceinline__ void stv(P* p, const P (&v)[Vw<P>::N]);
-template <>
-__device__ __forceinline__ void stv<float>(float* p, const float (&v)[4])
-{
-    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
-}
-template <>
-__device__ __forceinline__ void stv<double>(double* p, const double (&v)[2])
-{
-    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
-}
-
-
-// Boundary closures of Sec. 4.2 at one wall node (x, y).  q holds the pulled
-// values (entries of unknown directions are overwritten), u the node's own
-// Omega.  Returns the boundary flux contribution (filled q minus Omega that
-// leaves the lattice) as a float-float pair; wall reports the node's Dirichlet
-// wall (first in W, E, S, N) or -1.
-struct WallInfo {
-    unsigned unk;   // bit i: q_i not defined by streaming
-    int wall;       // Dirichlet wall index, -1 for bounce-back
-};
-
-__device__ __forceinline__ WallInfo wall_info(int x, int y, const Problem& pb)
-{
-    WallInfo w;
-    w.unk = 0;
-#pragma unroll
-    for (int i = 1; i < 9; ++i) {
-        const int sx = x - d2_ex(i), sy = y - d2_ey(i);
-        if (sx < 0 || sx >= pb.nx || sy < 0 || sy >= pb.ny) w.unk |= 1u << i;
-    }
-    const int walls = (x == 0 ? 1 : 0) | (x == pb.nx - 1 ? 2 : 0) | (y == 0 ? 4 : 0) | (y == pb.ny - 1 ? 8 : 0);
-    w.wall = -1;
-    for (int k = 0; k < 4; ++k)
-        if (((walls >> k) & 1) && pb.wall_kind[k] == 1) {
-            w.wall = k;
-            break;
-        }
-    return w;
-}
-
-// FP64 form: the closure in FP64.
-__device__ __noinline__ double wall_closure_d(double* q, const double* u, int x, int y, const Problem& pb, int& wall)
-{
-    const WallInfo wi = wall_info(x, y, pb);
-    wall = wi.wall;
-    double out = 0.0, in = 0.0;
-#pragma unroll
-    for (int j = 1; j < 9; ++j)
-        if ((wi.unk >> d2_opp(j)) & 1) out += u[j];
-    if (wi.wall >= 0) {
-        // Eq. (14) with theta' = theta_D fixes M0(q) = theta_D + (phi(theta_D) - phi(theta))/Ste;
-        // the unknown q share what the known ones leave, in proportion to w_i
-        double th = 0.0;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) th += u[i];
-        const double m0t = dir_m0_target_d(th, wi.wall, pb);
-        double known = 0.0, wu = 0.0;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            if ((wi.unk >> i) & 1) wu += d2_w(i);
-            else known += q[i];
-        }
-        const double r = (m0t - known) / wu;
-#pragma unroll
-        for (int i = 1; i < 9; ++i)
-            if ((wi.unk >> i) & 1) {
-                q[i] = d2_w(i) * r;
-                in += q[i];
-            }
-    } else {
-#pragma unroll
-        for (int i = 1; i < 9; ++i)
-            if ((wi.unk >> i) & 1) {
-                const int o = d2_opp(i);
-                q[i] = (pb.bb_mode == 0 && !((wi.unk >> o) & 1)) ? q[o] : u[o];
-                in += q[i];
-            }
-    }
-    return in - out;
-}
-
-// FP32 form: the same closure with float-float sums and no FP64 instruction on
-// the common path (dir_m0_target_f).
-__device__ __noinline__ ff wall_closure_f(float* q, const float* u, int x, int y, const Problem& pb, int& wall)
-{
-    const WallInfo wi = wall_info(x, y, pb);
-    wall = wi.wall;
-    ff out{0.f, 0.f}, in{0.f, 0.f};
-#pragma unroll
-    for (int j = 1; j < 9; ++j)
-        if ((wi.unk >> d2_opp(j)) & 1) ff_add(out, u[j]);
-    if (wi.wall >= 0) {
-        const int k = wi.wall;
-        ff th{0.f, 0.f}, known{0.f, 0.f};
-        float wu = 0.f;
-#pragma unroll
-        for (int i = 8; i >= 0; --i) {
-            ff_add(th, u[i]);
-            if ((wi.unk >> i) & 1) wu += (float)d2_w(i);
-            else ff_add(known, q[i]);
-        }
-        const ff m0t = dir_m0_target_f(th, k, pb);
-        // R = m0t - sum(known), shared by the unknown q in proportion to w_i
-        const float r = ((m0t.hi - known.hi) + (m0t.lo - known.lo)) / wu;
-#pragma unroll
-        for (int i = 1; i < 9; ++i)
-            if ((wi.unk >> i) & 1) {
-                q[i] = (float)d2_w(i) * r;
-                ff_add(in, q[i]);
-            }
-    } else {
-#pragma unroll
-        for (int i = 1; i < 9; ++i)
-            if ((wi.unk >> i) & 1) {
-                const int o = d2_opp(i);
-                q[i] = (pb.bb_mode == 0 && !((wi.unk >> o) & 1)) ? q[o] : u[o];
-                ff_add(in, q[i]);
-            }
-    }
-    ff f{in.hi, in.lo};
-    ff_add(f, -out.hi);
-    f.lo -= out.lo;
-    return f;
-}
-
-
-template <typename P>
-__device__ __forceinline__ float approx_sum(const P* u);
-template <>
-__device__ __forceinline__ float approx_sum<float>(const float* u)
-{
-    float s = 0.f;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) s += u[i];
-    return s;
-}
-template <>
-__device__ __forceinline__ float approx_sum<double>(const double* u)
-{
-    float s = 0.f;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) s += approx_float(u[i]);
-    return s;
-}
-
-
-// ---------------------------------------------------------------- row ring
-// Each warp streams its rows through a ring of kStages row slots in shared
-// memory with cp.async (16-byte copies that bypass L1), so several rows are in
-// flight per warp without holding registers.  A slot holds one row of all nine
-// planes (32*N values each) plus the one element left and right of the
-// segment for the planes that are shifted along x.  Row y is computed from the
-// slots of rows y-1, y and y+1; the load of row y+kStages-1 is then issued into
-// the slot of row y-1.  Waits are cp.async.wait_group (no spinning).
-#ifndef LBM_RING_STAGES
-#define LBM_RING_STAGES 5
-#endif
-#ifndef LBM_STEP_MIN_BLOCKS
-#define LBM_STEP_MIN_BLOCKS 4
-#endif
-constexpr int kStages = LBM_RING_STAGES;
-
-template <typename P>
-struct Ring {
-    static constexpr int N = Vw<P>::N;
-    static constexpr int ROW = 32 * N;                  // values per plane row
-    static constexpr int HALO = 9 * ROW;                // offset of the halo values
-    static constexpr int SLOT = (9 * ROW + 18 + 3) / 4 * 4;   // values per slot, 16-byte multiple
-    static constexpr int WARP_BYTES = kStages * SLOT * (int)sizeof(P);
-};
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
-{
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-template <int BYTES>
-__device__ __forceinline__ void cp_async_small(void* smem, const void* gmem)
-{
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int K>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory"); }
-
-// Issue the copies of row r (-1 .. ny) of all planes into `slot`.
-template <typename P>
-__device__ __forceinline__ void ring_load(P* slot, const P* src, long long pl, long long pitch, int r, int segx,
-                                          int lane, bool has_left, bool has_right)
-{
-    using R = Ring<P>;
-    const P* row = src + (long long)(r + 1) * pitch + segx;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) cp_async16(slot + i * R::ROW + lane * R::N, row + i * pl + lane * R::N);
-    if (lane == 0 && has_left) {
-        // planes shifted along +x (1, 5, 8) pull the element left of the segment
-        cp_async_small<sizeof(P)>(slot + R::HALO + 2 * 1, row + 1 * pl - 1);
-        cp_async_small<sizeof(P)>(slot + R::HALO + 2 * 5, row + 5 * pl - 1);
-        cp_async_small<sizeof(P)>(slot + R::HALO + 2 * 8, row + 8 * pl - 1);
-    }
-    if (lane == 31 && has_right) {
-        // planes shifted along -x (3, 6, 7) pull the element right of the segment
-        cp_async_small<sizeof(P)>(slot + R::HALO + 2 * 3 + 1, row + 3 * pl + R::ROW);
-        cp_async_small<sizeof(P)>(slot + R::HALO + 2 * 6 + 1, row + 6 * pl + R::ROW);
-        cp_async_small<sizeof(P)>(slot + R::HALO + 2 * 7 + 1, row + 7 * pl + R::ROW);
-    }
-}
-
-template <typename P>
-__device__ __forceinline__ void lds(const P* p, P (&v)[Vw<P>::N]);
-template <>
-__device__ __forceinline__ void lds<float>(const float* p, float (&v)[4])
-{
-    const float4 t = *reinterpret_cast<const float4*>(p);
-    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
-}
-template <>
-__device__ __forceinline__ void lds<double>(const double* p, double (&v)[2])
-{
-    const double2 t = *reinterpret_cast<const double2*>(p);
-    v[0] = t.x; v[1] = t.y;
-}
-
-// Everything of one row after the pulls: wall closures, moments, the exact
-// saturated branch, deferral of Newton nodes to the job list, relaxation and
-// stores (Omega~_i = (1-omega) q_i + w_i c with c = theta' - (1-omega) m0).
-// Row outputs: straight to the plane rows in global memory, or to a row buffer
-// in shared memory that a TMA bulk store writes out.
-template <typename P, int N>
-struct GlobalRowOut {
-    P* row;          // dst + (y + 1) * pitch + x0
-    long long pl;
-    __device__ __forceinline__ void store(int i, const P (&o)[N]) const { stv_n(row + i * pl, o); }
-};
-
-template <typename P, int N, bool REC, bool EDGE, typename Out>
-__device__ __forceinline__ void row_update(const Problem& pb, int y, int x0, int lane, P (&qf)[9][N], const P (&u0)[N],
-                                           const P (&u1)[N], const P (&u2)[N], const P (&u3)[N], const P (&u4)[N],
-                                           const P (&u5)[N], const P (&u6)[N], const P (&u7)[N], const P (&u8)[N],
-                                           const Out& out, double* __restrict__ rec, Acc<P>& acc, TileSums& ts,
-                                           DevStats* st, int pi, NewtonJob* jobs, unsigned int* job_count, const P omc,
-                                           const float om_f, const double omc_d, const P (&wP)[3], const float thr_f,
-                                           const int nx, const int ny)
-{
-    const long long pitch = pb.pitch;
-    P c[N];          // per node: theta' - (1-omega) m0, rounded to P
-    double thn[REC ? N : 1];
-    bool newton_k[N];
-    typename M0T<P>::T m0[N];
-    bool any_wall = false;
-    bool dir_k[N];
-    int wall_k[N];
-#pragma unroll
-    for (int k = 0; k < N; ++k) { dir_k[k] = false; wall_k[k] = -1; }
-    if constexpr (EDGE) {
-#pragma unroll
-        for (int k = 0; k < N; ++k) {
-            const int x = x0 + k;
-            any_wall |= (x < nx) && (x == 0 || x == nx - 1 || y == 0 || y == ny - 1);
-        }
-    }
-    // EDGE = false: the caller knows the warp's row has no wall node and no node beyond nx
-    if (EDGE && __any_sync(kFull, any_wall)) {
-#pragma unroll
-        for (int k = 0; k < N; ++k) {
-            const int x = x0 + k;
-            if (x < nx && (x == 0 || x == nx - 1 || y == 0 || y == ny - 1)) {
-                P qq[9], uu[9];
-#pragma unroll
-                for (int i = 0; i < 9; ++i) qq[i] = qf[i][k];
-                uu[0] = u0[k]; uu[1] = u1[k]; uu[2] = u2[k]; uu[3] = u3[k]; uu[4] = u4[k];
-                uu[5] = u5[k]; uu[6] = u6[k]; uu[7] = u7[k]; uu[8] = u8[k];
-                if constexpr (sizeof(P) == 4) {
-                    const ff fl = wall_closure_f(qq, uu, x, y, pb, wall_k[k]);
-                    ff_add(ts.flux_f, fl.hi);
-                    ts.flux_f.lo += fl.lo;
-                } else {
-                    ts.flux += wall_closure_d(qq, uu, x, y, pb, wall_k[k]);
-                }
-                dir_k[k] = wall_k[k] >= 0;
-#pragma unroll
-                for (int i = 0; i < 9; ++i) qf[i][k] = qq[i];
-            }
-        }
-    }
-
-    bool any_newton = false;
-    float row_m0 = 0.f;   // FP32 form: sum of theta' = m0 over this lane's saturated nodes
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-        const int x = x0 + k;
-        const bool valid = !EDGE || x < nx;
-        const P u[9] = {u0[k], u1[k], u2[k], u3[k], u4[k], u5[k], u6[k], u7[k], u8[k]};
-        const float tf = approx_sum<P>(u);
-        float mf;
-        if constexpr (sizeof(P) == 4) {
-            // FP32 form: a plain FP32 sum (small weights first) decides saturation and
-            // gives theta' = m0 there, to the rounding of the stored populations; the
-            // float-float sum is formed only where it is needed (Newton and
-            // Dirichlet nodes)
-            mf = 0.f;
-#pragma unroll
-            for (int i = 8; i >= 0; --i) mf += qf[i][k];
-        } else {
-            m0_init(m0[k]);
-#pragma unroll
-            for (int i = 8; i >= 0; --i) m0_add(m0[k], qf[i][k]);
-            mf = m0_f(m0[k]);
-        }
-        const float marg = 1e-5f * (1.0f + fabsf(tf));
-        const bool sat_liq = tf >= thr_f + marg && mf >= thr_f + marg;
-        const bool sat_sol = tf <= -thr_f - marg && mf <= -thr_f - marg;
-        newton_k[k] = valid && !dir_k[k] && !(sat_liq || sat_sol);
-        any_newton |= newton_k[k];
-        if (!valid) {
-            c[k] = (P)0;
-            if constexpr (REC) thn[k] = 0.0;
-#pragma unroll
-            for (int i = 0; i < 9; ++i) qf[i][k] = (P)0;
-        } else if (dir_k[k]) {
-            // theta' = theta_D; c = theta_D - (1-omega) m0
-            const int wk = wall_k[k];
-            ts.dir_count[wk] += 1;
-            if constexpr (sizeof(P) == 4) {
-                ff mm;
-                m0_init(mm);
-#pragma unroll
-                for (int i = 8; i >= 0; --i) ff_add(mm, qf[i][k]);
-                const float oc = (float)omc;
-                c[k] = (P)((pb.wall_th_hi[wk] - oc * mm.hi) + (pb.wall_th_lo[wk] - oc * mm.lo));
-                acc.add_ff(ff{pb.wall_th_hi[wk], pb.wall_th_lo[wk]});
-            } else {
-                c[k] = (P)(pb.wall_theta[wk] - omc_d * m0_d(m0[k]));
-                acc.add_d(pb.wall_theta[wk]);
-            }
-            if constexpr (REC) thn[k] = pb.wall_theta[wk];
-        } else if (!newton_k[k]) {
-            // saturated: theta' = m0, no source; c = omega * m0
-            if constexpr (sizeof(P) == 4) {
-                c[k] = (P)(om_f * mf);
-                row_m0 += mf;
-                if constexpr (REC) thn[k] = (double)mf;
-            } else {
-                const double md = m0_d(m0[k]);
-                c[k] = (P)(pb.omega * md);
-                acc.add_d(md);
-                if constexpr (REC) thn[k] = md;
-            }
-            ts.liquid += sat_liq ? 1 : 0;
-        }
-    }
-    if constexpr (sizeof(P) == 4) acc.add_ff(ff{row_m0, 0.f});
-    if (__any_sync(kFull, any_newton)) {
-        // The local Newton solve of these nodes is deferred to the job kernel,
-        // which spreads the FP64 work of the front band over the whole GPU:
-        // append (m0, theta) to the job list and store q_i unrelaxed.
-        int cnt = 0;
-#pragma unroll
-        for (int k = 0; k < N; ++k) cnt += newton_k[k] ? 1 : 0;
-        int incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += v;
-        }
-        const int total = __shfl_sync(kFull, incl, 31);
-        unsigned base = 0;
-        if (lane == 0) base = atomicAdd(job_count, (unsigned)total);
-        base = __shfl_sync(kFull, base, 0);
-        unsigned slot = base + (unsigned)(incl - cnt);
-#pragma unroll
-        for (int k = 0; k < N; ++k) {
-            if (!newton_k[k]) continue;
-            const P u[9] = {u0[k], u1[k], u2[k], u3[k], u4[k], u5[k], u6[k], u7[k], u8[k]};
-            NewtonJob jb;
-            jb.prob = pi;
-            jb.node = y * nx + x0 + k;
-            if constexpr (sizeof(P) == 4) {
-                ff t, mm;
-                m0_init(t);
-                m0_init(mm);
-#pragma unroll
-                for (int i = 8; i >= 0; --i) {
-                    ff_add(t, u[i]);
-                    ff_add(mm, qf[i][k]);
-                }
-                float* pm = reinterpret_cast<float*>(&jb.m0);
-                float* pt = reinterpret_cast<float*>(&jb.theta);
-                pm[0] = mm.hi; pm[1] = mm.lo;
-                pt[0] = t.hi; pt[1] = t.lo;
-            } else {
-                double th = 0.0;
-#pragma unroll
-                for (int i = 8; i >= 0; --i) th += u[i];
-                jb.m0 = m0_d(m0[k]);
-                jb.theta = th;
-            }
-            jobs[slot] = jb;
-            ++slot;
-            c[k] = (P)0;
-            if constexpr (REC) thn[k] = 0.0;
-        }
-    }
-
-    // Omega~_i = (1-omega) q_i + w_i c
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const P wi = i == 0 ? wP[0] : (i <= 4 ? wP[1] : wP[2]);
-        P o[N];
-#pragma unroll
-        for (int k = 0; k < N; ++k) o[k] = newton_k[k] ? qf[i][k] : fma(omc, qf[i][k], wi * c[k]);
-        out.store(i, o);
-    }
-    if constexpr (REC) {
-        st_rec<N>(rec + (long long)y * pitch + x0, thn);
-    }
-
-}
-
-// EEBM row update (Algorithm 2 in the stored-Omega form): after the pulls and
-// the closures (Dirichlet target M0(q) = H(theta_D)), H = M0(q) is the
-// enthalpy, theta = Theta(H), and the collision relaxes toward the modified
-// equilibrium, Omega~_i = (1-omega) q_i + omega w_i theta for i != 0 and
-// Omega~_0 = (1-omega) q_0 + omega (H - (1-w_0) theta).  No Newton node; the
-// energy is the sum of H.
-template <typename P, int N, bool REC, bool EDGE, typename Out>
-__device__ __forceinline__ void row_update_eebm(const Problem& pb, int y, int x0, P (&qf)[9][N], const P (&u0)[N],
-                                                const P (&u1)[N], const P (&u2)[N], const P (&u3)[N],
-                                                const P (&u4)[N], const P (&u5)[N], const P (&u6)[N],
-                                                const P (&u7)[N], const P (&u8)[N], const Out& out,
-                                                double* __restrict__ rec, Acc<P>& acc, TileSums& ts, const P omc,
-                                                const P (&wP)[3], const int nx, const int ny)
-{
-    const long long pitch = pb.pitch;
-    if constexpr (EDGE) {
-        bool any_wall = false;
-#pragma unroll
-        for (int k = 0; k < N; ++k) {
-            const int x = x0 + k;
-            any_wall |= (x < nx) && (x == 0 || x == nx - 1 || y == 0 || y == ny - 1);
-        }
-        if (__any_sync(kFull, any_wall)) {
-#pragma unroll
-            for (int k = 0; k < N; ++k) {
-                const int x = x0 + k;
-                if (x < nx && (x == 0 || x == nx - 1 || y == 0 || y == ny - 1)) {
-                    P qq[9], uu[9];
-                    int wall;
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) qq[i] = qf[i][k];
-                    uu[0] = u0[k]; uu[1] = u1[k]; uu[2] = u2[k]; uu[3] = u3[k]; uu[4] = u4[k];
-                    uu[5] = u5[k]; uu[6] = u6[k]; uu[7] = u7[k]; uu[8] = u8[k];
-                    if constexpr (sizeof(P) == 4) {
-                        const ff fl = wall_closure_f(qq, uu, x, y, pb, wall);
-                        ff_add(ts.flux_f, fl.hi);
-                        ts.flux_f.lo += fl.lo;
-                    } else {
-                        ts.flux += wall_closure_d(qq, uu, x, y, pb, wall);
-                    }
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) qf[i][k] = qq[i];
-                }
-            }
-        }
-    }
-    const P om = (P)1 - omc;
-    const P inv_ste = (P)pb.inv_ste;
-    P hs = 0;
-    double thn[REC ? N : 1];
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-        const bool valid = !EDGE || x0 + k < nx;
-        P H = 0;
-#pragma unroll
-        for (int i = 8; i >= 0; --i) H += qf[i][k];
-        if (!valid) {
-            H = 0;
-#pragma unroll
-            for (int i = 0; i < 9; ++i) qf[i][k] = (P)0;
-        }
-        const P th = eebm_theta(H, inv_ste);
-        hs += H;
-        if constexpr (REC) thn[k] = (double)th;
-        qf[0][k] = fma(omc, qf[0][k], om * (H - ((P)1 - wP[0]) * th));
-#pragma unroll
-        for (int i = 1; i < 9; ++i) qf[i][k] = fma(omc, qf[i][k], om * (i <= 4 ? wP[1] : wP[2]) * th);
-    }
-    if constexpr (sizeof(P) == 4) acc.add_ff(ff{hs, 0.f});
-    else acc.add_d(hs);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        P o[N];
-#pragma unroll
-        for (int k = 0; k < N; ++k) o[k] = qf[i][k];
-        out.store(i, o);
-    }
-    if constexpr (REC) st_rec<N>(rec + (long long)y * pitch + x0, thn);
-}
-
-// One warp tile: segment `seg` of problem pb, rows [ya, yb).
-template <typename P, bool REC>
-__device__ __forceinline__ void d2q9_tile(const Problem& pb, const P* __restrict__ src, P* __restrict__ dst,
-                                          double* __restrict__ rec, int seg, int ya, int yb, Acc<P>& acc,
-                                          TileSums& ts, DevStats* st, P* ring, int pi, NewtonJob* jobs,
-                                          unsigned int* job_count)
-{
-    using R = Ring<P>;
-    constexpr int N = R::N;
-    const int lane = threadIdx.x & 31;
-    const int segx = seg * 32 * N;
-    const int x0 = segx + lane * N;
-    const long long pl = pb.plane;
-    const long long pitch = pb.pitch;
-    const bool has_left = segx > 0;
-    const bool has_right = segx + 32 * N < pb.nx;
-    // problem constants, converted once per tile (the compiler cannot hoist loads
-    // of *pb above the stores of the loop, and a conversion from FP64 costs an
-    // FP64-pipe instruction on this GPU)
-    const P omc = (P)(1.0 - pb.omega);
-    const float om_f = (float)pb.omega;
-    const double omc_d = 1.0 - pb.omega;
-    const double inv_delta = pb.inv_delta;
-    const int nx = pb.nx, ny = pb.ny;
-    const P wP[3] = {(P)d2_w(0), (P)d2_w(1), (P)d2_w(5)};
-    const float thr_f = (float)pb.sat;
-
-    // prologue: rows ya-1 .. ya+kStages-2 (one per slot), one commit group per row.
-    // Iteration y then needs rows <= y+1 and leaves rows y+2 .. y+kStages-2 in
-    // flight (wait_group kStages-3); it refills the slot of row y-1 with row y+kStages-1.
-#pragma unroll
-    for (int s = 0; s < kStages; ++s) {
-        const int r = ya - 1 + s;
-        if (r <= yb) ring_load<P>(ring + ((r + 1) % kStages) * R::SLOT, src, pl, pitch, r, segx, lane, has_left, has_right);
-        cp_async_commit();
-    }
-
-    for (int y = ya; y < yb; ++y) {
-        cp_async_wait<kStages - 3>();   // rows <= y+1 have landed (for this lane)
-        __syncwarp();                   // ... and for every lane of the warp
-        const P* sm1 = ring + ((y) % kStages) * R::SLOT;        // row y-1  (slot index (r+1) % S)
-        const P* s0 = ring + ((y + 1) % kStages) * R::SLOT;     // row y
-        const P* sp1 = ring + ((y + 2) % kStages) * R::SLOT;    // row y+1
-
-        P u0[N], u1[N], u2[N], u3[N], u4[N], u5[N], u6[N], u7[N], u8[N];
-        lds<P>(s0 + 0 * R::ROW + lane * N, u0);
-        lds<P>(s0 + 1 * R::ROW + lane * N, u1);
-        lds<P>(s0 + 2 * R::ROW + lane * N, u2);
-        lds<P>(s0 + 3 * R::ROW + lane * N, u3);
-        lds<P>(s0 + 4 * R::ROW + lane * N, u4);
-        lds<P>(s0 + 5 * R::ROW + lane * N, u5);
-        lds<P>(s0 + 6 * R::ROW + lane * N, u6);
-        lds<P>(s0 + 7 * R::ROW + lane * N, u7);
-        lds<P>(s0 + 8 * R::ROW + lane * N, u8);
-
-        P qf[9][N];
-        {
-            P t[N], s[N];
-#pragma unroll
-            for (int k = 0; k < N; ++k) qf[0][k] = u0[k];
-            from_left<P, N>(u1, s0[R::HALO + 2 * 1], lane, s);
-#pragma unroll
-            for (int k = 0; k < N; ++k) qf[1][k] = s[k];
-            from_right<P, N>(u3, s0[R::HALO + 2 * 3 + 1], lane, s);
-#pragma unroll
-            for (int k = 0; k < N; ++k) qf[3][k] = s[k];
-            lds<P>(sm1 + 2 * R::ROW + lane * N, t);
-#pragma unroll
-            for (int k = 0; k < N; ++k) qf[2][k] = t[k];
-            lds<P>(sm1 + 5 * R::ROW + lane * N, t);
-            from_left<P, N>(t, sm1[R::HALO + 2 * 5], lane, s);
-#pragma unroll
-            for (int k = 0; k < N; ++k) qf[5][k] = s[k];
-            lds<P>(sm1 + 6 * R::ROW + lane * N, t);
-            from_right<P, N>(t, sm1[R::HALO + 2 * 6 + 1], lane, s);
-#pragma unroll
-            for (int k = 0; k < N; ++k) qf[6][k] = s[k];
-            lds<P>(sp1 + 4 * R::ROW + lane * N, t);
-#pragma unroll
-            for (int k = 0; k < N; ++k) qf[4][k] = t[k];
-            lds<P>(sp1 + 7 * R::ROW + lane * N, t);
-            from_right<P, N>(t, sp1[R::HALO + 2 * 7 + 1], lane, s);
-#pragma unroll
-            for (int k = 0; k < N; ++k) qf[7][k] = s[k];
-            lds<P>(sp1 + 8 * R::ROW + lane * N, t);
-            from_left<P, N>(t, sp1[R::HALO + 2 * 8], lane, s);
-#pragma unroll
-            for (int k = 0; k < N; ++k) qf[8][k] = s[k];
-        }
-
-        // every lane has its values of row y-1 in registers: refill that slot with
-        // row y+kStages-1 now, so the load overlaps this row's arithmetic
-        __syncwarp();
-        {
-            const int rn = y + kStages - 1;
-            if (rn <= yb) ring_load<P>(ring + ((rn + 1) % kStages) * R::SLOT, src, pl, pitch, rn, segx, lane, has_left, has_right);
-            cp_async_commit();
-        }
-        if (pb.method == 1)
-            row_update_eebm<P, N, REC, true>(pb, y, x0, qf, u0, u1, u2, u3, u4, u5, u6, u7, u8,
-                                             GlobalRowOut<P, N>{dst + (long long)(y + 1) * pitch + x0, pl}, rec, acc,
-                                             ts, omc, wP, nx, ny);
-        else
-            row_update<P, N, REC, true>(pb, y, x0, lane, qf, u0, u1, u2, u3, u4, u5, u6, u7, u8,
-                                        GlobalRowOut<P, N>{dst + (long long)(y + 1) * pitch + x0, pl}, rec, acc, ts, st,
-                                        pi, jobs, job_count, omc, om_f, omc_d, wP, thr_f, nx, ny);
-
-    }
-    cp_async_wait<0>();
-    __syncwarp();
 }
 
 // ---------------------------------------------------------------- direct tile
@@ -688,9 +63,9 @@ __device__ __forceinline__ void ldg_n(const double* p, double (&v)[1]) { v[0] = 
 template <typename P, bool REC>
 __device__ __forceinline__ void d2q9_tile_direct(const Problem& pb, const P* __restrict__ src, P* __restrict__ dst,
                                                  double* __restrict__ rec, int seg, int ya, int yb, Acc<P>& acc,
-                                                 TileSums& ts, DevStats* st, int pi, NewtonJob* jobs,
-                                                 unsigned int* job_count)
+                                                 TileSums& ts, int pi, NewtonJob* jobs, unsigned int* job_count)
 {
+    GlobalJobSink sink{jobs, job_count};
     constexpr int N = Vd<P>::N;
     const int lane = threadIdx.x & 31;
     const int segx = seg * 32 * N;
@@ -783,11 +158,11 @@ __device__ __forceinline__ void d2q9_tile_direct(const Problem& pb, const P* __r
         else if (seg_interior && y > 0 && y < ny - 1)
             row_update<P, N, REC, false>(pb, y, x0, lane, qf, cur.r0, cur.r1, cur.c2, cur.r3, cu4, cur.c5, cur.c6, cu7,
                                          cu8, GlobalRowOut<P, N>{dst + (long long)(y + 1) * pitch + x0, pl}, rec, acc,
-                                         ts, st, pi, jobs, job_count, omc, om_f, omc_d, wP, thr_f, nx, ny);
+                                         ts, pi, sink, omc, om_f, omc_d, wP, thr_f, nx, ny);
         else
             row_update<P, N, REC, true>(pb, y, x0, lane, qf, cur.r0, cur.r1, cur.c2, cur.r3, cu4, cur.c5, cur.c6, cu7,
                                         cu8, GlobalRowOut<P, N>{dst + (long long)(y + 1) * pitch + x0, pl}, rec, acc,
-                                        ts, st, pi, jobs, job_count, omc, om_f, omc_d, wP, thr_f, nx, ny);
+                                        ts, pi, sink, omc, om_f, omc_d, wP, thr_f, nx, ny);
         // roll the register window
 #pragma unroll
         for (int k = 0; k < N; ++k) { up2[k] = cur.c2[k]; cu4[k] = cur.n4[k]; cu7[k] = cur.n7[k]; cu8[k] = cur.n8[k]; }
@@ -801,20 +176,9 @@ __device__ __forceinline__ void d2q9_tile_direct(const Problem& pb, const P* __r
     }
 }
 
-#ifndef LBM_STEP_DIRECT
-#define LBM_STEP_DIRECT 1
-#endif
-
-
-
-
 template <typename P, bool REC>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, LBM_STEP_MIN_BLOCKS) d2q9_step_kernel(StepArgs a)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) d2q9_step_kernel(StepArgs a)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    using R = Ring<P>;
-    const int wib = threadIdx.x >> 5;
-    P* ring = reinterpret_cast<P*>(smem + wib * R::WARP_BYTES);
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -838,14 +202,259 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, LBM_STEP_MIN_BLOCKS) d2q9
         P* dst = static_cast<P*>(pb.state[a.parity ^ 1]);
         Acc<P> acc;
         TileSums ts;
-#if LBM_STEP_DIRECT
-        d2q9_tile_direct<P, REC>(pb, src, dst, a.rec, seg, ya, yb, acc, ts, st, pi, a.jobs, a.job_count);
-#else
-        d2q9_tile<P, REC>(pb, src, dst, a.rec, seg, ya, yb, acc, ts, st, ring, pi, a.jobs, a.job_count);
-#endif
+        d2q9_tile_direct<P, REC>(pb, src, dst, a.rec, seg, ya, yb, acc, ts, pi, a.jobs, a.job_count);
         flush_tile_sums<P>(acc, ts, st, lane);
     }
     // statistics are published by the job kernel that follows every step
+}
+
+// ---------------------------------------------------------------- flat step
+// Single-problem FP32 step.  A tile is 128 columns x 8 rows; a block (8
+// warps) computes one tile at a time, one row per warp, four consecutive
+// columns per lane; blocks take tiles grid-stride (a persistent grid of the
+// resident blocks, strips of one row band before the next band).  Every pull
+// is a read-only load from global memory: for row y a lane loads the nine
+// planes of row y (its four columns; one 128-bit load each), planes 2, 5, 6
+// of row y - 1 and 4, 7, 8 of row y + 1, and the six elements just left or
+// right of its columns that the diagonal and horizontal pulls need.  The
+// rows above and below are also loaded by the neighbouring warps and tiles at
+// about the same time, so L1 and L2 serve them and DRAM sees each population
+// read once.  No shared memory, no barrier inside the loop: many independent
+// 128-bit loads per thread keep the memory system busy.  Loads left of column
+// 0 or right of the last column read other rows' elements; they only feed
+// directions that the wall closures replace.  The energy and node-count sums
+// of a block are combined once per launch.
+// The loads of one row of the flat step: the nine planes of row y (u), and
+// the pulled values q_i(x) = Omega_i(x - e_i) (qf), for four columns x0..x0+3.
+__device__ __forceinline__ void flat_load_row(const float* __restrict__ row, long long pitch, long long pl,
+                                              float (&u)[9][4], float (&qf)[9][4])
+{
+    const float* up = row - pitch;   // row y - 1
+    const float* dn = row + pitch;   // row y + 1
+#pragma unroll
+    for (int i = 0; i < 9; ++i) ldg4(row + i * pl, u[i]);
+    float a2[4], a5[4], a6[4], b4[4], b7[4], b8[4];
+    ldg4(up + 2 * pl, a2);
+    ldg4(up + 5 * pl, a5);
+    ldg4(up + 6 * pl, a6);
+    ldg4(dn + 4 * pl, b4);
+    ldg4(dn + 7 * pl, b7);
+    ldg4(dn + 8 * pl, b8);
+    const float e1 = __ldg(row + 1 * pl - 1);   // Omega_1(x0 - 1, y)
+    const float e3 = __ldg(row + 3 * pl + 4);   // Omega_3(x0 + 4, y)
+    const float e5 = __ldg(up + 5 * pl - 1);    // Omega_5(x0 - 1, y - 1)
+    const float e6 = __ldg(up + 6 * pl + 4);    // Omega_6(x0 + 4, y - 1)
+    const float e7 = __ldg(dn + 7 * pl + 4);    // Omega_7(x0 + 4, y + 1)
+    const float e8 = __ldg(dn + 8 * pl - 1);    // Omega_8(x0 - 1, y + 1)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        qf[0][k] = u[0][k];
+        qf[2][k] = a2[k];
+        qf[4][k] = b4[k];
+    }
+    qf[1][0] = e1; qf[1][1] = u[1][0]; qf[1][2] = u[1][1]; qf[1][3] = u[1][2];
+    qf[3][0] = u[3][1]; qf[3][1] = u[3][2]; qf[3][2] = u[3][3]; qf[3][3] = e3;
+    qf[5][0] = e5; qf[5][1] = a5[0]; qf[5][2] = a5[1]; qf[5][3] = a5[2];
+    qf[6][0] = a6[1]; qf[6][1] = a6[2]; qf[6][2] = a6[3]; qf[6][3] = e6;
+    qf[7][0] = b7[1]; qf[7][1] = b7[2]; qf[7][2] = b7[3]; qf[7][3] = e7;
+    qf[8][0] = e8; qf[8][1] = b8[0]; qf[8][2] = b8[1]; qf[8][3] = b8[2];
+}
+
+#ifndef LBM_FLAT_PERSIST
+#define LBM_FLAT_PERSIST 0   // 1: grid of the resident blocks, tiles grid-stride; 0: one tile per block
+#endif
+#ifndef LBM_FLAT_MINB
+#define LBM_FLAT_MINB 3   // resident blocks per SM the register budget is fitted to
+#endif
+// Interior rows: strips 1 .. nsegs-2 (no wall column, no padding column),
+// rows 1 .. ny-2; IREBM (Algorithm 3) or, with EEBM, Algorithm 2.  Tile t: strip 1 + t % (nsegs - 2), rows 8 (t / (nsegs - 2))
+// + warp.  The other rows are computed by d2q9_edge_kernel.
+template <bool REC, bool EEBM>
+__global__ void __launch_bounds__(256, LBM_FLAT_MINB) d2q9_flat_kernel(const StepArgs a)
+{
+    __shared__ WarpSums wsum[8];
+    const Problem& pb = a.probs[0];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nx = pb.nx, ny = pb.ny;
+    const long long pl = pb.plane, pitch = pb.pitch;
+    const int nin = pb.pitch / 128 - 2;   // interior strips (>= 1, or the kernel is not launched)
+    const int ntiles = nin * ((ny + 7) / 8);
+    const float* __restrict__ src = static_cast<const float*>(pb.state[a.parity]);
+    float* __restrict__ dst = static_cast<float*>(pb.state[a.parity ^ 1]);
+    const float omc = (float)(1.0 - pb.omega);
+    const float om_f = (float)pb.omega;
+    const float wP[3] = {(float)d2_w(0), (float)d2_w(1), (float)d2_w(5)};
+    const float thr_f = (float)pb.sat;
+    Acc<float> acc;
+    TileSums ts;
+    GlobalJobSink sink{a.jobs, a.job_count};
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int seg = 1 + t % nin;
+        const int y = (t / nin) * 8 + warp;
+        if (y < 1 || y >= ny - 1) continue;
+        const int x0 = seg * 128 + 4 * lane;
+        const float* row = src + (y + 1) * pitch + x0;
+        float* orow = dst + (y + 1) * pitch + x0;
+        if constexpr (EEBM) {
+            float u[9][4], qf[9][4];
+            flat_load_row(row, pitch, pl, u, qf);
+            row_update_eebm<float, 4, REC, false>(pb, y, x0, qf, u[0], u[1], u[2], u[3], u[4], u[5], u[6], u[7], u[8],
+                                                  GlobalRowOut<float, 4>{orow, pl}, a.rec, acc, ts, omc, wP, nx, ny);
+            continue;
+        }
+        // interior IREBM row: the arithmetic of row_update's interior branch
+        // (same operations, same order), with nothing else live
+        float u[9][4], qf[9][4];
+        flat_load_row(row, pitch, pl, u, qf);
+        float c[4];
+        bool newton[4];
+        bool any_newton = false;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float uk[9] = {u[0][k], u[1][k], u[2][k], u[3][k], u[4][k], u[5][k], u[6][k], u[7][k], u[8][k]};
+            const float tf = approx_sum<float>(uk);
+            float mf = 0.f;
+#pragma unroll
+            for (int i = 8; i >= 0; --i) mf += qf[i][k];
+            const float marg = 1e-5f * (1.0f + fabsf(tf));
+            const bool sat_liq = tf >= thr_f + marg && mf >= thr_f + marg;
+            const bool sat_sol = tf <= -thr_f - marg && mf <= -thr_f - marg;
+            newton[k] = !(sat_liq || sat_sol);
+            any_newton |= newton[k];
+            c[k] = newton[k] ? 0.f : om_f * mf;
+            if (!newton[k]) {
+                acc.add_f(mf);
+                ts.liquid += sat_liq ? 1 : 0;
+            }
+        }
+        float wc[3][4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            wc[0][k] = wP[0] * c[k];
+            wc[1][k] = wP[1] * c[k];
+            wc[2][k] = wP[2] * c[k];
+        }
+        if (__any_sync(kFull, any_newton)) {
+            // nodes that need the local Newton solve: stored unrelaxed, their
+            // index appended to the job list (the job kernel forms m0, theta)
+            int cnt = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) cnt += newton[k] ? 1 : 0;
+            int incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const unsigned base = sink.reserve((unsigned)__shfl_sync(kFull, incl, 31), lane);
+            unsigned slot = base + (unsigned)(incl - cnt);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (newton[k]) {
+                    NewtonJob jb;
+                    jb.prob = 0;
+                    jb.node = y * nx + x0 + k;
+                    jb.m0 = jb.theta = 0.0;
+                    sink.put(slot++, jb);
+                }
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const int cl = i == 0 ? 0 : (i <= 4 ? 1 : 2);
+                float o[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) o[k] = newton[k] ? qf[i][k] : fmaf(omc, qf[i][k], wc[cl][k]);
+                stv_n(orow + i * pl, o);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const int cl = i == 0 ? 0 : (i <= 4 ? 1 : 2);
+                float o[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) o[k] = fmaf(omc, qf[i][k], wc[cl][k]);
+                stv_n(orow + i * pl, o);
+            }
+        }
+        if constexpr (REC) {
+            double thn[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float mf = 0.f;
+#pragma unroll
+                for (int i = 8; i >= 0; --i) mf += qf[i][k];
+                thn[k] = newton[k] ? 0.0 : (double)mf;
+            }
+            st_rec<4>(a.rec + (long long)y * pitch + x0, thn);
+        }
+    }
+    const WarpSums w = warp_tile_sums<float>(acc, ts);
+    if (lane == 0) wsum[warp] = w;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        WarpSums tot = wsum[0];
+        for (int k = 1; k < 8; ++k) add_sums(tot, wsum[k]);
+        emit_sums(tot, &a.stats[pb.stats]);
+    }
+}
+
+// Rows of the single-problem FP32 step that touch a wall: every row of the
+// first and last 128-column strips, and rows 0 and ny-1 of the other strips;
+// one row per warp, the full row update (closures of Sec. 4.2, Newton
+// hand-off, EEBM).  Runs alongside d2q9_flat_kernel (both read the source
+// state and write disjoint rows).
+template <bool REC>
+__global__ void __launch_bounds__(256) d2q9_edge_kernel(const StepArgs a)
+{
+    __shared__ WarpSums wsum[8];
+    const Problem& pb = a.probs[0];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nx = pb.nx, ny = pb.ny;
+    const long long pl = pb.plane, pitch = pb.pitch;
+    const int nsegs = pb.pitch / 128;
+    const int nside = nsegs >= 2 ? 2 : 1;                  // wall strips
+    const int nin = nsegs - nside;                          // other strips: rows 0 and ny-1
+    const int nrows = nside * ny + nin * (ny > 1 ? 2 : 1);
+    const float* __restrict__ src = static_cast<const float*>(pb.state[a.parity]);
+    float* __restrict__ dst = static_cast<float*>(pb.state[a.parity ^ 1]);
+    const float omc = (float)(1.0 - pb.omega);
+    const float om_f = (float)pb.omega;
+    const double omc_d = 1.0 - pb.omega;
+    const float wP[3] = {(float)d2_w(0), (float)d2_w(1), (float)d2_w(5)};
+    const float thr_f = (float)pb.sat;
+    Acc<float> acc;
+    TileSums ts;
+    GlobalJobSink sink{a.jobs, a.job_count};
+    for (int r = blockIdx.x * 8 + warp; r < nrows; r += gridDim.x * 8) {
+        int seg, y;
+        if (r < nside * ny) {
+            seg = r < ny ? 0 : nsegs - 1;
+            y = r % ny;
+        } else {
+            const int j = r - nside * ny;
+            seg = 1 + j % nin;
+            y = (j / nin) == 0 ? 0 : ny - 1;
+        }
+        const int x0 = seg * 128 + 4 * lane;
+        float u[9][4], qf[9][4];
+        flat_load_row(src + (y + 1) * pitch + x0, pitch, pl, u, qf);
+        const GlobalRowOut<float, 4> out{dst + (y + 1) * pitch + x0, pl};
+        if (pb.method == 1)
+            row_update_eebm<float, 4, REC, true>(pb, y, x0, qf, u[0], u[1], u[2], u[3], u[4], u[5], u[6], u[7], u[8],
+                                                 out, a.rec, acc, ts, omc, wP, nx, ny);
+        else
+            row_update<float, 4, REC, true>(pb, y, x0, lane, qf, u[0], u[1], u[2], u[3], u[4], u[5], u[6], u[7], u[8],
+                                            out, a.rec, acc, ts, 0, sink, omc, om_f, omc_d, wP, thr_f, nx, ny);
+    }
+    const WarpSums w = warp_tile_sums<float>(acc, ts);
+    if (lane == 0) wsum[warp] = w;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        WarpSums tot = wsum[0];
+        for (int k = 1; k < 8; ++k) add_sums(tot, wsum[k]);
+        emit_sums(tot, &a.stats[pb.stats]);
+    }
 }
 
 // ---------------------------------------------------------------- TMA row pipeline
@@ -961,6 +570,7 @@ __global__ void __launch_bounds__(kTmaThreads, LBM_TMA_MIN_BLOCKS) d2q9_tma_kern
     const long long pitch = pb.pitch;
     Acc<float> acc;
     TileSums ts;
+    GlobalJobSink sink{a.jobs, a.job_count};
     auto wait_row = [&](int r) -> bool {
         const int k = r - (ya - 1);
         return mbar_wait_bounded(&full[k % kTmaStages], (unsigned)((k / kTmaStages) & 1));
@@ -996,10 +606,10 @@ __global__ void __launch_bounds__(kTmaThreads, LBM_TMA_MIN_BLOCKS) d2q9_tma_kern
                                                  omc, wP, nx, ny);
         else if (warp_interior_x && y > 0 && y < ny - 1)
             row_update<float, 1, REC, false>(pb, y, x, lane, qf, u0, u1, u2, u3, u4, u5, u6, u7, u8, out, a.rec, acc,
-                                             ts, st, pi, a.jobs, a.job_count, omc, om_f, omc_d, wP, thr_f, nx, ny);
+                                             ts, pi, sink, omc, om_f, omc_d, wP, thr_f, nx, ny);
         else
             row_update<float, 1, REC, true>(pb, y, x, lane, qf, u0, u1, u2, u3, u4, u5, u6, u7, u8, out, a.rec, acc,
-                                            ts, st, pi, a.jobs, a.job_count, omc, om_f, omc_d, wP, thr_f, nx, ny);
+                                            ts, pi, sink, omc, om_f, omc_d, wP, thr_f, nx, ny);
     }
     if (!ok && lane == 0) atomicExch(&st->error, 4);   // LBM_ERR_TIMEOUT
     flush_tile_sums<float>(acc, ts, st, lane);
@@ -1023,61 +633,12 @@ __global__ void __launch_bounds__(128) newton_jobs_kernel(JobArgs a)
     const unsigned nw = (gridDim.x * blockDim.x) >> 5;
     for (unsigned base = gw * 32; base < count; base += nw * 32) {
         const unsigned j = base + lane;
-        int sidx = -1, it = 0;
-        Fx e{0, 0ull};
+        NewtonResult r;
         if (j < count) {
             const NewtonJob jb = a.jobs[j];
-            const Problem& pb = a.probs[jb.prob];
-            sidx = pb.stats;
-            double m0, th;
-            if constexpr (sizeof(P) == 4) {
-                const float* pm = reinterpret_cast<const float*>(&jb.m0);
-                const float* pt = reinterpret_cast<const float*>(&jb.theta);
-                m0 = (double)pm[0] + (double)pm[1];
-                th = (double)pt[0] + (double)pt[1];
-            } else {
-                m0 = jb.m0;
-                th = jb.theta;
-            }
-            const double pth = phi_of(th, pb.inv_delta);
-            const NewtonOut nr = newton_mixed(m0, th, pth, pb);
-            if (!nr.ok || !isfinite(nr.root)) atomicOr(&a.stats[sidx].error, 3);
-            const double tn = m0 + (pth - nr.phi_root) * pb.inv_ste;
-            const P c = (P)(tn - (1.0 - pb.omega) * m0);
-            const P omc = (P)(1.0 - pb.omega);
-            const int x = jb.node % pb.nx, y = jb.node / pb.nx;
-            P* d = static_cast<P*>(pb.state[a.parity ^ 1]) + (long long)(y + 1) * pb.pitch + x;
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const P wi = (P)lat_w(Q, i);
-                d[i * pb.plane] = fma(omc, d[i * pb.plane], wi * c);
-            }
-            if (REC) a.rec[(long long)y * pb.pitch + x] = tn;
-            e = to_fixed(tn + nr.phi_root * pb.inv_ste);
-            it = nr.iters;
+            r = newton_job_apply<P, REC, Q>(jb, a.probs[jb.prob], a.parity, a.rec, a.stats);
         }
-        // lanes of the same problem: the lowest lane sums them exactly and adds once
-        const unsigned grp = __match_any_sync(kFull, sidx);
-        const int leader = __ffs(grp) - 1;
-        Fx sum{0, 0ull};
-        int n = 0, mx = 0;
-        for (int l = 0; l < 32; ++l) {
-            Fx v;
-            v.hi = __shfl_sync(kFull, e.hi, l);
-            v.lo = __shfl_sync(kFull, e.lo, l);
-            const int vi = __shfl_sync(kFull, it, l);
-            if ((grp >> l) & 1) {
-                fx_add(sum, v);
-                ++n;
-                mx = max(mx, vi);
-            }
-        }
-        if (lane == leader && sidx >= 0) {
-            DevStats* st = &a.stats[sidx];
-            acc_add_fx(&st->cur_energy, sum);
-            atomicAdd(&st->cur_newton, (unsigned long long)n);
-            atomicMax(&st->cur_maxit, mx);
-        }
+        newton_group_add(r, a.stats);
     }
     // last block: publish every problem's step statistics, clear the job list
     __shared__ bool last;
@@ -1099,31 +660,14 @@ __global__ void __launch_bounds__(128) newton_jobs_kernel(JobArgs a)
     }
 }
 
-template <typename P>
-constexpr int step_smem_bytes()
-{
-    return LBM_STEP_DIRECT ? 0 : kWarpsPerBlock * Ring<P>::WARP_BYTES;
-}
-
 template <typename P, bool REC>
 static cudaError_t launch_t(const StepArgs& a, int grid, cudaStream_t s)
 {
-    constexpr int sm = step_smem_bytes<P>();
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(d2q9_step_kernel<P, REC>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    d2q9_step_kernel<P, REC><<<grid, kWarpsPerBlock * 32, sm, s>>>(a);
+    d2q9_step_kernel<P, REC><<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
     return cudaGetLastError();
 }
 
-int d2q9_segment_width(int precision)
-{
-    if (LBM_STEP_DIRECT) return precision == 1 ? 32 * Vd<float>::N : 32 * Vd<double>::N;
-    return precision == 1 ? 32 * 4 : 32 * 2;
-}
+int d2q9_segment_width(int precision) { return precision == 1 ? 32 * Vd<float>::N : 32 * Vd<double>::N; }
 
 cudaError_t launch_d2q9_step(int precision, const StepArgs& a, int grid, cudaStream_t s)
 {
@@ -1139,6 +683,59 @@ cudaError_t launch_d2q9_tma(const StepArgs& a, const TmaMaps& m, cudaStream_t s)
     if (a.rec) d2q9_tma_kernel<true><<<grid, kTmaThreads, 0, s>>>(a, m);
     else d2q9_tma_kernel<false><<<grid, kTmaThreads, 0, s>>>(a, m);
     return cudaGetLastError();
+}
+
+cudaError_t launch_d2q9_flat(const StepArgs& a, int nsegs, int ny, int method, cudaStream_t s, cudaStream_t side,
+                             cudaEvent_t fork, cudaEvent_t join)
+{
+    static int grid[64] = {0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidValue;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (!grid[dev]) {
+        int n = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, d2q9_flat_kernel<false, false>, 256, 0);
+        grid[dev] = sms * (n > 0 ? n : 1);
+    }
+    // rows that touch a wall: on the side stream when one is given, in
+    // parallel with the interior rows (they write disjoint rows)
+    const int nside = nsegs >= 2 ? 2 : 1;
+    const int nrows = nside * ny + (nsegs - nside) * (ny > 1 ? 2 : 1);
+    const int ge = std::min((nrows + 7) / 8, sms * 4);
+    cudaStream_t es = s;
+    if (side && fork && join) {
+        e = cudaEventRecord(fork, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(side, fork, 0);
+        if (e != cudaSuccess) return e;
+        es = side;
+    }
+    if (a.rec) d2q9_edge_kernel<true><<<ge, 256, 0, es>>>(a);
+    else d2q9_edge_kernel<false><<<ge, 256, 0, es>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // interior rows (if any strip has no wall column)
+    const int nin = nsegs - 2;
+    if (nin >= 1 && ny > 2) {
+        const int ntiles = nin * ((ny + 7) / 8);
+        const int g = LBM_FLAT_PERSIST ? grid[dev] : ntiles;   // one tile per block unless persistent
+        if (method == 1) {
+            if (a.rec) d2q9_flat_kernel<true, true><<<g, 256, 0, s>>>(a);
+            else d2q9_flat_kernel<false, true><<<g, 256, 0, s>>>(a);
+        } else {
+            if (a.rec) d2q9_flat_kernel<true, false><<<g, 256, 0, s>>>(a);
+            else d2q9_flat_kernel<false, false><<<g, 256, 0, s>>>(a);
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (es != s) {
+        e = cudaEventRecord(join, side);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, join, 0);
+    }
+    return e;
 }
 
 int d2q9_tma_blocks_per_sm()
@@ -1178,17 +775,10 @@ cudaError_t launch_newton_jobs(int precision, int q, const JobArgs& a, cudaStrea
 int d2q9_blocks_per_sm(int precision)
 {
     int n = 0;
-    if (precision == 1) {
-        cudaFuncSetAttribute(d2q9_step_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             step_smem_bytes<float>());
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, d2q9_step_kernel<float, false>, kWarpsPerBlock * 32,
-                                                      step_smem_bytes<float>());
-    } else {
-        cudaFuncSetAttribute(d2q9_step_kernel<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             step_smem_bytes<double>());
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, d2q9_step_kernel<double, false>, kWarpsPerBlock * 32,
-                                                      step_smem_bytes<double>());
-    }
+    if (precision == 1)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, d2q9_step_kernel<float, false>, kWarpsPerBlock * 32, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, d2q9_step_kernel<double, false>, kWarpsPerBlock * 32, 0);
     return n > 0 ? n : 1;
 }
 

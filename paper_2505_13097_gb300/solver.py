@@ -75,6 +75,9 @@ class Stefan:
         w = _abi.WALLS[wall] if isinstance(wall, str) else int(wall)
         check(self.lib.lbm_stefan_set_bc(self.h, w, int(kind), float(theta_wall)))
 
+    def set_ste(self, ste):
+        check(self.lib.lbm_stefan_set_ste(self.h, float(ste)))
+
     def set_method(self, method):
         """"IREBM" (Algorithm 3, default), "EEBM" (Algorithm 2) or "ILFBM"
         (Algorithm 1, D1Q3 FP64); set_ic follows."""
@@ -109,6 +112,11 @@ class Stefan:
         out = (ctypes.c_double * 2)()
         check(self.lib.lbm_stefan_step_timed(self.h, int(nsteps), ctypes.cast(out, ctypes.POINTER(ctypes.c_double))))
         return out[0], out[1]
+
+    def set_wait_test(self, wait_limit_s=2.0, withhold_load=-1):
+        """Test hook of the FP32 D2Q9 step: bound of its waits on row loads, and
+        a load (0, 1, 2) of its first work item that it skips (-1: none)."""
+        check(self.lib.lbm_stefan_set_wait_test(self.h, float(wait_limit_s), int(withhold_load)))
 
     def step_record(self, n, traj):
         """traj: CUDA float64 tensor holding at least n planes of ny x row_stride."""
@@ -181,6 +189,15 @@ class Stefan:
         check(self.lib.lbm_stefan_adjoint_run(self.h, int(traj.shape[0]) - 1, ctypes.c_void_p(traj.data_ptr()),
                                               ctypes.c_void_p(adj.data_ptr()), ctypes.c_void_p(adj_other.data_ptr()),
                                               ctypes.byref(idx)))
+        return (adj, adj_other) if idx.value == 0 else (adj_other, adj)
+
+    def adjoint_segment(self, checkpoint, n, traj, adj, adj_other):
+        """Reload `checkpoint`, recompute n steps recording theta into traj[:n+1],
+        run n reverse steps; returns (result, spare) buffers."""
+        idx = ctypes.c_int()
+        check(self.lib.lbm_stefan_adjoint_segment(self.h, ctypes.c_void_p(checkpoint.data_ptr()), int(n),
+                                                  ctypes.c_void_p(traj.data_ptr()), ctypes.c_void_p(adj.data_ptr()),
+                                                  ctypes.c_void_p(adj_other.data_ptr()), ctypes.byref(idx)))
         return (adj, adj_other) if idx.value == 0 else (adj_other, adj)
 
     def adjoint_finish(self, adj0, g_theta0):

@@ -164,3 +164,49 @@ def random_direction(shape, seed) -> np.ndarray:
     """Unit-variance normal direction (finite-difference checks)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return rng.standard_normal(size=shape)
+
+
+# ------------------------------------------------------------------ bench parity cases
+# Small versions of the benchmark legs: the same lattices, precisions, methods,
+# walls and parameters, at sizes the FP64 oracle finishes in seconds.  The
+# oracle's results on them are stored in tests/golden/bench_refs.npz (written
+# by tests/golden/make_bench_refs.py); bench.py runs each case through the
+# same kernels as its leg and reports the error against those results beside
+# the leg's speed.  Entries: name -> (case, method, extra solver arguments).
+ILFBM_BAR_KW = {"newton_tol": 1e-12, "newton_max_iter": 200}
+ILFBM_CAVITY_KW = {"newton_tol": 1e-12, "newton_max_iter": 400}
+
+
+def bench_parity_cases():
+    melt = melt_2d(n=130, steps=300).scaled(ny=64)
+    cav5 = cavity_2d(n=64, steps=200)
+    cav9 = cavity_2d(n=64, steps=100, precision=FP64).scaled(lattice=2, bb_mode=0)
+    bar = bar_1d(steps=2000)
+    cases = {
+        "melt_2d_fp32": (melt, "IREBM", {}),
+        "melt_2d_fp64": (melt.scaled(precision=FP64), "IREBM", {}),
+        "eebm_fp32": (melt, "EEBM", {}),
+        "d2q5_cavity_fp32": (cav5, "IREBM", {}),
+        "d2q5_cavity_fp64": (cav5.scaled(precision=FP64), "IREBM", {}),
+        "d2q5_eebm_fp32": (cav5, "EEBM", {}),
+        "d1q3_melt_512": (melt_1d(), "IREBM", {}),
+        "bar_1d_irebm": (bar, "IREBM", {}),
+        "bar_1d_eebm": (bar, "EEBM", {}),
+        "bar_1d_ilfbm": (bar, "ILFBM", dict(ILFBM_BAR_KW)),
+        "cavity_d2q9_irebm": (cav9, "IREBM", {}),
+        "cavity_d2q9_eebm": (cav9, "EEBM", {}),
+        "cavity_d2q9_ilfbm": (cav9, "ILFBM", dict(ILFBM_CAVITY_KW)),
+    }
+    for ste in CORNER_STE:
+        cases["corner_ste%g" % ste] = (corner_2d(n=64, ste=ste, steps=300), "IREBM", {})
+    return cases
+
+
+def bench_parity_batch() -> List[Case]:
+    """Six problems drawn like the batched workload, sides 40 to 80, 100 steps."""
+    return batch_2d(count=6, lo=40, hi=80, steps=100)
+
+
+def bench_parity_adjoint() -> Case:
+    """The adjoint workload at 48 x 48 over 40 steps (FP32 forward)."""
+    return adjoint_2d(n=48, steps=40)

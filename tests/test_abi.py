@@ -76,6 +76,10 @@ def test_null_handles_are_rejected(lib):
     assert lib.lbm_stefan_set_ic(None, None, 0) == _abi.LBM_ERR_ARG
     assert lib.lbm_stefan_create(None, None, None) == _abi.LBM_ERR_ARG
     assert lib.lbm_stefan_batch_create(0, None, 1, 1e-14, 60, None, None) == _abi.LBM_ERR_ARG
+    assert lib.lbm_stefan_set_ste(None, 0.1) == _abi.LBM_ERR_ARG
+    assert lib.lbm_stefan_set_wait_test(None, 0.01, -1) == _abi.LBM_ERR_ARG
+    idx = ctypes.c_int()
+    assert lib.lbm_stefan_adjoint_segment(None, None, 1, None, None, None, ctypes.byref(idx)) == _abi.LBM_ERR_ARG
     lib.lbm_stefan_destroy(None)
     lib.lbm_stefan_batch_destroy(None)
 

@@ -36,8 +36,11 @@ def bench(monkeypatch):
 
     monkeypatch.setattr(b, "ClockSampler", Clocks)
     monkeypatch.setattr(b, "bench_single",
-                        lambda *a, **k: (126.0, {"kernel_ms": (0.265, 0.056), "imbalance": 0.0, "newton_nodes": 5}))
+                        lambda *a, **k: (126.0, {"kernel_ms": (0.265, 0.0), "imbalance": 0.0, "newton_nodes": 5,
+                                                 "newton_iters": 11, "newton_max_iter": 3}))
     monkeypatch.setattr(b, "bench_e2e", lambda *a, **k: (130.0, 8 * 4096 * 4096, 8 * 4096 * 4096))
+    monkeypatch.setattr(b, "oracle_errors",
+                        lambda *a, **k: {"melt_2d_fp32": {"max_rel_dtheta": 1e-7, "max_abs_dphi": 1e-6}})
     return b
 
 
@@ -57,7 +60,9 @@ def test_json_line_keys(bench, capsys):
     assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["peak"] == 6795.1
     assert r["achieved"] == pytest.approx(72 * 4096 * 4096 / 0.265e-3 / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
-    assert "workload" in d["config"] and d["gpu_launches"] == 800
+    assert "workload" in d["config"] and d["gpu_launches"] == 400
+    assert d["error_vs_oracle"]["max_rel_dtheta"] == 1e-7
+    assert d["newton_mean_iterations_last_step"] == pytest.approx(11 / 5)
     assert set(d["e2e"]) >= {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"}
 
 
