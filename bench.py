@@ -1,7 +1,8 @@
 """Benchmark of the IREBM time step on GB300 (one JSON line on stdout).
 
-Headline: D2Q9 MLUPS of the fused step in the FP32 form (FP32 populations,
-FP64 Newton) on the 4096 x 4096 melting workload, timed with CUDA events on
+Headline: D2Q9 MLUPS of the step in the FP32 form (FP32 populations, FP64
+Newton; three launches per step: the interior rows, the wall rows on a
+second stream, the Newton job kernel) on the 4096 x 4096 melting workload, timed with CUDA events on
 the launching stream over --steps steps after --warmup untimed steps.  The
 timed window sits at the middle of the 10,000-step job (the state is first
 advanced, untimed, to step 5,000 - (warmup + steps)/2) so the Newton front band
@@ -12,7 +13,7 @@ Also reported: the FP64 form on the same workload, the 2048^2 FP64 corner
 workload for Ste in {0.01, 0.1, 1}, EEBM (Algorithm 2) on the same window, 256
 batched problems in one persistent graph-captured launch per step, the
 adjoint/forward time ratio on 1024^2 with sqrt(T) checkpointing, the 512-node
-D1Q3 workload (fused steps), the paper's 2D cavity on D2Q5 (4096^2, Eq. 17
+D1Q3 workload (all steps of a call in one launch), the paper's 2D cavity on D2Q5 (4096^2, Eq. 17
 closure; IREBM FP32 and FP64, EEBM), the paper's 1D bar (N = 801) and its 2D
 cavity on D2Q9 (N = 801, FP64) with the three schemes (IREBM, EEBM, ILFBM).
 
@@ -40,10 +41,10 @@ BYTES_FP32 = 9 * 4 * 2   # algorithmic bytes per node update: each population re
 BYTES_FP64 = 9 * 8 * 2
 BYTES_D2Q5_FP32 = 5 * 4 * 2   # D2Q5: five populations
 BYTES_D2Q5_FP64 = 5 * 8 * 2
-# DRAM bytes (read + write) per node of one launch of the fused FP32 D2Q9 kernel,
-# from an ncu capture (None until the current kernel has been captured)
-FUSED_TRAFFIC_PER_NODE = None
-FUSED_TRAFFIC_NOTE = "not captured for the current kernel yet"
+# DRAM bytes (read + write) per interior node of one launch of the flat FP32 D2Q9
+# interior kernel, from an ncu capture (None until the current kernel has been captured)
+FLAT_TRAFFIC_PER_NODE = None
+FLAT_TRAFFIC_NOTE = "not captured for the current kernel yet"
 
 
 def log(*a):
@@ -593,8 +594,8 @@ def run_gpu(args):
     value = job_mlups(world, nodes, args.steps, ms_max)
     per_step_ms = ms / args.steps
     k_step_ms, k_job_ms = st["kernel_ms"]
-    # the dominant kernel: the fused step kernel, 72 algorithmic bytes per node update
-    # (it also solves the Newton nodes: one launch per step)
+    # the dominant kernels: the flat interior kernel and the concurrent wall-row kernel,
+    # 72 algorithmic bytes per node update, timed together from the first launch to the join
     achieved = BYTES_FP32 * nodes / (k_step_ms * 1e-3) / 1e9
 
     extra = {}
@@ -652,11 +653,13 @@ def run_gpu(args):
                          "frac": achieved / peak,
                          # dram__bytes_read.sum + dram__bytes_write.sum of one launch of this kernel in an ncu
                          # capture, per launch at this node count (None: not captured since the kernel changed)
-                         "traffic": FUSED_TRAFFIC_PER_NODE * nodes if FUSED_TRAFFIC_PER_NODE else None,
-                         "traffic_note": FUSED_TRAFFIC_NOTE,
+                         "traffic": FLAT_TRAFFIC_PER_NODE * nodes if FLAT_TRAFFIC_PER_NODE else None,
+                         "traffic_note": FLAT_TRAFFIC_NOTE,
                          "bytes_per_node": BYTES_FP32, "units_per_launch": nodes,
-                         "kernel": "d2q9_fused_kernel<false>", "kernel_ms": k_step_ms,
-                         "launches_per_step": 1, "second_kernel_ms": k_job_ms,
+                         "kernel": "d2q9_flat_kernel<false,false> + d2q9_edge_kernel<false> (concurrent)",
+                         "kernel_ms": k_step_ms,
+                         "launches_per_step": 3, "second_kernel": "newton_jobs_kernel<float,false,9>",
+                         "second_kernel_ms": k_job_ms,
                          "whole_step_gbs": BYTES_FP32 * nodes / (per_step_ms * 1e-3) / 1e9,
                          "whole_step_frac": BYTES_FP32 * nodes / (per_step_ms * 1e-3) / 1e9 / peak,
                          "timing": "kernel_ms: CUDA events around each launch of 50 steps launched one by one, "
@@ -669,7 +672,7 @@ def run_gpu(args):
                     "what": "lbm_stefan_set_state from a pinned host copy of the state at the start of the "
                             "headline's window (all populations), %d steps, lbm_stefan_get_fields to pinned host "
                             "theta; wall clock" % args.steps},
-            "gpu_launches": args.steps,   # one fused kernel launch per step
+            "gpu_launches": 3 * args.steps,   # interior rows, wall rows, Newton jobs per step
             "clocks": clk.summary(),
             "energy_imbalance_last_step": st["imbalance"],
             "newton_nodes_last_step": st["newton_nodes"],

@@ -8,11 +8,13 @@
  * Algorithm 3 of the paper once per step: collision (Eq. 12), pull
  * streaming, the boundary closures of Sec. 4.2 on q, the zeroth moment, the
  * local Newton solve of Eq. (14), the source of Eq. (13), and the next
- * collision.  Kernel launches per step: D2Q9 with FP32 populations, one
- * (a persistent kernel that also solves the Newton nodes); D2Q9 in FP64 and
- * D2Q5, two (the stream/collide kernel, which hands the nodes that need the
- * Newton iteration to a list, then the kernel that solves that list); D1Q3,
- * one launch for all the steps of a call.
+ * collision.  Kernel launches per step: D2Q9 with FP32 populations, three
+ * (the interior rows, the rows that touch a wall, which run concurrently on a
+ * second stream when the handle's stream is not the legacy default one, then
+ * the kernel that solves the Newton list); D2Q9 in FP64 and D2Q5, two (the
+ * stream/collide kernel, which hands the nodes that need the Newton iteration
+ * to a list, then the kernel that solves that list); D1Q3, one launch for all
+ * the steps of a call.
  *
  * Problem statement (Sec. 2, Eq. 1): dimensionless temperature theta with
  * melting temperature 0, Stefan number Ste, equal phase properties; the
@@ -50,7 +52,8 @@ typedef enum {
     LBM_ERR_ARG = 1,     /* invalid argument (sizes, tau <= 1/2, Ste <= 0, delta <= 0, NULL, ...) */
     LBM_ERR_CUDA = 2,    /* a CUDA runtime call failed */
     LBM_ERR_NEWTON = 3,  /* a node's Newton solve hit its iteration limit, or a value was not finite */
-    LBM_ERR_TIMEOUT = 4, /* a bounded device wait ran out (the FP32 D2Q9 step's waits for its row loads) */
+    LBM_ERR_TIMEOUT = 4, /* a bounded device wait ran out (the TMA row-pipeline kernel's waits for its row
+                            loads: FP32 D2Q9 batches, and single problems under lbm_stefan_set_wait_test) */
     LBM_ERR_STATE = 5    /* call out of order (e.g. step before set_ic) */
 } lbm_status;
 
@@ -157,23 +160,26 @@ lbm_status lbm_stefan_step(lbm_stefan* h, int nsteps);
 /* D2Q9 and D2Q5: advance nsteps >= 1 steps launched one by one (no graph) with a
  * CUDA event before, between and after the kernels of each step, wait for
  * them, and return the mean device time per step of each kernel in ms:
- * ms_kernels[0] the stream/collide kernel (in the FP32 D2Q9 form the fused
- * kernel, which also solves the Newton nodes), ms_kernels[1] the Newton job
- * kernel (0 in the FP32 D2Q9 form, which has none).  Same result as
+ * ms_kernels[0] the stream/collide kernel (in the FP32 D2Q9 form the interior
+ * and wall-row kernels together, from the first launch to the join of the
+ * two streams), ms_kernels[1] the Newton job kernel.  Same result as
  * lbm_stefan_step; for measuring each kernel against its roofline.
  * Synchronizes. */
 lbm_status lbm_stefan_step_timed(lbm_stefan* h, int nsteps, double* ms_kernels);
 
-/* Test hook of the FP32 D2Q9 step, which waits for row loads that it issued
- * itself (other steps ignore it).  wait_limit_s > 0 bounds every such wait
- * (default 2 s).  withhold_load in {0, 1, 2} makes the step skip that load
- * of its first work item (a range of rows of the 128-column strip at x = 0;
- * load 0 is the row above the range, load 1 its first row): the wait for it
- * runs out, the step stops that warp after the loads it has in flight have
- * landed, and the next synchronizing call returns LBM_ERR_TIMEOUT (the
- * handle's state is then undefined; create a new one).  withhold_load = -1
- * restores normal steps.  LBM_ERR_ARG for a value outside [-1, 2] or a wait
- * limit outside (0, 60] s. */
+/* Test hook of the TMA row-pipeline kernel (the FP32 D2Q9 kernel whose
+ * blocks wait for row loads that they issued themselves; FP32 D2Q9 batches
+ * run it).  Only FP32 D2Q9 handles use it; other handles ignore it.
+ * wait_limit_s > 0 bounds every such wait (default 2 s).  While
+ * withhold_load is in {0, 1, 2}, the handle's steps run that kernel in place
+ * of the flat interior / wall-row pair, and its first block skips that row
+ * load (its rows are a range of the 128-column strip at x = 0; load 0 is the
+ * row above the range, load 1 its first row): the waits for it run out, the
+ * block stops after the loads it has in flight have landed (each of those
+ * waits bounded too), and the next synchronizing call returns
+ * LBM_ERR_TIMEOUT (the handle's state is then undefined; create a new one).
+ * withhold_load = -1 restores normal steps (the flat pair).  LBM_ERR_ARG for
+ * a value outside [-1, 2] or a wait limit outside (0, 60] s. */
 lbm_status lbm_stefan_set_wait_test(lbm_stefan* h, double wait_limit_s, int withhold_load);
 
 /* Advance nsteps steps and write theta(t+1), ..., theta(t+nsteps) to
@@ -272,13 +278,14 @@ lbm_status lbm_stefan_adjoint_finish(lbm_stefan* h, const void* adj0, double* g_
 void lbm_stefan_destroy(lbm_stefan* h);
 
 /* ---------------------------------------------------------------- batches
- * Many independent D2Q9 problems of uneven sizes advanced by one persistent
- * kernel launch per step; the launches of a call are captured in a CUDA
- * graph.  In FP32 the launch is the fused kernel of the single-problem FP32
- * step over a list of work items (a 128-column strip of one problem over a
- * range of rows); in FP64 the warp-tile kernel plus the Newton job kernel.
- * The tile height (FP32: the row count of the first work items) and the
- * order of the problems come from lbm_stefan_batch_autotune (or defaults). */
+ * Many independent D2Q9 problems of uneven sizes advanced by two kernel
+ * launches per step, both over all problems: the step kernel, then the Newton
+ * job kernel; the launches of a call are captured in a CUDA graph.  In FP32
+ * the step kernel is the TMA row-pipeline kernel over a table of tiles (a
+ * 128-column strip of one problem over a range of rows, one tile per block);
+ * in FP64 the persistent warp-tile kernel over a schedule of warp tiles.  The
+ * tile height and the order of the tiles come from lbm_stefan_batch_autotune
+ * (or defaults). */
 
 typedef struct {
     int nx, ny;                 /* >= 2 each */
@@ -298,9 +305,8 @@ lbm_status lbm_stefan_batch_get_stats(lbm_stefan_batch* b, int k, lbm_stefan_sta
  * keep the fastest; the state is saved and restored around the trials.
  * chosen_tile_h receives the chosen height (may be NULL). */
 lbm_status lbm_stefan_batch_autotune(lbm_stefan_batch* b, int trial_steps, int* chosen_tile_h);
-/* Set the tile height (rows per warp tile; FP32: rows of the first work items,
- * later ones have half and a quarter as many) and schedule (0 = problem order,
- * 1 = largest problems (FP64: longest tiles) first) explicitly. */
+/* Set the tile height (rows per tile) and schedule (0 = problem order,
+ * 1 = largest problems first in FP32, longest tiles first in FP64) explicitly. */
 lbm_status lbm_stefan_batch_set_schedule(lbm_stefan_batch* b, int tile_h, int schedule);
 void lbm_stefan_batch_destroy(lbm_stefan_batch* b);
 

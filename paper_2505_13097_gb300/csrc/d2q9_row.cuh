@@ -1,5 +1,6 @@
 // Row update of the D2Q9 step kernels, shared by the warp-tile kernel
-// (FP64 form, batches, the no-allocation step) and the fused FP32 kernel:
+// (FP64 form, the no-allocation step), the TMA row-pipeline kernel (FP32
+// batches) and the wall rows of the flat FP32 step:
 // the boundary closures of Sec. 4.2 at wall nodes, the moments, the exact
 // saturated branch, the hand-off of nodes that need the local Newton solve of
 // Eq. (14), and the relaxation toward the next step's Omega (Eq. 12).
@@ -146,7 +147,7 @@ __device__ __forceinline__ float approx_sum<double>(const double* u)
 // Nodes whose local Newton solve is deferred go to a sink: reserve(total,
 // lane) returns (to every lane) the first of `total` consecutive slots, and
 // put(slot, job) stores one job.  The global job list below is solved by
-// newton_jobs_kernel after the step; the fused kernel keeps a queue per warp.
+// newton_jobs_kernel after the step.
 struct GlobalJobSink {
     NewtonJob* jobs;
     unsigned int* count;

@@ -133,43 +133,10 @@ struct TmaMaps {
     const int4* tiles;
     const CUtensorMap* gmaps;
     int ntiles;
+    long long wait_ns = 2000000000LL;    // bound of every wait on a row load, in nanoseconds
+    int withhold_load = -1;              // test hook: >= 0 skips that row load of block 0 (0: the row
+                                         // above its first row); -1: off
 };
-
-// Counters of one launch of the fused FP32 D2Q9 step.  Between launches all
-// are zero except `streaming`, which holds the launch's warp count.
-struct FusedCounters {
-    unsigned int item_next;      // next work item to take
-    unsigned int streaming;      // warps still taking work items
-    unsigned int batch_tail;     // Newton batches reserved
-    unsigned int ticket;         // blocks finished (the last one publishes and resets)
-};
-
-// Per-launch arguments of the fused FP32 D2Q9 step (step_fused.cu): one
-// persistent, cooperative launch per step whose warps take work items
-// (problem, 128-column strip, first row, end row) from `items` in list order,
-// stream them through a TMA row ring of their own, and hand the nodes that
-// need the Newton iteration, 32 at a time, to the queue of a block chosen
-// round-robin, whose warps solve them between rows.  The last block
-// publishes the statistics and resets the counters.
-struct FusedArgs {
-    const Problem* probs;        // device array
-    const CUtensorMap* maps;     // device array: 2 per problem (state[0], state[1])
-    const int4* items;           // device array of work items
-    int nitems;
-    int nprob;
-    int parity;                  // read state[parity], write state[parity ^ 1]
-    double* rec;                 // optional theta' record plane (single problem only)
-    DevStats* stats;
-    FusedCounters* ctr;
-    NewtonJob* jobs;             // batches of 32 deferred Newton nodes (batch_cap batches)
-    int batch_cap;
-    unsigned int* bq_tail;       // per block (stride kBqStride): batches queued for it; zero between launches
-    unsigned int* bq;            // per block: bq_cap entries, batch index + 1 (0: not yet written)
-    int bq_cap;
-    long long wait_ns;           // bound of every wait (row loads, queue entries, the end) in nanoseconds
-    int withhold_load;           // test hook: >= 0 skips this load of item 0 (0: the row above it; -1: none)
-};
-constexpr int kBqStride = 32;    // unsigned ints between two blocks' queue tails (128 bytes)
 
 // Per-launch arguments of the Newton job kernel (runs after every D2Q9 step).
 struct JobArgs {
@@ -220,11 +187,6 @@ cudaError_t launch_d2q9_flat(const StepArgs& a, int nsegs, int ny, int method, c
                              cudaEvent_t fork, cudaEvent_t join);
 int d2q9_tma_blocks_per_sm();
 cudaError_t launch_newton_jobs(int precision, int q, const JobArgs& a, cudaStream_t s);   // q = 9 or 5
-
-// Fused FP32 D2Q9 step (step_fused.cu): one persistent launch per step
-cudaError_t launch_d2q9_fused(const FusedArgs& a, cudaStream_t s);
-int d2q9_fused_grid();                   // resident blocks on this GPU (the persistent, cooperative grid)
-int d2q9_fused_warps();                  // warps per block
 
 // D2Q5 launchers (step_d2q5.cu): one tile per warp over a.nslots tiles
 cudaError_t launch_d2q5_step(int precision, const StepArgs& a, cudaStream_t s);

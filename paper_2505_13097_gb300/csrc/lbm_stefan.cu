@@ -71,58 +71,6 @@ struct GraphCache {
 
 }  // namespace
 
-namespace lbm {
-// Counters, Newton batch array and batch queues of the fused FP32 D2Q9
-// kernel, sized for `nodes` nodes and the kernel's (fixed) cooperative grid:
-// every full batch holds 32 of the nodes, and each streaming warp adds at
-// most one padded batch at its end.
-struct FusedQueues {
-    FusedCounters* ctr = nullptr;
-    NewtonJob* jobs = nullptr;
-    unsigned int* bq_tail = nullptr;
-    unsigned int* bq = nullptr;
-    int batch_cap = 0, bq_cap = 0;
-    cudaError_t alloc(long long nodes)
-    {
-        const int grid = d2q9_fused_grid();
-        if (grid <= 0) return cudaErrorInvalidConfiguration;
-        const long long cap = nodes / 32 + (long long)grid * d2q9_fused_warps() + 1;
-        if (cap > (1LL << 30)) return cudaErrorInvalidValue;
-        batch_cap = (int)cap;
-        bq_cap = (batch_cap + grid - 1) / grid + 1;
-        FusedCounters c0 = {};
-        c0.streaming = (unsigned)(grid * d2q9_fused_warps());   // the first launch's streaming warps
-        cudaError_t e = cudaMalloc(&ctr, sizeof(FusedCounters));
-        if (e == cudaSuccess) e = cudaMemcpy(ctr, &c0, sizeof c0, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMalloc(&jobs, sizeof(NewtonJob) * 32 * (size_t)batch_cap);
-        if (e == cudaSuccess) e = cudaMalloc(&bq_tail, sizeof(unsigned int) * (size_t)grid * kBqStride);
-        if (e == cudaSuccess) e = cudaMemset(bq_tail, 0, sizeof(unsigned int) * (size_t)grid * kBqStride);
-        if (e == cudaSuccess) e = cudaMalloc(&bq, sizeof(unsigned int) * (size_t)grid * bq_cap);
-        if (e == cudaSuccess) e = cudaMemset(bq, 0, sizeof(unsigned int) * (size_t)grid * bq_cap);
-        return e;
-    }
-    void fill(FusedArgs& f) const
-    {
-        f.ctr = ctr;
-        f.jobs = jobs;
-        f.batch_cap = batch_cap;
-        f.bq_tail = bq_tail;
-        f.bq = bq;
-        f.bq_cap = bq_cap;
-    }
-    void release()
-    {
-        cudaFree(ctr);
-        cudaFree(jobs);
-        cudaFree(bq_tail);
-        cudaFree(bq);
-        ctr = nullptr;
-        jobs = nullptr;
-        bq_tail = bq = nullptr;
-    }
-};
-}  // namespace lbm
-
 struct lbm_stefan {
     lbm_stefan_params p;
     Problem hp;
@@ -143,15 +91,9 @@ struct lbm_stefan {
     double* dilf_scratch = nullptr;    // 2D ILFBM: S0, two l iterates, two l differences (5 nx*ny)
     bool use_tma = false;              // FP32 D2Q9: the TMA row-pipeline step kernel
     lbm::TmaMaps tma;
-    bool use_fused = false;            // FP32 D2Q9: the fused persistent step kernel
-    CUtensorMap* dmaps = nullptr;      // fused kernel: descriptors of state[0], state[1]
-    int4* ditems = nullptr;            // fused kernel: work items
-    int nitems = 0;
-    lbm::FusedQueues fq;               // fused kernel: counters and Newton batch queues
     cudaStream_t side = nullptr;       // flat FP32 step: stream of the wall-row kernel
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    long long wait_ns = 2000000000LL;  // bound of the fused kernel's waits on row loads
-    int withhold_load = -1;            // test hook of the fused kernel (-1: off)
+    int withhold_load = -1;            // test hook of the TMA kernel's row loads (-1: off)
     GraphCache graph;
     // captured adjoint segments (lbm_stefan_adjoint_segment): recompute + reverse
     // steps for one (length, trajectory, adjoint buffers) combination each
@@ -197,10 +139,6 @@ struct lbm_stefan_batch {
     lbm::TmaMaps tma;
     CUtensorMap* dmaps = nullptr;      // 2 descriptors per problem
     int4* dtiles = nullptr;
-    bool use_fused = false;            // FP32: the fused persistent step kernel over a work-item list
-    int4* ditems = nullptr;
-    int nitems = 0;
-    lbm::FusedQueues fq;
     GraphCache graph;
 };
 
@@ -315,26 +253,12 @@ static lbm::JobArgs job_args(const Problem* probs, int nprob, int parity, double
     return j;
 }
 
-static lbm::FusedArgs fused_args(lbm_stefan* h, int parity, double* rec)
-{
-    lbm::FusedArgs f;
-    f.probs = h->dprob;
-    f.maps = h->dmaps;
-    f.items = h->ditems;
-    f.nitems = h->nitems;
-    f.nprob = 1;
-    f.parity = parity;
-    f.rec = rec;
-    f.stats = h->dstats;
-    h->fq.fill(f);
-    f.wait_ns = h->wait_ns;
-    f.withhold_load = h->withhold_load;
-    return f;
-}
-
-// One step.  FP32 D2Q9: one launch of the fused kernel.  FP64 D2Q9 and D2Q5:
-// two launches, the stream/collide kernel, which defers the nodes that need
-// the Newton iteration, and the job kernel that solves them.  D1Q3: one launch.
+// One step.  D2Q9 and D2Q5: the stream/collide kernel(s), which defer the
+// nodes that need the Newton iteration, then the job kernel that solves them
+// (FP32 D2Q9: the flat interior kernel and the wall-row kernel, three launches
+// in all; FP64 D2Q9 and D2Q5: two).  D1Q3: one launch.  While the wait test
+// hook is on, the FP32 D2Q9 step runs the TMA row-pipeline kernel instead of
+// the flat pair (the kernel with the waits the hook exercises).
 static cudaError_t launch_one(lbm_stefan* h, int parity, double* rec)
 {
     StepArgs a = single_args(h, parity, rec);
@@ -346,10 +270,9 @@ static cudaError_t launch_one(lbm_stefan* h, int parity, double* rec)
                                        h->stream);
     }
     if (h->p.lattice == LBM_D2Q9) {
-        if (h->use_fused) return lbm::launch_d2q9_fused(fused_args(h, parity, rec), h->stream);
         cudaError_t e;
         if (h->use_tma) {
-            e = LBM_FLAT ? lbm::launch_d2q9_flat(a, h->hp.pitch / 128, h->hp.ny, h->hp.method, h->stream, h->side,
+            e = LBM_FLAT && h->withhold_load < 0 ? lbm::launch_d2q9_flat(a, h->hp.pitch / 128, h->hp.ny, h->hp.method, h->stream, h->side,
                                                     h->ev_fork, h->ev_join)
                          : lbm::launch_d2q9_tma(a, h->tma, h->stream);
         } else {
@@ -443,94 +366,6 @@ static bool setup_tma(lbm_stefan* h)
     return per_sm > 0;
 }
 
-// ------------------------------------------------------------------ fused kernel
-#ifndef LBM_USE_FUSED
-#define LBM_USE_FUSED 0
-#endif
-
-#ifndef LBM_FUSED_ROWS
-#define LBM_FUSED_ROWS 16   // largest row count of a work item
-#endif
-
-// Work items of the fused kernel: (problem, 128-column strip, first row, end
-// row), in the order the warps take them.  Guided self-scheduling: while R
-// strip-rows remain, the next item has clamp(ceil(R / (2 * warps)), 1,
-// rows_max) rows, so the items taken last are one or two rows long and the
-// warps finish together although their speeds differ.  Items are taken from
-// the strips in turn (problems in `order`, strips left to right), so the rows
-// shared by neighbouring items are loaded at about the same time (from L2 the
-// second time).
-static std::vector<int4> fused_items(const std::vector<Problem>& probs, const std::vector<int>& order, int rows_max,
-                                     int warps)
-{
-    struct Strip {
-        int prob, seg, next, end;
-    };
-    std::vector<Strip> strips;
-    long long remaining = 0;
-    for (int k : order) {
-        const Problem& pb = probs[k];
-        for (int seg = 0; seg < pb.pitch / lbm::kTmaW; ++seg) {
-            strips.push_back({k, seg, 0, pb.ny});
-            remaining += pb.ny;
-        }
-    }
-    std::vector<int4> items;
-    const long long div = 2LL * std::max(1, warps);
-    const int rmax = std::max(1, rows_max);
-    while (remaining > 0) {
-        bool any = false;
-        for (Strip& st : strips) {
-            if (st.next >= st.end) continue;
-            const long long want = std::min<long long>(rmax, std::max<long long>(1, (remaining + div - 1) / div));
-            const int rows = (int)std::min<long long>(want, st.end - st.next);
-            items.push_back(make_int4(st.prob, st.seg, st.next, st.next + rows));
-            st.next += rows;
-            remaining -= rows;
-            any = true;
-        }
-        if (!any) break;
-    }
-    return items;
-}
-
-static int fused_warps()
-{
-    const int g = lbm::d2q9_fused_grid();
-    return g > 0 ? g * lbm::d2q9_fused_warps() : 1;
-}
-
-static cudaError_t upload_items(const std::vector<int4>& items, int4** ditems, int* nitems)
-{
-    if (*ditems) cudaFree(*ditems);
-    *ditems = nullptr;
-    *nitems = 0;
-    cudaError_t e = cudaMalloc(ditems, sizeof(int4) * std::max<size_t>(1, items.size()));
-    if (e == cudaSuccess) e = cudaMemcpy(*ditems, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) *nitems = (int)items.size();
-    return e;
-}
-
-// Descriptors, work items and counter of the fused kernel; false leaves the
-// two-kernel step in use.
-static bool setup_fused(lbm_stefan* h)
-{
-    const Problem& hp = h->hp;
-    if (hp.pitch % lbm::kTmaW != 0 || (hp.plane * 4) % 16 != 0 || lbm::d2q9_fused_grid() <= 0) return false;
-    CUtensorMap maps[2];
-    for (int k = 0; k < 2; ++k)
-        if (!encode_state_map(&maps[k], hp.state[k], hp, lbm::kTmaW + 2 * lbm::kTmaHalo)) return false;
-    cudaError_t e = cudaMalloc(&h->dmaps, sizeof maps);
-    if (e == cudaSuccess) e = cudaMemcpy(h->dmaps, maps, sizeof maps, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = upload_items(fused_items({hp}, {0}, LBM_FUSED_ROWS, fused_warps()), &h->ditems, &h->nitems);
-    if (e == cudaSuccess) e = h->fq.alloc((long long)hp.nx * hp.ny);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return true;
-}
-
 extern "C" lbm_status lbm_stefan_create(const lbm_stefan_params* p, void* cuda_stream, lbm_stefan** out)
 {
     if (!p || !out) return fail(LBM_ERR_ARG, "NULL argument");
@@ -582,8 +417,7 @@ extern "C" lbm_status lbm_stefan_create(const lbm_stefan_params* p, void* cuda_s
     h->hp.state[0] = bufs[0];
     h->hp.state[1] = bufs[1];
     h->hp.stats = 0;
-    if (e == cudaSuccess && tma && LBM_USE_FUSED) h->use_fused = setup_fused(h);
-    if (e == cudaSuccess && tma && !h->use_fused) h->use_tma = setup_tma(h);
+    if (e == cudaSuccess && tma) h->use_tma = setup_tma(h);
     // the flat FP32 step runs its wall rows on a side stream (non-default streams only:
     // the legacy stream would serialize with it)
     if (e == cudaSuccess && h->use_tma && LBM_FLAT && h->stream != nullptr) {
@@ -591,8 +425,8 @@ extern "C" lbm_status lbm_stefan_create(const lbm_stefan_params* p, void* cuda_s
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
     }
-    // the list of deferred Newton nodes of the two-kernel steps (the fused kernel has its own)
-    if (e == cudaSuccess && q != 3 && !h->use_fused)
+    // the list of deferred Newton nodes (D2Q9, D2Q5)
+    if (e == cudaSuccess && q != 3)
         e = cudaMalloc(&h->djobs, sizeof(lbm::NewtonJob) * (size_t)p->nx * p->ny);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -789,18 +623,10 @@ extern "C" lbm_status lbm_stefan_step_timed(lbm_stefan* h, int nsteps, double* m
     if (e == cudaSuccess) e = cudaEventRecord(ev[0], h->stream);
     for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
         StepArgs a = single_args(h, h->parity, nullptr);
-        if (h->use_fused) {
-            // one launch per step: the second interval is empty
-            e = lbm::launch_d2q9_fused(fused_args(h, h->parity, nullptr), h->stream);
-            if (e == cudaSuccess) e = cudaEventRecord(ev[2 * k + 1], h->stream);
-            if (e == cudaSuccess) e = cudaEventRecord(ev[2 * k + 2], h->stream);
-            h->parity ^= 1;
-            continue;
-        }
         if (h->p.lattice == LBM_D2Q5) {
             e = lbm::launch_d2q5_step(h->precision, a, h->stream);
         } else if (h->use_tma) {
-            e = LBM_FLAT ? lbm::launch_d2q9_flat(a, h->hp.pitch / 128, h->hp.ny, h->hp.method, h->stream, h->side,
+            e = LBM_FLAT && h->withhold_load < 0 ? lbm::launch_d2q9_flat(a, h->hp.pitch / 128, h->hp.ny, h->hp.method, h->stream, h->side,
                                                     h->ev_fork, h->ev_join)
                          : lbm::launch_d2q9_tma(a, h->tma, h->stream);
         } else {
@@ -925,7 +751,8 @@ extern "C" lbm_status lbm_stefan_set_wait_test(lbm_stefan* h, double wait_limit_
     if (!h) return fail(LBM_ERR_ARG, "NULL handle");
     if (!(wait_limit_s > 0.0) || !(wait_limit_s <= 60.0)) return fail(LBM_ERR_ARG, "wait_limit_s must be in (0, 60]");
     if (withhold_load < -1 || withhold_load > 2) return fail(LBM_ERR_ARG, "withhold_load must be -1, 0, 1 or 2");
-    h->wait_ns = (long long)(wait_limit_s * 1e9);
+    h->tma.wait_ns = (long long)(wait_limit_s * 1e9);
+    h->tma.withhold_load = withhold_load;
     h->withhold_load = withhold_load;
     h->graph.reset();   // captured launches carry the old values
     h->reset_seg_graphs();
@@ -1148,9 +975,6 @@ extern "C" void lbm_stefan_destroy(lbm_stefan* h)
     cudaFree(h->djob_count);
     cudaFree(h->dilf);
     cudaFree(h->dilf_scratch);
-    cudaFree(h->dmaps);
-    cudaFree(h->ditems);
-    h->fq.release();
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->side) cudaStreamDestroy(h->side);
@@ -1250,17 +1074,7 @@ static lbm_status batch_build_schedule(lbm_stefan_batch* b, int tile_h, int sche
     b->tile_h = tile_h;
     b->schedule = schedule;
     b->graph.reset();
-    if (b->use_fused) {
-        // fused kernel: tile_h is the largest row count of a work item;
-        // schedule 1 lists the largest problems first
-        std::vector<int> order(b->count);
-        for (int k = 0; k < b->count; ++k) order[k] = k;
-        if (schedule == 1)
-            std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-                return (long long)b->hp[x].nx * b->hp[x].ny > (long long)b->hp[y].nx * b->hp[y].ny;
-            });
-        CUDA_TRY(upload_items(fused_items(b->hp, order, tile_h, fused_warps()), &b->ditems, &b->nitems));
-    } else if (b->use_tma) {
+    if (b->use_tma) {
         lbm_status s = batch_build_tma_tiles(b, tile_h, schedule);
         if (s != LBM_OK) return s;
     }
@@ -1275,21 +1089,6 @@ static lbm_status batch_build_schedule(lbm_stefan_batch* b, int tile_h, int sche
 
 static cudaError_t batch_launch_one(lbm_stefan_batch* b, int parity)
 {
-    if (b->use_fused) {
-        lbm::FusedArgs f;
-        f.probs = b->dprobs;
-        f.maps = b->dmaps;
-        f.items = b->ditems;
-        f.nitems = b->nitems;
-        f.nprob = b->count;
-        f.parity = parity;
-        f.rec = nullptr;
-        f.stats = b->dstats;
-        b->fq.fill(f);
-        f.wait_ns = 2000000000LL;
-        f.withhold_load = -1;
-        return lbm::launch_d2q9_fused(f, b->stream);
-    }
     StepArgs a;
     a.probs = b->dprobs;
     a.nprob = b->count;
@@ -1377,10 +1176,8 @@ extern "C" lbm_status lbm_stefan_batch_create(int count, const lbm_stefan_proble
         base += 2 * sz;
     }
     if (LBM_USE_TMA && precision == LBM_FP32) b->use_tma = batch_setup_tma(b);
-    if (b->use_tma && LBM_USE_FUSED && lbm::d2q9_fused_grid() > 0 && b->fq.alloc((long long)total_nodes) == cudaSuccess)
-        b->use_fused = true;
     cudaGetLastError();
-    lbm_status s = batch_build_schedule(b, b->use_fused ? LBM_FUSED_ROWS : 16, 1);
+    lbm_status s = batch_build_schedule(b, 16, 1);
     if (s != LBM_OK) {
         lbm_stefan_batch_destroy(b);
         return s;
@@ -1519,10 +1316,7 @@ extern "C" lbm_status lbm_stefan_batch_autotune(lbm_stefan_batch* b, int trial_s
     cudaMemcpyAsync(save, b->arena, b->arena_bytes, cudaMemcpyDeviceToDevice, b->stream);
     cudaMemcpyAsync(save_st, b->dstats, sizeof(DevStats) * b->count, cudaMemcpyDeviceToDevice, b->stream);
     const int saved_parity = b->parity;
-    // fused kernel: largest row count of a work item; otherwise rows per tile
-    const int cands_fused[] = {4, 8, 16, 32};
-    const int cands_tiles[] = {8, 16, 32, 64};
-    const int* cands_h = b->use_fused ? cands_fused : cands_tiles;
+    const int cands_h[] = {8, 16, 32, 64};   // rows per tile
     const int cands_s[] = {1, 0};
     float best = 1e30f;
     int best_h = b->tile_h, best_s = b->schedule;
@@ -1583,8 +1377,6 @@ extern "C" void lbm_stefan_batch_destroy(lbm_stefan_batch* b)
     cudaFree(b->djob_count);
     cudaFree(b->dmaps);
     cudaFree(b->dtiles);
-    cudaFree(b->ditems);
-    b->fq.release();
     delete b;
 }
 

@@ -274,7 +274,7 @@ __device__ __forceinline__ void newton_group_add(const NewtonResult& r, DevStats
 // lane issues tiled tensor loads of whole rows into a ring of shared-memory
 // slots, each completing on the slot's `full` mbarrier; consumers release a
 // slot on its `empty` mbarrier.  Every wait is bounded.
-constexpr int kTmaWaitLimit = 1 << 20;   // try_wait calls before a wait gives up
+constexpr int kTmaWaitLimit = 1 << 24;   // most try_wait calls of one wait (the time limit comes first)
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count)
@@ -301,10 +301,22 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* b, unsigned pa
                  : "memory");
     return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* b, unsigned parity)
+__device__ __forceinline__ unsigned long long global_ns()
 {
-    for (int i = 0; i < kTmaWaitLimit; ++i)
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for phase `parity` of an mbarrier for at most limit_ns nanoseconds
+// (and at most kTmaWaitLimit polls); false when the wait gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* b, unsigned parity, long long limit_ns)
+{
+    if (mbar_try_wait(b, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (int i = 0; i < kTmaWaitLimit; ++i) {
         if (mbar_try_wait(b, parity)) return true;
+        if ((long long)(global_ns() - t0) > limit_ns) return false;
+    }
     return false;
 }
 // one row of every plane of the tensor map, box origin (x, row, plane 0)

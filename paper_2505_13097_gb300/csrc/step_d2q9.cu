@@ -210,9 +210,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) d2q9_step_kernel(StepA
 
 // ---------------------------------------------------------------- flat step
 // Single-problem FP32 step.  A tile is 128 columns x 8 rows; a block (8
-// warps) computes one tile at a time, one row per warp, four consecutive
-// columns per lane; blocks take tiles grid-stride (a persistent grid of the
-// resident blocks, strips of one row band before the next band).  Every pull
+// warps) computes one tile, one row per warp, four consecutive columns per
+// lane; consecutive blocks take the strips of one row band before the next
+// band.  Every pull
 // is a read-only load from global memory: for row y a lane loads the nine
 // planes of row y (its four columns; one 128-bit load each), planes 2, 5, 6
 // of row y - 1 and 4, 7, 8 of row y + 1, and the six elements just left or
@@ -260,9 +260,6 @@ __device__ __forceinline__ void flat_load_row(const float* __restrict__ row, lon
     qf[8][0] = e8; qf[8][1] = b8[0]; qf[8][2] = b8[1]; qf[8][3] = b8[2];
 }
 
-#ifndef LBM_FLAT_PERSIST
-#define LBM_FLAT_PERSIST 0   // 1: grid of the resident blocks, tiles grid-stride; 0: one tile per block
-#endif
 #ifndef LBM_FLAT_MINB
 #define LBM_FLAT_MINB 3   // resident blocks per SM the register budget is fitted to
 #endif
@@ -538,19 +535,20 @@ __global__ void __launch_bounds__(kTmaThreads, LBM_TMA_MIN_BLOCKS) d2q9_tma_kern
             for (int r = ya - 1; r <= yb; ++r) {
                 const int k = r - (ya - 1);
                 const int sl = k % kTmaStages;
-                if (k >= kTmaStages && !mbar_wait_bounded(&empty[sl], (unsigned)((k / kTmaStages - 1) & 1))) {
+                if (k >= kTmaStages && !mbar_wait_bounded(&empty[sl], (unsigned)((k / kTmaStages - 1) & 1), m.wait_ns)) {
                     ok = false;
                     break;
                 }
+                last = k;
+                if (k == m.withhold_load && blockIdx.x == 0) continue;   // test hook: this row never arrives
                 mbar_expect_tx(&full[sl], kTmaRowBytes);
                 tma_load_rows(lmap, ring + sl * kTmaSlot, &full[sl], segx - kTmaHalo, r + 1);
-                last = k;
             }
             if (!ok) {
                 atomicExch(&st->error, 4);   // LBM_ERR_TIMEOUT
                 // the copies still in flight land before the block may exit
                 for (int k = max(0, last - kTmaStages + 1); k <= last; ++k)
-                    (void)mbar_wait_bounded(&full[k % kTmaStages], (unsigned)((k / kTmaStages) & 1));
+                    (void)mbar_wait_bounded(&full[k % kTmaStages], (unsigned)((k / kTmaStages) & 1), m.wait_ns);
             }
         }
         return;
@@ -573,7 +571,7 @@ __global__ void __launch_bounds__(kTmaThreads, LBM_TMA_MIN_BLOCKS) d2q9_tma_kern
     GlobalJobSink sink{a.jobs, a.job_count};
     auto wait_row = [&](int r) -> bool {
         const int k = r - (ya - 1);
-        return mbar_wait_bounded(&full[k % kTmaStages], (unsigned)((k / kTmaStages) & 1));
+        return mbar_wait_bounded(&full[k % kTmaStages], (unsigned)((k / kTmaStages) & 1), m.wait_ns);
     };
     bool ok = wait_row(ya - 1) && wait_row(ya);
     for (int y = ya; ok && y < yb; ++y) {
@@ -688,18 +686,10 @@ cudaError_t launch_d2q9_tma(const StepArgs& a, const TmaMaps& m, cudaStream_t s)
 cudaError_t launch_d2q9_flat(const StepArgs& a, int nsegs, int ny, int method, cudaStream_t s, cudaStream_t side,
                              cudaEvent_t fork, cudaEvent_t join)
 {
-    static int grid[64] = {0};
-    int dev = 0;
+    int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidValue;
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (!grid[dev]) {
-        int n = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, d2q9_flat_kernel<false, false>, 256, 0);
-        grid[dev] = sms * (n > 0 ? n : 1);
-    }
     // rows that touch a wall: on the side stream when one is given, in
     // parallel with the interior rows (they write disjoint rows)
     const int nside = nsegs >= 2 ? 2 : 1;
@@ -719,8 +709,7 @@ cudaError_t launch_d2q9_flat(const StepArgs& a, int nsegs, int ny, int method, c
     // interior rows (if any strip has no wall column)
     const int nin = nsegs - 2;
     if (nin >= 1 && ny > 2) {
-        const int ntiles = nin * ((ny + 7) / 8);
-        const int g = LBM_FLAT_PERSIST ? grid[dev] : ntiles;   // one tile per block unless persistent
+        const int g = nin * ((ny + 7) / 8);   // one tile (4 x 256 columns, 8 rows) per block
         if (method == 1) {
             if (a.rec) d2q9_flat_kernel<true, true><<<g, 256, 0, s>>>(a);
             else d2q9_flat_kernel<false, true><<<g, 256, 0, s>>>(a);

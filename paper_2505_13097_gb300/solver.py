@@ -114,8 +114,9 @@ class Stefan:
         return out[0], out[1]
 
     def set_wait_test(self, wait_limit_s=2.0, withhold_load=-1):
-        """Test hook of the FP32 D2Q9 step: bound of its waits on row loads, and
-        a load (0, 1, 2) of its first work item that it skips (-1: none)."""
+        """Test hook of the TMA row-pipeline kernel: bound of its waits on row
+        loads, and a row load (0, 1, 2) of its first block that it skips; while a
+        load is withheld this FP32 D2Q9 handle steps with that kernel (-1: off)."""
         check(self.lib.lbm_stefan_set_wait_test(self.h, float(wait_limit_s), int(withhold_load)))
 
     def step_record(self, n, traj):

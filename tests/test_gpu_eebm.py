@@ -14,7 +14,7 @@ from paper_2505_13097_gb300 import _abi, workloads
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = [(97, 70), (130, 33), (64, 2)]
+SHAPES = [(97, 70), (130, 33), (64, 2), (515, 37), (400, 11)]   # the last two: interior strips
 WALLS = [
     {"W": (1, 1.0), "S": (1, -0.5), "E": (0, 0.0), "N": (0, 0.0)},
     {"W": (1, 0.8), "E": (1, 0.0), "S": (0, 0.0), "N": (1, 1.5)},

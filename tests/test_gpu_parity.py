@@ -107,6 +107,49 @@ def test_d2q9_fp32_parity(gpu, orc, shape, wi):
     assert np.max(np.abs(ph_g - phi(th_o, c.delta))) < TOL32_PHI
 
 
+# More than two 128-column strips: the interior rows run in the flat kernel,
+# the first and last strips and rows 0 and ny - 1 in the wall-row kernel;
+# ragged last strip and last 8-row band.  The initial field ramps through
+# theta = 0 at mid-width, so the interior rows hand nodes to the Newton job
+# kernel.  On the legacy stream and on a stream of the handle's own (there
+# the wall rows run concurrently on a second stream).
+@pytest.mark.parametrize("shape", [(515, 37), (384, 3), (700, 9), (1029, 18)])
+@pytest.mark.parametrize("wi", range(4))
+@pytest.mark.parametrize("own_stream", [False, True], ids=["legacy_stream", "own_stream"])
+def test_d2q9_fp32_flat_parity(gpu, orc, shape, wi, own_stream):
+    import torch
+    nx, ny = shape
+    c = workloads.Case("t", 2, nx, ny, 1.0, 0.01, 0.1, D2_WALLS[wi], 0, workloads.FP32)
+    ramp = 0.3 * (np.arange(nx) - nx / 2) / (nx / 2)
+    th0 = ramp[None, :] + workloads.random_field((ny, nx), -1e-3, 1e-3, seed=nx + 3 * ny + wi)
+    stream = torch.cuda.Stream() if own_stream else None
+    th_g, ph_g, _, th_o, st = run_pair(gpu, orc, c, 200, th0, stream=stream)
+    et, ep = rel_err(th_g, th_o), np.max(np.abs(ph_g - phi(th_o, c.delta)))
+    print("flat FP32 %dx%d walls %d: max|d theta|/max|theta| %.2e, max|d phi| %.2e, Newton nodes %d"
+          % (nx, ny, wi, et, ep, st["newton_nodes"]))
+    assert et < TOL32_T
+    assert ep < TOL32_PHI
+    assert st["newton_nodes"] > 0 and st["error"] == 0
+
+
+def test_d2q9_fp32_streams_bitwise_equal(gpu):
+    """The wall rows on a second stream give the same bits as in order."""
+    import torch
+    c = workloads.melt_2d(n=600, steps=60)
+    th0 = c.theta0()
+    th0[:, 250:350] += 0.2      # mushy nodes in the interior strips as well
+    outs = []
+    for stream in (None, torch.cuda.Stream()):
+        S = gpu.Stefan.from_case(c, stream=stream)
+        S.set_ic(th0)
+        S.step(c.steps)
+        outs.append((S.theta(), S.stats()))
+        S.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    for k in ("energy", "flux", "newton_nodes", "newton_iters"):
+        assert outs[0][1][k] == outs[1][1][k], k
+
+
 def test_d2q9_fp32_parity_melt_256(gpu, orc):
     # the 2D melting workload at 256 x 256, 2,000 steps
     c = workloads.melt_2d(n=256, steps=2000)

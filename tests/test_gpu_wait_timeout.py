@@ -1,13 +1,15 @@
-"""Failure detection of the FP32 D2Q9 step's bounded waits, without a GPU fault.
+"""Failure detection of the bounded device waits, without a GPU fault.
 
-The step waits for row loads that it issued itself (TMA copies completing on
-mbarriers), each wait bounded in time.  Through the test hook
-lbm_stefan_set_wait_test the step skips one row load of its first work item,
-so that the wait for it runs out after a short limit (5 ms here): the warp
-records LBM_ERR_TIMEOUT, waits for the copies it still has in flight and
-stops; the launch ends normally and the next synchronizing call returns the
-status.  Nothing faults or hangs, and a fresh handle on the same device then
-steps and matches the FP64 oracle.
+The TMA row-pipeline kernel (the FP32 D2Q9 step of batches) waits for row
+loads that its blocks issued themselves (TMA copies completing on
+mbarriers), each wait bounded in time.  While the test hook
+lbm_stefan_set_wait_test is on, a single FP32 D2Q9 handle steps with that
+kernel, and its first block skips one row load, so that the waits for it run
+out after a short limit (5 ms here): the block records LBM_ERR_TIMEOUT,
+waits (bounded) for the copies it still has in flight and stops; the launch
+ends normally and the next synchronizing call returns the status.  Nothing
+faults or hangs, and a fresh handle on the same device then steps and
+matches the FP64 oracle.
 """
 import numpy as np
 import pytest
