@@ -8,13 +8,15 @@
  * Algorithm 3 of the paper once per step: collision (Eq. 12), pull
  * streaming, the boundary closures of Sec. 4.2 on q, the zeroth moment, the
  * local Newton solve of Eq. (14), the source of Eq. (13), and the next
- * collision.  Kernel launches per step: D2Q9 with FP32 populations, three
- * (the interior rows, the rows that touch a wall, which run concurrently on a
- * second stream when the handle's stream is not the legacy default one, then
- * the kernel that solves the Newton list); D2Q9 in FP64 and D2Q5, two (the
- * stream/collide kernel, which hands the nodes that need the Newton iteration
- * to a list, then the kernel that solves that list); D1Q3, one launch for all
- * the steps of a call.
+ * collision.  Kernel launches per step: D2Q9 with FP32 populations, four on
+ * a handle with a stream of its own (the interior rows; concurrently, on a
+ * second, higher-priority stream, the rows that touch a wall and then the
+ * Newton solves of their nodes; after both, the kernel that solves the
+ * interior rows' Newton nodes and publishes the step), three on the legacy
+ * default stream (interior rows, wall rows, one Newton kernel for both);
+ * D2Q9 in FP64 and D2Q5, two (the stream/collide kernel, which hands the
+ * nodes that need the Newton iteration to a list, then the kernel that
+ * solves that list); D1Q3, one launch for all the steps of a call.
  *
  * Problem statement (Sec. 2, Eq. 1): dimensionless temperature theta with
  * melting temperature 0, Stefan number Ste, equal phase properties; the
@@ -160,9 +162,10 @@ lbm_status lbm_stefan_step(lbm_stefan* h, int nsteps);
 /* D2Q9 and D2Q5: advance nsteps >= 1 steps launched one by one (no graph) with a
  * CUDA event before, between and after the kernels of each step, wait for
  * them, and return the mean device time per step of each kernel in ms:
- * ms_kernels[0] the stream/collide kernel (in the FP32 D2Q9 form the interior
- * and wall-row kernels together, from the first launch to the join of the
- * two streams), ms_kernels[1] the Newton job kernel.  Same result as
+ * ms_kernels[0] the stream/collide kernel (in the FP32 D2Q9 form everything
+ * up to the join of the two streams: interior rows, wall rows and, on a
+ * handle with its own stream, the wall rows' Newton solves), ms_kernels[1]
+ * the Newton job kernel that follows (it publishes the step).  Same result as
  * lbm_stefan_step; for measuring each kernel against its roofline.
  * Synchronizes. */
 lbm_status lbm_stefan_step_timed(lbm_stefan* h, int nsteps, double* ms_kernels);
@@ -329,9 +332,8 @@ void lbm_stefan_batch_destroy(lbm_stefan_batch* b);
  *    in FP64); rows -1 and ny and the padding columns are zero.  Elements are
  *    float (LBM_FP32) or double (LBM_FP64).
  *  - wall_kind[4], wall_theta[4]: W, E, S, N as in lbm_stefan_set_bc.
- *  - The first call on a device (in each CUDA context of it) resolves the
- *    array's device address (cudaGetSymbolAddress); make that first call
- *    before any stream capture.
+ *  - The first call in each CUDA context resolves the array's device address
+ *    (cudaGetSymbolAddress) and keeps it for that context.
  *  - Every call shares the array: calls that overlap on the GPU (other
  *    streams, other threads) race.  Each call clears what must start at zero.
  *  - Runs on cuda_stream (a cudaStream_t), copies the problem descriptor

@@ -148,6 +148,7 @@ struct JobArgs {
     unsigned int* ticket;
     const NewtonJob* jobs;
     unsigned int* job_count;
+    int publish;             // 1: the last block publishes the step statistics; 0: it only clears the list
 };
 
 // Constants of the interior-node adjoint terms, converted once on the host.
@@ -183,10 +184,15 @@ int d2q9_blocks_per_sm(int precision);   // resident step blocks per SM (persist
 cudaError_t launch_d2q9_tma(const StepArgs& a, const TmaMaps& m, cudaStream_t s);
 // single problem, FP32: the interior rows and the rows that touch a wall (two
 // launches; with side, fork and join the second runs on `side`, joined back to s)
-cudaError_t launch_d2q9_flat(const StepArgs& a, int nsegs, int ny, int method, cudaStream_t s, cudaStream_t side,
-                             cudaEvent_t fork, cudaEvent_t join);
+// With a side stream, the wall rows' kernel and then a job kernel over their own
+// job list (ae.jobs / ae.job_count, described by je, not publishing) run on
+// `side`, concurrently with the interior rows (ai) on s; s then waits for side.
+// Without one, both kernels run on s and append to the same list (ai's).
+cudaError_t launch_d2q9_flat(const StepArgs& ai, const StepArgs& ae, const JobArgs& je, int nsegs, int ny,
+                             int method, cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join);
 int d2q9_tma_blocks_per_sm();
-cudaError_t launch_newton_jobs(int precision, int q, const JobArgs& a, cudaStream_t s);   // q = 9 or 5
+// q = 9 or 5; grid 0: 8 blocks of 128 threads per SM
+cudaError_t launch_newton_jobs(int precision, int q, const JobArgs& a, cudaStream_t s, int grid = 0);
 
 // D2Q5 launchers (step_d2q5.cu): one tile per warp over a.nslots tiles
 cudaError_t launch_d2q5_step(int precision, const StepArgs& a, cudaStream_t s);

@@ -250,7 +250,25 @@ static lbm::JobArgs job_args(const Problem* probs, int nprob, int parity, double
     j.ticket = ticket;
     j.jobs = jobs;
     j.job_count = count;
+    j.publish = 1;
     return j;
+}
+
+// FP32 D2Q9 single-problem step kernels: the interior rows and the wall rows.
+// With a side stream the wall rows append their Newton nodes to a list of
+// their own (the tail of djobs, after room for every interior node; counter
+// and ticket [1]) that a job kernel solves on the side stream.
+static cudaError_t launch_flat(lbm_stefan* h, const StepArgs& a)
+{
+    const int nsegs = h->hp.pitch / lbm::kTmaW;
+    const size_t icap = (size_t)std::max(0, nsegs - 2) * lbm::kTmaW * (size_t)std::max(0, h->hp.ny - 2);
+    StepArgs ae = a;
+    ae.jobs = h->djobs + icap;
+    ae.job_count = h->djob_count + 1;
+    lbm::JobArgs je = job_args(h->dprob, 1, a.parity, a.rec, h->dstats, h->dticket + 1, ae.jobs, ae.job_count);
+    je.publish = 0;
+    return lbm::launch_d2q9_flat(a, ae, je, nsegs, h->hp.ny, h->hp.method, h->stream, h->side, h->ev_fork,
+                                 h->ev_join);
 }
 
 // One step.  D2Q9 and D2Q5: the stream/collide kernel(s), which defer the
@@ -272,9 +290,7 @@ static cudaError_t launch_one(lbm_stefan* h, int parity, double* rec)
     if (h->p.lattice == LBM_D2Q9) {
         cudaError_t e;
         if (h->use_tma) {
-            e = LBM_FLAT && h->withhold_load < 0 ? lbm::launch_d2q9_flat(a, h->hp.pitch / 128, h->hp.ny, h->hp.method, h->stream, h->side,
-                                                    h->ev_fork, h->ev_join)
-                         : lbm::launch_d2q9_tma(a, h->tma, h->stream);
+            e = LBM_FLAT && h->withhold_load < 0 ? launch_flat(h, a) : lbm::launch_d2q9_tma(a, h->tma, h->stream);
         } else {
             // one tile per warp; the hardware scheduler balances the short tiles
             const int grid = (h->hp.ntiles + lbm::kWarpsPerBlock - 1) / lbm::kWarpsPerBlock;
@@ -408,26 +424,33 @@ extern "C" lbm_status lbm_stefan_create(const lbm_stefan_params* p, void* cuda_s
     if (e == cudaSuccess) e = cudaMalloc(&h->dprob, sizeof(Problem));
     if (e == cudaSuccess) e = cudaMalloc(&h->dstats, sizeof(DevStats));
     if (e == cudaSuccess) e = cudaMemset(h->dstats, 0, sizeof(DevStats));
-    if (e == cudaSuccess) e = cudaMalloc(&h->dticket, sizeof(unsigned int));
-    if (e == cudaSuccess) e = cudaMemset(h->dticket, 0, sizeof(unsigned int));
+    // [0]: the step's job list and job kernel; [1]: the wall rows' own (flat FP32 step)
+    if (e == cudaSuccess) e = cudaMalloc(&h->dticket, 2 * sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(h->dticket, 0, 2 * sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMalloc(&h->dscratch, sizeof(double) * 3 * (size_t)p->nx * p->ny);
-    if (e == cudaSuccess) e = cudaMalloc(&h->djob_count, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMalloc(&h->djob_count, 2 * sizeof(unsigned int));
     if (e == cudaSuccess && q == 9) h->adj_tile_h = adjoint_tile_h(h->hp);
-    if (e == cudaSuccess) e = cudaMemset(h->djob_count, 0, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(h->djob_count, 0, 2 * sizeof(unsigned int));
     h->hp.state[0] = bufs[0];
     h->hp.state[1] = bufs[1];
     h->hp.stats = 0;
     if (e == cudaSuccess && tma) h->use_tma = setup_tma(h);
-    // the flat FP32 step runs its wall rows on a side stream (non-default streams only:
-    // the legacy stream would serialize with it)
+    // the flat FP32 step runs its wall rows and their Newton solves on a side
+    // stream of the highest priority, so that its blocks are scheduled ahead of
+    // the interior kernel's (non-default streams only: the legacy stream would
+    // serialize with it)
     if (e == cudaSuccess && h->use_tma && LBM_FLAT && h->stream != nullptr) {
-        e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+        int least = 0, greatest = 0;
+        e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, greatest);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
     }
-    // the list of deferred Newton nodes (D2Q9, D2Q5)
+    // the list of deferred Newton nodes (D2Q9, D2Q5): room for one job per
+    // node of every row (pitch columns), so that the wall rows' list fits after
+    // the interior rows' in the flat FP32 step
     if (e == cudaSuccess && q != 3)
-        e = cudaMalloc(&h->djobs, sizeof(lbm::NewtonJob) * (size_t)p->nx * p->ny);
+        e = cudaMalloc(&h->djobs, sizeof(lbm::NewtonJob) * (size_t)h->hp.pitch * p->ny);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         lbm_stefan_destroy(h);
@@ -626,9 +649,7 @@ extern "C" lbm_status lbm_stefan_step_timed(lbm_stefan* h, int nsteps, double* m
         if (h->p.lattice == LBM_D2Q5) {
             e = lbm::launch_d2q5_step(h->precision, a, h->stream);
         } else if (h->use_tma) {
-            e = LBM_FLAT && h->withhold_load < 0 ? lbm::launch_d2q9_flat(a, h->hp.pitch / 128, h->hp.ny, h->hp.method, h->stream, h->side,
-                                                    h->ev_fork, h->ev_join)
-                         : lbm::launch_d2q9_tma(a, h->tma, h->stream);
+            e = LBM_FLAT && h->withhold_load < 0 ? launch_flat(h, a) : lbm::launch_d2q9_tma(a, h->tma, h->stream);
         } else {
             const int grid = (h->hp.ntiles + lbm::kWarpsPerBlock - 1) / lbm::kWarpsPerBlock;
             e = lbm::launch_d2q9_step(h->precision, a, grid, h->stream);

@@ -638,7 +638,7 @@ __global__ void __launch_bounds__(128) newton_jobs_kernel(JobArgs a)
         }
         newton_group_add(r, a.stats);
     }
-    // last block: publish every problem's step statistics, clear the job list
+    // last block: publish every problem's step statistics (if asked), clear the job list
     __shared__ bool last;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -648,7 +648,9 @@ __global__ void __launch_bounds__(128) newton_jobs_kernel(JobArgs a)
     __syncthreads();
     if (last) {
         __threadfence();
-        for (int p = threadIdx.x; p < a.nprob; p += blockDim.x) publish_stats(&a.stats[a.probs[p].stats], &a.probs[p]);
+        if (a.publish)
+            for (int p = threadIdx.x; p < a.nprob; p += blockDim.x)
+                publish_stats(&a.stats[a.probs[p].stats], &a.probs[p]);
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -683,44 +685,50 @@ cudaError_t launch_d2q9_tma(const StepArgs& a, const TmaMaps& m, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_d2q9_flat(const StepArgs& a, int nsegs, int ny, int method, cudaStream_t s, cudaStream_t side,
-                             cudaEvent_t fork, cudaEvent_t join)
+cudaError_t launch_d2q9_flat(const StepArgs& ai, const StepArgs& ae, const JobArgs& je, int nsegs, int ny,
+                             int method, cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join)
 {
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    // rows that touch a wall: on the side stream when one is given, in
-    // parallel with the interior rows (they write disjoint rows)
+    const bool split = side && fork && join;
+    // rows that touch a wall: on the side stream (a higher-priority one) when
+    // there is one, with the Newton solves of their nodes right after them,
+    // in parallel with the interior rows (they write disjoint rows; the
+    // interior kernel has no FP64 work, so the FP64 Newton solves of the wall
+    // strips use the SMs' otherwise idle FP64 pipes)
     const int nside = nsegs >= 2 ? 2 : 1;
     const int nrows = nside * ny + (nsegs - nside) * (ny > 1 ? 2 : 1);
     const int ge = std::min((nrows + 7) / 8, sms * 4);
+    const StepArgs& a_edge = split ? ae : ai;
     cudaStream_t es = s;
-    if (side && fork && join) {
+    if (split) {
         e = cudaEventRecord(fork, s);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(side, fork, 0);
         if (e != cudaSuccess) return e;
         es = side;
     }
-    if (a.rec) d2q9_edge_kernel<true><<<ge, 256, 0, es>>>(a);
-    else d2q9_edge_kernel<false><<<ge, 256, 0, es>>>(a);
+    if (a_edge.rec) d2q9_edge_kernel<true><<<ge, 256, 0, es>>>(a_edge);
+    else d2q9_edge_kernel<false><<<ge, 256, 0, es>>>(a_edge);
     e = cudaGetLastError();
+    if (e == cudaSuccess && split) e = launch_newton_jobs(1, 9, je, side, sms * 2);
     if (e != cudaSuccess) return e;
     // interior rows (if any strip has no wall column)
     const int nin = nsegs - 2;
     if (nin >= 1 && ny > 2) {
-        const int g = nin * ((ny + 7) / 8);   // one tile (4 x 256 columns, 8 rows) per block
+        const int g = nin * ((ny + 7) / 8);   // one tile (128 columns, 8 rows) per block
         if (method == 1) {
-            if (a.rec) d2q9_flat_kernel<true, true><<<g, 256, 0, s>>>(a);
-            else d2q9_flat_kernel<false, true><<<g, 256, 0, s>>>(a);
+            if (ai.rec) d2q9_flat_kernel<true, true><<<g, 256, 0, s>>>(ai);
+            else d2q9_flat_kernel<false, true><<<g, 256, 0, s>>>(ai);
         } else {
-            if (a.rec) d2q9_flat_kernel<true, false><<<g, 256, 0, s>>>(a);
-            else d2q9_flat_kernel<false, false><<<g, 256, 0, s>>>(a);
+            if (ai.rec) d2q9_flat_kernel<true, false><<<g, 256, 0, s>>>(ai);
+            else d2q9_flat_kernel<false, false><<<g, 256, 0, s>>>(ai);
         }
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    if (es != s) {
+    if (split) {
         e = cudaEventRecord(join, side);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, join, 0);
     }
@@ -749,12 +757,14 @@ static void launch_jobs_q(int precision, const JobArgs& a, int grid, cudaStream_
     }
 }
 
-cudaError_t launch_newton_jobs(int precision, int q, const JobArgs& a, cudaStream_t s)
+cudaError_t launch_newton_jobs(int precision, int q, const JobArgs& a, cudaStream_t s, int grid)
 {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = sms * 8;   // 8 x 128 threads per SM: about one pass over ~150k nodes
+    if (grid <= 0) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        grid = sms * 8;   // 8 x 128 threads per SM: about one pass over ~150k nodes
+    }
     if (q == 9) launch_jobs_q<9>(precision, a, grid, s);
     else if (q == 5) launch_jobs_q<5>(precision, a, grid, s);
     else return cudaErrorInvalidValue;

@@ -9,9 +9,14 @@ The reference curves of the paper's comparison are not available.  What the
 mathematics fixes instead:
 * the W and S walls are the same, so theta is symmetric about x = y;
 * a y-uniform D2Q9 or D2Q5 state evolves as D1Q3 (the velocities with equal
-  e_x carry the D1Q3 weights 2/3, 1/6, 1/6), and by 40 h heat has diffused
-  about 0.43 m, so the row at y = 3 m (3 m from the S wall, 1 m from the N
-  line) is the oracle's planar D1Q3 run of the same setup, to rounding;
+  e_x carry the D1Q3 weights 2/3, 1/6, 1/6), so the row on the N symmetry
+  line (y = 4 m, the farthest from the S wall) is the oracle's planar D1Q3
+  run of the same setup, up to the S wall's influence 4 m away and to
+  rounding: within 10 times the planar oracle's own one-ulp divergence (its
+  run from theta0 moved by one ulp at random nodes; the mushy zone amplifies
+  rounding by up to 1/(2 delta Ste) per step) plus 3 erfc(4 m / (2 sqrt(alpha
+  t))), the linear-diffusion bound on a wall 3 degrees (dimensionless) colder
+  at that distance (the latent heat only slows the cold front);
 * that planar run follows the Neumann solution (Sec. 2) of the equivalent
   melting problem (theta_hat = -theta/2: wall 1, liquid -1/2, Ste 2 x
   0.0521, delta / 2) to O(delta + dx): within one lattice spacing;
@@ -19,6 +24,8 @@ mathematics fixes instead:
 The front positions along the diagonal and along the planar row at 5, 20 and
 40 h are printed.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -50,11 +57,16 @@ def setup(lattice):
     return c, dx, steps
 
 
-def planar_oracle(orc, c, steps):
+def planar_oracle(orc, c, steps, perturb=False):
     """The oracle's D1Q3 run of the planar problem (W wall Dirichlet, E adiabatic),
-    theta after each of `steps` (cumulative)."""
+    theta after each of `steps` (cumulative); perturb: theta0 moved by one ulp at
+    random nodes."""
     P = orc.Problem(1, N, 1, tau=c.tau, delta=c.delta, ste=c.ste, walls={"W": c.walls["W"], "E": (0, 0.0)})
-    f = P.init(np.full((1, N), c.theta_init))
+    th0 = np.full((1, N), c.theta_init)
+    if perturb:
+        rng = np.random.Generator(np.random.PCG64(12345))
+        th0 = th0 + np.spacing(th0) * rng.choice([-1, 0, 1], size=th0.shape)
+    f = P.init(th0)
     out, done = [], 0
     for s in steps:
         for _ in range(s - done):
@@ -71,8 +83,12 @@ def first_zero(row):
 
 @pytest.fixture(scope="module")
 def planar(orc):
+    """Planar oracle rows at 5, 20, 40 h and the rounding floor of each."""
     c, dx, steps = setup(3)
-    return planar_oracle(orc, c, steps)
+    ref = planar_oracle(orc, c, steps)
+    alt = planar_oracle(orc, c, steps, perturb=True)
+    floors = [np.max(np.abs(a - r)) / np.max(np.abs(r)) for a, r in zip(alt, ref)]
+    return list(zip(ref, floors))
 
 
 @pytest.mark.parametrize("lattice", [3, 2], ids=["d2q5_eq17", "d2q9_mirror"])
@@ -82,9 +98,9 @@ def test_quarter_cavity_to_40h(gpu, planar, lattice):
     S = gpu.Stefan.from_case(c)
     S.set_ic(c.theta0())
     lam = neumann.stefan_lambda(2.0 * c.ste, -0.5)
-    yrow = 3 * (N - 1) // 4                 # y = 3 m
+    yrow = N - 1                            # y = 4 m, the N symmetry line
     done = 0
-    for h, s, ref in zip(HOURS, steps, planar):
+    for h, s, (ref, floor) in zip(HOURS, steps, planar):
         S.step(s - done)
         done = s
         th = S.theta()
@@ -94,15 +110,16 @@ def test_quarter_cavity_to_40h(gpu, planar, lattice):
         drow = np.max(np.abs(th[yrow] - ref)) / np.max(np.abs(ref))
         t = ALPHA * h * 3600.0
         xn = 2.0 * lam * np.sqrt(t)
+        tol_row = max(1e-12, 10.0 * floor) + 3.0 * math.erfc(4.0 / (2.0 * np.sqrt(t)))
         x_row = first_zero(th[yrow]) * dx
         diag = np.diagonal(th)
         x_diag = first_zero(diag) * dx * np.sqrt(2.0)   # distance from the corner along x = y
-        print("lattice %d, %2d h (%d steps): front along y = 3 m %.5f m (Neumann %.5f m, %.2f spacings), "
-              "along x = y %.5f m from the corner; asymmetry %.1e, row vs planar oracle %.1e, "
+        print("lattice %d, %2d h (%d steps): front along y = 4 m %.5f m (Neumann %.5f m, %.2f spacings), "
+              "along x = y %.5f m from the corner; asymmetry %.1e, row vs planar oracle %.1e (bound %.1e), "
               "energy imbalance max %.1e" % (lattice, h, s, x_row, xn, (x_row - xn) / dx, x_diag, asym, drow,
-                                             st["imbalance_max"]))
+                                             tol_row, st["imbalance_max"]))
         assert asym < 1e-10
-        assert drow < 1e-10
+        assert drow < tol_row
         assert abs(x_row - xn) < dx
         assert st["imbalance_max"] < 1e-9 * abs(st["energy"])
         # the corner freezes faster than the planar front: along the diagonal the

@@ -51,7 +51,17 @@ def test_paper_1d_case_on_the_gpu(orc):
     rel = abs(xf - neumann.front(T, lam)) / neumann.front(T, lam)
     lo, hi = g["front_error_band_irebm"]
     assert lo - 1e-3 <= rel <= hi + 1e-3, rel
-    # and the same field as the oracle
+    # and the same field as the oracle: within 1e-12 relative, or ten times the
+    # oracle's own rounding floor over these 200,749 steps (the oracle started
+    # from theta0 moved by one ulp at random nodes), where that is larger
     P = orc.Problem(1, n, 1, tau=tau, delta=delta, ste=ste, walls={"W": (1, 1.0), "E": (1, th_c)})
     _, tho = P.run(th0, steps)
-    assert np.max(np.abs(th - tho)) <= 1e-9
+    rng = np.random.Generator(np.random.PCG64(12345))
+    pert = th0 + np.spacing(th0) * rng.choice([-1, 0, 1], size=th0.shape)
+    _, alt = P.run(pert, steps)
+    scale = np.max(np.abs(tho))
+    tol = max(1e-12, 10.0 * np.max(np.abs(alt - tho)) / scale)
+    e = np.max(np.abs(th - tho)) / scale
+    print("paper 1D case, %d steps: GPU vs oracle %.2e (tolerance %.2e); max error vs Neumann %.3e "
+          "(printed %.3e); interface error %.2e of its position" % (steps, e, tol, err, g["max_error_irebm"], rel))
+    assert e < tol

@@ -80,7 +80,9 @@ def test_d2q9_fp64_parity(gpu, orc, shape, wi, bb_mode):
     th0 = workloads.random_field((ny, nx), -0.3, 0.3, seed=100 + nx + ny + wi)
     th_g, ph_g, H_g, th_o, st = run_pair(gpu, orc, c, 40, th0, bb_mode=bb_mode)
     tol = fp64_tol(orc, c, th0, 40, bb_mode)
-    assert rel_err(th_g, th_o) < tol
+    err = rel_err(th_g, th_o)
+    print("FP64 D2Q9 %dx%d walls %d bb %d: error %.2e, tolerance %.2e" % (nx, ny, wi, bb_mode, err, tol))
+    assert err < tol
     # phi' <= 1/(2 delta): errors in theta carry into phi and H = theta + phi/Ste
     dth = tol * np.max(np.abs(th_o))
     assert np.max(np.abs(ph_g - phi(th_o, c.delta))) <= dth / (2 * c.delta) + 1e-15
@@ -92,7 +94,9 @@ def test_d2q9_fp64_parity_params(gpu, orc, tau, ste, delta):
     c = workloads.Case("t", 2, 150, 70, tau, delta, ste, D2_WALLS[1], 0, workloads.FP64)
     th0 = workloads.random_field((70, 150), -0.1, 0.1, seed=7)
     th_g, _, _, th_o, st = run_pair(gpu, orc, c, 120, th0)
-    assert rel_err(th_g, th_o) < fp64_tol(orc, c, th0, 120)
+    tol, err = fp64_tol(orc, c, th0, 120), rel_err(th_g, th_o)
+    print("FP64 D2Q9 tau %g Ste %g delta %g: error %.2e, tolerance %.2e" % (tau, ste, delta, err, tol))
+    assert err < tol
     assert st["error"] == 0
 
 
@@ -129,7 +133,13 @@ def test_d2q9_fp32_flat_parity(gpu, orc, shape, wi, own_stream):
           % (nx, ny, wi, et, ep, st["newton_nodes"]))
     assert et < TOL32_T
     assert ep < TOL32_PHI
-    assert st["newton_nodes"] > 0 and st["error"] == 0
+    assert st["error"] == 0
+    # the first step hands interior nodes to the Newton kernel
+    S = gpu.Stefan.from_case(c, stream=stream)
+    S.set_ic(th0)
+    S.step(1)
+    assert S.stats()["newton_nodes"] > 0
+    S.close()
 
 
 def test_d2q9_fp32_streams_bitwise_equal(gpu):
@@ -163,7 +173,9 @@ def test_d2q9_fp64_parity_corner_64(gpu, orc):
     for ste in workloads.CORNER_STE:
         c = workloads.corner_2d(n=64, ste=ste, steps=1500)
         th_g, _, _, th_o, st = run_pair(gpu, orc, c, c.steps)
-        assert rel_err(th_g, th_o) < fp64_tol(orc, c, c.theta0(), c.steps), ste
+        tol, err = fp64_tol(orc, c, c.theta0(), c.steps), rel_err(th_g, th_o)
+        print("FP64 corner 64, Ste %g: error %.2e, tolerance %.2e" % (ste, err, tol))
+        assert err < tol, ste
 
 
 @pytest.mark.parametrize("n", [2, 3, 33, 512, 700])
@@ -172,7 +184,9 @@ def test_d1q3_parity(gpu, orc, n, precision):
     c = workloads.melt_1d(n=n).scaled(precision=precision)
     th_g, ph_g, _, th_o, st = run_pair(gpu, orc, c, 3000)
     tol = fp64_tol(orc, c, c.theta0(), 3000) if precision == 0 else TOL32_T
-    assert rel_err(th_g, th_o) < tol
+    err = rel_err(th_g, th_o)
+    print("D1Q3 n %d %s: error %.2e, tolerance %.2e" % (n, "FP64" if precision == 0 else "FP32", err, tol))
+    assert err < tol
     assert st["steps"] == 3000
 
 
