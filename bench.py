@@ -243,13 +243,14 @@ def bench_e2e(torch, solver, case, steps, stream, centre=None):
     return (t1 - t0) * 1e3, nbytes, 8 * n
 
 
-def bench_batch(torch, solver, workloads, steps, warmup, stream):
-    cases = workloads.batch_2d()
+def bench_batch(torch, solver, workloads, steps, warmup, stream, count=256, hi=1024, centre=None):
+    cases = workloads.batch_2d(count=count, hi=hi)
     B = solver.StefanBatch(cases, stream=stream)
     for k, c in enumerate(cases):
         B.set_ic(k, c.theta0())
     tile_h = B.autotune(trial_steps=5)
-    pre = max(0, cases[0].steps // 2 - steps // 2 - warmup)
+    centre = cases[0].steps // 2 if centre is None else centre
+    pre = max(0, centre - steps // 2 - warmup)
     B.step(pre + warmup)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -578,6 +579,13 @@ def run_gpu(args):
         if rank == 0:
             print(json.dumps({"bar_1d": bench_bar_1d(torch, solver, workloads, stream, steps=args.steps)}), flush=True)
         return 0
+    if args.only_batch:
+        # profiling aid: the batch leg alone (--batch-count problems, sides up to --batch-hi)
+        if rank == 0:
+            print(json.dumps({"batch": bench_batch(torch, solver, workloads, args.steps, args.warmup, stream,
+                                                   count=args.batch_count, hi=args.batch_hi,
+                                                   centre=args.window_step)}), flush=True)
+        return 0
     if args.only_d2q5:
         # profiling aid: the D2Q5 cavity leg alone, FP32
         if rank == 0:
@@ -703,6 +711,11 @@ def main():
                     help="time the 1D bar (IREBM, EEBM, ILFBM) alone, --steps steps each; a profiling aid")
     ap.add_argument("--only-d2q5", action="store_true",
                     help="time the D2Q5 cavity leg alone, FP32, side --n (default 4096); a profiling aid")
+    ap.add_argument("--only-batch", action="store_true",
+                    help="time the batch leg alone (--batch-count problems, sides log-uniform in [64, --batch-hi]); "
+                         "a profiling aid")
+    ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--batch-hi", type=int, default=1024)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

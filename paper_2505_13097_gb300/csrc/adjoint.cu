@@ -312,7 +312,7 @@ __device__ __forceinline__ void interior_terms(double A, double th0, double th1,
     gs += A * (phi_of(th1, c.inv_delta) - phi_of(th0, c.inv_delta)) * c.inv_ste * c.inv_ste / Fp;
 }
 
-__device__ __forceinline__ float lat_w_f(int i) { return i == 0 ? 4.0f / 9.0f : (i <= 4 ? 1.0f / 9.0f : 1.0f / 36.0f); }
+__device__ __forceinline__ float lat_w_f(int i) { return d2_wf(i); }
 template <typename P> __device__ __forceinline__ P lat_w_p(int i);
 template <> __device__ __forceinline__ float lat_w_p<float>(int i) { return lat_w_f(i); }
 template <> __device__ __forceinline__ double lat_w_p<double>(int i) { return d2_w(i); }

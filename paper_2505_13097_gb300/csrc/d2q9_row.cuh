@@ -97,7 +97,7 @@ static __device__ __noinline__ ff wall_closure_f(float* q, const float* u, int x
 #pragma unroll
         for (int i = 8; i >= 0; --i) {
             ff_add(th, u[i]);
-            if ((wi.unk >> i) & 1) wu += (float)d2_w(i);
+            if ((wi.unk >> i) & 1) wu += d2_wf(i);
             else ff_add(known, q[i]);
         }
         const ff m0t = dir_m0_target_f(th, k, pb);
@@ -106,7 +106,7 @@ static __device__ __noinline__ ff wall_closure_f(float* q, const float* u, int x
 #pragma unroll
         for (int i = 1; i < 9; ++i)
             if ((wi.unk >> i) & 1) {
-                q[i] = (float)d2_w(i) * r;
+                q[i] = d2_wf(i) * r;
                 ff_add(in, q[i]);
             }
     } else {

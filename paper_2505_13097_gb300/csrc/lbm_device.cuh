@@ -32,6 +32,23 @@ __host__ __device__ constexpr double d5_w(int i) { return i == 0 ? 1.0 / 3.0 : 1
 // weight i of the lattice with q velocities (3, 5 or 9)
 __host__ __device__ constexpr double lat_w(int q, int i) { return q == 9 ? d2_w(i) : (q == 5 ? d5_w(i) : d1_w(i)); }
 
+// FP32 weights.  The nearest floats to 4/9, 1/9, 1/36 sum to 1 + 2^-27, and
+// those to 1/3, 1/6 (D2Q5) to 1 + 2^-25.  A relaxation toward w_i c in FP32
+// multiplies the zeroth moment by that sum every step: on the 4096^2 melting
+// workload (tau = 1) theta drifted by 7.5e-9 of itself per step, 2.5e-5 after
+// 10,000 steps.  Here one weight of each set is one ulp below the nearest
+// float (1/36, resp. 1/3), so that each set sums to exactly 1; the products
+// w_i c still round, but without a bias.
+__host__ __device__ constexpr float d2_wf(int i) { return i == 0 ? 0x1.c71c72p-2f : (i <= 4 ? 0x1.c71c72p-4f : 0x1.c71c70p-6f); }
+__host__ __device__ constexpr float d5_wf(int i) { return i == 0 ? 0x1.555554p-2f : 0x1.555556p-3f; }
+// the weights of the population precision P (float: the exact-sum sets above)
+template <typename P> __host__ __device__ constexpr P lat_wp(int q, int i);
+template <> __host__ __device__ constexpr float lat_wp<float>(int q, int i)
+{
+    return q == 9 ? d2_wf(i) : (q == 5 ? d5_wf(i) : (float)d1_w(i));
+}
+template <> __host__ __device__ constexpr double lat_wp<double>(int q, int i) { return lat_w(q, i); }
+
 // ---------------------------------------------------------------- float-float
 // Unevaluated sum hi + lo of two floats; two_sum is Knuth's error-free
 // transformation (no fast-math: the compiler keeps the order of operations).

@@ -227,7 +227,7 @@ __device__ __forceinline__ NewtonResult newton_job_apply(const NewtonJob& jb, co
     const P omc = (P)(1.0 - pb.omega);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const P wi = (P)lat_w(Q, i);
+        const P wi = lat_wp<P>(Q, i);
         d[i * pb.plane] = fma(omc, qv[i], wi * c);
     }
     (void)x;

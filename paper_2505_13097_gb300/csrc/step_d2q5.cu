@@ -447,7 +447,7 @@ __device__ __forceinline__ void d2q5_tile(const Problem& pb, const P* __restrict
     const P omc = (P)(1.0 - pb.omega);
     const float om_f = (float)pb.omega;
     const double omc_d = 1.0 - pb.omega;
-    const P w0 = (P)d5_w(0), w1 = (P)d5_w(1);
+    const P w0 = lat_wp<P>(5, 0), w1 = lat_wp<P>(5, 1);
     const float thr_f = (float)pb.sat;
     const int ny = pb.ny;
 

@@ -79,7 +79,7 @@ __device__ __forceinline__ void d2q9_tile_direct(const Problem& pb, const P* __r
     const float om_f = (float)pb.omega;
     const double omc_d = 1.0 - pb.omega;
     const int nx = pb.nx, ny = pb.ny;
-    const P wP[3] = {(P)d2_w(0), (P)d2_w(1), (P)d2_w(5)};
+    const P wP[3] = {lat_wp<P>(9, 0), lat_wp<P>(9, 1), lat_wp<P>(9, 5)};
     const float thr_f = (float)pb.sat;
 
     auto rp = [&](int i, int r) -> const P* { return src + i * pl + (long long)(r + 1) * pitch + x0; };
@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(256, LBM_FLAT_MINB) d2q9_flat_kernel(const Ste
     float* __restrict__ dst = static_cast<float*>(pb.state[a.parity ^ 1]);
     const float omc = (float)(1.0 - pb.omega);
     const float om_f = (float)pb.omega;
-    const float wP[3] = {(float)d2_w(0), (float)d2_w(1), (float)d2_w(5)};
+    const float wP[3] = {d2_wf(0), d2_wf(1), d2_wf(5)};
     const float thr_f = (float)pb.sat;
     Acc<float> acc;
     TileSums ts;
@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(256) d2q9_edge_kernel(const StepArgs a)
     const float omc = (float)(1.0 - pb.omega);
     const float om_f = (float)pb.omega;
     const double omc_d = 1.0 - pb.omega;
-    const float wP[3] = {(float)d2_w(0), (float)d2_w(1), (float)d2_w(5)};
+    const float wP[3] = {d2_wf(0), d2_wf(1), d2_wf(5)};
     const float thr_f = (float)pb.sat;
     Acc<float> acc;
     TileSums ts;
@@ -559,7 +559,7 @@ __global__ void __launch_bounds__(kTmaThreads, LBM_TMA_MIN_BLOCKS) d2q9_tma_kern
     const float omc = (float)(1.0 - pb.omega);
     const float om_f = (float)pb.omega;
     const double omc_d = 1.0 - pb.omega;
-    const float wP[3] = {(float)d2_w(0), (float)d2_w(1), (float)d2_w(5)};
+    const float wP[3] = {d2_wf(0), d2_wf(1), d2_wf(5)};
     const float thr_f = (float)pb.sat;
     const int wx0 = segx + warp * 32;   // first column of this warp
     const bool warp_interior_x = wx0 > 0 && wx0 + 31 < nx - 1;

@@ -105,8 +105,9 @@ def test_config2_melt_2d_front_to_the_end(melt_full, orc):
     _, th1 = P.run(np.full((1, c.nx), c.theta_init), c.steps)
     xo = first_zero(th1[0])
     spread = r["lines"].max() - r["lines"].min()
-    print("config 2: mean front %.4f nodes, Neumann %.4f, oracle planar %.4f, spread over rows %.2e"
-          % (r["front"], xn, xo, spread))
+    print("config 2: mean front %.4f nodes, Neumann %.4f, oracle planar %.4f, spread over rows %.2e; "
+          "energy %.6e, last step's imbalance %.2e (max %.2e)"
+          % (r["front"], xn, xo, spread, st["energy"], st["imbalance"], st["imbalance_max"]))
     assert abs(r["front"] - xn) < 0.5
     assert abs(r["front"] - xo) < 0.02
     assert spread < 0.05
