@@ -418,30 +418,52 @@ __device__ __forceinline__ StepStripe* my_stripe(DevStats* st)
     return &st->cur[(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) % kStripes];
 }
 
-// Publish one problem's step statistics (called by the last block only).
-// E = fixed-point sum + (liquid nodes + sum_w Dirichlet nodes of wall w * phi(theta_w)) / Ste.
-__device__ __forceinline__ void publish_stats(DevStats* st, const Problem* pb)
+// Totals of one problem's stripes.
+struct StatSums {
+    unsigned long long e[4], f[4], dir[4], newton, iters, liquid;
+};
+
+// Read one stripe into `s` and clear it.
+__device__ __forceinline__ void stripe_take(StepStripe* stripe, StatSums& s)
 {
-    AccSum esum = {{0ull, 0ull, 0ull, 0ull}}, fsum = {{0ull, 0ull, 0ull, 0ull}};
-    unsigned long long newton = 0, iters = 0, liquid = 0, dir[4] = {0, 0, 0, 0};
-    for (int k = 0; k < kStripes; ++k) {
-        volatile StepStripe* c = &st->cur[k];
-        for (int j = 0; j < 4; ++j) {
-            esum.limb[j] += c->energy.limb[j];
-            fsum.limb[j] += c->flux.limb[j];
-            dir[j] += c->dir[j];
-        }
-        newton += c->newton;
-        iters += c->iters;
-        liquid += c->liquid;
+    volatile StepStripe* c = stripe;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        s.e[j] += c->energy.limb[j];
+        s.f[j] += c->flux.limb[j];
+        s.dir[j] += c->dir[j];
+    }
+    s.newton += c->newton;
+    s.iters += c->iters;
+    s.liquid += c->liquid;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        c->energy.limb[j] = 0ull;
+        c->flux.limb[j] = 0ull;
+        c->dir[j] = 0ull;
+    }
+    c->newton = 0ull;
+    c->iters = 0ull;
+    c->liquid = 0ull;
+}
+
+// The published step statistics from the stripe totals.
+// E = fixed-point sum + (liquid nodes + sum_w Dirichlet nodes of wall w * phi(theta_w)) / Ste.
+__device__ __forceinline__ void publish_totals(DevStats* st, const Problem* pb, const StatSums& s)
+{
+    AccSum esum, fsum;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        esum.limb[j] = s.e[j];
+        fsum.limb[j] = s.f[j];
     }
     double e = acc_read(&esum);
     const double f = acc_read(&fsum);
     volatile DevStats* v = st;
     if (pb) {
-        double c = (double)liquid;
+        double c = (double)s.liquid;
         for (int w = 0; w < 4; ++w)
-            if (dir[w]) c += (double)dir[w] * pb->wall_phi[w];
+            if (s.dir[w]) c += (double)s.dir[w] * pb->wall_phi[w];
         e += c * pb->inv_ste;
     }
     if (v->have_energy) {
@@ -456,21 +478,34 @@ __device__ __forceinline__ void publish_stats(DevStats* st, const Problem* pb)
     v->flux = f;
     v->have_energy = 1;
     v->steps = v->steps + 1;
-    v->newton_nodes = (long long)newton;
-    v->newton_iters = (long long)iters;
+    v->newton_nodes = (long long)s.newton;
+    v->newton_iters = (long long)s.iters;
     v->newton_max_iter = v->cur_maxit;
-    for (int k = 0; k < kStripes; ++k) {
-        volatile StepStripe* c = &st->cur[k];
-        for (int j = 0; j < 4; ++j) {
-            c->energy.limb[j] = 0ull;
-            c->flux.limb[j] = 0ull;
-            c->dir[j] = 0ull;
-        }
-        c->newton = 0ull;
-        c->iters = 0ull;
-        c->liquid = 0ull;
-    }
     v->cur_maxit = 0;
+}
+
+// Publish one problem's step statistics and clear its stripes (one thread of
+// the last block).
+__device__ __forceinline__ void publish_stats(DevStats* st, const Problem* pb)
+{
+    StatSums s = {};
+    for (int k = 0; k < kStripes; ++k) stripe_take(&st->cur[k], s);
+    publish_totals(st, pb, s);
+}
+
+// The same with one warp: lane k takes stripe k, the warp adds the totals
+// (integer sums: the result is the one thread's), lane 0 publishes.
+__device__ __forceinline__ void publish_stats_warp(DevStats* st, const Problem* pb, int lane)
+{
+    static_assert(kStripes == 32, "one stripe per lane");
+    StatSums s = {};
+    stripe_take(&st->cur[lane], s);
+    unsigned long long* v = &s.e[0];   // the 15 fields in order
+#pragma unroll
+    for (int k = 0; k < 15; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(kFull, v[k], o);
+    if (lane == 0) publish_totals(st, pb, s);
 }
 
 // Last-block pattern: every block calls this after its warps have added their

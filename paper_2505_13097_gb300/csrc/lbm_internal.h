@@ -191,8 +191,8 @@ cudaError_t launch_d2q9_tma(const StepArgs& a, const TmaMaps& m, cudaStream_t s)
 cudaError_t launch_d2q9_flat(const StepArgs& ai, const StepArgs& ae, const JobArgs& je, int nsegs, int ny,
                              int method, cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join);
 int d2q9_tma_blocks_per_sm();
-// q = 9 or 5; grid 0: 8 blocks of 128 threads per SM
-cudaError_t launch_newton_jobs(int precision, int q, const JobArgs& a, cudaStream_t s, int grid = 0);
+// q = 9 or 5; grid 0: 8 blocks of 128 threads per SM; prio != 0: that scheduling priority
+cudaError_t launch_newton_jobs(int precision, int q, const JobArgs& a, cudaStream_t s, int grid = 0, int prio = 0);
 
 // D2Q5 launchers (step_d2q5.cu): one tile per warp over a.nslots tiles
 cudaError_t launch_d2q5_step(int precision, const StepArgs& a, cudaStream_t s);

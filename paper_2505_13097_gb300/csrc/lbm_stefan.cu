@@ -568,7 +568,8 @@ static lbm_status capture_graph(lbm_stefan* h)
         if (g) cudaGraphDestroy(g);
         return fail(LBM_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
     }
-    e = cudaGraphInstantiate(&h->graph.exec, g, 0);
+    // per-node priorities: the wall rows' kernels keep their higher priority
+    e = cudaGraphInstantiate(&h->graph.exec, g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
     h->graph.steps = kGraphSteps;
@@ -949,7 +950,7 @@ extern "C" lbm_status lbm_stefan_adjoint_segment(lbm_stefan* h, const void* chec
         CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = segment_launches(h, nsteps, theta_traj, adj, adj_other, 0);
         cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
-        if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+        if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&exec, g, cudaGraphInstantiateFlagUseNodePriority);
         if (g) cudaGraphDestroy(g);
         if (e != cudaSuccess || e2 != cudaSuccess || !exec)
             return fail(LBM_ERR_CUDA, "segment capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));

@@ -648,9 +648,16 @@ __global__ void __launch_bounds__(128) newton_jobs_kernel(JobArgs a)
     __syncthreads();
     if (last) {
         __threadfence();
-        if (a.publish)
-            for (int p = threadIdx.x; p < a.nprob; p += blockDim.x)
-                publish_stats(&a.stats[a.probs[p].stats], &a.probs[p]);
+        if (a.publish) {
+            const int nw = blockDim.x >> 5, w = threadIdx.x >> 5;
+            if (a.nprob <= nw) {
+                // few problems: a warp each, one stripe per lane
+                if (w < a.nprob) publish_stats_warp(&a.stats[a.probs[w].stats], &a.probs[w], threadIdx.x & 31);
+            } else {
+                for (int p = threadIdx.x; p < a.nprob; p += blockDim.x)
+                    publish_stats(&a.stats[a.probs[p].stats], &a.probs[p]);
+            }
+        }
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -658,6 +665,25 @@ __global__ void __launch_bounds__(128) newton_jobs_kernel(JobArgs a)
             *a.ticket = 0u;
         }
     }
+}
+
+// A launch with an explicit scheduling priority (0: the stream's own).  The
+// priority is a launch attribute, so a graph captured from the stream keeps
+// it per kernel node.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_prio(void (*k)(KArgs...), int grid, int block, cudaStream_t s, int prio, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributePriority;
+    at[0].val.priority = prio;
+    cfg.attrs = at;
+    cfg.numAttrs = prio != 0 ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, args...);
 }
 
 template <typename P, bool REC>
@@ -703,16 +729,17 @@ cudaError_t launch_d2q9_flat(const StepArgs& ai, const StepArgs& ae, const JobAr
     const int ge = std::min((nrows + 7) / 8, sms * 4);
     const StepArgs& a_edge = split ? ae : ai;
     cudaStream_t es = s;
+    int prio = 0;
     if (split) {
-        e = cudaEventRecord(fork, s);
+        int least = 0;
+        e = cudaDeviceGetStreamPriorityRange(&least, &prio);
+        if (e == cudaSuccess) e = cudaEventRecord(fork, s);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(side, fork, 0);
         if (e != cudaSuccess) return e;
         es = side;
     }
-    if (a_edge.rec) d2q9_edge_kernel<true><<<ge, 256, 0, es>>>(a_edge);
-    else d2q9_edge_kernel<false><<<ge, 256, 0, es>>>(a_edge);
-    e = cudaGetLastError();
-    if (e == cudaSuccess && split) e = launch_newton_jobs(1, 9, je, side, sms * 2);
+    e = launch_prio(a_edge.rec ? d2q9_edge_kernel<true> : d2q9_edge_kernel<false>, ge, 256, es, prio, a_edge);
+    if (e == cudaSuccess && split) e = launch_newton_jobs(1, 9, je, side, sms * 2, prio);
     if (e != cudaSuccess) return e;
     // interior rows (if any strip has no wall column)
     const int nin = nsegs - 2;
@@ -746,18 +773,15 @@ int d2q9_tma_blocks_per_sm()
 }
 
 template <int Q>
-static void launch_jobs_q(int precision, const JobArgs& a, int grid, cudaStream_t s)
+static cudaError_t launch_jobs_q(int precision, const JobArgs& a, int grid, cudaStream_t s, int prio)
 {
-    if (precision == 1) {
-        if (a.rec) newton_jobs_kernel<float, true, Q><<<grid, 128, 0, s>>>(a);
-        else newton_jobs_kernel<float, false, Q><<<grid, 128, 0, s>>>(a);
-    } else {
-        if (a.rec) newton_jobs_kernel<double, true, Q><<<grid, 128, 0, s>>>(a);
-        else newton_jobs_kernel<double, false, Q><<<grid, 128, 0, s>>>(a);
-    }
+    void (*k)(JobArgs) = precision == 1
+                             ? (a.rec ? newton_jobs_kernel<float, true, Q> : newton_jobs_kernel<float, false, Q>)
+                             : (a.rec ? newton_jobs_kernel<double, true, Q> : newton_jobs_kernel<double, false, Q>);
+    return launch_prio(k, grid, 128, s, prio, a);
 }
 
-cudaError_t launch_newton_jobs(int precision, int q, const JobArgs& a, cudaStream_t s, int grid)
+cudaError_t launch_newton_jobs(int precision, int q, const JobArgs& a, cudaStream_t s, int grid, int prio)
 {
     if (grid <= 0) {
         int dev = 0, sms = 0;
@@ -765,10 +789,9 @@ cudaError_t launch_newton_jobs(int precision, int q, const JobArgs& a, cudaStrea
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         grid = sms * 8;   // 8 x 128 threads per SM: about one pass over ~150k nodes
     }
-    if (q == 9) launch_jobs_q<9>(precision, a, grid, s);
-    else if (q == 5) launch_jobs_q<5>(precision, a, grid, s);
-    else return cudaErrorInvalidValue;
-    return cudaGetLastError();
+    if (q == 9) return launch_jobs_q<9>(precision, a, grid, s, prio);
+    if (q == 5) return launch_jobs_q<5>(precision, a, grid, s, prio);
+    return cudaErrorInvalidValue;
 }
 
 int d2q9_blocks_per_sm(int precision)
