@@ -101,7 +101,13 @@ typedef struct {
 /* ---------------------------------------------------------------- one problem
  * State buffers (lbm_stefan_layout): q planes of populations (ny + 2 rows of
  * row_stride elements each, the first and last rows zero halo rows); D1Q3
- * adds a fourth plane, the liquid fraction of LBM_ILFBM. */
+ * adds a fourth plane, the liquid fraction of LBM_ILFBM (D2Q9 / D2Q5 with
+ * ILFBM: a plane after the q); then a 256-byte tail.  The populations are the
+ * post-collision Omega_i of the stored-Omega form.  FP32 D2Q9 / D2Q5 states
+ * store Omega_i - w_i s, s being a float in the first 4 bytes of the tail
+ * (M0 = s + the sum of the stored values): set_ic sets s to the mean of the
+ * initial M0 (theta0; EEBM: its enthalpy), so that stored values near s are
+ * small and round finely.  The tail is zero in the other forms. */
 
 /* Create a problem.  cuda_stream is a cudaStream_t (NULL = legacy default
  * stream).  All walls start adiabatic; the state is undefined until set_ic. */
@@ -329,8 +335,10 @@ void lbm_stefan_batch_destroy(lbm_stefan_batch* b);
  *  - Buffers (device, caller-owned, distinct): the state layout of
  *    lbm_stefan_layout / lbm_stefan_get_state: 9 planes; each plane has ny + 2
  *    rows of `pitch` elements (pitch = nx rounded up to 128 elements in FP32, 64
- *    in FP64); rows -1 and ny and the padding columns are zero.  Elements are
- *    float (LBM_FP32) or double (LBM_FP64).
+ *    in FP64); rows -1 and ny and the padding columns are zero; then the
+ *    256-byte tail (FP32: the shift s, see the state buffers above), which the
+ *    call copies from state_in to state_out.  Elements are float (LBM_FP32) or
+ *    double (LBM_FP64).
  *  - wall_kind[4], wall_theta[4]: W, E, S, N as in lbm_stefan_set_bc.
  *  - The first call in each CUDA context resolves the array's device address
  *    (cudaGetSymbolAddress) and keeps it for that context.

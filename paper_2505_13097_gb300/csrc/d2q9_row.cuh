@@ -81,8 +81,10 @@ static __device__ __noinline__ double wall_closure_d(double* q, const double* u,
 }
 
 // FP32 form: the same closure with float-float sums and no FP64 instruction on
-// the common path (dir_m0_target_f).
-static __device__ __noinline__ ff wall_closure_f(float* q, const float* u, int x, int y, const Problem& pb, int& wall)
+// the common path (dir_m0_target_f).  q and u hold Omega less w_i sh (the
+// state's shift): theta = sum u + sh, and the unknown q share the target less sh.
+static __device__ __noinline__ ff wall_closure_f(float* q, const float* u, int x, int y, const Problem& pb, int& wall,
+                                                 float sh)
 {
     const WallInfo wi = wall_info(x, y, pb);
     wall = wi.wall;
@@ -100,7 +102,9 @@ static __device__ __noinline__ ff wall_closure_f(float* q, const float* u, int x
             if ((wi.unk >> i) & 1) wu += d2_wf(i);
             else ff_add(known, q[i]);
         }
-        const ff m0t = dir_m0_target_f(th, k, pb);
+        ff_add(th, sh);
+        ff m0t = dir_m0_target_f(th, k, pb);
+        ff_add(m0t, -sh);
         // R = m0t - sum(known), shared by the unknown q in proportion to w_i
         const float r = ((m0t.hi - known.hi) + (m0t.lo - known.lo)) / wu;
 #pragma unroll
@@ -179,8 +183,9 @@ __device__ __forceinline__ void row_update(const Problem& pb, int y, int x0, int
                                            const Out& out, double* __restrict__ rec, Acc<P>& acc, TileSums& ts,
                                            int pi, Sink& sink, const P omc,
                                            const float om_f, const double omc_d, const P (&wP)[3], const float thr_f,
-                                           const int nx, const int ny)
+                                           const int nx, const int ny, const float sh)
 {
+    // sh: the state's shift (FP32 form; the stored values are Omega_i - w_i sh)
     const long long pitch = pb.pitch;
     P c[N];          // per node: theta' - (1-omega) m0, rounded to P
     double thn[REC ? N : 1];
@@ -210,7 +215,7 @@ __device__ __forceinline__ void row_update(const Problem& pb, int y, int x0, int
                 uu[0] = u0[k]; uu[1] = u1[k]; uu[2] = u2[k]; uu[3] = u3[k]; uu[4] = u4[k];
                 uu[5] = u5[k]; uu[6] = u6[k]; uu[7] = u7[k]; uu[8] = u8[k];
                 if constexpr (sizeof(P) == 4) {
-                    const ff fl = wall_closure_f(qq, uu, x, y, pb, wall_k[k]);
+                    const ff fl = wall_closure_f(qq, uu, x, y, pb, wall_k[k], sh);
                     ff_add(ts.flux_f, fl.hi);
                     ts.flux_f.lo += fl.lo;
                 } else {
@@ -229,8 +234,8 @@ __device__ __forceinline__ void row_update(const Problem& pb, int y, int x0, int
         const int x = x0 + k;
         const bool valid = !EDGE || x < nx;
         const P u[9] = {u0[k], u1[k], u2[k], u3[k], u4[k], u5[k], u6[k], u7[k], u8[k]};
-        const float tf = approx_sum<P>(u);
-        float mf;
+        const float tf = sizeof(P) == 4 ? approx_sum<P>(u) + sh : approx_sum<P>(u);
+        float mf;   // FP32 form: M0(q) less sh
         if constexpr (sizeof(P) == 4) {
             // FP32 form: a plain FP32 sum (small weights first) decides saturation and
             // gives theta' = m0 there, to the rounding of the stored populations; the
@@ -245,9 +250,10 @@ __device__ __forceinline__ void row_update(const Problem& pb, int y, int x0, int
             for (int i = 8; i >= 0; --i) m0_add(m0[k], qf[i][k]);
             mf = m0_f(m0[k]);
         }
+        const float mt = sizeof(P) == 4 ? mf + sh : mf;   // M0(q)
         const float marg = 1e-5f * (1.0f + fabsf(tf));
-        const bool sat_liq = tf >= thr_f + marg && mf >= thr_f + marg;
-        const bool sat_sol = tf <= -thr_f - marg && mf <= -thr_f - marg;
+        const bool sat_liq = tf >= thr_f + marg && mt >= thr_f + marg;
+        const bool sat_sol = tf <= -thr_f - marg && mt <= -thr_f - marg;
         newton_k[k] = valid && !dir_k[k] && !(sat_liq || sat_sol);
         any_newton |= newton_k[k];
         if (!valid) {
@@ -265,7 +271,8 @@ __device__ __forceinline__ void row_update(const Problem& pb, int y, int x0, int
 #pragma unroll
                 for (int i = 8; i >= 0; --i) ff_add(mm, qf[i][k]);
                 const float oc = (float)omc;
-                c[k] = (P)((pb.wall_th_hi[wk] - oc * mm.hi) + (pb.wall_th_lo[wk] - oc * mm.lo));
+                // c less omega sh: (theta_D - sh) - (1-omega) M0(q less sh)
+                c[k] = (P)(((pb.wall_th_hi[wk] - sh) - oc * mm.hi) + (pb.wall_th_lo[wk] - oc * mm.lo));
                 acc.add_ff(ff{pb.wall_th_hi[wk], pb.wall_th_lo[wk]});
             } else {
                 c[k] = (P)(pb.wall_theta[wk] - omc_d * m0_d(m0[k]));
@@ -275,9 +282,11 @@ __device__ __forceinline__ void row_update(const Problem& pb, int y, int x0, int
         } else if (!newton_k[k]) {
             // saturated: theta' = m0, no source; c = omega * m0
             if constexpr (sizeof(P) == 4) {
+                // less the shift: c - omega sh = omega (m0 - sh); the energy term m0 - sh
                 c[k] = (P)(om_f * mf);
                 acc.add_f(mf);
-                if constexpr (REC) thn[k] = (double)mf;
+                ts.shifted += 1;
+                if constexpr (REC) thn[k] = (double)mf + (double)sh;
             } else {
                 const double md = m0_d(m0[k]);
                 c[k] = (P)(pb.omega * md);
@@ -374,8 +383,9 @@ __device__ __forceinline__ void row_update_eebm(const Problem& pb, int y, int x0
                                                 const P (&u4)[N], const P (&u5)[N], const P (&u6)[N],
                                                 const P (&u7)[N], const P (&u8)[N], const Out& out,
                                                 double* __restrict__ rec, Acc<P>& acc, TileSums& ts, const P omc,
-                                                const P (&wP)[3], const int nx, const int ny)
+                                                const P (&wP)[3], const int nx, const int ny, const float sh)
 {
+    // sh: the state's shift in enthalpy units (FP32 form; stored Omega_i - w_i sh)
     const long long pitch = pb.pitch;
     if constexpr (EDGE) {
         bool any_wall = false;
@@ -396,7 +406,7 @@ __device__ __forceinline__ void row_update_eebm(const Problem& pb, int y, int x0
                     uu[0] = u0[k]; uu[1] = u1[k]; uu[2] = u2[k]; uu[3] = u3[k]; uu[4] = u4[k];
                     uu[5] = u5[k]; uu[6] = u6[k]; uu[7] = u7[k]; uu[8] = u8[k];
                     if constexpr (sizeof(P) == 4) {
-                        const ff fl = wall_closure_f(qq, uu, x, y, pb, wall);
+                        const ff fl = wall_closure_f(qq, uu, x, y, pb, wall, sh);
                         ff_add(ts.flux_f, fl.hi);
                         ts.flux_f.lo += fl.lo;
                     } else {
@@ -415,20 +425,33 @@ __device__ __forceinline__ void row_update_eebm(const Problem& pb, int y, int x0
 #pragma unroll
     for (int k = 0; k < N; ++k) {
         const bool valid = !EDGE || x0 + k < nx;
-        P H = 0;
+        P Hs = 0;   // H less the shift (FP32 form)
 #pragma unroll
-        for (int i = 8; i >= 0; --i) H += qf[i][k];
+        for (int i = 8; i >= 0; --i) Hs += qf[i][k];
         if (!valid) {
-            H = 0;
+            Hs = 0;
 #pragma unroll
             for (int i = 0; i < 9; ++i) qf[i][k] = (P)0;
         }
-        const P th = eebm_theta(H, inv_ste);
-        hs += H;
-        if constexpr (REC) thn[k] = (double)th;
-        qf[0][k] = fma(omc, qf[0][k], om * (H - ((P)1 - wP[0]) * th));
+        hs += Hs;
+        if constexpr (sizeof(P) == 4) {
+            const float H = Hs + sh;
+            const float th = eebm_theta(H, inv_ste);
+            if constexpr (REC) thn[k] = (double)th;
+            ts.shifted += valid ? 1 : 0;
+            // stored values less w_i sh: omega (H - (1-w_0) theta - w_0 sh) and omega w_i (theta - sh)
+            qf[0][k] = fma(omc, qf[0][k], om * (H - ((P)1 - wP[0]) * th - wP[0] * sh));
+            const float tr = th - sh;
 #pragma unroll
-        for (int i = 1; i < 9; ++i) qf[i][k] = fma(omc, qf[i][k], om * (i <= 4 ? wP[1] : wP[2]) * th);
+            for (int i = 1; i < 9; ++i) qf[i][k] = fma(omc, qf[i][k], om * (i <= 4 ? wP[1] : wP[2]) * tr);
+        } else {
+            const P H = Hs;
+            const P th = eebm_theta(H, inv_ste);
+            if constexpr (REC) thn[k] = (double)th;
+            qf[0][k] = fma(omc, qf[0][k], om * (H - ((P)1 - wP[0]) * th));
+#pragma unroll
+            for (int i = 1; i < 9; ++i) qf[i][k] = fma(omc, qf[i][k], om * (i <= 4 ? wP[1] : wP[2]) * th);
+        }
     }
     if constexpr (sizeof(P) == 4) acc.add_ff(ff{hs, 0.f});
     else acc.add_d(hs);

@@ -20,11 +20,42 @@ __device__ __forceinline__ bool dirichlet_value(const Problem& pb, int x, int y,
     return false;
 }
 
+// The shift s of an FP32 state (its populations are stored less w_i s): the
+// mean over the nodes of the initial M0 (theta0; EEBM: H(theta0)), rounded to
+// a float, written to the tail of both buffers.  With most nodes near s the
+// stored values are small, and so are their rounding errors: on a smooth
+// field, storing Omega_i itself in FP32 lets the rounding of w_i theta drift
+// coherently (2.4e-5 of theta after 10,000 steps of the 4096^2 melting
+// workload).  One block; a fixed summation order (deterministic).
+__global__ void __launch_bounds__(1024) shift_kernel(const Problem* dprob, const double* __restrict__ theta0)
+{
+    __shared__ double part[1024];
+    const Problem& pb = *dprob;
+    const long long n = (long long)pb.nx * pb.ny;
+    double v = 0.0;
+    for (long long k = threadIdx.x; k < n; k += blockDim.x) {
+        const double th = theta0[k];
+        v += pb.method == 1 ? th + (th > 0.0 ? pb.inv_ste : 0.0) : th;
+    }
+    part[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const float sh = n > 0 ? (float)(part[0] / (double)n) : 0.f;
+        for (int b = 0; b < 2; ++b) *reinterpret_cast<float*>(static_cast<char*>(pb.state[b]) + pb.tail_off) = sh;
+    }
+}
+
 template <typename P>
 __global__ void init_state_kernel(const Problem* dprob, const double* __restrict__ theta0, int parity, DevStats* st)
 {
     const Problem& pb = *dprob;
     P* s = static_cast<P*>(pb.state[parity]);
+    // FP32: the populations are stored less w_i sh
+    const double sh = sizeof(P) == 4 ? (double)state_shift(pb, parity) : 0.0;
     const long long n = (long long)pb.nx * pb.ny;
     double e = 0.0;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
@@ -37,11 +68,12 @@ __global__ void init_state_kernel(const Problem* dprob, const double* __restrict
             const double H = th + (th > 0.0 ? pb.inv_ste : 0.0);
             for (int i = 0; i < pb.q; ++i)
                 s[i * pb.plane + (long long)(y + 1) * pb.pitch + x] =
-                    (P)(i == 0 ? H - (1.0 - lat_w(pb.q, 0)) * th : lat_w(pb.q, i) * th);
+                    (P)(i == 0 ? H - (1.0 - lat_w(pb.q, 0)) * th - lat_w(pb.q, 0) * sh : lat_w(pb.q, i) * (th - sh));
             e += H;
             continue;
         }
-        for (int i = 0; i < pb.q; ++i) s[i * pb.plane + (long long)(y + 1) * pb.pitch + x] = (P)(lat_w(pb.q, i) * th);
+        for (int i = 0; i < pb.q; ++i)
+            s[i * pb.plane + (long long)(y + 1) * pb.pitch + x] = (P)(lat_w(pb.q, i) * (th - sh));
         if (pb.method == 2) {
             // ILFBM (Algorithm 1): the liquid fraction of the initial phase, plane q
             const double l = th > 0.0 ? 1.0 : 0.0;
@@ -99,10 +131,11 @@ __global__ void fields_kernel(const Problem* dprob, int parity, double* theta, d
 {
     const Problem& pb = *dprob;
     const P* s = static_cast<const P*>(pb.state[parity]);
+    const double sh = sizeof(P) == 4 ? (double)state_shift(pb, parity) : 0.0;   // FP32: stored less w_i sh
     const long long n = (long long)pb.nx * pb.ny;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(k % pb.nx), y = (int)(k / pb.nx);
-        double th = 0.0;
+        double th = sh;
         for (int i = pb.q - 1; i >= 0; --i) th += (double)s[i * pb.plane + (long long)(y + 1) * pb.pitch + x];
         if (pb.method == 1) {
             // EEBM: M0 is the enthalpy; theta = Theta(H), liquid fraction min(max(Ste H, 0), 1)
@@ -138,6 +171,7 @@ __global__ void front_kernel(const Problem* dprob, int parity, int wall, double*
     const bool rows = wall <= 1;
     const int nlines = rows ? pb.ny : pb.nx;
     const int n = rows ? pb.nx : pb.ny;
+    const double sh = sizeof(P) == 4 ? (double)state_shift(pb, parity) : 0.0;   // FP32: stored less w_i sh
     const int lane = threadIdx.x & 31;
     const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -148,7 +182,7 @@ __global__ void front_kernel(const Problem* dprob, int parity, int wall, double*
             else if (wall == 1) { x = pb.nx - 1 - i; y = line; }
             else if (wall == 2) { x = line; y = i; }
             else { x = line; y = pb.ny - 1 - i; }
-            double th = 0.0;
+            double th = sh;
             for (int k = pb.q - 1; k >= 0; --k) th += (double)s[k * pb.plane + (long long)(y + 1) * pb.pitch + x];
             return pb.method == 1 ? eebm_theta(th, pb.inv_ste) : th;
         };
@@ -203,6 +237,12 @@ cudaError_t launch_init_state(int precision, const Problem* dprob, const Problem
                               int parity, DevStats* st, cudaStream_t s)
 {
     const int g = grid_for((long long)hp.nx * hp.ny);
+    // FP32 D2Q9 / D2Q5 states carry a shift (FP64 and D1Q3 tails stay zero)
+    if (precision == 1 && hp.q != 3) {
+        shift_kernel<<<1, 1024, 0, s>>>(dprob, theta0);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     if (precision == 1) init_state_kernel<float><<<g, 256, 0, s>>>(dprob, theta0, parity, st);
     else init_state_kernel<double><<<g, 256, 0, s>>>(dprob, theta0, parity, st);
     return cudaGetLastError();

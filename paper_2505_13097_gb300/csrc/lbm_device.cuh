@@ -420,8 +420,14 @@ __device__ __forceinline__ StepStripe* my_stripe(DevStats* st)
 
 // Totals of one problem's stripes.
 struct StatSums {
-    unsigned long long e[4], f[4], dir[4], newton, iters, liquid;
+    unsigned long long e[4], f[4], dir[4], newton, iters, liquid, shifted;
 };
+
+// The shift s of a state (FP32 D2Q9 / D2Q5; 0 for the other forms): its tail.
+__device__ __forceinline__ float state_shift(const Problem& pb, int parity)
+{
+    return __ldg(reinterpret_cast<const float*>(static_cast<const char*>(pb.state[parity]) + pb.tail_off));
+}
 
 // Read one stripe into `s` and clear it.
 __device__ __forceinline__ void stripe_take(StepStripe* stripe, StatSums& s)
@@ -436,6 +442,7 @@ __device__ __forceinline__ void stripe_take(StepStripe* stripe, StatSums& s)
     s.newton += c->newton;
     s.iters += c->iters;
     s.liquid += c->liquid;
+    s.shifted += c->shifted;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         c->energy.limb[j] = 0ull;
@@ -445,6 +452,7 @@ __device__ __forceinline__ void stripe_take(StepStripe* stripe, StatSums& s)
     c->newton = 0ull;
     c->iters = 0ull;
     c->liquid = 0ull;
+    c->shifted = 0ull;
 }
 
 // The published step statistics from the stripe totals.
@@ -465,6 +473,7 @@ __device__ __forceinline__ void publish_totals(DevStats* st, const Problem* pb, 
         for (int w = 0; w < 4; ++w)
             if (s.dir[w]) c += (double)s.dir[w] * pb->wall_phi[w];
         e += c * pb->inv_ste;
+        if (s.shifted) e += (double)s.shifted * (double)state_shift(*pb, 0);
     }
     if (v->have_energy) {
         double imb = e - v->energy - f;
@@ -500,9 +509,9 @@ __device__ __forceinline__ void publish_stats_warp(DevStats* st, const Problem* 
     static_assert(kStripes == 32, "one stripe per lane");
     StatSums s = {};
     stripe_take(&st->cur[lane], s);
-    unsigned long long* v = &s.e[0];   // the 15 fields in order
+    unsigned long long* v = &s.e[0];   // the 16 fields in order
 #pragma unroll
-    for (int k = 0; k < 15; ++k)
+    for (int k = 0; k < 16; ++k)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(kFull, v[k], o);
     if (lane == 0) publish_totals(st, pb, s);

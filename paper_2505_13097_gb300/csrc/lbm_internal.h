@@ -37,6 +37,7 @@ struct alignas(128) StepStripe {
     unsigned long long iters;      // sum of their iteration counts
     unsigned long long liquid;     // saturated liquid nodes (each adds 1/Ste to the energy)
     unsigned long long dir[4];     // Dirichlet nodes per wall (each adds phi(theta_wall)/Ste)
+    unsigned long long shifted;    // nodes whose energy term was added less the state's shift s
 };
 constexpr int kStripes = 32;
 
@@ -64,6 +65,9 @@ struct DevStats {
 // starts at (y + 1) * pitch.  pitch is a multiple of the warp segment width.
 struct Problem {
     void* state[2];          // ping-pong population buffers
+    long long tail_off;      // byte offset of each buffer's tail (after the planes); the tail of an
+                             // FP32 D2Q9 / D2Q5 state holds the shift s (a float, the same in both
+                             // buffers): the planes hold Omega_i - w_i s, so M0 = sum of the stored + s
     int nx, ny, pitch;
     int q;                   // 3 (D1Q3), 5 (D2Q5) or 9 (D2Q9)
     long long plane;         // elements per plane

@@ -212,7 +212,13 @@ static void fill_problem(Problem& pb, int q, int nx, int ny, int pitch, double t
     pb.nseg = pitch / segw;
     pb.nstrip = (ny + tile_h - 1) / tile_h;
     pb.ntiles = pb.nseg * pb.nstrip;
+    // the planes (D1Q3: a fourth, the ILFBM liquid fraction), then the tail
+    pb.tail_off = (long long)(q == 3 ? 4 : q) * pb.plane * (precision == LBM_FP32 ? 4 : 8);
 }
+
+// Bytes after the planes of a state buffer: the shift of an FP32 D2Q9 / D2Q5
+// state (a float; zero otherwise), in a block of its own.
+constexpr size_t kStateTail = 256;
 
 static lbm_status upload_problem(lbm_stefan* h)
 {
@@ -414,7 +420,7 @@ extern "C" lbm_status lbm_stefan_create(const lbm_stefan_params* p, void* cuda_s
     fill_problem(h->hp, q, p->nx, p->ny, pitch, p->tau, p->delta, p->ste, p->newton_tol, p->newton_max_iter,
                  p->bb_mode, 16, segw, p->precision);
     // D1Q3: a fourth plane holds the liquid fraction of ILFBM (Algorithm 1), zero otherwise
-    h->state_bytes = (size_t)(q == 3 ? 4 : q) * h->hp.plane * h->elem;
+    h->state_bytes = (size_t)h->hp.tail_off + kStateTail;
     cudaError_t e = cudaSuccess;
     void* bufs[2] = {nullptr, nullptr};
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
@@ -506,7 +512,7 @@ extern "C" lbm_status lbm_stefan_set_method(lbm_stefan* h, int method)
             return fail(LBM_ERR_ARG, "ILFBM on D1Q3 holds the lattice in one block: at most 2,844 nodes");
         if (h->p.lattice != LBM_D1Q3) {
             // the liquid fraction needs a plane of its own after the q populations
-            const size_t need = (size_t)(h->hp.q + 1) * h->hp.plane * h->elem;
+            const size_t need = (size_t)(h->hp.q + 1) * h->hp.plane * h->elem + kStateTail;
             if (h->state_bytes < need) {
                 void* nb[2] = {nullptr, nullptr};
                 cudaError_t e = cudaSuccess;
@@ -525,6 +531,7 @@ extern "C" lbm_status lbm_stefan_set_method(lbm_stefan* h, int method)
                 h->hp.state[0] = nb[0];
                 h->hp.state[1] = nb[1];
                 h->state_bytes = need;
+                h->hp.tail_off = (long long)(need - kStateTail);
             }
             if (!h->dilf) CUDA_TRY(cudaMalloc(&h->dilf, 8 * sizeof(unsigned int)));
             if (!h->dilf_scratch)
@@ -806,6 +813,10 @@ extern "C" lbm_status lbm_stefan_set_state(lbm_stefan* h, const void* buf, int o
     if (!h || !buf) return fail(LBM_ERR_ARG, "NULL argument");
     CUDA_TRY(cudaMemcpyAsync(h->hp.state[0], buf, h->state_bytes,
                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+    // both buffers carry the state's shift
+    CUDA_TRY(cudaMemcpyAsync(static_cast<char*>(h->hp.state[1]) + h->hp.tail_off,
+                             static_cast<const char*>(h->hp.state[0]) + h->hp.tail_off, kStateTail,
+                             cudaMemcpyDeviceToDevice, h->stream));
     // the energy of a loaded state is not known until the next step publishes one
     CUDA_TRY(cudaMemsetAsync(&h->dstats->have_energy, 0, sizeof(int), h->stream));
     if (!on_device) CUDA_TRY(cudaStreamSynchronize(h->stream));
@@ -939,6 +950,9 @@ extern "C" lbm_status lbm_stefan_adjoint_segment(lbm_stefan* h, const void* chec
     if (adj == adj_other) return fail(LBM_ERR_ARG, "adj and adj_other must differ");
     // reload the checkpoint into state[0]
     CUDA_TRY(cudaMemcpyAsync(h->hp.state[0], checkpoint, h->state_bytes, cudaMemcpyDeviceToDevice, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(static_cast<char*>(h->hp.state[1]) + h->hp.tail_off,
+                             static_cast<const char*>(h->hp.state[0]) + h->hp.tail_off, kStateTail,
+                             cudaMemcpyDeviceToDevice, h->stream));
     CUDA_TRY(cudaMemsetAsync(&h->dstats->have_energy, 0, sizeof(int), h->stream));
     h->parity = 0;
     h->ic = true;
@@ -1168,7 +1182,7 @@ extern "C" lbm_status lbm_stefan_batch_create(int count, const lbm_stefan_proble
             pb.wall_theta[w] = p.wall_theta[w];
         }
         pb.stats = k;
-        b->state_bytes[k] = (size_t)9 * pb.plane * b->elem;
+        b->state_bytes[k] = (size_t)pb.tail_off + kStateTail;
         total += 2 * ((b->state_bytes[k] + 255) / 256 * 256);
         maxn = std::max(maxn, (size_t)p.nx * p.ny);
         total_nodes += (size_t)p.nx * p.ny;
@@ -1515,6 +1529,9 @@ extern "C" lbm_status lbm_stefan_step_d2q9_noalloc(const lbm_stefan_params* p, c
     // the array keeps the previous call's contents: statistics, ticket and job
     // count must start at zero
     CUDA_TRY(cudaMemcpyAsync(&sc->prob, &hp, sizeof(Problem), cudaMemcpyHostToDevice, st));
+    // the output state carries the input's shift (its tail)
+    CUDA_TRY(cudaMemcpyAsync(static_cast<char*>(state_out) + hp.tail_off,
+                             static_cast<const char*>(state_in) + hp.tail_off, kStateTail, cudaMemcpyDeviceToDevice, st));
     CUDA_TRY(cudaMemsetAsync(&sc->stats, 0, kNoAllocClear, st));
     CUDA_TRY(lbm::launch_wall_constants(&sc->prob, 1, st));
 

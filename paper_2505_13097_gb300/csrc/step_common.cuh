@@ -62,6 +62,7 @@ struct TileSums {
     ff flux_f{0.f, 0.f};                // FP32 form
     int dir_count[4] = {0, 0, 0, 0};   // Dirichlet nodes per wall (adds phi(theta_D)/Ste each)
     int liquid = 0, newton = 0, maxit = 0;
+    int shifted = 0;                    // energy terms added less the state's shift
 };
 
 // A warp's partial sums, totalled in a fixed lane order (every lane gets the
@@ -70,6 +71,7 @@ struct WarpSums {
     Fx e{0, 0ull}, f{0, 0ull};
     int nl = 0;        // saturated liquid nodes
     int nd[4] = {0, 0, 0, 0};   // Dirichlet nodes per wall
+    int ns = 0;        // energy terms added less the state's shift
 };
 
 template <typename P>
@@ -96,6 +98,7 @@ __device__ __forceinline__ WarpSums warp_tile_sums(const Acc<P>& acc, const Tile
         w.f = to_fixed(warp_sum(ts.flux));
     }
     w.nl = warp_sum_i(ts.liquid);
+    w.ns = warp_sum_i(ts.shifted);
 #pragma unroll
     for (int k = 0; k < 4; ++k) w.nd[k] = warp_sum_i(ts.dir_count[k]);
     return w;
@@ -106,6 +109,7 @@ __device__ __forceinline__ void add_sums(WarpSums& a, const WarpSums& b)
     fx_add(a.e, b.e);
     fx_add(a.f, b.f);
     a.nl += b.nl;
+    a.ns += b.ns;
 #pragma unroll
     for (int k = 0; k < 4; ++k) a.nd[k] += b.nd[k];
 }
@@ -118,6 +122,7 @@ __device__ __forceinline__ void emit_sums(const WarpSums& w, DevStats* st)
     acc_add_fx(&c->energy, w.e);
     acc_add_fx(&c->flux, w.f);
     if (w.nl) atomicAdd(&c->liquid, (unsigned long long)w.nl);
+    if (w.ns) atomicAdd(&c->shifted, (unsigned long long)w.ns);
 #pragma unroll
     for (int k = 0; k < 4; ++k)
         if (w.nd[k]) atomicAdd(&c->dir[k], (unsigned long long)w.nd[k]);
@@ -200,12 +205,12 @@ __device__ __forceinline__ NewtonResult newton_job_apply(const NewtonJob& jb, co
     P qv[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) qv[i] = __ldcg(d + i * pb.plane);
-    double m0, th;
+    double m0, th, sh = 0.0;
     if constexpr (sizeof(P) == 4) {
         // FP32 form: the job carries only the node; m0 = M0(q) from the stored
         // unrelaxed q_i and theta = M0(f) = sum of the node's Omega_i(t) (the
         // step's source state), both as float-float sums in the order the
-        // step kernel uses (last plane first)
+        // step kernel uses (last plane first), plus the state's shift s
         const P* sv = static_cast<const P*>(pb.state[parity]) + at;
         ff mm{0.f, 0.f}, t{0.f, 0.f};
 #pragma unroll
@@ -213,8 +218,9 @@ __device__ __forceinline__ NewtonResult newton_job_apply(const NewtonJob& jb, co
             ff_add(t, __ldg(sv + i * pb.plane));
             ff_add(mm, qv[i]);
         }
-        m0 = ff_to_double(mm);
-        th = ff_to_double(t);
+        sh = (double)state_shift(pb, parity);
+        m0 = ff_to_double(mm) + sh;
+        th = ff_to_double(t) + sh;
     } else {
         m0 = jb.m0;
         th = jb.theta;
@@ -223,7 +229,8 @@ __device__ __forceinline__ NewtonResult newton_job_apply(const NewtonJob& jb, co
     const NewtonOut nr = newton_mixed(m0, th, pth, pb);
     if (!nr.ok || !isfinite(nr.root)) atomicCAS(&stats[r.sidx].error, 0, 3);
     const double tn = m0 + (pth - nr.phi_root) * pb.inv_ste;
-    const P c = (P)(tn - (1.0 - pb.omega) * m0);
+    // c = theta' - (1-omega) m0; stored values less w_i s: c - omega s
+    const P c = (P)((tn - sh) - (1.0 - pb.omega) * (m0 - sh));
     const P omc = (P)(1.0 - pb.omega);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {

@@ -159,12 +159,15 @@ __device__ __noinline__ ff wall5_closure_f(float* q, const float* u, int x, int 
     for (int j = 1; j < 5; ++j)
         if ((wi.unk >> d2_opp(j)) & 1) ff_add(out, u[j]);
     if (wi.wall >= 0 || pb.bb_mode == 2) {
-        ff m0t{0.f, 0.f};
+        ff m0t{0.f, 0.f};   // target of M0(q), less the state's shift sh (q, u are Omega - w_i sh)
         if (wi.wall >= 0) {
+            const float sh = __ldg(reinterpret_cast<const float*>(reinterpret_cast<const char*>(src) + pb.tail_off));
             ff th{0.f, 0.f};
 #pragma unroll
             for (int i = 4; i >= 0; --i) ff_add(th, u[i]);
+            ff_add(th, sh);
             m0t = dir_m0_target_f(th, wi.wall, pb);
+            ff_add(m0t, -sh);
         } else {
             float nq[5];
             pulled5<float>(src, pb, wi.sx, wi.sy, nq);
@@ -213,6 +216,9 @@ __device__ __forceinline__ void row5_update(const Problem& pb, const P* __restri
 {
     const int nx = pb.nx, ny = pb.ny;
     const long long pl = pb.plane;
+    // the state's shift (FP32 form: the stored values are Omega_i - w_i sh; 0 in FP64)
+    const float sh = sizeof(P) == 4 ? __ldg(reinterpret_cast<const float*>(reinterpret_cast<const char*>(src) + pb.tail_off))
+                                    : 0.f;
     P c[N];
     double thn[REC ? N : 1];
     bool newton_k[N], dir_k[N];
@@ -261,15 +267,17 @@ __device__ __forceinline__ void row5_update(const Problem& pb, const P* __restri
             // rounding of the stored populations; float-float sums only where needed
 #pragma unroll
             for (int i = 4; i >= 0; --i) { tf += u[i][k]; mf += qf[i][k]; }
+            tf += sh;   // theta; mf stays M0(q) - sh
         } else {
             m0_init(m0[k]);
 #pragma unroll
             for (int i = 4; i >= 0; --i) { tf += approx_float(u[i][k]); m0_add(m0[k], qf[i][k]); }
             mf = m0_f(m0[k]);
         }
+        const float mt = mf + sh;   // M0(q)
         const float marg = 1e-5f * (1.0f + fabsf(tf));
-        const bool sat_liq = tf >= thr_f + marg && mf >= thr_f + marg;
-        const bool sat_sol = tf <= -thr_f - marg && mf <= -thr_f - marg;
+        const bool sat_liq = tf >= thr_f + marg && mt >= thr_f + marg;
+        const bool sat_sol = tf <= -thr_f - marg && mt <= -thr_f - marg;
         newton_k[k] = valid && !dir_k[k] && !(sat_liq || sat_sol);
         any_newton |= newton_k[k];
         if (!valid) {
@@ -286,7 +294,7 @@ __device__ __forceinline__ void row5_update(const Problem& pb, const P* __restri
 #pragma unroll
                 for (int i = 4; i >= 0; --i) ff_add(mm, qf[i][k]);
                 const float oc = (float)omc;
-                c[k] = (P)((pb.wall_th_hi[wk] - oc * mm.hi) + (pb.wall_th_lo[wk] - oc * mm.lo));
+                c[k] = (P)(((pb.wall_th_hi[wk] - sh) - oc * mm.hi) + (pb.wall_th_lo[wk] - oc * mm.lo));
                 acc.add_ff(ff{pb.wall_th_hi[wk], pb.wall_th_lo[wk]});
             } else {
                 c[k] = (P)(pb.wall_theta[wk] - omc_d * m0_d(m0[k]));
@@ -296,9 +304,10 @@ __device__ __forceinline__ void row5_update(const Problem& pb, const P* __restri
         } else if (!newton_k[k]) {
             // saturated: theta' = m0, no source; c = omega m0
             if constexpr (sizeof(P) == 4) {
-                c[k] = (P)(om_f * mf);
-                acc.add_f(mf);
-                if constexpr (REC) thn[k] = (double)mf;
+                c[k] = (P)(om_f * mf);   // less omega sh
+                acc.add_f(mf);           // less sh
+                ts.shifted += 1;
+                if constexpr (REC) thn[k] = (double)mf + (double)sh;
             } else {
                 const double md = m0_d(m0[k]);
                 c[k] = (P)(pb.omega * md);
@@ -396,25 +405,31 @@ __device__ __forceinline__ void row5_update_eebm(const Problem& pb, const P* __r
     }
     const P om = (P)1 - omc;
     const P inv_ste = (P)pb.inv_ste;
+    // the state's shift in enthalpy units (FP32 form; 0 in FP64)
+    const P sh = sizeof(P) == 4 ? (P)__ldg(reinterpret_cast<const float*>(reinterpret_cast<const char*>(src) + pb.tail_off))
+                                : (P)0;
     P hs = 0;
     double thn[REC ? N : 1];
 #pragma unroll
     for (int k = 0; k < N; ++k) {
         const bool valid = !EDGE || x0 + k < nx;
-        P H = 0;
+        P Hs = 0;   // H less the shift
 #pragma unroll
-        for (int i = 4; i >= 0; --i) H += qf[i][k];
+        for (int i = 4; i >= 0; --i) Hs += qf[i][k];
         if (!valid) {
-            H = 0;
+            Hs = 0;
 #pragma unroll
             for (int i = 0; i < 5; ++i) qf[i][k] = (P)0;
         }
+        hs += Hs;
+        if constexpr (sizeof(P) == 4) ts.shifted += valid ? 1 : 0;
+        const P H = Hs + sh;
         const P th = eebm_theta(H, inv_ste);
-        hs += H;
         if constexpr (REC) thn[k] = (double)th;
-        qf[0][k] = fma(omc, qf[0][k], om * (H - ((P)1 - w0) * th));
+        // stored values less w_i sh
+        qf[0][k] = fma(omc, qf[0][k], om * (H - ((P)1 - w0) * th - w0 * sh));
 #pragma unroll
-        for (int i = 1; i < 5; ++i) qf[i][k] = fma(omc, qf[i][k], om * w1 * th);
+        for (int i = 1; i < 5; ++i) qf[i][k] = fma(omc, qf[i][k], om * w1 * (th - sh));
     }
     if constexpr (sizeof(P) == 4) acc.add_ff(ff{hs, 0.f});
     else acc.add_d(hs);

@@ -81,6 +81,9 @@ __device__ __forceinline__ void d2q9_tile_direct(const Problem& pb, const P* __r
     const int nx = pb.nx, ny = pb.ny;
     const P wP[3] = {lat_wp<P>(9, 0), lat_wp<P>(9, 1), lat_wp<P>(9, 5)};
     const float thr_f = (float)pb.sat;
+    // the state's shift (FP32 form; 0 in FP64)
+    const float sh = sizeof(P) == 4 ? __ldg(reinterpret_cast<const float*>(reinterpret_cast<const char*>(src) + pb.tail_off))
+                                    : 0.f;
 
     auto rp = [&](int i, int r) -> const P* { return src + i * pl + (long long)(r + 1) * pitch + x0; };
     auto hl = [&](int i, int r) -> P {
@@ -154,15 +157,15 @@ __device__ __forceinline__ void d2q9_tile_direct(const Problem& pb, const P* __r
         if (pb.method == 1)
             row_update_eebm<P, N, REC, true>(pb, y, x0, qf, cur.r0, cur.r1, cur.c2, cur.r3, cu4, cur.c5, cur.c6, cu7,
                                              cu8, GlobalRowOut<P, N>{dst + (long long)(y + 1) * pitch + x0, pl}, rec,
-                                             acc, ts, omc, wP, nx, ny);
+                                             acc, ts, omc, wP, nx, ny, sh);
         else if (seg_interior && y > 0 && y < ny - 1)
             row_update<P, N, REC, false>(pb, y, x0, lane, qf, cur.r0, cur.r1, cur.c2, cur.r3, cu4, cur.c5, cur.c6, cu7,
                                          cu8, GlobalRowOut<P, N>{dst + (long long)(y + 1) * pitch + x0, pl}, rec, acc,
-                                         ts, pi, sink, omc, om_f, omc_d, wP, thr_f, nx, ny);
+                                         ts, pi, sink, omc, om_f, omc_d, wP, thr_f, nx, ny, sh);
         else
             row_update<P, N, REC, true>(pb, y, x0, lane, qf, cur.r0, cur.r1, cur.c2, cur.r3, cu4, cur.c5, cur.c6, cu7,
                                         cu8, GlobalRowOut<P, N>{dst + (long long)(y + 1) * pitch + x0, pl}, rec, acc,
-                                        ts, pi, sink, omc, om_f, omc_d, wP, thr_f, nx, ny);
+                                        ts, pi, sink, omc, om_f, omc_d, wP, thr_f, nx, ny, sh);
         // roll the register window
 #pragma unroll
         for (int k = 0; k < N; ++k) { up2[k] = cur.c2[k]; cu4[k] = cur.n4[k]; cu7[k] = cur.n7[k]; cu8[k] = cur.n8[k]; }
@@ -283,6 +286,7 @@ __global__ void __launch_bounds__(256, LBM_FLAT_MINB) d2q9_flat_kernel(const Ste
     const float om_f = (float)pb.omega;
     const float wP[3] = {d2_wf(0), d2_wf(1), d2_wf(5)};
     const float thr_f = (float)pb.sat;
+    const float sh = state_shift(pb, a.parity);   // stored values are Omega_i - w_i sh
     Acc<float> acc;
     TileSums ts;
     GlobalJobSink sink{a.jobs, a.job_count};
@@ -297,7 +301,7 @@ __global__ void __launch_bounds__(256, LBM_FLAT_MINB) d2q9_flat_kernel(const Ste
             float u[9][4], qf[9][4];
             flat_load_row(row, pitch, pl, u, qf);
             row_update_eebm<float, 4, REC, false>(pb, y, x0, qf, u[0], u[1], u[2], u[3], u[4], u[5], u[6], u[7], u[8],
-                                                  GlobalRowOut<float, 4>{orow, pl}, a.rec, acc, ts, omc, wP, nx, ny);
+                                                  GlobalRowOut<float, 4>{orow, pl}, a.rec, acc, ts, omc, wP, nx, ny, sh);
             continue;
         }
         // interior IREBM row: the arithmetic of row_update's interior branch
@@ -310,19 +314,21 @@ __global__ void __launch_bounds__(256, LBM_FLAT_MINB) d2q9_flat_kernel(const Ste
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const float uk[9] = {u[0][k], u[1][k], u[2][k], u[3][k], u[4][k], u[5][k], u[6][k], u[7][k], u[8][k]};
-            const float tf = approx_sum<float>(uk);
-            float mf = 0.f;
+            const float tf = approx_sum<float>(uk) + sh;   // theta
+            float mf = 0.f;                                  // M0(q) - sh
 #pragma unroll
             for (int i = 8; i >= 0; --i) mf += qf[i][k];
+            const float mt = mf + sh;
             const float marg = 1e-5f * (1.0f + fabsf(tf));
-            const bool sat_liq = tf >= thr_f + marg && mf >= thr_f + marg;
-            const bool sat_sol = tf <= -thr_f - marg && mf <= -thr_f - marg;
+            const bool sat_liq = tf >= thr_f + marg && mt >= thr_f + marg;
+            const bool sat_sol = tf <= -thr_f - marg && mt <= -thr_f - marg;
             newton[k] = !(sat_liq || sat_sol);
             any_newton |= newton[k];
-            c[k] = newton[k] ? 0.f : om_f * mf;
+            c[k] = newton[k] ? 0.f : om_f * mf;   // c - omega sh = omega (m0 - sh)
             if (!newton[k]) {
                 acc.add_f(mf);
                 ts.liquid += sat_liq ? 1 : 0;
+                ts.shifted += 1;
             }
         }
         float wc[3][4];
@@ -380,7 +386,7 @@ __global__ void __launch_bounds__(256, LBM_FLAT_MINB) d2q9_flat_kernel(const Ste
                 float mf = 0.f;
 #pragma unroll
                 for (int i = 8; i >= 0; --i) mf += qf[i][k];
-                thn[k] = newton[k] ? 0.0 : (double)mf;
+                thn[k] = newton[k] ? 0.0 : (double)mf + (double)sh;
             }
             st_rec<4>(a.rec + (long long)y * pitch + x0, thn);
         }
@@ -420,6 +426,7 @@ __global__ void __launch_bounds__(256) d2q9_edge_kernel(const StepArgs a)
     const double omc_d = 1.0 - pb.omega;
     const float wP[3] = {d2_wf(0), d2_wf(1), d2_wf(5)};
     const float thr_f = (float)pb.sat;
+    const float sh = state_shift(pb, a.parity);   // stored values are Omega_i - w_i sh
     Acc<float> acc;
     TileSums ts;
     GlobalJobSink sink{a.jobs, a.job_count};
@@ -439,10 +446,10 @@ __global__ void __launch_bounds__(256) d2q9_edge_kernel(const StepArgs a)
         const GlobalRowOut<float, 4> out{dst + (y + 1) * pitch + x0, pl};
         if (pb.method == 1)
             row_update_eebm<float, 4, REC, true>(pb, y, x0, qf, u[0], u[1], u[2], u[3], u[4], u[5], u[6], u[7], u[8],
-                                                 out, a.rec, acc, ts, omc, wP, nx, ny);
+                                                 out, a.rec, acc, ts, omc, wP, nx, ny, sh);
         else
             row_update<float, 4, REC, true>(pb, y, x0, lane, qf, u[0], u[1], u[2], u[3], u[4], u[5], u[6], u[7], u[8],
-                                            out, a.rec, acc, ts, 0, sink, omc, om_f, omc_d, wP, thr_f, nx, ny);
+                                            out, a.rec, acc, ts, 0, sink, omc, om_f, omc_d, wP, thr_f, nx, ny, sh);
     }
     const WarpSums w = warp_tile_sums<float>(acc, ts);
     if (lane == 0) wsum[warp] = w;
@@ -561,6 +568,7 @@ __global__ void __launch_bounds__(kTmaThreads, LBM_TMA_MIN_BLOCKS) d2q9_tma_kern
     const double omc_d = 1.0 - pb.omega;
     const float wP[3] = {d2_wf(0), d2_wf(1), d2_wf(5)};
     const float thr_f = (float)pb.sat;
+    const float sh = state_shift(pb, a.parity);   // stored values are Omega_i - w_i sh
     const int wx0 = segx + warp * 32;   // first column of this warp
     const bool warp_interior_x = wx0 > 0 && wx0 + 31 < nx - 1;
     float* dst = static_cast<float*>(pb.state[a.parity ^ 1]);
@@ -601,13 +609,13 @@ __global__ void __launch_bounds__(kTmaThreads, LBM_TMA_MIN_BLOCKS) d2q9_tma_kern
         const GlobalRowOut<float, 1> out{dst + (long long)(y + 1) * pitch + x, pl};
         if (pb.method == 1)
             row_update_eebm<float, 1, REC, true>(pb, y, x, qf, u0, u1, u2, u3, u4, u5, u6, u7, u8, out, a.rec, acc, ts,
-                                                 omc, wP, nx, ny);
+                                                 omc, wP, nx, ny, sh);
         else if (warp_interior_x && y > 0 && y < ny - 1)
             row_update<float, 1, REC, false>(pb, y, x, lane, qf, u0, u1, u2, u3, u4, u5, u6, u7, u8, out, a.rec, acc,
-                                             ts, pi, sink, omc, om_f, omc_d, wP, thr_f, nx, ny);
+                                             ts, pi, sink, omc, om_f, omc_d, wP, thr_f, nx, ny, sh);
         else
             row_update<float, 1, REC, true>(pb, y, x, lane, qf, u0, u1, u2, u3, u4, u5, u6, u7, u8, out, a.rec, acc,
-                                            ts, pi, sink, omc, om_f, omc_d, wP, thr_f, nx, ny);
+                                            ts, pi, sink, omc, om_f, omc_d, wP, thr_f, nx, ny, sh);
     }
     if (!ok && lane == 0) atomicExch(&st->error, 4);   // LBM_ERR_TIMEOUT
     flush_tile_sums<float>(acc, ts, st, lane);
@@ -622,8 +630,14 @@ __global__ void __launch_bounds__(kTmaThreads, LBM_TMA_MIN_BLOCKS) d2q9_tma_kern
 // Energy contributions theta' + phi(theta')/Ste are summed per problem as
 // exact 128-bit fixed-point integers (independent of the job order).  The last
 // warp to finish publishes the step statistics and clears the job list.
+// Threads per block of the job kernel.  Its last block is found with one
+// atomic ticket per block, and same-address atomics serialize in L2: with 1,216
+// blocks an empty job list still took 16 us, so the grid is kept small (two
+// blocks of 256 threads per SM; each warp takes jobs grid-stride).
+constexpr int kJobThreads = 256;
+
 template <typename P, bool REC, int Q>
-__global__ void __launch_bounds__(128) newton_jobs_kernel(JobArgs a)
+__global__ void __launch_bounds__(kJobThreads) newton_jobs_kernel(JobArgs a)
 {
     const unsigned count = *reinterpret_cast<volatile unsigned*>(a.job_count);
     const int lane = threadIdx.x & 31;
@@ -778,7 +792,7 @@ static cudaError_t launch_jobs_q(int precision, const JobArgs& a, int grid, cuda
     void (*k)(JobArgs) = precision == 1
                              ? (a.rec ? newton_jobs_kernel<float, true, Q> : newton_jobs_kernel<float, false, Q>)
                              : (a.rec ? newton_jobs_kernel<double, true, Q> : newton_jobs_kernel<double, false, Q>);
-    return launch_prio(k, grid, 128, s, prio, a);
+    return launch_prio(k, grid, kJobThreads, s, prio, a);
 }
 
 cudaError_t launch_newton_jobs(int precision, int q, const JobArgs& a, cudaStream_t s, int grid, int prio)
@@ -787,7 +801,7 @@ cudaError_t launch_newton_jobs(int precision, int q, const JobArgs& a, cudaStrea
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        grid = sms * 8;   // 8 x 128 threads per SM: about one pass over ~150k nodes
+        grid = sms * 2;
     }
     if (q == 9) return launch_jobs_q<9>(precision, a, grid, s, prio);
     if (q == 5) return launch_jobs_q<5>(precision, a, grid, s, prio);

@@ -51,8 +51,9 @@ def noalloc_call(_abi, c, src, dst, stream, bb_mode=0, maxit=60):
 
 
 def planes(torch, c, buf):
+    """The nine planes of a state buffer (the last 256 bytes are its tail)."""
     dt = torch.float32 if c.precision == workloads.FP32 else torch.float64
-    return buf.view(dt).reshape(9, c.ny + 2, -1)[:, 1:-1, :c.nx]
+    return buf[:buf.numel() - 256].view(dt).reshape(9, c.ny + 2, -1)[:, 1:-1, :c.nx]
 
 
 def regular_states(solver, c, stream, pre, bb_mode=0):
