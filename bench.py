@@ -579,6 +579,15 @@ def run_gpu(args):
         if rank == 0:
             print(json.dumps({"bar_1d": bench_bar_1d(torch, solver, workloads, stream, steps=args.steps)}), flush=True)
         return 0
+    if args.only_corner:
+        # profiling aid: the FP64 corner leg alone, Ste 0.1, side --n (default 2048)
+        if rank == 0:
+            cc = workloads.corner_2d(n=args.n or 2048, ste=0.1)
+            msc, stc = bench_single(torch, solver, cc, args.steps, args.warmup, stream, centre=args.window_step)
+            print(json.dumps({"corner": {"workload": cc.name, "mlups": cc.nx * cc.ny * args.steps / msc / 1e3,
+                                         "kernel_ms": stc["kernel_ms"], "newton_nodes": stc["newton_nodes"]}}),
+                  flush=True)
+        return 0
     if args.only_batch:
         # profiling aid: the batch leg alone (--batch-count problems, sides up to --batch-hi)
         if rank == 0:
@@ -711,6 +720,8 @@ def main():
                     help="time the 1D bar (IREBM, EEBM, ILFBM) alone, --steps steps each; a profiling aid")
     ap.add_argument("--only-d2q5", action="store_true",
                     help="time the D2Q5 cavity leg alone, FP32, side --n (default 4096); a profiling aid")
+    ap.add_argument("--only-corner", action="store_true",
+                    help="time the FP64 corner leg alone (Ste 0.1, side --n, default 2048); a profiling aid")
     ap.add_argument("--only-batch", action="store_true",
                     help="time the batch leg alone (--batch-count problems, sides log-uniform in [64, --batch-hi]); "
                          "a profiling aid")

@@ -20,13 +20,16 @@ __device__ __forceinline__ bool dirichlet_value(const Problem& pb, int x, int y,
     return false;
 }
 
-// The shift s of an FP32 state (its populations are stored less w_i s): the
-// mean over the nodes of the initial M0 (theta0; EEBM: H(theta0)), rounded to
-// a float, written to the tail of both buffers.  With most nodes near s the
-// stored values are small, and so are their rounding errors: on a smooth
-// field, storing Omega_i itself in FP32 lets the rounding of w_i theta drift
-// coherently (2.4e-5 of theta after 10,000 steps of the 4096^2 melting
-// workload).  One block; a fixed summation order (deterministic).
+// The shift s of an FP32 state (its populations are stored less w_i s),
+// written to the tail of both buffers: half the mean over the nodes of the
+// initial M0 (theta0; EEBM: H(theta0)), rounded to a float.  A stored value's
+// rounding error scales with its size, |M0 - s| w_i.  Storing Omega_i itself
+// (s = 0) lets the rounding of a smooth field far from the front drift
+// coherently (on the 4096^2 melting workload, 2.45e-5 of theta after 10,000
+// steps against the FP64 form); s = the mean of M0 removes that but makes the
+// values at the melting point (M0 = 0, where phi' is largest) the large ones
+// (max |d phi| 1.04e-4).  Halfway between the two bounds both.  One block; a
+// fixed summation order (deterministic).
 __global__ void __launch_bounds__(1024) shift_kernel(const Problem* dprob, const double* __restrict__ theta0)
 {
     __shared__ double part[1024];
@@ -44,7 +47,7 @@ __global__ void __launch_bounds__(1024) shift_kernel(const Problem* dprob, const
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        const float sh = n > 0 ? (float)(part[0] / (double)n) : 0.f;
+        const float sh = n > 0 ? (float)(0.5 * part[0] / (double)n) : 0.f;
         for (int b = 0; b < 2; ++b) *reinterpret_cast<float*>(static_cast<char*>(pb.state[b]) + pb.tail_off) = sh;
     }
 }

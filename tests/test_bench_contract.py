@@ -46,7 +46,7 @@ def bench(monkeypatch):
 
 def test_json_line_keys(bench, capsys):
     args = argparse.Namespace(gpus=1, steps=400, warmup=20, impl="gpu", quick=True, no_cpu=True, n=None,
-                              window_step=None, only_bar=False, only_d2q5=False, only_batch=False,
+                              window_step=None, only_bar=False, only_d2q5=False, only_batch=False, only_corner=False,
                               batch_count=256, batch_hi=1024)
     assert bench.run_gpu(args) == 0
     lines = [l for l in capsys.readouterr().out.splitlines() if l.startswith("{")]

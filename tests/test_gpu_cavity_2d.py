@@ -9,14 +9,20 @@ The reference curves of the paper's comparison are not available.  What the
 mathematics fixes instead:
 * the W and S walls are the same, so theta is symmetric about x = y;
 * a y-uniform D2Q9 or D2Q5 state evolves as D1Q3 (the velocities with equal
-  e_x carry the D1Q3 weights 2/3, 1/6, 1/6), so the row on the N symmetry
-  line (y = 4 m, the farthest from the S wall) is the oracle's planar D1Q3
-  run of the same setup, up to the S wall's influence 4 m away and to
-  rounding: within 10 times the planar oracle's own one-ulp divergence (its
-  run from theta0 moved by one ulp at random nodes; the mushy zone amplifies
-  rounding by up to 1/(2 delta Ste) per step) plus 3 erfc(4 m / (2 sqrt(alpha
-  t))), the linear-diffusion bound on a wall 3 degrees (dimensionless) colder
-  at that distance (the latent heat only slows the cold front);
+  e_x carry the D1Q3 weights 2/3, 1/6, 1/6), so a row far from the S wall is
+  the oracle's planar D1Q3 run of the same setup, up to the influence of the
+  nearest boundary that is not planar and to rounding: within 10 times the
+  planar oracle's own one-ulp divergence (its run from theta0 moved by one
+  ulp at random nodes; the mushy zone amplifies rounding by up to
+  1/(2 delta Ste) per step) plus 3 erfc(d / (2 sqrt(alpha t))), the
+  linear-diffusion bound of a disturbance of at most 3 (dimensionless)
+  degrees at distance d (the latent heat only slows it).  On D2Q5 the N line
+  is planar-exact (Eq. 17 with a y-uniform field), so the row on it (y = 4 m,
+  d = 4 m from the S wall) is compared; on D2Q9 the bounce-back on the N
+  line sends a diagonal population back from x - 1 instead of mirroring it,
+  which is not planar where theta varies along x (measured: 7.7e-3 at the
+  front on the N line after 5 h), so the row at y = 2 m is compared (d = 2 m
+  from both);
 * that planar run follows the Neumann solution (Sec. 2) of the equivalent
   melting problem (theta_hat = -theta/2: wall 1, liquid -1/2, Ste 2 x
   0.0521, delta / 2) to O(delta + dx): within one lattice spacing;
@@ -98,7 +104,8 @@ def test_quarter_cavity_to_40h(gpu, planar, lattice):
     S = gpu.Stefan.from_case(c)
     S.set_ic(c.theta0())
     lam = neumann.stefan_lambda(2.0 * c.ste, -0.5)
-    yrow = N - 1                            # y = 4 m, the N symmetry line
+    # D2Q5: the N symmetry line (y = 4 m); D2Q9: y = 2 m (see above)
+    yrow, dist = (N - 1, 4.0) if lattice == 3 else ((N - 1) // 2, 2.0)
     done = 0
     for h, s, (ref, floor) in zip(HOURS, steps, planar):
         S.step(s - done)
@@ -110,13 +117,13 @@ def test_quarter_cavity_to_40h(gpu, planar, lattice):
         drow = np.max(np.abs(th[yrow] - ref)) / np.max(np.abs(ref))
         t = ALPHA * h * 3600.0
         xn = 2.0 * lam * np.sqrt(t)
-        tol_row = max(1e-12, 10.0 * floor) + 3.0 * math.erfc(4.0 / (2.0 * np.sqrt(t)))
+        tol_row = max(1e-12, 10.0 * floor) + 3.0 * math.erfc(dist / (2.0 * np.sqrt(t)))
         x_row = first_zero(th[yrow]) * dx
         diag = np.diagonal(th)
         x_diag = first_zero(diag) * dx * np.sqrt(2.0)   # distance from the corner along x = y
-        print("lattice %d, %2d h (%d steps): front along y = 4 m %.5f m (Neumann %.5f m, %.2f spacings), "
+        print("lattice %d, %2d h (%d steps): front along y = %g m %.5f m (Neumann %.5f m, %.2f spacings), "
               "along x = y %.5f m from the corner; asymmetry %.1e, row vs planar oracle %.1e (bound %.1e), "
-              "energy imbalance max %.1e" % (lattice, h, s, x_row, xn, (x_row - xn) / dx, x_diag, asym, drow,
+              "energy imbalance max %.1e" % (lattice, h, s, yrow * dx, x_row, xn, (x_row - xn) / dx, x_diag, asym, drow,
                                              tol_row, st["imbalance_max"]))
         assert asym < 1e-10
         assert drow < tol_row

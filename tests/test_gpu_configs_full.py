@@ -112,7 +112,15 @@ def test_config2_melt_2d_front_to_the_end(melt_full, orc):
     assert abs(r["front"] - xo) < 0.02
     assert spread < 0.05
     assert np.max(np.abs(r["theta"][:, 0] - 1.0)) < 1e-6
-    assert abs(st["imbalance"]) < 1e-9 * abs(st["energy"]) + 1e-6
+    # energy balance: FP64 form to 1e-9 of E; FP32 form to the rounding of its
+    # stored populations in one step (each of the 9 per node rounded once by the
+    # relaxation and once by its product w_i c: 18 half-ulps of the largest)
+    st64 = melt_full[workloads.FP64]["stats"]
+    assert abs(st64["imbalance"]) < 1e-9 * abs(st64["energy"])
+    bound32 = c.nx * c.ny * 18 * 0.5 * 2.0 ** -24 * np.max(np.abs(r["theta"]))
+    print("config 2 energy balance: FP32 form %.2e (bound %.2e), FP64 form %.2e of E = %.4e"
+          % (st["imbalance"], bound32, st64["imbalance"], st64["energy"]))
+    assert abs(st["imbalance"]) < bound32
 
 
 def test_config2_fp32_form_against_fp64_form_full_size(melt_full):
