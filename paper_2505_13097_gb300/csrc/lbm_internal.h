@@ -152,7 +152,12 @@ struct JobArgs {
     unsigned int* ticket;
     const NewtonJob* jobs;
     unsigned int* job_count;
-    int publish;             // 1: the last block publishes the step statistics; 0: it only clears the list
+    int publish;             // 1: the step's statistics are published after this launch; 0: never by it
+    // parts > 1: the step has `parts` job launches (concurrent, on two streams);
+    // the last block of each adds one to *done, and the one that completes the
+    // count publishes (and clears *done)
+    int parts;
+    unsigned int* done;
 };
 
 // Constants of the interior-node adjoint terms, converted once on the host.
@@ -188,12 +193,14 @@ int d2q9_blocks_per_sm(int precision);   // resident step blocks per SM (persist
 cudaError_t launch_d2q9_tma(const StepArgs& a, const TmaMaps& m, cudaStream_t s);
 // single problem, FP32: the interior rows and the rows that touch a wall (two
 // launches; with side, fork and join the second runs on `side`, joined back to s)
-// With a side stream, the wall rows' kernel and then a job kernel over their own
-// job list (ae.jobs / ae.job_count, described by je, not publishing) run on
-// `side`, concurrently with the interior rows (ai) on s; s then waits for side.
-// Without one, both kernels run on s and append to the same list (ai's).
-cudaError_t launch_d2q9_flat(const StepArgs& ai, const StepArgs& ae, const JobArgs& je, int nsegs, int ny,
-                             int method, cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join);
+// The whole step.  With a side stream, the wall rows' kernel and then a job
+// kernel over their own job list (ae.jobs / ae.job_count, described by je) run
+// on `side`, concurrently with the interior rows (ai) and the job kernel over
+// theirs (ji) on s, each job launch with parts = 2; s then waits for side.
+// Without one, everything runs on s and both row kernels append to ai's list
+// (ji, parts = 1; je unused).
+cudaError_t launch_d2q9_flat(const StepArgs& ai, const StepArgs& ae, const JobArgs& ji, const JobArgs& je, int nsegs,
+                             int ny, int method, cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join);
 int d2q9_tma_blocks_per_sm();
 // q = 9 or 5; grid 0: 8 blocks of 128 threads per SM; prio != 0: that scheduling priority
 cudaError_t launch_newton_jobs(int precision, int q, const JobArgs& a, cudaStream_t s, int grid = 0, int prio = 0);

@@ -257,6 +257,8 @@ static lbm::JobArgs job_args(const Problem* probs, int nprob, int parity, double
     j.jobs = jobs;
     j.job_count = count;
     j.publish = 1;
+    j.parts = 1;
+    j.done = nullptr;
     return j;
 }
 
@@ -268,12 +270,15 @@ static cudaError_t launch_flat(lbm_stefan* h, const StepArgs& a)
 {
     const int nsegs = h->hp.pitch / lbm::kTmaW;
     const size_t icap = (size_t)std::max(0, nsegs - 2) * lbm::kTmaW * (size_t)std::max(0, h->hp.ny - 2);
+    const bool split = h->side != nullptr;
     StepArgs ae = a;
     ae.jobs = h->djobs + icap;
     ae.job_count = h->djob_count + 1;
+    lbm::JobArgs ji = job_args(h->dprob, 1, a.parity, a.rec, h->dstats, h->dticket, h->djobs, h->djob_count);
     lbm::JobArgs je = job_args(h->dprob, 1, a.parity, a.rec, h->dstats, h->dticket + 1, ae.jobs, ae.job_count);
-    je.publish = 0;
-    return lbm::launch_d2q9_flat(a, ae, je, nsegs, h->hp.ny, h->hp.method, h->stream, h->side, h->ev_fork,
+    ji.parts = je.parts = split ? 2 : 1;
+    ji.done = je.done = h->dticket + 2;
+    return lbm::launch_d2q9_flat(a, ae, ji, je, nsegs, h->hp.ny, h->hp.method, h->stream, h->side, h->ev_fork,
                                  h->ev_join);
 }
 
@@ -295,8 +300,9 @@ static cudaError_t launch_one(lbm_stefan* h, int parity, double* rec)
     }
     if (h->p.lattice == LBM_D2Q9) {
         cudaError_t e;
+        if (h->use_tma && LBM_FLAT && h->withhold_load < 0) return launch_flat(h, a);   // with its job kernels
         if (h->use_tma) {
-            e = LBM_FLAT && h->withhold_load < 0 ? launch_flat(h, a) : lbm::launch_d2q9_tma(a, h->tma, h->stream);
+            e = lbm::launch_d2q9_tma(a, h->tma, h->stream);
         } else {
             // one tile per warp; the hardware scheduler balances the short tiles
             const int grid = (h->hp.ntiles + lbm::kWarpsPerBlock - 1) / lbm::kWarpsPerBlock;
@@ -430,9 +436,10 @@ extern "C" lbm_status lbm_stefan_create(const lbm_stefan_params* p, void* cuda_s
     if (e == cudaSuccess) e = cudaMalloc(&h->dprob, sizeof(Problem));
     if (e == cudaSuccess) e = cudaMalloc(&h->dstats, sizeof(DevStats));
     if (e == cudaSuccess) e = cudaMemset(h->dstats, 0, sizeof(DevStats));
-    // [0]: the step's job list and job kernel; [1]: the wall rows' own (flat FP32 step)
-    if (e == cudaSuccess) e = cudaMalloc(&h->dticket, 2 * sizeof(unsigned int));
-    if (e == cudaSuccess) e = cudaMemset(h->dticket, 0, 2 * sizeof(unsigned int));
+    // [0]: the step's job list and job kernel; [1]: the wall rows' own (flat FP32
+    // step); ticket [2]: the flat step's finished job launches
+    if (e == cudaSuccess) e = cudaMalloc(&h->dticket, 3 * sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(h->dticket, 0, 3 * sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMalloc(&h->dscratch, sizeof(double) * 3 * (size_t)p->nx * p->ny);
     if (e == cudaSuccess) e = cudaMalloc(&h->djob_count, 2 * sizeof(unsigned int));
     if (e == cudaSuccess && q == 9) h->adj_tile_h = adjoint_tile_h(h->hp);
@@ -654,16 +661,19 @@ extern "C" lbm_status lbm_stefan_step_timed(lbm_stefan* h, int nsteps, double* m
     if (e == cudaSuccess) e = cudaEventRecord(ev[0], h->stream);
     for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
         StepArgs a = single_args(h, h->parity, nullptr);
+        const bool flat = h->p.lattice == LBM_D2Q9 && h->use_tma && LBM_FLAT && h->withhold_load < 0;
         if (h->p.lattice == LBM_D2Q5) {
             e = lbm::launch_d2q5_step(h->precision, a, h->stream);
+        } else if (flat) {
+            e = launch_flat(h, a);   // the whole step: its job kernels included
         } else if (h->use_tma) {
-            e = LBM_FLAT && h->withhold_load < 0 ? launch_flat(h, a) : lbm::launch_d2q9_tma(a, h->tma, h->stream);
+            e = lbm::launch_d2q9_tma(a, h->tma, h->stream);
         } else {
             const int grid = (h->hp.ntiles + lbm::kWarpsPerBlock - 1) / lbm::kWarpsPerBlock;
             e = lbm::launch_d2q9_step(h->precision, a, grid, h->stream);
         }
         if (e == cudaSuccess) e = cudaEventRecord(ev[2 * k + 1], h->stream);
-        if (e == cudaSuccess)
+        if (e == cudaSuccess && !flat)
             e = lbm::launch_newton_jobs(h->precision, h->hp.q,
                                         job_args(h->dprob, 1, h->parity, nullptr, h->dstats, h->dticket, h->djobs,
                                                  h->djob_count),

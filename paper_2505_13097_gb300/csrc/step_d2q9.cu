@@ -660,6 +660,23 @@ __global__ void __launch_bounds__(kJobThreads) newton_jobs_kernel(JobArgs a)
         last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
     }
     __syncthreads();
+    if (last && a.publish && a.parts > 1) {
+        // the step's other job launch may not have finished: the later one publishes
+        __shared__ bool final_part;
+        if (threadIdx.x == 0) {
+            __threadfence();
+            final_part = atomicAdd(a.done, 1u) == (unsigned)a.parts - 1;
+            if (final_part) *a.done = 0u;
+        }
+        __syncthreads();
+        if (!final_part) {
+            if (threadIdx.x == 0) {
+                *a.job_count = 0u;
+                *a.ticket = 0u;
+            }
+            return;
+        }
+    }
     if (last) {
         __threadfence();
         if (a.publish) {
@@ -725,8 +742,8 @@ cudaError_t launch_d2q9_tma(const StepArgs& a, const TmaMaps& m, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_d2q9_flat(const StepArgs& ai, const StepArgs& ae, const JobArgs& je, int nsegs, int ny,
-                             int method, cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join)
+cudaError_t launch_d2q9_flat(const StepArgs& ai, const StepArgs& ae, const JobArgs& ji, const JobArgs& je, int nsegs,
+                             int ny, int method, cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join)
 {
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -735,9 +752,10 @@ cudaError_t launch_d2q9_flat(const StepArgs& ai, const StepArgs& ae, const JobAr
     const bool split = side && fork && join;
     // rows that touch a wall: on the side stream (a higher-priority one) when
     // there is one, with the Newton solves of their nodes right after them,
-    // in parallel with the interior rows (they write disjoint rows; the
-    // interior kernel has no FP64 work, so the FP64 Newton solves of the wall
-    // strips use the SMs' otherwise idle FP64 pipes)
+    // in parallel with the interior rows and their Newton solves (they write
+    // disjoint rows; the interior kernel has no FP64 work, so the FP64 Newton
+    // solves of the wall strips use the SMs' otherwise idle FP64 pipes).  The
+    // later of the two job launches publishes the step.
     const int nside = nsegs >= 2 ? 2 : 1;
     const int nrows = nside * ny + (nsegs - nside) * (ny > 1 ? 2 : 1);
     const int ge = std::min((nrows + 7) / 8, sms * 4);
@@ -769,7 +787,8 @@ cudaError_t launch_d2q9_flat(const StepArgs& ai, const StepArgs& ae, const JobAr
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    if (split) {
+    e = launch_newton_jobs(1, 9, ji, s);
+    if (e == cudaSuccess && split) {
         e = cudaEventRecord(join, side);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, join, 0);
     }

@@ -250,7 +250,8 @@ def test_step_timed_matches_step(gpu, precision):
         S.set_ic(c.theta0())
         if timed:
             k0, k1 = S.step_timed(c.steps)
-            assert k0 > 0.0 and k1 > 0.0
+            # FP32: the whole step is in k0 (its Newton solves run inside it, on two streams)
+            assert k0 > 0.0 and (k1 >= 0.0 if precision == workloads.FP32 else k1 > 0.0)
         else:
             S.step(c.steps)
         outs.append((S.theta(), S.stats()["energy"], S.stats()["steps"]))
