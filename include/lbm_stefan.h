@@ -8,12 +8,9 @@
  * Algorithm 3 of the paper once per step: collision (Eq. 12), pull
  * streaming, the boundary closures of Sec. 4.2 on q, the zeroth moment, the
  * local Newton solve of Eq. (14), the source of Eq. (13), and the next
- * collision.  Kernel launches per step: D2Q9 with FP32 populations, four on
- * a handle with a stream of its own (the interior rows, then the Newton
- * solves of their nodes; concurrently, on a second, higher-priority stream,
- * the rows that touch a wall, then the Newton solves of theirs; the later of
- * the two Newton launches publishes the step), three on the legacy default
- * stream (interior rows, wall rows, one Newton kernel for both);
+ * collision.  Kernel launches per step: D2Q9 with FP32 populations, three
+ * (the S and N wall rows, rows 1 .. ny-2, then the kernel that solves the
+ * list of nodes that need the Newton iteration and publishes the step);
  * D2Q9 in FP64 and D2Q5, two (the stream/collide kernel, which hands the
  * nodes that need the Newton iteration to a list, then the kernel that
  * solves that list); D1Q3, one launch for all the steps of a call.
@@ -168,10 +165,8 @@ lbm_status lbm_stefan_step(lbm_stefan* h, int nsteps);
 /* D2Q9 and D2Q5: advance nsteps >= 1 steps launched one by one (no graph) with a
  * CUDA event before, between and after the kernels of each step, wait for
  * them, and return the mean device time per step of each kernel in ms:
- * ms_kernels[0] the stream/collide kernel, ms_kernels[1] the Newton job
- * kernel.  The single-problem FP32 D2Q9 step runs on two streams with its
- * Newton solves interleaved: ms_kernels[0] is the whole step (every launch,
- * up to the join of the streams) and ms_kernels[1] is 0.  Same result as
+ * ms_kernels[0] the stream/collide kernel (FP32 D2Q9: the wall-row and the
+ * flat kernel together), ms_kernels[1] the Newton job kernel.  Same result as
  * lbm_stefan_step; for measuring each kernel against its roofline.
  * Synchronizes. */
 lbm_status lbm_stefan_step_timed(lbm_stefan* h, int nsteps, double* ms_kernels);

@@ -121,6 +121,12 @@ struct StepArgs {
     unsigned int* ticket;    // last-block counter, zero between launches
     NewtonJob* jobs;         // deferred Newton nodes (D2Q9), capacity = total nodes
     unsigned int* job_count; // number of jobs; reset by the job kernel
+    // FP32 D2Q9 flat step over several problems: one block per tile
+    // (problem, 128-column strip, first of 8 rows) and one warp per wall row
+    // (problem, 2 strip + (0: row 0, 1: row ny-1)); NULL: a single problem
+    const int4* ftiles = nullptr;
+    const int2* wrows = nullptr;
+    int nwrows = 0;
 };
 
 // TMA descriptors of the single-problem FP32 D2Q9 step: state[0], state[1]
@@ -152,12 +158,7 @@ struct JobArgs {
     unsigned int* ticket;
     const NewtonJob* jobs;
     unsigned int* job_count;
-    int publish;             // 1: the step's statistics are published after this launch; 0: never by it
-    // parts > 1: the step has `parts` job launches (concurrent, on two streams);
-    // the last block of each adds one to *done, and the one that completes the
-    // count publishes (and clears *done)
-    int parts;
-    unsigned int* done;
+    int publish;             // 1: the last block publishes the step statistics; 0: it only clears the list
 };
 
 // Constants of the interior-node adjoint terms, converted once on the host.
@@ -193,17 +194,13 @@ int d2q9_blocks_per_sm(int precision);   // resident step blocks per SM (persist
 cudaError_t launch_d2q9_tma(const StepArgs& a, const TmaMaps& m, cudaStream_t s);
 // single problem, FP32: the interior rows and the rows that touch a wall (two
 // launches; with side, fork and join the second runs on `side`, joined back to s)
-// The whole step.  With a side stream, the wall rows' kernel and then a job
-// kernel over their own job list (ae.jobs / ae.job_count, described by je) run
-// on `side`, concurrently with the interior rows (ai) and the job kernel over
-// theirs (ji) on s, each job launch with parts = 2; s then waits for side.
-// Without one, everything runs on s and both row kernels append to ai's list
-// (ji, parts = 1; je unused).
-cudaError_t launch_d2q9_flat(const StepArgs& ai, const StepArgs& ae, const JobArgs& ji, const JobArgs& je, int nsegs,
-                             int ny, int method, cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join);
+// FP32 D2Q9 flat step: the wall-row kernel (nwrows rows) and the flat kernel
+// (nftiles blocks), both appending Newton nodes to a.jobs; the job kernel is
+// the caller's.
+cudaError_t launch_d2q9_flat(const StepArgs& a, int nftiles, int nwrows, int method, cudaStream_t s);
 int d2q9_tma_blocks_per_sm();
-// q = 9 or 5; grid 0: 8 blocks of 128 threads per SM; prio != 0: that scheduling priority
-cudaError_t launch_newton_jobs(int precision, int q, const JobArgs& a, cudaStream_t s, int grid = 0, int prio = 0);
+// q = 9 or 5; grid 0: two blocks per SM
+cudaError_t launch_newton_jobs(int precision, int q, const JobArgs& a, cudaStream_t s, int grid = 0);
 
 // D2Q5 launchers (step_d2q5.cu): one tile per warp over a.nslots tiles
 cudaError_t launch_d2q5_step(int precision, const StepArgs& a, cudaStream_t s);

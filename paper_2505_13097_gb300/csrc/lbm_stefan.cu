@@ -91,8 +91,6 @@ struct lbm_stefan {
     double* dilf_scratch = nullptr;    // 2D ILFBM: S0, two l iterates, two l differences (5 nx*ny)
     bool use_tma = false;              // FP32 D2Q9: the TMA row-pipeline step kernel
     lbm::TmaMaps tma;
-    cudaStream_t side = nullptr;       // flat FP32 step: stream of the wall-row kernel
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int withhold_load = -1;            // test hook of the TMA kernel's row loads (-1: off)
     GraphCache graph;
     // captured adjoint segments (lbm_stefan_adjoint_segment): recompute + reverse
@@ -257,37 +255,28 @@ static lbm::JobArgs job_args(const Problem* probs, int nprob, int parity, double
     j.jobs = jobs;
     j.job_count = count;
     j.publish = 1;
-    j.parts = 1;
-    j.done = nullptr;
     return j;
 }
 
-// FP32 D2Q9 single-problem step kernels: the interior rows and the wall rows.
-// With a side stream the wall rows append their Newton nodes to a list of
-// their own (the tail of djobs, after room for every interior node; counter
-// and ticket [1]) that a job kernel solves on the side stream.
-static cudaError_t launch_flat(lbm_stefan* h, const StepArgs& a)
+// FP32 D2Q9 single-problem step: the S and N wall rows, rows 1 .. ny-2 of
+// every 128-column strip, then the Newton job kernel.
+static cudaError_t launch_flat(lbm_stefan* h, const StepArgs& a, bool jobs = true)
 {
     const int nsegs = h->hp.pitch / lbm::kTmaW;
-    const size_t icap = (size_t)std::max(0, nsegs - 2) * lbm::kTmaW * (size_t)std::max(0, h->hp.ny - 2);
-    const bool split = h->side != nullptr;
-    StepArgs ae = a;
-    ae.jobs = h->djobs + icap;
-    ae.job_count = h->djob_count + 1;
-    lbm::JobArgs ji = job_args(h->dprob, 1, a.parity, a.rec, h->dstats, h->dticket, h->djobs, h->djob_count);
-    lbm::JobArgs je = job_args(h->dprob, 1, a.parity, a.rec, h->dstats, h->dticket + 1, ae.jobs, ae.job_count);
-    ji.parts = je.parts = split ? 2 : 1;
-    ji.done = je.done = h->dticket + 2;
-    return lbm::launch_d2q9_flat(a, ae, ji, je, nsegs, h->hp.ny, h->hp.method, h->stream, h->side, h->ev_fork,
-                                 h->ev_join);
+    const int nftiles = h->hp.ny > 2 ? nsegs * ((h->hp.ny + 7) / 8) : 0;
+    cudaError_t e = lbm::launch_d2q9_flat(a, nftiles, 2 * nsegs, h->hp.method, h->stream);
+    if (e != cudaSuccess || !jobs) return e;
+    return lbm::launch_newton_jobs(1, 9, job_args(h->dprob, 1, a.parity, a.rec, h->dstats, h->dticket, h->djobs,
+                                                  h->djob_count),
+                                   h->stream);
 }
 
 // One step.  D2Q9 and D2Q5: the stream/collide kernel(s), which defer the
 // nodes that need the Newton iteration, then the job kernel that solves them
-// (FP32 D2Q9: the flat interior kernel and the wall-row kernel, three launches
-// in all; FP64 D2Q9 and D2Q5: two).  D1Q3: one launch.  While the wait test
-// hook is on, the FP32 D2Q9 step runs the TMA row-pipeline kernel instead of
-// the flat pair (the kernel with the waits the hook exercises).
+// (FP32 D2Q9: the wall-row kernel and the flat kernel, three launches in all;
+// FP64 D2Q9 and D2Q5: two).  D1Q3: one launch.  While the wait test hook is
+// on, the FP32 D2Q9 step runs the TMA row-pipeline kernel instead of the
+// flat pair (the kernel with the waits the hook exercises).
 static cudaError_t launch_one(lbm_stefan* h, int parity, double* rec)
 {
     StepArgs a = single_args(h, parity, rec);
@@ -300,7 +289,7 @@ static cudaError_t launch_one(lbm_stefan* h, int parity, double* rec)
     }
     if (h->p.lattice == LBM_D2Q9) {
         cudaError_t e;
-        if (h->use_tma && LBM_FLAT && h->withhold_load < 0) return launch_flat(h, a);   // with its job kernels
+        if (h->use_tma && LBM_FLAT && h->withhold_load < 0) return launch_flat(h, a);   // with its job kernel
         if (h->use_tma) {
             e = lbm::launch_d2q9_tma(a, h->tma, h->stream);
         } else {
@@ -436,34 +425,19 @@ extern "C" lbm_status lbm_stefan_create(const lbm_stefan_params* p, void* cuda_s
     if (e == cudaSuccess) e = cudaMalloc(&h->dprob, sizeof(Problem));
     if (e == cudaSuccess) e = cudaMalloc(&h->dstats, sizeof(DevStats));
     if (e == cudaSuccess) e = cudaMemset(h->dstats, 0, sizeof(DevStats));
-    // [0]: the step's job list and job kernel; [1]: the wall rows' own (flat FP32
-    // step); ticket [2]: the flat step's finished job launches
-    if (e == cudaSuccess) e = cudaMalloc(&h->dticket, 3 * sizeof(unsigned int));
-    if (e == cudaSuccess) e = cudaMemset(h->dticket, 0, 3 * sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMalloc(&h->dticket, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(h->dticket, 0, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMalloc(&h->dscratch, sizeof(double) * 3 * (size_t)p->nx * p->ny);
-    if (e == cudaSuccess) e = cudaMalloc(&h->djob_count, 2 * sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMalloc(&h->djob_count, sizeof(unsigned int));
     if (e == cudaSuccess && q == 9) h->adj_tile_h = adjoint_tile_h(h->hp);
-    if (e == cudaSuccess) e = cudaMemset(h->djob_count, 0, 2 * sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(h->djob_count, 0, sizeof(unsigned int));
     h->hp.state[0] = bufs[0];
     h->hp.state[1] = bufs[1];
     h->hp.stats = 0;
     if (e == cudaSuccess && tma) h->use_tma = setup_tma(h);
-    // the flat FP32 step runs its wall rows and their Newton solves on a side
-    // stream of the highest priority, so that its blocks are scheduled ahead of
-    // the interior kernel's (non-default streams only: the legacy stream would
-    // serialize with it)
-    if (e == cudaSuccess && h->use_tma && LBM_FLAT && h->stream != nullptr) {
-        int least = 0, greatest = 0;
-        e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
-        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, greatest);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
-    }
-    // the list of deferred Newton nodes (D2Q9, D2Q5): room for one job per
-    // node of every row (pitch columns), so that the wall rows' list fits after
-    // the interior rows' in the flat FP32 step
+    // the list of deferred Newton nodes (D2Q9, D2Q5): one job per node at most
     if (e == cudaSuccess && q != 3)
-        e = cudaMalloc(&h->djobs, sizeof(lbm::NewtonJob) * (size_t)h->hp.pitch * p->ny);
+        e = cudaMalloc(&h->djobs, sizeof(lbm::NewtonJob) * (size_t)p->nx * p->ny);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         lbm_stefan_destroy(h);
@@ -582,8 +556,7 @@ static lbm_status capture_graph(lbm_stefan* h)
         if (g) cudaGraphDestroy(g);
         return fail(LBM_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
     }
-    // per-node priorities: the wall rows' kernels keep their higher priority
-    e = cudaGraphInstantiate(&h->graph.exec, g, cudaGraphInstantiateFlagUseNodePriority);
+    e = cudaGraphInstantiate(&h->graph.exec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
     h->graph.steps = kGraphSteps;
@@ -665,7 +638,7 @@ extern "C" lbm_status lbm_stefan_step_timed(lbm_stefan* h, int nsteps, double* m
         if (h->p.lattice == LBM_D2Q5) {
             e = lbm::launch_d2q5_step(h->precision, a, h->stream);
         } else if (flat) {
-            e = launch_flat(h, a);   // the whole step: its job kernels included
+            e = launch_flat(h, a, false);
         } else if (h->use_tma) {
             e = lbm::launch_d2q9_tma(a, h->tma, h->stream);
         } else {
@@ -673,7 +646,7 @@ extern "C" lbm_status lbm_stefan_step_timed(lbm_stefan* h, int nsteps, double* m
             e = lbm::launch_d2q9_step(h->precision, a, grid, h->stream);
         }
         if (e == cudaSuccess) e = cudaEventRecord(ev[2 * k + 1], h->stream);
-        if (e == cudaSuccess && !flat)
+        if (e == cudaSuccess)
             e = lbm::launch_newton_jobs(h->precision, h->hp.q,
                                         job_args(h->dprob, 1, h->parity, nullptr, h->dstats, h->dticket, h->djobs,
                                                  h->djob_count),
@@ -974,7 +947,7 @@ extern "C" lbm_status lbm_stefan_adjoint_segment(lbm_stefan* h, const void* chec
         CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = segment_launches(h, nsteps, theta_traj, adj, adj_other, 0);
         cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
-        if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&exec, g, cudaGraphInstantiateFlagUseNodePriority);
+        if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
         if (g) cudaGraphDestroy(g);
         if (e != cudaSuccess || e2 != cudaSuccess || !exec)
             return fail(LBM_ERR_CUDA, "segment capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
@@ -1021,9 +994,6 @@ extern "C" void lbm_stefan_destroy(lbm_stefan* h)
     cudaFree(h->djob_count);
     cudaFree(h->dilf);
     cudaFree(h->dilf_scratch);
-    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
-    if (h->ev_join) cudaEventDestroy(h->ev_join);
-    if (h->side) cudaStreamDestroy(h->side);
     delete h;
 }
 

@@ -263,132 +263,268 @@ __device__ __forceinline__ void flat_load_row(const float* __restrict__ row, lon
     qf[8][0] = e8; qf[8][1] = b8[0]; qf[8][2] = b8[1]; qf[8][3] = b8[2];
 }
 
+// What the scalar path adds for one node to its lane's sums.
+struct ColdSums {
+    ff e{0.f, 0.f};      // energy term (saturated and EEBM nodes: less the state's shift)
+    ff flux{0.f, 0.f};   // boundary flux
+    int liquid = 0, shifted = 0, dir = -1;
+};
+
+// One node (x, y), 1 <= y <= ny-2, of the flat step that the vector path
+// leaves out: a node on the W or E wall, or any node of a four-column group
+// that holds one (or reaches past nx).  The arithmetic of row_update /
+// row_update_eebm for one FP32 node, with scalar loads and stores; a Newton
+// node takes a job slot of its own.  Kept out of line, so that the vector
+// path's registers do not pay for the closures.
+static __device__ __noinline__ void flat_cold_node(const Problem& pb, int pi, const float* __restrict__ src,
+                                                   float* __restrict__ dst, double* __restrict__ rec, int x, int y,
+                                                   float sh, NewtonJob* jobs, unsigned int* job_count, ColdSums& cs)
+{
+    const long long pl = pb.plane, pitch = pb.pitch;
+    const long long at = (long long)(y + 1) * pitch + x;
+    float u[9], q[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        u[i] = __ldg(src + i * pl + at);
+        q[i] = __ldg(src + i * pl + at - d2_ey(i) * pitch - d2_ex(i));   // Omega_i(x - e_i)
+    }
+    int wall = -1;
+    if (x == 0 || x == pb.nx - 1) cs.flux = wall_closure_f(q, u, x, y, pb, wall, sh);
+    const float omc = (float)(1.0 - pb.omega);
+    const float wP[3] = {d2_wf(0), d2_wf(1), d2_wf(5)};
+    float* d = dst + at;
+    if (pb.method == 1) {
+        // EEBM (row_update_eebm)
+        float Hs = 0.f;
+#pragma unroll
+        for (int i = 8; i >= 0; --i) Hs += q[i];
+        const float om = 1.0f - omc;
+        const float H = Hs + sh;
+        const float th = eebm_theta(H, (float)pb.inv_ste);
+        d[0] = fmaf(omc, q[0], om * (H - (1.0f - wP[0]) * th - wP[0] * sh));
+        const float tr = th - sh;
+#pragma unroll
+        for (int i = 1; i < 9; ++i) d[i * pl] = fmaf(omc, q[i], om * (i <= 4 ? wP[1] : wP[2]) * tr);
+        cs.e = ff{Hs, 0.f};
+        cs.shifted = 1;
+        if (rec) rec[(long long)y * pitch + x] = (double)th;
+        return;
+    }
+    const float tf = approx_sum<float>(u) + sh;
+    float mf = 0.f;
+#pragma unroll
+    for (int i = 8; i >= 0; --i) mf += q[i];
+    const float mt = mf + sh;
+    const float thr_f = (float)pb.sat;
+    const float marg = 1e-5f * (1.0f + fabsf(tf));
+    const bool sat_liq = tf >= thr_f + marg && mt >= thr_f + marg;
+    const bool sat_sol = tf <= -thr_f - marg && mt <= -thr_f - marg;
+    float c;
+    double thn;
+    if (wall >= 0) {
+        // Dirichlet node: theta' = theta_D; c less omega sh
+        ff mm{0.f, 0.f};
+#pragma unroll
+        for (int i = 8; i >= 0; --i) ff_add(mm, q[i]);
+        c = ((pb.wall_th_hi[wall] - sh) - omc * mm.hi) + (pb.wall_th_lo[wall] - omc * mm.lo);
+        cs.e = ff{pb.wall_th_hi[wall], pb.wall_th_lo[wall]};
+        cs.dir = wall;
+        thn = pb.wall_theta[wall];
+    } else if (sat_liq || sat_sol) {
+        c = (float)pb.omega * mf;
+        cs.e = ff{mf, 0.f};
+        cs.shifted = 1;
+        cs.liquid = sat_liq ? 1 : 0;
+        thn = (double)mf + (double)sh;
+    } else {
+        // the local Newton solve of Eq. (14) is deferred: q stored unrelaxed
+        NewtonJob jb;
+        jb.prob = pi;
+        jb.node = y * pb.nx + x;
+        jb.m0 = jb.theta = 0.0;
+        jobs[atomicAdd(job_count, 1u)] = jb;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) d[i * pl] = q[i];
+        if (rec) rec[(long long)y * pitch + x] = 0.0;
+        return;
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) d[i * pl] = fmaf(omc, q[i], wP[i == 0 ? 0 : (i <= 4 ? 1 : 2)] * c);
+    if (rec) rec[(long long)y * pitch + x] = thn;
+}
+
 #ifndef LBM_FLAT_MINB
 #define LBM_FLAT_MINB 3   // resident blocks per SM the register budget is fitted to
 #endif
-// Interior rows: strips 1 .. nsegs-2 (no wall column, no padding column),
-// rows 1 .. ny-2; IREBM (Algorithm 3) or, with EEBM, Algorithm 2.  Tile t: strip 1 + t % (nsegs - 2), rows 8 (t / (nsegs - 2))
-// + warp.  The other rows are computed by d2q9_edge_kernel.
+// Rows 1 .. ny-2 of every 128-column strip; IREBM (Algorithm 3) or, with
+// EEBM, Algorithm 2.  A block takes one tile of 128 columns x 8 rows (single
+// problem: tile t = strip t % nsegs, rows 8 (t / nsegs) + warp; batches: the
+// tile table a.ftiles, entry (problem, strip, first row)).  Lanes whose four
+// columns are all inside (1 <= x <= nx-2) run the vector path below; a lane
+// whose group holds column 0 or nx-1 or reaches past nx leaves it and runs
+// flat_cold_node for each of its nodes inside the lattice.  Rows 0 and ny-1
+// are the wall-row kernel's.
 template <bool REC, bool EEBM>
 __global__ void __launch_bounds__(256, LBM_FLAT_MINB) d2q9_flat_kernel(const StepArgs a)
 {
     __shared__ WarpSums wsum[8];
-    const Problem& pb = a.probs[0];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
+    int pi, seg, y;
+    if (a.ftiles) {
+        const int4 t = a.ftiles[blockIdx.x];
+        pi = t.x;
+        seg = t.y;
+        y = t.z + warp;
+    } else {
+        const int nsegs = a.probs[0].pitch / 128;
+        pi = 0;
+        seg = blockIdx.x % nsegs;
+        y = (blockIdx.x / nsegs) * 8 + warp;
+    }
+    const Problem& pb = a.probs[pi];
     const int nx = pb.nx, ny = pb.ny;
-    const long long pl = pb.plane, pitch = pb.pitch;
-    const int nin = pb.pitch / 128 - 2;   // interior strips (>= 1, or the kernel is not launched)
-    const int ntiles = nin * ((ny + 7) / 8);
-    const float* __restrict__ src = static_cast<const float*>(pb.state[a.parity]);
-    float* __restrict__ dst = static_cast<float*>(pb.state[a.parity ^ 1]);
-    const float omc = (float)(1.0 - pb.omega);
-    const float om_f = (float)pb.omega;
-    const float wP[3] = {d2_wf(0), d2_wf(1), d2_wf(5)};
-    const float thr_f = (float)pb.sat;
-    const float sh = state_shift(pb, a.parity);   // stored values are Omega_i - w_i sh
     Acc<float> acc;
     TileSums ts;
-    GlobalJobSink sink{a.jobs, a.job_count};
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int seg = 1 + t % nin;
-        const int y = (t / nin) * 8 + warp;
-        if (y < 1 || y >= ny - 1) continue;
-        const int x0 = seg * 128 + 4 * lane;
+    const int x0 = seg * 128 + 4 * lane;
+    if (y >= 1 && y < ny - 1) {   // the same for the whole warp
+        const long long pl = pb.plane, pitch = pb.pitch;
+        const float* __restrict__ src = static_cast<const float*>(pb.state[a.parity]);
+        float* __restrict__ dst = static_cast<float*>(pb.state[a.parity ^ 1]);
+        const float omc = (float)(1.0 - pb.omega);
+        const float wP[3] = {d2_wf(0), d2_wf(1), d2_wf(5)};
+        const float sh = state_shift(pb, a.parity);   // stored values are Omega_i - w_i sh
         const float* row = src + (y + 1) * pitch + x0;
         float* orow = dst + (y + 1) * pitch + x0;
-        if constexpr (EEBM) {
-            float u[9][4], qf[9][4];
-            flat_load_row(row, pitch, pl, u, qf);
-            row_update_eebm<float, 4, REC, false>(pb, y, x0, qf, u[0], u[1], u[2], u[3], u[4], u[5], u[6], u[7], u[8],
-                                                  GlobalRowOut<float, 4>{orow, pl}, a.rec, acc, ts, omc, wP, nx, ny, sh);
-            continue;
-        }
-        // interior IREBM row: the arithmetic of row_update's interior branch
-        // (same operations, same order), with nothing else live
+        // cold: the group holds column 0 or nx-1, or lies (partly) past nx
+        const bool cold = x0 == 0 || x0 + 3 >= nx - 1;
+        // every load of the vector path stays inside the buffer, cold lanes included
         float u[9][4], qf[9][4];
         flat_load_row(row, pitch, pl, u, qf);
-        float c[4];
-        bool newton[4];
-        bool any_newton = false;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const float uk[9] = {u[0][k], u[1][k], u[2][k], u[3][k], u[4][k], u[5][k], u[6][k], u[7][k], u[8][k]};
-            const float tf = approx_sum<float>(uk) + sh;   // theta
-            float mf = 0.f;                                  // M0(q) - sh
-#pragma unroll
-            for (int i = 8; i >= 0; --i) mf += qf[i][k];
-            const float mt = mf + sh;
-            const float marg = 1e-5f * (1.0f + fabsf(tf));
-            const bool sat_liq = tf >= thr_f + marg && mt >= thr_f + marg;
-            const bool sat_sol = tf <= -thr_f - marg && mt <= -thr_f - marg;
-            newton[k] = !(sat_liq || sat_sol);
-            any_newton |= newton[k];
-            c[k] = newton[k] ? 0.f : om_f * mf;   // c - omega sh = omega (m0 - sh)
-            if (!newton[k]) {
-                acc.add_f(mf);
-                ts.liquid += sat_liq ? 1 : 0;
-                ts.shifted += 1;
-            }
-        }
-        float wc[3][4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            wc[0][k] = wP[0] * c[k];
-            wc[1][k] = wP[1] * c[k];
-            wc[2][k] = wP[2] * c[k];
-        }
-        if (__any_sync(kFull, any_newton)) {
-            // nodes that need the local Newton solve: stored unrelaxed, their
-            // index appended to the job list (the job kernel forms m0, theta)
-            int cnt = 0;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) cnt += newton[k] ? 1 : 0;
-            int incl = cnt;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int v = __shfl_up_sync(kFull, incl, o);
-                if (lane >= o) incl += v;
-            }
-            const unsigned base = sink.reserve((unsigned)__shfl_sync(kFull, incl, 31), lane);
-            unsigned slot = base + (unsigned)(incl - cnt);
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                if (newton[k]) {
-                    NewtonJob jb;
-                    jb.prob = 0;
-                    jb.node = y * nx + x0 + k;
-                    jb.m0 = jb.theta = 0.0;
-                    sink.put(slot++, jb);
-                }
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                const int cl = i == 0 ? 0 : (i <= 4 ? 1 : 2);
-                float o[4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) o[k] = newton[k] ? qf[i][k] : fmaf(omc, qf[i][k], wc[cl][k]);
-                stv_n(orow + i * pl, o);
-            }
-        } else {
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                const int cl = i == 0 ? 0 : (i <= 4 ? 1 : 2);
-                float o[4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) o[k] = fmaf(omc, qf[i][k], wc[cl][k]);
-                stv_n(orow + i * pl, o);
-            }
-        }
-        if constexpr (REC) {
-            double thn[4];
+        if constexpr (EEBM) {
+            const float om = 1.0f - omc;
+            const float inv_ste = (float)pb.inv_ste;
+            float hs = 0.f;
+            double thn[REC ? 4 : 1];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                float mf = 0.f;
+                float Hs = 0.f;   // H less the shift
+#pragma unroll
+                for (int i = 8; i >= 0; --i) Hs += qf[i][k];
+                hs += Hs;
+                const float H = Hs + sh;
+                const float th = eebm_theta(H, inv_ste);
+                if constexpr (REC) thn[k] = (double)th;
+                qf[0][k] = fmaf(omc, qf[0][k], om * (H - (1.0f - wP[0]) * th - wP[0] * sh));
+                const float tr = th - sh;
+#pragma unroll
+                for (int i = 1; i < 9; ++i) qf[i][k] = fmaf(omc, qf[i][k], om * (i <= 4 ? wP[1] : wP[2]) * tr);
+            }
+            if (!cold) {
+                acc.add_ff(ff{hs, 0.f});
+                ts.shifted += 4;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    float o[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) o[k] = qf[i][k];
+                    stv_n(orow + i * pl, o);
+                }
+                if constexpr (REC) st_rec<4>(a.rec + (long long)y * pitch + x0, thn);
+            }
+        } else {
+            // interior IREBM nodes: the arithmetic of row_update's interior branch
+            const float om_f = (float)pb.omega;
+            const float thr_f = (float)pb.sat;
+            float c[4];
+            bool newton[4];
+            bool any_newton = false;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float uk[9] = {u[0][k], u[1][k], u[2][k], u[3][k], u[4][k], u[5][k], u[6][k], u[7][k], u[8][k]};
+                const float tf = approx_sum<float>(uk) + sh;   // theta
+                float mf = 0.f;                                  // M0(q) - sh
 #pragma unroll
                 for (int i = 8; i >= 0; --i) mf += qf[i][k];
-                thn[k] = newton[k] ? 0.0 : (double)mf + (double)sh;
+                const float mt = mf + sh;
+                const float marg = 1e-5f * (1.0f + fabsf(tf));
+                const bool sat_liq = tf >= thr_f + marg && mt >= thr_f + marg;
+                const bool sat_sol = tf <= -thr_f - marg && mt <= -thr_f - marg;
+                newton[k] = !cold && !(sat_liq || sat_sol);
+                any_newton |= newton[k];
+                c[k] = newton[k] ? 0.f : om_f * mf;   // c - omega sh = omega (m0 - sh)
+                if (!newton[k] && !cold) {
+                    acc.add_f(mf);
+                    ts.liquid += sat_liq ? 1 : 0;
+                    ts.shifted += 1;
+                }
             }
-            st_rec<4>(a.rec + (long long)y * pitch + x0, thn);
+            float wc[3][4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                wc[0][k] = wP[0] * c[k];
+                wc[1][k] = wP[1] * c[k];
+                wc[2][k] = wP[2] * c[k];
+            }
+            if (__any_sync(kFull, any_newton)) {
+                // nodes that need the local Newton solve: stored unrelaxed, their
+                // index appended to the job list (the job kernel forms m0, theta)
+                int cnt = 0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) cnt += newton[k] ? 1 : 0;
+                int incl = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(kFull, incl, o);
+                    if (lane >= o) incl += v;
+                }
+                GlobalJobSink sink{a.jobs, a.job_count};
+                const unsigned base = sink.reserve((unsigned)__shfl_sync(kFull, incl, 31), lane);
+                unsigned slot = base + (unsigned)(incl - cnt);
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (newton[k]) {
+                        NewtonJob jb;
+                        jb.prob = pi;
+                        jb.node = y * nx + x0 + k;
+                        jb.m0 = jb.theta = 0.0;
+                        a.jobs[slot++] = jb;
+                    }
+            }
+            if (!cold) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    const int cl = i == 0 ? 0 : (i <= 4 ? 1 : 2);
+                    float o[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) o[k] = newton[k] ? qf[i][k] : fmaf(omc, qf[i][k], wc[cl][k]);
+                    stv_n(orow + i * pl, o);
+                }
+                if constexpr (REC) {
+                    double thn[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        float mf = 0.f;
+#pragma unroll
+                        for (int i = 8; i >= 0; --i) mf += qf[i][k];
+                        thn[k] = newton[k] ? 0.0 : (double)mf + (double)sh;
+                    }
+                    st_rec<4>(a.rec + (long long)y * pitch + x0, thn);
+                }
+            }
+        }
+        if (cold) {
+            // the group's nodes inside the lattice, one at a time
+            for (int k = 0; k < 4 && x0 + k < nx; ++k) {
+                ColdSums cs;
+                flat_cold_node(pb, pi, src, dst, a.rec, x0 + k, y, sh, a.jobs, a.job_count, cs);
+                acc.add_ff(cs.e);
+                ff_add(ts.flux_f, cs.flux.hi);
+                ts.flux_f.lo += cs.flux.lo;
+                ts.liquid += cs.liquid;
+                ts.shifted += cs.shifted;
+                if (cs.dir >= 0) ts.dir_count[cs.dir] += 1;
+            }
         }
     }
     const WarpSums w = warp_tile_sums<float>(acc, ts);
@@ -401,45 +537,40 @@ __global__ void __launch_bounds__(256, LBM_FLAT_MINB) d2q9_flat_kernel(const Ste
     }
 }
 
-// Rows of the single-problem FP32 step that touch a wall: every row of the
-// first and last 128-column strips, and rows 0 and ny-1 of the other strips;
-// one row per warp, the full row update (closures of Sec. 4.2, Newton
-// hand-off, EEBM).  Runs alongside d2q9_flat_kernel (both read the source
-// state and write disjoint rows).
+// Rows 0 and ny-1 (the S and N walls) of every 128-column strip, FP32: one
+// row per warp, the full row update (closures of Sec. 4.2, Newton hand-off,
+// EEBM).  Row r: single problem, strip r / 2, row 0 or ny-1 by r % 2;
+// batches: the table a.wrows, entry (problem, 2 strip + (0: row 0, 1: row ny-1)).
+// Each warp adds its sums to its row's problem after the row.
 template <bool REC>
-__global__ void __launch_bounds__(256) d2q9_edge_kernel(const StepArgs a)
+__global__ void __launch_bounds__(256) d2q9_wall_rows_kernel(const StepArgs a)
 {
-    __shared__ WarpSums wsum[8];
-    const Problem& pb = a.probs[0];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int nx = pb.nx, ny = pb.ny;
-    const long long pl = pb.plane, pitch = pb.pitch;
-    const int nsegs = pb.pitch / 128;
-    const int nside = nsegs >= 2 ? 2 : 1;                  // wall strips
-    const int nin = nsegs - nside;                          // other strips: rows 0 and ny-1
-    const int nrows = nside * ny + nin * (ny > 1 ? 2 : 1);
-    const float* __restrict__ src = static_cast<const float*>(pb.state[a.parity]);
-    float* __restrict__ dst = static_cast<float*>(pb.state[a.parity ^ 1]);
-    const float omc = (float)(1.0 - pb.omega);
-    const float om_f = (float)pb.omega;
-    const double omc_d = 1.0 - pb.omega;
-    const float wP[3] = {d2_wf(0), d2_wf(1), d2_wf(5)};
-    const float thr_f = (float)pb.sat;
-    const float sh = state_shift(pb, a.parity);   // stored values are Omega_i - w_i sh
-    Acc<float> acc;
-    TileSums ts;
-    GlobalJobSink sink{a.jobs, a.job_count};
+    const int nrows = a.wrows ? a.nwrows : 2 * (a.probs[0].pitch / 128);
     for (int r = blockIdx.x * 8 + warp; r < nrows; r += gridDim.x * 8) {
-        int seg, y;
-        if (r < nside * ny) {
-            seg = r < ny ? 0 : nsegs - 1;
-            y = r % ny;
-        } else {
-            const int j = r - nside * ny;
-            seg = 1 + j % nin;
-            y = (j / nin) == 0 ? 0 : ny - 1;
+        int pi = 0, code = r;
+        if (a.wrows) {
+            const int2 e = a.wrows[r];
+            pi = e.x;
+            code = e.y;
         }
+        const Problem& pb = a.probs[pi];
+        const int nx = pb.nx, ny = pb.ny;
+        const long long pl = pb.plane, pitch = pb.pitch;
+        const int seg = code >> 1;
+        const int y = (code & 1) ? ny - 1 : 0;
+        const float* __restrict__ src = static_cast<const float*>(pb.state[a.parity]);
+        float* __restrict__ dst = static_cast<float*>(pb.state[a.parity ^ 1]);
+        const float omc = (float)(1.0 - pb.omega);
+        const float om_f = (float)pb.omega;
+        const double omc_d = 1.0 - pb.omega;
+        const float wP[3] = {d2_wf(0), d2_wf(1), d2_wf(5)};
+        const float thr_f = (float)pb.sat;
+        const float sh = state_shift(pb, a.parity);   // stored values are Omega_i - w_i sh
+        Acc<float> acc;
+        TileSums ts;
+        GlobalJobSink sink{a.jobs, a.job_count};
         const int x0 = seg * 128 + 4 * lane;
         float u[9][4], qf[9][4];
         flat_load_row(src + (y + 1) * pitch + x0, pitch, pl, u, qf);
@@ -449,15 +580,8 @@ __global__ void __launch_bounds__(256) d2q9_edge_kernel(const StepArgs a)
                                                  out, a.rec, acc, ts, omc, wP, nx, ny, sh);
         else
             row_update<float, 4, REC, true>(pb, y, x0, lane, qf, u[0], u[1], u[2], u[3], u[4], u[5], u[6], u[7], u[8],
-                                            out, a.rec, acc, ts, 0, sink, omc, om_f, omc_d, wP, thr_f, nx, ny, sh);
-    }
-    const WarpSums w = warp_tile_sums<float>(acc, ts);
-    if (lane == 0) wsum[warp] = w;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        WarpSums tot = wsum[0];
-        for (int k = 1; k < 8; ++k) add_sums(tot, wsum[k]);
-        emit_sums(tot, &a.stats[pb.stats]);
+                                            out, a.rec, acc, ts, pi, sink, omc, om_f, omc_d, wP, thr_f, nx, ny, sh);
+        flush_tile_sums<float>(acc, ts, &a.stats[pb.stats], lane);
     }
 }
 
@@ -660,23 +784,6 @@ __global__ void __launch_bounds__(kJobThreads) newton_jobs_kernel(JobArgs a)
         last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (last && a.publish && a.parts > 1) {
-        // the step's other job launch may not have finished: the later one publishes
-        __shared__ bool final_part;
-        if (threadIdx.x == 0) {
-            __threadfence();
-            final_part = atomicAdd(a.done, 1u) == (unsigned)a.parts - 1;
-            if (final_part) *a.done = 0u;
-        }
-        __syncthreads();
-        if (!final_part) {
-            if (threadIdx.x == 0) {
-                *a.job_count = 0u;
-                *a.ticket = 0u;
-            }
-            return;
-        }
-    }
     if (last) {
         __threadfence();
         if (a.publish) {
@@ -696,25 +803,6 @@ __global__ void __launch_bounds__(kJobThreads) newton_jobs_kernel(JobArgs a)
             *a.ticket = 0u;
         }
     }
-}
-
-// A launch with an explicit scheduling priority (0: the stream's own).  The
-// priority is a launch attribute, so a graph captured from the stream keeps
-// it per kernel node.
-template <typename... KArgs, typename... Args>
-static cudaError_t launch_prio(void (*k)(KArgs...), int grid, int block, cudaStream_t s, int prio, Args... args)
-{
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3((unsigned)block);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributePriority;
-    at[0].val.priority = prio;
-    cfg.attrs = at;
-    cfg.numAttrs = prio != 0 ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, k, args...);
 }
 
 template <typename P, bool REC>
@@ -742,55 +830,29 @@ cudaError_t launch_d2q9_tma(const StepArgs& a, const TmaMaps& m, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_d2q9_flat(const StepArgs& ai, const StepArgs& ae, const JobArgs& ji, const JobArgs& je, int nsegs,
-                             int ny, int method, cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join)
+cudaError_t launch_d2q9_flat(const StepArgs& a, int nftiles, int nwrows, int method, cudaStream_t s)
 {
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    const bool split = side && fork && join;
-    // rows that touch a wall: on the side stream (a higher-priority one) when
-    // there is one, with the Newton solves of their nodes right after them,
-    // in parallel with the interior rows and their Newton solves (they write
-    // disjoint rows; the interior kernel has no FP64 work, so the FP64 Newton
-    // solves of the wall strips use the SMs' otherwise idle FP64 pipes).  The
-    // later of the two job launches publishes the step.
-    const int nside = nsegs >= 2 ? 2 : 1;
-    const int nrows = nside * ny + (nsegs - nside) * (ny > 1 ? 2 : 1);
-    const int ge = std::min((nrows + 7) / 8, sms * 4);
-    const StepArgs& a_edge = split ? ae : ai;
-    cudaStream_t es = s;
-    int prio = 0;
-    if (split) {
-        int least = 0;
-        e = cudaDeviceGetStreamPriorityRange(&least, &prio);
-        if (e == cudaSuccess) e = cudaEventRecord(fork, s);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(side, fork, 0);
-        if (e != cudaSuccess) return e;
-        es = side;
-    }
-    e = launch_prio(a_edge.rec ? d2q9_edge_kernel<true> : d2q9_edge_kernel<false>, ge, 256, es, prio, a_edge);
-    if (e == cudaSuccess && split) e = launch_newton_jobs(1, 9, je, side, sms * 2, prio);
-    if (e != cudaSuccess) return e;
-    // interior rows (if any strip has no wall column)
-    const int nin = nsegs - 2;
-    if (nin >= 1 && ny > 2) {
-        const int g = nin * ((ny + 7) / 8);   // one tile (128 columns, 8 rows) per block
-        if (method == 1) {
-            if (ai.rec) d2q9_flat_kernel<true, true><<<g, 256, 0, s>>>(ai);
-            else d2q9_flat_kernel<false, true><<<g, 256, 0, s>>>(ai);
-        } else {
-            if (ai.rec) d2q9_flat_kernel<true, false><<<g, 256, 0, s>>>(ai);
-            else d2q9_flat_kernel<false, false><<<g, 256, 0, s>>>(ai);
-        }
+    // the S and N wall rows (few), then rows 1 .. ny-2 of every strip
+    if (nwrows > 0) {
+        const int g = std::min((nwrows + 7) / 8, sms * 4);
+        if (a.rec) d2q9_wall_rows_kernel<true><<<g, 256, 0, s>>>(a);
+        else d2q9_wall_rows_kernel<false><<<g, 256, 0, s>>>(a);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    e = launch_newton_jobs(1, 9, ji, s);
-    if (e == cudaSuccess && split) {
-        e = cudaEventRecord(join, side);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, join, 0);
+    if (nftiles > 0) {
+        if (method == 1) {
+            if (a.rec) d2q9_flat_kernel<true, true><<<nftiles, 256, 0, s>>>(a);
+            else d2q9_flat_kernel<false, true><<<nftiles, 256, 0, s>>>(a);
+        } else {
+            if (a.rec) d2q9_flat_kernel<true, false><<<nftiles, 256, 0, s>>>(a);
+            else d2q9_flat_kernel<false, false><<<nftiles, 256, 0, s>>>(a);
+        }
+        e = cudaGetLastError();
     }
     return e;
 }
@@ -806,15 +868,16 @@ int d2q9_tma_blocks_per_sm()
 }
 
 template <int Q>
-static cudaError_t launch_jobs_q(int precision, const JobArgs& a, int grid, cudaStream_t s, int prio)
+static cudaError_t launch_jobs_q(int precision, const JobArgs& a, int grid, cudaStream_t s)
 {
     void (*k)(JobArgs) = precision == 1
                              ? (a.rec ? newton_jobs_kernel<float, true, Q> : newton_jobs_kernel<float, false, Q>)
                              : (a.rec ? newton_jobs_kernel<double, true, Q> : newton_jobs_kernel<double, false, Q>);
-    return launch_prio(k, grid, kJobThreads, s, prio, a);
+    k<<<grid, kJobThreads, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
-cudaError_t launch_newton_jobs(int precision, int q, const JobArgs& a, cudaStream_t s, int grid, int prio)
+cudaError_t launch_newton_jobs(int precision, int q, const JobArgs& a, cudaStream_t s, int grid)
 {
     if (grid <= 0) {
         int dev = 0, sms = 0;
@@ -822,8 +885,8 @@ cudaError_t launch_newton_jobs(int precision, int q, const JobArgs& a, cudaStrea
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         grid = sms * 2;
     }
-    if (q == 9) return launch_jobs_q<9>(precision, a, grid, s, prio);
-    if (q == 5) return launch_jobs_q<5>(precision, a, grid, s, prio);
+    if (q == 9) return launch_jobs_q<9>(precision, a, grid, s);
+    if (q == 5) return launch_jobs_q<5>(precision, a, grid, s);
     return cudaErrorInvalidValue;
 }
 
