@@ -282,14 +282,14 @@ lbm_status lbm_stefan_adjoint_finish(lbm_stefan* h, const void* adj0, double* g_
 void lbm_stefan_destroy(lbm_stefan* h);
 
 /* ---------------------------------------------------------------- batches
- * Many independent D2Q9 problems of uneven sizes advanced by two kernel
- * launches per step, both over all problems: the step kernel, then the Newton
- * job kernel; the launches of a call are captured in a CUDA graph.  In FP32
- * the step kernel is the TMA row-pipeline kernel over a table of tiles (a
- * 128-column strip of one problem over a range of rows, one tile per block);
- * in FP64 the persistent warp-tile kernel over a schedule of warp tiles.  The
- * tile height and the order of the tiles come from lbm_stefan_batch_autotune
- * (or defaults). */
+ * Many independent D2Q9 problems of uneven sizes advanced by kernel launches
+ * over all problems at once, then the Newton job kernel; the launches of a
+ * call are captured in a CUDA graph.  FP32: the kernels of the single-problem
+ * FP32 step over tables (the S and N wall rows of every problem, then one
+ * block per 128-column x 8-row tile of every problem); FP64: the persistent
+ * warp-tile kernel over a schedule of warp tiles.  The order of the problems
+ * (and, in FP64, the tile height) come from lbm_stefan_batch_autotune (or
+ * defaults). */
 
 typedef struct {
     int nx, ny;                 /* >= 2 each */
@@ -305,12 +305,13 @@ lbm_status lbm_stefan_batch_set_ic(lbm_stefan_batch* b, int k, const double* the
 lbm_status lbm_stefan_batch_step(lbm_stefan_batch* b, int nsteps);
 lbm_status lbm_stefan_batch_get_fields(lbm_stefan_batch* b, int k, double* theta, int on_device);
 lbm_status lbm_stefan_batch_get_stats(lbm_stefan_batch* b, int k, lbm_stefan_stats* out);
-/* Time candidate tile heights and schedules for trial_steps steps each and
- * keep the fastest; the state is saved and restored around the trials.
- * chosen_tile_h receives the chosen height (may be NULL). */
+/* Time candidate schedules (FP64: and tile heights) for trial_steps steps
+ * each and keep the fastest; the state is saved and restored around the
+ * trials.  chosen_tile_h receives the chosen height (FP32: 8; may be NULL). */
 lbm_status lbm_stefan_batch_autotune(lbm_stefan_batch* b, int trial_steps, int* chosen_tile_h);
-/* Set the tile height (rows per tile) and schedule (0 = problem order,
- * 1 = largest problems first in FP32, longest tiles first in FP64) explicitly. */
+/* Set the tile height (rows per warp tile, FP64; FP32 tiles have 8 rows and
+ * ignore it) and schedule (0 = problem order, 1 = largest problems first in
+ * FP32, longest tiles first in FP64) explicitly. */
 lbm_status lbm_stefan_batch_set_schedule(lbm_stefan_batch* b, int tile_h, int schedule);
 void lbm_stefan_batch_destroy(lbm_stefan_batch* b);
 

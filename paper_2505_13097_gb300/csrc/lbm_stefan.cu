@@ -137,6 +137,11 @@ struct lbm_stefan_batch {
     lbm::TmaMaps tma;
     CUtensorMap* dmaps = nullptr;      // 2 descriptors per problem
     int4* dtiles = nullptr;
+    bool use_flat = false;             // FP32: the flat and wall-row kernels over tables
+    int4* dftiles = nullptr;           // (problem, strip, first row) per flat block
+    int nftiles = 0;
+    int2* dwrows = nullptr;            // (problem, 2 strip + S/N) per wall row
+    int nwrows = 0;
     GraphCache graph;
 };
 
@@ -1020,6 +1025,43 @@ static bool batch_setup_tma(lbm_stefan_batch* b)
     return lbm::d2q9_tma_blocks_per_sm() > 0;   // also selects the shared-memory carveout
 }
 
+// Flat-kernel tables: every problem's 128-column strips in 8-row tiles
+// (strips fastest, then bands), and its S and N rows; schedule 1 puts the
+// largest problems first.
+static lbm_status batch_build_flat_tables(lbm_stefan_batch* b, int schedule)
+{
+    std::vector<int> order(b->count);
+    for (int k = 0; k < b->count; ++k) order[k] = k;
+    if (schedule == 1)
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+            return (long long)b->hp[x].nx * b->hp[x].ny > (long long)b->hp[y].nx * b->hp[y].ny;
+        });
+    std::vector<int4> tiles;
+    std::vector<int2> rows;
+    for (int k : order) {
+        const Problem& pb = b->hp[k];
+        const int nsegs = pb.pitch / lbm::kTmaW;
+        if (pb.ny > 2)
+            for (int y0 = 0; y0 < pb.ny - 1; y0 += 8)
+                for (int seg = 0; seg < nsegs; ++seg) tiles.push_back(make_int4(k, seg, y0, 0));
+        for (int seg = 0; seg < nsegs; ++seg) {
+            rows.push_back(make_int2(k, 2 * seg));
+            rows.push_back(make_int2(k, 2 * seg + 1));
+        }
+    }
+    cudaFree(b->dftiles);
+    cudaFree(b->dwrows);
+    b->dftiles = nullptr;
+    b->dwrows = nullptr;
+    CUDA_TRY(cudaMalloc(&b->dftiles, sizeof(int4) * std::max<size_t>(1, tiles.size())));
+    CUDA_TRY(cudaMemcpy(b->dftiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMalloc(&b->dwrows, sizeof(int2) * rows.size()));
+    CUDA_TRY(cudaMemcpy(b->dwrows, rows.data(), sizeof(int2) * rows.size(), cudaMemcpyHostToDevice));
+    b->nftiles = (int)tiles.size();
+    b->nwrows = (int)rows.size();
+    return LBM_OK;
+}
+
 // TMA tiles: every problem's 128-column strips cut into row ranges of about
 // `rows` rows; schedule 1 puts the largest problems first.
 static lbm_status batch_build_tma_tiles(lbm_stefan_batch* b, int rows, int schedule)
@@ -1087,10 +1129,13 @@ static lbm_status batch_build_schedule(lbm_stefan_batch* b, int tile_h, int sche
     CUDA_TRY(lbm::launch_wall_constants(b->dprobs, b->count, nullptr));
     CUDA_TRY(cudaDeviceSynchronize());
     b->nslots = total;
-    b->tile_h = tile_h;
+    b->tile_h = b->use_flat ? 8 : tile_h;
     b->schedule = schedule;
     b->graph.reset();
-    if (b->use_tma) {
+    if (b->use_flat) {
+        lbm_status s = batch_build_flat_tables(b, schedule);
+        if (s != LBM_OK) return s;
+    } else if (b->use_tma) {
         lbm_status s = batch_build_tma_tiles(b, tile_h, schedule);
         if (s != LBM_OK) return s;
     }
@@ -1116,8 +1161,16 @@ static cudaError_t batch_launch_one(lbm_stefan_batch* b, int parity)
     a.ticket = b->dticket;
     a.jobs = b->djobs;
     a.job_count = b->djob_count;
-    cudaError_t e = b->use_tma ? lbm::launch_d2q9_tma(a, b->tma, b->stream)
-                               : lbm::launch_d2q9_step(b->precision, a, b->grid, b->stream);
+    cudaError_t e;
+    if (b->use_flat) {
+        a.ftiles = b->dftiles;
+        a.wrows = b->dwrows;
+        a.nwrows = b->nwrows;
+        e = lbm::launch_d2q9_flat(a, b->nftiles, b->nwrows, 0, b->stream);
+    } else {
+        e = b->use_tma ? lbm::launch_d2q9_tma(a, b->tma, b->stream)
+                       : lbm::launch_d2q9_step(b->precision, a, b->grid, b->stream);
+    }
     if (e != cudaSuccess) return e;
     return lbm::launch_newton_jobs(b->precision, 9,
                                    job_args(b->dprobs, b->count, parity, nullptr, b->dstats, b->dticket, b->djobs,
@@ -1191,7 +1244,8 @@ extern "C" lbm_status lbm_stefan_batch_create(int count, const lbm_stefan_proble
         b->hp[k].state[1] = base + sz;
         base += 2 * sz;
     }
-    if (LBM_USE_TMA && precision == LBM_FP32) b->use_tma = batch_setup_tma(b);
+    if (precision == LBM_FP32) b->use_flat = LBM_FLAT != 0;
+    if (!b->use_flat && LBM_USE_TMA && precision == LBM_FP32) b->use_tma = batch_setup_tma(b);
     cudaGetLastError();
     lbm_status s = batch_build_schedule(b, 16, 1);
     if (s != LBM_OK) {
@@ -1340,7 +1394,8 @@ extern "C" lbm_status lbm_stefan_batch_autotune(lbm_stefan_batch* b, int trial_s
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     lbm_status st = LBM_OK;
-    for (int ci = 0; ci < 4; ++ci) {
+    // the flat FP32 kernels have fixed 8-row tiles: only the order is tuned
+    for (int ci = 0; ci < (b->use_flat ? 1 : 4); ++ci) {
         const int hs = cands_h[ci];
         for (int sc : cands_s) {
             st = batch_build_schedule(b, hs, sc);
@@ -1393,6 +1448,8 @@ extern "C" void lbm_stefan_batch_destroy(lbm_stefan_batch* b)
     cudaFree(b->djob_count);
     cudaFree(b->dmaps);
     cudaFree(b->dtiles);
+    cudaFree(b->dftiles);
+    cudaFree(b->dwrows);
     delete b;
 }
 
