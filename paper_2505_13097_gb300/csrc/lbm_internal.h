@@ -127,6 +127,7 @@ struct StepArgs {
     const int4* ftiles = nullptr;
     const int2* wrows = nullptr;
     int nwrows = 0;
+    const int2* crows = nullptr;   // (problem, first row) per 32-row block of W / E groups
 };
 
 // TMA descriptors of the single-problem FP32 D2Q9 step: state[0], state[1]
@@ -194,10 +195,10 @@ int d2q9_blocks_per_sm(int precision);   // resident step blocks per SM (persist
 cudaError_t launch_d2q9_tma(const StepArgs& a, const TmaMaps& m, cudaStream_t s);
 // single problem, FP32: the interior rows and the rows that touch a wall (two
 // launches; with side, fork and join the second runs on `side`, joined back to s)
-// FP32 D2Q9 flat step: the wall-row kernel (nwrows rows) and the flat kernel
-// (nftiles blocks), both appending Newton nodes to a.jobs; the job kernel is
-// the caller's.
-cudaError_t launch_d2q9_flat(const StepArgs& a, int nftiles, int nwrows, int method, cudaStream_t s);
+// FP32 D2Q9 flat step: the wall kernel (nwrows S / N rows, ncblocks blocks of
+// W / E groups) and the flat kernel (nftiles blocks), both appending Newton
+// nodes to a.jobs; the job kernel is the caller's.
+cudaError_t launch_d2q9_flat(const StepArgs& a, int nftiles, int nwrows, int ncblocks, int method, cudaStream_t s);
 int d2q9_tma_blocks_per_sm();
 // q = 9 or 5; grid 0: two blocks per SM
 cudaError_t launch_newton_jobs(int precision, int q, const JobArgs& a, cudaStream_t s, int grid = 0);

@@ -142,6 +142,8 @@ struct lbm_stefan_batch {
     int nftiles = 0;
     int2* dwrows = nullptr;            // (problem, 2 strip + S/N) per wall row
     int nwrows = 0;
+    int2* dcrows = nullptr;            // (problem, first row) per 32-row block of W / E groups
+    int ncblocks = 0;
     GraphCache graph;
 };
 
@@ -263,13 +265,15 @@ static lbm::JobArgs job_args(const Problem* probs, int nprob, int parity, double
     return j;
 }
 
-// FP32 D2Q9 single-problem step: the S and N wall rows, rows 1 .. ny-2 of
-// every 128-column strip, then the Newton job kernel.
+// FP32 D2Q9 single-problem step: the nodes on or next to a wall (the wall
+// kernel), rows 1 .. ny-2 of every 128-column strip (the flat kernel), then
+// the Newton job kernel.
 static cudaError_t launch_flat(lbm_stefan* h, const StepArgs& a, bool jobs = true)
 {
     const int nsegs = h->hp.pitch / lbm::kTmaW;
     const int nftiles = h->hp.ny > 2 ? nsegs * ((h->hp.ny + 7) / 8) : 0;
-    cudaError_t e = lbm::launch_d2q9_flat(a, nftiles, 2 * nsegs, h->hp.method, h->stream);
+    const int ncblocks = h->hp.ny > 2 ? (h->hp.ny - 2 + 31) / 32 : 0;
+    cudaError_t e = lbm::launch_d2q9_flat(a, nftiles, 2 * nsegs, ncblocks, h->hp.method, h->stream);
     if (e != cudaSuccess || !jobs) return e;
     return lbm::launch_newton_jobs(1, 9, job_args(h->dprob, 1, a.parity, a.rec, h->dstats, h->dticket, h->djobs,
                                                   h->djob_count),
@@ -1037,13 +1041,15 @@ static lbm_status batch_build_flat_tables(lbm_stefan_batch* b, int schedule)
             return (long long)b->hp[x].nx * b->hp[x].ny > (long long)b->hp[y].nx * b->hp[y].ny;
         });
     std::vector<int4> tiles;
-    std::vector<int2> rows;
+    std::vector<int2> rows, crows;
     for (int k : order) {
         const Problem& pb = b->hp[k];
         const int nsegs = pb.pitch / lbm::kTmaW;
-        if (pb.ny > 2)
+        if (pb.ny > 2) {
             for (int y0 = 0; y0 < pb.ny - 1; y0 += 8)
                 for (int seg = 0; seg < nsegs; ++seg) tiles.push_back(make_int4(k, seg, y0, 0));
+            for (int y0 = 1; y0 < pb.ny - 1; y0 += 32) crows.push_back(make_int2(k, y0));
+        }
         for (int seg = 0; seg < nsegs; ++seg) {
             rows.push_back(make_int2(k, 2 * seg));
             rows.push_back(make_int2(k, 2 * seg + 1));
@@ -1051,14 +1057,19 @@ static lbm_status batch_build_flat_tables(lbm_stefan_batch* b, int schedule)
     }
     cudaFree(b->dftiles);
     cudaFree(b->dwrows);
+    cudaFree(b->dcrows);
     b->dftiles = nullptr;
     b->dwrows = nullptr;
+    b->dcrows = nullptr;
     CUDA_TRY(cudaMalloc(&b->dftiles, sizeof(int4) * std::max<size_t>(1, tiles.size())));
     CUDA_TRY(cudaMemcpy(b->dftiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMalloc(&b->dwrows, sizeof(int2) * rows.size()));
     CUDA_TRY(cudaMemcpy(b->dwrows, rows.data(), sizeof(int2) * rows.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMalloc(&b->dcrows, sizeof(int2) * std::max<size_t>(1, crows.size())));
+    CUDA_TRY(cudaMemcpy(b->dcrows, crows.data(), sizeof(int2) * crows.size(), cudaMemcpyHostToDevice));
     b->nftiles = (int)tiles.size();
     b->nwrows = (int)rows.size();
+    b->ncblocks = (int)crows.size();
     return LBM_OK;
 }
 
@@ -1166,7 +1177,8 @@ static cudaError_t batch_launch_one(lbm_stefan_batch* b, int parity)
         a.ftiles = b->dftiles;
         a.wrows = b->dwrows;
         a.nwrows = b->nwrows;
-        e = lbm::launch_d2q9_flat(a, b->nftiles, b->nwrows, 0, b->stream);
+        a.crows = b->dcrows;
+        e = lbm::launch_d2q9_flat(a, b->nftiles, b->nwrows, b->ncblocks, 0, b->stream);
     } else {
         e = b->use_tma ? lbm::launch_d2q9_tma(a, b->tma, b->stream)
                        : lbm::launch_d2q9_step(b->precision, a, b->grid, b->stream);
@@ -1450,6 +1462,7 @@ extern "C" void lbm_stefan_batch_destroy(lbm_stefan_batch* b)
     cudaFree(b->dtiles);
     cudaFree(b->dftiles);
     cudaFree(b->dwrows);
+    cudaFree(b->dcrows);
     delete b;
 }
 

@@ -274,9 +274,9 @@ struct ColdSums {
 // leaves out: a node on the W or E wall, or any node of a four-column group
 // that holds one (or reaches past nx).  The arithmetic of row_update /
 // row_update_eebm for one FP32 node, with scalar loads and stores; a Newton
-// node takes a job slot of its own.  Kept out of line, so that the vector
-// path's registers do not pay for the closures.
-static __device__ __noinline__ void flat_cold_node(const Problem& pb, int pi, const float* __restrict__ src,
+// node takes a job slot of its own.  Run by the wall kernel, one node per
+// thread, so that the flat kernel carries no closure code.
+__device__ __forceinline__ void flat_cold_node(const Problem& pb, int pi, const float* __restrict__ src,
                                                    float* __restrict__ dst, double* __restrict__ rec, int x, int y,
                                                    float sh, NewtonJob* jobs, unsigned int* job_count, ColdSums& cs)
 {
@@ -513,19 +513,7 @@ __global__ void __launch_bounds__(256, LBM_FLAT_MINB) d2q9_flat_kernel(const Ste
                 }
             }
         }
-        if (cold) {
-            // the group's nodes inside the lattice, one at a time
-            for (int k = 0; k < 4 && x0 + k < nx; ++k) {
-                ColdSums cs;
-                flat_cold_node(pb, pi, src, dst, a.rec, x0 + k, y, sh, a.jobs, a.job_count, cs);
-                acc.add_ff(cs.e);
-                ff_add(ts.flux_f, cs.flux.hi);
-                ts.flux_f.lo += cs.flux.lo;
-                ts.liquid += cs.liquid;
-                ts.shifted += cs.shifted;
-                if (cs.dir >= 0) ts.dir_count[cs.dir] += 1;
-            }
-        }
+        // cold lanes: their nodes are the wall kernel's
     }
     const WarpSums w = warp_tile_sums<float>(acc, ts);
     if (lane == 0) wsum[warp] = w;
@@ -537,52 +525,94 @@ __global__ void __launch_bounds__(256, LBM_FLAT_MINB) d2q9_flat_kernel(const Ste
     }
 }
 
-// Rows 0 and ny-1 (the S and N walls) of every 128-column strip, FP32: one
-// row per warp, the full row update (closures of Sec. 4.2, Newton hand-off,
-// EEBM).  Row r: single problem, strip r / 2, row 0 or ny-1 by r % 2;
-// batches: the table a.wrows, entry (problem, 2 strip + (0: row 0, 1: row ny-1)).
-// Each warp adds its sums to its row's problem after the row.
+// The nodes the flat kernel leaves out, FP32.
+//  * Blocks [0, nrb): rows 0 and ny-1 (the S and N walls) of every
+//    128-column strip, one row per warp, the full row update (closures of
+//    Sec. 4.2, Newton hand-off, EEBM).  Row r: single problem, strip r / 2,
+//    row 0 or ny-1 by r % 2; batches: the table a.wrows, entry (problem,
+//    2 strip + (0: row 0, 1: row ny-1)).
+//  * Blocks [nrb, nrb + ncb): in rows 1 .. ny-2, the nodes of the four-column
+//    groups that hold column 0 or nx-1 or reach past nx, one node per thread
+//    (flat_cold_node): 32 rows per block, eight slots per row (x = 0 .. 3 and
+//    x = xe .. xe + 3, xe the group of column nx-1 when it is not the first).
+//    Single problem: block nrb + b takes rows 1 + 32 b ...; batches: the table
+//    a.crows, entry (problem, first row).
+// Each warp adds its sums to its problem after each row (part 1) or at the
+// end (part 2).
 template <bool REC>
-__global__ void __launch_bounds__(256) d2q9_wall_rows_kernel(const StepArgs a)
+__global__ void __launch_bounds__(256) d2q9_wall_kernel(const StepArgs a, int nrb)
 {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int nrows = a.wrows ? a.nwrows : 2 * (a.probs[0].pitch / 128);
-    for (int r = blockIdx.x * 8 + warp; r < nrows; r += gridDim.x * 8) {
-        int pi = 0, code = r;
-        if (a.wrows) {
-            const int2 e = a.wrows[r];
-            pi = e.x;
-            code = e.y;
+    if ((int)blockIdx.x < nrb) {
+        const int nrows = a.wrows ? a.nwrows : 2 * (a.probs[0].pitch / 128);
+        for (int r = blockIdx.x * 8 + warp; r < nrows; r += nrb * 8) {
+            int pi = 0, code = r;
+            if (a.wrows) {
+                const int2 e = a.wrows[r];
+                pi = e.x;
+                code = e.y;
+            }
+            const Problem& pb = a.probs[pi];
+            const int nx = pb.nx, ny = pb.ny;
+            const long long pl = pb.plane, pitch = pb.pitch;
+            const int seg = code >> 1;
+            const int y = (code & 1) ? ny - 1 : 0;
+            const float* __restrict__ src = static_cast<const float*>(pb.state[a.parity]);
+            float* __restrict__ dst = static_cast<float*>(pb.state[a.parity ^ 1]);
+            const float omc = (float)(1.0 - pb.omega);
+            const float om_f = (float)pb.omega;
+            const double omc_d = 1.0 - pb.omega;
+            const float wP[3] = {d2_wf(0), d2_wf(1), d2_wf(5)};
+            const float thr_f = (float)pb.sat;
+            const float sh = state_shift(pb, a.parity);   // stored values are Omega_i - w_i sh
+            Acc<float> acc;
+            TileSums ts;
+            GlobalJobSink sink{a.jobs, a.job_count};
+            const int x0 = seg * 128 + 4 * lane;
+            float u[9][4], qf[9][4];
+            flat_load_row(src + (y + 1) * pitch + x0, pitch, pl, u, qf);
+            const GlobalRowOut<float, 4> out{dst + (y + 1) * pitch + x0, pl};
+            if (pb.method == 1)
+                row_update_eebm<float, 4, REC, true>(pb, y, x0, qf, u[0], u[1], u[2], u[3], u[4], u[5], u[6], u[7],
+                                                     u[8], out, a.rec, acc, ts, omc, wP, nx, ny, sh);
+            else
+                row_update<float, 4, REC, true>(pb, y, x0, lane, qf, u[0], u[1], u[2], u[3], u[4], u[5], u[6], u[7],
+                                                u[8], out, a.rec, acc, ts, pi, sink, omc, om_f, omc_d, wP, thr_f, nx,
+                                                ny, sh);
+            flush_tile_sums<float>(acc, ts, &a.stats[pb.stats], lane);
         }
-        const Problem& pb = a.probs[pi];
-        const int nx = pb.nx, ny = pb.ny;
-        const long long pl = pb.plane, pitch = pb.pitch;
-        const int seg = code >> 1;
-        const int y = (code & 1) ? ny - 1 : 0;
-        const float* __restrict__ src = static_cast<const float*>(pb.state[a.parity]);
-        float* __restrict__ dst = static_cast<float*>(pb.state[a.parity ^ 1]);
-        const float omc = (float)(1.0 - pb.omega);
-        const float om_f = (float)pb.omega;
-        const double omc_d = 1.0 - pb.omega;
-        const float wP[3] = {d2_wf(0), d2_wf(1), d2_wf(5)};
-        const float thr_f = (float)pb.sat;
-        const float sh = state_shift(pb, a.parity);   // stored values are Omega_i - w_i sh
-        Acc<float> acc;
-        TileSums ts;
-        GlobalJobSink sink{a.jobs, a.job_count};
-        const int x0 = seg * 128 + 4 * lane;
-        float u[9][4], qf[9][4];
-        flat_load_row(src + (y + 1) * pitch + x0, pitch, pl, u, qf);
-        const GlobalRowOut<float, 4> out{dst + (y + 1) * pitch + x0, pl};
-        if (pb.method == 1)
-            row_update_eebm<float, 4, REC, true>(pb, y, x0, qf, u[0], u[1], u[2], u[3], u[4], u[5], u[6], u[7], u[8],
-                                                 out, a.rec, acc, ts, omc, wP, nx, ny, sh);
-        else
-            row_update<float, 4, REC, true>(pb, y, x0, lane, qf, u[0], u[1], u[2], u[3], u[4], u[5], u[6], u[7], u[8],
-                                            out, a.rec, acc, ts, pi, sink, omc, om_f, omc_d, wP, thr_f, nx, ny, sh);
-        flush_tile_sums<float>(acc, ts, &a.stats[pb.stats], lane);
+        return;
     }
+    // part 2: the W and E groups of rows 1 .. ny-2
+    const int b = blockIdx.x - nrb;
+    int pi = 0, y0 = 1 + 32 * b;
+    if (a.crows) {
+        const int2 e = a.crows[b];
+        pi = e.x;
+        y0 = e.y;
+    }
+    const Problem& pb = a.probs[pi];
+    const int nx = pb.nx, ny = pb.ny;
+    const int y = y0 + (threadIdx.x >> 3);
+    const int slot = threadIdx.x & 7;
+    const int xe = max(4, ((nx - 1) >> 2) << 2);
+    const int x = slot < 4 ? slot : xe + slot - 4;
+    Acc<float> acc;
+    TileSums ts;
+    if (y >= 1 && y < ny - 1 && x < nx && (slot >= 4 || x < 4)) {
+        ColdSums cs;
+        flat_cold_node(pb, pi, static_cast<const float*>(pb.state[a.parity]), static_cast<float*>(pb.state[a.parity ^ 1]),
+                       a.rec, x, y, state_shift(pb, a.parity), a.jobs, a.job_count, cs);
+        acc.add_ff(cs.e);
+        ff_add(ts.flux_f, cs.flux.hi);
+        ts.flux_f.lo += cs.flux.lo;
+        ts.liquid += cs.liquid;
+        ts.shifted += cs.shifted;
+        if (cs.dir >= 0) ts.dir_count[cs.dir] += 1;
+    }
+    flush_tile_sums<float>(acc, ts, &a.stats[pb.stats], lane);
+    (void)warp;
 }
 
 // ---------------------------------------------------------------- TMA row pipeline
@@ -830,17 +860,17 @@ cudaError_t launch_d2q9_tma(const StepArgs& a, const TmaMaps& m, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_d2q9_flat(const StepArgs& a, int nftiles, int nwrows, int method, cudaStream_t s)
+cudaError_t launch_d2q9_flat(const StepArgs& a, int nftiles, int nwrows, int ncblocks, int method, cudaStream_t s)
 {
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    // the S and N wall rows (few), then rows 1 .. ny-2 of every strip
-    if (nwrows > 0) {
-        const int g = std::min((nwrows + 7) / 8, sms * 4);
-        if (a.rec) d2q9_wall_rows_kernel<true><<<g, 256, 0, s>>>(a);
-        else d2q9_wall_rows_kernel<false><<<g, 256, 0, s>>>(a);
+    // the nodes on or next to a wall (few), then rows 1 .. ny-2 of every strip
+    const int nrb = std::min((nwrows + 7) / 8, sms * 4);
+    if (nrb + ncblocks > 0) {
+        if (a.rec) d2q9_wall_kernel<true><<<nrb + ncblocks, 256, 0, s>>>(a, nrb);
+        else d2q9_wall_kernel<false><<<nrb + ncblocks, 256, 0, s>>>(a, nrb);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
