@@ -8,9 +8,14 @@
  * Algorithm 3 of the paper once per step: collision (Eq. 12), pull
  * streaming, the boundary closures of Sec. 4.2 on q, the zeroth moment, the
  * local Newton solve of Eq. (14), the source of Eq. (13), and the next
- * collision.  Kernel launches per step: D2Q9 with FP32 populations, three
- * (the S and N wall rows, rows 1 .. ny-2, then the kernel that solves the
- * list of nodes that need the Newton iteration and publishes the step);
+ * collision.  Kernel launches per step: D2Q9 with FP32 populations, three on
+ * the legacy default stream (the nodes on or next to a wall, rows 1 .. ny-2
+ * of every 128-column strip, then the kernel that solves the list of nodes
+ * that need the Newton iteration and publishes the step), five on a stream of
+ * the handle's own (rows 1 .. ny-2 of the left and of the right half of the
+ * strips; on a second, higher-priority stream the wall nodes, then the
+ * Newton solves of those and of the left half, beside the right half; then
+ * the right half's solves);
  * D2Q9 in FP64 and D2Q5, two (the stream/collide kernel, which hands the
  * nodes that need the Newton iteration to a list, then the kernel that
  * solves that list); D1Q3, one launch for all the steps of a call.
@@ -165,8 +170,8 @@ lbm_status lbm_stefan_step(lbm_stefan* h, int nsteps);
 /* D2Q9 and D2Q5: advance nsteps >= 1 steps launched one by one (no graph) with a
  * CUDA event before, between and after the kernels of each step, wait for
  * them, and return the mean device time per step of each kernel in ms:
- * ms_kernels[0] the stream/collide kernel (FP32 D2Q9: the wall-row and the
- * flat kernel together), ms_kernels[1] the Newton job kernel.  Same result as
+ * ms_kernels[0] the stream/collide kernel (FP32 D2Q9: every launch of the
+ * step but the last Newton launch), ms_kernels[1] the (last) Newton job kernel.  Same result as
  * lbm_stefan_step; for measuring each kernel against its roofline.
  * Synchronizes. */
 lbm_status lbm_stefan_step_timed(lbm_stefan* h, int nsteps, double* ms_kernels);

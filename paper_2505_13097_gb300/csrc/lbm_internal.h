@@ -128,6 +128,8 @@ struct StepArgs {
     const int2* wrows = nullptr;
     int nwrows = 0;
     const int2* crows = nullptr;   // (problem, first row) per 32-row block of W / E groups
+    // single problem: the flat kernel's strips seg0 .. seg0 + nsegc - 1 (nsegc 0: all)
+    int seg0 = 0, nsegc = 0;
 };
 
 // TMA descriptors of the single-problem FP32 D2Q9 step: state[0], state[1]
@@ -200,8 +202,8 @@ cudaError_t launch_d2q9_tma(const StepArgs& a, const TmaMaps& m, cudaStream_t s)
 // nodes to a.jobs; the job kernel is the caller's.
 cudaError_t launch_d2q9_flat(const StepArgs& a, int nftiles, int nwrows, int ncblocks, int method, cudaStream_t s);
 int d2q9_tma_blocks_per_sm();
-// q = 9 or 5; grid 0: two blocks per SM
-cudaError_t launch_newton_jobs(int precision, int q, const JobArgs& a, cudaStream_t s, int grid = 0);
+// q = 9 or 5; grid 0: two blocks per SM; prio != 0: that scheduling priority
+cudaError_t launch_newton_jobs(int precision, int q, const JobArgs& a, cudaStream_t s, int grid = 0, int prio = 0);
 
 // D2Q5 launchers (step_d2q5.cu): one tile per warp over a.nslots tiles
 cudaError_t launch_d2q5_step(int precision, const StepArgs& a, cudaStream_t s);

@@ -92,6 +92,8 @@ struct lbm_stefan {
     bool use_tma = false;              // FP32 D2Q9: the TMA row-pipeline step kernel
     lbm::TmaMaps tma;
     int withhold_load = -1;            // test hook of the TMA kernel's row loads (-1: off)
+    cudaStream_t side = nullptr;       // split FP32 D2Q9 step: stream of the left half's Newton solves
+    cudaEvent_t ev_fork = nullptr, ev_half = nullptr, ev_join = nullptr;
     GraphCache graph;
     // captured adjoint segments (lbm_stefan_adjoint_segment): recompute + reverse
     // steps for one (length, trajectory, adjoint buffers) combination each
@@ -265,19 +267,92 @@ static lbm::JobArgs job_args(const Problem* probs, int nprob, int parity, double
     return j;
 }
 
+#ifndef LBM_SPLIT
+#define LBM_SPLIT 1   // FP32 D2Q9 on a stream of its own: the left strips' Newton solves beside the right strips
+#endif
+
+// The two job lists of a split FP32 D2Q9 step: list A (the wall kernel's and
+// the left strips' nodes) from djobs, list B (the right strips') after it.
+static size_t split_cap_a(const Problem& hp)
+{
+    const int nsegs = hp.pitch / lbm::kTmaW;
+    return (size_t)(nsegs / 2) * lbm::kTmaW * hp.ny + 2 * (size_t)hp.pitch + 8 * (size_t)hp.ny;
+}
+
+static cudaError_t launch_flat_final_jobs(lbm_stefan* h, const StepArgs& a);
+
 // FP32 D2Q9 single-problem step: the nodes on or next to a wall (the wall
 // kernel), rows 1 .. ny-2 of every 128-column strip (the flat kernel), then
-// the Newton job kernel.
-static cudaError_t launch_flat(lbm_stefan* h, const StepArgs& a, bool jobs = true)
+// the Newton job kernel.  With a side stream the strips are cut into a left
+// and a right half: the Newton solves of the wall kernel's and the left
+// half's nodes run on the side stream (at a higher priority) while the right
+// half streams; the right half's solves follow the join and publish the
+// step.  The interior kernel does no FP64 work and the solves little else,
+// so a front band in the left half costs FP64 time beside HBM time.
+// final_jobs = false leaves out the last job launch (step_timed times it).
+static cudaError_t launch_flat(lbm_stefan* h, const StepArgs& a, bool final_jobs = true)
 {
     const int nsegs = h->hp.pitch / lbm::kTmaW;
-    const int nftiles = h->hp.ny > 2 ? nsegs * ((h->hp.ny + 7) / 8) : 0;
+    const int nbands = h->hp.ny > 2 ? (h->hp.ny + 7) / 8 : 0;
     const int ncblocks = h->hp.ny > 2 ? (h->hp.ny - 2 + 31) / 32 : 0;
-    cudaError_t e = lbm::launch_d2q9_flat(a, nftiles, 2 * nsegs, ncblocks, h->hp.method, h->stream);
-    if (e != cudaSuccess || !jobs) return e;
-    return lbm::launch_newton_jobs(1, 9, job_args(h->dprob, 1, a.parity, a.rec, h->dstats, h->dticket, h->djobs,
-                                                  h->djob_count),
-                                   h->stream);
+    const int half = nsegs / 2;
+    cudaError_t e;
+    if (!(h->side && half >= 1 && nbands > 0)) {
+        e = lbm::launch_d2q9_flat(a, nsegs * nbands, 2 * nsegs, ncblocks, h->hp.method, h->stream);
+        if (e != cudaSuccess || !final_jobs) return e;
+        return lbm::launch_newton_jobs(1, 9, job_args(h->dprob, 1, a.parity, a.rec, h->dstats, h->dticket, h->djobs,
+                                                      h->djob_count),
+                                       h->stream);
+    }
+    // side: the wall kernel (beside the left half), then the left half's and
+    // its own Newton solves; main: the left half, the right half, the join,
+    // the right half's solves (which publish the step)
+    int least = 0, prio = 0, dev = 0, sms = 0;
+    e = cudaDeviceGetStreamPriorityRange(&least, &prio);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_fork, h->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->side, h->ev_fork, 0);
+    if (e == cudaSuccess) e = lbm::launch_d2q9_flat(a, 0, 2 * nsegs, ncblocks, h->hp.method, h->side);   // list A
+    StepArgs aa = a;   // list A: djobs, counter 0
+    aa.seg0 = 0;
+    aa.nsegc = half;
+    if (e == cudaSuccess) e = lbm::launch_d2q9_flat(aa, half * nbands, 0, 0, h->hp.method, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_half, h->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->side, h->ev_half, 0);
+    if (e != cudaSuccess) return e;
+    lbm::JobArgs ja = job_args(h->dprob, 1, a.parity, a.rec, h->dstats, h->dticket, h->djobs, h->djob_count);
+    ja.publish = 0;
+    e = lbm::launch_newton_jobs(1, 9, ja, h->side, sms, prio);   // one block per SM beside the streaming blocks
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_join, h->side);
+    if (e != cudaSuccess) return e;
+    StepArgs ab = a;   // list B: after list A, counter 1
+    ab.jobs = h->djobs + split_cap_a(h->hp);
+    ab.job_count = h->djob_count + 1;
+    ab.seg0 = half;
+    ab.nsegc = nsegs - half;
+    e = lbm::launch_d2q9_flat(ab, (nsegs - half) * nbands, 0, 0, h->hp.method, h->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_join, 0);
+    if (e != cudaSuccess || !final_jobs) return e;
+    return launch_flat_final_jobs(h, a);
+}
+
+// The last job launch of a flat step (after launch_flat(h, a, false)).
+static cudaError_t launch_flat_final_jobs(lbm_stefan* h, const StepArgs& a)
+{
+    const int nsegs = h->hp.pitch / lbm::kTmaW;
+    const bool split = h->side && nsegs / 2 >= 1 && h->hp.ny > 2;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // split: the right half's list, often short or empty: a smaller grid (its
+    // last-block ticket is one same-address atomic per block)
+    return lbm::launch_newton_jobs(1, 9,
+                                   split ? job_args(h->dprob, 1, a.parity, a.rec, h->dstats, h->dticket + 1,
+                                                    h->djobs + split_cap_a(h->hp), h->djob_count + 1)
+                                         : job_args(h->dprob, 1, a.parity, a.rec, h->dstats, h->dticket, h->djobs,
+                                                    h->djob_count),
+                                   h->stream, split ? sms : 0);
 }
 
 // One step.  D2Q9 and D2Q5: the stream/collide kernel(s), which defer the
@@ -434,19 +509,34 @@ extern "C" lbm_status lbm_stefan_create(const lbm_stefan_params* p, void* cuda_s
     if (e == cudaSuccess) e = cudaMalloc(&h->dprob, sizeof(Problem));
     if (e == cudaSuccess) e = cudaMalloc(&h->dstats, sizeof(DevStats));
     if (e == cudaSuccess) e = cudaMemset(h->dstats, 0, sizeof(DevStats));
-    if (e == cudaSuccess) e = cudaMalloc(&h->dticket, sizeof(unsigned int));
-    if (e == cudaSuccess) e = cudaMemset(h->dticket, 0, sizeof(unsigned int));
+    // [0]: the step's job list and job kernel; [1]: the split step's second list
+    if (e == cudaSuccess) e = cudaMalloc(&h->dticket, 2 * sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(h->dticket, 0, 2 * sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMalloc(&h->dscratch, sizeof(double) * 3 * (size_t)p->nx * p->ny);
-    if (e == cudaSuccess) e = cudaMalloc(&h->djob_count, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMalloc(&h->djob_count, 2 * sizeof(unsigned int));
     if (e == cudaSuccess && q == 9) h->adj_tile_h = adjoint_tile_h(h->hp);
-    if (e == cudaSuccess) e = cudaMemset(h->djob_count, 0, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(h->djob_count, 0, 2 * sizeof(unsigned int));
     h->hp.state[0] = bufs[0];
     h->hp.state[1] = bufs[1];
     h->hp.stats = 0;
     if (e == cudaSuccess && tma) h->use_tma = setup_tma(h);
+    // the split FP32 step (non-default streams only: the legacy stream would
+    // serialize with its side stream), side stream of the highest priority
+    if (e == cudaSuccess && h->use_tma && LBM_FLAT && LBM_SPLIT && h->stream != nullptr) {
+        int least = 0, greatest = 0;
+        e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, greatest);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_half, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+    }
     // the list of deferred Newton nodes (D2Q9, D2Q5): one job per node at most
-    if (e == cudaSuccess && q != 3)
-        e = cudaMalloc(&h->djobs, sizeof(lbm::NewtonJob) * (size_t)p->nx * p->ny);
+    // (split FP32 step: two lists, the first with room for the wall kernel's
+    // and the left half's nodes)
+    const size_t njobs = h->side ? split_cap_a(h->hp) + (size_t)(h->hp.pitch / lbm::kTmaW - h->hp.pitch / lbm::kTmaW / 2) *
+                                                            lbm::kTmaW * p->ny
+                                 : (size_t)p->nx * p->ny;
+    if (e == cudaSuccess && q != 3) e = cudaMalloc(&h->djobs, sizeof(lbm::NewtonJob) * njobs);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         lbm_stefan_destroy(h);
@@ -565,7 +655,8 @@ static lbm_status capture_graph(lbm_stefan* h)
         if (g) cudaGraphDestroy(g);
         return fail(LBM_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
     }
-    e = cudaGraphInstantiate(&h->graph.exec, g, 0);
+    // per-node priorities: the split step's side Newton launch keeps its higher priority
+    e = cudaGraphInstantiate(&h->graph.exec, g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
     h->graph.steps = kGraphSteps;
@@ -656,10 +747,11 @@ extern "C" lbm_status lbm_stefan_step_timed(lbm_stefan* h, int nsteps, double* m
         }
         if (e == cudaSuccess) e = cudaEventRecord(ev[2 * k + 1], h->stream);
         if (e == cudaSuccess)
-            e = lbm::launch_newton_jobs(h->precision, h->hp.q,
-                                        job_args(h->dprob, 1, h->parity, nullptr, h->dstats, h->dticket, h->djobs,
-                                                 h->djob_count),
-                                        h->stream);
+            e = flat ? launch_flat_final_jobs(h, a)
+                     : lbm::launch_newton_jobs(h->precision, h->hp.q,
+                                               job_args(h->dprob, 1, h->parity, nullptr, h->dstats, h->dticket,
+                                                        h->djobs, h->djob_count),
+                                               h->stream);
         if (e == cudaSuccess) e = cudaEventRecord(ev[2 * k + 2], h->stream);
         h->parity ^= 1;
     }
@@ -956,7 +1048,7 @@ extern "C" lbm_status lbm_stefan_adjoint_segment(lbm_stefan* h, const void* chec
         CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = segment_launches(h, nsteps, theta_traj, adj, adj_other, 0);
         cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
-        if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+        if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&exec, g, cudaGraphInstantiateFlagUseNodePriority);
         if (g) cudaGraphDestroy(g);
         if (e != cudaSuccess || e2 != cudaSuccess || !exec)
             return fail(LBM_ERR_CUDA, "segment capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
@@ -1001,6 +1093,10 @@ extern "C" void lbm_stefan_destroy(lbm_stefan* h)
     cudaFree(h->dscratch);
     cudaFree(h->djobs);
     cudaFree(h->djob_count);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_half) cudaEventDestroy(h->ev_half);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->side) cudaStreamDestroy(h->side);
     cudaFree(h->dilf);
     cudaFree(h->dilf_scratch);
     delete h;

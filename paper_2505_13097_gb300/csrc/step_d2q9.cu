@@ -377,9 +377,9 @@ __global__ void __launch_bounds__(256, LBM_FLAT_MINB) d2q9_flat_kernel(const Ste
         seg = t.y;
         y = t.z + warp;
     } else {
-        const int nsegs = a.probs[0].pitch / 128;
+        const int nsegs = a.nsegc > 0 ? a.nsegc : a.probs[0].pitch / 128;
         pi = 0;
-        seg = blockIdx.x % nsegs;
+        seg = a.seg0 + blockIdx.x % nsegs;
         y = (blockIdx.x / nsegs) * 8 + warp;
     }
     const Problem& pb = a.probs[pi];
@@ -436,7 +436,7 @@ __global__ void __launch_bounds__(256, LBM_FLAT_MINB) d2q9_flat_kernel(const Ste
             // interior IREBM nodes: the arithmetic of row_update's interior branch
             const float om_f = (float)pb.omega;
             const float thr_f = (float)pb.sat;
-            float c[4];
+            float c[4], esum = 0.f;   // the lane's energy terms, less the shift
             bool newton[4];
             bool any_newton = false;
 #pragma unroll
@@ -454,11 +454,12 @@ __global__ void __launch_bounds__(256, LBM_FLAT_MINB) d2q9_flat_kernel(const Ste
                 any_newton |= newton[k];
                 c[k] = newton[k] ? 0.f : om_f * mf;   // c - omega sh = omega (m0 - sh)
                 if (!newton[k] && !cold) {
-                    acc.add_f(mf);
+                    esum += mf;
                     ts.liquid += sat_liq ? 1 : 0;
                     ts.shifted += 1;
                 }
             }
+            acc.add_f(esum);   // one float-float addition per lane and row
             float wc[3][4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -898,16 +899,26 @@ int d2q9_tma_blocks_per_sm()
 }
 
 template <int Q>
-static cudaError_t launch_jobs_q(int precision, const JobArgs& a, int grid, cudaStream_t s)
+static cudaError_t launch_jobs_q(int precision, const JobArgs& a, int grid, cudaStream_t s, int prio)
 {
     void (*k)(JobArgs) = precision == 1
                              ? (a.rec ? newton_jobs_kernel<float, true, Q> : newton_jobs_kernel<float, false, Q>)
                              : (a.rec ? newton_jobs_kernel<double, true, Q> : newton_jobs_kernel<double, false, Q>);
-    k<<<grid, kJobThreads, 0, s>>>(a);
-    return cudaGetLastError();
+    // an explicit scheduling priority is a launch attribute, which a graph
+    // captured from the stream keeps per kernel node
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)kJobThreads);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributePriority;
+    at[0].val.priority = prio;
+    cfg.attrs = at;
+    cfg.numAttrs = prio != 0 ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, a);
 }
 
-cudaError_t launch_newton_jobs(int precision, int q, const JobArgs& a, cudaStream_t s, int grid)
+cudaError_t launch_newton_jobs(int precision, int q, const JobArgs& a, cudaStream_t s, int grid, int prio)
 {
     if (grid <= 0) {
         int dev = 0, sms = 0;
@@ -915,8 +926,8 @@ cudaError_t launch_newton_jobs(int precision, int q, const JobArgs& a, cudaStrea
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         grid = sms * 2;
     }
-    if (q == 9) return launch_jobs_q<9>(precision, a, grid, s);
-    if (q == 5) return launch_jobs_q<5>(precision, a, grid, s);
+    if (q == 9) return launch_jobs_q<9>(precision, a, grid, s, prio);
+    if (q == 5) return launch_jobs_q<5>(precision, a, grid, s, prio);
     return cudaErrorInvalidValue;
 }
 
