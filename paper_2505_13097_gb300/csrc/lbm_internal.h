@@ -141,11 +141,6 @@ struct TmaMaps {
     CUtensorMap load[2];                 // single problem
     int nsegs;                           // pitch / kTmaW column strips (single problem)
     int nparts;                          // row ranges per strip; grid = nsegs * nparts
-    // batches: block b takes tile tiles[b] = (problem, strip, first row, end row)
-    // with the descriptors gmaps[2 * problem + parity] (device memory)
-    const int4* tiles;
-    const CUtensorMap* gmaps;
-    int ntiles;
     long long wait_ns = 2000000000LL;    // bound of every wait on a row load, in nanoseconds
     int withhold_load = -1;              // test hook: >= 0 skips that row load of block 0 (0: the row
                                          // above its first row); -1: off

@@ -17,9 +17,6 @@
 #ifndef LBM_PLANE_PAD
 #define LBM_PLANE_PAD 0
 #endif
-#ifndef LBM_FLAT
-#define LBM_FLAT 1   // single FP32 D2Q9 problem: the flat step kernel (else the TMA row pipeline)
-#endif
 
 using lbm::DevStats;
 using lbm::Problem;
@@ -89,7 +86,8 @@ struct lbm_stefan {
     int adj_tile_h = lbm::kAdjTileH;   // rows per warp tile of the D2Q9 adjoint
     unsigned int* dilf = nullptr;      // 2D ILFBM: inner-loop flags (done, iteration, changed x 3)
     double* dilf_scratch = nullptr;    // 2D ILFBM: S0, two l iterates, two l differences (5 nx*ny)
-    bool use_tma = false;              // FP32 D2Q9: the TMA row-pipeline step kernel
+    bool flat = false;                 // FP32 D2Q9: the flat and wall kernels
+    bool use_tma = false;              // FP32 D2Q9: the TMA row-pipeline kernel (for the wait test hook)
     lbm::TmaMaps tma;
     int withhold_load = -1;            // test hook of the TMA kernel's row loads (-1: off)
     cudaStream_t side = nullptr;       // split FP32 D2Q9 step: stream of the left half's Newton solves
@@ -135,10 +133,6 @@ struct lbm_stefan_batch {
     size_t scratch_elems = 0;
     lbm::NewtonJob* djobs = nullptr;
     unsigned int* djob_count = nullptr;
-    bool use_tma = false;              // FP32: the TMA row-pipeline kernel over a tile table
-    lbm::TmaMaps tma;
-    CUtensorMap* dmaps = nullptr;      // 2 descriptors per problem
-    int4* dtiles = nullptr;
     bool use_flat = false;             // FP32: the flat and wall-row kernels over tables
     int4* dftiles = nullptr;           // (problem, strip, first row) per flat block
     int nftiles = 0;
@@ -373,7 +367,7 @@ static cudaError_t launch_one(lbm_stefan* h, int parity, double* rec)
     }
     if (h->p.lattice == LBM_D2Q9) {
         cudaError_t e;
-        if (h->use_tma && LBM_FLAT && h->withhold_load < 0) return launch_flat(h, a);   // with its job kernel
+        if (h->flat && h->withhold_load < 0) return launch_flat(h, a);   // with its job kernels
         if (h->use_tma) {
             e = lbm::launch_d2q9_tma(a, h->tma, h->stream);
         } else {
@@ -519,10 +513,11 @@ extern "C" lbm_status lbm_stefan_create(const lbm_stefan_params* p, void* cuda_s
     h->hp.state[0] = bufs[0];
     h->hp.state[1] = bufs[1];
     h->hp.stats = 0;
+    h->flat = p->lattice == LBM_D2Q9 && p->precision == LBM_FP32;
     if (e == cudaSuccess && tma) h->use_tma = setup_tma(h);
     // the split FP32 step (non-default streams only: the legacy stream would
     // serialize with its side stream), side stream of the highest priority
-    if (e == cudaSuccess && h->use_tma && LBM_FLAT && LBM_SPLIT && h->stream != nullptr) {
+    if (e == cudaSuccess && h->flat && LBM_SPLIT && h->stream != nullptr) {
         int least = 0, greatest = 0;
         e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
         if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, greatest);
@@ -734,7 +729,7 @@ extern "C" lbm_status lbm_stefan_step_timed(lbm_stefan* h, int nsteps, double* m
     if (e == cudaSuccess) e = cudaEventRecord(ev[0], h->stream);
     for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
         StepArgs a = single_args(h, h->parity, nullptr);
-        const bool flat = h->p.lattice == LBM_D2Q9 && h->use_tma && LBM_FLAT && h->withhold_load < 0;
+        const bool flat = h->flat && h->withhold_load < 0;
         if (h->p.lattice == LBM_D2Q5) {
             e = lbm::launch_d2q5_step(h->precision, a, h->stream);
         } else if (flat) {
@@ -1108,23 +1103,6 @@ extern "C" const char* lbm_stefan_last_error(void) { return g_err; }
 
 // Descriptors of every problem's two state buffers for the TMA kernel; false
 // leaves the batch on the warp-tile kernel.
-static bool batch_setup_tma(lbm_stefan_batch* b)
-{
-    std::vector<CUtensorMap> maps(2 * (size_t)b->count);
-    for (int k = 0; k < b->count; ++k) {
-        const Problem& hp = b->hp[k];
-        if (hp.pitch % lbm::kTmaW != 0) return false;
-        for (int p = 0; p < 2; ++p)
-            if (!encode_state_map(&maps[2 * k + p], hp.state[p], hp, lbm::kTmaW + 2 * lbm::kTmaHalo)) return false;
-    }
-    if (cudaMalloc(&b->dmaps, sizeof(CUtensorMap) * maps.size()) != cudaSuccess ||
-        cudaMemcpy(b->dmaps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return lbm::d2q9_tma_blocks_per_sm() > 0;   // also selects the shared-memory carveout
-}
-
 // Flat-kernel tables: every problem's 128-column strips in 8-row tiles
 // (strips fastest, then bands), and its S and N rows; schedule 1 puts the
 // largest problems first.
@@ -1169,38 +1147,6 @@ static lbm_status batch_build_flat_tables(lbm_stefan_batch* b, int schedule)
     return LBM_OK;
 }
 
-// TMA tiles: every problem's 128-column strips cut into row ranges of about
-// `rows` rows; schedule 1 puts the largest problems first.
-static lbm_status batch_build_tma_tiles(lbm_stefan_batch* b, int rows, int schedule)
-{
-    std::vector<int> order(b->count);
-    for (int k = 0; k < b->count; ++k) order[k] = k;
-    if (schedule == 1)
-        std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-            return (long long)b->hp[x].nx * b->hp[x].ny > (long long)b->hp[y].nx * b->hp[y].ny;
-        });
-    std::vector<int4> tiles;
-    for (int k : order) {
-        const Problem& pb = b->hp[k];
-        const int nsegs = pb.pitch / lbm::kTmaW;
-        const int nparts = std::max(1, (pb.ny + rows - 1) / rows);
-        for (int part = 0; part < nparts; ++part)
-            for (int seg = 0; seg < nsegs; ++seg)
-                tiles.push_back(make_int4(k, seg, (int)((long long)pb.ny * part / nparts),
-                                          (int)((long long)pb.ny * (part + 1) / nparts)));
-    }
-    if (b->dtiles) cudaFree(b->dtiles);
-    b->dtiles = nullptr;
-    CUDA_TRY(cudaMalloc(&b->dtiles, sizeof(int4) * tiles.size()));
-    CUDA_TRY(cudaMemcpy(b->dtiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice));
-    b->tma.tiles = b->dtiles;
-    b->tma.gmaps = b->dmaps;
-    b->tma.ntiles = (int)tiles.size();
-    b->tma.nsegs = 1;
-    b->tma.nparts = 1;
-    return LBM_OK;
-}
-
 static lbm_status batch_build_schedule(lbm_stefan_batch* b, int tile_h, int schedule)
 {
     const int segw = lbm::d2q9_segment_width(b->precision);
@@ -1242,9 +1188,6 @@ static lbm_status batch_build_schedule(lbm_stefan_batch* b, int tile_h, int sche
     if (b->use_flat) {
         lbm_status s = batch_build_flat_tables(b, schedule);
         if (s != LBM_OK) return s;
-    } else if (b->use_tma) {
-        lbm_status s = batch_build_tma_tiles(b, tile_h, schedule);
-        if (s != LBM_OK) return s;
     }
     // persistent grid: as many blocks as fit on the GPU at once
     int dev = 0, sms = 0, per_sm = 0;
@@ -1276,8 +1219,7 @@ static cudaError_t batch_launch_one(lbm_stefan_batch* b, int parity)
         a.crows = b->dcrows;
         e = lbm::launch_d2q9_flat(a, b->nftiles, b->nwrows, b->ncblocks, 0, b->stream);
     } else {
-        e = b->use_tma ? lbm::launch_d2q9_tma(a, b->tma, b->stream)
-                       : lbm::launch_d2q9_step(b->precision, a, b->grid, b->stream);
+        e = lbm::launch_d2q9_step(b->precision, a, b->grid, b->stream);
     }
     if (e != cudaSuccess) return e;
     return lbm::launch_newton_jobs(b->precision, 9,
@@ -1352,8 +1294,7 @@ extern "C" lbm_status lbm_stefan_batch_create(int count, const lbm_stefan_proble
         b->hp[k].state[1] = base + sz;
         base += 2 * sz;
     }
-    if (precision == LBM_FP32) b->use_flat = LBM_FLAT != 0;
-    if (!b->use_flat && LBM_USE_TMA && precision == LBM_FP32) b->use_tma = batch_setup_tma(b);
+    b->use_flat = precision == LBM_FP32;
     cudaGetLastError();
     lbm_status s = batch_build_schedule(b, 16, 1);
     if (s != LBM_OK) {
@@ -1554,8 +1495,6 @@ extern "C" void lbm_stefan_batch_destroy(lbm_stefan_batch* b)
     cudaFree(b->dscratch);
     cudaFree(b->djobs);
     cudaFree(b->djob_count);
-    cudaFree(b->dmaps);
-    cudaFree(b->dtiles);
     cudaFree(b->dftiles);
     cudaFree(b->dwrows);
     cudaFree(b->dcrows);

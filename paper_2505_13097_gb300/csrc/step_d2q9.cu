@@ -653,24 +653,13 @@ __global__ void __launch_bounds__(kTmaThreads, LBM_TMA_MIN_BLOCKS) d2q9_tma_kern
     __shared__ __align__(8) unsigned long long full[kTmaStages];
     __shared__ __align__(8) unsigned long long empty[kTmaStages];
 
-    int pi, seg, ya, yb;
-    const CUtensorMap* lmap;
-    if (m.tiles) {
-        const int4 t = m.tiles[blockIdx.x];
-        pi = t.x;
-        seg = t.y;
-        ya = t.z;
-        yb = t.w;
-        lmap = &m.gmaps[2 * pi + a.parity];
-    } else {
-        pi = 0;
-        seg = blockIdx.x % m.nsegs;
-        const int part = blockIdx.x / m.nsegs;
-        const int nyp = a.probs[0].ny;
-        ya = (int)((long long)nyp * part / m.nparts);
-        yb = (int)((long long)nyp * (part + 1) / m.nparts);
-        lmap = &m.load[a.parity];
-    }
+    const int pi = 0;
+    const int seg = blockIdx.x % m.nsegs;
+    const int part = blockIdx.x / m.nsegs;
+    const int nyp = a.probs[0].ny;
+    const int ya = (int)((long long)nyp * part / m.nparts);
+    const int yb = (int)((long long)nyp * (part + 1) / m.nparts);
+    const CUtensorMap* lmap = &m.load[a.parity];
     const Problem& pb = a.probs[pi];
     DevStats* st = &a.stats[pb.stats];
     const int tid = threadIdx.x;
@@ -854,7 +843,7 @@ cudaError_t launch_d2q9_step(int precision, const StepArgs& a, int grid, cudaStr
 
 cudaError_t launch_d2q9_tma(const StepArgs& a, const TmaMaps& m, cudaStream_t s)
 {
-    const int grid = m.tiles ? m.ntiles : m.nsegs * m.nparts;
+    const int grid = m.nsegs * m.nparts;
     if (grid <= 0) return cudaErrorInvalidValue;
     if (a.rec) d2q9_tma_kernel<true><<<grid, kTmaThreads, 0, s>>>(a, m);
     else d2q9_tma_kernel<false><<<grid, kTmaThreads, 0, s>>>(a, m);
