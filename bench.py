@@ -42,10 +42,20 @@ BYTES_FP32 = 9 * 4 * 2   # algorithmic bytes per node update: each population re
 BYTES_FP64 = 9 * 8 * 2
 BYTES_D2Q5_FP32 = 5 * 4 * 2   # D2Q5: five populations
 BYTES_D2Q5_FP64 = 5 * 8 * 2
-# DRAM bytes (read + write) per interior node of one launch of the flat FP32 D2Q9
-# interior kernel, from an ncu capture (None until the current kernel has been captured)
-FLAT_TRAFFIC_PER_NODE = None
-FLAT_TRAFFIC_NOTE = "not captured for the current kernel yet"
+# DRAM bytes (read + write) per node of one launch of the flat FP32 D2Q9 kernel,
+# from an ncu capture of a smaller case scaled by the node count (None: not
+# captured since the kernel changed)
+FLAT_TRAFFIC_PER_NODE = 106955520 / 2086920
+FLAT_TRAFFIC_NOTE = ("ncu capture of one launch (left half of the strips) on the 2048^2 melting workload at "
+                     "step 301: 77.2 MB read + 29.7 MB written for 2,086,920 nodes, 51.3 B per node; writes "
+                     "still in L2 when the launch ends are written back during the next; scaled by nodes")
+
+
+def flat_nodes(nx, ny):
+    """Nodes of one step in the flat kernel: rows 1 .. ny-2 outside the W and E four-column groups."""
+    xe = max(4, ((nx - 1) >> 2) << 2)
+    cold = min(4, nx) + max(0, nx - xe)
+    return max(0, ny - 2) * (nx - cold)
 
 
 def log(*a):
@@ -163,7 +173,11 @@ def bench_single(torch, solver, case, steps, warmup, stream, barrier=None, centr
     ms = time_steps(torch, S, steps, stream)
     st = S.stats()
     # per-kernel device times (CUDA events between the two launches of a step)
-    st["kernel_ms"] = S.step_timed(min(steps, 50)) if case.lattice in (2, 3) else None
+    if case.lattice == 2 and case.precision == 1:
+        k0, k1, kf = S.step_timed(min(steps, 50), flat=True)
+        st["kernel_ms"], st["flat_ms"] = (k0, k1), kf
+    else:
+        st["kernel_ms"] = S.step_timed(min(steps, 50)) if case.lattice in (2, 3) else None
     S.close()
     return ms, st
 
@@ -612,10 +626,13 @@ def run_gpu(args):
     value = job_mlups(world, nodes, args.steps, ms_max)
     per_step_ms = ms / args.steps
     k_step_ms, k_job_ms = st["kernel_ms"]
-    # the dominant kernel: the flat kernel (two launches, the left and right halves),
-    # with the wall kernel and the left half's Newton solves beside it on a second
-    # stream: 72 algorithmic bytes per node update over the time to the join
-    achieved = BYTES_FP32 * nodes / (k_step_ms * 1e-3) / 1e9
+    # the dominant kernel: the flat kernel, two launches per step (the left and the
+    # right half of the strips), timed with events on the handle's stream around each
+    # launch (the wall kernel and the left half's Newton solves run beside the right
+    # half on a second stream); 72 algorithmic bytes per node it updates
+    fnodes = flat_nodes(case.nx, case.ny)
+    flat_launch_ms = st["flat_ms"] / 2
+    achieved = BYTES_FP32 * (fnodes / 2) / (flat_launch_ms * 1e-3) / 1e9
 
     extra = {}
     if rank == 0 and not args.quick:
@@ -672,18 +689,23 @@ def run_gpu(args):
                          "frac": achieved / peak,
                          # dram__bytes_read.sum + dram__bytes_write.sum of one launch of this kernel in an ncu
                          # capture, per launch at this node count (None: not captured since the kernel changed)
-                         "traffic": FLAT_TRAFFIC_PER_NODE * nodes if FLAT_TRAFFIC_PER_NODE else None,
+                         "traffic": FLAT_TRAFFIC_PER_NODE * fnodes / 2 if FLAT_TRAFFIC_PER_NODE else None,
                          "traffic_note": FLAT_TRAFFIC_NOTE,
-                         "bytes_per_node": BYTES_FP32, "units_per_launch": nodes,
-                         "kernel": "d2q9_flat_kernel<false,false> (two halves; d2q9_wall_kernel<false> and "
-                                   "newton_jobs_kernel<float,false,9> beside them)",
-                         "kernel_ms": k_step_ms,
-                         "launches_per_step": 5, "second_kernel": "newton_jobs_kernel<float,false,9>",
+                         "bytes_per_node": BYTES_FP32, "units_per_launch": fnodes / 2,
+                         "kernel": "d2q9_flat_kernel<false,false> (two launches per step: the left and the right "
+                                   "half of the strips; d2q9_wall_kernel<false> and the left half's "
+                                   "newton_jobs_kernel<float,false,9> beside the right half on a second stream)",
+                         "kernel_ms": flat_launch_ms,
+                         "launches_per_step": 5,
+                         "step_kernels_ms": k_step_ms,
+                         "second_kernel": "newton_jobs_kernel<float,false,9> (the right half's, after the join)",
                          "second_kernel_ms": k_job_ms,
                          "whole_step_gbs": BYTES_FP32 * nodes / (per_step_ms * 1e-3) / 1e9,
                          "whole_step_frac": BYTES_FP32 * nodes / (per_step_ms * 1e-3) / 1e9 / peak,
-                         "timing": "kernel_ms: CUDA events around each launch of 50 steps launched one by one, "
-                                   "right after the timed window",
+                         "timing": "kernel_ms: mean of the flat launches' CUDA-event times (on the handle's "
+                                   "stream) over 50 steps launched one by one right after the timed window; "
+                                   "step_kernels_ms: every launch but the last job launch, same steps; "
+                                   "whole_step: the timed window (graph replays)",
                          "peak_source": peak_kind},
             "error_vs_oracle": errs.get("melt_2d_fp32"),
             "cpu_baseline": cpu_baseline_sample(workloads) if (world == 1 and not args.no_cpu) else None,

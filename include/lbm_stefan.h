@@ -170,8 +170,10 @@ lbm_status lbm_stefan_step(lbm_stefan* h, int nsteps);
 /* D2Q9 and D2Q5: advance nsteps >= 1 steps launched one by one (no graph) with a
  * CUDA event before, between and after the kernels of each step, wait for
  * them, and return the mean device time per step of each kernel in ms:
- * ms_kernels[0] the stream/collide kernel (FP32 D2Q9: every launch of the
- * step but the last Newton launch), ms_kernels[1] the (last) Newton job kernel.  Same result as
+ * ms_kernels (3 doubles): [0] the stream/collide kernel (FP32 D2Q9: every
+ * launch of the step but the last Newton launch), [1] the (last) Newton job
+ * kernel, [2] FP32 D2Q9: the flat kernel's launches alone (events on the
+ * handle's stream around each; 0 for the other forms).  Same result as
  * lbm_stefan_step; for measuring each kernel against its roofline.
  * Synchronizes. */
 lbm_status lbm_stefan_step_timed(lbm_stefan* h, int nsteps, double* ms_kernels);

@@ -283,8 +283,10 @@ static cudaError_t launch_flat_final_jobs(lbm_stefan* h, const StepArgs& a);
 // half streams; the right half's solves follow the join and publish the
 // step.  The interior kernel does no FP64 work and the solves little else,
 // so a front band in the left half costs FP64 time beside HBM time.
-// final_jobs = false leaves out the last job launch (step_timed times it).
-static cudaError_t launch_flat(lbm_stefan* h, const StepArgs& a, bool final_jobs = true)
+// final_jobs = false leaves out the last job launch (step_timed times it);
+// fev (step_timed): four events recorded on the handle's stream before and
+// after the flat launches (left half, right half; one launch without a split).
+static cudaError_t launch_flat(lbm_stefan* h, const StepArgs& a, bool final_jobs = true, cudaEvent_t* fev = nullptr)
 {
     const int nsegs = h->hp.pitch / lbm::kTmaW;
     const int nbands = h->hp.ny > 2 ? (h->hp.ny + 7) / 8 : 0;
@@ -292,7 +294,13 @@ static cudaError_t launch_flat(lbm_stefan* h, const StepArgs& a, bool final_jobs
     const int half = nsegs / 2;
     cudaError_t e;
     if (!(h->side && half >= 1 && nbands > 0)) {
-        e = lbm::launch_d2q9_flat(a, nsegs * nbands, 2 * nsegs, ncblocks, h->hp.method, h->stream);
+        // the wall kernel, then the flat kernel
+        e = lbm::launch_d2q9_flat(a, 0, 2 * nsegs, ncblocks, h->hp.method, h->stream);
+        if (e == cudaSuccess && fev) e = cudaEventRecord(fev[0], h->stream);
+        if (e == cudaSuccess) e = lbm::launch_d2q9_flat(a, nsegs * nbands, 0, 0, h->hp.method, h->stream);
+        if (e == cudaSuccess && fev) e = cudaEventRecord(fev[1], h->stream);
+        if (e == cudaSuccess && fev) e = cudaEventRecord(fev[2], h->stream);
+        if (e == cudaSuccess && fev) e = cudaEventRecord(fev[3], h->stream);
         if (e != cudaSuccess || !final_jobs) return e;
         return lbm::launch_newton_jobs(1, 9, job_args(h->dprob, 1, a.parity, a.rec, h->dstats, h->dticket, h->djobs,
                                                       h->djob_count),
@@ -311,7 +319,9 @@ static cudaError_t launch_flat(lbm_stefan* h, const StepArgs& a, bool final_jobs
     StepArgs aa = a;   // list A: djobs, counter 0
     aa.seg0 = 0;
     aa.nsegc = half;
+    if (e == cudaSuccess && fev) e = cudaEventRecord(fev[0], h->stream);
     if (e == cudaSuccess) e = lbm::launch_d2q9_flat(aa, half * nbands, 0, 0, h->hp.method, h->stream);
+    if (e == cudaSuccess && fev) e = cudaEventRecord(fev[1], h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_half, h->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(h->side, h->ev_half, 0);
     if (e != cudaSuccess) return e;
@@ -325,7 +335,9 @@ static cudaError_t launch_flat(lbm_stefan* h, const StepArgs& a, bool final_jobs
     ab.job_count = h->djob_count + 1;
     ab.seg0 = half;
     ab.nsegc = nsegs - half;
-    e = lbm::launch_d2q9_flat(ab, (nsegs - half) * nbands, 0, 0, h->hp.method, h->stream);
+    if (fev) e = cudaEventRecord(fev[2], h->stream);
+    if (e == cudaSuccess) e = lbm::launch_d2q9_flat(ab, (nsegs - half) * nbands, 0, 0, h->hp.method, h->stream);
+    if (e == cudaSuccess && fev) e = cudaEventRecord(fev[3], h->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_join, 0);
     if (e != cudaSuccess || !final_jobs) return e;
     return launch_flat_final_jobs(h, a);
@@ -723,9 +735,11 @@ extern "C" lbm_status lbm_stefan_step_timed(lbm_stefan* h, int nsteps, double* m
     if (nsteps < 1) return fail(LBM_ERR_ARG, "nsteps must be >= 1");
     if (!h->ic) return fail(LBM_ERR_STATE, "set_ic must come before step_timed");
     std::vector<cudaEvent_t> ev(2 * (size_t)nsteps + 1, nullptr);
+    std::vector<cudaEvent_t> fev(h->flat ? 4 * (size_t)nsteps : 0, nullptr);   // around the flat launches
     lbm_status st = LBM_OK;
     cudaError_t e = cudaSuccess;
     for (size_t k = 0; k < ev.size() && e == cudaSuccess; ++k) e = cudaEventCreate(&ev[k]);
+    for (size_t k = 0; k < fev.size() && e == cudaSuccess; ++k) e = cudaEventCreate(&fev[k]);
     if (e == cudaSuccess) e = cudaEventRecord(ev[0], h->stream);
     for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
         StepArgs a = single_args(h, h->parity, nullptr);
@@ -733,7 +747,7 @@ extern "C" lbm_status lbm_stefan_step_timed(lbm_stefan* h, int nsteps, double* m
         if (h->p.lattice == LBM_D2Q5) {
             e = lbm::launch_d2q5_step(h->precision, a, h->stream);
         } else if (flat) {
-            e = launch_flat(h, a, false);
+            e = launch_flat(h, a, false, &fev[4 * (size_t)k]);
         } else if (h->use_tma) {
             e = lbm::launch_d2q9_tma(a, h->tma, h->stream);
         } else {
@@ -751,19 +765,28 @@ extern "C" lbm_status lbm_stefan_step_timed(lbm_stefan* h, int nsteps, double* m
         h->parity ^= 1;
     }
     if (e == cudaSuccess) e = cudaEventSynchronize(ev.back());
-    double t0 = 0.0, t1 = 0.0;
+    double t0 = 0.0, t1 = 0.0, t2 = 0.0;
     for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
         float a = 0.f, b = 0.f;
         e = cudaEventElapsedTime(&a, ev[2 * k], ev[2 * k + 1]);
         if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[2 * k + 1], ev[2 * k + 2]);
         t0 += a;
         t1 += b;
+        if (!fev.empty() && e == cudaSuccess) {
+            float c = 0.f, d = 0.f;
+            e = cudaEventElapsedTime(&c, fev[4 * (size_t)k], fev[4 * (size_t)k + 1]);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&d, fev[4 * (size_t)k + 2], fev[4 * (size_t)k + 3]);
+            t2 += (double)c + d;
+        }
     }
     for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
+    for (cudaEvent_t x : fev)
         if (x) cudaEventDestroy(x);
     if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "CUDA error: %s", cudaGetErrorString(e));
     ms_kernels[0] = t0 / nsteps;
     ms_kernels[1] = t1 / nsteps;
+    ms_kernels[2] = t2 / nsteps;
     return st;
 }
 

@@ -106,12 +106,13 @@ class Stefan:
                                                  la.ctypes.data_as(dp), lb.ctypes.data_as(dp)))
         return a.value, b.value, la, lb
 
-    def step_timed(self, nsteps):
+    def step_timed(self, nsteps, flat=False):
         """Advance nsteps D2Q9 or D2Q5 steps launch by launch; returns the mean device
-        time per step (ms) of the stream/collide kernel and of the job kernel."""
-        out = (ctypes.c_double * 2)()
+        time per step (ms) of the stream/collide kernel and of the job kernel, and
+        with flat=True also that of the FP32 D2Q9 flat kernel's launches."""
+        out = (ctypes.c_double * 3)()
         check(self.lib.lbm_stefan_step_timed(self.h, int(nsteps), ctypes.cast(out, ctypes.POINTER(ctypes.c_double))))
-        return out[0], out[1]
+        return (out[0], out[1], out[2]) if flat else (out[0], out[1])
 
     def set_wait_test(self, wait_limit_s=2.0, withhold_load=-1):
         """Test hook of the TMA row-pipeline kernel: bound of its waits on row

@@ -36,7 +36,7 @@ def bench(monkeypatch):
 
     monkeypatch.setattr(b, "ClockSampler", Clocks)
     monkeypatch.setattr(b, "bench_single",
-                        lambda *a, **k: (126.0, {"kernel_ms": (0.265, 0.0), "imbalance": 0.0, "newton_nodes": 5,
+                        lambda *a, **k: (126.0, {"kernel_ms": (0.265, 0.0), "flat_ms": 0.2, "imbalance": 0.0, "newton_nodes": 5,
                                                  "newton_iters": 11, "newton_max_iter": 3}))
     monkeypatch.setattr(b, "bench_e2e", lambda *a, **k: (130.0, 8 * 4096 * 4096, 8 * 4096 * 4096))
     monkeypatch.setattr(b, "oracle_errors",
@@ -59,7 +59,9 @@ def test_json_line_keys(bench, capsys):
     assert d["ms_per_step"] == pytest.approx(126.0 / 400)
     r = d["roofline"]
     assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["peak"] == 6795.1
-    assert r["achieved"] == pytest.approx(72 * 4096 * 4096 / 0.265e-3 / 1e9)
+    # the flat kernel: two launches of 0.1 ms, each over half of rows 1 .. 4094 outside the W / E groups
+    assert r["achieved"] == pytest.approx(72 * (4094 * 4088 / 2) / 0.1e-3 / 1e9)
+    assert r["units_per_launch"] == 4094 * 4088 / 2
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
     assert "workload" in d["config"] and d["gpu_launches"] == 5 * 400
     assert d["error_vs_oracle"]["max_rel_dtheta"] == 1e-7
