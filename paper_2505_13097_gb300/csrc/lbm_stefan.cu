@@ -140,6 +140,10 @@ struct lbm_stefan_batch {
     int nwrows = 0;
     int2* dcrows = nullptr;            // (problem, first row) per 32-row block of W / E groups
     int ncblocks = 0;
+    int nftiles_left = 0;              // the tiles of the problems' left halves come first
+    size_t total_nodes = 0;
+    cudaStream_t side = nullptr;       // split step (stream of its own): the left halves' Newton solves
+    cudaEvent_t ev_fork = nullptr, ev_half = nullptr, ev_join = nullptr;
     GraphCache graph;
 };
 
@@ -1137,16 +1141,28 @@ static lbm_status batch_build_flat_tables(lbm_stefan_batch* b, int schedule)
         std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
             return (long long)b->hp[x].nx * b->hp[x].ny > (long long)b->hp[y].nx * b->hp[y].ny;
         });
+    // every problem's left-half tiles (strips below max(1, nsegs / 2)), then the
+    // right-half tiles: the split step solves the first group's Newton nodes
+    // beside the second group's streaming
     std::vector<int4> tiles;
     std::vector<int2> rows, crows;
+    for (int side = 0; side < 2; ++side) {
+        for (int k : order) {
+            const Problem& pb = b->hp[k];
+            const int nsegs = pb.pitch / lbm::kTmaW;
+            const int half = std::max(1, nsegs / 2);
+            if (pb.ny > 2)
+                for (int y0 = 0; y0 < pb.ny - 1; y0 += 8)
+                    for (int seg = side ? half : 0; seg < (side ? nsegs : half); ++seg)
+                        tiles.push_back(make_int4(k, seg, y0, 0));
+        }
+        if (side == 0) b->nftiles_left = (int)tiles.size();
+    }
     for (int k : order) {
         const Problem& pb = b->hp[k];
         const int nsegs = pb.pitch / lbm::kTmaW;
-        if (pb.ny > 2) {
-            for (int y0 = 0; y0 < pb.ny - 1; y0 += 8)
-                for (int seg = 0; seg < nsegs; ++seg) tiles.push_back(make_int4(k, seg, y0, 0));
+        if (pb.ny > 2)
             for (int y0 = 1; y0 < pb.ny - 1; y0 += 32) crows.push_back(make_int2(k, y0));
-        }
         for (int seg = 0; seg < nsegs; ++seg) {
             rows.push_back(make_int2(k, 2 * seg));
             rows.push_back(make_int2(k, 2 * seg + 1));
@@ -1235,6 +1251,42 @@ static cudaError_t batch_launch_one(lbm_stefan_batch* b, int parity)
     a.jobs = b->djobs;
     a.job_count = b->djob_count;
     cudaError_t e;
+    if (b->use_flat && b->side) {
+        // as the single problem's split step: the wall kernels and then the
+        // Newton solves of the wall nodes and the left halves on the side stream
+        // (list A), beside the right halves' streaming (list B, after the join)
+        int least = 0, prio = 0, dev = 0, sms = 0;
+        e = cudaDeviceGetStreamPriorityRange(&least, &prio);
+        if (e == cudaSuccess) e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        a.ftiles = b->dftiles;
+        a.wrows = b->dwrows;
+        a.nwrows = b->nwrows;
+        a.crows = b->dcrows;
+        if (e == cudaSuccess) e = cudaEventRecord(b->ev_fork, b->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->ev_fork, 0);
+        if (e == cudaSuccess) e = lbm::launch_d2q9_flat(a, 0, b->nwrows, b->ncblocks, 0, b->side);
+        if (e == cudaSuccess) e = lbm::launch_d2q9_flat(a, b->nftiles_left, 0, 0, 0, b->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(b->ev_half, b->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->ev_half, 0);
+        if (e != cudaSuccess) return e;
+        lbm::JobArgs ja = job_args(b->dprobs, b->count, parity, nullptr, b->dstats, b->dticket, b->djobs, b->djob_count);
+        ja.publish = 0;
+        e = lbm::launch_newton_jobs(b->precision, 9, ja, b->side, sms, prio);
+        if (e == cudaSuccess) e = cudaEventRecord(b->ev_join, b->side);
+        if (e != cudaSuccess) return e;
+        StepArgs ab = a;
+        ab.ftiles = b->dftiles + b->nftiles_left;
+        ab.jobs = b->djobs + b->total_nodes;
+        ab.job_count = b->djob_count + 1;
+        e = lbm::launch_d2q9_flat(ab, b->nftiles - b->nftiles_left, 0, 0, 0, b->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_join, 0);
+        if (e != cudaSuccess) return e;
+        return lbm::launch_newton_jobs(b->precision, 9,
+                                       job_args(b->dprobs, b->count, parity, nullptr, b->dstats, b->dticket + 1,
+                                                ab.jobs, ab.job_count),
+                                       b->stream);
+    }
     if (b->use_flat) {
         a.ftiles = b->dftiles;
         a.wrows = b->dwrows;
@@ -1298,12 +1350,23 @@ extern "C" lbm_status lbm_stefan_batch_create(int count, const lbm_stefan_proble
     if (e == cudaSuccess) e = cudaMalloc(&b->dprobs, sizeof(Problem) * count);
     if (e == cudaSuccess) e = cudaMalloc(&b->dstats, sizeof(DevStats) * count);
     if (e == cudaSuccess) e = cudaMemset(b->dstats, 0, sizeof(DevStats) * count);
-    if (e == cudaSuccess) e = cudaMalloc(&b->dticket, sizeof(unsigned int));
-    if (e == cudaSuccess) e = cudaMemset(b->dticket, 0, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->dticket, 2 * sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(b->dticket, 0, 2 * sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMalloc(&b->dscratch, sizeof(double) * maxn);
-    if (e == cudaSuccess) e = cudaMalloc(&b->djobs, sizeof(lbm::NewtonJob) * total_nodes);
-    if (e == cudaSuccess) e = cudaMalloc(&b->djob_count, sizeof(unsigned int));
-    if (e == cudaSuccess) e = cudaMemset(b->djob_count, 0, sizeof(unsigned int));
+    // FP32 on a stream of its own: the split step, two job lists of total_nodes each
+    const bool split = precision == LBM_FP32 && LBM_SPLIT && b->stream != nullptr;
+    if (e == cudaSuccess && split) {
+        int least = 0, greatest = 0;
+        e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b->side, cudaStreamNonBlocking, greatest);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_half, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming);
+    }
+    b->total_nodes = total_nodes;
+    if (e == cudaSuccess) e = cudaMalloc(&b->djobs, sizeof(lbm::NewtonJob) * total_nodes * (split ? 2 : 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->djob_count, 2 * sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(b->djob_count, 0, 2 * sizeof(unsigned int));
     if (e != cudaSuccess) {
         lbm_stefan_batch_destroy(b);
         return fail(LBM_ERR_CUDA, "batch allocation failed: %s", cudaGetErrorString(e));
@@ -1359,7 +1422,7 @@ static lbm_status batch_capture(lbm_stefan_batch* b)
         if (g) cudaGraphDestroy(g);
         return fail(LBM_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
     }
-    e = cudaGraphInstantiate(&b->graph.exec, g, 0);
+    e = cudaGraphInstantiate(&b->graph.exec, g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
     b->graph.steps = kGraphSteps;
@@ -1521,6 +1584,10 @@ extern "C" void lbm_stefan_batch_destroy(lbm_stefan_batch* b)
     cudaFree(b->dftiles);
     cudaFree(b->dwrows);
     cudaFree(b->dcrows);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_half) cudaEventDestroy(b->ev_half);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
+    if (b->side) cudaStreamDestroy(b->side);
     delete b;
 }
 

@@ -526,67 +526,70 @@ __global__ void __launch_bounds__(256, LBM_FLAT_MINB) d2q9_flat_kernel(const Ste
     }
 }
 
-// The nodes the flat kernel leaves out, FP32.
-//  * Blocks [0, nrb): rows 0 and ny-1 (the S and N walls) of every
+// The nodes the flat kernel leaves out, FP32, in two kernels.
+//  * d2q9_wall_kernel: rows 0 and ny-1 (the S and N walls) of every
 //    128-column strip, one row per warp, the full row update (closures of
 //    Sec. 4.2, Newton hand-off, EEBM).  Row r: single problem, strip r / 2,
 //    row 0 or ny-1 by r % 2; batches: the table a.wrows, entry (problem,
-//    2 strip + (0: row 0, 1: row ny-1)).
-//  * Blocks [nrb, nrb + ncb): in rows 1 .. ny-2, the nodes of the four-column
+//    2 strip + (0: row 0, 1: row ny-1)).  Each warp adds its sums to its
+//    problem after each row.
+//  * d2q9_wall_cols_kernel: in rows 1 .. ny-2, the nodes of the four-column
 //    groups that hold column 0 or nx-1 or reach past nx, one node per thread
 //    (flat_cold_node): 32 rows per block, eight slots per row (x = 0 .. 3 and
 //    x = xe .. xe + 3, xe the group of column nx-1 when it is not the first).
-//    Single problem: block nrb + b takes rows 1 + 32 b ...; batches: the table
+//    Single problem: block b takes rows 1 + 32 b ...; batches: the table
 //    a.crows, entry (problem, first row).
-// Each warp adds its sums to its problem after each row (part 1) or at the
-// end (part 2).
 template <bool REC>
-__global__ void __launch_bounds__(256) d2q9_wall_kernel(const StepArgs a, int nrb)
+__global__ void __launch_bounds__(256) d2q9_wall_kernel(const StepArgs a)
 {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    if ((int)blockIdx.x < nrb) {
-        const int nrows = a.wrows ? a.nwrows : 2 * (a.probs[0].pitch / 128);
-        for (int r = blockIdx.x * 8 + warp; r < nrows; r += nrb * 8) {
-            int pi = 0, code = r;
-            if (a.wrows) {
-                const int2 e = a.wrows[r];
-                pi = e.x;
-                code = e.y;
-            }
-            const Problem& pb = a.probs[pi];
-            const int nx = pb.nx, ny = pb.ny;
-            const long long pl = pb.plane, pitch = pb.pitch;
-            const int seg = code >> 1;
-            const int y = (code & 1) ? ny - 1 : 0;
-            const float* __restrict__ src = static_cast<const float*>(pb.state[a.parity]);
-            float* __restrict__ dst = static_cast<float*>(pb.state[a.parity ^ 1]);
-            const float omc = (float)(1.0 - pb.omega);
-            const float om_f = (float)pb.omega;
-            const double omc_d = 1.0 - pb.omega;
-            const float wP[3] = {d2_wf(0), d2_wf(1), d2_wf(5)};
-            const float thr_f = (float)pb.sat;
-            const float sh = state_shift(pb, a.parity);   // stored values are Omega_i - w_i sh
-            Acc<float> acc;
-            TileSums ts;
-            GlobalJobSink sink{a.jobs, a.job_count};
-            const int x0 = seg * 128 + 4 * lane;
-            float u[9][4], qf[9][4];
-            flat_load_row(src + (y + 1) * pitch + x0, pitch, pl, u, qf);
-            const GlobalRowOut<float, 4> out{dst + (y + 1) * pitch + x0, pl};
-            if (pb.method == 1)
-                row_update_eebm<float, 4, REC, true>(pb, y, x0, qf, u[0], u[1], u[2], u[3], u[4], u[5], u[6], u[7],
-                                                     u[8], out, a.rec, acc, ts, omc, wP, nx, ny, sh);
-            else
-                row_update<float, 4, REC, true>(pb, y, x0, lane, qf, u[0], u[1], u[2], u[3], u[4], u[5], u[6], u[7],
-                                                u[8], out, a.rec, acc, ts, pi, sink, omc, om_f, omc_d, wP, thr_f, nx,
-                                                ny, sh);
-            flush_tile_sums<float>(acc, ts, &a.stats[pb.stats], lane);
+    const int nrows = a.wrows ? a.nwrows : 2 * (a.probs[0].pitch / 128);
+    for (int r = blockIdx.x * 8 + warp; r < nrows; r += gridDim.x * 8) {
+        int pi = 0, code = r;
+        if (a.wrows) {
+            const int2 e = a.wrows[r];
+            pi = e.x;
+            code = e.y;
         }
-        return;
+        const Problem& pb = a.probs[pi];
+        const int nx = pb.nx, ny = pb.ny;
+        const long long pl = pb.plane, pitch = pb.pitch;
+        const int seg = code >> 1;
+        const int y = (code & 1) ? ny - 1 : 0;
+        const float* __restrict__ src = static_cast<const float*>(pb.state[a.parity]);
+        float* __restrict__ dst = static_cast<float*>(pb.state[a.parity ^ 1]);
+        const float omc = (float)(1.0 - pb.omega);
+        const float om_f = (float)pb.omega;
+        const double omc_d = 1.0 - pb.omega;
+        const float wP[3] = {d2_wf(0), d2_wf(1), d2_wf(5)};
+        const float thr_f = (float)pb.sat;
+        const float sh = state_shift(pb, a.parity);   // stored values are Omega_i - w_i sh
+        Acc<float> acc;
+        TileSums ts;
+        GlobalJobSink sink{a.jobs, a.job_count};
+        const int x0 = seg * 128 + 4 * lane;
+        float u[9][4], qf[9][4];
+        flat_load_row(src + (y + 1) * pitch + x0, pitch, pl, u, qf);
+        const GlobalRowOut<float, 4> out{dst + (y + 1) * pitch + x0, pl};
+        if (pb.method == 1)
+            row_update_eebm<float, 4, REC, true>(pb, y, x0, qf, u[0], u[1], u[2], u[3], u[4], u[5], u[6], u[7],
+                                                 u[8], out, a.rec, acc, ts, omc, wP, nx, ny, sh);
+        else
+            row_update<float, 4, REC, true>(pb, y, x0, lane, qf, u[0], u[1], u[2], u[3], u[4], u[5], u[6], u[7],
+                                            u[8], out, a.rec, acc, ts, pi, sink, omc, om_f, omc_d, wP, thr_f, nx,
+                                            ny, sh);
+        flush_tile_sums<float>(acc, ts, &a.stats[pb.stats], lane);
     }
-    // part 2: the W and E groups of rows 1 .. ny-2
-    const int b = blockIdx.x - nrb;
+}
+
+// (one node per thread needs far fewer registers than the row update, so more
+// blocks fit on an SM than in the rows kernel)
+template <bool REC>
+__global__ void __launch_bounds__(256) d2q9_wall_cols_kernel(const StepArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const int b = blockIdx.x;
     int pi = 0, y0 = 1 + 32 * b;
     if (a.crows) {
         const int2 e = a.crows[b];
@@ -613,7 +616,6 @@ __global__ void __launch_bounds__(256) d2q9_wall_kernel(const StepArgs a, int nr
         if (cs.dir >= 0) ts.dir_count[cs.dir] += 1;
     }
     flush_tile_sums<float>(acc, ts, &a.stats[pb.stats], lane);
-    (void)warp;
 }
 
 // ---------------------------------------------------------------- TMA row pipeline
@@ -858,9 +860,15 @@ cudaError_t launch_d2q9_flat(const StepArgs& a, int nftiles, int nwrows, int ncb
     if (e != cudaSuccess) return e;
     // the nodes on or next to a wall (few), then rows 1 .. ny-2 of every strip
     const int nrb = std::min((nwrows + 7) / 8, sms * 4);
-    if (nrb + ncblocks > 0) {
-        if (a.rec) d2q9_wall_kernel<true><<<nrb + ncblocks, 256, 0, s>>>(a, nrb);
-        else d2q9_wall_kernel<false><<<nrb + ncblocks, 256, 0, s>>>(a, nrb);
+    if (nrb > 0) {
+        if (a.rec) d2q9_wall_kernel<true><<<nrb, 256, 0, s>>>(a);
+        else d2q9_wall_kernel<false><<<nrb, 256, 0, s>>>(a);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (ncblocks > 0) {
+        if (a.rec) d2q9_wall_cols_kernel<true><<<ncblocks, 256, 0, s>>>(a);
+        else d2q9_wall_cols_kernel<false><<<ncblocks, 256, 0, s>>>(a);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

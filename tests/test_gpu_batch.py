@@ -22,9 +22,11 @@ def small_batch(count=8, seed=5):
 
 
 @pytest.mark.parametrize("tile_h,schedule", [(16, 1), (8, 0), (64, 1), (5, 0)])
-def test_batch_matches_oracle(gpu, orc, tile_h, schedule):
+@pytest.mark.parametrize("own_stream", [False, True], ids=["legacy_stream", "own_stream"])
+def test_batch_matches_oracle(gpu, orc, tile_h, schedule, own_stream):
+    import torch
     cases = small_batch()
-    B = gpu.StefanBatch(cases)
+    B = gpu.StefanBatch(cases, stream=torch.cuda.Stream() if own_stream else None)
     B.set_schedule(tile_h, schedule)
     for k, c in enumerate(cases):
         B.set_ic(k, c.theta0())
@@ -82,3 +84,29 @@ def test_autotune_keeps_state(gpu):
         assert np.array_equal(ref.theta(k), B.theta(k))
     B.close()
     ref.close()
+
+
+def test_batch_split_step_equals_one_stream(gpu, orc):
+    """On a stream of its own an FP32 batch runs the split step (the left
+    halves' Newton solves on a second stream beside the right halves); it gives
+    the bits of the one-stream step, and the oracle's field."""
+    import torch
+    cases = workloads.batch_2d(count=6, lo=200, hi=600, seed=9)
+    cases = [c.scaled(theta_init=0.0, noise=0.2) for c in cases]   # mushy nodes in every strip
+    outs = []
+    for stream in (None, torch.cuda.Stream()):
+        B = gpu.StefanBatch(cases, stream=stream)
+        for k, c in enumerate(cases):
+            B.set_ic(k, c.theta0())
+        B.step(60)
+        outs.append(([B.theta(k) for k in range(len(cases))], [B.stats(k) for k in range(len(cases))]))
+        B.close()
+    for k in range(len(cases)):
+        assert np.array_equal(outs[0][0][k], outs[1][0][k]), k
+        assert outs[0][1][k]["energy"] == outs[1][1][k]["energy"], k
+        assert outs[1][1][k]["newton_nodes"] > 0
+    k = min(range(len(cases)), key=lambda j: cases[j].nx)
+    c = cases[k]
+    P = orc.Problem(2, c.nx, c.ny, tau=c.tau, delta=c.delta, ste=c.ste, walls=c.walls)
+    _, ref = P.run(c.theta0(), 60)
+    assert np.max(np.abs(outs[1][0][k] - ref)) / np.max(np.abs(ref)) < 2e-5
