@@ -79,6 +79,7 @@ struct Problem {
     // that a solve spends no FP64 instruction on them
     double inv_delta2, inv_delta3;
     float inv_ste_f, inv_delta_f, delta_f;
+    float omega_f, omc_f, sat_f;   // (float) omega, (float)(1 - omega), (float) sat
     int maxit;
     int bb_mode;
     int wall_kind[4];        // W, E, S, N
@@ -157,6 +158,17 @@ struct JobArgs {
     const NewtonJob* jobs;
     unsigned int* job_count;
     int publish;             // 1: the last block publishes the step statistics; 0: it only clears the list
+    // Two launches may share one list: with `cursor` set, each warp takes the
+    // next 32 jobs of `jobs` from that counter (atomicAdd), so a launch that
+    // starts late takes what an earlier one has not reached; without it the
+    // warps take the list grid-stride.  `jobs2` / `job_count2`: a second list
+    // that this launch alone solves (grid-stride) after the first.  `nblocks`:
+    // the blocks of every launch that shares `ticket` (0: this launch's grid);
+    // the last of them publishes and clears both lists and the cursor.
+    unsigned int* cursor = nullptr;
+    const NewtonJob* jobs2 = nullptr;
+    unsigned int* job_count2 = nullptr;
+    int nblocks = 0;
 };
 
 // Constants of the interior-node adjoint terms, converted once on the host.
@@ -198,7 +210,9 @@ cudaError_t launch_d2q9_tma(const StepArgs& a, const TmaMaps& m, cudaStream_t s)
 cudaError_t launch_d2q9_flat(const StepArgs& a, int nftiles, int nwrows, int ncblocks, int method, cudaStream_t s);
 int d2q9_tma_blocks_per_sm();
 // q = 9 or 5; grid 0: two blocks per SM; prio != 0: that scheduling priority
-cudaError_t launch_newton_jobs(int precision, int q, const JobArgs& a, cudaStream_t s, int grid = 0, int prio = 0);
+// side: 64-thread blocks (the launch beside the flat stencil kernel), else 256
+cudaError_t launch_newton_jobs(int precision, int q, const JobArgs& a, cudaStream_t s, int grid = 0, int prio = 0,
+                               bool side = false);
 
 // D2Q5 launchers (step_d2q5.cu): one tile per warp over a.nslots tiles
 cudaError_t launch_d2q5_step(int precision, const StepArgs& a, cudaStream_t s);

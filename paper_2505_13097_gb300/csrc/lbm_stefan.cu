@@ -211,6 +211,9 @@ static void fill_problem(Problem& pb, int q, int nx, int ny, int pitch, double t
     pb.inv_delta_f = (float)pb.inv_delta;
     pb.delta_f = (float)delta;
     pb.sat = saturation_threshold(precision, delta, ste);
+    pb.omega_f = (float)pb.omega;
+    pb.omc_f = (float)(1.0 - pb.omega);
+    pb.sat_f = (float)pb.sat;
     pb.maxit = maxit;
     pb.bb_mode = bb_mode;
     pb.tile_h = tile_h;
@@ -280,16 +283,45 @@ static size_t split_cap_a(const Problem& hp)
 static cudaError_t launch_flat_final_jobs(lbm_stefan* h, const StepArgs& a);
 
 // FP32 D2Q9 single-problem step: the nodes on or next to a wall (the wall
-// kernel), rows 1 .. ny-2 of every 128-column strip (the flat kernel), then
+// kernels), rows 1 .. ny-2 of every 128-column strip (the flat kernel), then
 // the Newton job kernel.  With a side stream the strips are cut into a left
-// and a right half: the Newton solves of the wall kernel's and the left
-// half's nodes run on the side stream (at a higher priority) while the right
-// half streams; the right half's solves follow the join and publish the
-// step.  The interior kernel does no FP64 work and the solves little else,
-// so a front band in the left half costs FP64 time beside HBM time.
-// final_jobs = false leaves out the last job launch (step_timed times it);
-// fev (step_timed): four events recorded on the handle's stream before and
-// after the flat launches (left half, right half; one launch without a split).
+// and a right half.  List A holds the Newton nodes of the wall kernels and of
+// the left half, list B those of the right half.  On the side stream, 64-thread
+// job blocks (one per SM, at a higher priority) take list A from a shared
+// cursor while the right half streams: they fit beside the flat kernel's three
+// blocks per SM.  After the right half, a full job launch takes what is left of
+// list A, then list B; the last block of the two launches publishes the step.
+// The side stream joins the main one at the end.  Which launch solves a node
+// does not change its result.
+// final_jobs = false leaves out the last job launch (step_timed times it) and
+// joins before it; fev (step_timed): four events recorded on the handle's
+// stream before and after the flat launches (left half, right half; one
+// launch without a split).
+static lbm::JobArgs split_jobs_first(const Problem* probs, int nprob, int parity, double* rec, DevStats* st,
+                                     unsigned int* ticket, lbm::NewtonJob* jobs, unsigned int* counts, int nblocks)
+{
+    lbm::JobArgs j = job_args(probs, nprob, parity, rec, st, ticket, jobs, counts);
+    j.cursor = counts + 2;
+    j.nblocks = nblocks;
+    return j;
+}
+
+static lbm::JobArgs split_jobs_last(const lbm::JobArgs& first, lbm::NewtonJob* jobs_b, unsigned int* counts)
+{
+    lbm::JobArgs j = first;
+    j.jobs2 = jobs_b;
+    j.job_count2 = counts + 1;
+    return j;
+}
+
+static int device_sms()
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    return sms;
+}
+
 static cudaError_t launch_flat(lbm_stefan* h, const StepArgs& a, bool final_jobs = true, cudaEvent_t* fev = nullptr)
 {
     const int nsegs = h->hp.pitch / lbm::kTmaW;
@@ -298,7 +330,7 @@ static cudaError_t launch_flat(lbm_stefan* h, const StepArgs& a, bool final_jobs
     const int half = nsegs / 2;
     cudaError_t e;
     if (!(h->side && half >= 1 && nbands > 0)) {
-        // the wall kernel, then the flat kernel
+        // the wall kernels, then the flat kernel
         e = lbm::launch_d2q9_flat(a, 0, 2 * nsegs, ncblocks, h->hp.method, h->stream);
         if (e == cudaSuccess && fev) e = cudaEventRecord(fev[0], h->stream);
         if (e == cudaSuccess) e = lbm::launch_d2q9_flat(a, nsegs * nbands, 0, 0, h->hp.method, h->stream);
@@ -310,13 +342,9 @@ static cudaError_t launch_flat(lbm_stefan* h, const StepArgs& a, bool final_jobs
                                                       h->djob_count),
                                        h->stream);
     }
-    // side: the wall kernel (beside the left half), then the left half's and
-    // its own Newton solves; main: the left half, the right half, the join,
-    // the right half's solves (which publish the step)
-    int least = 0, prio = 0, dev = 0, sms = 0;
-    e = cudaDeviceGetStreamPriorityRange(&least, &prio);
-    if (e == cudaSuccess) e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int least = 0, prio = 0;
+    const int sms = device_sms();
+    e = sms > 0 ? cudaDeviceGetStreamPriorityRange(&least, &prio) : cudaErrorInvalidDevice;
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_fork, h->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(h->side, h->ev_fork, 0);
     if (e == cudaSuccess) e = lbm::launch_d2q9_flat(a, 0, 2 * nsegs, ncblocks, h->hp.method, h->side);   // list A
@@ -329,9 +357,9 @@ static cudaError_t launch_flat(lbm_stefan* h, const StepArgs& a, bool final_jobs
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_half, h->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(h->side, h->ev_half, 0);
     if (e != cudaSuccess) return e;
-    lbm::JobArgs ja = job_args(h->dprob, 1, a.parity, a.rec, h->dstats, h->dticket, h->djobs, h->djob_count);
-    ja.publish = 0;
-    e = lbm::launch_newton_jobs(1, 9, ja, h->side, sms, prio);   // one block per SM beside the streaming blocks
+    const lbm::JobArgs ja =
+        split_jobs_first(h->dprob, 1, a.parity, a.rec, h->dstats, h->dticket, h->djobs, h->djob_count, 2 * sms);
+    e = lbm::launch_newton_jobs(1, 9, ja, h->side, sms, prio, true);
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_join, h->side);
     if (e != cudaSuccess) return e;
     StepArgs ab = a;   // list B: after list A, counter 1
@@ -342,9 +370,11 @@ static cudaError_t launch_flat(lbm_stefan* h, const StepArgs& a, bool final_jobs
     if (fev) e = cudaEventRecord(fev[2], h->stream);
     if (e == cudaSuccess) e = lbm::launch_d2q9_flat(ab, (nsegs - half) * nbands, 0, 0, h->hp.method, h->stream);
     if (e == cudaSuccess && fev) e = cudaEventRecord(fev[3], h->stream);
+    if (e != cudaSuccess) return e;
+    if (!final_jobs) return cudaStreamWaitEvent(h->stream, h->ev_join, 0);
+    e = launch_flat_final_jobs(h, a);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_join, 0);
-    if (e != cudaSuccess || !final_jobs) return e;
-    return launch_flat_final_jobs(h, a);
+    return e;
 }
 
 // The last job launch of a flat step (after launch_flat(h, a, false)).
@@ -352,17 +382,16 @@ static cudaError_t launch_flat_final_jobs(lbm_stefan* h, const StepArgs& a)
 {
     const int nsegs = h->hp.pitch / lbm::kTmaW;
     const bool split = h->side && nsegs / 2 >= 1 && h->hp.ny > 2;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // split: the right half's list, often short or empty: a smaller grid (its
-    // last-block ticket is one same-address atomic per block)
-    return lbm::launch_newton_jobs(1, 9,
-                                   split ? job_args(h->dprob, 1, a.parity, a.rec, h->dstats, h->dticket + 1,
-                                                    h->djobs + split_cap_a(h->hp), h->djob_count + 1)
-                                         : job_args(h->dprob, 1, a.parity, a.rec, h->dstats, h->dticket, h->djobs,
-                                                    h->djob_count),
-                                   h->stream, split ? sms : 0);
+    const int sms = device_sms();
+    if (sms <= 0) return cudaErrorInvalidDevice;
+    if (!split)
+        return lbm::launch_newton_jobs(1, 9, job_args(h->dprob, 1, a.parity, a.rec, h->dstats, h->dticket, h->djobs,
+                                                      h->djob_count),
+                                       h->stream);
+    const lbm::JobArgs ja =
+        split_jobs_first(h->dprob, 1, a.parity, a.rec, h->dstats, h->dticket, h->djobs, h->djob_count, 2 * sms);
+    return lbm::launch_newton_jobs(1, 9, split_jobs_last(ja, h->djobs + split_cap_a(h->hp), h->djob_count), h->stream,
+                                   sms);
 }
 
 // One step.  D2Q9 and D2Q5: the stream/collide kernel(s), which defer the
@@ -523,9 +552,9 @@ extern "C" lbm_status lbm_stefan_create(const lbm_stefan_params* p, void* cuda_s
     if (e == cudaSuccess) e = cudaMalloc(&h->dticket, 2 * sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMemset(h->dticket, 0, 2 * sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMalloc(&h->dscratch, sizeof(double) * 3 * (size_t)p->nx * p->ny);
-    if (e == cudaSuccess) e = cudaMalloc(&h->djob_count, 2 * sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMalloc(&h->djob_count, 3 * sizeof(unsigned int));   // lists A, B; cursor of A
     if (e == cudaSuccess && q == 9) h->adj_tile_h = adjoint_tile_h(h->hp);
-    if (e == cudaSuccess) e = cudaMemset(h->djob_count, 0, 2 * sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(h->djob_count, 0, 3 * sizeof(unsigned int));
     h->hp.state[0] = bufs[0];
     h->hp.state[1] = bufs[1];
     h->hp.stats = 0;
@@ -585,6 +614,7 @@ extern "C" lbm_status lbm_stefan_set_ste(lbm_stefan* h, double ste)
     h->hp.inv_ste = 1.0 / ste;
     h->hp.inv_ste_f = (float)h->hp.inv_ste;
     h->hp.sat = saturation_threshold(h->precision, h->hp.delta, ste);
+    h->hp.sat_f = (float)h->hp.sat;
     h->graph.reset();
     h->reset_seg_graphs();
     return upload_problem(h);
@@ -1252,13 +1282,13 @@ static cudaError_t batch_launch_one(lbm_stefan_batch* b, int parity)
     a.job_count = b->djob_count;
     cudaError_t e;
     if (b->use_flat && b->side) {
-        // as the single problem's split step: the wall kernels and then the
-        // Newton solves of the wall nodes and the left halves on the side stream
-        // (list A), beside the right halves' streaming (list B, after the join)
-        int least = 0, prio = 0, dev = 0, sms = 0;
-        e = cudaDeviceGetStreamPriorityRange(&least, &prio);
-        if (e == cudaSuccess) e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        // as the single problem's split step: the wall kernels, then the Newton
+        // solves of the wall nodes and the left halves (list A, shared cursor)
+        // in 64-thread blocks on the side stream beside the right halves'
+        // streaming; then a full job launch takes the rest of list A and list B
+        int least = 0, prio = 0;
+        const int sms = device_sms();
+        e = sms > 0 ? cudaDeviceGetStreamPriorityRange(&least, &prio) : cudaErrorInvalidDevice;
         a.ftiles = b->dftiles;
         a.wrows = b->dwrows;
         a.nwrows = b->nwrows;
@@ -1270,9 +1300,10 @@ static cudaError_t batch_launch_one(lbm_stefan_batch* b, int parity)
         if (e == cudaSuccess) e = cudaEventRecord(b->ev_half, b->stream);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->ev_half, 0);
         if (e != cudaSuccess) return e;
-        lbm::JobArgs ja = job_args(b->dprobs, b->count, parity, nullptr, b->dstats, b->dticket, b->djobs, b->djob_count);
-        ja.publish = 0;
-        e = lbm::launch_newton_jobs(b->precision, 9, ja, b->side, sms, prio);
+        const int gb = 2 * sms;
+        const lbm::JobArgs ja = split_jobs_first(b->dprobs, b->count, parity, nullptr, b->dstats, b->dticket, b->djobs,
+                                                 b->djob_count, sms + gb);
+        e = lbm::launch_newton_jobs(b->precision, 9, ja, b->side, sms, prio, true);
         if (e == cudaSuccess) e = cudaEventRecord(b->ev_join, b->side);
         if (e != cudaSuccess) return e;
         StepArgs ab = a;
@@ -1280,12 +1311,10 @@ static cudaError_t batch_launch_one(lbm_stefan_batch* b, int parity)
         ab.jobs = b->djobs + b->total_nodes;
         ab.job_count = b->djob_count + 1;
         e = lbm::launch_d2q9_flat(ab, b->nftiles - b->nftiles_left, 0, 0, 0, b->stream);
+        if (e == cudaSuccess)
+            e = lbm::launch_newton_jobs(b->precision, 9, split_jobs_last(ja, ab.jobs, b->djob_count), b->stream, gb);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_join, 0);
-        if (e != cudaSuccess) return e;
-        return lbm::launch_newton_jobs(b->precision, 9,
-                                       job_args(b->dprobs, b->count, parity, nullptr, b->dstats, b->dticket + 1,
-                                                ab.jobs, ab.job_count),
-                                       b->stream);
+        return e;
     }
     if (b->use_flat) {
         a.ftiles = b->dftiles;
@@ -1365,8 +1394,8 @@ extern "C" lbm_status lbm_stefan_batch_create(int count, const lbm_stefan_proble
     }
     b->total_nodes = total_nodes;
     if (e == cudaSuccess) e = cudaMalloc(&b->djobs, sizeof(lbm::NewtonJob) * total_nodes * (split ? 2 : 1));
-    if (e == cudaSuccess) e = cudaMalloc(&b->djob_count, 2 * sizeof(unsigned int));
-    if (e == cudaSuccess) e = cudaMemset(b->djob_count, 0, 2 * sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->djob_count, 3 * sizeof(unsigned int));   // lists A, B; cursor of A
+    if (e == cudaSuccess) e = cudaMemset(b->djob_count, 0, 3 * sizeof(unsigned int));
     if (e != cudaSuccess) {
         lbm_stefan_batch_destroy(b);
         return fail(LBM_ERR_CUDA, "batch allocation failed: %s", cudaGetErrorString(e));

@@ -460,10 +460,10 @@ __device__ __forceinline__ void d2q5_tile(const Problem& pb, const P* __restrict
     const bool seg_interior = has_left && has_right;   // no wall column, every node inside
     // problem constants, converted once per tile
     const P omc = (P)(1.0 - pb.omega);
-    const float om_f = (float)pb.omega;
+    const float om_f = pb.omega_f;
     const double omc_d = 1.0 - pb.omega;
     const P w0 = lat_wp<P>(5, 0), w1 = lat_wp<P>(5, 1);
-    const float thr_f = (float)pb.sat;
+    const float thr_f = pb.sat_f;
     const int ny = pb.ny;
 
     auto rp = [&](int i, int r) -> const P* { return src + i * pl + (long long)(r + 1) * pitch + x0; };

@@ -76,11 +76,11 @@ __device__ __forceinline__ void d2q9_tile_direct(const Problem& pb, const P* __r
     const bool has_right = segx + 32 * N < pb.nx;
     const bool seg_interior = has_left && has_right;   // no wall column, every node inside
     const P omc = (P)(1.0 - pb.omega);
-    const float om_f = (float)pb.omega;
+    const float om_f = pb.omega_f;
     const double omc_d = 1.0 - pb.omega;
     const int nx = pb.nx, ny = pb.ny;
     const P wP[3] = {lat_wp<P>(9, 0), lat_wp<P>(9, 1), lat_wp<P>(9, 5)};
-    const float thr_f = (float)pb.sat;
+    const float thr_f = pb.sat_f;
     // the state's shift (FP32 form; 0 in FP64)
     const float sh = sizeof(P) == 4 ? __ldg(reinterpret_cast<const float*>(reinterpret_cast<const char*>(src) + pb.tail_off))
                                     : 0.f;
@@ -290,7 +290,7 @@ __device__ __forceinline__ void flat_cold_node(const Problem& pb, int pi, const 
     }
     int wall = -1;
     if (x == 0 || x == pb.nx - 1) cs.flux = wall_closure_f(q, u, x, y, pb, wall, sh);
-    const float omc = (float)(1.0 - pb.omega);
+    const float omc = pb.omc_f;
     const float wP[3] = {d2_wf(0), d2_wf(1), d2_wf(5)};
     float* d = dst + at;
     if (pb.method == 1) {
@@ -315,7 +315,7 @@ __device__ __forceinline__ void flat_cold_node(const Problem& pb, int pi, const 
 #pragma unroll
     for (int i = 8; i >= 0; --i) mf += q[i];
     const float mt = mf + sh;
-    const float thr_f = (float)pb.sat;
+    const float thr_f = pb.sat_f;
     const float marg = 1e-5f * (1.0f + fabsf(tf));
     const bool sat_liq = tf >= thr_f + marg && mt >= thr_f + marg;
     const bool sat_sol = tf <= -thr_f - marg && mt <= -thr_f - marg;
@@ -331,7 +331,7 @@ __device__ __forceinline__ void flat_cold_node(const Problem& pb, int pi, const 
         cs.dir = wall;
         thn = pb.wall_theta[wall];
     } else if (sat_liq || sat_sol) {
-        c = (float)pb.omega * mf;
+        c = pb.omega_f * mf;
         cs.e = ff{mf, 0.f};
         cs.shifted = 1;
         cs.liquid = sat_liq ? 1 : 0;
@@ -391,7 +391,7 @@ __global__ void __launch_bounds__(256, LBM_FLAT_MINB) d2q9_flat_kernel(const Ste
         const long long pl = pb.plane, pitch = pb.pitch;
         const float* __restrict__ src = static_cast<const float*>(pb.state[a.parity]);
         float* __restrict__ dst = static_cast<float*>(pb.state[a.parity ^ 1]);
-        const float omc = (float)(1.0 - pb.omega);
+        const float omc = pb.omc_f;
         const float wP[3] = {d2_wf(0), d2_wf(1), d2_wf(5)};
         const float sh = state_shift(pb, a.parity);   // stored values are Omega_i - w_i sh
         const float* row = src + (y + 1) * pitch + x0;
@@ -434,8 +434,8 @@ __global__ void __launch_bounds__(256, LBM_FLAT_MINB) d2q9_flat_kernel(const Ste
             }
         } else {
             // interior IREBM nodes: the arithmetic of row_update's interior branch
-            const float om_f = (float)pb.omega;
-            const float thr_f = (float)pb.sat;
+            const float om_f = pb.omega_f;
+            const float thr_f = pb.sat_f;
             float c[4], esum = 0.f;   // the lane's energy terms, less the shift
             bool newton[4];
             bool any_newton = false;
@@ -559,11 +559,11 @@ __global__ void __launch_bounds__(256) d2q9_wall_kernel(const StepArgs a)
         const int y = (code & 1) ? ny - 1 : 0;
         const float* __restrict__ src = static_cast<const float*>(pb.state[a.parity]);
         float* __restrict__ dst = static_cast<float*>(pb.state[a.parity ^ 1]);
-        const float omc = (float)(1.0 - pb.omega);
-        const float om_f = (float)pb.omega;
+        const float omc = pb.omc_f;
+        const float om_f = pb.omega_f;
         const double omc_d = 1.0 - pb.omega;
         const float wP[3] = {d2_wf(0), d2_wf(1), d2_wf(5)};
-        const float thr_f = (float)pb.sat;
+        const float thr_f = pb.sat_f;
         const float sh = state_shift(pb, a.parity);   // stored values are Omega_i - w_i sh
         Acc<float> acc;
         TileSums ts;
@@ -709,11 +709,11 @@ __global__ void __launch_bounds__(kTmaThreads, LBM_TMA_MIN_BLOCKS) d2q9_tma_kern
 
     // ---- consumers
     const int x = segx + tid;
-    const float omc = (float)(1.0 - pb.omega);
-    const float om_f = (float)pb.omega;
+    const float omc = pb.omc_f;
+    const float om_f = pb.omega_f;
     const double omc_d = 1.0 - pb.omega;
     const float wP[3] = {d2_wf(0), d2_wf(1), d2_wf(5)};
-    const float thr_f = (float)pb.sat;
+    const float thr_f = pb.sat_f;
     const float sh = state_shift(pb, a.parity);   // stored values are Omega_i - w_i sh
     const int wx0 = segx + warp * 32;   // first column of this warp
     const bool warp_interior_x = wx0 > 0 && wx0 + 31 < nx - 1;
@@ -779,38 +779,77 @@ __global__ void __launch_bounds__(kTmaThreads, LBM_TMA_MIN_BLOCKS) d2q9_tma_kern
 // Threads per block of the job kernel.  Its last block is found with one
 // atomic ticket per block, and same-address atomics serialize in L2: with 1,216
 // blocks an empty job list still took 16 us, so the grid is kept small (two
-// blocks of 256 threads per SM; each warp takes jobs grid-stride).
+// blocks of 256 threads per SM; each warp takes jobs grid-stride or from a
+// shared cursor).  The FP32 form is held to 64 registers: a 64-thread block
+// (4,096 registers) then fits beside three blocks of the flat stencil kernel
+// (3 x 20,480), so the solves that run beside the streaming take no block
+// slot from it; a launch of 256-thread blocks runs the same code.
+#ifndef LBM_JOB_SIDE_WARPS
+#define LBM_JOB_SIDE_WARPS 2   // warps per block of the job launch beside the flat kernel (1: 80 registers)
+#endif
 constexpr int kJobThreads = 256;
+constexpr int kJobSideThreads = 32 * LBM_JOB_SIDE_WARPS;
+constexpr int kJobMinBlocksF = LBM_JOB_SIDE_WARPS == 2 ? 4 : 1;
+
+// One warp's 32 jobs from `base` of a list of `count` (lanes past the end idle).
+template <typename P, bool REC, int Q>
+__device__ __forceinline__ void newton_job_group(const JobArgs& a, const NewtonJob* jobs, unsigned base,
+                                                 unsigned count, int lane)
+{
+    const unsigned j = base + lane;
+    NewtonResult r;
+    if (j < count) {
+        const NewtonJob jb = jobs[j];
+        r = newton_job_apply<P, REC, Q>(jb, a.probs[jb.prob], a.parity, a.rec, a.stats);
+    }
+    newton_group_add(r, a.stats);
+}
 
 template <typename P, bool REC, int Q>
-__global__ void __launch_bounds__(kJobThreads) newton_jobs_kernel(JobArgs a)
+__global__ void __launch_bounds__(kJobThreads, sizeof(P) == 4 ? kJobMinBlocksF : 1) newton_jobs_kernel(JobArgs a)
 {
     const unsigned count = *reinterpret_cast<volatile unsigned*>(a.job_count);
     const int lane = threadIdx.x & 31;
     const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const unsigned nw = (gridDim.x * blockDim.x) >> 5;
-    for (unsigned base = gw * 32; base < count; base += nw * 32) {
-        const unsigned j = base + lane;
-        NewtonResult r;
-        if (j < count) {
-            const NewtonJob jb = a.jobs[j];
-            r = newton_job_apply<P, REC, Q>(jb, a.probs[jb.prob], a.parity, a.rec, a.stats);
+    if (a.cursor) {
+        // shared list: 32 jobs per take; a plain read first, so that a warp
+        // that finds the list taken issues no atomic
+        volatile unsigned* cur = a.cursor;
+        for (;;) {
+            unsigned base = 0;
+            if (lane == 0) {
+                base = *cur;
+                if (base < count) base = atomicAdd(a.cursor, 32u);
+            }
+            base = __shfl_sync(kFull, base, 0);
+            if (base >= count) break;
+            newton_job_group<P, REC, Q>(a, a.jobs, base, count, lane);
         }
-        newton_group_add(r, a.stats);
+    } else {
+        for (unsigned base = gw * 32; base < count; base += nw * 32)
+            newton_job_group<P, REC, Q>(a, a.jobs, base, count, lane);
     }
-    // last block: publish every problem's step statistics (if asked), clear the job list
+    if (a.jobs2) {
+        const unsigned count2 = *reinterpret_cast<volatile unsigned*>(a.job_count2);
+        for (unsigned base = gw * 32; base < count2; base += nw * 32)
+            newton_job_group<P, REC, Q>(a, a.jobs2, base, count2, lane);
+    }
+    // last block (of every launch sharing the ticket): publish every problem's
+    // step statistics (if asked), clear the job lists
     __shared__ bool last;
     __syncthreads();
     if (threadIdx.x == 0) {
+        const unsigned total = a.nblocks > 0 ? (unsigned)a.nblocks : gridDim.x;
         __threadfence();
-        last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
+        last = atomicAdd(a.ticket, 1u) == total - 1;
     }
     __syncthreads();
     if (last) {
         __threadfence();
         if (a.publish) {
-            const int nw = blockDim.x >> 5, w = threadIdx.x >> 5;
-            if (a.nprob <= nw) {
+            const int nwb = blockDim.x >> 5, w = threadIdx.x >> 5;
+            if (a.nprob <= nwb) {
                 // few problems: a warp each, one stripe per lane
                 if (w < a.nprob) publish_stats_warp(&a.stats[a.probs[w].stats], &a.probs[w], threadIdx.x & 31);
             } else {
@@ -822,6 +861,8 @@ __global__ void __launch_bounds__(kJobThreads) newton_jobs_kernel(JobArgs a)
         __syncthreads();
         if (threadIdx.x == 0) {
             *a.job_count = 0u;
+            if (a.cursor) *a.cursor = 0u;
+            if (a.job_count2) *a.job_count2 = 0u;
             *a.ticket = 0u;
         }
     }
@@ -896,7 +937,7 @@ int d2q9_tma_blocks_per_sm()
 }
 
 template <int Q>
-static cudaError_t launch_jobs_q(int precision, const JobArgs& a, int grid, cudaStream_t s, int prio)
+static cudaError_t launch_jobs_q(int precision, const JobArgs& a, int grid, cudaStream_t s, int prio, int threads)
 {
     void (*k)(JobArgs) = precision == 1
                              ? (a.rec ? newton_jobs_kernel<float, true, Q> : newton_jobs_kernel<float, false, Q>)
@@ -905,7 +946,7 @@ static cudaError_t launch_jobs_q(int precision, const JobArgs& a, int grid, cuda
     // captured from the stream keeps per kernel node
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3((unsigned)kJobThreads);
+    cfg.blockDim = dim3((unsigned)threads);
     cfg.stream = s;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributePriority;
@@ -915,16 +956,17 @@ static cudaError_t launch_jobs_q(int precision, const JobArgs& a, int grid, cuda
     return cudaLaunchKernelEx(&cfg, k, a);
 }
 
-cudaError_t launch_newton_jobs(int precision, int q, const JobArgs& a, cudaStream_t s, int grid, int prio)
+cudaError_t launch_newton_jobs(int precision, int q, const JobArgs& a, cudaStream_t s, int grid, int prio, bool side)
 {
+    const int threads = side ? kJobSideThreads : kJobThreads;
     if (grid <= 0) {
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         grid = sms * 2;
     }
-    if (q == 9) return launch_jobs_q<9>(precision, a, grid, s, prio);
-    if (q == 5) return launch_jobs_q<5>(precision, a, grid, s, prio);
+    if (q == 9) return launch_jobs_q<9>(precision, a, grid, s, prio, threads);
+    if (q == 5) return launch_jobs_q<5>(precision, a, grid, s, prio, threads);
     return cudaErrorInvalidValue;
 }
 
