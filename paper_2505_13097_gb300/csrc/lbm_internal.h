@@ -161,10 +161,12 @@ struct JobArgs {
     // Two launches may share one list: with `cursor` set, each warp takes the
     // next 32 jobs of `jobs` from that counter (atomicAdd), so a launch that
     // starts late takes what an earlier one has not reached; without it the
-    // warps take the list grid-stride.  `jobs2` / `job_count2`: a second list
-    // that this launch alone solves (grid-stride) after the first.  `nblocks`:
-    // the blocks of every launch that shares `ticket` (0: this launch's grid);
-    // the last of them publishes and clears both lists and the cursor.
+    // warps take the list grid-stride.  `jobs2`: a second list, counted by
+    // `job_count2`, that this launch alone solves (grid-stride) after the
+    // first; a launch with `job_count2` set but no `jobs2` leaves it to the
+    // other.  `nblocks`: the blocks of every launch that shares `ticket` (0:
+    // this launch's grid); the last of them publishes and clears both counts
+    // and the cursor (so each launch that shares the ticket carries both).
     unsigned int* cursor = nullptr;
     const NewtonJob* jobs2 = nullptr;
     unsigned int* job_count2 = nullptr;

@@ -302,15 +302,15 @@ static lbm::JobArgs split_jobs_first(const Problem* probs, int nprob, int parity
 {
     lbm::JobArgs j = job_args(probs, nprob, parity, rec, st, ticket, jobs, counts);
     j.cursor = counts + 2;
+    j.job_count2 = counts + 1;   // cleared by whichever launch ends last
     j.nblocks = nblocks;
     return j;
 }
 
-static lbm::JobArgs split_jobs_last(const lbm::JobArgs& first, lbm::NewtonJob* jobs_b, unsigned int* counts)
+static lbm::JobArgs split_jobs_last(const lbm::JobArgs& first, lbm::NewtonJob* jobs_b)
 {
     lbm::JobArgs j = first;
     j.jobs2 = jobs_b;
-    j.job_count2 = counts + 1;
     return j;
 }
 
@@ -390,7 +390,7 @@ static cudaError_t launch_flat_final_jobs(lbm_stefan* h, const StepArgs& a)
                                        h->stream);
     const lbm::JobArgs ja =
         split_jobs_first(h->dprob, 1, a.parity, a.rec, h->dstats, h->dticket, h->djobs, h->djob_count, 2 * sms);
-    return lbm::launch_newton_jobs(1, 9, split_jobs_last(ja, h->djobs + split_cap_a(h->hp), h->djob_count), h->stream,
+    return lbm::launch_newton_jobs(1, 9, split_jobs_last(ja, h->djobs + split_cap_a(h->hp)), h->stream,
                                    sms);
 }
 
@@ -1312,7 +1312,7 @@ static cudaError_t batch_launch_one(lbm_stefan_batch* b, int parity)
         ab.job_count = b->djob_count + 1;
         e = lbm::launch_d2q9_flat(ab, b->nftiles - b->nftiles_left, 0, 0, 0, b->stream);
         if (e == cudaSuccess)
-            e = lbm::launch_newton_jobs(b->precision, 9, split_jobs_last(ja, ab.jobs, b->djob_count), b->stream, gb);
+            e = lbm::launch_newton_jobs(b->precision, 9, split_jobs_last(ja, ab.jobs), b->stream, gb);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_join, 0);
         return e;
     }
