@@ -160,7 +160,9 @@ struct JobArgs {
     int publish;             // 1: the last block publishes the step statistics; 0: it only clears the list
     // Two launches may share one list: with `cursor` set, each warp takes the
     // next 32 jobs of `jobs` from that counter (atomicAdd), so a launch that
-    // starts late takes what an earlier one has not reached; without it the
+    // starts late takes what an earlier one has not reached (every launch that
+    // shares the cursor must start after the list is complete: a warp that
+    // read a shorter count would claim jobs it then skips); without it the
     // warps take the list grid-stride.  `jobs2`: a second list, counted by
     // `job_count2`, that this launch alone solves (grid-stride) after the
     // first; a launch with `job_count2` set but no `jobs2` leaves it to the

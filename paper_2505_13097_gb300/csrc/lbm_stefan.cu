@@ -92,6 +92,7 @@ struct lbm_stefan {
     int withhold_load = -1;            // test hook of the TMA kernel's row loads (-1: off)
     cudaStream_t side = nullptr;       // split FP32 D2Q9 step: stream of the left half's Newton solves
     cudaEvent_t ev_fork = nullptr, ev_half = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_walls = nullptr;   // split step: the wall kernels are done (list A's wall part is final)
     GraphCache graph;
     // captured adjoint segments (lbm_stefan_adjoint_segment): recompute + reverse
     // steps for one (length, trajectory, adjoint buffers) combination each
@@ -144,6 +145,7 @@ struct lbm_stefan_batch {
     size_t total_nodes = 0;
     cudaStream_t side = nullptr;       // split step (stream of its own): the left halves' Newton solves
     cudaEvent_t ev_fork = nullptr, ev_half = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_walls = nullptr;   // split step: the wall kernels are done (list A's wall part is final)
     GraphCache graph;
 };
 
@@ -290,7 +292,8 @@ static cudaError_t launch_flat_final_jobs(lbm_stefan* h, const StepArgs& a);
 // job blocks (one per SM, at a higher priority) take list A from a shared
 // cursor while the right half streams: they fit beside the flat kernel's three
 // blocks per SM.  After the right half, a full job launch takes what is left of
-// list A, then list B; the last block of the two launches publishes the step.
+// list A, then list B (it waits for the wall kernels, whose nodes are part of
+// list A); the last block of the two launches publishes the step.
 // The side stream joins the main one at the end.  Which launch solves a node
 // does not change its result.
 // final_jobs = false leaves out the last job launch (step_timed times it) and
@@ -348,6 +351,7 @@ static cudaError_t launch_flat(lbm_stefan* h, const StepArgs& a, bool final_jobs
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_fork, h->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(h->side, h->ev_fork, 0);
     if (e == cudaSuccess) e = lbm::launch_d2q9_flat(a, 0, 2 * nsegs, ncblocks, h->hp.method, h->side);   // list A
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_walls, h->side);
     StepArgs aa = a;   // list A: djobs, counter 0
     aa.seg0 = 0;
     aa.nsegc = half;
@@ -372,7 +376,10 @@ static cudaError_t launch_flat(lbm_stefan* h, const StepArgs& a, bool final_jobs
     if (e == cudaSuccess && fev) e = cudaEventRecord(fev[3], h->stream);
     if (e != cudaSuccess) return e;
     if (!final_jobs) return cudaStreamWaitEvent(h->stream, h->ev_join, 0);
-    e = launch_flat_final_jobs(h, a);
+    // the last job launch reads list A's count and takes the rest of it: the
+    // wall kernels (side stream) must have appended their nodes
+    e = cudaStreamWaitEvent(h->stream, h->ev_walls, 0);
+    if (e == cudaSuccess) e = launch_flat_final_jobs(h, a);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_join, 0);
     return e;
 }
@@ -569,6 +576,7 @@ extern "C" lbm_status lbm_stefan_create(const lbm_stefan_params* p, void* cuda_s
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_half, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_walls, cudaEventDisableTiming);
     }
     // the list of deferred Newton nodes (D2Q9, D2Q5): one job per node at most
     // (split FP32 step: two lists, the first with room for the wall kernel's
@@ -1148,6 +1156,7 @@ extern "C" void lbm_stefan_destroy(lbm_stefan* h)
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_half) cudaEventDestroy(h->ev_half);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->ev_walls) cudaEventDestroy(h->ev_walls);
     if (h->side) cudaStreamDestroy(h->side);
     cudaFree(h->dilf);
     cudaFree(h->dilf_scratch);
@@ -1296,6 +1305,7 @@ static cudaError_t batch_launch_one(lbm_stefan_batch* b, int parity)
         if (e == cudaSuccess) e = cudaEventRecord(b->ev_fork, b->stream);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->ev_fork, 0);
         if (e == cudaSuccess) e = lbm::launch_d2q9_flat(a, 0, b->nwrows, b->ncblocks, 0, b->side);
+        if (e == cudaSuccess) e = cudaEventRecord(b->ev_walls, b->side);
         if (e == cudaSuccess) e = lbm::launch_d2q9_flat(a, b->nftiles_left, 0, 0, 0, b->stream);
         if (e == cudaSuccess) e = cudaEventRecord(b->ev_half, b->stream);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->ev_half, 0);
@@ -1311,6 +1321,7 @@ static cudaError_t batch_launch_one(lbm_stefan_batch* b, int parity)
         ab.jobs = b->djobs + b->total_nodes;
         ab.job_count = b->djob_count + 1;
         e = lbm::launch_d2q9_flat(ab, b->nftiles - b->nftiles_left, 0, 0, 0, b->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_walls, 0);   // list A's wall nodes are in
         if (e == cudaSuccess)
             e = lbm::launch_newton_jobs(b->precision, 9, split_jobs_last(ja, ab.jobs), b->stream, gb);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_join, 0);
@@ -1391,6 +1402,7 @@ extern "C" lbm_status lbm_stefan_batch_create(int count, const lbm_stefan_proble
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_half, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_walls, cudaEventDisableTiming);
     }
     b->total_nodes = total_nodes;
     if (e == cudaSuccess) e = cudaMalloc(&b->djobs, sizeof(lbm::NewtonJob) * total_nodes * (split ? 2 : 1));
@@ -1616,6 +1628,7 @@ extern "C" void lbm_stefan_batch_destroy(lbm_stefan_batch* b)
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     if (b->ev_half) cudaEventDestroy(b->ev_half);
     if (b->ev_join) cudaEventDestroy(b->ev_join);
+    if (b->ev_walls) cudaEventDestroy(b->ev_walls);
     if (b->side) cudaStreamDestroy(b->side);
     delete b;
 }
