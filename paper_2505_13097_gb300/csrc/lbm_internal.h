@@ -214,7 +214,7 @@ cudaError_t launch_d2q9_tma(const StepArgs& a, const TmaMaps& m, cudaStream_t s)
 cudaError_t launch_d2q9_flat(const StepArgs& a, int nftiles, int nwrows, int ncblocks, int method, cudaStream_t s);
 int d2q9_tma_blocks_per_sm();
 // q = 9 or 5; grid 0: two blocks per SM; prio != 0: that scheduling priority
-// side: 64-thread blocks (the launch beside the flat stencil kernel), else 256
+// side: the launch beside the flat stencil kernel (kJobSideThreads per block), else 256
 cudaError_t launch_newton_jobs(int precision, int q, const JobArgs& a, cudaStream_t s, int grid = 0, int prio = 0,
                                bool side = false);
 

@@ -288,10 +288,9 @@ static cudaError_t launch_flat_final_jobs(lbm_stefan* h, const StepArgs& a);
 // kernels), rows 1 .. ny-2 of every 128-column strip (the flat kernel), then
 // the Newton job kernel.  With a side stream the strips are cut into a left
 // and a right half.  List A holds the Newton nodes of the wall kernels and of
-// the left half, list B those of the right half.  On the side stream, 64-thread
-// job blocks (one per SM, at a higher priority) take list A from a shared
-// cursor while the right half streams: they fit beside the flat kernel's three
-// blocks per SM.  After the right half, a full job launch takes what is left of
+// the left half, list B those of the right half.  On the side stream, job
+// blocks (one per SM, at a higher priority) take list A from a shared cursor
+// while the right half streams.  After the right half, a full job launch takes what is left of
 // list A, then list B (it waits for the wall kernels, whose nodes are part of
 // list A); the last block of the two launches publishes the step.
 // The side stream joins the main one at the end.  Which launch solves a node
@@ -1293,7 +1292,7 @@ static cudaError_t batch_launch_one(lbm_stefan_batch* b, int parity)
     if (b->use_flat && b->side) {
         // as the single problem's split step: the wall kernels, then the Newton
         // solves of the wall nodes and the left halves (list A, shared cursor)
-        // in 64-thread blocks on the side stream beside the right halves'
+        // on the side stream beside the right halves'
         // streaming; then a full job launch takes the rest of list A and list B
         int least = 0, prio = 0;
         const int sms = device_sms();

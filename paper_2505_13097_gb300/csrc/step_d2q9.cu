@@ -778,14 +778,15 @@ __global__ void __launch_bounds__(kTmaThreads, LBM_TMA_MIN_BLOCKS) d2q9_tma_kern
 // warp to finish publishes the step statistics and clears the job list.
 // Threads per block of the job kernel.  Its last block is found with one
 // atomic ticket per block, and same-address atomics serialize in L2: with 1,216
-// blocks an empty job list still took 16 us, so the grid is kept small (two
-// blocks of 256 threads per SM; each warp takes jobs grid-stride or from a
-// shared cursor).  The FP32 form is held to 64 registers: a 64-thread block
-// (4,096 registers) then fits beside three blocks of the flat stencil kernel
-// (3 x 20,480), so the solves that run beside the streaming take no block
-// slot from it; a launch of 256-thread blocks runs the same code.
+// blocks an empty job list still took 16 us, so the grid is kept small (one or
+// two blocks of 256 threads per SM; each warp takes jobs grid-stride or from a
+// shared cursor).  A solve is a chain of dependent FP64 operations: it needs
+// many warps per SM to keep the FP64 pipe busy.  Beside the flat kernel, 64-
+// thread blocks at 64 registers (which fit beside its three blocks per SM)
+// solved the front band of the 4096^2 melting workload at a third of the rate
+// of one 256-thread block per SM, and the step took 14 % longer.
 #ifndef LBM_JOB_SIDE_WARPS
-#define LBM_JOB_SIDE_WARPS 2   // warps per block of the job launch beside the flat kernel (1: 80 registers)
+#define LBM_JOB_SIDE_WARPS 8   // warps per block of the job launch beside the flat kernel
 #endif
 constexpr int kJobThreads = 256;
 constexpr int kJobSideThreads = 32 * LBM_JOB_SIDE_WARPS;
