@@ -216,6 +216,10 @@ static void fill_problem(Problem& pb, int q, int nx, int ny, int pitch, double t
     pb.omega_f = (float)pb.omega;
     pb.omc_f = (float)(1.0 - pb.omega);
     pb.sat_f = (float)pb.sat;
+    pb.inv_ste_lo = (float)(pb.inv_ste - (double)pb.inv_ste_f);
+    pb.inv_delta_lo = (float)(pb.inv_delta - (double)pb.inv_delta_f);
+    pb.omc_lo = (float)((1.0 - pb.omega) - (double)pb.omc_f);
+    pb.tol_ff = (float)std::max(tol, 1e-12);
     pb.maxit = maxit;
     pb.bb_mode = bb_mode;
     pb.tile_h = tile_h;
@@ -620,6 +624,7 @@ extern "C" lbm_status lbm_stefan_set_ste(lbm_stefan* h, double ste)
     h->hp.ste = ste;
     h->hp.inv_ste = 1.0 / ste;
     h->hp.inv_ste_f = (float)h->hp.inv_ste;
+    h->hp.inv_ste_lo = (float)(h->hp.inv_ste - (double)h->hp.inv_ste_f);
     h->hp.sat = saturation_threshold(h->precision, h->hp.delta, ste);
     h->hp.sat_f = (float)h->hp.sat;
     h->graph.reset();

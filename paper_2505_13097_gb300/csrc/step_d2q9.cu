@@ -768,9 +768,10 @@ __global__ void __launch_bounds__(kTmaThreads, LBM_TMA_MIN_BLOCKS) d2q9_tma_kern
 }
 
 // ---------------------------------------------------------------- Newton jobs
-// Local Newton solves deferred by the step kernel (Eq. 14, mixed-precision
-// form), one job per lane, consecutive jobs per warp; Q = 9 (D2Q9) or 5 (D2Q5)
-// planes.  For each job:
+// Local Newton solves deferred by the step kernel (Eq. 14; FP64 form: FP32
+// then FP64 steps, newton_mixed; FP32 form: FP32 then float-float steps,
+// newton_ff), one job per lane, consecutive jobs per warp; Q = 9 (D2Q9) or 5
+// (D2Q5) planes.  For each job:
 //   theta' = m0 + (phi(theta) - phi(root))/Ste,  c = theta' - (1-omega) m0,
 //   Omega~_i = (1-omega) q_i + w_i c   (q_i was stored by the step kernel).
 // Energy contributions theta' + phi(theta')/Ste are summed per problem as
@@ -784,13 +785,15 @@ __global__ void __launch_bounds__(kTmaThreads, LBM_TMA_MIN_BLOCKS) d2q9_tma_kern
 // many warps per SM to keep the FP64 pipe busy.  Beside the flat kernel, 64-
 // thread blocks at 64 registers (which fit beside its three blocks per SM)
 // solved the front band of the 4096^2 melting workload at a third of the rate
-// of one 256-thread block per SM, and the step took 14 % longer.
+// of one 256-thread block per SM, and the step took 14 % longer.  The FP32
+// form's kernel is held to 80 registers (three blocks per SM), so that its
+// block beside the flat kernel takes the place of one flat block, not two.
 #ifndef LBM_JOB_SIDE_WARPS
 #define LBM_JOB_SIDE_WARPS 8   // warps per block of the job launch beside the flat kernel
 #endif
 constexpr int kJobThreads = 256;
 constexpr int kJobSideThreads = 32 * LBM_JOB_SIDE_WARPS;
-constexpr int kJobMinBlocksF = LBM_JOB_SIDE_WARPS == 2 ? 4 : 1;
+constexpr int kJobMinBlocksF = LBM_JOB_SIDE_WARPS == 2 ? 4 : 3;
 
 // One warp's 32 jobs from `base` of a list of `count` (lanes past the end idle).
 template <typename P, bool REC, int Q>
