@@ -545,6 +545,20 @@ __device__ __forceinline__ void stripe_take(StepStripe* stripe, StatSums& s)
 // E = fixed-point sum + (liquid nodes + sum_w Dirichlet nodes of wall w * phi(theta_w)) / Ste.
 __device__ __forceinline__ void publish_totals(DevStats* st, const Problem* pb, const StatSums& s)
 {
+    // every input first, as independent L2 loads (ld.global.cg), so that the
+    // publication waits for about one memory round trip, not one per field
+    const int have = __ldcg(&st->have_energy);
+    const double e_old = __ldcg(&st->energy), imax = __ldcg(&st->imbalance_max);
+    const long long steps = __ldcg(&st->steps);
+    const int cmax = __ldcg(&st->cur_maxit);
+    double inv_ste = 0.0, wphi[4] = {0.0, 0.0, 0.0, 0.0};
+    float shift = 0.0f;
+    if (pb) {
+        inv_ste = pb->inv_ste;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) wphi[w] = pb->wall_phi[w];
+        if (s.shifted) shift = state_shift(*pb, 0);
+    }
     AccSum esum, fsum;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -553,30 +567,26 @@ __device__ __forceinline__ void publish_totals(DevStats* st, const Problem* pb, 
     }
     double e = acc_read(&esum);
     const double f = acc_read(&fsum);
-    volatile DevStats* v = st;
     if (pb) {
         double c = (double)s.liquid;
+#pragma unroll
         for (int w = 0; w < 4; ++w)
-            if (s.dir[w]) c += (double)s.dir[w] * pb->wall_phi[w];
-        e += c * pb->inv_ste;
-        if (s.shifted) e += (double)s.shifted * (double)state_shift(*pb, 0);
+            if (s.dir[w]) c += (double)s.dir[w] * wphi[w];
+        e += c * inv_ste;
+        if (s.shifted) e += (double)s.shifted * (double)shift;
     }
-    if (v->have_energy) {
-        double imb = e - v->energy - f;
-        v->imbalance = imb;
-        if (fabs(imb) > v->imbalance_max) v->imbalance_max = fabs(imb);
-    } else {
-        v->imbalance = 0.0;
-    }
-    v->energy_prev = v->energy;
-    v->energy = e;
-    v->flux = f;
-    v->have_energy = 1;
-    v->steps = v->steps + 1;
-    v->newton_nodes = (long long)s.newton;
-    v->newton_iters = (long long)s.iters;
-    v->newton_max_iter = v->cur_maxit;
-    v->cur_maxit = 0;
+    const double imb = have ? e - e_old - f : 0.0;
+    __stcg(&st->imbalance, imb);
+    if (have && fabs(imb) > imax) __stcg(&st->imbalance_max, fabs(imb));
+    __stcg(&st->energy_prev, e_old);
+    __stcg(&st->energy, e);
+    __stcg(&st->flux, f);
+    __stcg(&st->have_energy, 1);
+    __stcg(&st->steps, steps + 1);
+    __stcg(&st->newton_nodes, (long long)s.newton);
+    __stcg(&st->newton_iters, (long long)s.iters);
+    __stcg(&st->newton_max_iter, cmax);
+    __stcg(&st->cur_maxit, 0);
 }
 
 // Publish one problem's step statistics and clear its stripes (one thread of

@@ -812,7 +812,10 @@ __device__ __forceinline__ void newton_job_group(const JobArgs& a, const NewtonJ
 template <typename P, bool REC, int Q>
 __global__ void __launch_bounds__(kJobThreads, sizeof(P) == 4 ? kJobMinBlocksF : 1) newton_jobs_kernel(JobArgs a)
 {
+    // the counts (and the cursor) as independent loads, one round trip
     const unsigned count = *reinterpret_cast<volatile unsigned*>(a.job_count);
+    const unsigned count2 = a.jobs2 ? *reinterpret_cast<volatile unsigned*>(a.job_count2) : 0u;
+    unsigned cur0 = a.cursor ? *reinterpret_cast<volatile unsigned*>(a.cursor) : 0u;
     const int lane = threadIdx.x & 31;
     const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const unsigned nw = (gridDim.x * blockDim.x) >> 5;
@@ -820,10 +823,10 @@ __global__ void __launch_bounds__(kJobThreads, sizeof(P) == 4 ? kJobMinBlocksF :
         // shared list: 32 jobs per take; a plain read first, so that a warp
         // that finds the list taken issues no atomic
         volatile unsigned* cur = a.cursor;
-        for (;;) {
+        for (bool first = true;; first = false) {
             unsigned base = 0;
             if (lane == 0) {
-                base = *cur;
+                base = first ? cur0 : *cur;
                 if (base < count) base = atomicAdd(a.cursor, 32u);
             }
             base = __shfl_sync(kFull, base, 0);
@@ -835,7 +838,6 @@ __global__ void __launch_bounds__(kJobThreads, sizeof(P) == 4 ? kJobMinBlocksF :
             newton_job_group<P, REC, Q>(a, a.jobs, base, count, lane);
     }
     if (a.jobs2) {
-        const unsigned count2 = *reinterpret_cast<volatile unsigned*>(a.job_count2);
         for (unsigned base = gw * 32; base < count2; base += nw * 32)
             newton_job_group<P, REC, Q>(a, a.jobs2, base, count2, lane);
     }
