@@ -45,9 +45,9 @@ BYTES_D2Q5_FP64 = 5 * 8 * 2
 # DRAM bytes (read + write) per node of one launch of the flat FP32 D2Q9 kernel,
 # from an ncu capture of a smaller case scaled by the node count (None: not
 # captured since the kernel changed)
-FLAT_TRAFFIC_PER_NODE = 106955520 / 2086920
+FLAT_TRAFFIC_PER_NODE = (77219072 + 29094656) / 2086920
 FLAT_TRAFFIC_NOTE = ("ncu capture of one launch (left half of the strips) on the 2048^2 melting workload at "
-                     "step 301: 77.2 MB read + 29.7 MB written for 2,086,920 nodes, 51.3 B per node; writes "
+                     "step 301: 77.2 MB read + 29.1 MB written for 2,086,920 nodes, 50.9 B per node; writes "
                      "still in L2 when the launch ends are written back during the next; scaled by nodes")
 
 
@@ -693,12 +693,13 @@ def run_gpu(args):
                          "traffic_note": FLAT_TRAFFIC_NOTE,
                          "bytes_per_node": BYTES_FP32, "units_per_launch": fnodes / 2,
                          "kernel": "d2q9_flat_kernel<false,false> (two launches per step: the left and the right "
-                                   "half of the strips; d2q9_wall_kernel<false> and the left half's "
-                                   "newton_jobs_kernel<float,false,9> beside the right half on a second stream)",
+                                   "half of the strips; d2q9_wall_kernel<false>, d2q9_wall_cols_kernel<false> and "
+                                   "the left half's newton_jobs_kernel<float,false,9> on a second stream)",
                          "kernel_ms": flat_launch_ms,
-                         "launches_per_step": 5,
+                         "launches_per_step": 6,
                          "step_kernels_ms": k_step_ms,
-                         "second_kernel": "newton_jobs_kernel<float,false,9> (the right half's, after the join)",
+                         "second_kernel": "newton_jobs_kernel<float,false,9> (the last job launch: the rest of "
+                                          "the left half's list, the right half's, the publication)",
                          "second_kernel_ms": k_job_ms,
                          "whole_step_gbs": BYTES_FP32 * nodes / (per_step_ms * 1e-3) / 1e9,
                          "whole_step_frac": BYTES_FP32 * nodes / (per_step_ms * 1e-3) / 1e9 / peak,
@@ -714,7 +715,7 @@ def run_gpu(args):
                     "what": "lbm_stefan_set_state from a pinned host copy of the state at the start of the "
                             "headline's window (all populations), %d steps, lbm_stefan_get_fields to pinned host "
                             "theta; wall clock" % args.steps},
-            "gpu_launches": 5 * args.steps,   # two flat halves, wall kernel, two Newton launches
+            "gpu_launches": 6 * args.steps,   # two flat halves, two wall kernels, two Newton launches
             "clocks": clk.summary(),
             "energy_imbalance_last_step": st["imbalance"],
             "newton_nodes_last_step": st["newton_nodes"],

@@ -8,14 +8,14 @@
  * Algorithm 3 of the paper once per step: collision (Eq. 12), pull
  * streaming, the boundary closures of Sec. 4.2 on q, the zeroth moment, the
  * local Newton solve of Eq. (14), the source of Eq. (13), and the next
- * collision.  Kernel launches per step: D2Q9 with FP32 populations, three on
- * the legacy default stream (the nodes on or next to a wall, rows 1 .. ny-2
+ * collision.  Kernel launches per step: D2Q9 with FP32 populations, four on
+ * the legacy default stream (the nodes on or next to a wall in two, rows 1 .. ny-2
  * of every 128-column strip, then the kernel that solves the list of nodes
- * that need the Newton iteration and publishes the step), five on a stream of
+ * that need the Newton iteration and publishes the step), six on a stream of
  * the handle's own (rows 1 .. ny-2 of the left and of the right half of the
- * strips; on a second, higher-priority stream the wall nodes, then the
- * Newton solves of those and of the left half, beside the right half; then
- * the right half's solves);
+ * strips; on a second, higher-priority stream the S / N wall rows and the
+ * W / E wall groups, then Newton solves of those and of the left half beside
+ * the right half; then a launch that solves the rest and publishes the step);
  * D2Q9 in FP64 and D2Q5, two (the stream/collide kernel, which hands the
  * nodes that need the Newton iteration to a list, then the kernel that
  * solves that list); D1Q3, one launch for all the steps of a call.

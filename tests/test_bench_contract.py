@@ -63,7 +63,7 @@ def test_json_line_keys(bench, capsys):
     assert r["achieved"] == pytest.approx(72 * (4094 * 4088 / 2) / 0.1e-3 / 1e9)
     assert r["units_per_launch"] == 4094 * 4088 / 2
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
-    assert "workload" in d["config"] and d["gpu_launches"] == 5 * 400
+    assert "workload" in d["config"] and d["gpu_launches"] == 6 * 400
     assert d["error_vs_oracle"]["max_rel_dtheta"] == 1e-7
     assert d["newton_mean_iterations_last_step"] == pytest.approx(11 / 5)
     assert set(d["e2e"]) >= {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"}
