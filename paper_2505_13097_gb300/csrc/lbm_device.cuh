@@ -8,7 +8,6 @@
 #include <stdint.h>
 
 #include "lbm_internal.h"
-#include "ffmath.cuh"
 
 namespace lbm {
 
@@ -51,9 +50,11 @@ template <> __host__ __device__ constexpr float lat_wp<float>(int q, int i)
 template <> __host__ __device__ constexpr double lat_wp<double>(int q, int i) { return lat_w(q, i); }
 
 // ---------------------------------------------------------------- float-float
-// ff (ffmath.cuh): the unevaluated sum hi + lo of two floats.  ff_add: a
-// running sum that adds a float with Knuth's two_sum and collects the errors
-// in lo (no fast-math: the compiler keeps the order of operations).
+// Unevaluated sum hi + lo of two floats; two_sum is Knuth's error-free
+// transformation (no fast-math: the compiler keeps the order of operations).
+struct ff {
+    float hi, lo;
+};
 __device__ __forceinline__ void ff_add(ff& a, float b)
 {
     float s = __fadd_rn(a.hi, b);
@@ -170,17 +171,19 @@ __device__ __forceinline__ NewtonOut newton_solve(double m0, double theta, doubl
 //     1e-3 delta) falls back to newton_solve from theta.
 // The FP32 and derived constants come converted in the Problem: on this GPU
 // every FP64 instruction, conversions included, shares the narrow FP64 pipe.
-// FP32 stage of the mixed-precision solves: plain Newton (tanhf) inside the
-// bracket from x; it stops at FP32 precision or when the update no longer
-// halves (the FP32 rounding floor of F is reached).  Only an iterate that
-// leaves the bracket is replaced by the midpoint.  k: iterations taken.
-__device__ __forceinline__ float newton_stage32(float mf, float pf, float x, const Problem& pb, int& k)
+__device__ __forceinline__ NewtonOut newton_mixed(double m0, double theta, double phi_theta, const Problem& pb)
 {
-    const float isf = pb.inv_ste_f, idf = pb.inv_delta_f;
+    const double inv_ste = pb.inv_ste, inv_delta = pb.inv_delta, tol = pb.tol;
+    const int maxit = pb.maxit;
+    const float mf = (float)m0, pf = (float)phi_theta, isf = pb.inv_ste_f, idf = pb.inv_delta_f;
     float lo = mf + (pf - 1.0f) * isf, hi = mf + pf * isf;
+    float x = (float)theta;
     const float xfloor = pb.delta_f;
     float step_prev = hi - lo;
-    k = 0;
+    int k = 0;
+    // FP32 stage: plain Newton inside the bracket; it stops at FP32 precision or
+    // when the update no longer halves (the FP32 rounding floor of F is reached).
+    // Only an iterate that leaves the bracket is replaced by the midpoint.
     for (; k < 16; ++k) {
         const float t = tanhf(x * idf);
         const float F = (x - mf) + (0.5f * t + 0.5f - pf) * isf;
@@ -202,15 +205,6 @@ __device__ __forceinline__ float newton_stage32(float mf, float pf, float x, con
         }
         x = xn;
     }
-    return x;
-}
-
-__device__ __forceinline__ NewtonOut newton_mixed(double m0, double theta, double phi_theta, const Problem& pb)
-{
-    const double inv_ste = pb.inv_ste, inv_delta = pb.inv_delta, tol = pb.tol;
-    const int maxit = pb.maxit;
-    int k = 0;
-    const float x = newton_stage32((float)m0, (float)phi_theta, (float)theta, pb, k);
     const bool conv32 = isfinite(x);
     const double delta = pb.delta;
     if (conv32) {
@@ -253,86 +247,6 @@ __device__ __forceinline__ NewtonOut newton_mixed(double m0, double theta, doubl
     NewtonOut r = newton_solve(m0, theta, phi_theta, inv_ste, inv_delta, tol, maxit);
     r.iters += k;
     r.ok = r.ok && r.iters <= maxit;
-    return r;
-}
-
-// The FP32 form's solve: the FP32 stage, then float-float steps on the FP32
-// pipe (ffmath.cuh) instead of FP64 ones.  m0, theta and phi(theta) come as
-// float-float values.  At x (float-float), with phi and 1 - phi from ff_phi:
-//   F    = (x - m0) + (phi(x) - phi(theta))/Ste             (float-float)
-//   phi' = (2/delta) phi (1 - phi),  F' = 1 + phi'/Ste       (float-float)
-//   phi'' = (2/delta) phi' (1 - 2 phi),
-//   phi''' = (2/delta)(phi'' (1 - 2 phi) - 2 phi'^2)         (float)
-//   dn = -F/F' (float-float quotient); Halley's step d = dn / (1 + eps) with
-//   eps = dn F''/(2F'), as dn (1 - eps + eps^2) (the correction in float;
-//   |eps| <= |dn|/delta <= 3e-5 when accepted, so eps^3 is below 3e-14).
-// Accepted when the predicted error of theta', (F' - 1) C |dn|^3 with
-// C = F''^2/(4F'^2) + |F'''|/(6F') (Halley's cubic term), is below
-// 0.1 tol_ff max(1, |x|) and |d| <= 3e-5 delta; then phi(x + d) = phi(x) +
-// phi' d + phi'' d^2/2 + phi''' d^3/6 (phi' d in float-float, the rest in
-// float; the quartic remainder is below 1e-18).  tol_ff = max(tol, 1e-12):
-// float-float resolves F to about 2^-47 (|x - m0| + |phi(x) - phi(theta)|/Ste),
-// so a tighter tolerance would chase rounding.  From the FP32 start one step
-// is the rule; up to three are taken.  As in newton_mixed, no FP32
-// convergence or an update above 1e-3 delta falls back to the FP64
-// newton_solve from theta.
-struct NewtonFF {
-    ff root;
-    ff phi_root;
-    int iters;
-    bool ok;
-};
-
-__device__ __forceinline__ NewtonFF newton_ff(const ff& m0, const ff& theta, const ff& phi_theta, const Problem& pb)
-{
-    const ff idl{pb.inv_delta_f, pb.inv_delta_lo}, isl{pb.inv_ste_f, pb.inv_ste_lo};
-    const float isf = pb.inv_ste_f, two_id = 2.0f * pb.inv_delta_f;
-    const float tolf = pb.tol_ff, delta_f = pb.delta_f;
-    const int maxit = pb.maxit;
-    int k = 0;
-    const float x32 = newton_stage32(ff_float(m0), ff_float(phi_theta), ff_float(theta), pb, k);
-    NewtonFF r;
-    if (isfinite(x32)) {
-        ff x{x32, 0.0f};
-        for (int j = 0; j < 3; ++j) {
-            const PhiFF p = ff_phi(x, idl);
-            const ff F = ff_sum(ff_sum(x, ff_neg(m0)), ff_prod(ff_sum(p.phi, ff_neg(phi_theta)), isl));
-            const ff pp = ff_prod(p.phi, p.phic);                 // phi (1 - phi)
-            const ff d1 = ff_prod(ff{2.0f * pp.hi, 2.0f * pp.lo}, idl);   // phi' = 2 pp / delta
-            const ff Fp = ff_sum_f(ff_prod(d1, isl), 1.0f);
-            const ff dn = ff_neg(ff_quot(F, Fp));
-            const float adn = fabsf(dn.hi);
-            if (!(adn <= 1e-3f * delta_f)) break;   // FP32 start not close enough
-            const float om2 = p.phic.hi - p.phi.hi;                // 1 - 2 phi
-            const float d1f = d1.hi;
-            const float d2 = two_id * d1f * om2;                   // phi''
-            const float d3 = two_id * (d2 * om2 - 2.0f * d1f * d1f);   // phi'''
-            const float Fpf = Fp.hi;
-            const float eps = 0.5f * dn.hi * d2 * isf / Fpf;
-            const ff d = ff_sum_f(dn, -dn.hi * (eps - eps * eps));   // dn / (1 + eps) to second order
-            const float C = (0.25f * d2 * d2 * isf / Fpf + fabsf(d3) * (1.0f / 6.0f)) * isf / Fpf;
-            const float ad = fabsf(d.hi);
-            if (ad <= 3e-5f * delta_f && (Fpf - 1.0f) * C * adn * adn * adn <= 0.1f * tolf * fmaxf(1.0f, fabsf(x.hi))) {
-                const float dh = d.hi;
-                const float rest = dh * dh * (0.5f * d2 + dh * d3 * (1.0f / 6.0f));
-                r.root = ff_sum(x, d);
-                r.phi_root = ff_sum_f(ff_sum(p.phi, ff_prod(d1, d)), rest);
-                r.iters = k + j + 1;
-                r.ok = r.iters <= maxit;
-                return r;
-            }
-            x = ff_sum(x, d);
-        }
-    }
-    // fallback: the FP64 solve from theta
-    const double m0d = (double)m0.hi + (double)m0.lo, thd = (double)theta.hi + (double)theta.lo;
-    const double ptd = (double)phi_theta.hi + (double)phi_theta.lo;
-    const NewtonOut o = newton_solve(m0d, thd, ptd, pb.inv_ste, pb.inv_delta, pb.tol, maxit);
-    const float rh = (float)o.root, ph = (float)o.phi_root;
-    r.root = ff{rh, (float)(o.root - (double)rh)};
-    r.phi_root = ff{ph, (float)(o.phi_root - (double)ph)};
-    r.iters = o.iters + k;
-    r.ok = o.ok && r.iters <= maxit;
     return r;
 }
 

@@ -80,10 +80,6 @@ struct Problem {
     double inv_delta2, inv_delta3;
     float inv_ste_f, inv_delta_f, delta_f;
     float omega_f, omc_f, sat_f;   // (float) omega, (float)(1 - omega), (float) sat
-    // float-float constants of the FP32 form's Newton solves (hi + lo of the
-    // FP64 value) and its convergence floor max(tol, 1e-12)
-    float inv_ste_lo, inv_delta_lo, omc_lo;
-    float tol_ff;
     int maxit;
     int bb_mode;
     int wall_kind[4];        // W, E, S, N

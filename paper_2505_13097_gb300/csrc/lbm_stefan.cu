@@ -216,10 +216,6 @@ static void fill_problem(Problem& pb, int q, int nx, int ny, int pitch, double t
     pb.omega_f = (float)pb.omega;
     pb.omc_f = (float)(1.0 - pb.omega);
     pb.sat_f = (float)pb.sat;
-    pb.inv_ste_lo = (float)(pb.inv_ste - (double)pb.inv_ste_f);
-    pb.inv_delta_lo = (float)(pb.inv_delta - (double)pb.inv_delta_f);
-    pb.omc_lo = (float)((1.0 - pb.omega) - (double)pb.omc_f);
-    pb.tol_ff = (float)std::max(tol, 1e-12);
     pb.maxit = maxit;
     pb.bb_mode = bb_mode;
     pb.tile_h = tile_h;
@@ -293,7 +289,7 @@ static cudaError_t launch_flat_final_jobs(lbm_stefan* h, const StepArgs& a);
 // the Newton job kernel.  With a side stream the strips are cut into a left
 // and a right half.  List A holds the Newton nodes of the wall kernels and of
 // the left half, list B those of the right half.  On the side stream, job
-// blocks (one per two SMs, at a higher priority) take list A from a shared cursor
+// blocks (one per SM, at a higher priority) take list A from a shared cursor
 // while the right half streams.  After the right half, a full job launch takes what is left of
 // list A, then list B (it waits for the wall kernels, whose nodes are part of
 // list A); the last block of the two launches publishes the step.
@@ -320,12 +316,12 @@ static lbm::JobArgs split_jobs_last(const lbm::JobArgs& first, lbm::NewtonJob* j
     return j;
 }
 
-// Blocks of the single problem's side Newton launch: one per two SMs.  Each
-// takes the place of one of the flat kernel's three blocks on its SM while it
-// runs; measured at step 5,000 of the 4096^2 melting workload: 0.2320 ms per
-// step against 0.2345 with one block per SM and 0.2380 with two (the last job
-// launch solves what the side launch has not reached).
-static int split_side_blocks(int sms) { return sms / 2 > 0 ? sms / 2 : 1; }
+// Blocks of the single problem's side Newton launch: one per SM.  Each takes
+// the place of one of the flat kernel's three blocks on its SM while it runs;
+// the FP64 refinement of the solves keeps the band's work on the FP64 pipe, so
+// fewer side blocks would leave more of list A to the last job launch, after
+// the streaming.
+static int split_side_blocks(int sms) { return sms > 0 ? sms : 1; }
 
 static int device_sms()
 {
@@ -633,7 +629,6 @@ extern "C" lbm_status lbm_stefan_set_ste(lbm_stefan* h, double ste)
     h->hp.ste = ste;
     h->hp.inv_ste = 1.0 / ste;
     h->hp.inv_ste_f = (float)h->hp.inv_ste;
-    h->hp.inv_ste_lo = (float)(h->hp.inv_ste - (double)h->hp.inv_ste_f);
     h->hp.sat = saturation_threshold(h->precision, h->hp.delta, ste);
     h->hp.sat_f = (float)h->hp.sat;
     h->graph.reset();

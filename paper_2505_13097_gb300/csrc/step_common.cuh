@@ -205,13 +205,12 @@ __device__ __forceinline__ NewtonResult newton_job_apply(const NewtonJob& jb, co
     P qv[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) qv[i] = __ldcg(d + i * pb.plane);
+    double m0, th, sh = 0.0;
     if constexpr (sizeof(P) == 4) {
         // FP32 form: the job carries only the node; m0 = M0(q) from the stored
         // unrelaxed q_i and theta = M0(f) = sum of the node's Omega_i(t) (the
-        // step's source state), both as float-float sums in the order the step
-        // kernel uses (last plane first), plus the state's shift s; the solve
-        // and theta' in float-float (newton_ff), no FP64 instruction unless
-        // the solve falls back
+        // step's source state), both as float-float sums in the order the
+        // step kernel uses (last plane first), plus the state's shift s
         const P* sv = static_cast<const P*>(pb.state[parity]) + at;
         ff mm{0.f, 0.f}, t{0.f, 0.f};
 #pragma unroll
@@ -219,51 +218,30 @@ __device__ __forceinline__ NewtonResult newton_job_apply(const NewtonJob& jb, co
             ff_add(t, __ldg(sv + i * pb.plane));
             ff_add(mm, qv[i]);
         }
-        const float sh = state_shift(pb, parity);
-        const ff mq = fast_two_sum(mm.hi, mm.lo);   // M0(q) - s
-        const ff m0 = ff_sum_f(mq, sh);
-        const ff th = ff_sum_f(fast_two_sum(t.hi, t.lo), sh);
-        const ff isl{pb.inv_ste_f, pb.inv_ste_lo};
-        const ff pth = ff_phi(th, ff{pb.inv_delta_f, pb.inv_delta_lo}).phi;
-        const NewtonFF nr = newton_ff(m0, th, pth, pb);
-        if (!nr.ok || !isfinite(nr.root.hi)) atomicCAS(&stats[r.sidx].error, 0, 3);
-        // theta' = m0 + (phi(theta) - phi(root))/Ste
-        const ff tn = ff_sum(m0, ff_prod(ff_sum(pth, ff_neg(nr.phi_root)), isl));
-        // c = theta' - (1-omega) m0; stored values less w_i s: c - omega s =
-        // (theta' - s) - (1-omega)(m0 - s)
-        const float c = ff_float(ff_sum(ff_sum_f(tn, -sh), ff_neg(ff_prod(ff{pb.omc_f, pb.omc_lo}, mq))));
-        const P omc = pb.omc_f;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const P wi = lat_wp<P>(Q, i);
-            d[i * pb.plane] = fma(omc, qv[i], wi * c);
-        }
-        if (REC) rec[(long long)y * pb.pitch + x] = (double)tn.hi + (double)tn.lo;
-        // energy term theta' + phi(theta')/Ste as an exact fixed-point sum of
-        // its two floats
-        const ff en = ff_sum(tn, ff_prod(nr.phi_root, isl));
-        r.e = float_to_fixed(en.hi);
-        fx_add(r.e, float_to_fixed(en.lo));
-        r.it = nr.iters;
-        return r;
+        sh = (double)state_shift(pb, parity);
+        m0 = ff_to_double(mm) + sh;
+        th = ff_to_double(t) + sh;
     } else {
-        const double m0 = jb.m0, th = jb.theta;
-        const double pth = phi_of(th, pb.inv_delta);
-        const NewtonOut nr = newton_mixed(m0, th, pth, pb);
-        if (!nr.ok || !isfinite(nr.root)) atomicCAS(&stats[r.sidx].error, 0, 3);
-        const double tn = m0 + (pth - nr.phi_root) * pb.inv_ste;
-        const P c = (P)(tn - (1.0 - pb.omega) * m0);
-        const P omc = (P)(1.0 - pb.omega);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const P wi = lat_wp<P>(Q, i);
-            d[i * pb.plane] = fma(omc, qv[i], wi * c);
-        }
-        if (REC) rec[(long long)y * pb.pitch + x] = tn;
-        r.e = to_fixed(tn + nr.phi_root * pb.inv_ste);
-        r.it = nr.iters;
-        return r;
+        m0 = jb.m0;
+        th = jb.theta;
     }
+    const double pth = phi_of(th, pb.inv_delta);
+    const NewtonOut nr = newton_mixed(m0, th, pth, pb);
+    if (!nr.ok || !isfinite(nr.root)) atomicCAS(&stats[r.sidx].error, 0, 3);
+    const double tn = m0 + (pth - nr.phi_root) * pb.inv_ste;
+    // c = theta' - (1-omega) m0; stored values less w_i s: c - omega s
+    const P c = (P)((tn - sh) - (1.0 - pb.omega) * (m0 - sh));
+    const P omc = (P)(1.0 - pb.omega);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const P wi = lat_wp<P>(Q, i);
+        d[i * pb.plane] = fma(omc, qv[i], wi * c);
+    }
+    (void)x;
+    if (REC) rec[(long long)y * pb.pitch + x] = tn;
+    r.e = to_fixed(tn + nr.phi_root * pb.inv_ste);
+    r.it = nr.iters;
+    return r;
 }
 
 // The warp's results, grouped by problem: the lowest lane of each group sums

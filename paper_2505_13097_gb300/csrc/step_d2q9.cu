@@ -768,10 +768,9 @@ __global__ void __launch_bounds__(kTmaThreads, LBM_TMA_MIN_BLOCKS) d2q9_tma_kern
 }
 
 // ---------------------------------------------------------------- Newton jobs
-// Local Newton solves deferred by the step kernel (Eq. 14; FP64 form: FP32
-// then FP64 steps, newton_mixed; FP32 form: FP32 then float-float steps,
-// newton_ff), one job per lane, consecutive jobs per warp; Q = 9 (D2Q9) or 5
-// (D2Q5) planes.  For each job:
+// Local Newton solves deferred by the step kernel (Eq. 14, mixed-precision
+// form: FP32 then FP64 steps, newton_mixed), one job per lane, consecutive jobs
+// per warp; Q = 9 (D2Q9) or 5 (D2Q5) planes.  For each job:
 //   theta' = m0 + (phi(theta) - phi(root))/Ste,  c = theta' - (1-omega) m0,
 //   Omega~_i = (1-omega) q_i + w_i c   (q_i was stored by the step kernel).
 // Energy contributions theta' + phi(theta')/Ste are summed per problem as
