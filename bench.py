@@ -283,7 +283,7 @@ def bench_batch(torch, solver, workloads, steps, warmup, stream, count=256, hi=1
 
 
 def bench_adjoint(torch, solver, workloads, stream, n=1024, repeats=3):
-    """n^2, 2,000 steps, FP32 forward with float-float Newton, sqrt(T) checkpoints.
+    """n^2, 2,000 steps, FP32 forward with FP64 Newton, sqrt(T) checkpoints.
     One untimed forward + backward first creates the run's handle, checkpoint
     buffers and CUDA graphs; then `repeats` forward and backward passes are
     timed (wall clock between device synchronizations) and their medians
@@ -677,9 +677,9 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "dtype_detail": "FP32 populations and relaxation, FP32 m0 at saturated nodes, float-float moments at Newton and Dirichlet nodes, Newton refinement and theta' in float-float, fixed-point energy sums",
+            "dtype_detail": "FP32 populations and relaxation, FP32 m0 at saturated nodes, float-float moments at Newton and Dirichlet nodes, FP64 Newton refinement, fixed-point energy sums",
             "data": "synthetic",
-            "config": {"workload": "%s: D2Q9 %dx%d, FP32 populations with float-float Newton, west wall +1, other "
+            "config": {"workload": "%s: D2Q9 %dx%d, FP32 populations with FP64 Newton, west wall +1, other "
                                    "walls adiabatic, Ste 0.1, delta 0.01, tau 1.0, theta0 -0.2 + U(+-1e-3) seed 0; "
                                    "timed window centred on step %d of the 10,000-step job"
                                    % (case.name, case.nx, case.ny,

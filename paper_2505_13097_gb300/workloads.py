@@ -8,7 +8,7 @@ benchmark configurations:
 
 * ``melt_1d``        D1Q3, 512 nodes on [0,1], FP64, solid at -0.5, hot wall +1 on
                      the west, adiabatic east, Ste 0.1, delta 0.01, 20,000 steps;
-* ``melt_2d``        D2Q9 4096 x 4096, FP32 populations / float-float Newton, -0.2 plus
+* ``melt_2d``        D2Q9 4096 x 4096, FP32 populations / FP64 Newton, -0.2 plus
                      uniform noise of amplitude 1e-3 (seed 0), west wall +1, other
                      walls adiabatic, Ste 0.1, delta 0.01, 10,000 steps;
 * ``corner_2d``      D2Q9 2048 x 2048, FP64, liquid at +0.3, south and west walls
