@@ -292,11 +292,13 @@ void lbm_stefan_destroy(lbm_stefan* h);
  * Many independent D2Q9 problems of uneven sizes advanced by kernel launches
  * over all problems at once, then the Newton job kernel; the launches of a
  * call are captured in a CUDA graph.  FP32: the kernels of the single-problem
- * FP32 step over tables (the S and N wall rows of every problem, then one
- * block per 128-column x 8-row tile of every problem); FP64: the persistent
- * warp-tile kernel over a schedule of warp tiles.  The order of the problems
- * (and, in FP64, the tile height) come from lbm_stefan_batch_autotune (or
- * defaults). */
+ * FP32 step over tables (the S and N wall rows and the W and E wall groups of
+ * every problem, one block per 128-column x 8-row tile of every problem); on
+ * a stream of the batch's own, the single problem's split step (the left
+ * halves' Newton solves beside the right halves' streaming on a second
+ * stream); FP64: the persistent warp-tile kernel over a schedule of warp
+ * tiles.  The order of the problems (and, in FP64, the tile height) come from
+ * lbm_stefan_batch_autotune (or defaults). */
 
 typedef struct {
     int nx, ny;                 /* >= 2 each */
